@@ -1,0 +1,360 @@
+"""ctypes binding of the FP64 CPU oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg use it; the CUDA product path never does.
+
+Every function mirrors one step of the method; see the comments in oracle.c for
+the passage of the paper each step follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so in-tree (gcc, -ffp-contract=off: no fused multiply-add)."""
+    stale = (not os.path.exists(_LIB)
+             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Opts(C.Structure):
+    _fields_ = [("theta_color", C.c_double), ("theta_amg", C.c_double), ("mu", C.c_int),
+                ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
+                ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("setup_called", C.c_int),
+                ("setup_count", C.c_int), ("levels", C.c_int), ("converged", C.c_int),
+                ("rel_res", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        vp = C.c_void_p
+        L.o_csr_n.argtypes = [vp]
+        L.o_csr_ncol.argtypes = [vp]
+        L.o_csr_nnz.argtypes = [vp]
+        L.o_csr_copy.argtypes = [vp, _i32p, _i32p, vp]
+        L.o_csr_free.argtypes = [vp]
+        L.o_bsr3_spmv.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p]
+        for f in ("o_strength_color", "o_strength_rs"):
+            getattr(L, f).argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double]
+            getattr(L, f).restype = vp
+        L.o_sym_union.argtypes = [C.c_int, _i32p, _i32p]
+        L.o_sym_union.restype = vp
+        L.o_jp_color.argtypes = [C.c_int, _i32p, _i32p, C.c_uint64, C.c_int, C.c_int, _i32p]
+        L.o_hash.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int]
+        L.o_hash.restype = C.c_uint32
+        L.o_pmis.argtypes = [C.c_int, _i32p, _i32p, C.c_uint64, C.c_int, C.c_int, _i32p]
+        L.o_interp_direct.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p]
+        L.o_interp_direct.restype = vp
+        L.o_transpose.argtypes = [C.c_int, C.c_int, _i32p, _i32p, vp]
+        L.o_transpose.restype = vp
+        L.o_spgemm.argtypes = [C.c_int, C.c_int, _i32p, _i32p, _f64p, C.c_int, _i32p, _i32p, _f64p]
+        L.o_spgemm.restype = vp
+        L.o_mcgs_sweep.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _f64p, _f64p,
+                                   C.c_int]
+        L.o_dense_lu_solve.argtypes = [C.c_int, _f64p, _f64p, _f64p]
+        L.o_decouple.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _f64p, _f64p]
+        L.o_bilu0.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_uint64, _i32p, _f64p]
+        L.o_bilu0_solve.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _f64p, _f64p]
+        L.o_fgmres_identity.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
+                                        C.c_int, C.c_int, C.POINTER(Stats), vp]
+        L.o_default_opts.argtypes = [C.POINTER(Opts)]
+        L.o_setup.argtypes = [C.POINTER(vp), C.c_int, _i32p, _i32p, _f64p, C.POINTER(Opts)]
+        L.o_update.argtypes = [vp, C.c_int, _i32p, _i32p, _f64p]
+        L.o_solve.argtypes = [vp, _f64p, _f64p, C.c_double, C.POINTER(Stats)]
+        L.o_destroy.argtypes = [vp]
+        L.o_num_levels.argtypes = [vp]
+        L.o_last_iters.argtypes = [vp]
+        L.o_level_info.argtypes = [vp, C.c_int] + [C.POINTER(C.c_int)] * 5
+        L.o_level_get.argtypes = [vp, C.c_int, _i32p, _i32p, _f64p, vp, vp, vp, vp, vp]
+        L.o_get_weights.argtypes = [vp, _f64p]
+        L.o_bilu_ncolors.argtypes = [vp]
+        L.o_bilu_get.argtypes = [vp, _i32p, _f64p]
+        L.o_cpr_apply.argtypes = [vp, _f64p, _f64p]
+        L.o_vcycle.argtypes = [vp, _f64p, _f64p]
+        L.o_bilu_apply.argtypes = [vp, _f64p, _f64p]
+        _lib = L
+    return _lib
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().o_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class CSR:
+    n: int
+    ncol: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray | None = None
+
+    def dense(self) -> np.ndarray:
+        D = np.zeros((self.n, self.ncol))
+        for i in range(self.n):
+            for p in range(self.rowptr[i], self.rowptr[i + 1]):
+                D[i, self.col[p]] = 1.0 if self.val is None else self.val[p]
+        return D
+
+    def pattern(self) -> set:
+        return {(i, int(self.col[p])) for i in range(self.n)
+                for p in range(self.rowptr[i], self.rowptr[i + 1])}
+
+
+def _take(ptr, with_val=True) -> CSR:
+    L = lib()
+    n, ncol, nnz = L.o_csr_n(ptr), L.o_csr_ncol(ptr), L.o_csr_nnz(ptr)
+    rp = np.zeros(n + 1, np.int32)
+    cl = np.zeros(nnz, np.int32)
+    v = np.zeros(nnz, np.float64) if with_val else None
+    L.o_csr_copy(ptr, rp, cl, v.ctypes.data if with_val else None)
+    L.o_csr_free(ptr)
+    return CSR(n, ncol, rp, cl, v)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- primitives
+
+def bsr3_spmv(J, x):
+    y = np.zeros(3 * J.nb)
+    lib().o_bsr3_spmv(J.nb, _i32(J.rowptr), _i32(J.col), _f64(J.val), _f64(x), y)
+    return y
+
+
+def strength_color(rowptr, col, val, theta) -> CSR:
+    n = len(rowptr) - 1
+    return _take(lib().o_strength_color(n, _i32(rowptr), _i32(col), _f64(val), theta), False)
+
+
+def sym_union(S: CSR) -> CSR:
+    return _take(lib().o_sym_union(S.n, _i32(S.rowptr), _i32(S.col)), False)
+
+
+def jp_color(G: CSR, seed=0, salt=0, level=0):
+    color = np.zeros(G.n, np.int32)
+    nc = lib().o_jp_color(G.n, _i32(G.rowptr), _i32(G.col), seed, salt, level, color)
+    return color, nc
+
+
+def hash32(seed, salt, level, i) -> int:
+    return int(lib().o_hash(seed, salt, level, i))
+
+
+def strength_rs(rowptr, col, val, theta=0.25) -> CSR:
+    n = len(rowptr) - 1
+    return _take(lib().o_strength_rs(n, _i32(rowptr), _i32(col), _f64(val), theta), False)
+
+
+def pmis(S: CSR, seed=0, salt=1, level=0):
+    cf = np.zeros(S.n, np.int32)
+    nc = lib().o_pmis(S.n, _i32(S.rowptr), _i32(S.col), seed, salt, level, cf)
+    return cf, nc
+
+
+def interp_direct(rowptr, col, val, S: CSR, cf) -> CSR:
+    n = len(rowptr) - 1
+    return _take(lib().o_interp_direct(n, _i32(rowptr), _i32(col), _f64(val), _i32(S.rowptr),
+                                       _i32(S.col), _i32(cf)))
+
+
+def transpose(M: CSR) -> CSR:
+    v = None if M.val is None else _f64(M.val)
+    return _take(lib().o_transpose(M.n, M.ncol, _i32(M.rowptr), _i32(M.col),
+                                   None if v is None else v.ctypes.data), M.val is not None)
+
+
+def spgemm(A: CSR, B: CSR) -> CSR:
+    return _take(lib().o_spgemm(A.n, A.ncol, _i32(A.rowptr), _i32(A.col), _f64(A.val), B.ncol,
+                                _i32(B.rowptr), _i32(B.col), _f64(B.val)))
+
+
+def mcgs_sweep(rowptr, col, val, color, ncolors, b, x, descending=False):
+    x = _f64(x).copy()
+    n = len(rowptr) - 1
+    lib().o_mcgs_sweep(n, _i32(rowptr), _i32(col), _f64(val), _i32(color), ncolors, _f64(b), x,
+                       int(descending))
+    return x
+
+
+def dense_lu_solve(A, b):
+    A = _f64(A)
+    x = np.zeros(A.shape[0])
+    rc = lib().o_dense_lu_solve(A.shape[0], A, _f64(b), x)
+    if rc != 0:
+        raise RuntimeError(f"oracle dense LU failed ({rc})")
+    return x
+
+
+def decouple(J, mode=1):
+    w = np.zeros(3 * J.nb)
+    ap = np.zeros(J.nnzb)
+    rc = lib().o_decouple(J.nb, _i32(J.rowptr), _i32(J.col), _f64(J.val), mode, w, ap)
+    if rc != 0:
+        raise RuntimeError(f"oracle decoupling failed ({rc})")
+    return w, ap
+
+
+def bilu0(J, seed=0):
+    bcolor = np.zeros(J.nb, np.int32)
+    lu = np.zeros(9 * J.nnzb)
+    nc = lib().o_bilu0(J.nb, _i32(J.rowptr), _i32(J.col), _f64(J.val), seed, bcolor, lu)
+    if nc < 0:
+        raise RuntimeError(f"oracle BILU(0) failed ({nc})")
+    return bcolor, nc, lu
+
+
+def bilu0_solve(J, bcolor, nbcolors, lu, r):
+    z = np.zeros(3 * J.nb)
+    lib().o_bilu0_solve(J.nb, _i32(J.rowptr), _i32(J.col), _f64(lu), _i32(bcolor), nbcolors,
+                        _f64(r), z)
+    return z
+
+
+def fgmres_identity(J, b, x0=None, rtol=1e-10, m=30, max_restarts=100):
+    x = np.zeros(3 * J.nb) if x0 is None else _f64(x0).copy()
+    st = Stats()
+    hist = np.zeros(m * max_restarts)
+    rc = lib().o_fgmres_identity(J.nb, _i32(J.rowptr), _i32(J.col), _f64(J.val), _f64(b), x,
+                                 rtol, m, max_restarts, C.byref(st), hist.ctypes.data)
+    return x, st.as_dict(), hist[:st.iters], rc
+
+
+# ---------------------------------------------------------------- the solver
+
+class Solver:
+    """CPR-FGMRES with adaptive setup (Alg. 2 + Alg. 3), FP64 on the CPU."""
+
+    def __init__(self, J, **opts):
+        self.opts = default_opts(**opts)
+        self._h = C.c_void_p()
+        self._keep = (_i32(J.rowptr), _i32(J.col), _f64(J.val))
+        self.nb = J.nb
+        self.nnzb = J.nnzb
+        rc = lib().o_setup(C.byref(self._h), J.nb, *self._keep, C.byref(self.opts))
+        if rc != 0:
+            raise RuntimeError(f"oracle setup failed ({rc})")
+
+    def update(self, J):
+        self._keep = (_i32(J.rowptr), _i32(J.col), _f64(J.val))
+        rc = lib().o_update(self._h, J.nb, *self._keep)
+        if rc != 0:
+            raise RuntimeError(f"oracle update failed ({rc})")
+        self.nb, self.nnzb = J.nb, J.nnzb
+
+    def solve(self, b, x0=None, rtol=1e-6):
+        x = np.zeros(3 * self.nb) if x0 is None else _f64(x0).copy()
+        st = Stats()
+        rc = lib().o_solve(self._h, _f64(b), x, rtol, C.byref(st))
+        if rc < 0:
+            raise RuntimeError(f"oracle solve failed ({rc})")
+        return x, st.as_dict()
+
+    # inspection
+    @property
+    def nlev(self) -> int:
+        return lib().o_num_levels(self._h)
+
+    def level(self, l: int) -> dict:
+        n, nnz, ncol, nc, nnzp = (C.c_int() for _ in range(5))
+        lib().o_level_info(self._h, l, C.byref(n), C.byref(nnz), C.byref(ncol), C.byref(nc),
+                           C.byref(nnzp))
+        n, nnz, ncolors, nc, nnzp = n.value, nnz.value, ncol.value, nc.value, nnzp.value
+        rp = np.zeros(n + 1, np.int32)
+        cl = np.zeros(nnz, np.int32)
+        v = np.zeros(nnz)
+        color = np.zeros(n, np.int32)
+        cf = np.zeros(n, np.int32)
+        prow = np.zeros(n + 1, np.int32)
+        pcol = np.zeros(nnzp, np.int32)
+        pval = np.zeros(nnzp)
+        has_p = nnzp > 0 or nc > 0
+        lib().o_level_get(self._h, l, rp, cl, v, color.ctypes.data if ncolors else None,
+                          cf.ctypes.data if has_p else None, prow.ctypes.data if has_p else None,
+                          pcol.ctypes.data if has_p else None, pval.ctypes.data if has_p else None)
+        out = {"A": CSR(n, n, rp, cl, v), "ncolors": ncolors, "color": color if ncolors else None}
+        if has_p:
+            out.update(cf=cf, nc=nc, P=CSR(n, nc, prow, pcol, pval))
+        return out
+
+    def weights(self):
+        w = np.zeros(3 * self.nb)
+        lib().o_get_weights(self._h, w)
+        return w
+
+    def bilu(self):
+        bc = np.zeros(self.nb, np.int32)
+        lu = np.zeros(9 * self.nnzb)
+        lib().o_bilu_get(self._h, bc, lu)
+        return bc, lib().o_bilu_ncolors(self._h), lu
+
+    def cpr_apply(self, v):
+        z = np.zeros(3 * self.nb)
+        lib().o_cpr_apply(self._h, _f64(v), z)
+        return z
+
+    def vcycle(self, b):
+        x = np.zeros(len(b))
+        lib().o_vcycle(self._h, _f64(b), x)
+        return x
+
+    def bilu_apply(self, r):
+        z = np.zeros(3 * self.nb)
+        lib().o_bilu_apply(self._h, _f64(r), z)
+        return z
+
+    @property
+    def last_iters(self) -> int:
+        return lib().o_last_iters(self._h)
+
+    def close(self):
+        if self._h:
+            lib().o_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,1388 @@
+/*
+ * FP64 CPU oracle of the CPR-preconditioned FGMRES solve phase with adaptive
+ * setup (Alg. 1-3), multi-color Gauss-Seidel over the strong-connection matrix
+ * (Eq. 5.1, Alg. 6) inside a classical AMG V-cycle, and multicolor BILU(0).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg; never by the CUDA product path, with which it
+ * shares no code.
+ *
+ * Written to be checked against the paper by eye: one step per function, loops
+ * in the order the definitions state, no blocking and no fusion.  Built with
+ * -ffp-contract=off so that every a*b+c is rounded twice, exactly as written.
+ *
+ * Readings of points the paper leaves open (each is named where it is used):
+ *  R1 decoupling: Pi_P^T r takes w_i . r_i with w_i = D_i^-T e_1 (ABF) or e_1.
+ *  R2 Eq. 5.1 sums |a_ik| over the whole row, diagonal included; the coloring
+ *     graph is S united with its transpose.
+ *  R3 colors: Jones-Plassmann with key (degree, hash, index) replaces the
+ *     sequential greedy Alg. 4-5; each selected vertex takes the smallest
+ *     color its colored neighbours leave free.
+ *  R4 rows of one color are relaxed Jacobi-style (all read the iterate at the
+ *     start of the color), so weakly coupled same-color rows stay deterministic.
+ *  R5 V(1,1): pre-smoothing colors ascending, post-smoothing descending,
+ *     starting from zero; classical strength, PMIS, direct interpolation,
+ *     R = P^T, Galerkin R A P, dense LU on the coarsest level.
+ *  R6 second stage: block ILU(0) in (color, index) order of a coloring of the
+ *     block graph at theta = 0.
+ *  R7 It of Alg. 3 is the number of inner (Arnoldi) steps of the last solve;
+ *     a reused B keeps its own copy of A for line 3 of Alg. 1.
+ *  Hash: MurmurHash3's 32-bit finalizer (fmix32), a published mixing function.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MAXLEV 32
+
+struct o_csr {
+    int n, ncol, nnz;
+    int *rowptr, *col;
+    double *val; /* NULL for a pattern */
+};
+
+typedef struct {
+    o_csr A;       /* level matrix A_l */
+    int *color;    /* Eq. 5.1 coloring of A_l (not on the coarsest level) */
+    int ncolors;
+    int *cf;       /* 1 = C point, 0 = F point */
+    int nc;        /* number of C points = size of level l+1 */
+    o_csr P, R;    /* interpolation (n_l x n_{l+1}) and R = P^T */
+    double *x, *b, *r, *tmp; /* V-cycle work vectors */
+} level_t;
+
+struct o_handle {
+    o_opts opt;
+    int nb, nnzb;
+    int *rowptr, *col;
+    double *val;   /* outer operator A^(k) */
+    double *pval;  /* the copy of A inside B (Alg. 1 line 3), frozen with B (R7) */
+    double *w;     /* decoupling weights, 3 per block row (R1) */
+    int nlev;
+    level_t lev[MAXLEV];
+    double *clu;   /* coarsest level: dense LU, row-major, with row pivots */
+    int *cpiv;
+    int *bcolor;   /* BILU(0) block colors (R6) */
+    int nbcolors;
+    double *lu;    /* L blocks (unit diagonal implied), U blocks, U_ii^-1 at the diagonal */
+    double *work1, *work2, *work3, *rp, *ep; /* CPR apply work vectors */
+    long last_iters; /* It of the previous solve (R7); -1 = none since the last setup */
+    int setup_count, setup_called, updates;
+};
+
+/* ------------------------------------------------------------------ helpers */
+
+static void *xcalloc(size_t n, size_t sz) {
+    void *p = calloc(n ? n : 1, sz);
+    if (!p) abort();
+    return p;
+}
+
+static o_csr csr_alloc(int n, int ncol, int nnz, int with_val) {
+    o_csr c;
+    c.n = n;
+    c.ncol = ncol;
+    c.nnz = nnz;
+    c.rowptr = xcalloc((size_t)n + 1, sizeof(int));
+    c.col = xcalloc((size_t)nnz, sizeof(int));
+    c.val = with_val ? xcalloc((size_t)nnz, sizeof(double)) : NULL;
+    return c;
+}
+
+static void csr_release(o_csr *c) {
+    free(c->rowptr);
+    free(c->col);
+    free(c->val);
+    memset(c, 0, sizeof(*c));
+}
+
+static o_csr *csr_box(o_csr c) {
+    o_csr *p = xcalloc(1, sizeof(o_csr));
+    *p = c;
+    return p;
+}
+
+static o_csr csr_view(int n, int ncol, const int *rowptr, const int *col, const double *val) {
+    o_csr c;
+    c.n = n;
+    c.ncol = ncol;
+    c.nnz = rowptr[n];
+    c.rowptr = (int *)rowptr;
+    c.col = (int *)col;
+    c.val = (double *)val;
+    return c;
+}
+
+int o_csr_n(const o_csr *c) { return c->n; }
+int o_csr_ncol(const o_csr *c) { return c->ncol; }
+int o_csr_nnz(const o_csr *c) { return c->nnz; }
+void o_csr_copy(const o_csr *c, int *rowptr, int *col, double *val) {
+    memcpy(rowptr, c->rowptr, sizeof(int) * ((size_t)c->n + 1));
+    memcpy(col, c->col, sizeof(int) * (size_t)c->nnz);
+    if (val && c->val) memcpy(val, c->val, sizeof(double) * (size_t)c->nnz);
+}
+void o_csr_free(o_csr *c) {
+    if (!c) return;
+    csr_release(c);
+    free(c);
+}
+
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+static double dot(int n, const double *a, const double *b) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* MurmurHash3 32-bit finalizer. */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+/* Per-vertex hash weight: salt 0 = smoother coloring, 1 = PMIS, 2 = BILU coloring. */
+uint32_t o_hash(uint64_t seed, int salt, int level, int i) {
+    uint32_t s32 = (uint32_t)(seed ^ (seed >> 32));
+    uint32_t base = fmix32(s32 + 1000003u * (uint32_t)salt + (uint32_t)level);
+    return fmix32((uint32_t)i ^ base);
+}
+
+/* Lexicographic comparison of keys (a, h, i): nonzero iff key 1 > key 2. */
+static int key_greater(long a1, uint32_t h1, int i1, long a2, uint32_t h2, int i2) {
+    if (a1 != a2) return a1 > a2;
+    if (h1 != h2) return h1 > h2;
+    return i1 > i2;
+}
+
+/* ------------------------------------------------------- 3x3 block algebra */
+
+/* c = a * b */
+static void mat3_mul(const double *a, const double *b, double *c) {
+    for (int r = 0; r < 3; r++)
+        for (int s = 0; s < 3; s++) {
+            double t = 0.0;
+            for (int k = 0; k < 3; k++) t += a[3 * r + k] * b[3 * k + s];
+            c[3 * r + s] = t;
+        }
+}
+
+/* Inverse by the adjugate; returns 0 if the block is singular. */
+static int mat3_inv(const double *a, double *inv) {
+    double c00 = a[4] * a[8] - a[5] * a[7];
+    double c01 = a[5] * a[6] - a[3] * a[8];
+    double c02 = a[3] * a[7] - a[4] * a[6];
+    double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    if (det == 0.0 || !isfinite(det)) return 0;
+    inv[0] = c00 / det;
+    inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+    inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+    inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+    inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+    return 1;
+}
+
+/* ------------------------------------------------------------- 3x3 BSR SpMV */
+
+/* y = A x for a 3x3 BSR matrix (Eq. 2.8 layout). */
+void o_bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val,
+                 const double *x, double *y) {
+    for (int i = 0; i < nb; i++) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            const double *blk = val + 9 * (size_t)p;
+            const double *xj = x + 3 * (size_t)col[p];
+            for (int r = 0; r < 3; r++)
+                for (int c = 0; c < 3; c++) s[r] += blk[3 * r + c] * xj[c];
+        }
+        y[3 * i] = s[0];
+        y[3 * i + 1] = s[1];
+        y[3 * i + 2] = s[2];
+    }
+}
+
+static void bsr3_resid(int nb, const int *rowptr, const int *col, const double *val,
+                       const double *b, const double *x, double *r) {
+    o_bsr3_spmv(nb, rowptr, col, val, x, r);
+    for (int i = 0; i < 3 * nb; i++) r[i] = b[i] - r[i];
+}
+
+/* -------------------------------------------------------------- decoupling */
+
+/*
+ * Pressure decoupling and the pressure matrix (Eq. 3.1, reading R1).
+ * mode 1: w_i = D_i^-T e_1, i.e. the first row of D_i^-1 by the adjugate:
+ *   w_i = (C00, C10, C20) / det(D_i),  det = D00 C00 + D10 C10 + D20 C20.
+ * mode 0: w_i = e_1 (plain injection).
+ * A_P[i][j] = w_i . (column 0 of block A_ij), on the full block pattern.
+ */
+int o_decouple(int nb, const int *rowptr, const int *col, const double *val, int mode,
+               double *w, double *apval) {
+    for (int i = 0; i < nb; i++) {
+        if (mode == 0) {
+            w[3 * i] = 1.0;
+            w[3 * i + 1] = 0.0;
+            w[3 * i + 2] = 0.0;
+            continue;
+        }
+        const double *d = NULL;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (col[p] == i) d = val + 9 * (size_t)p;
+        if (!d) return O_ERR_INVALID;
+        double c00 = d[4] * d[8] - d[5] * d[7];
+        double c10 = d[2] * d[7] - d[1] * d[8];
+        double c20 = d[1] * d[5] - d[2] * d[4];
+        double det = (d[0] * c00 + d[3] * c10) + d[6] * c20;
+        if (det == 0.0 || !isfinite(det)) return O_ERR_SINGULAR;
+        w[3 * i] = c00 / det;
+        w[3 * i + 1] = c10 / det;
+        w[3 * i + 2] = c20 / det;
+    }
+    for (int i = 0; i < nb; i++)
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            const double *a = val + 9 * (size_t)p;
+            apval[p] = (w[3 * i] * a[0] + w[3 * i + 1] * a[3]) + w[3 * i + 2] * a[6];
+        }
+    return O_OK;
+}
+
+/* ------------------------------------------------- strength and coloring */
+
+/* Eq. 5.1: j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik| (reading R2). */
+static o_csr strength_color(const o_csr *A, double theta) {
+    int n = A->n;
+    o_csr S = csr_alloc(n, n, A->nnz, 0);
+    int nnz = 0;
+    for (int i = 0; i < n; i++) {
+        double rowsum = 0.0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) rowsum += fabs(A->val[p]);
+        double t = theta * rowsum;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            int j = A->col[p];
+            if (j != i && fabs(A->val[p]) > t) S.col[nnz++] = j;
+        }
+        S.rowptr[i + 1] = nnz;
+    }
+    S.nnz = nnz;
+    return S;
+}
+
+o_csr *o_strength_color(int n, const int *rowptr, const int *col, const double *val,
+                        double theta) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    return csr_box(strength_color(&A, theta));
+}
+
+/* Transpose by counting; scanning source rows in ascending order leaves each
+ * row of the result sorted. */
+static o_csr transpose(const o_csr *A) {
+    o_csr T = csr_alloc(A->ncol, A->n, A->nnz, A->val != NULL);
+    for (int p = 0; p < A->nnz; p++) T.rowptr[A->col[p] + 1]++;
+    for (int j = 0; j < A->ncol; j++) T.rowptr[j + 1] += T.rowptr[j];
+    int *next = xcalloc((size_t)A->ncol, sizeof(int));
+    for (int j = 0; j < A->ncol; j++) next[j] = T.rowptr[j];
+    for (int i = 0; i < A->n; i++)
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            int q = next[A->col[p]]++;
+            T.col[q] = i;
+            if (A->val) T.val[q] = A->val[p];
+        }
+    free(next);
+    return T;
+}
+
+o_csr *o_transpose(int n, int ncol, const int *rowptr, const int *col, const double *val) {
+    o_csr A = csr_view(n, ncol, rowptr, col, val);
+    return csr_box(transpose(&A));
+}
+
+/* Pattern of S united with S^T (the undirected graph of R2), sorted rows. */
+static o_csr sym_union(const o_csr *S) {
+    o_csr T = transpose(S);
+    int n = S->n;
+    o_csr G = csr_alloc(n, n, S->nnz + T.nnz, 0);
+    int nnz = 0;
+    for (int i = 0; i < n; i++) {
+        int p = S->rowptr[i], pe = S->rowptr[i + 1];
+        int q = T.rowptr[i], qe = T.rowptr[i + 1];
+        while (p < pe || q < qe) {
+            int a = p < pe ? S->col[p] : n;
+            int b = q < qe ? T.col[q] : n;
+            int c = a < b ? a : b;
+            if (a == c) p++;
+            if (b == c) q++;
+            G.col[nnz++] = c;
+        }
+        G.rowptr[i + 1] = nnz;
+    }
+    G.nnz = nnz;
+    csr_release(&T);
+    return G;
+}
+
+o_csr *o_sym_union(int n, const int *rowptr, const int *col) {
+    o_csr S = csr_view(n, n, rowptr, col, NULL);
+    return csr_box(sym_union(&S));
+}
+
+/*
+ * Jones-Plassmann coloring of an undirected graph G (reading R3).
+ * key(i) = (deg_G(i), hash(i), i).  Each round, from the round-start state,
+ * every uncolored vertex whose key beats all uncolored neighbours is selected;
+ * each selected vertex takes the smallest color not held by a neighbour.
+ * Returns the number of colors.
+ */
+static int jp_color(const o_csr *G, uint64_t seed, int salt, int level, int *color) {
+    int n = G->n;
+    uint32_t *h = xcalloc((size_t)n, sizeof(uint32_t));
+    char *sel = xcalloc((size_t)n, 1);
+    char *used = xcalloc((size_t)n + 2, 1);
+    for (int i = 0; i < n; i++) {
+        color[i] = -1;
+        h[i] = o_hash(seed, salt, level, i);
+    }
+    int left = n, ncolors = 0;
+    while (left > 0) {
+        for (int i = 0; i < n; i++) {
+            sel[i] = 0;
+            if (color[i] >= 0) continue;
+            int best = 1;
+            long di = G->rowptr[i + 1] - G->rowptr[i];
+            for (int p = G->rowptr[i]; p < G->rowptr[i + 1] && best; p++) {
+                int j = G->col[p];
+                if (j == i || color[j] >= 0) continue;
+                long dj = G->rowptr[j + 1] - G->rowptr[j];
+                if (!key_greater(di, h[i], i, dj, h[j], j)) best = 0;
+            }
+            sel[i] = (char)best;
+        }
+        for (int i = 0; i < n; i++) {
+            if (!sel[i]) continue;
+            int deg = G->rowptr[i + 1] - G->rowptr[i];
+            for (int p = G->rowptr[i]; p < G->rowptr[i + 1]; p++) {
+                int c = color[G->col[p]];
+                if (c >= 0 && c <= deg) used[c] = 1;
+            }
+            int c = 0;
+            while (used[c]) c++;
+            for (int p = G->rowptr[i]; p < G->rowptr[i + 1]; p++) {
+                int cj = color[G->col[p]];
+                if (cj >= 0 && cj <= deg) used[cj] = 0;
+            }
+            color[i] = c;
+            if (c + 1 > ncolors) ncolors = c + 1;
+            left--;
+        }
+    }
+    free(h);
+    free(sel);
+    free(used);
+    return ncolors;
+}
+
+int o_jp_color(int n, const int *rowptr, const int *col, uint64_t seed, int salt, int level,
+               int *color) {
+    o_csr G = csr_view(n, n, rowptr, col, NULL);
+    return jp_color(&G, seed, salt, level, color);
+}
+
+/* ------------------------------------------------------------ coarsening */
+
+/*
+ * Classical (Ruge-Stueben) strength: with s = sign(a_ii) (+1 when a_ii >= 0),
+ * j in S_i iff j != i and -s a_ij >= theta * max_{k != i}(-s a_ik), provided
+ * that maximum is positive (otherwise S_i is empty).
+ */
+static o_csr strength_rs(const o_csr *A, double theta) {
+    int n = A->n;
+    o_csr S = csr_alloc(n, n, A->nnz, 0);
+    int nnz = 0;
+    for (int i = 0; i < n; i++) {
+        double aii = 0.0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++)
+            if (A->col[p] == i) aii = A->val[p];
+        double s = aii < 0.0 ? -1.0 : 1.0;
+        double m = 0.0;
+        int have = 0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            if (A->col[p] == i) continue;
+            double v = -s * A->val[p];
+            if (!have || v > m) m = v;
+            have = 1;
+        }
+        if (have && m > 0.0) {
+            double t = theta * m;
+            for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+                int j = A->col[p];
+                if (j != i && -s * A->val[p] >= t) S.col[nnz++] = j;
+            }
+        }
+        S.rowptr[i + 1] = nnz;
+    }
+    S.nnz = nnz;
+    return S;
+}
+
+o_csr *o_strength_rs(int n, const int *rowptr, const int *col, const double *val,
+                     double theta) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    return csr_box(strength_rs(&A, theta));
+}
+
+/*
+ * PMIS C/F splitting on the strength graph S (S_i = points i depends on).
+ * lambda_i = |S^T_i| (how many points depend on i); key = (lambda, hash, index).
+ * A point with S_i and S^T_i both empty is F from the start.  Each round, from
+ * the round-start state, an undecided point whose key beats every undecided
+ * point of S_i u S^T_i becomes C; then every undecided point with a C point in
+ * S_i becomes F.  cf: 1 = C, 0 = F.  Returns the number of C points.
+ */
+static int pmis(const o_csr *S, uint64_t seed, int salt, int level, int *cf) {
+    int n = S->n;
+    o_csr T = transpose(S);
+    uint32_t *h = xcalloc((size_t)n, sizeof(uint32_t));
+    char *newc = xcalloc((size_t)n, 1);
+    int undecided = 0;
+    for (int i = 0; i < n; i++) {
+        h[i] = o_hash(seed, salt, level, i);
+        int si = S->rowptr[i + 1] - S->rowptr[i];
+        int ti = T.rowptr[i + 1] - T.rowptr[i];
+        cf[i] = (si == 0 && ti == 0) ? 0 : -1;
+        if (cf[i] < 0) undecided++;
+    }
+    while (undecided > 0) {
+        for (int i = 0; i < n; i++) {
+            newc[i] = 0;
+            if (cf[i] != -1) continue;
+            long li = T.rowptr[i + 1] - T.rowptr[i];
+            int best = 1;
+            for (int pass = 0; pass < 2 && best; pass++) {
+                const o_csr *M = pass == 0 ? S : &T;
+                for (int p = M->rowptr[i]; p < M->rowptr[i + 1] && best; p++) {
+                    int j = M->col[p];
+                    if (cf[j] != -1) continue;
+                    long lj = T.rowptr[j + 1] - T.rowptr[j];
+                    if (!key_greater(li, h[i], i, lj, h[j], j)) best = 0;
+                }
+            }
+            newc[i] = (char)best;
+        }
+        for (int i = 0; i < n; i++)
+            if (newc[i]) {
+                cf[i] = 1;
+                undecided--;
+            }
+        for (int i = 0; i < n; i++) {
+            if (cf[i] != -1) continue;
+            for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++)
+                if (cf[S->col[p]] == 1) {
+                    cf[i] = 0;
+                    undecided--;
+                    break;
+                }
+        }
+    }
+    int nc = 0;
+    for (int i = 0; i < n; i++) nc += cf[i] == 1;
+    csr_release(&T);
+    free(h);
+    free(newc);
+    return nc;
+}
+
+int o_pmis(int n, const int *srowptr, const int *scol, uint64_t seed, int salt, int level,
+           int *cf) {
+    o_csr S = csr_view(n, n, srowptr, scol, NULL);
+    return pmis(&S, seed, salt, level, cf);
+}
+
+/*
+ * Direct interpolation (Stueben) with separate scaling of negative and
+ * positive couplings.  C point i: P_i = e_{cidx(i)}.  F point i with
+ * C_i = S_i n C (sorted): with s = sign(a_ii) and a~ = s a,
+ *   alpha = sum_{k != i} min(a~_ik, 0) / sum_{k in C_i} min(a~_ik, 0),
+ *   beta  = sum_{k != i} max(a~_ik, 0) / sum_{k in C_i} max(a~_ik, 0),
+ *   d = a~_ii, or a~_ii + sum_{k != i} max(a~_ik, 0) when C_i has no positive
+ *   entry (the positive part is lumped into the diagonal),
+ *   w_ij = -alpha a~_ij / d  (a~_ij < 0),   -beta a~_ij / d  (otherwise).
+ * An F point with C_i empty gets an empty row.
+ */
+static o_csr interp_direct(const o_csr *A, const o_csr *S, const int *cf) {
+    int n = A->n;
+    int *cidx = xcalloc((size_t)n, sizeof(int));
+    int nc = 0;
+    for (int i = 0; i < n; i++) cidx[i] = cf[i] == 1 ? nc++ : -1;
+    int nnz = 0;
+    for (int i = 0; i < n; i++) {
+        if (cf[i] == 1) {
+            nnz++;
+            continue;
+        }
+        for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++) nnz += cf[S->col[p]] == 1;
+    }
+    o_csr P = csr_alloc(n, nc, nnz, 1);
+    int q = 0;
+    for (int i = 0; i < n; i++) {
+        if (cf[i] == 1) {
+            P.col[q] = cidx[i];
+            P.val[q] = 1.0;
+            q++;
+            P.rowptr[i + 1] = q;
+            continue;
+        }
+        double aii = 0.0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++)
+            if (A->col[p] == i) aii = A->val[p];
+        double s = aii < 0.0 ? -1.0 : 1.0;
+        double sum_n_neg = 0.0, sum_n_pos = 0.0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            if (A->col[p] == i) continue;
+            double v = s * A->val[p];
+            if (v < 0.0) sum_n_neg += v;
+            else sum_n_pos += v;
+        }
+        /* a~_ik for k in C_i: walk S_i and A's row together (both sorted) */
+        double sum_c_neg = 0.0, sum_c_pos = 0.0;
+        int pa = A->rowptr[i];
+        for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++) {
+            int j = S->col[p];
+            if (cf[j] != 1) continue;
+            while (A->col[pa] != j) pa++;
+            double v = s * A->val[pa];
+            if (v < 0.0) sum_c_neg += v;
+            else sum_c_pos += v;
+        }
+        double d = s * aii;
+        double alpha = 0.0, beta = 0.0;
+        if (sum_c_neg != 0.0) alpha = sum_n_neg / sum_c_neg;
+        if (sum_c_pos != 0.0) beta = sum_n_pos / sum_c_pos;
+        else d = d + sum_n_pos;
+        pa = A->rowptr[i];
+        for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++) {
+            int j = S->col[p];
+            if (cf[j] != 1) continue;
+            while (A->col[pa] != j) pa++;
+            double v = s * A->val[pa];
+            double f = v < 0.0 ? -alpha : -beta;
+            P.col[q] = cidx[j];
+            P.val[q] = (f * v) / d;
+            q++;
+        }
+        P.rowptr[i + 1] = q;
+    }
+    free(cidx);
+    return P;
+}
+
+o_csr *o_interp_direct(int n, const int *rowptr, const int *col, const double *val,
+                       const int *srowptr, const int *scol, const int *cf) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    o_csr S = csr_view(n, n, srowptr, scol, NULL);
+    return csr_box(interp_direct(&A, &S, cf));
+}
+
+/*
+ * C = A B, Gustavson's row-by-row product with a dense accumulator: for each
+ * row i, for k in A_i ascending, for j in B_k ascending, acc[j] += a_ik b_kj.
+ * The pattern is the structural product (explicit zeros kept), sorted.
+ */
+static o_csr spgemm(const o_csr *A, const o_csr *B) {
+    int n = A->n, m = B->ncol;
+    int *mark = xcalloc((size_t)m, sizeof(int));
+    double *acc = xcalloc((size_t)m, sizeof(double));
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    long nnz = 0;
+    for (int i = 0; i < n; i++)
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            int k = A->col[p];
+            for (int q = B->rowptr[k]; q < B->rowptr[k + 1]; q++)
+                if (mark[B->col[q]] != i) {
+                    mark[B->col[q]] = i;
+                    nnz++;
+                }
+        }
+    o_csr C = csr_alloc(n, m, (int)nnz, 1);
+    for (int j = 0; j < m; j++) mark[j] = -1;
+    int c = 0;
+    for (int i = 0; i < n; i++) {
+        int start = c;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+            int k = A->col[p];
+            for (int q = B->rowptr[k]; q < B->rowptr[k + 1]; q++) {
+                int j = B->col[q];
+                if (mark[j] != i) {
+                    mark[j] = i;
+                    acc[j] = 0.0;
+                    C.col[c++] = j;
+                }
+                acc[j] = acc[j] + A->val[p] * B->val[q];
+            }
+        }
+        qsort(C.col + start, (size_t)(c - start), sizeof(int), cmp_int);
+        for (int q = start; q < c; q++) C.val[q] = acc[C.col[q]];
+        C.rowptr[i + 1] = c;
+    }
+    free(mark);
+    free(acc);
+    return C;
+}
+
+o_csr *o_spgemm(int n, int ncolA, const int *arow, const int *acol, const double *aval,
+                int ncolB, const int *brow, const int *bcol, const double *bval) {
+    o_csr A = csr_view(n, ncolA, arow, acol, aval);
+    o_csr B = csr_view(ncolA, ncolB, brow, bcol, bval);
+    return csr_box(spgemm(&A, &B));
+}
+
+/* ----------------------------------------------------------- dense LU */
+
+/* LU with partial pivoting (largest |a|, lowest row index on ties), in place. */
+static int dense_lu(int n, double *a, int *piv) {
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = fabs(a[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double v = fabs(a[(size_t)i * n + k]);
+            if (v > best) {
+                best = v;
+                p = i;
+            }
+        }
+        piv[k] = p;
+        if (best == 0.0) return O_ERR_SINGULAR;
+        if (p != k)
+            for (int j = 0; j < n; j++) {
+                double t = a[(size_t)k * n + j];
+                a[(size_t)k * n + j] = a[(size_t)p * n + j];
+                a[(size_t)p * n + j] = t;
+            }
+        for (int i = k + 1; i < n; i++) {
+            double l = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+            a[(size_t)i * n + k] = l;
+            for (int j = k + 1; j < n; j++) a[(size_t)i * n + j] -= l * a[(size_t)k * n + j];
+        }
+    }
+    return O_OK;
+}
+
+static void dense_lu_solve(int n, const double *lu, const int *piv, const double *b, double *x) {
+    for (int i = 0; i < n; i++) x[i] = b[i];
+    for (int k = 0; k < n; k++) {
+        double t = x[k];
+        x[k] = x[piv[k]];
+        x[piv[k]] = t;
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < i; j++) x[i] -= lu[(size_t)i * n + j] * x[j];
+    for (int i = n - 1; i >= 0; i--) {
+        for (int j = i + 1; j < n; j++) x[i] -= lu[(size_t)i * n + j] * x[j];
+        x[i] /= lu[(size_t)i * n + i];
+    }
+}
+
+int o_dense_lu_solve(int n, const double *a, const double *b, double *x) {
+    double *lu = xcalloc((size_t)n * n, sizeof(double));
+    int *piv = xcalloc((size_t)n, sizeof(int));
+    memcpy(lu, a, sizeof(double) * (size_t)n * n);
+    int rc = dense_lu(n, lu, piv);
+    if (rc == O_OK) dense_lu_solve(n, lu, piv, b, x);
+    free(lu);
+    free(piv);
+    return rc;
+}
+
+/* ------------------------------------------------- multi-color Gauss-Seidel */
+
+/*
+ * One sweep of PGS-SCM (Alg. 6): colors in order (ascending, or descending
+ * when `descending`), each row i of the color taking
+ *   x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii
+ * with every x_j read as of the start of the color (reading R4).
+ */
+static void mcgs_sweep(const o_csr *A, const int *color, int ncolors, const double *b,
+                       double *x, int descending, double *tmp) {
+    for (int t = 0; t < ncolors; t++) {
+        int c = descending ? ncolors - 1 - t : t;
+        for (int i = 0; i < A->n; i++) {
+            if (color[i] != c) continue;
+            double s = b[i], d = 0.0;
+            for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++) {
+                int j = A->col[p];
+                if (j == i) d = A->val[p];
+                else s -= A->val[p] * x[j];
+            }
+            tmp[i] = s / d;
+        }
+        for (int i = 0; i < A->n; i++)
+            if (color[i] == c) x[i] = tmp[i];
+    }
+}
+
+void o_mcgs_sweep(int n, const int *rowptr, const int *col, const double *val, const int *color,
+                  int ncolors, const double *b, double *x, int descending) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    double *tmp = xcalloc((size_t)n, sizeof(double));
+    mcgs_sweep(&A, color, ncolors, b, x, descending, tmp);
+    free(tmp);
+}
+
+/* ----------------------------------------------------------------- BILU(0) */
+
+/* Positions of rows in (color, index) order; order[t] = row at position t. */
+static void color_order(int n, const int *color, int ncolors, int *order, int *pos) {
+    int t = 0;
+    for (int c = 0; c < ncolors; c++)
+        for (int i = 0; i < n; i++)
+            if (color[i] == c) {
+                pos[i] = t;
+                order[t++] = i;
+            }
+}
+
+/* Block coloring for BILU(0): JP on the off-diagonal block graph at theta = 0. */
+static int bilu_coloring(int nb, const int *rowptr, const int *col, uint64_t seed, int *bcolor) {
+    o_csr S = csr_alloc(nb, nb, rowptr[nb], 0);
+    int nnz = 0;
+    for (int i = 0; i < nb; i++) {
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (col[p] != i) S.col[nnz++] = col[p];
+        S.rowptr[i + 1] = nnz;
+    }
+    S.nnz = nnz;
+    o_csr G = sym_union(&S);
+    int nc = jp_color(&G, seed, 2, 0, bcolor);
+    csr_release(&S);
+    csr_release(&G);
+    return nc;
+}
+
+static int find_col(const int *col, int lo, int hi, int j) {
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (col[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < 0 || col[lo] != j) ? -1 : lo;
+}
+
+/*
+ * Block ILU(0) in (color, index) order (reading R6), row by row: for row i and
+ * each k before i in that order (ascending), L_ik = A_ik U_kk^-1, then
+ * A_ij -= L_ik U_kj for every j after k in row k that is also in row i's
+ * pattern.  The factor array holds L_ik and U_ij in A's pattern and U_ii^-1 at
+ * the diagonal positions.
+ */
+static int bilu0_factor(int nb, const int *rowptr, const int *col, const double *val,
+                        const int *bcolor, int nbcolors, double *lu) {
+    int *order = xcalloc((size_t)nb, sizeof(int));
+    int *pos = xcalloc((size_t)nb, sizeof(int));
+    int *diag = xcalloc((size_t)nb, sizeof(int));
+    color_order(nb, bcolor, nbcolors, order, pos);
+    memcpy(lu, val, sizeof(double) * 9 * (size_t)rowptr[nb]);
+    int rc = O_OK;
+    for (int i = 0; i < nb; i++) {
+        diag[i] = find_col(col, rowptr[i], rowptr[i + 1], i);
+        if (diag[i] < 0) rc = O_ERR_INVALID;
+    }
+    int maxlen = 0;
+    for (int i = 0; i < nb; i++)
+        if (rowptr[i + 1] - rowptr[i] > maxlen) maxlen = rowptr[i + 1] - rowptr[i];
+    int *lower = xcalloc((size_t)maxlen + 1, sizeof(int));
+    for (int t = 0; t < nb && rc == O_OK; t++) {
+        int i = order[t];
+        /* entries of row i that come before i, sorted by position */
+        int nl = 0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
+            if (pos[col[p]] < t) lower[nl++] = p;
+        for (int a = 1; a < nl; a++)
+            for (int b = a; b > 0 && pos[col[lower[b - 1]]] > pos[col[lower[b]]]; b--) {
+                int x = lower[b];
+                lower[b] = lower[b - 1];
+                lower[b - 1] = x;
+            }
+        for (int a = 0; a < nl; a++) {
+            int p = lower[a];
+            int k = col[p];
+            double L[9];
+            mat3_mul(lu + 9 * (size_t)p, lu + 9 * (size_t)diag[k], L);
+            memcpy(lu + 9 * (size_t)p, L, sizeof(L));
+            for (int q = rowptr[k]; q < rowptr[k + 1]; q++) {
+                int j = col[q];
+                if (pos[j] <= pos[k]) continue;
+                int r = find_col(col, rowptr[i], rowptr[i + 1], j);
+                if (r < 0) continue;
+                double LU[9];
+                mat3_mul(L, lu + 9 * (size_t)q, LU);
+                for (int e = 0; e < 9; e++) lu[9 * (size_t)r + e] -= LU[e];
+            }
+        }
+        double inv[9];
+        if (!mat3_inv(lu + 9 * (size_t)diag[i], inv)) {
+            rc = O_ERR_SINGULAR;
+            break;
+        }
+        memcpy(lu + 9 * (size_t)diag[i], inv, sizeof(inv));
+    }
+    free(lower);
+    free(order);
+    free(pos);
+    free(diag);
+    return rc;
+}
+
+/* Solve (L U) z = r: forward then backward substitution in (color, index) order. */
+void o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,
+                   const int *bcolor, int nbcolors, const double *r, double *z) {
+    int *order = xcalloc((size_t)nb, sizeof(int));
+    int *pos = xcalloc((size_t)nb, sizeof(int));
+    color_order(nb, bcolor, nbcolors, order, pos);
+    double *y = xcalloc(3 * (size_t)nb, sizeof(double));
+    for (int t = 0; t < nb; t++) {
+        int i = order[t];
+        double s[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            int j = col[p];
+            if (pos[j] >= t) continue;
+            const double *L = lu + 9 * (size_t)p;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) s[a] -= L[3 * a + b] * y[3 * j + b];
+        }
+        y[3 * i] = s[0];
+        y[3 * i + 1] = s[1];
+        y[3 * i + 2] = s[2];
+    }
+    for (int t = nb - 1; t >= 0; t--) {
+        int i = order[t];
+        double s[3] = {y[3 * i], y[3 * i + 1], y[3 * i + 2]};
+        const double *Dinv = NULL;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            int j = col[p];
+            if (j == i) {
+                Dinv = lu + 9 * (size_t)p;
+                continue;
+            }
+            if (pos[j] < t) continue;
+            const double *U = lu + 9 * (size_t)p;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) s[a] -= U[3 * a + b] * z[3 * j + b];
+        }
+        for (int a = 0; a < 3; a++)
+            z[3 * i + a] = (Dinv[3 * a] * s[0] + Dinv[3 * a + 1] * s[1]) + Dinv[3 * a + 2] * s[2];
+    }
+    free(y);
+    free(order);
+    free(pos);
+}
+
+int o_bilu0(int nb, const int *rowptr, const int *col, const double *val, uint64_t seed,
+            int *bcolor, double *lu) {
+    int nc = bilu_coloring(nb, rowptr, col, seed, bcolor);
+    int rc = bilu0_factor(nb, rowptr, col, val, bcolor, nc, lu);
+    return rc == O_OK ? nc : rc;
+}
+
+/* ------------------------------------------------------------- hierarchy */
+
+void o_default_opts(o_opts *o) {
+    o->theta_color = 0.05;
+    o->theta_amg = 0.25;
+    o->mu = 30;
+    o->restart = 30;
+    o->max_restarts = 100;
+    o->precond_fp32 = 0;
+    o->decouple = 1;
+    o->pre = 1;
+    o->post = 1;
+    o->coarse_max = 256;
+    o->max_levels = 20;
+    o->seed = 0;
+}
+
+static void free_setup(o_handle *h) {
+    for (int l = 0; l < h->nlev; l++) {
+        level_t *L = &h->lev[l];
+        csr_release(&L->A);
+        csr_release(&L->P);
+        csr_release(&L->R);
+        free(L->color);
+        free(L->cf);
+        free(L->x);
+        free(L->b);
+        free(L->r);
+        free(L->tmp);
+        memset(L, 0, sizeof(*L));
+    }
+    h->nlev = 0;
+    free(h->clu);
+    free(h->cpiv);
+    free(h->bcolor);
+    free(h->lu);
+    free(h->w);
+    free(h->pval);
+    h->clu = NULL;
+    h->cpiv = NULL;
+    h->bcolor = NULL;
+    h->lu = NULL;
+    h->w = NULL;
+    h->pval = NULL;
+}
+
+/* Zero diagonals make the smoother undefined (no silent regularisation). */
+static int check_diag(const o_csr *A) {
+    for (int i = 0; i < A->n; i++) {
+        double d = 0.0;
+        for (int p = A->rowptr[i]; p < A->rowptr[i + 1]; p++)
+            if (A->col[p] == i) d = A->val[p];
+        if (d == 0.0 || !isfinite(d)) return O_ERR_SINGULAR;
+    }
+    return O_OK;
+}
+
+/* Build B from the current A (Alg. 1's preconditioner, Sec. 3.1, Alg. 6). */
+static int build_preconditioner(o_handle *h) {
+    free_setup(h);
+    const o_opts *o = &h->opt;
+    int nb = h->nb, nnzb = h->nnzb;
+    h->pval = xcalloc(9 * (size_t)nnzb, sizeof(double));
+    memcpy(h->pval, h->val, sizeof(double) * 9 * (size_t)nnzb);
+    h->w = xcalloc(3 * (size_t)nb, sizeof(double));
+    /* level 0: the pressure matrix A_P */
+    o_csr A0 = csr_alloc(nb, nb, nnzb, 1);
+    memcpy(A0.rowptr, h->rowptr, sizeof(int) * ((size_t)nb + 1));
+    memcpy(A0.col, h->col, sizeof(int) * (size_t)nnzb);
+    int rc = o_decouple(nb, h->rowptr, h->col, h->val, o->decouple, h->w, A0.val);
+    if (rc != O_OK) {
+        csr_release(&A0);
+        return rc;
+    }
+    h->lev[0].A = A0;
+    int l = 0;
+    for (;;) {
+        level_t *L = &h->lev[l];
+        h->nlev = l + 1;
+        int n = L->A.n;
+        rc = check_diag(&L->A);
+        if (rc != O_OK) return rc;
+        L->x = xcalloc((size_t)n, sizeof(double));
+        L->b = xcalloc((size_t)n, sizeof(double));
+        L->r = xcalloc((size_t)n, sizeof(double));
+        L->tmp = xcalloc((size_t)n, sizeof(double));
+        if (n <= o->coarse_max || l + 1 >= o->max_levels || l + 1 >= MAXLEV) break;
+        o_csr S = strength_rs(&L->A, o->theta_amg);
+        L->cf = xcalloc((size_t)n, sizeof(int));
+        int nc = pmis(&S, o->seed, 1, l, L->cf);
+        if (nc == 0 || (double)nc > 0.95 * (double)n) {
+            csr_release(&S);
+            free(L->cf);
+            L->cf = NULL;
+            break;
+        }
+        L->nc = nc;
+        L->P = interp_direct(&L->A, &S, L->cf);
+        csr_release(&S);
+        L->R = transpose(&L->P);
+        o_csr AP = spgemm(&L->A, &L->P);
+        h->lev[l + 1].A = spgemm(&L->R, &AP);
+        csr_release(&AP);
+        /* the smoother's coloring (Eq. 5.1, Alg. 4-6 intent, reading R3) */
+        o_csr Sc = strength_color(&L->A, o->theta_color);
+        o_csr G = sym_union(&Sc);
+        L->color = xcalloc((size_t)n, sizeof(int));
+        L->ncolors = jp_color(&G, o->seed, 0, l, L->color);
+        csr_release(&Sc);
+        csr_release(&G);
+        l++;
+    }
+    /* coarsest level: dense LU */
+    level_t *C = &h->lev[h->nlev - 1];
+    int n = C->A.n;
+    h->clu = xcalloc((size_t)n * n, sizeof(double));
+    h->cpiv = xcalloc((size_t)n, sizeof(int));
+    for (int i = 0; i < n; i++)
+        for (int p = C->A.rowptr[i]; p < C->A.rowptr[i + 1]; p++)
+            h->clu[(size_t)i * n + C->A.col[p]] = C->A.val[p];
+    rc = dense_lu(n, h->clu, h->cpiv);
+    if (rc != O_OK) return rc;
+    /* second stage */
+    h->bcolor = xcalloc((size_t)nb, sizeof(int));
+    h->nbcolors = bilu_coloring(nb, h->rowptr, h->col, o->seed, h->bcolor);
+    h->lu = xcalloc(9 * (size_t)nnzb, sizeof(double));
+    rc = bilu0_factor(nb, h->rowptr, h->col, h->pval, h->bcolor, h->nbcolors, h->lu);
+    return rc;
+}
+
+/* V(pre, post) cycle for A_l e = b with zero initial guess (reading R5). */
+static void vcycle(o_handle *h, int l, const double *b, double *x) {
+    level_t *L = &h->lev[l];
+    int n = L->A.n;
+    if (l == h->nlev - 1) {
+        dense_lu_solve(n, h->clu, h->cpiv, b, x);
+        return;
+    }
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    for (int s = 0; s < h->opt.pre; s++) mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 0, L->tmp);
+    /* r = b - A x, b_c = R r */
+    for (int i = 0; i < n; i++) {
+        double s = b[i];
+        for (int p = L->A.rowptr[i]; p < L->A.rowptr[i + 1]; p++)
+            s -= L->A.val[p] * x[L->A.col[p]];
+        L->r[i] = s;
+    }
+    level_t *Lc = &h->lev[l + 1];
+    for (int I = 0; I < L->R.n; I++) {
+        double s = 0.0;
+        for (int p = L->R.rowptr[I]; p < L->R.rowptr[I + 1]; p++)
+            s += L->R.val[p] * L->r[L->R.col[p]];
+        Lc->b[I] = s;
+    }
+    vcycle(h, l + 1, Lc->b, Lc->x);
+    /* x += P x_c */
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int p = L->P.rowptr[i]; p < L->P.rowptr[i + 1]; p++)
+            s += L->P.val[p] * Lc->x[L->P.col[p]];
+        x[i] += s;
+    }
+    for (int s = 0; s < h->opt.post; s++)
+        mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 1, L->tmp);
+}
+
+/*
+ * One CPR application z = B v (Alg. 1 from x = 0, Eq. 3.1):
+ *   r_P = Pi_P^T v (decoupled restriction), e_P = B_P r_P (AMG V-cycle),
+ *   z = Pi_P e_P, r = v - A z, z += R r (BILU(0)).
+ */
+static void cpr_apply(o_handle *h, const double *v, double *z) {
+    int nb = h->nb;
+    for (int i = 0; i < nb; i++)
+        h->rp[i] = (h->w[3 * i] * v[3 * i] + h->w[3 * i + 1] * v[3 * i + 1]) +
+                   h->w[3 * i + 2] * v[3 * i + 2];
+    vcycle(h, 0, h->rp, h->ep);
+    for (int i = 0; i < nb; i++) {
+        z[3 * i] = h->ep[i];
+        z[3 * i + 1] = 0.0;
+        z[3 * i + 2] = 0.0;
+    }
+    bsr3_resid(nb, h->rowptr, h->col, h->pval, v, z, h->work1);
+    o_bilu0_solve(nb, h->rowptr, h->col, h->lu, h->bcolor, h->nbcolors, h->work1, h->work2);
+    for (int i = 0; i < 3 * nb; i++) z[i] += h->work2[i];
+}
+
+void o_cpr_apply(o_handle *h, const double *v, double *z) { cpr_apply(h, v, z); }
+void o_vcycle(o_handle *h, const double *b, double *x) { vcycle(h, 0, b, x); }
+void o_bilu_apply(o_handle *h, const double *r, double *z) {
+    o_bilu0_solve(h->nb, h->rowptr, h->col, h->lu, h->bcolor, h->nbcolors, r, z);
+}
+
+/* ----------------------------------------------------------------- FGMRES */
+
+typedef void (*precond_fn)(void *ctx, const double *v, double *z);
+
+typedef struct {
+    int nb;
+    const int *rowptr, *col;
+    const double *val;
+} op_ctx;
+
+static void identity_pc(void *ctx, const double *v, double *z) {
+    int n = 3 * ((op_ctx *)ctx)->nb;
+    memcpy(z, v, sizeof(double) * (size_t)n);
+}
+
+static void cpr_pc(void *ctx, const double *v, double *z) { cpr_apply((o_handle *)ctx, v, z); }
+
+/*
+ * Right-preconditioned flexible GMRES(m) following Alg. 2: Arnoldi with
+ * classical Gram-Schmidt (all h_ij from the same vector), Givens rotations on
+ * the Hessenberg matrix, stop when the estimated residual |g_{j+1}| falls
+ * below rtol*||r_0|| (r_0 of the initial guess) or when h_{j+1,j} = 0; after
+ * each cycle x += Z y and the true residual decides whether to restart.
+ * Z keeps the preconditioned vectors (flexible variant).  `hist`, when not
+ * NULL, receives the estimated relative residual after every inner step.
+ */
+static int fgmres(int nb, const int *rowptr, const int *col, const double *val, precond_fn pc,
+                  void *pctx, const double *b, double *x, double rtol, int m, int max_restarts,
+                  o_stats *st, double *hist) {
+    int n = 3 * nb;
+    double *V = xcalloc((size_t)(m + 1) * n, sizeof(double));
+    double *Z = xcalloc((size_t)m * n, sizeof(double));
+    double *H = xcalloc((size_t)(m + 1) * m, sizeof(double)); /* H[i*m + j] */
+    double *cs = xcalloc((size_t)m, sizeof(double));
+    double *sn = xcalloc((size_t)m, sizeof(double));
+    double *g = xcalloc((size_t)m + 1, sizeof(double));
+    double *y = xcalloc((size_t)m, sizeof(double));
+    double *r = xcalloc((size_t)n, sizeof(double));
+    double *w = xcalloc((size_t)n, sizeof(double));
+    int rc = O_NOT_CONVERGED, iters = 0, cycles = 0;
+    bsr3_resid(nb, rowptr, col, val, b, x, r);
+    double norm0 = sqrt(dot(n, r, r));
+    double rnorm = norm0;
+    if (!isfinite(norm0)) {
+        rc = O_ERR_BREAKDOWN;
+        goto done;
+    }
+    if (norm0 == 0.0) {
+        rc = O_OK;
+        goto done;
+    }
+    for (cycles = 0; cycles < max_restarts; cycles++) {
+        double beta = rnorm;
+        for (int i = 0; i < n; i++) V[i] = r[i] / beta;
+        for (int i = 0; i <= m; i++) g[i] = 0.0;
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; j++) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            pc(pctx, vj, zj);
+            o_bsr3_spmv(nb, rowptr, col, val, zj, w);
+            for (int i = 0; i <= j; i++) H[i * m + j] = dot(n, w, V + (size_t)i * n);
+            for (int i = 0; i <= j; i++) {
+                double hij = H[i * m + j];
+                const double *vi = V + (size_t)i * n;
+                for (int q = 0; q < n; q++) w[q] -= hij * vi[q];
+            }
+            double hn = sqrt(dot(n, w, w));
+            H[(j + 1) * m + j] = hn;
+            iters++;
+            k = j + 1;
+            if (!isfinite(hn)) {
+                rc = O_ERR_BREAKDOWN;
+                goto done;
+            }
+            /* apply the previous rotations to column j, then a new one */
+            for (int i = 0; i < j; i++) {
+                double a = H[i * m + j], c = H[(i + 1) * m + j];
+                H[i * m + j] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[j * m + j], c = H[(j + 1) * m + j];
+            double den = sqrt(a * a + c * c);
+            cs[j] = den == 0.0 ? 1.0 : a / den;
+            sn[j] = den == 0.0 ? 0.0 : c / den;
+            H[j * m + j] = den;
+            H[(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (hist) hist[iters - 1] = fabs(g[j + 1]) / norm0;
+            if (hn == 0.0) break;
+            for (int q = 0; q < n; q++) V[(size_t)(j + 1) * n + q] = w[q] / hn;
+            if (fabs(g[j + 1]) / norm0 < rtol) break;
+        }
+        /* y = H_k^-1 g (upper triangular), x += Z y */
+        for (int i = k - 1; i >= 0; i--) {
+            double s = g[i];
+            for (int q = i + 1; q < k; q++) s -= H[i * m + q] * y[q];
+            y[i] = s / H[i * m + i];
+        }
+        for (int i = 0; i < k; i++) {
+            const double *zi = Z + (size_t)i * n;
+            for (int q = 0; q < n; q++) x[q] += y[i] * zi[q];
+        }
+        bsr3_resid(nb, rowptr, col, val, b, x, r);
+        rnorm = sqrt(dot(n, r, r));
+        if (!isfinite(rnorm)) {
+            rc = O_ERR_BREAKDOWN;
+            break;
+        }
+        if (rnorm / norm0 < rtol) {
+            rc = O_OK;
+            cycles++;
+            break;
+        }
+    }
+done:
+    if (st) {
+        st->iters = iters;
+        st->restarts = cycles;
+        st->converged = rc == O_OK;
+        st->rel_res = norm0 > 0.0 ? rnorm / norm0 : 0.0;
+    }
+    free(V);
+    free(Z);
+    free(H);
+    free(cs);
+    free(sn);
+    free(g);
+    free(y);
+    free(r);
+    free(w);
+    return rc;
+}
+
+int o_fgmres_identity(int nb, const int *rowptr, const int *col, const double *val,
+                      const double *b, double *x, double rtol, int m, int max_restarts,
+                      o_stats *st, double *hist) {
+    op_ctx ctx = {nb, rowptr, col, val};
+    return fgmres(nb, rowptr, col, val, identity_pc, &ctx, b, x, rtol, m, max_restarts, st, hist);
+}
+
+/* ------------------------------------------------------------------- API */
+
+static int check_bsr(int nb, const int *rowptr, const int *col) {
+    if (nb <= 0 || rowptr[0] != 0) return O_ERR_INVALID;
+    for (int i = 0; i < nb; i++) {
+        if (rowptr[i + 1] < rowptr[i]) return O_ERR_INVALID;
+        int has_diag = 0;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+            if (col[p] < 0 || col[p] >= nb) return O_ERR_INVALID;
+            if (p > rowptr[i] && col[p] <= col[p - 1]) return O_ERR_INVALID;
+            has_diag |= col[p] == i;
+        }
+        if (!has_diag) return O_ERR_INVALID;
+    }
+    return O_OK;
+}
+
+static void alloc_work(o_handle *h) {
+    size_t n = 3 * (size_t)h->nb;
+    h->work1 = xcalloc(n, sizeof(double));
+    h->work2 = xcalloc(n, sizeof(double));
+    h->work3 = xcalloc(n, sizeof(double));
+    h->rp = xcalloc((size_t)h->nb, sizeof(double));
+    h->ep = xcalloc((size_t)h->nb, sizeof(double));
+}
+
+static void free_matrix(o_handle *h) {
+    free(h->rowptr);
+    free(h->col);
+    free(h->val);
+    free(h->work1);
+    free(h->work2);
+    free(h->work3);
+    free(h->rp);
+    free(h->ep);
+    h->rowptr = h->col = NULL;
+    h->val = h->work1 = h->work2 = h->work3 = h->rp = h->ep = NULL;
+}
+
+static int load_matrix(o_handle *h, int nb, const int *rowptr, const int *col,
+                       const double *val) {
+    int rc = check_bsr(nb, rowptr, col);
+    if (rc != O_OK) return rc;
+    free_matrix(h);
+    h->nb = nb;
+    h->nnzb = rowptr[nb];
+    h->rowptr = xcalloc((size_t)nb + 1, sizeof(int));
+    h->col = xcalloc((size_t)h->nnzb, sizeof(int));
+    h->val = xcalloc(9 * (size_t)h->nnzb, sizeof(double));
+    memcpy(h->rowptr, rowptr, sizeof(int) * ((size_t)nb + 1));
+    memcpy(h->col, col, sizeof(int) * (size_t)h->nnzb);
+    memcpy(h->val, val, sizeof(double) * 9 * (size_t)h->nnzb);
+    alloc_work(h);
+    return O_OK;
+}
+
+int o_setup(o_handle **out, int nb, const int *rowptr, const int *col, const double *val,
+            const o_opts *opt) {
+    o_handle *h = xcalloc(1, sizeof(o_handle));
+    if (opt) h->opt = *opt;
+    else o_default_opts(&h->opt);
+    int rc = load_matrix(h, nb, rowptr, col, val);
+    if (rc == O_OK) rc = build_preconditioner(h);
+    if (rc != O_OK) {
+        o_destroy(h);
+        *out = NULL;
+        return rc;
+    }
+    h->setup_count = 1;
+    h->setup_called = 1;
+    h->updates = 1;
+    h->last_iters = -1;
+    *out = h;
+    return O_OK;
+}
+
+/*
+ * A new Jacobian A^(k) (Alg. 3): the previous B is reused iff k > 1, a solve
+ * has run since the last setup, It^(k-1) <= mu and the size and pattern are
+ * unchanged (Remark 4.2); otherwise B is rebuilt from A^(k).
+ */
+int o_update(o_handle *h, int nb, const int *rowptr, const int *col, const double *val) {
+    int same = nb == h->nb && rowptr[nb] == h->nnzb &&
+               memcmp(rowptr, h->rowptr, sizeof(int) * ((size_t)nb + 1)) == 0 &&
+               memcmp(col, h->col, sizeof(int) * (size_t)h->nnzb) == 0;
+    int rc;
+    if (same) {
+        memcpy(h->val, val, sizeof(double) * 9 * (size_t)h->nnzb);
+    } else {
+        rc = load_matrix(h, nb, rowptr, col, val);
+        if (rc != O_OK) return rc;
+    }
+    h->updates++;
+    int reuse = same && h->updates > 1 && h->last_iters >= 0 && h->last_iters <= h->opt.mu;
+    h->setup_called = !reuse;
+    if (reuse) return O_OK;
+    rc = build_preconditioner(h);
+    if (rc != O_OK) return rc;
+    h->setup_count++;
+    h->last_iters = -1;
+    return O_OK;
+}
+
+int o_solve(o_handle *h, const double *b, double *x, double rtol, o_stats *st) {
+    o_stats s;
+    memset(&s, 0, sizeof(s));
+    int rc = fgmres(h->nb, h->rowptr, h->col, h->val, cpr_pc, h, b, x, rtol, h->opt.restart,
+                    h->opt.max_restarts, &s, NULL);
+    h->last_iters = s.iters;
+    s.setup_called = h->setup_called;
+    s.setup_count = h->setup_count;
+    s.levels = h->nlev;
+    if (st) *st = s;
+    return rc;
+}
+
+void o_destroy(o_handle *h) {
+    if (!h) return;
+    free_setup(h);
+    free_matrix(h);
+    free(h);
+}
+
+/* ------------------------------------------------------------ inspection */
+
+int o_num_levels(const o_handle *h) { return h->nlev; }
+int o_last_iters(const o_handle *h) { return (int)h->last_iters; }
+
+void o_level_info(const o_handle *h, int l, int *n, int *nnz, int *ncolors, int *nc, int *nnzP) {
+    const level_t *L = &h->lev[l];
+    *n = L->A.n;
+    *nnz = L->A.nnz;
+    *ncolors = L->ncolors;
+    *nc = L->cf ? L->nc : 0;
+    *nnzP = L->cf ? L->P.nnz : 0;
+}
+
+void o_level_get(const o_handle *h, int l, int *rowptr, int *col, double *val, int *color,
+                 int *cf, int *prow, int *pcol, double *pval) {
+    const level_t *L = &h->lev[l];
+    o_csr_copy(&L->A, rowptr, col, val);
+    if (L->color && color) memcpy(color, L->color, sizeof(int) * (size_t)L->A.n);
+    if (L->cf && cf) memcpy(cf, L->cf, sizeof(int) * (size_t)L->A.n);
+    if (L->cf && prow) o_csr_copy(&L->P, prow, pcol, pval);
+}
+
+void o_get_weights(const o_handle *h, double *w) {
+    memcpy(w, h->w, sizeof(double) * 3 * (size_t)h->nb);
+}
+
+int o_bilu_ncolors(const o_handle *h) { return h->nbcolors; }
+
+void o_bilu_get(const o_handle *h, int *bcolor, double *lu) {
+    memcpy(bcolor, h->bcolor, sizeof(int) * (size_t)h->nb);
+    memcpy(lu, h->lu, sizeof(double) * 9 * (size_t)h->nnzb);
+}

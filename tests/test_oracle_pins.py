@@ -1,0 +1,518 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks one oracle step against something other than the oracle:
+library routines (numpy/scipy/networkx), closed forms, the paper's stated
+propositions and special cases, or brute force on tiny inputs.
+"""
+import os
+
+import networkx as nx
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import blackoil_synth as bs
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def csr_dense(rowptr, col, val, n, m=None):
+    return sp.csr_matrix((val, col, rowptr), shape=(n, m or n)).toarray()
+
+
+def read_grid(name):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, name)) if not l.startswith("#")]
+    return np.array([[int(v) for v in r] for r in rows if r])
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return bs.tiny()
+
+
+# ------------------------------------------------------------------ SpMV
+
+def test_bsr3_spmv_matches_scipy():
+    J = bs.jacobian("20x20x5")
+    x = np.random.default_rng(1).standard_normal(J.n)
+    y = oracle.bsr3_spmv(J, x)
+    ref = J.to_scipy() @ x
+    assert np.allclose(y, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+# ------------------------------------------------------------- decoupling
+
+def test_decoupling_weights_and_pressure_matrix(tiny):
+    J = tiny
+    w, ap = oracle.decouple(J, mode=1)
+    blocks = J.val.reshape(-1, 3, 3)
+    A = J.to_dense()
+    W = np.zeros((J.n, J.nb))
+    Pi = np.zeros((J.n, J.nb))
+    for i in range(J.nb):
+        p = J.rowptr[i] + list(J.col[J.rowptr[i]:J.rowptr[i + 1]]).index(i)
+        # w_i = D_i^-T e_1  <=>  D_i^T w_i = e_1
+        assert np.allclose(blocks[p].T @ w[3 * i:3 * i + 3], [1, 0, 0], atol=1e-12)
+        W[3 * i:3 * i + 3, i] = w[3 * i:3 * i + 3]
+        Pi[3 * i, i] = 1.0
+    AP = W.T @ A @ Pi                                   # Pi_P^T A Pi_P with weights
+    APo = csr_dense(J.rowptr, J.col, ap, J.nb)
+    assert np.allclose(APo, AP, rtol=1e-12, atol=1e-12 * np.abs(AP).max())
+    # mode 0: injection, A_P = the [0][0] entries
+    w0, ap0 = oracle.decouple(J, mode=0)
+    assert np.array_equal(w0.reshape(-1, 3), np.tile([1.0, 0, 0], (J.nb, 1)))
+    assert np.array_equal(ap0, blocks[:, 0, 0])
+
+
+# ------------------------------------------------------- strength, coloring
+
+def _graph(G):
+    g = nx.Graph()
+    g.add_nodes_from(range(G.n))
+    for i in range(G.n):
+        for p in range(G.rowptr[i], G.rowptr[i + 1]):
+            if G.col[p] != i:
+                g.add_edge(i, int(G.col[p]))
+    return g
+
+
+def _pressure_level0(J):
+    _, ap = oracle.decouple(J, 1)
+    return J.rowptr, J.col, ap
+
+
+def test_strength_special_cases():
+    rp, cl, v = bs.random_sparse(40, 0.15, seed=3, neg_offdiag=False)
+    n = len(rp) - 1
+    S1 = oracle.strength_color(rp, cl, v, 1.0)
+    assert S1.rowptr[-1] == 0                          # theta = 1: no strong edge (Sec. 5.2)
+    S0 = oracle.strength_color(rp, cl, v, 0.0)
+    off = {(i, int(cl[p])) for i in range(n) for p in range(rp[i], rp[i + 1])
+           if cl[p] != i and v[p] != 0}
+    assert S0.pattern() == off                          # theta = 0: every off-diagonal nonzero
+    Sa = oracle.strength_color(rp, cl, v, 0.05).pattern()
+    Sb = oracle.strength_color(rp, cl, v, 0.1).pattern()
+    assert Sb <= Sa <= off                              # monotone in theta
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.05, 0.1, 0.3])
+def test_jp_coloring_props_and_greedy_equivalence(theta):
+    J = bs.jacobian("20x20x5")
+    rp, cl, ap = _pressure_level0(J)
+    S = oracle.strength_color(rp, cl, ap, theta)
+    G = oracle.sym_union(S)
+    color, nc = oracle.jp_color(G, seed=7, salt=0, level=0)
+    g = _graph(G)
+    # Prop. 5.3: everyone colored, finitely many colors; goal (c): no edge inside a color
+    assert color.min() == 0 and color.max() == nc - 1
+    assert all(color[a] != color[b] for a, b in g.edges)
+    # Prop. 5.1: c <= max degree + 1
+    assert nc <= max(dict(g.degree).values(), default=0) + 1
+    # JP with key (deg, hash, i) == first-fit greedy in descending key order
+    key = {i: (g.degree[i], oracle.hash32(7, 0, 0, i), i) for i in range(G.n)}
+    order = sorted(range(G.n), key=lambda i: key[i], reverse=True)
+    greedy = nx.coloring.greedy_color(g, strategy=lambda gg, colors: iter(order))
+    assert all(greedy[i] == color[i] for i in range(G.n))
+
+
+def test_theta_one_gives_one_color_and_jacobi():
+    J = bs.jacobian("20x20x5")
+    rp, cl, ap = _pressure_level0(J)
+    G = oracle.sym_union(oracle.strength_color(rp, cl, ap, 1.0))
+    color, nc = oracle.jp_color(G)
+    assert nc == 1                                       # Sec. 5.2: theta = 1 => c = 1
+    rng = np.random.default_rng(0)
+    b, x0 = rng.standard_normal(J.nb), rng.standard_normal(J.nb)
+    x1 = oracle.mcgs_sweep(rp, cl, ap, color, nc, b, x0)
+    A = csr_dense(rp, cl, ap, J.nb)
+    jac = x0 + (b - A @ x0) / np.diag(A)                 # one Jacobi step
+    assert np.allclose(x1, jac, rtol=1e-12, atol=1e-12 * np.abs(jac).max())
+
+
+def test_prop52_color_blocks_diagonal_at_theta0():
+    J = bs.jacobian("20x20x5")
+    rp, cl, ap = _pressure_level0(J)
+    G = oracle.sym_union(oracle.strength_color(rp, cl, ap, 0.0))
+    color, nc = oracle.jp_color(G, seed=3)
+    A = csr_dense(rp, cl, ap, J.nb)
+    for c in range(nc):
+        idx = np.nonzero(color == c)[0]
+        blk = A[np.ix_(idx, idx)]
+        assert np.count_nonzero(blk - np.diag(np.diag(blk))) == 0
+
+
+def test_five_point_grid_coloring():
+    rp, cl, v = bs.laplacian_2d(9, 7)
+    G = oracle.sym_union(oracle.strength_color(rp, cl, v, 0.0))
+    color, nc = oracle.jp_color(G, seed=1)
+    g = _graph(G)
+    assert 2 <= nc <= 5
+    assert all(color[a] != color[b] for a, b in g.edges)
+
+
+def _seq_gs_in_order(A, b, x, order):
+    """Sequential GS visiting rows in `order` (scipy triangular solve on the permuted matrix)."""
+    Ap = A[np.ix_(order, order)]
+    lower = sp.csr_matrix(np.tril(Ap))
+    upper = np.triu(Ap, 1)
+    xp = spla.spsolve_triangular(lower, b[order] - upper @ x[order], lower=True)
+    out = np.empty_like(x)
+    out[order] = xp
+    return out
+
+
+def test_mcgs_theta0_equals_sequential_gs_in_color_order():
+    J = bs.jacobian("20x20x5")
+    rp, cl, ap = _pressure_level0(J)
+    G = oracle.sym_union(oracle.strength_color(rp, cl, ap, 0.0))
+    color, nc = oracle.jp_color(G, seed=5)
+    A = csr_dense(rp, cl, ap, J.nb)
+    rng = np.random.default_rng(2)
+    b, x0 = rng.standard_normal(J.nb), rng.standard_normal(J.nb)
+    order = np.lexsort((np.arange(J.nb), color))
+    x1 = oracle.mcgs_sweep(rp, cl, ap, color, nc, b, x0)
+    ref = _seq_gs_in_order(A, b, x0, order)
+    assert np.allclose(x1, ref, rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+    # descending colors == sequential GS over the reversed color order
+    x2 = oracle.mcgs_sweep(rp, cl, ap, color, nc, b, x0, descending=True)
+    order_d = np.lexsort((np.arange(J.nb), -color))
+    ref2 = _seq_gs_in_order(A, b, x0, order_d)
+    assert np.allclose(x2, ref2, rtol=1e-11, atol=1e-11 * np.abs(ref2).max())
+
+
+@pytest.mark.parametrize("grid", ["redblack_4x4.txt", "fourcolor_4x4.txt"])
+def test_structured_grid_colorings_from_the_paper(grid):
+    """Sec. 3.2 / Fig. 2: multi-color GS over the red-black (5-point) and the
+    four-color (9-point) groupings equals sequential GS in color order."""
+    colors = read_grid(grid).ravel().astype(np.int32)
+    n = 16
+    nine = grid.startswith("four")
+    A = np.zeros((n, n))
+    for j in range(4):
+        for i in range(4):
+            c = i + 4 * j
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    if (di, dj) == (0, 0) or (not nine and di != 0 and dj != 0):
+                        continue
+                    ii, jj = i + di, j + dj
+                    if 0 <= ii < 4 and 0 <= jj < 4:
+                        A[c, ii + 4 * jj] = -1.0
+            A[c, c] = -A[c].sum() + 0.5
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    rp, cl, v = M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data
+    # the grouping is a valid coloring (goal (c)) with 2 resp. 4 colors
+    nc = int(colors.max()) + 1
+    assert nc == (4 if nine else 2)
+    assert all(colors[a] != colors[b] for a, b in zip(*np.nonzero(A - np.diag(np.diag(A)))))
+    rng = np.random.default_rng(4)
+    b, x0 = rng.standard_normal(n), rng.standard_normal(n)
+    x1 = oracle.mcgs_sweep(rp, cl, v, colors, nc, b, x0)
+    ref = _seq_gs_in_order(A, b, x0, np.lexsort((np.arange(n), colors)))
+    assert np.allclose(x1, ref, rtol=1e-13, atol=1e-13)
+
+
+# -------------------------------------------------------------- coarsening
+
+def _pmis_sequential(S, seed, salt, level):
+    """Brute force: PMIS's result equals a sequential sweep in descending key
+    order where a point becomes C unless a C point of larger key lies in S_i."""
+    n = S.n
+    T = oracle.transpose(S)
+    lam = np.diff(T.rowptr)
+    key = [(int(lam[i]), oracle.hash32(seed, salt, level, i), i) for i in range(n)]
+    cf = -np.ones(n, int)
+    for i in range(n):
+        if S.rowptr[i + 1] == S.rowptr[i] and lam[i] == 0:
+            cf[i] = 0
+    for i in sorted(range(n), key=lambda i: key[i], reverse=True):
+        if cf[i] != -1:
+            continue
+        Si = S.col[S.rowptr[i]:S.rowptr[i + 1]]
+        cf[i] = 0 if any(cf[j] == 1 for j in Si) else 1
+    return cf
+
+
+@pytest.mark.parametrize("which", ["laplace", "random", "pressure"])
+def test_pmis_properties_and_sequential_equivalence(which):
+    if which == "laplace":
+        rp, cl, v = bs.laplacian_2d(12, 9, shift=0.01)
+    elif which == "random":
+        rp, cl, v = bs.random_sparse(60, 0.08, seed=11)
+    else:
+        rp, cl, v = _pressure_level0(bs.jacobian("20x20x5"))
+    S = oracle.strength_rs(rp, cl, v, 0.25)
+    cf, nc = oracle.pmis(S, seed=3, salt=1, level=0)
+    n = S.n
+    assert set(np.unique(cf)) <= {0, 1} and nc == int(cf.sum()) and nc > 0
+    T = oracle.transpose(S)
+    for i in range(n):
+        Si = S.col[S.rowptr[i]:S.rowptr[i + 1]]
+        if cf[i] == 0 and len(Si):
+            assert any(cf[j] == 1 for j in Si)          # every F point has a strong C point
+        if len(Si) == 0 and T.rowptr[i + 1] == T.rowptr[i]:
+            assert cf[i] == 0                            # isolated points are F
+    assert np.array_equal(cf, _pmis_sequential(S, 3, 1, 0))
+
+
+def test_rs_strength_special_cases():
+    rp, cl, v = bs.laplacian_2d(6, 5, shift=0.1)
+    S = oracle.strength_rs(rp, cl, v, 0.25)
+    off = {(i, int(cl[p])) for i in range(len(rp) - 1) for p in range(rp[i], rp[i + 1])
+           if cl[p] != i}
+    assert S.pattern() == off                            # equal couplings: all strong
+    # a positive off-diagonal entry is never strong (sign convention)
+    v2 = v.copy()
+    p = rp[7] + 1 if cl[rp[7]] == 7 else rp[7]
+    v2[p] = 0.5
+    S2 = oracle.strength_rs(rp, cl, v2, 0.25)
+    assert (7, int(cl[p])) not in S2.pattern()
+
+
+def _zero_rowsum(n_x, n_y, pos_frac, seed):
+    """Zero-row-sum matrix with negative (and optionally some positive) couplings."""
+    rp, cl, v = bs.laplacian_2d(n_x, n_y)
+    rng = np.random.default_rng(seed)
+    A = csr_dense(rp, cl, v, len(rp) - 1)
+    n = A.shape[0]
+    off = A - np.diag(np.diag(A))
+    scale = rng.uniform(0.5, 2.0, (n, n))
+    off = off * (scale + scale.T) / 2
+    flip = (rng.random((n, n)) < pos_frac) & (off != 0)
+    off = np.where(flip, 0.1 * np.abs(off), off)
+    A = off - np.diag(off.sum(axis=1))
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    return M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data, A
+
+
+@pytest.mark.parametrize("pos_frac", [0.0, 0.15])
+def test_direct_interpolation_preserves_constants(pos_frac):
+    rp, cl, v, A = _zero_rowsum(10, 8, pos_frac, seed=2)
+    n = A.shape[0]
+    S = oracle.strength_rs(rp, cl, v, 0.25)
+    cf, nc = oracle.pmis(S, seed=1)
+    P = oracle.interp_direct(rp, cl, v, S, cf)
+    Pd = P.dense()
+    cidx = np.cumsum(cf) - 1
+    for i in range(n):
+        if cf[i] == 1:
+            assert np.array_equal(Pd[i], np.eye(nc)[cidx[i]])   # C rows are unit rows
+    # Stueben: for zero row sums, P 1 = 1 on F rows with strong C points
+    ones = Pd @ np.ones(nc)
+    has_c = np.array([any(cf[j] == 1 for j in S.col[S.rowptr[i]:S.rowptr[i + 1]])
+                      for i in range(n)])
+    assert np.allclose(ones[has_c], 1.0, rtol=0, atol=1e-13)
+    assert (P.val > 0).all()
+
+
+def test_transpose_and_galerkin_product_match_dense():
+    J = bs.jacobian("20x20x5")
+    rp, cl, ap = _pressure_level0(J)
+    S = oracle.strength_rs(rp, cl, ap, 0.25)
+    cf, nc = oracle.pmis(S, seed=0)
+    P = oracle.interp_direct(rp, cl, ap, S, cf)
+    R = oracle.transpose(P)
+    assert np.array_equal(R.dense(), P.dense().T)
+    A = oracle.CSR(J.nb, J.nb, rp, cl, ap)
+    Ac = oracle.spgemm(R, oracle.spgemm(A, P))
+    ref = P.dense().T @ A.dense() @ P.dense()
+    D = Ac.dense()
+    assert np.allclose(D, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    nzr = set(zip(*np.nonzero(np.abs(ref) > 1e-12 * np.abs(ref).max())))
+    assert nzr <= Ac.pattern()                                   # pattern covers the product
+    for i in range(Ac.n):                                        # sorted, unique columns
+        c = Ac.col[Ac.rowptr[i]:Ac.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+def test_dense_lu_matches_numpy():
+    rng = np.random.default_rng(5)
+    for n in (1, 7, 64):
+        A = rng.standard_normal((n, n)) + n * np.eye(n) * 0.1
+        A[0, 0] = 0.0 if n > 1 else 1.0                          # force a pivot swap
+        b = rng.standard_normal(n)
+        assert np.allclose(oracle.dense_lu_solve(A, b), np.linalg.solve(A, b), rtol=1e-10)
+
+
+# ------------------------------------------------------------------ BILU(0)
+
+def _bilu_dense_factors(J, bcolor, nbcolors, lu):
+    order = np.lexsort((np.arange(J.nb), bcolor))
+    pos = np.empty(J.nb, int)
+    pos[order] = np.arange(J.nb)
+    L = np.eye(J.n)
+    U = np.zeros((J.n, J.n))
+    blk = lu.reshape(-1, 3, 3)
+    for i in range(J.nb):
+        for p in range(J.rowptr[i], J.rowptr[i + 1]):
+            j = J.col[p]
+            sl_i, sl_j = slice(3 * i, 3 * i + 3), slice(3 * j, 3 * j + 3)
+            if j == i:
+                U[sl_i, sl_j] = np.linalg.inv(blk[p])
+            elif pos[j] < pos[i]:
+                L[sl_i, sl_j] = blk[p]
+            else:
+                U[sl_i, sl_j] = blk[p]
+    return L, U
+
+
+def test_bilu0_defining_property(tiny):
+    J = tiny
+    bcolor, nbc, lu = oracle.bilu0(J, seed=4)
+    # coloring of the block graph is valid (theta = 0: no two neighbours share a color)
+    for i in range(J.nb):
+        for p in range(J.rowptr[i], J.rowptr[i + 1]):
+            if J.col[p] != i:
+                assert bcolor[J.col[p]] != bcolor[i]
+    L, U = _bilu_dense_factors(J, bcolor, nbc, lu)
+    LU = L @ U
+    A = J.to_dense()
+    mask = np.zeros_like(A, bool)
+    for i in range(J.nb):
+        for p in range(J.rowptr[i], J.rowptr[i + 1]):
+            j = J.col[p]
+            mask[3 * i:3 * i + 3, 3 * j:3 * j + 3] = True
+    # (L U)_ij = A_ij on the block pattern
+    assert np.allclose(LU[mask], A[mask], rtol=1e-11, atol=1e-11 * np.abs(A).max())
+    r = np.random.default_rng(0).standard_normal(J.n)
+    z = oracle.bilu0_solve(J, bcolor, nbc, lu, r)
+    assert np.allclose(z, np.linalg.solve(LU, r), rtol=1e-10, atol=1e-12)
+
+
+def test_bilu0_block_diagonal_is_exact():
+    J = bs.tiny(3, 3, 1, wells="none")
+    keep = J.col == np.repeat(np.arange(J.nb), np.diff(J.rowptr))
+    Jd = bs.Jacobian(J.nb, np.concatenate([[0], np.cumsum(np.ones(J.nb, int))]).astype(np.int32),
+                     np.arange(J.nb, dtype=np.int32),
+                     J.val.reshape(-1, 9)[keep].ravel().copy(), J.b)
+    bcolor, nbc, lu = oracle.bilu0(Jd)
+    r = np.random.default_rng(1).standard_normal(Jd.n)
+    z = oracle.bilu0_solve(Jd, bcolor, nbc, lu, r)
+    assert np.allclose(z, np.linalg.solve(Jd.to_dense(), r), rtol=1e-12)
+
+
+# ------------------------------------------------------ CPR, Eq. 3.1, FGMRES
+
+def test_cpr_apply_is_eq31_with_exact_pressure_solve(tiny):
+    """Eq. 3.1: B = Pi B_P W^T + M^-1 (I - A Pi B_P W^T), B_P = A_P^-1 (one level)."""
+    J = tiny
+    s = oracle.Solver(J, coarse_max=10 ** 6)
+    assert s.nlev == 1
+    A = J.to_dense()
+    w = s.weights()
+    W = np.zeros((J.n, J.nb))
+    Pi = np.zeros((J.n, J.nb))
+    for i in range(J.nb):
+        W[3 * i:3 * i + 3, i] = w[3 * i:3 * i + 3]
+        Pi[3 * i, i] = 1.0
+    AP = W.T @ A @ Pi
+    bc, nbc, lu = s.bilu()
+    L, U = _bilu_dense_factors(J, bc, nbc, lu)
+    Minv = np.linalg.inv(L @ U)
+    C1 = Pi @ np.linalg.inv(AP) @ W.T
+    B = C1 + Minv @ (np.eye(J.n) - A @ C1)
+    Bo = np.column_stack([s.cpr_apply(e) for e in np.eye(J.n)])
+    assert np.allclose(Bo, B, rtol=1e-9, atol=1e-9 * np.abs(B).max())
+    # and I - B A = (I - M^-1 A)(I - Pi B_P W^T A)
+    I = np.eye(J.n)
+    assert np.allclose(I - Bo @ A, (I - Minv @ A) @ (I - C1 @ A), atol=1e-8)
+    s.close()
+
+
+def test_vcycle_two_level_composition(tiny):
+    """V(1,0) with an exact coarse solve: x = S b + P A_c^-1 R (b - A S b)."""
+    J = tiny
+    s = oracle.Solver(J, coarse_max=4, max_levels=2, pre=1, post=0)
+    assert s.nlev == 2
+    L0, L1 = s.level(0), s.level(1)
+    A = L0["A"].dense()
+    P = L0["P"].dense()
+    Ac = L1["A"].dense()
+    assert np.allclose(Ac, P.T @ A @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    b = np.random.default_rng(3).standard_normal(J.nb)
+    a0 = L0["A"]
+    Sb = oracle.mcgs_sweep(a0.rowptr, a0.col, a0.val, L0["color"], L0["ncolors"], b,
+                           np.zeros(J.nb))
+    ref = Sb + P @ np.linalg.solve(Ac, P.T @ (b - A @ Sb))
+    x = s.vcycle(b)
+    assert np.allclose(x, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    s.close()
+
+
+@pytest.mark.parametrize("coarse_max", [10 ** 6, 8])
+def test_whole_solve_reaches_direct_solution(tiny, coarse_max):
+    J = tiny
+    s = oracle.Solver(J, coarse_max=coarse_max)
+    x, st = s.solve(J.b, rtol=1e-12)
+    ref = np.linalg.solve(J.to_dense(), J.b)
+    assert st["converged"]
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+    s.close()
+
+
+def test_fgmres_identity_exact_in_n_steps():
+    rng = np.random.default_rng(8)
+    J = bs.tiny(3, 3, 1, wells="none", seed=3)             # 9 block rows, n = 27 <= 30
+    x, st, hist, rc = oracle.fgmres_identity(J, J.b, rtol=1e-13, m=30, max_restarts=1)
+    ref = np.linalg.solve(J.to_dense(), J.b)
+    assert rc == 0 and st["iters"] <= J.n and st["restarts"] == 1
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.all(np.diff(hist) <= 1e-15)                     # GMRES residuals never increase
+    x0 = rng.standard_normal(J.n)
+    x2, st2, _, rc2 = oracle.fgmres_identity(J, J.b, x0=x0, rtol=1e-13, m=30, max_restarts=1)
+    assert rc2 == 0 and np.linalg.norm(x2 - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_zero_rhs_and_initial_guess():
+    J = bs.tiny()
+    s = oracle.Solver(J)
+    x, st = s.solve(np.zeros(J.n))
+    assert st["iters"] == 0 and st["converged"] and not x.any()
+    # a nonzero initial guess reaches the same solution (criterion relative to r_0, Alg. 2)
+    ref = np.linalg.solve(J.to_dense(), J.b)
+    x0 = np.random.default_rng(0).standard_normal(J.n)
+    x, st = s.solve(J.b, x0=x0, rtol=1e-12)
+    assert st["converged"] and np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+    s.close()
+
+
+# ------------------------------------------------------------- adaptive rule
+
+@pytest.mark.parametrize("mu", [0, 5, 10 ** 6])
+def test_adaptive_setup_rule(mu):
+    """Alg. 3: reuse B^(k-1) iff k > 1 and It^(k-1) <= mu; mu = 0 is plain CPR."""
+    g = bs.GridSpec(6, 6, 3, 0.0, 1.0, 1.0, None, "corners", seed=2)
+    seq = list(bs.jacobian_sequence(g, 6, drift=0.05))
+    s = oracle.Solver(seq[0], mu=mu)
+    calls, iters = [1], []
+    _, st = s.solve(seq[0].b)
+    iters.append(st["iters"])
+    for J in seq[1:]:
+        s.update(J)
+        _, st = s.solve(J.b)
+        calls.append(st["setup_called"])
+        iters.append(st["iters"])
+        assert st["converged"]
+    expect = [1] + [int(iters[k - 1] > mu) for k in range(1, len(seq))]
+    assert calls == expect
+    if mu == 0:
+        assert calls == [1] * len(seq)
+    if mu == 10 ** 6:
+        assert calls == [1] + [0] * (len(seq) - 1)
+    s.close()
+
+
+def test_pattern_change_forces_setup():
+    """Remark 4.2: a new size forces a new setup whatever mu says."""
+    s = oracle.Solver(bs.tiny(4, 4, 2), mu=10 ** 6)
+    s.solve(bs.tiny(4, 4, 2).b)
+    J2 = bs.tiny(5, 4, 2)
+    s.update(J2)
+    x, st = s.solve(J2.b)
+    assert st["setup_called"] == 1 and st["converged"]
+    s.close()
