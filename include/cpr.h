@@ -1,0 +1,177 @@
+/*
+ * cpr.h -- C ABI of the B300 (sm_103a) CPR-preconditioned FGMRES solver for
+ * fully implicit black-oil Jacobians in 3x3 block sparse row form.
+ *
+ * Method: arXiv 2201.01970, "Parallel Multi-Stage Preconditioners with
+ * Adaptive Setup for the Black Oil Model".
+ *   - the CPR preconditioner B: Eq. 3.1 and Alg. 1 (Sec. 3.1);
+ *   - the outer solver: right-preconditioned GMRES, Alg. 2 (Sec. 4), run here
+ *     in its flexible form (FGMRES) with restart length m;
+ *   - the adaptive setup rule: Alg. 3 and Remark 4.2 (Sec. 4);
+ *   - the AMG smoother: multi-color Gauss-Seidel over the colors of the
+ *     strong-connection matrix, Eq. 5.1 and Alg. 6 (Sec. 5.2).
+ *
+ * Conventions for every call below
+ *   - Block rows: nb >= 1.  A 3x3 block is 9 doubles, row-major.  rowptr has
+ *     nb+1 entries starting at 0; col indices of a row are strictly increasing
+ *     and each row holds its diagonal block.  Violations return CPR_ERR_INVALID.
+ *   - Vectors have 3*nb doubles, ordered (P, S_1, S_2) per block row (Eq. 2.8);
+ *     well rows (Eq. 2.7) are ordinary block rows.
+ *   - Pointers passed to cpr_setup, cpr_update and cpr_solve may be host or
+ *     device (CUDA) pointers; the library detects which.  Host buffers are
+ *     copied in and out inside the call (pinned host memory copies fastest).
+ *   - All GPU work is ordered on opts.stream (NULL: a stream the handle
+ *     creates).  cpr_solve returns after the result is in x.
+ *   - Ownership: the caller owns A, b and x.  The library copies A's values
+ *     into its own storage, so A may be freed or overwritten after the call
+ *     returns.  The handle owns everything else until cpr_destroy.
+ *   - Errors: 0 = success, 1 = CPR_NOT_CONVERGED (x holds the last iterate),
+ *     negative = failure (see CPR_ERR_*).  After a failure the handle may only
+ *     be destroyed, except for CPR_ERR_INVALID from cpr_update/cpr_solve,
+ *     which leaves it unchanged.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef CPR_B300_H
+#define CPR_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPR_OK 0
+#define CPR_NOT_CONVERGED 1
+#define CPR_ERR_INVALID (-1)   /* malformed matrix, sizes or options */
+#define CPR_ERR_CUDA (-2)      /* a CUDA call failed */
+#define CPR_ERR_OOM (-3)       /* device memory exhausted */
+#define CPR_ERR_SINGULAR (-4)  /* zero pivot: block diagonal, smoother diagonal or coarse LU */
+#define CPR_ERR_BREAKDOWN (-5) /* NaN/Inf in the iteration or the right-hand side */
+#define CPR_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+
+typedef struct cpr_handle cpr_handle;
+
+/* A 3x3 BSR matrix (Eq. 2.7/2.8): val has 9*nnzb doubles. */
+typedef struct {
+    int32_t nb, nnzb;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const double *val;
+} cpr_bsr3;
+
+typedef struct {
+    double theta_color; /* Eq. 5.1 strength threshold for the smoother's coloring; default 0.05 */
+    double theta_amg;   /* classical strength threshold for C/F splitting; default 0.25 */
+    int mu;             /* Alg. 3 threshold: reuse B while It^(k-1) <= mu; 0 = setup every time; default 30 */
+    int restart;        /* FGMRES restart length m, 1..64; default 30 */
+    int max_restarts;   /* maximum restart cycles (MaxIt of Alg. 2); default 100 */
+    int precond_fp32;   /* 1: B computes in FP32 (storage and accumulation); outer FGMRES stays FP64 */
+    int decouple;       /* 1: ABF weights w_i = D_i^-T e_1 for Pi_P^T; 0: plain injection; default 1 */
+    int pre, post;      /* V-cycle smoothing sweeps; default 1, 1 */
+    int coarse_max;     /* coarsest level size solved densely; default 256, at most 4096 */
+    int max_levels;     /* default 20 */
+    uint64_t seed;      /* hash seed of coloring and C/F splitting; default 0 */
+    void *stream;       /* cudaStream_t; NULL = the handle creates its own */
+} cpr_opts;
+
+typedef struct {
+    int iters;          /* inner (Arnoldi) steps of this solve = It of Alg. 3 */
+    int restarts;       /* restart cycles used */
+    int setup_called;   /* 1 if the last cpr_setup/cpr_update built B */
+    int setup_count;    /* total builds of B by this handle */
+    int levels;         /* AMG levels, coarsest included */
+    int converged;
+    double rel_res;     /* ||b - A x|| / ||b - A x_0||, true FP64 residual */
+    double setup_ms;    /* wall time of the last build of B (0 if reused) */
+    double solve_ms;    /* wall time of this cpr_solve */
+} cpr_stats;
+
+/* Fill *o with the defaults listed above. */
+void cpr_default_opts(cpr_opts *o);
+
+/*
+ * Build the handle and the preconditioner B^(1) from A^(1) (Alg. 2 line 1 with
+ * k = 1; Alg. 1's setup: decoupling, AMG hierarchy with Eq. 5.1 colorings,
+ * BILU(0)), all on the device.  opts may be NULL for defaults.
+ * Returns CPR_ERR_INVALID, _OOM, _SINGULAR or _CUDA on failure (*h = NULL).
+ */
+int cpr_setup(cpr_handle **h, const cpr_bsr3 *A, const cpr_opts *opts);
+
+/*
+ * Hand the next Newton Jacobian A^(k) to the handle (Alg. 3): the outer
+ * operator becomes A^(k); B is kept iff the previous solve took
+ * It^(k-1) <= mu steps and the size and pattern are unchanged (Remark 4.2),
+ * otherwise B is rebuilt from A^(k).  A kept B keeps the copy of A it was
+ * built from for its own second residual (Alg. 1 line 3).
+ */
+int cpr_update(cpr_handle *h, const cpr_bsr3 *A);
+
+/*
+ * Solve A^(k) x = b by FGMRES(m) right-preconditioned with B (Alg. 2): x is
+ * the initial guess on entry and the solution on return.  Stops when the true
+ * residual satisfies ||b - A x|| < rtol ||b - A x_0|| or after max_restarts
+ * cycles (CPR_NOT_CONVERGED).  b with NaN/Inf: CPR_ERR_BREAKDOWN.  st may be
+ * NULL.
+ */
+int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
+
+/* Release every resource of the handle (NULL is accepted). */
+void cpr_destroy(cpr_handle *h);
+
+/* A static string describing a return code. */
+const char *cpr_strerror(int code);
+
+/* ------------------------------------------------------------------------
+ * Component entry points: one application of a part of B.  All vectors are
+ * DEVICE pointers with the handle's sizes; work is ordered on the handle's
+ * stream and the call returns after it completes.  In FP32 mode the inputs
+ * are rounded to FP32 on entry and results widened on exit.
+ * ---------------------------------------------------------------------- */
+
+/* z = B v: one CPR application from x = 0 (Alg. 1, Eq. 3.1); v, z: 3*nb. */
+int cpr_apply(cpr_handle *h, const double *v, double *z);
+
+/* x = B_P b: one AMG V(pre,post) cycle on the pressure matrix A_P (Sec. 3.1,
+ * smoother Alg. 6) from x = 0; b, x: nb. */
+int cpr_vcycle(cpr_handle *h, const double *b, double *x);
+
+/* z = R r with R = (L U)^-1, the multicolor BILU(0) second stage (Eq. 3.1);
+ * r, z: 3*nb. */
+int cpr_bilu_apply(cpr_handle *h, const double *r, double *z);
+
+/* y = A x (or r = b - A x when b != NULL) for a 3x3 BSR matrix (Eq. 2.8),
+ * all DEVICE pointers, stateless, ordered on `stream` (cudaStream_t; NULL =
+ * legacy default stream), asynchronous. */
+int cpr_bsr3_spmv(const cpr_bsr3 *A, const double *x, const double *b, double *y, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Inspection: copies of the current B's setup results into HOST buffers, in
+ * the natural (input) numbering, for checking and diagnostics.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    int n, nnz;    /* size and nonzeros of A_l */
+    int ncolors;   /* colors of the Eq. 5.1 coloring (0 on the coarsest level) */
+    int nc;        /* C points = size of level l+1 (0 on the coarsest level) */
+    int nnz_p;     /* nonzeros of the interpolation P_l (0 on the coarsest level) */
+} cpr_level_info;
+
+int cpr_num_levels(const cpr_handle *h);
+int cpr_get_level_info(const cpr_handle *h, int level, cpr_level_info *info);
+
+/* Any pointer may be NULL to skip it.  rowptr: n+1, col/val: nnz, color/cf: n
+ * (cf: 1 = C, 0 = F), prow: n+1, pcol/pval: nnz_p. */
+int cpr_copy_level(const cpr_handle *h, int level, int32_t *rowptr, int32_t *col, double *val,
+                   int32_t *color, int32_t *cf, int32_t *prow, int32_t *pcol, double *pval);
+
+/* w: 3*nb decoupling weights (Pi_P^T row weights). */
+int cpr_copy_weights(const cpr_handle *h, double *w);
+
+/* bcolor: nb block colors; lu: 9*nnzb factor blocks in A's pattern (L_ij below
+ * the diagonal in (color, index) order, U_ij above it, U_ii^-1 on it). */
+int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolors);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPR_B300_H */

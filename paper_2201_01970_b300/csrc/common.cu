@@ -1,0 +1,146 @@
+// Shared host utilities: errors, scans, small device reads.
+#include <cstdio>
+
+#include "cpr_internal.cuh"
+
+namespace cpr {
+
+void fail(int code, const std::string &what) { throw Error{code, what}; }
+
+void check_cuda(cudaError_t e, const char *expr, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    int code = e == cudaErrorMemoryAllocation ? CPR_ERR_OOM : CPR_ERR_CUDA;
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s failed at %s:%d: %s", expr, file, line, cudaGetErrorString(e));
+    fail(code, buf);
+}
+
+int grid_for(long n, int block, int cap) {
+    long g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- scan
+// Exclusive scan of n ints into n+1 outputs (out[n] = total): per-tile sums,
+// a recursive scan of the tile sums, then a per-tile scan plus the offset.
+
+namespace {
+constexpr int kScanBlock = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ int block_exclusive_scan(int v, int *total) {
+    __shared__ int warp_sums[kScanBlock / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < kScanBlock / 32 ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kScanBlock / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - v + (wid > 0 ? warp_sums[wid - 1] : 0);
+    *total = warp_sums[kScanBlock / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+__global__ void k_tile_sums(const int *in, int n, int *sums) {
+    long base = (long)blockIdx.x * kScanTile;
+    int s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        long i = base + (long)k * kScanBlock + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    int total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_tile_scan(const int *in, int n, const int *tile_off, int *out) {
+    long base = (long)blockIdx.x * kScanTile;
+    int v[kScanItems];
+    int s = 0;
+    for (int k = 0; k < kScanItems; k++) {
+        long i = base + (long)threadIdx.x * kScanItems + k;
+        v[k] = i < n ? in[i] : 0;
+        s += v[k];
+    }
+    int total;
+    int excl = block_exclusive_scan(s, &total) + (tile_off ? tile_off[blockIdx.x] : 0);
+    for (int k = 0; k < kScanItems; k++) {
+        long i = base + (long)threadIdx.x * kScanItems + k;
+        if (i < n) out[i] = excl;
+        excl += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanBlock - 1) out[n] = excl;
+}
+}  // namespace
+
+void exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
+    if (n <= 0) {
+        CK(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return;
+    }
+    int tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_tile_scan<<<1, kScanBlock, 0, s>>>(in, n, nullptr, out);
+        CK_LAUNCH();
+        return;
+    }
+    DVec<int> sums, offs;
+    sums.alloc(tiles, s);
+    offs.alloc(tiles + 1, s);
+    k_tile_sums<<<tiles, kScanBlock, 0, s>>>(in, n, sums.p);
+    CK_LAUNCH();
+    exclusive_scan(sums.p, offs.p, tiles, s);
+    k_tile_scan<<<tiles, kScanBlock, 0, s>>>(in, n, offs.p, out);
+    CK_LAUNCH();
+}
+
+int read_int(const int *dptr, cudaStream_t s) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+}
+
+static uint32_t fmix32_host(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Hash weight of vertex i is fmix32(i ^ base), base = fmix32(seed32 + 1000003*salt + level);
+// salt 0 = smoother coloring, 1 = PMIS, 2 = BILU coloring (MurmurHash3's finalizer).
+uint32_t hash_base(uint64_t seed, int salt, int level) {
+    uint32_t s32 = (uint32_t)(seed ^ (seed >> 32));
+    return fmix32_host(s32 + 1000003u * (uint32_t)salt + (uint32_t)level);
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace cpr

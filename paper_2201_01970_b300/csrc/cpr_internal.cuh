@@ -1,0 +1,174 @@
+// Internal declarations of the B300 CPR-FGMRES library: device buffers, the
+// handle, the hierarchy, and the host-side entry points of each part.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "cpr.h"
+
+namespace cpr {
+
+// ------------------------------------------------------------------ errors
+
+struct Error {
+    int code;
+    std::string what;
+};
+
+[[noreturn]] void fail(int code, const std::string &what);
+void check_cuda(cudaError_t e, const char *expr, const char *file, int line);
+#define CK(x) ::cpr::check_cuda((x), #x, __FILE__, __LINE__)
+#define CK_LAUNCH() ::cpr::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// ------------------------------------------------------------ device buffers
+
+// Stream-ordered device allocation (cudaMallocAsync pool); move-only.
+template <class T>
+struct DVec {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DVec() = default;
+    DVec(const DVec &) = delete;
+    DVec &operator=(const DVec &) = delete;
+    DVec(DVec &&o) noexcept { *this = std::move(o); }
+    DVec &operator=(DVec &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            s = o.s;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    ~DVec() { release(); }
+    void alloc(size_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        if (count) {
+            cudaError_t e = cudaMallocAsync((void **)&p, count * sizeof(T), stream);
+            if (e == cudaErrorMemoryAllocation) {
+                cudaGetLastError();
+                p = nullptr;
+                n = 0;
+                fail(CPR_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes");
+            }
+            CK(e);
+        }
+    }
+    void zero() {
+        if (n) CK(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+};
+
+// Scalar CSR matrix on the device.
+struct DCsr {
+    int n = 0, ncol = 0, nnz = 0;
+    DVec<int> rowptr, col;
+    DVec<double> val;
+};
+
+// One AMG level: A_l in natural numbering (the setup result, bit-identical to
+// the plain definition's), its coloring, C/F split and transfer operators,
+// the FP32 shadows and the V-cycle's work vectors.
+struct Level {
+    DCsr A, P, R;
+    DVec<int> color, cf;
+    int ncolors = 0, nc = 0;
+    std::vector<int> color_off;   // rows of color c: rows_by_color[color_off[c] .. color_off[c+1])
+    DVec<int> rows_by_color;
+    DVec<double> dinv;            // 1 / a_ii
+    DVec<float> Aval32, Pval32, Rval32, dinv32;
+    DVec<double> x, b, r;         // FP64 work vectors
+    DVec<float> x32, b32, r32;    // FP32 work vectors
+};
+
+// Split multicolor BILU(0) factors.
+struct Bilu {
+    DVec<int> color;
+    int ncolors = 0;
+    std::vector<int> color_off;
+    DVec<int> rows_by_color;
+    DVec<double> lu;               // factor array in A's pattern (inspection)
+    DVec<int> Lrowptr, Lcol, Urowptr, Ucol;
+    DVec<double> Lval, Uval, Dinv;
+    DVec<float> Lval32, Uval32, Dinv32;
+};
+
+}  // namespace cpr
+
+// The opaque handle of the C ABI.
+struct cpr_handle {
+    cpr_opts opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nb = 0, nnzb = 0;
+    cpr::DVec<int> rowptr, col;     // outer operator A^(k) (copy)
+    cpr::DVec<double> val;
+    // --- the preconditioner B (frozen between setups) ---
+    bool have_B = false;
+    cpr::DVec<double> pcol0;        // column 0 of every block of the A that B was built from
+    cpr::DVec<float> pcol0_32;
+    cpr::DVec<double> w;            // decoupling weights, 3 per block row
+    cpr::DVec<float> w32;
+    std::vector<cpr::Level> lev;
+    int cn = 0;                     // coarsest size
+    cpr::DVec<double> cinv;         // dense inverse of the coarsest A, column-major
+    cpr::Bilu bilu;
+    // --- Krylov workspace ---
+    int m_alloc = 0;
+    cpr::DVec<double> V, Z, wv, r;  // V: (m+1) x N, Z: m x N
+    cpr::DVec<double> dscal;        // device scalars (H, g, cs, sn, norms)
+    cpr::DVec<double> red;          // reduction partials
+    cpr::DVec<int> dint;            // device ints (step index, flags)
+    cpr::DVec<float> t32a, t32b;    // FP32 vectors of length 3*nb inside B
+    cpr::DVec<double> t64a, t64b;   // FP64 vectors inside B
+    double *pinned = nullptr;       // pinned host scalars
+    cpr::DVec<int> err;             // device error flag
+    // --- adaptive state (Alg. 3) ---
+    long last_iters = -1;
+    int setup_count = 0, setup_called = 0, updates = 0;
+    double setup_ms = 0.0;
+};
+
+namespace cpr {
+
+constexpr int kMaxRestart = 64;
+constexpr int kMaxCoarse = 4096;
+
+int grid_for(long n, int block, int cap = 1 << 30);
+void exclusive_scan(const int *in, int *out, int n, cudaStream_t s);   // out has n+1 entries
+int read_int(const int *dptr, cudaStream_t s);
+uint32_t hash_base(uint64_t seed, int salt, int level);
+bool is_device_ptr(const void *p);
+
+// setup.cu
+void build_preconditioner(cpr_handle *h);
+void free_preconditioner(cpr_handle *h);
+void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr, cudaStream_t s);
+
+// solve.cu
+void ensure_workspace(cpr_handle *h);
+void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
+             long z_ld);
+void vcycle_apply(cpr_handle *h, const double *b, double *x);
+void bilu_apply(cpr_handle *h, const double *r, double *z);
+int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
+void bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val, const double *x,
+               const double *b, double *y, cudaStream_t s);
+
+}  // namespace cpr
