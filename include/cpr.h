@@ -121,6 +121,10 @@ void cpr_destroy(cpr_handle *h);
 /* A static string describing a return code. */
 const char *cpr_strerror(int code);
 
+/* A text description of the most recent failure on the calling thread (valid
+ * until the next failing call on that thread). */
+const char *cpr_last_error_detail(void);
+
 /* ------------------------------------------------------------------------
  * Component entry points: one application of a part of B.  All vectors are
  * DEVICE pointers with the handle's sizes; work is ordered on the handle's

@@ -1,0 +1,250 @@
+"""Python binding of libcpr_b300.so, the B300 CPR-preconditioned FGMRES library.
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels (include/cpr.h documents each call).  Arrays may be numpy arrays (host)
+or torch CUDA tensors (device); the library detects which.  There is no CPU
+fallback: importing works without a GPU, but every call needs the CUDA
+library, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcpr_b300.so")
+
+CPR_OK = 0
+CPR_NOT_CONVERGED = 1
+CPR_ERR_INVALID = -1
+CPR_ERR_CUDA = -2
+CPR_ERR_OOM = -3
+CPR_ERR_SINGULAR = -4
+CPR_ERR_BREAKDOWN = -5
+CPR_ERR_TIMEOUT = -6
+
+
+class Opts(C.Structure):
+    _fields_ = [("theta_color", C.c_double), ("theta_amg", C.c_double), ("mu", C.c_int),
+                ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
+                ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("setup_called", C.c_int),
+                ("setup_count", C.c_int), ("levels", C.c_int), ("converged", C.c_int),
+                ("rel_res", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Bsr3(C.Structure):
+    _fields_ = [("nb", C.c_int32), ("nnzb", C.c_int32), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class LevelInfo(C.Structure):
+    _fields_ = [("n", C.c_int), ("nnz", C.c_int), ("ncolors", C.c_int), ("nc", C.c_int),
+                ("nnz_p", C.c_int)]
+
+
+class CprError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        detail = ""
+        try:
+            detail = lib().cpr_last_error_detail().decode()
+        except Exception:
+            pass
+        msg = lib().cpr_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} ({code}) {detail}".strip())
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2201_01970_b300.build.build() (nvcc, sm_103a)")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.cpr_default_opts.argtypes = [C.POINTER(Opts)]
+        L.cpr_setup.argtypes = [C.POINTER(vp), C.POINTER(Bsr3), C.POINTER(Opts)]
+        L.cpr_update.argtypes = [vp, C.POINTER(Bsr3)]
+        L.cpr_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Stats)]
+        L.cpr_destroy.argtypes = [vp]
+        L.cpr_strerror.argtypes = [C.c_int]
+        L.cpr_strerror.restype = C.c_char_p
+        L.cpr_last_error_detail.restype = C.c_char_p
+        L.cpr_apply.argtypes = [vp, vp, vp]
+        L.cpr_vcycle.argtypes = [vp, vp, vp]
+        L.cpr_bilu_apply.argtypes = [vp, vp, vp]
+        L.cpr_bsr3_spmv.argtypes = [C.POINTER(Bsr3), vp, vp, vp, vp]
+        L.cpr_num_levels.argtypes = [vp]
+        L.cpr_get_level_info.argtypes = [vp, C.c_int, C.POINTER(LevelInfo)]
+        L.cpr_copy_level.argtypes = [vp, C.c_int] + [vp] * 8
+        L.cpr_copy_weights.argtypes = [vp, vp]
+        L.cpr_copy_bilu.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str, allow_not_converged: bool = False) -> int:
+    if rc == CPR_OK or (allow_not_converged and rc == CPR_NOT_CONVERGED):
+        return rc
+    raise CprError(rc, where)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _as_bsr3(A) -> tuple:
+    """A Bsr3 descriptor for an object with nb, rowptr, col, val (numpy or torch)."""
+    rowptr, col, val = A.rowptr, A.col, A.val
+    if isinstance(rowptr, np.ndarray):
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+    nb = int(A.nb)
+    d = Bsr3(nb, int(col.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val))
+    return d, (rowptr, col, val)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().cpr_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class Solver:
+    """A cpr_handle: setup(A) at construction, update(A) per Newton step, solve(b)."""
+
+    def __init__(self, A, **opts):
+        if "stream" not in opts:
+            opts["stream"] = _torch_stream()
+        self.opts = default_opts(**opts)
+        self._h = C.c_void_p()
+        d, keep = _as_bsr3(A)
+        _check(lib().cpr_setup(C.byref(self._h), C.byref(d), C.byref(self.opts)), "cpr_setup")
+        self.nb, self.nnzb = d.nb, d.nnzb
+
+    def update(self, A) -> None:
+        d, keep = _as_bsr3(A)
+        _check(lib().cpr_update(self._h, C.byref(d)), "cpr_update")
+        self.nb, self.nnzb = d.nb, d.nnzb
+
+    def solve(self, b, x=None, rtol: float = 1e-6):
+        """Solve A x = b; returns (x, stats).  x (initial guess) is overwritten in place."""
+        if x is None:
+            if isinstance(b, np.ndarray):
+                x = np.zeros_like(b, dtype=np.float64)
+            else:
+                import torch
+                x = torch.zeros_like(b)
+        st = Stats()
+        rc = lib().cpr_solve(self._h, _ptr(b), _ptr(x), float(rtol), C.byref(st))
+        _check(rc, "cpr_solve", allow_not_converged=True)
+        return x, st.as_dict()
+
+    # component applications (device tensors)
+    def apply(self, v, z) -> None:
+        _check(lib().cpr_apply(self._h, _ptr(v), _ptr(z)), "cpr_apply")
+
+    def vcycle(self, b, x) -> None:
+        _check(lib().cpr_vcycle(self._h, _ptr(b), _ptr(x)), "cpr_vcycle")
+
+    def bilu_apply(self, r, z) -> None:
+        _check(lib().cpr_bilu_apply(self._h, _ptr(r), _ptr(z)), "cpr_bilu_apply")
+
+    # inspection (host numpy copies, natural numbering)
+    @property
+    def nlev(self) -> int:
+        return lib().cpr_num_levels(self._h)
+
+    def level(self, l: int) -> dict:
+        info = LevelInfo()
+        _check(lib().cpr_get_level_info(self._h, l, C.byref(info)), "cpr_get_level_info")
+        n, nnz, nnzp = info.n, info.nnz, info.nnz_p
+        out = {"n": n, "nnz": nnz, "ncolors": info.ncolors, "nc": info.nc,
+               "rowptr": np.zeros(n + 1, np.int32), "col": np.zeros(nnz, np.int32),
+               "val": np.zeros(nnz), "color": np.zeros(n, np.int32), "cf": np.zeros(n, np.int32),
+               "prow": np.zeros(n + 1, np.int32), "pcol": np.zeros(nnzp, np.int32),
+               "pval": np.zeros(nnzp)}
+        keys = ["rowptr", "col", "val", "color", "cf", "prow", "pcol", "pval"]
+        _check(lib().cpr_copy_level(self._h, l, *[_ptr(out[k]) if out[k].size else None
+                                                  for k in keys]), "cpr_copy_level")
+        if not info.ncolors:
+            out["color"] = None
+        if not info.nc:
+            out["cf"] = out["prow"] = out["pcol"] = out["pval"] = None
+        return out
+
+    def weights(self) -> np.ndarray:
+        w = np.zeros(3 * self.nb)
+        _check(lib().cpr_copy_weights(self._h, _ptr(w)), "cpr_copy_weights")
+        return w
+
+    def bilu(self):
+        bc = np.zeros(self.nb, np.int32)
+        lu = np.zeros(9 * self.nnzb)
+        nc = C.c_int()
+        _check(lib().cpr_copy_bilu(self._h, _ptr(bc), _ptr(lu), C.byref(nc)), "cpr_copy_bilu")
+        return bc, nc.value, lu
+
+    def close(self) -> None:
+        if self._h:
+            lib().cpr_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bsr3_spmv(A, x, b=None, y=None, stream=None):
+    """y = A x (or b - A x) on the device; A's arrays and x, b, y are CUDA tensors."""
+    import torch
+    d, keep = _as_bsr3(A)
+    if y is None:
+        y = torch.empty_like(x)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().cpr_bsr3_spmv(C.byref(d), _ptr(x), _ptr(b), _ptr(y), stream), "cpr_bsr3_spmv")
+    return y

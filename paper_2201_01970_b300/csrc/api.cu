@@ -1,0 +1,362 @@
+// The C ABI (include/cpr.h): handle lifetime, the adaptive setup rule of
+// Alg. 3, host/device argument marshalling, and the inspection copies.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+
+#include "cpr_internal.cuh"
+
+using namespace cpr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guarded(F f) {
+    try {
+        return f();
+    } catch (const Error &e) {
+        g_last_error = e.what;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return CPR_ERR_OOM;
+    } catch (...) {
+        g_last_error = "unknown failure";
+        return CPR_ERR_CUDA;
+    }
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void check_opts(const cpr_opts &o) {
+    bool ok = o.restart >= 1 && o.restart <= kMaxRestart && o.max_restarts >= 1 && o.pre >= 0 &&
+              o.post >= 0 && o.coarse_max >= 1 && o.coarse_max <= kMaxCoarse && o.max_levels >= 1 &&
+              o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
+              o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1);
+    if (!ok) fail(CPR_ERR_INVALID, "options out of range");
+}
+
+// Host-side structural check of a host-resident pattern (same rules as the device check).
+void check_pattern_host(int nb, int nnzb, const int32_t *rowptr, const int32_t *col) {
+    if (rowptr[0] != 0 || rowptr[nb] != nnzb) fail(CPR_ERR_INVALID, "rowptr does not span nnzb");
+    for (int i = 0; i < nb; i++) {
+        int a = rowptr[i], b = rowptr[i + 1];
+        if (b < a) fail(CPR_ERR_INVALID, "rowptr not monotone");
+        bool diag = false;
+        for (int p = a; p < b; p++) {
+            if (col[p] < 0 || col[p] >= nb || (p > a && col[p] <= col[p - 1]))
+                fail(CPR_ERR_INVALID, "column index out of range or unsorted");
+            diag |= col[p] == i;
+        }
+        if (!diag) fail(CPR_ERR_INVALID, "missing diagonal block");
+    }
+}
+
+void copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (!bytes) return;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+}
+
+// Upload A's pattern into (rowptr, col) and validate it.
+void load_pattern(cpr_handle *h, const cpr_bsr3 *A, DVec<int> &rowptr, DVec<int> &col) {
+    if (!A || A->nb < 1 || A->nnzb < A->nb || !A->rowptr || !A->col || !A->val)
+        fail(CPR_ERR_INVALID, "bad matrix descriptor");
+    cudaStream_t s = h->stream;
+    bool dev = is_device_ptr(A->rowptr);
+    if (!dev) check_pattern_host(A->nb, A->nnzb, A->rowptr, A->col);
+    rowptr.alloc(A->nb + 1, s);
+    col.alloc(A->nnzb, s);
+    copy_in(rowptr.p, A->rowptr, sizeof(int) * (A->nb + 1), s);
+    copy_in(col.p, A->col, sizeof(int) * (size_t)A->nnzb, s);
+    if (dev) {
+        validate_bsr(rowptr.p, col.p, A->nb, A->nnzb, h->err.p, s);
+        int e = read_int(h->err.p, s);
+        if (e) {
+            CK(cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
+            fail(CPR_ERR_INVALID, "malformed BSR pattern");
+        }
+    }
+}
+
+__global__ void k_compare(long n, const int *a, const int *b, int *diff) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        if (a[i] != b[i]) atomicExch(diff, 1);
+}
+
+__global__ void k_has_nonfinite(long n, const double *a, int *flag) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicExch(flag, 1);
+}
+
+void build_timed(cpr_handle *h) {
+    double t0 = now_ms();
+    build_preconditioner(h);
+    h->setup_ms = now_ms() - t0;
+    h->setup_count++;
+    h->setup_called = 1;
+    h->last_iters = -1;
+    ensure_workspace(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+void cpr_default_opts(cpr_opts *o) {
+    o->theta_color = 0.05;
+    o->theta_amg = 0.25;
+    o->mu = 30;
+    o->restart = 30;
+    o->max_restarts = 100;
+    o->precond_fp32 = 0;
+    o->decouple = 1;
+    o->pre = 1;
+    o->post = 1;
+    o->coarse_max = 256;
+    o->max_levels = 20;
+    o->seed = 0;
+    o->stream = nullptr;
+}
+
+const char *cpr_strerror(int code) {
+    switch (code) {
+    case CPR_OK: return "ok";
+    case CPR_NOT_CONVERGED: return "not converged within max_restarts cycles";
+    case CPR_ERR_INVALID: return "invalid argument or malformed matrix";
+    case CPR_ERR_CUDA: return "CUDA call failed";
+    case CPR_ERR_OOM: return "out of device memory";
+    case CPR_ERR_SINGULAR: return "singular pivot (block diagonal, smoother diagonal or coarse LU)";
+    case CPR_ERR_BREAKDOWN: return "NaN/Inf in the iteration or right-hand side";
+    case CPR_ERR_TIMEOUT: return "bounded device wait gave up";
+    default: return "unknown code";
+    }
+}
+
+// Detail of the last failure on this thread (diagnostics; not part of the stable ABI).
+const char *cpr_last_error_detail(void) { return g_last_error.c_str(); }
+
+int cpr_setup(cpr_handle **out, const cpr_bsr3 *A, const cpr_opts *opts) {
+    if (!out) return CPR_ERR_INVALID;
+    *out = nullptr;
+    cpr_handle *h = new cpr_handle();
+    int rc = guarded([&] {
+        if (opts) h->opt = *opts;
+        else cpr_default_opts(&h->opt);
+        check_opts(h->opt);
+        if (h->opt.stream) {
+            h->stream = (cudaStream_t)h->opt.stream;
+        } else {
+            // a blocking stream: ordered with the legacy default stream that callers
+            // (torch included) use unless they pass their own stream
+            CK(cudaStreamCreate(&h->stream));
+            h->own_stream = true;
+        }
+        h->err.alloc(1, h->stream);
+        h->err.zero();
+        load_pattern(h, A, h->rowptr, h->col);
+        h->nb = A->nb;
+        h->nnzb = A->nnzb;
+        h->val.alloc(9 * (size_t)A->nnzb, h->stream);
+        copy_in(h->val.p, A->val, sizeof(double) * 9 * (size_t)A->nnzb, h->stream);
+        h->updates = 1;
+        build_timed(h);
+        return CPR_OK;
+    });
+    if (rc != CPR_OK) {
+        cpr_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return CPR_OK;
+}
+
+int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
+    if (!h) return CPR_ERR_INVALID;
+    return guarded([&] {
+        cudaStream_t s = h->stream;
+        DVec<int> rp, cl;
+        load_pattern(h, A, rp, cl);
+        bool same = A->nb == h->nb && A->nnzb == h->nnzb;
+        if (same) {
+            DVec<int> diff;
+            diff.alloc(1, s);
+            diff.zero();
+            k_compare<<<grid_for(h->nb + 1, 256, 1184), 256, 0, s>>>(h->nb + 1, rp.p, h->rowptr.p, diff.p);
+            k_compare<<<grid_for(h->nnzb, 256, 1184), 256, 0, s>>>(h->nnzb, cl.p, h->col.p, diff.p);
+            CK_LAUNCH();
+            same = read_int(diff.p, s) == 0;
+        }
+        if (!same) {
+            h->rowptr = std::move(rp);
+            h->col = std::move(cl);
+            h->nb = A->nb;
+            h->nnzb = A->nnzb;
+            h->val.alloc(9 * (size_t)A->nnzb, s);
+        }
+        copy_in(h->val.p, A->val, sizeof(double) * 9 * (size_t)A->nnzb, s);
+        h->updates++;
+        // Alg. 3: reuse B^(k-1) iff k > 1 and It^(k-1) <= mu (and Remark 4.2: same size/pattern)
+        bool reuse = same && h->have_B && h->last_iters >= 0 && h->last_iters <= h->opt.mu;
+        if (reuse) {
+            h->setup_called = 0;
+            h->setup_ms = 0.0;
+            return CPR_OK;
+        }
+        build_timed(h);
+        return CPR_OK;
+    });
+}
+
+int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
+    if (!h || !b || !x || !(rtol > 0.0)) return CPR_ERR_INVALID;
+    return guarded([&] {
+        double t0 = now_ms();
+        cudaStream_t s = h->stream;
+        size_t bytes = sizeof(double) * 3 * (size_t)h->nb;
+        bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+        const double *db = b;
+        double *dx = x;
+        if (!bdev) {
+            CK(cudaMemcpyAsync(h->dev_b.p, b, bytes, cudaMemcpyHostToDevice, s));
+            db = h->dev_b.p;
+        }
+        if (!xdev) {
+            CK(cudaMemcpyAsync(h->dev_x.p, x, bytes, cudaMemcpyHostToDevice, s));
+            dx = h->dev_x.p;
+        }
+        {
+            DVec<int> flag;
+            flag.alloc(1, s);
+            flag.zero();
+            k_has_nonfinite<<<grid_for(3L * h->nb, 256, 1184), 256, 0, s>>>(3L * h->nb, db, flag.p);
+            CK_LAUNCH();
+            if (read_int(flag.p, s)) fail(CPR_ERR_BREAKDOWN, "non-finite right-hand side");
+        }
+        cpr_stats local{};
+        int rc = fgmres(h, db, dx, rtol, &local);
+        if (!xdev) CK(cudaMemcpyAsync(x, dx, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        local.setup_called = h->setup_called;
+        local.setup_count = h->setup_count;
+        local.levels = (int)h->lev.size();
+        local.setup_ms = h->setup_called ? h->setup_ms : 0.0;
+        local.solve_ms = now_ms() - t0;
+        if (st) *st = local;
+        return rc;
+    });
+}
+
+void cpr_destroy(cpr_handle *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    try {
+        free_preconditioner(h);
+    } catch (...) {
+    }
+    cudaStream_t s = h->stream;
+    bool own = h->own_stream;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    delete h;  // DVec destructors free on the stream
+    if (s) cudaStreamSynchronize(s);
+    if (own && s) cudaStreamDestroy(s);
+}
+
+int cpr_apply(cpr_handle *h, const double *v, double *z) {
+    if (!h || !v || !z) return CPR_ERR_INVALID;
+    return guarded([&] {
+        apply_B(h, v, 0, nullptr, z, 0);
+        CK(cudaStreamSynchronize(h->stream));
+        return CPR_OK;
+    });
+}
+
+int cpr_vcycle(cpr_handle *h, const double *b, double *x) {
+    if (!h || !b || !x) return CPR_ERR_INVALID;
+    return guarded([&] {
+        vcycle_apply(h, b, x);
+        CK(cudaStreamSynchronize(h->stream));
+        return CPR_OK;
+    });
+}
+
+int cpr_bilu_apply(cpr_handle *h, const double *r, double *z) {
+    if (!h || !r || !z) return CPR_ERR_INVALID;
+    return guarded([&] {
+        bilu_apply(h, r, z);
+        CK(cudaStreamSynchronize(h->stream));
+        return CPR_OK;
+    });
+}
+
+int cpr_bsr3_spmv(const cpr_bsr3 *A, const double *x, const double *b, double *y, void *stream) {
+    if (!A || A->nb < 1 || !A->rowptr || !A->col || !A->val || !x || !y) return CPR_ERR_INVALID;
+    return guarded([&] {
+        bsr3_spmv(A->nb, A->rowptr, A->col, A->val, x, b, y, (cudaStream_t)stream);
+        return CPR_OK;
+    });
+}
+
+int cpr_num_levels(const cpr_handle *h) { return h ? (int)h->lev.size() : 0; }
+
+int cpr_get_level_info(const cpr_handle *h, int level, cpr_level_info *info) {
+    if (!h || !info || level < 0 || level >= (int)h->lev.size()) return CPR_ERR_INVALID;
+    const Level &L = h->lev[level];
+    info->n = L.A.n;
+    info->nnz = L.A.nnz;
+    info->ncolors = L.ncolors;
+    info->nc = L.nc;
+    info->nnz_p = L.P.nnz;
+    return CPR_OK;
+}
+
+int cpr_copy_level(const cpr_handle *h, int level, int32_t *rowptr, int32_t *col, double *val,
+                   int32_t *color, int32_t *cf, int32_t *prow, int32_t *pcol, double *pval) {
+    if (!h || level < 0 || level >= (int)h->lev.size()) return CPR_ERR_INVALID;
+    return guarded([&] {
+        const Level &L = h->lev[level];
+        cudaStream_t s = h->stream;
+        auto d2h = [&](void *dst, const void *src, size_t bytes) {
+            if (dst && src && bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        };
+        d2h(rowptr, L.A.rowptr.p, sizeof(int) * (L.A.n + 1));
+        d2h(col, L.A.col.p, sizeof(int) * (size_t)L.A.nnz);
+        d2h(val, L.A.val.p, sizeof(double) * (size_t)L.A.nnz);
+        if (L.ncolors) d2h(color, L.color.p, sizeof(int) * L.A.n);
+        if (L.nc) {
+            d2h(cf, L.cf.p, sizeof(int) * L.A.n);
+            d2h(prow, L.P.rowptr.p, sizeof(int) * (L.A.n + 1));
+            d2h(pcol, L.P.col.p, sizeof(int) * (size_t)L.P.nnz);
+            d2h(pval, L.P.val.p, sizeof(double) * (size_t)L.P.nnz);
+        }
+        CK(cudaStreamSynchronize(s));
+        return CPR_OK;
+    });
+}
+
+int cpr_copy_weights(const cpr_handle *h, double *w) {
+    if (!h || !w) return CPR_ERR_INVALID;
+    return guarded([&] {
+        CK(cudaMemcpyAsync(w, h->w.p, sizeof(double) * 3 * (size_t)h->nb, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return CPR_OK;
+    });
+}
+
+int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolors) {
+    if (!h) return CPR_ERR_INVALID;
+    return guarded([&] {
+        cudaStream_t s = h->stream;
+        if (bcolor) CK(cudaMemcpyAsync(bcolor, h->bilu.color.p, sizeof(int) * h->nb, cudaMemcpyDeviceToHost, s));
+        if (lu) CK(cudaMemcpyAsync(lu, h->bilu.lu.p, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyDeviceToHost, s));
+        if (nbcolors) *nbcolors = h->bilu.ncolors;
+        CK(cudaStreamSynchronize(s));
+        return CPR_OK;
+    });
+}
+
+}  // extern "C"

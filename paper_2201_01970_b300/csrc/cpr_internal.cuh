@@ -136,7 +136,8 @@ struct cpr_handle {
     cpr::DVec<double> red;          // reduction partials
     cpr::DVec<int> dint;            // device ints (step index, flags)
     cpr::DVec<float> t32a, t32b;    // FP32 vectors of length 3*nb inside B
-    cpr::DVec<double> t64a, t64b;   // FP64 vectors inside B
+    cpr::DVec<double> t64a;         // FP64 vector of length 3*nb inside B
+    cpr::DVec<double> dev_b, dev_x; // device copies of host b / x
     double *pinned = nullptr;       // pinned host scalars
     cpr::DVec<int> err;             // device error flag
     // --- adaptive state (Alg. 3) ---

@@ -1,0 +1,794 @@
+// Solve phase: one application of the CPR preconditioner B (Alg. 1 from x = 0,
+// Eq. 3.1) and the flexible GMRES(m) outer loop of Alg. 2.
+//
+// Kernels are templated on the preconditioner's value type T (double, or
+// float in FP32-preconditioner mode: FP32 storage and accumulation inside B).
+// The outer operator, the Arnoldi process (CGS), the Givens rotations and the
+// true residual always run in FP64.  Every step is a sparse, bandwidth-bound
+// sweep: no tensor cores.  Kernels that belong to one Arnoldi step read the
+// step index j and a "done" flag from device memory, so a step never needs a
+// host round trip and whole steps can be replayed as a graph.
+#include <algorithm>
+#include <cmath>
+
+#include "cpr_internal.cuh"
+
+namespace cpr {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kRedBlocks = 296;   // 2 CTAs per SM on 148 SMs
+constexpr int kDotGroup = 8;      // vectors per register group in the CGS dot kernel
+
+// Layout of the device scalar block (doubles) for restart length m.
+struct ScalLayout {
+    int m;
+    __host__ __device__ int H(int i, int j) const { return i * m + j; }   // (m+1) x m
+    __host__ __device__ int cs() const { return (m + 1) * m; }
+    __host__ __device__ int sn() const { return cs() + m; }
+    __host__ __device__ int g() const { return sn() + m; }                 // m+1
+    __host__ __device__ int y() const { return g() + m + 1; }              // m
+    __host__ __device__ int hcol() const { return y() + m; }               // m+1
+    __host__ __device__ int norm0() const { return hcol() + m + 1; }
+    __host__ __device__ int rnorm() const { return norm0() + 1; }
+    __host__ __device__ int inv_hn() const { return norm0() + 2; }
+    __host__ __device__ int rtol() const { return norm0() + 3; }
+    __host__ __device__ int est() const { return norm0() + 4; }
+    __host__ __device__ int size() const { return norm0() + 5; }
+};
+// Device ints: [0] step j, [1] done, [2] steps in this cycle, [3] breakdown.
+enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_COUNT = 8 };
+
+__device__ __forceinline__ int step_of(const int *jptr) { return jptr ? *jptr : 0; }
+
+// --------------------------------------------------------------- BSR SpMV
+
+// y = A x, or y = b - A x.  G lanes per block row; lane t of a row handles the
+// (block, row-of-block) items t, t+G, ...: 3 contiguous values of the block
+// times 3 contiguous values of x.
+template <int G>
+__global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
+                            const double *__restrict__ val, const double *__restrict__ x_base,
+                            long xld, const int *jptr, const double *__restrict__ b,
+                            double *__restrict__ y, const int *done) {
+    if (done && *done) return;
+    const double *x = x_base + (size_t)step_of(jptr) * xld;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int row = (int)(tid / G), lane = (int)(tid % G);
+    bool active = row < nb;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (active) {
+        int s = rowptr[row], e = rowptr[row + 1];
+        int items = 3 * (e - s);
+        for (int t = lane; t < items; t += G) {
+            int blk = t / 3, r = t - 3 * blk;
+            int p = s + blk;
+            const double *v = val + 9 * (size_t)p + 3 * r;
+            const double *xj = x + 3 * (size_t)col[p];
+            double d = v[0] * xj[0] + v[1] * xj[1] + v[2] * xj[2];
+            if (r == 0) a0 += d;
+            else if (r == 1) a1 += d;
+            else a2 += d;
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o, G);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o, G);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
+    }
+    if (active && lane == 0) {
+        size_t q = 3 * (size_t)row;
+        if (b) {
+            y[q] = b[q] - a0;
+            y[q + 1] = b[q + 1] - a1;
+            y[q + 2] = b[q + 2] - a2;
+        } else {
+            y[q] = a0;
+            y[q + 1] = a1;
+            y[q + 2] = a2;
+        }
+    }
+}
+
+// --------------------------------------------------- restriction / prolongation
+
+// r_P[i] = w_i . v_i (Pi_P^T with decoupling weights); v = v_base + j * ld.
+template <class T>
+__global__ void k_restrict(int nb, const double *v_base, long ld, const int *jptr, const T *w,
+                           T *rp, const int *done) {
+    if (done && *done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
+    rp[i] = (w[3 * i] * (T)v[0] + w[3 * i + 1] * (T)v[1]) + w[3 * i + 2] * (T)v[2];
+}
+
+// Second residual of Alg. 1: r = v - A z with z = Pi_P e_P, so only column 0 of
+// every block (the frozen copy c0) takes part.  G lanes per block row.
+template <class T, int G>
+__global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                const T *__restrict__ c0, const T *__restrict__ ep,
+                                const double *v_base, long ld, const int *jptr, T *__restrict__ r,
+                                const int *done) {
+    if (done && *done) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int row = (int)(tid / G), lane = (int)(tid % G);
+    bool active = row < nb;
+    T a0 = 0, a1 = 0, a2 = 0;
+    if (active) {
+        int s = rowptr[row], e = rowptr[row + 1];
+        int items = 3 * (e - s);
+        for (int t = lane; t < items; t += G) {
+            int blk = t / 3, rr = t - 3 * blk;
+            int p = s + blk;
+            T d = c0[3 * (size_t)p + rr] * ep[col[p]];
+            if (rr == 0) a0 += d;
+            else if (rr == 1) a1 += d;
+            else a2 += d;
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o, G);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o, G);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
+    }
+    if (active && lane == 0) {
+        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)row;
+        r[3 * (size_t)row] = (T)v[0] - a0;
+        r[3 * (size_t)row + 1] = (T)v[1] - a1;
+        r[3 * (size_t)row + 2] = (T)v[2] - a2;
+    }
+}
+
+// ------------------------------------------------------ multi-color GS (Alg. 6)
+
+// First color of a sweep from x = 0: every neighbour is still zero.
+template <class T>
+__global__ void k_mcgs_first(const int *rows, int cnt, const T *b, const T *dinv, T *x,
+                             const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    int i = rows[t];
+    x[i] = b[i] * dinv[i];
+}
+
+// Rows of one color: x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii.  Rows of one
+// color never read each other's new values (Jacobi within a color).
+template <class T>
+__global__ void k_mcgs_color(const int *rows, int cnt, const int *__restrict__ rowptr,
+                             const int *__restrict__ col, const T *__restrict__ val, const T *b,
+                             const T *dinv, T *x, const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    int i = rows[t];
+    T s = b[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+        int j = col[p];
+        if (j != i) s -= val[p] * x[j];
+    }
+    x[i] = s * dinv[i];
+}
+
+// r = b - A x on a scalar CSR level.
+template <class T>
+__global__ void k_csr_resid(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                            const T *__restrict__ val, const T *b, const T *x, T *r,
+                            const int *done) {
+    if (done && *done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = b[i];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) s -= val[p] * x[col[p]];
+    r[i] = s;
+}
+
+// y = M x (add = false) or y += M x (add = true) for a scalar CSR operator (R or P).
+template <class T>
+__global__ void k_csr_spmv(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                           const T *__restrict__ val, const T *x, T *y, bool add, const int *done) {
+    if (done && *done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T s = 0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * x[col[p]];
+    y[i] = add ? y[i] + s : s;
+}
+
+// Coarsest level: x = A_L^-1 b with the FP64 inverse (column-major).
+template <class T>
+__global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b, T *x,
+                               const int *done) {
+    if (done && *done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = 0; j < n; j++) s += inv[(size_t)j * n + i] * (double)b[j];
+    x[i] = (T)s;
+}
+
+// ------------------------------------------------------------- BILU(0) sweeps
+
+// Forward substitution for one color, in place: y_i = r_i - sum_{lower} L_ij y_j.
+template <class T>
+__global__ void k_bilu_fwd(const int *rows, int cnt, const int *__restrict__ lr,
+                           const int *__restrict__ lc, const T *__restrict__ lv, T *y,
+                           const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    int i = rows[t];
+    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+    for (int p = lr[i]; p < lr[i + 1]; p++) {
+        const T *L = lv + 9 * (size_t)p;
+        const T *yj = y + 3 * (size_t)lc[p];
+        T y0 = yj[0], y1 = yj[1], y2 = yj[2];
+        s0 -= L[0] * y0 + L[1] * y1 + L[2] * y2;
+        s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
+        s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
+    }
+    y[3 * (size_t)i] = s0;
+    y[3 * (size_t)i + 1] = s1;
+    y[3 * (size_t)i + 2] = s2;
+}
+
+// Backward substitution for one color, in place: z_i = U_ii^-1 (y_i - sum_{upper} U_ij z_j).
+// The result, plus Pi_P e_P when ep != nullptr, is also written to out (FP64).
+template <class T>
+__global__ void k_bilu_bwd(const int *rows, int cnt, const int *__restrict__ ur,
+                           const int *__restrict__ uc, const T *__restrict__ uv,
+                           const T *__restrict__ dinv, T *y, const T *ep, double *out_base, long ld,
+                           const int *jptr, const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    int i = rows[t];
+    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+    for (int p = ur[i]; p < ur[i + 1]; p++) {
+        const T *U = uv + 9 * (size_t)p;
+        const T *zj = y + 3 * (size_t)uc[p];
+        T z0 = zj[0], z1 = zj[1], z2 = zj[2];
+        s0 -= U[0] * z0 + U[1] * z1 + U[2] * z2;
+        s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
+        s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
+    }
+    const T *D = dinv + 9 * (size_t)i;
+    T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
+    T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
+    T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
+    y[3 * (size_t)i] = z0;
+    y[3 * (size_t)i + 1] = z1;
+    y[3 * (size_t)i + 2] = z2;
+    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
+    out[0] = (double)z0 + (ep ? (double)ep[i] : 0.0);
+    out[1] = (double)z1;
+    out[2] = (double)z2;
+}
+
+// ------------------------------------------------------------- small kernels
+
+template <class T>
+__global__ void k_cast(long n, const double *a, T *b) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        b[i] = (T)a[i];
+}
+
+template <class T>
+__global__ void k_widen(long n, const T *a, double *b) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+template <class T>
+__global__ void k_zero(long n, T *a, const int *done) {
+    if (done && *done) return;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        a[i] = 0;
+}
+
+// ------------------------------------------------------------ Krylov kernels
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum of v into out (thread 0), deterministic order.
+__device__ double block_sum(double v) {
+    __shared__ double ws[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += ws[w];
+    return s;
+}
+
+// Partial sums of a.b per block: part[blockIdx.x].
+__global__ void k_dot_partial(long n, const double *a, const double *b, double *part) {
+    double s = 0.0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n; q += (long)gridDim.x * blockDim.x)
+        s += a[q] * b[q];
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// CGS dots of Alg. 2: part[blk * ldp + i] = sum_q V_i[q] w[q] for i = 0..j.
+__global__ void k_cgs_dots(long N, const double *__restrict__ V, const double *__restrict__ w,
+                           const int *jptr, double *part, int ldp, const int *done) {
+    if (*done) return;
+    int nvec = *jptr + 1;
+    for (int g0 = 0; g0 < nvec; g0 += kDotGroup) {
+        double acc[kDotGroup];
+#pragma unroll
+        for (int k = 0; k < kDotGroup; k++) acc[k] = 0.0;
+        for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+            double wq = w[q];
+#pragma unroll
+            for (int k = 0; k < kDotGroup; k++)
+                if (g0 + k < nvec) acc[k] += V[(size_t)(g0 + k) * N + q] * wq;
+        }
+#pragma unroll
+        for (int k = 0; k < kDotGroup; k++) {
+            double s = block_sum(acc[k]);
+            if (threadIdx.x == 0 && g0 + k < nvec) part[(size_t)blockIdx.x * ldp + g0 + k] = s;
+        }
+    }
+}
+
+// hcol[i] = sum over blocks of part[.][i] (fixed order).
+__global__ void k_reduce_cols(const double *part, int nblk, int ldp, const int *jptr, double *hcol,
+                              const int *done) {
+    if (*done) return;
+    int nvec = *jptr + 1;
+    int i = threadIdx.x;
+    if (i >= nvec) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += part[(size_t)b * ldp + i];
+    hcol[i] = s;
+}
+
+// w -= sum_{i<=j} h_i V_i, and per-block partial sums of ||w||^2 into part.
+__global__ void k_cgs_update(long N, const double *__restrict__ V, double *__restrict__ w,
+                             const int *jptr, const double *hcol, double *part, const int *done) {
+    if (*done) return;
+    __shared__ double sh[kMaxRestart + 1];
+    int nvec = *jptr + 1;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = hcol[i];
+    __syncthreads();
+    double s = 0.0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+        double wq = w[q];
+        for (int i = 0; i < nvec; i++) wq -= sh[i] * V[(size_t)i * N + q];
+        w[q] = wq;
+        s += wq * wq;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// One Givens step (Saad's form) for column j of the Hessenberg matrix, the
+// residual estimate |g_{j+1}| / ||r_0|| and the stop decision of Alg. 2.
+__global__ void k_givens(const double *part, int nblk, double *sc, int m, int *di) {
+    if (di[I_DONE]) return;
+    ScalLayout L{m};
+    int j = di[I_J];
+    double hn2 = 0.0;
+    for (int b = 0; b < nblk; b++) hn2 += part[b];
+    double hn = sqrt(hn2);
+    for (int i = 0; i <= j; i++) sc[L.H(i, j)] = sc[L.hcol() + i];
+    sc[L.H(j + 1, j)] = hn;
+    for (int i = 0; i < j; i++) {
+        double a = sc[L.H(i, j)], c = sc[L.H(i + 1, j)];
+        sc[L.H(i, j)] = sc[L.cs() + i] * a + sc[L.sn() + i] * c;
+        sc[L.H(i + 1, j)] = -sc[L.sn() + i] * a + sc[L.cs() + i] * c;
+    }
+    double a = sc[L.H(j, j)], c = sc[L.H(j + 1, j)];
+    double den = sqrt(a * a + c * c);
+    double cj = den == 0.0 ? 1.0 : a / den, sj = den == 0.0 ? 0.0 : c / den;
+    sc[L.cs() + j] = cj;
+    sc[L.sn() + j] = sj;
+    sc[L.H(j, j)] = den;
+    sc[L.H(j + 1, j)] = 0.0;
+    double gj = sc[L.g() + j];
+    sc[L.g() + j + 1] = -sj * gj;
+    sc[L.g() + j] = cj * gj;
+    double est = fabs(sc[L.g() + j + 1]) / sc[L.norm0()];
+    sc[L.est()] = est;
+    sc[L.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
+    di[I_K] = j + 1;
+    di[I_J] = j + 1;
+    bool brk = !isfinite(hn) || !isfinite(est);
+    if (brk) di[I_BREAK] = 1;
+    if (brk || hn == 0.0 || est < sc[L.rtol()] || j + 1 >= m) di[I_DONE] = 1;
+}
+
+// V_{j+1} = w / h_{j+1,j} (after k_givens advanced the step index to j+1).
+__global__ void k_next_basis(long N, const double *w, double *V, const double *sc, int m,
+                             const int *di) {
+    if (di[I_DONE]) return;
+    ScalLayout L{m};
+    double s = sc[L.inv_hn()];
+    double *v = V + (size_t)di[I_J] * N;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x)
+        v[q] = w[q] * s;
+}
+
+// Start of a cycle: beta = sqrt(sum part), V_0 = r / beta, g = beta e_1, j = 0.
+// On the first cycle (first != 0) also ||r_0|| = beta.
+__global__ void k_cycle_start_scal(const double *part, int nblk, double *sc, int m, int *di,
+                                   int first, double rtol) {
+    ScalLayout L{m};
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += part[b];
+    double beta = sqrt(s);
+    if (first) {
+        sc[L.norm0()] = beta;
+        sc[L.rtol()] = rtol;
+    }
+    sc[L.rnorm()] = beta;
+    for (int i = 0; i <= m; i++) sc[L.g() + i] = 0.0;
+    sc[L.g()] = beta;
+    sc[L.inv_hn()] = beta > 0.0 ? 1.0 / beta : 0.0;
+    di[I_J] = 0;
+    di[I_K] = 0;
+    di[I_BREAK] = isfinite(beta) ? 0 : 1;
+    di[I_DONE] = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+    di[I_ZERO] = 0;
+}
+
+__global__ void k_scale_into(long N, const double *r, double *v, const double *sc, int m) {
+    ScalLayout L{m};
+    double s = sc[L.inv_hn()];
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x)
+        v[q] = r[q] * s;
+}
+
+// y = H_k^-1 g_k (upper triangular back substitution), k = steps of the cycle.
+__global__ void k_solve_y(double *sc, int m, const int *di) {
+    ScalLayout L{m};
+    int k = di[I_K];
+    for (int i = k - 1; i >= 0; i--) {
+        double s = sc[L.g() + i];
+        for (int q = i + 1; q < k; q++) s -= sc[L.H(i, q)] * sc[L.y() + q];
+        sc[L.y() + i] = s / sc[L.H(i, i)];
+    }
+}
+
+// x += sum_{i<k} y_i Z_i.
+__global__ void k_update_x(long N, const double *__restrict__ Z, double *x, const double *sc, int m,
+                           const int *di) {
+    __shared__ double sy[kMaxRestart];
+    ScalLayout L{m};
+    int k = di[I_K];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = sc[L.y() + i];
+    __syncthreads();
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+        double s = x[q];
+        for (int i = 0; i < k; i++) s += sy[i] * Z[(size_t)i * N + q];
+        x[q] = s;
+    }
+}
+
+// ------------------------------------------------------------ host helpers
+
+template <class T>
+struct Vals;
+template <>
+struct Vals<double> {
+    static const double *A(const Level &L) { return L.A.val.p; }
+    static const double *P(const Level &L) { return L.P.val.p; }
+    static const double *R(const Level &L) { return L.R.val.p; }
+    static const double *dinv(const Level &L) { return L.dinv.p; }
+    static double *x(Level &L) { return L.x.p; }
+    static double *b(Level &L) { return L.b.p; }
+    static double *r(Level &L) { return L.r.p; }
+    static const double *w(const cpr_handle *h) { return h->w.p; }
+    static const double *c0(const cpr_handle *h) { return h->pcol0.p; }
+    static const double *Lv(const cpr_handle *h) { return h->bilu.Lval.p; }
+    static const double *Uv(const cpr_handle *h) { return h->bilu.Uval.p; }
+    static const double *Dv(const cpr_handle *h) { return h->bilu.Dinv.p; }
+    static double *tmp(cpr_handle *h) { return h->t64a.p; }
+};
+template <>
+struct Vals<float> {
+    static const float *A(const Level &L) { return L.Aval32.p; }
+    static const float *P(const Level &L) { return L.Pval32.p; }
+    static const float *R(const Level &L) { return L.Rval32.p; }
+    static const float *dinv(const Level &L) { return L.dinv32.p; }
+    static float *x(Level &L) { return L.x32.p; }
+    static float *b(Level &L) { return L.b32.p; }
+    static float *r(Level &L) { return L.r32.p; }
+    static const float *w(const cpr_handle *h) { return h->w32.p; }
+    static const float *c0(const cpr_handle *h) { return h->pcol0_32.p; }
+    static const float *Lv(const cpr_handle *h) { return h->bilu.Lval32.p; }
+    static const float *Uv(const cpr_handle *h) { return h->bilu.Uval32.p; }
+    static const float *Dv(const cpr_handle *h) { return h->bilu.Dinv32.p; }
+    static float *tmp(cpr_handle *h) { return h->t32a.p; }
+};
+
+// One smoothing sweep over the colors of level L (ascending or descending).
+template <class T>
+void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, const int *done) {
+    cudaStream_t s = h->stream;
+    for (int t = 0; t < L.ncolors; t++) {
+        int c = descending ? L.ncolors - 1 - t : t;
+        int cnt = L.color_off[c + 1] - L.color_off[c];
+        if (!cnt) continue;
+        const int *rows = L.rows_by_color.p + L.color_off[c];
+        if (from_zero && t == 0) {
+            k_mcgs_first<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, Vals<T>::b(L),
+                                                                     Vals<T>::dinv(L), Vals<T>::x(L), done);
+        } else {
+            k_mcgs_color<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, L.A.rowptr.p, L.A.col.p,
+                                                                     Vals<T>::A(L), Vals<T>::b(L),
+                                                                     Vals<T>::dinv(L), Vals<T>::x(L), done);
+        }
+        CK_LAUNCH();
+    }
+}
+
+// V(pre, post) cycle on level l: x_l = B_l b_l from x_l = 0 (reading: pre-smoothing
+// with colors ascending, post-smoothing descending).
+template <class T>
+void vcycle(cpr_handle *h, int l, const int *done) {
+    cudaStream_t s = h->stream;
+    Level &L = h->lev[l];
+    int n = L.A.n;
+    if (l == (int)h->lev.size() - 1) {
+        k_coarse_solve<T><<<grid_for(n, 128), 128, 0, s>>>(n, h->cinv.p, Vals<T>::b(L), Vals<T>::x(L), done);
+        CK_LAUNCH();
+        return;
+    }
+    k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, Vals<T>::x(L), done);
+    CK_LAUNCH();
+    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, done);
+    k_csr_resid<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, Vals<T>::A(L),
+                                                          Vals<T>::b(L), Vals<T>::x(L), Vals<T>::r(L), done);
+    CK_LAUNCH();
+    Level &C = h->lev[l + 1];
+    k_csr_spmv<T><<<grid_for(L.R.n, kBlock), kBlock, 0, s>>>(L.R.n, L.R.rowptr.p, L.R.col.p, Vals<T>::R(L),
+                                                             Vals<T>::r(L), Vals<T>::b(C), false, done);
+    CK_LAUNCH();
+    vcycle<T>(h, l + 1, done);
+    k_csr_spmv<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.P.rowptr.p, L.P.col.p, Vals<T>::P(L),
+                                                         Vals<T>::x(C), Vals<T>::x(L), true, done);
+    CK_LAUNCH();
+    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, done);
+}
+
+// BILU(0) solve in place on y (forward by ascending colors, backward by
+// descending colors); the backward sweep writes out (+ Pi_P e_P when ep).
+template <class T>
+void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, const int *jptr,
+                const int *done) {
+    cudaStream_t s = h->stream;
+    Bilu &B = h->bilu;
+    for (int c = 0; c < B.ncolors; c++) {
+        int cnt = B.color_off[c + 1] - B.color_off[c];
+        if (!cnt) continue;
+        k_bilu_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
+                                                               B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), y, done);
+        CK_LAUNCH();
+    }
+    for (int c = B.ncolors - 1; c >= 0; c--) {
+        int cnt = B.color_off[c + 1] - B.color_off[c];
+        if (!cnt) continue;
+        k_bilu_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
+                                                               B.Urowptr.p, B.Ucol.p, Vals<T>::Uv(h),
+                                                               Vals<T>::Dv(h), y, ep, out_base, ld, jptr, done);
+        CK_LAUNCH();
+    }
+}
+
+constexpr int kSpmvLanes = 8;
+
+template <class T>
+void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
+               long z_ld, const int *done) {
+    cudaStream_t s = h->stream;
+    int nb = h->nb;
+    Level &L0 = h->lev[0];
+    // r_P = Pi_P^T v
+    k_restrict<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, v_base, v_ld, jptr, Vals<T>::w(h),
+                                                          Vals<T>::b(L0), done);
+    CK_LAUNCH();
+    // e_P = B_P r_P
+    vcycle<T>(h, 0, done);
+    // r = v - A Pi_P e_P
+    long threads = (long)nb * kSpmvLanes;
+    k_prolong_resid<T, kSpmvLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        nb, h->rowptr.p, h->col.p, Vals<T>::c0(h), Vals<T>::x(L0), v_base, v_ld, jptr, Vals<T>::tmp(h), done);
+    CK_LAUNCH();
+    // z = Pi_P e_P + (LU)^-1 r
+    bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::x(L0), z_base, z_ld, jptr, done);
+}
+
+void spmv_launch(int nb, const int *rowptr, const int *col, const double *val, const double *x,
+                 long xld, const int *jptr, const double *b, double *y, cudaStream_t s,
+                 const int *done) {
+    long threads = (long)nb * kSpmvLanes;
+    k_bsr3_spmv<kSpmvLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        nb, rowptr, col, val, x, xld, jptr, b, y, done);
+    CK_LAUNCH();
+}
+
+// ||a||^2 partials into h->red, then a one-thread kernel consumes them.
+void norm_partials(cpr_handle *h, const double *a, long n) {
+    k_dot_partial<<<kRedBlocks, kBlock, 0, h->stream>>>(n, a, a, h->red.p);
+    CK_LAUNCH();
+}
+
+}  // namespace
+
+// ================================================================== public
+
+void bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val, const double *x,
+               const double *b, double *y, cudaStream_t s) {
+    spmv_launch(nb, rowptr, col, val, x, 0, nullptr, b, y, s, nullptr);
+}
+
+void ensure_workspace(cpr_handle *h) {
+    cudaStream_t s = h->stream;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
+    bool size_ok = h->V.n == (size_t)(m + 1) * N && h->m_alloc == m;
+    if (!size_ok) {
+        h->V.alloc((size_t)(m + 1) * N, s);
+        h->Z.alloc((size_t)m * N, s);
+        h->wv.alloc(N, s);
+        h->r.alloc(N, s);
+        h->dev_b.alloc(N, s);
+        h->dev_x.alloc(N, s);
+        h->t64a.alloc(N, s);
+        h->m_alloc = m;
+        ScalLayout L{m};
+        h->dscal.alloc(L.size(), s);
+        h->dscal.zero();
+        h->red.alloc((size_t)kRedBlocks * (kMaxRestart + 3), s);
+        h->dint.alloc(I_COUNT, s);
+        h->dint.zero();
+    }
+    if (h->opt.precond_fp32 && h->t32a.n != (size_t)N) h->t32a.alloc(N, s);
+    if (!h->pinned) CK(cudaMallocHost((void **)&h->pinned, 64 * sizeof(double)));
+}
+
+void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
+             long z_ld) {
+    if (h->opt.precond_fp32) apply_B_t<float>(h, v_base, v_ld, jptr, z_base, z_ld, nullptr);
+    else apply_B_t<double>(h, v_base, v_ld, jptr, z_base, z_ld, nullptr);
+}
+
+void vcycle_apply(cpr_handle *h, const double *b, double *x) {
+    cudaStream_t s = h->stream;
+    Level &L0 = h->lev[0];
+    long n = L0.A.n;
+    if (h->opt.precond_fp32) {
+        k_cast<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, b, L0.b32.p);
+        vcycle<float>(h, 0, nullptr);
+        k_widen<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, L0.x32.p, x);
+    } else {
+        CK(cudaMemcpyAsync(L0.b.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        vcycle<double>(h, 0, nullptr);
+        CK(cudaMemcpyAsync(x, L0.x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    CK_LAUNCH();
+}
+
+void bilu_apply(cpr_handle *h, const double *r, double *z) {
+    cudaStream_t s = h->stream;
+    long N = 3L * h->nb;
+    if (h->opt.precond_fp32) {
+        k_cast<float><<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, r, h->t32a.p);
+        CK_LAUNCH();
+        bilu_solve<float>(h, h->t32a.p, nullptr, z, 0, nullptr, nullptr);
+    } else {
+        CK(cudaMemcpyAsync(h->t64a.p, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        bilu_solve<double>(h, h->t64a.p, nullptr, z, 0, nullptr, nullptr);
+    }
+}
+
+// Flexible GMRES(m), right-preconditioned with B (Alg. 2): CGS Arnoldi, Givens
+// rotations on the device, stop on |g_{j+1}| < rtol ||r_0|| or h_{j+1,j} = 0,
+// true residual after every cycle.  The host reads one flag per step and one
+// norm per cycle.
+int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
+    cudaStream_t s = h->stream;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
+    ScalLayout SL{m};
+    int *di = h->dint.p;
+    double *sc = h->dscal.p;
+    const int *done = di + I_DONE;
+    int iters = 0, cycles = 0, rc = CPR_NOT_CONVERGED;
+    double norm0 = 0.0, rnorm = 0.0;
+    int ldp = kMaxRestart + 2;
+    for (int cycle = 0; cycle < h->opt.max_restarts; cycle++) {
+        // r = b - A x, beta = ||r||, V_0 = r / beta
+        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
+        norm_partials(h, h->r.p, N);
+        k_cycle_start_scal<<<1, 1, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, cycle == 0, rtol);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rnorm = h->pinned[0];
+        if (cycle == 0) norm0 = rnorm;
+        if (!std::isfinite(rnorm)) {
+            rc = CPR_ERR_BREAKDOWN;
+            break;
+        }
+        if (cycle == 0 && norm0 == 0.0) {
+            rc = CPR_OK;
+            break;
+        }
+        if (cycle > 0 && rnorm / norm0 < rtol) {
+            rc = CPR_OK;
+            break;
+        }
+        k_scale_into<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->r.p, h->V.p, sc, m);
+        CK_LAUNCH();
+        cycles++;
+        int *pin_i = reinterpret_cast<int *>(h->pinned + 8);
+        for (int j = 0; j < m; j++) {
+            // z_j = B v_j ; w = A z_j
+            if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+            else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+            spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s,
+                        done);
+            // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||
+            k_cgs_dots<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, done);
+            CK_LAUNCH();
+            k_reduce_cols<<<1, 128, 0, s>>>(h->red.p, kRedBlocks, ldp, di + I_J, sc + SL.hcol(), done);
+            CK_LAUNCH();
+            k_cgs_update<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, sc + SL.hcol(),
+                                                       h->red.p + (size_t)kRedBlocks * ldp, done);
+            CK_LAUNCH();
+            k_givens<<<1, 1, 0, s>>>(h->red.p + (size_t)kRedBlocks * ldp, kRedBlocks, sc, m, di);
+            CK_LAUNCH();
+            k_next_basis<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->wv.p, h->V.p, sc, m, di);
+            CK_LAUNCH();
+            CK(cudaMemcpyAsync(pin_i, di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            iters++;
+            if (pin_i[I_BREAK]) {
+                rc = CPR_ERR_BREAKDOWN;
+                break;
+            }
+            if (pin_i[I_DONE]) break;
+        }
+        if (rc == CPR_ERR_BREAKDOWN) break;
+        // y = H^-1 g, x += Z y
+        k_solve_y<<<1, 1, 0, s>>>(sc, m, di);
+        CK_LAUNCH();
+        k_update_x<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->Z.p, x, sc, m, di);
+        CK_LAUNCH();
+    }
+    if (rc == CPR_NOT_CONVERGED && cycles == h->opt.max_restarts) {
+        // true residual after the last cycle
+        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
+        norm_partials(h, h->r.p, N);
+        k_cycle_start_scal<<<1, 1, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, 0, rtol);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rnorm = h->pinned[0];
+        if (rnorm / norm0 < rtol) rc = CPR_OK;
+    }
+    if (st) {
+        st->iters = iters;
+        st->restarts = cycles;
+        st->converged = rc == CPR_OK;
+        st->rel_res = norm0 > 0.0 ? rnorm / norm0 : 0.0;
+    }
+    h->last_iters = iters;
+    return rc;
+}
+
+}  // namespace cpr

@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Discrete setup results (colors, C/F splits, sparsity patterns) must match bit
+for bit; the setup's values are computed in the oracle's order with explicit
+rounding and must match exactly too.  Preconditioner applications match to
+1e-10 relative (FP64: only summation order differs), and full solves match to
+1e-8 relative with iteration counts within +-1.
+"""
+import numpy as np
+import pytest
+
+import blackoil_synth as bs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+APPLY_TOL = 1e-10
+SOLVE_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    return T
+
+
+@pytest.fixture(scope="module")
+def cpr():
+    import paper_2201_01970_b300 as m
+    from paper_2201_01970_b300 import build
+    build.build()
+    return m
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+class DevJ:
+    """A Jacobian whose arrays live on the device."""
+
+    def __init__(self, torch, J):
+        self.nb = J.nb
+        self.rowptr = dev(torch, J.rowptr)
+        self.col = dev(torch, J.col)
+        self.val = dev(torch, J.val)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def ragged():
+    return bs.jacobian(bs.GridSpec(37, 23, 9, 0.0, 1.5, 0.3, None, "five_spot", seed=5))
+
+
+CASES = {
+    "tiny": lambda: bs.tiny(),
+    "20x20x5": lambda: bs.jacobian("20x20x5"),
+    "37x23x9": ragged,
+}
+
+
+def compare_hierarchy(o, g):
+    assert g.nlev == o.nlev
+    for l in range(o.nlev):
+        ol, gl = o.level(l), g.level(l)
+        A = ol["A"]
+        assert gl["n"] == A.n and gl["nnz"] == len(A.col), l
+        np.testing.assert_array_equal(gl["rowptr"], A.rowptr)
+        np.testing.assert_array_equal(gl["col"], A.col)
+        np.testing.assert_array_equal(gl["val"], A.val)
+        if l < o.nlev - 1:
+            assert gl["ncolors"] == ol["ncolors"]
+            np.testing.assert_array_equal(gl["color"], ol["color"])
+            np.testing.assert_array_equal(gl["cf"], ol["cf"])
+            P = ol["P"]
+            np.testing.assert_array_equal(gl["prow"], P.rowptr)
+            np.testing.assert_array_equal(gl["pcol"], P.col)
+            np.testing.assert_array_equal(gl["pval"], P.val)
+    np.testing.assert_array_equal(g.weights(), o.weights())
+    gbc, gnc, glu = g.bilu()
+    obc, onc, olu = o.bilu()
+    assert gnc == onc
+    np.testing.assert_array_equal(gbc, obc)
+    np.testing.assert_array_equal(glu, olu)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("decouple", [1, 0])
+def test_setup_bit_exact(torch, cpr, case, decouple):
+    J = CASES[case]()
+    kw = dict(decouple=decouple, coarse_max=16 if case == "tiny" else 256)
+    o = oracle.Solver(J, **kw)
+    g = cpr.Solver(DevJ(torch, J), **kw)
+    compare_hierarchy(o, g)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_components_match_oracle(torch, cpr, case):
+    J = CASES[case]()
+    kw = dict(coarse_max=16 if case == "tiny" else 256)
+    o = oracle.Solver(J, **kw)
+    g = cpr.Solver(DevJ(torch, J), **kw)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(J.n)
+    z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
+    g.apply(dev(torch, v), z)
+    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    bp = rng.standard_normal(J.nb)
+    xp = torch.zeros(J.nb, dtype=torch.float64, device="cuda")
+    g.vcycle(dev(torch, bp), xp)
+    assert rel(xp.cpu().numpy(), o.vcycle(bp)) < APPLY_TOL
+    g.bilu_apply(dev(torch, v), z)
+    assert rel(z.cpu().numpy(), o.bilu_apply(v)) < APPLY_TOL
+    x = rng.standard_normal(J.n)
+    y = cpr.bsr3_spmv(DevJ(torch, J), dev(torch, x))
+    assert rel(y.cpu().numpy(), oracle.bsr3_spmv(J, x)) < 1e-13
+    r = cpr.bsr3_spmv(DevJ(torch, J), dev(torch, x), b=dev(torch, J.b))
+    assert rel(r.cpu().numpy(), J.b - oracle.bsr3_spmv(J, x)) < 1e-12
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_solve_matches_oracle(torch, cpr, case):
+    J = CASES[case]()
+    kw = dict(coarse_max=16 if case == "tiny" else 256)
+    o = oracle.Solver(J, **kw)
+    g = cpr.Solver(DevJ(torch, J), **kw)
+    xo, so = o.solve(J.b, rtol=1e-6)
+    xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
+    xg = xg.cpu().numpy()
+    assert sg["converged"] and so["converged"]
+    assert abs(sg["iters"] - so["iters"]) <= 1, (sg, so)
+    true_rel = np.linalg.norm(J.b - oracle.bsr3_spmv(J, xg)) / np.linalg.norm(J.b)
+    assert true_rel < 1e-6
+    if sg["iters"] == so["iters"]:
+        assert rel(xg, xo) < SOLVE_TOL
+    # host buffers through the same entry point give the same answer
+    xh = np.zeros(J.n)
+    xh, sh = g.solve(J.b, xh, rtol=1e-6)
+    assert sh["iters"] == sg["iters"] and rel(xh, xg) < 1e-12
+
+
+def test_direct_solution_with_exact_coarse_solve(torch, cpr):
+    J = bs.tiny()
+    g = cpr.Solver(DevJ(torch, J), coarse_max=4096)
+    assert g.nlev == 1
+    x, st = g.solve(dev(torch, J.b), rtol=1e-12)
+    ref = np.linalg.solve(J.to_dense(), J.b)
+    assert st["converged"] and rel(x.cpu().numpy(), ref) < 1e-8
+
+
+def test_fp32_preconditioner(torch, cpr):
+    J = ragged()
+    o = oracle.Solver(J)
+    xo, so = o.solve(J.b, rtol=1e-6)
+    g = cpr.Solver(DevJ(torch, J), precond_fp32=1)
+    xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
+    xg = xg.cpu().numpy()
+    true_rel = np.linalg.norm(J.b - oracle.bsr3_spmv(J, xg)) / np.linalg.norm(J.b)
+    assert sg["converged"] and true_rel < 1e-6
+    assert abs(sg["iters"] - so["iters"]) <= max(2, so["iters"] // 5)
+    # error against the FP64 oracle's solution, stated per solve
+    err = rel(xg, xo)
+    print(f"fp32-preconditioner error vs FP64 oracle: {err:.3e} ({sg['iters']} vs {so['iters']} iters)")
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("mu", [0, 8, 10 ** 6])
+def test_adaptive_rule_trace(torch, cpr, mu):
+    g_spec = bs.GridSpec(12, 10, 4, 0.0, 1.0, 1.0, None, "corners", seed=4)
+    seq = list(bs.jacobian_sequence(g_spec, 6, drift=0.05))
+    g = cpr.Solver(DevJ(torch, seq[0]), mu=mu)
+    o = oracle.Solver(seq[0], mu=mu)
+    calls, iters, ocalls = [], [], []
+    for k, J in enumerate(seq):
+        if k:
+            g.update(DevJ(torch, J))
+            o.update(J)
+        _, st = g.solve(dev(torch, J.b))
+        _, so = o.solve(J.b)
+        calls.append(st["setup_called"])
+        ocalls.append(so["setup_called"])
+        iters.append(st["iters"])
+        assert st["converged"]
+        assert abs(st["iters"] - so["iters"]) <= 1
+    assert calls == [1] + [int(iters[k - 1] > mu) for k in range(1, len(seq))]
+    if mu in (0, 10 ** 6):
+        assert calls == ocalls
+
+
+def test_edge_cases(torch, cpr):
+    # a single block row
+    J1 = bs.Jacobian(1, np.array([0, 1], np.int32), np.array([0], np.int32),
+                     np.array([4.0, 1, 0, 1, 3, 1, 0, 1, 2]), np.array([1.0, 2.0, 3.0]))
+    g = cpr.Solver(J1)
+    x, st = g.solve(J1.b.copy())
+    assert st["converged"] and rel(x, np.linalg.solve(J1.to_dense(), J1.b)) < 1e-12
+    J = bs.tiny()
+    g = cpr.Solver(DevJ(torch, J))
+    # zero right-hand side: no iterations, x = 0
+    x, st = g.solve(np.zeros(J.n))
+    assert st["iters"] == 0 and st["converged"] and not x.any()
+    # NaN in b
+    b = J.b.copy()
+    b[5] = np.nan
+    with pytest.raises(cpr.CprError) as e:
+        g.solve(b)
+    assert e.value.code == cpr.CPR_ERR_BREAKDOWN
+    # malformed pattern (unsorted columns), host and device
+    bad = bs.tiny()
+    bad.col = bad.col.copy()
+    bad.col[[0, 1]] = bad.col[[1, 0]]
+    with pytest.raises(cpr.CprError) as e:
+        cpr.Solver(bad)
+    assert e.value.code == cpr.CPR_ERR_INVALID
+    with pytest.raises(cpr.CprError) as e:
+        cpr.Solver(DevJ(torch, bad))
+    assert e.value.code == cpr.CPR_ERR_INVALID
+    # a singular diagonal block
+    sing = bs.tiny()
+    sing.val = sing.val.copy()
+    p = sing.rowptr[3] + list(sing.col[sing.rowptr[3]:sing.rowptr[4]]).index(3)
+    sing.val[9 * p:9 * p + 9] = 0.0
+    with pytest.raises(cpr.CprError) as e:
+        cpr.Solver(sing)
+    assert e.value.code == cpr.CPR_ERR_SINGULAR
+    # a new size forces a setup (Remark 4.2)
+    g = cpr.Solver(bs.tiny(4, 4, 2), mu=10 ** 6)
+    g.solve(bs.tiny(4, 4, 2).b)
+    J2 = bs.tiny(5, 4, 2)
+    g.update(J2)
+    x, st = g.solve(J2.b)
+    assert st["setup_called"] == 1 and st["converged"]
+    # a nonzero initial guess
+    g = cpr.Solver(J)
+    x0 = np.random.default_rng(0).standard_normal(J.n)
+    x, st = g.solve(J.b, x0.copy(), rtol=1e-10)
+    assert rel(x, np.linalg.solve(J.to_dense(), J.b)) < 1e-7
+
+
+def test_full_size_128x128x32(torch, cpr):
+    """The benchmark's workload: the whole hierarchy bit-exact, and one solve."""
+    J = bs.jacobian("128x128x32")
+    o = oracle.Solver(J)
+    dj = DevJ(torch, J)
+    g = cpr.Solver(dj)
+    compare_hierarchy(o, g)
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal(J.n)
+    z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
+    g.apply(dev(torch, v), z)
+    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
+    xg = xg.cpu().numpy()
+    assert sg["converged"]
+    true_rel = np.linalg.norm(J.b - oracle.bsr3_spmv(J, xg)) / np.linalg.norm(J.b)
+    assert true_rel < 1e-6
+    print("128x128x32:", sg)
