@@ -91,10 +91,13 @@ struct Level {
     int ncolors = 0, nc = 0;
     std::vector<int> color_off;   // rows of color c: rows_by_color[color_off[c] .. color_off[c+1])
     DVec<int> rows_by_color;
+    // color_coupled[c]: some row of color c couples to another row of color c
+    // in A_l (possible at theta > 0); such colors relax through the staging vector
+    std::vector<char> color_coupled;
     DVec<double> dinv;            // 1 / a_ii
     DVec<float> Aval32, Pval32, Rval32, dinv32;
-    DVec<double> x, b, r;         // FP64 work vectors
-    DVec<float> x32, b32, r32;    // FP32 work vectors
+    DVec<double> x, b, r, xs;     // FP64 work vectors (xs: staging of coupled colors)
+    DVec<float> x32, b32, r32, xs32;
 };
 
 // Split multicolor BILU(0) factors.

@@ -578,6 +578,16 @@ __global__ void k_scatter_color(int n, const int *color, int c, const int *pos, 
     if (i < n && color[i] == c) rows[base + pos[i]] = i;
 }
 
+// Count, per color, the couplings a_ij (i != j) between rows of that color.
+__global__ void k_same_color_edges(int n, const int *rowptr, const int *col, const int *color,
+                                   int *cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = color[i], k = 0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) k += col[p] != i && color[col[p]] == c;
+    if (k) atomicAdd(&cnt[c], k);
+}
+
 __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const double *val,
                                double *a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1115,6 +1125,17 @@ void build_preconditioner(cpr_handle *h) {
             Graph G = sym_union(Sc, s);
             L.ncolors = jp_color(h, G, 0, l, L.color);
             rows_by_color(h, n, L.color.p, L.ncolors, L.color_off, L.rows_by_color);
+            DVec<int> same;
+            same.alloc(L.ncolors, s);
+            same.zero();
+            k_same_color_edges<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.color.p,
+                                                                     same.p);
+            CK_LAUNCH();
+            std::vector<int> hs(L.ncolors);
+            CK(cudaMemcpyAsync(hs.data(), same.p, sizeof(int) * L.ncolors, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            L.color_coupled.assign(L.ncolors, 0);
+            for (int c = 0; c < L.ncolors; c++) L.color_coupled[c] = hs[c] != 0;
         }
         h->lev.emplace_back();
         h->lev[l + 1].A = std::move(Ac);
@@ -1196,7 +1217,9 @@ void build_preconditioner(cpr_handle *h) {
         L.x.alloc(n, s);
         L.b.alloc(n, s);
         L.r.alloc(n, s);
+        L.xs.alloc(n, s);
         if (f32) {
+            L.xs32.alloc(n, s);
             to_f32(L.A.val, L.Aval32, s);
             to_f32(L.dinv, L.dinv32, s);
             if (L.P.nnz) {

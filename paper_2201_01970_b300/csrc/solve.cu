@@ -156,12 +156,14 @@ __global__ void k_mcgs_first(const int *rows, int cnt, const T *b, const T *dinv
     x[i] = b[i] * dinv[i];
 }
 
-// Rows of one color: x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii.  Rows of one
-// color never read each other's new values (Jacobi within a color).
+// Rows of one color: x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii, every x_j
+// as of the start of the color (Jacobi within a color).  The new values go to
+// xout: x itself when no two rows of the color are coupled, otherwise a
+// staging vector that k_mcgs_commit copies back after all rows have read x.
 template <class T>
 __global__ void k_mcgs_color(const int *rows, int cnt, const int *__restrict__ rowptr,
                              const int *__restrict__ col, const T *__restrict__ val, const T *b,
-                             const T *dinv, T *x, const int *done) {
+                             const T *dinv, const T *x, T *xout, const int *done) {
     if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
@@ -171,7 +173,16 @@ __global__ void k_mcgs_color(const int *rows, int cnt, const int *__restrict__ r
         int j = col[p];
         if (j != i) s -= val[p] * x[j];
     }
-    x[i] = s * dinv[i];
+    xout[i] = s * dinv[i];
+}
+
+template <class T>
+__global__ void k_mcgs_commit(const int *rows, int cnt, const T *xs, T *x, const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    int i = rows[t];
+    x[i] = xs[i];
 }
 
 // r = b - A x on a scalar CSR level.
@@ -490,6 +501,7 @@ struct Vals<double> {
     static double *x(Level &L) { return L.x.p; }
     static double *b(Level &L) { return L.b.p; }
     static double *r(Level &L) { return L.r.p; }
+    static double *xs(Level &L) { return L.xs.p; }
     static const double *w(const cpr_handle *h) { return h->w.p; }
     static const double *c0(const cpr_handle *h) { return h->pcol0.p; }
     static const double *Lv(const cpr_handle *h) { return h->bilu.Lval.p; }
@@ -506,6 +518,7 @@ struct Vals<float> {
     static float *x(Level &L) { return L.x32.p; }
     static float *b(Level &L) { return L.b32.p; }
     static float *r(Level &L) { return L.r32.p; }
+    static float *xs(Level &L) { return L.xs32.p; }
     static const float *w(const cpr_handle *h) { return h->w32.p; }
     static const float *c0(const cpr_handle *h) { return h->pcol0_32.p; }
     static const float *Lv(const cpr_handle *h) { return h->bilu.Lval32.p; }
@@ -527,9 +540,17 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, const 
             k_mcgs_first<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, Vals<T>::b(L),
                                                                      Vals<T>::dinv(L), Vals<T>::x(L), done);
         } else {
+            bool coupled = L.color_coupled[c] != 0;
+            T *xout = coupled ? Vals<T>::xs(L) : Vals<T>::x(L);
             k_mcgs_color<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, L.A.rowptr.p, L.A.col.p,
                                                                      Vals<T>::A(L), Vals<T>::b(L),
-                                                                     Vals<T>::dinv(L), Vals<T>::x(L), done);
+                                                                     Vals<T>::dinv(L), Vals<T>::x(L), xout,
+                                                                     done);
+            if (coupled) {
+                CK_LAUNCH();
+                k_mcgs_commit<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, Vals<T>::xs(L),
+                                                                          Vals<T>::x(L), done);
+            }
         }
         CK_LAUNCH();
     }

@@ -109,6 +109,9 @@ def test_components_match_oracle(torch, cpr, case):
     z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
     g.apply(dev(torch, v), z)
     assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    z2 = torch.zeros_like(z)
+    g.apply(dev(torch, v), z2)
+    assert torch.equal(z, z2)                        # run-to-run deterministic
     bp = rng.standard_normal(J.nb)
     xp = torch.zeros(J.nb, dtype=torch.float64, device="cuda")
     g.vcycle(dev(torch, bp), xp)
