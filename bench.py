@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the CPR-preconditioned FGMRES solve phase on B300.
+
+One step = one Newton linear system of a drifting Jacobian sequence on the
+128x128x32 synthetic black-oil workload (524,297 3x3 block rows, 9 wells):
+cpr_update(A^(k)) (Alg. 3 decides setup or reuse, mu = 30) followed by
+cpr_solve(b^(k)) to rtol 1e-6 (FGMRES(30) with CPR).  The Jacobians and
+right-hand sides of the sequence are resident in HBM before timing starts.
+`value` is FP32-preconditioner solves/s (FP64 outer FGMRES); the FP64 arm is
+reported beside it.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import blackoil_synth as bs  # noqa: E402
+
+METRIC = "CPR solves/s & V-cycle HBM GB/s at rtol 1e-6, FP32-precond vs FP64; p50/p99 ms"
+UNIT = "solves/s"
+WORKLOAD = "128x128x32"
+NSEQ = 4            # Jacobians of the drifting sequence kept resident in HBM
+RTOL = 1e-6
+MU = 30
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ byte models
+
+def vcycle_bytes(levels, sv, pre=1, post=1):
+    """Algorithmic bytes of one V(pre,post) cycle: each level's matrix read once
+    per sweep and once for the residual, R and P read once, ~13 vector passes
+    per level, the coarsest dense inverse once."""
+    tot = 0
+    for lv in levels[:-1]:
+        tot += (pre + post + 1) * lv["nnz"] * (sv + 4) + 2 * lv["nnz_p"] * (sv + 4)
+        tot += 13 * lv["n"] * sv + (pre + post) * lv["n"] * 4
+    nL = levels[-1]["n"]
+    tot += 8 * nL * nL + 2 * nL * sv
+    return tot
+
+
+def bilu_bytes(nb, nnzb, sv):
+    """L and U blocks (9 values + a column index each), D^-1, row pointers and
+    color lists, and the vector passes of the forward and backward sweeps."""
+    return (nnzb - nb) * (9 * sv + 4) + nb * 9 * sv + 16 * nb + 6 * 3 * nb * sv + nb * sv + 24 * nb
+
+
+def spmv_bytes(nb, nnzb):
+    """FP64 BSR: 72 B of values + 4 B of column per block; x, y and rowptr per block row."""
+    return 76 * nnzb + 52 * nb
+
+
+def cgs_bytes(N, cycles_steps):
+    """Dots over j+1 basis vectors and w, then w -= V h: (2j+5) N doubles at step j."""
+    return sum(8 * N * (2 * j + 5) for k in cycles_steps for j in range(k))
+
+
+def cycle_steps(iters, m):
+    out = []
+    while iters > 0:
+        out.append(min(iters, m))
+        iters -= m
+    return out
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def host_sequence(seed_offset=0):
+    g = bs.CONFIGS[WORKLOAD]
+    if seed_offset:
+        import dataclasses
+        g = dataclasses.replace(g, seed=g.seed + seed_offset)
+    return list(bs.jacobian_sequence(g, NSEQ, drift=0.05))
+
+
+# --------------------------------------------------------------- our arm
+
+def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream):
+    """Time K update+solve steps of one precision arm; returns a dict."""
+    S = len(seq_dev)
+    solver = cpr.Solver(seq_dev[0], precond_fp32=int(fp32), mu=MU, stream=stream.cuda_stream)
+    x = torch.zeros_like(rhs_dev[0])
+    stats = []
+
+    def step(k):
+        if k:
+            solver.update(seq_dev[k % S])
+        with torch.cuda.stream(stream):
+            x.zero_()
+        _, st = solver.solve(rhs_dev[k % S], x, rtol=RTOL)
+        if not st["converged"]:
+            raise RuntimeError(f"solve did not converge: {st}")
+        return st
+
+    for k in range(W):
+        step(k)
+    solver.profile(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    launches0 = cpr.launch_count()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(K):
+        stats.append(step(W + i))
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = cpr.launch_count() - launches0
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
+    total = ev[0].elapsed_time(ev[K])
+    fam = {f: solver.profile_read(f) for f in range(5)}
+    levels = [solver.level(l) for l in range(solver.nlev)]
+    solver.close()
+    return {"per_ms": per, "total_ms": total, "stats": stats, "fam": fam, "levels": levels,
+            "launches": launches}
+
+
+def e2e_arm(cpr, torch, seq_host, K, W, stream):
+    """Same metric through the C ABI with pinned HOST buffers (copies inside the calls)."""
+    S = len(seq_host)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:1]).dtype, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    hseq = []
+    for J in seq_host:
+        hseq.append(bs.Jacobian(J.nb, pinned(J.rowptr), pinned(J.col), pinned(J.val), pinned(J.b)))
+    xh = pinned(np.zeros(3 * seq_host[0].nb))
+    solver = cpr.Solver(hseq[0], precond_fp32=1, mu=MU, stream=stream.cuda_stream)
+
+    def step(k):
+        if k:
+            solver.update(hseq[k % S])
+        xh[...] = 0.0
+        _, st = solver.solve(hseq[k % S].b, xh, rtol=RTOL)
+        return st
+
+    for k in range(W):
+        step(k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        step(W + i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    solver.close()
+    J = seq_host[0]
+    h2d = J.rowptr.nbytes + J.col.nbytes + J.val.nbytes + J.b.nbytes + xh.nbytes
+    return {"value": K / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(xh.nbytes)}
+
+
+def cpu_baseline(seq_host):
+    """The FP64 oracle, single-threaded on the host: one update (full setup, as
+    It > mu) and one solve of the same workload's second Jacobian."""
+    import oracle
+    oracle.build()
+    o = oracle.Solver(seq_host[0], mu=MU)
+    _, st0 = o.solve(seq_host[0].b, rtol=RTOL)
+    t0 = time.perf_counter()
+    o.update(seq_host[1])
+    _, st = o.solve(seq_host[1].b, rtol=RTOL)
+    dt = time.perf_counter() - t0
+    o.close()
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one update+solve of a {WORKLOAD} Jacobian (setup_called={st['setup_called']}, "
+                      f"{st['iters']} iterations, {dt:.1f} s)"}
+
+
+# ---------------------------------------------------------- reference arm
+
+def reference_arm(args, rank, world):
+    """The FP64 oracle as the reference implementation, on the host cores.
+    Each step is one update+solve of a bounded sample of the workload: the
+    full grid when K+W full steps fit the time budget, else a z-slab of it
+    (the first nz' layers, same generator), scaled to the full grid by cells."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    budget = 170.0
+    g = bs.CONFIGS[WORKLOAD]
+    t_full_est = 16.0
+    nz = max(1, min(g.nz, int(g.nz * budget / (max(1, args.steps + args.warmup) * t_full_est))))
+    import dataclasses
+    gs = dataclasses.replace(g, nz=nz)
+    seq = list(bs.jacobian_sequence(gs, NSEQ, drift=0.05))
+    scale = g.ncells / gs.ncells
+    o = oracle.Solver(seq[0], mu=MU)
+    times = []
+    for k in range(args.warmup + args.steps):
+        J = seq[(k + 1) % NSEQ]
+        t0 = time.perf_counter()
+        o.update(J)
+        _, st = o.solve(J.b, rtol=RTOL)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    o.close()
+    per_solve_full = statistics.mean(times) * scale
+    value = 1.0 / per_solve_full
+    sample = (f"{g.nx}x{g.ny}x{nz} slab of the {WORKLOAD} workload per step"
+              + (f", times scaled by {scale:.2f} (cells)" if scale != 1 else ""))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * per_solve_full,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} synthetic black-oil, drifting Newton sequence",
+                       "mu": MU, "rtol": RTOL, "restart": 30},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    import paper_2201_01970_b300 as cpr
+    from paper_2201_01970_b300 import build
+    if rank == 0:
+        build.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+
+    seq_host = host_sequence(seed_offset=rank)
+
+    class DJ:
+        def __init__(self, J):
+            self.nb = J.nb
+            self.rowptr = torch.from_numpy(J.rowptr).cuda()
+            self.col = torch.from_numpy(J.col).cuda()
+            self.val = torch.from_numpy(J.val).cuda()
+
+    seq_dev = [DJ(J) for J in seq_host]
+    rhs_dev = [torch.from_numpy(J.b).cuda() for J in seq_host]
+    torch.cuda.synchronize()
+    K, W = args.steps, args.warmup
+
+    clk = ClockSampler(local)
+    clk.start()
+    r32 = run_arm(cpr, torch, seq_dev, rhs_dev, True, K, W, world, stream)
+    r64 = run_arm(cpr, torch, seq_dev, rhs_dev, False, K, W, world, stream)
+    clocks = clk.stop()
+
+    e2e = None if args.no_e2e else e2e_arm(cpr, torch, seq_host, max(3, K // 2), 1, stream)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(seq_host)
+
+    t32 = max_over_ranks(r32["total_ms"], world)
+    t64 = max_over_ranks(r64["total_ms"], world)
+    value = sum_over_ranks(K, world) / (t32 / 1000.0)
+    v64 = sum_over_ranks(K, world) / (t64 / 1000.0)
+    if e2e is not None:
+        e2e["value"] = sum_over_ranks(e2e["value"], world)
+
+    J0 = seq_host[0]
+    nb, nnzb, N = J0.nb, J0.nnzb, 3 * J0.nb
+    hbm, peak_kind = peaks()
+
+    def fam_report(r, sv):
+        fam, lv = r["fam"], r["levels"]
+        out = {}
+        n, ms = fam[cpr.PROF_SPMV]
+        if n:
+            out["spmv"] = {"launches": n, "avg_us": 1000 * ms / n,
+                           "gbs": spmv_bytes(nb, nnzb) / (ms / n * 1e-3) / 1e9}
+        n, ms = fam[cpr.PROF_VCYCLE]
+        if n:
+            vb = vcycle_bytes(lv, sv)
+            out["vcycle"] = {"applications": n, "avg_us": 1000 * ms / n, "bytes": vb,
+                             "gbs": vb / (ms / n * 1e-3) / 1e9}
+        n, ms = fam[cpr.PROF_BILU]
+        if n:
+            bb = bilu_bytes(nb, nnzb, sv)
+            out["bilu"] = {"applications": n, "avg_us": 1000 * ms / n, "bytes": bb,
+                           "gbs": bb / (ms / n * 1e-3) / 1e9}
+        n, ms = fam[cpr.PROF_CGS]
+        if n:
+            cb = sum(cgs_bytes(N, cycle_steps(st["iters"], 30)) for st in r["stats"])
+            out["cgs"] = {"steps": n, "avg_us": 1000 * ms / n, "gbs": cb / (ms * 1e-3) / 1e9}
+        n, ms = fam[cpr.PROF_RESID2]
+        if n:
+            rb = nnzb * (3 * sv + 4) + nb * (4 + 3 * 8 + 3 * sv) + nnzb * sv
+            out["resid2"] = {"launches": n, "avg_us": 1000 * ms / n,
+                             "gbs": rb / (ms / n * 1e-3) / 1e9}
+        return out
+
+    f32 = fam_report(r32, 4)
+    f64 = fam_report(r64, 8)
+    sp = f64.get("spmv", {})
+    roof = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV, w = A z_j)", "bound": "hbm",
+            "achieved": sp.get("gbs"), "peak": hbm, "unit": "GB/s",
+            "frac": (sp.get("gbs") / hbm) if sp.get("gbs") else None,
+            "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+            "bytes_per_launch": spmv_bytes(nb, nnzb)}
+
+    def pct(a, q):
+        return float(np.percentile(np.array(a), q))
+
+    iters32 = [s["iters"] for s in r32["stats"]]
+    iters64 = [s["iters"] for s in r64["stats"]]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t32 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 preconditioner / f64 outer", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} synthetic black-oil (3x3 BSR, 9 wells), {NSEQ}-Jacobian "
+                               f"drifting Newton sequence resident in HBM, update+solve per step",
+                   "nb": nb, "nnzb": nnzb, "dof": N, "mu": MU, "rtol": RTOL, "restart": 30,
+                   "l2": "inputs larger than L2 (A values 261 MB per Jacobian)",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": pct(r32["per_ms"], 50), "p99_ms": pct(r32["per_ms"], 99),
+        "iters_mean": statistics.mean(iters32),
+        "setups_in_timed_region": sum(s["setup_called"] for s in r32["stats"]),
+        "fp64": {"value": v64, "unit": UNIT, "ms_per_step": t64 / K, "p50_ms": pct(r64["per_ms"], 50),
+                 "p99_ms": pct(r64["per_ms"], 99), "iters_mean": statistics.mean(iters64),
+                 "setups_in_timed_region": sum(s["setup_called"] for s in r64["stats"])},
+        "fp32_over_fp64": value / v64,
+        "vcycle_gbs": {"fp32": f32.get("vcycle", {}).get("gbs"), "fp64": f64.get("vcycle", {}).get("gbs"),
+                       "frac_fp32": (f32.get("vcycle", {}).get("gbs") or 0) / hbm,
+                       "frac_fp64": (f64.get("vcycle", {}).get("gbs") or 0) / hbm},
+        "families": {"fp32": f32, "fp64": f64},
+        "roofline": roof,
+        "gpu_launches": int(r32["launches"]),
+        "clocks": clocks,
+    }
+    if e2e is not None:
+        line["e2e"] = e2e
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,29 @@ int cpr_copy_weights(const cpr_handle *h, double *w);
  * the diagonal in (color, index) order, U_ij above it, U_ii^-1 on it). */
 int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolors);
 
+/* ------------------------------------------------------------------------
+ * Measurement hooks (diagnostics).
+ * ---------------------------------------------------------------------- */
+
+/* Number of kernels this library has launched in this process so far. */
+uint64_t cpr_launch_count(void);
+
+/* Kernel families that cpr_profile brackets with CUDA events on the handle's
+ * stream during cpr_solve. */
+#define CPR_PROF_SPMV 0      /* one outer BSR SpMV launch, w = A z or r = b - A x */
+#define CPR_PROF_VCYCLE 1    /* one whole V-cycle application (all its launches) */
+#define CPR_PROF_BILU 2      /* one whole BILU(0) forward+backward application */
+#define CPR_PROF_CGS 3       /* one CGS orthogonalisation (dots, reduction, update) */
+#define CPR_PROF_RESID2 4    /* one second-residual launch (Alg. 1 line 3) */
+#define CPR_PROF_NFAMILIES 5
+
+/* enable != 0: time the families above during later solves (adds two event
+ * records per bracketed region); 0: stop.  Both reset the accumulators. */
+int cpr_profile(cpr_handle *h, int enable);
+
+/* Accumulated bracket count and device milliseconds of one family. */
+int cpr_profile_read(const cpr_handle *h, int family, long *count, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,9 @@ def lib():
         L.cpr_copy_level.argtypes = [vp, C.c_int] + [vp] * 8
         L.cpr_copy_weights.argtypes = [vp, vp]
         L.cpr_copy_bilu.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
+        L.cpr_launch_count.restype = C.c_uint64
+        L.cpr_profile.argtypes = [vp, C.c_int]
+        L.cpr_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -226,6 +229,18 @@ class Solver:
         _check(lib().cpr_copy_bilu(self._h, _ptr(bc), _ptr(lu), C.byref(nc)), "cpr_copy_bilu")
         return bc, nc.value, lu
 
+    def profile(self, enable: bool = True) -> None:
+        _check(lib().cpr_profile(self._h, int(enable)), "cpr_profile")
+
+    def profile_read(self, family: int):
+        n, ms = C.c_long(), C.c_double()
+        _check(lib().cpr_profile_read(self._h, family, C.byref(n), C.byref(ms)), "cpr_profile_read")
+        return n.value, ms.value
+
+    @property
+    def stream(self) -> int:
+        return self.opts.stream or 0
+
     def close(self) -> None:
         if self._h:
             lib().cpr_destroy(self._h)
@@ -236,6 +251,13 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+PROF_SPMV, PROF_VCYCLE, PROF_BILU, PROF_CGS, PROF_RESID2 = range(5)
+
+
+def launch_count() -> int:
+    return int(lib().cpr_launch_count())
 
 
 def bsr3_spmv(A, x, b=None, y=None, stream=None):

@@ -104,7 +104,63 @@ void build_timed(cpr_handle *h) {
 
 }  // namespace
 
+namespace cpr {
+unsigned long long launch_count();
+
+void prof_begin(cpr_handle *h, int family) {
+    if (!h->prof) return;
+    if (h->ev_n == cpr_handle::kProfSlots) prof_flush(h);
+    int k = h->ev_n;
+    if (!h->ev_a[k]) {
+        CK(cudaEventCreate(&h->ev_a[k]));
+        CK(cudaEventCreate(&h->ev_b[k]));
+    }
+    h->ev_fam[k] = family;
+    CK(cudaEventRecord(h->ev_a[k], h->stream));
+}
+
+void prof_end(cpr_handle *h) {
+    if (!h->prof) return;
+    CK(cudaEventRecord(h->ev_b[h->ev_n], h->stream));
+    h->ev_n++;
+}
+
+void prof_flush(cpr_handle *h) {
+    if (!h->ev_n) return;
+    CK(cudaEventSynchronize(h->ev_b[h->ev_n - 1]));
+    for (int k = 0; k < h->ev_n; k++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, h->ev_a[k], h->ev_b[k]));
+        h->prof_cnt[h->ev_fam[k]]++;
+        h->prof_ms[h->ev_fam[k]] += ms;
+    }
+    h->ev_n = 0;
+}
+}  // namespace cpr
+
 extern "C" {
+
+uint64_t cpr_launch_count(void) { return (uint64_t)cpr::launch_count(); }
+
+int cpr_profile(cpr_handle *h, int enable) {
+    if (!h) return CPR_ERR_INVALID;
+    return guarded([&] {
+        prof_flush(h);
+        h->prof = enable != 0;
+        for (int f = 0; f < CPR_PROF_NFAMILIES; f++) {
+            h->prof_cnt[f] = 0;
+            h->prof_ms[f] = 0.0;
+        }
+        return CPR_OK;
+    });
+}
+
+int cpr_profile_read(const cpr_handle *h, int family, long *count, double *ms) {
+    if (!h || family < 0 || family >= CPR_PROF_NFAMILIES) return CPR_ERR_INVALID;
+    if (count) *count = h->prof_cnt[family];
+    if (ms) *ms = h->prof_ms[family];
+    return CPR_OK;
+}
 
 void cpr_default_opts(cpr_opts *o) {
     o->theta_color = 0.05;
@@ -238,6 +294,7 @@ int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats 
         }
         cpr_stats local{};
         int rc = fgmres(h, db, dx, rtol, &local);
+        prof_flush(h);
         if (!xdev) CK(cudaMemcpyAsync(x, dx, bytes, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         local.setup_called = h->setup_called;
@@ -260,6 +317,10 @@ void cpr_destroy(cpr_handle *h) {
     cudaStream_t s = h->stream;
     bool own = h->own_stream;
     if (h->pinned) cudaFreeHost(h->pinned);
+    for (int k = 0; k < cpr_handle::kProfSlots; k++) {
+        if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);
+        if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
+    }
     h->pinned = nullptr;
     delete h;  // DVec destructors free on the stream
     if (s) cudaStreamSynchronize(s);

@@ -7,6 +7,10 @@ namespace cpr {
 
 void fail(int code, const std::string &what) { throw Error{code, what}; }
 
+static unsigned long long g_launches = 0;
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 void check_cuda(cudaError_t e, const char *expr, const char *file, int line) {
     if (e == cudaSuccess) return;
     int code = e == cudaErrorMemoryAllocation ? CPR_ERR_OOM : CPR_ERR_CUDA;

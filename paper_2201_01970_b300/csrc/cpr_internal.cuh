@@ -24,7 +24,12 @@ struct Error {
 [[noreturn]] void fail(int code, const std::string &what);
 void check_cuda(cudaError_t e, const char *expr, const char *file, int line);
 #define CK(x) ::cpr::check_cuda((x), #x, __FILE__, __LINE__)
-#define CK_LAUNCH() ::cpr::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+void count_launch();
+#define CK_LAUNCH()                                                                   \
+    do {                                                                              \
+        ::cpr::count_launch();                                                        \
+        ::cpr::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);   \
+    } while (0)
 
 // ------------------------------------------------------------ device buffers
 
@@ -147,6 +152,14 @@ struct cpr_handle {
     long last_iters = -1;
     int setup_count = 0, setup_called = 0, updates = 0;
     double setup_ms = 0.0;
+    // --- event brackets of kernel families (cpr_profile) ---
+    bool prof = false;
+    static constexpr int kProfSlots = 512;
+    cudaEvent_t ev_a[kProfSlots] = {}, ev_b[kProfSlots] = {};
+    int ev_fam[kProfSlots] = {};
+    int ev_n = 0;
+    long prof_cnt[CPR_PROF_NFAMILIES] = {};
+    double prof_ms[CPR_PROF_NFAMILIES] = {};
 };
 
 namespace cpr {
@@ -159,6 +172,11 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t s);   // out ha
 int read_int(const int *dptr, cudaStream_t s);
 uint32_t hash_base(uint64_t seed, int salt, int level);
 bool is_device_ptr(const void *p);
+
+// event brackets (api.cu)
+void prof_begin(cpr_handle *h, int family);
+void prof_end(cpr_handle *h);
+void prof_flush(cpr_handle *h);
 
 // setup.cu
 void build_preconditioner(cpr_handle *h);

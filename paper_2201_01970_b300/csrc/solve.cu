@@ -622,14 +622,20 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
                                                           Vals<T>::b(L0), done);
     CK_LAUNCH();
     // e_P = B_P r_P
+    prof_begin(h, CPR_PROF_VCYCLE);
     vcycle<T>(h, 0, done);
+    prof_end(h);
     // r = v - A Pi_P e_P
     long threads = (long)nb * kSpmvLanes;
+    prof_begin(h, CPR_PROF_RESID2);
     k_prolong_resid<T, kSpmvLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
         nb, h->rowptr.p, h->col.p, Vals<T>::c0(h), Vals<T>::x(L0), v_base, v_ld, jptr, Vals<T>::tmp(h), done);
     CK_LAUNCH();
+    prof_end(h);
     // z = Pi_P e_P + (LU)^-1 r
+    prof_begin(h, CPR_PROF_BILU);
     bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::x(L0), z_base, z_ld, jptr, done);
+    prof_end(h);
 }
 
 void spmv_launch(int nb, const int *rowptr, const int *col, const double *val, const double *x,
@@ -761,8 +767,11 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
             // z_j = B v_j ; w = A z_j
             if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
             else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+            prof_begin(h, CPR_PROF_SPMV);
             spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s,
                         done);
+            prof_end(h);
+            prof_begin(h, CPR_PROF_CGS);
             // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||
             k_cgs_dots<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, done);
             CK_LAUNCH();
@@ -771,6 +780,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
             k_cgs_update<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, sc + SL.hcol(),
                                                        h->red.p + (size_t)kRedBlocks * ldp, done);
             CK_LAUNCH();
+            prof_end(h);
             k_givens<<<1, 1, 0, s>>>(h->red.p + (size_t)kRedBlocks * ldp, kRedBlocks, sc, m, di);
             CK_LAUNCH();
             k_next_basis<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->wv.p, h->V.p, sc, m, di);
