@@ -203,7 +203,7 @@ class Solver:
         info = LevelInfo()
         _check(lib().cpr_get_level_info(self._h, l, C.byref(info)), "cpr_get_level_info")
         n, nnz, nnzp = info.n, info.nnz, info.nnz_p
-        out = {"n": n, "nnz": nnz, "ncolors": info.ncolors, "nc": info.nc,
+        out = {"n": n, "nnz": nnz, "ncolors": info.ncolors, "nc": info.nc, "nnz_p": nnzp,
                "rowptr": np.zeros(n + 1, np.int32), "col": np.zeros(nnz, np.int32),
                "val": np.zeros(nnz), "color": np.zeros(n, np.int32), "cf": np.zeros(n, np.int32),
                "prow": np.zeros(n + 1, np.int32), "pcol": np.zeros(nnzp, np.int32),
