@@ -179,7 +179,7 @@ def host_sequence(seed_offset=0):
 
 # --------------------------------------------------------------- our arm
 
-def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream):
+def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_region=False):
     """Time K update+solve steps of one precision arm; returns a dict."""
     S = len(seq_dev)
     solver = cpr.Solver(seq_dev[0], precond_fp32=int(fp32), mu=MU, stream=stream.cuda_stream)
@@ -203,11 +203,15 @@ def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream):
     launches0 = cpr.launch_count()
     barrier(world)
     torch.cuda.synchronize()
+    if profile_region:
+        torch.cuda.profiler.start()
     ev[0].record(stream)
     for i in range(K):
         stats.append(step(W + i))
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    if profile_region:
+        torch.cuda.profiler.stop()
     barrier(world)
     launches = cpr.launch_count() - launches0
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
@@ -329,6 +333,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
+                    help="precision arms to time (the JSON line needs both)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the first timed region with cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -362,9 +370,21 @@ def main():
 
     clk = ClockSampler(local)
     clk.start()
-    r32 = run_arm(cpr, torch, seq_dev, rhs_dev, True, K, W, world, stream)
-    r64 = run_arm(cpr, torch, seq_dev, rhs_dev, False, K, W, world, stream)
+    pr = args.profile_region
+    r32 = r64 = None
+    if args.arm in ("both", "fp32"):
+        r32 = run_arm(cpr, torch, seq_dev, rhs_dev, True, K, W, world, stream, pr)
+        pr = False
+    if args.arm in ("both", "fp64"):
+        r64 = run_arm(cpr, torch, seq_dev, rhs_dev, False, K, W, world, stream, pr)
     clocks = clk.stop()
+    if r32 is None or r64 is None:
+        r = r32 or r64
+        if rank == 0:
+            print(json.dumps({"partial": args.arm, "ms_per_step": r["total_ms"] / K,
+                              "launches_per_step": r["launches"] / K,
+                              "iters": [st["iters"] for st in r["stats"]]}), flush=True)
+        return
 
     e2e = None if args.no_e2e else e2e_arm(cpr, torch, seq_host, max(3, K // 2), 1, stream)
     cpu = None
