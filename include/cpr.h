@@ -143,6 +143,23 @@ int cpr_vcycle(cpr_handle *h, const double *b, double *x);
  * r, z: 3*nb. */
 int cpr_bilu_apply(cpr_handle *h, const double *r, double *z);
 
+/* z = R r exactly as cpr_bilu_apply, for callers that must not allocate
+ * device memory at call time -- e.g. a simulator that reserves its whole
+ * device-memory budget at start-up, or code that runs while another component
+ * owns the allocator.  The paper has no counterpart: this is an interface
+ * variant only.  The sweeps' work vector (3*nb values) lives in a fixed
+ * device array of 65,536 block rows (1.5 MiB) that every GPU loading this
+ * library holds until the process exits; a handle with more block rows gets
+ * CPR_ERR_INVALID.  The call allocates nothing and frees nothing.  The first
+ * call on a device looks up that array's device address (with the device
+ * current), so make the first call before any stream capture.  All calls share
+ * the one array and leave their last contents in it; nothing in it needs to
+ * start at zero (each call writes every entry it reads first).  Calls whose
+ * GPU work overlaps -- two streams, two handles, two threads -- race on the
+ * array: serialise them.  r, z: DEVICE pointers, 3*nb; ordered on the handle's
+ * stream; returns after completion. */
+int cpr_bilu_apply_noalloc(cpr_handle *h, const double *r, double *z);
+
 /* y = A x (or r = b - A x when b != NULL) for a 3x3 BSR matrix (Eq. 2.8),
  * all DEVICE pointers, stateless, ordered on `stream` (cudaStream_t; NULL =
  * legacy default stream), asynchronous. */

@@ -107,6 +107,8 @@ void build_timed(cpr_handle *h) {
 namespace cpr {
 unsigned long long launch_count();
 
+void set_last_error(const std::string &what) { g_last_error = what; }
+
 void prof_begin(cpr_handle *h, int family) {
     if (!h->prof) return;
     if (h->ev_n == cpr_handle::kProfSlots) prof_flush(h);

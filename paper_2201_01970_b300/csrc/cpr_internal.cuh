@@ -173,6 +173,9 @@ int read_int(const int *dptr, cudaStream_t s);
 uint32_t hash_base(uint64_t seed, int salt, int level);
 bool is_device_ptr(const void *p);
 
+// text of the calling thread's last failure (api.cu)
+void set_last_error(const std::string &what);
+
 // event brackets (api.cu)
 void prof_begin(cpr_handle *h, int family);
 void prof_end(cpr_handle *h);
