@@ -111,6 +111,15 @@ void set_last_error(const std::string &what) { g_last_error = what; }
 
 void prof_begin(cpr_handle *h, int family) {
     if (!h->prof) return;
+    if (h->capturing >= 0) {
+        auto &g = h->sg[h->capturing];
+        cudaEvent_t a;
+        CK(cudaEventCreate(&a));
+        CK(cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal));
+        g.ev_a.push_back(a);
+        g.fam.push_back(family);
+        return;
+    }
     if (h->ev_n == cpr_handle::kProfSlots) prof_flush(h);
     int k = h->ev_n;
     if (!h->ev_a[k]) {
@@ -123,8 +132,38 @@ void prof_begin(cpr_handle *h, int family) {
 
 void prof_end(cpr_handle *h) {
     if (!h->prof) return;
+    if (h->capturing >= 0) {
+        auto &g = h->sg[h->capturing];
+        cudaEvent_t b;
+        CK(cudaEventCreate(&b));
+        CK(cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal));
+        g.ev_b.push_back(b);
+        return;
+    }
     CK(cudaEventRecord(h->ev_b[h->ev_n], h->stream));
     h->ev_n++;
+}
+
+// Accumulate the event-node brackets of step graph `which` (its last launch has completed).
+void prof_collect_graph(cpr_handle *h, int which) {
+    auto &g = h->sg[which];
+    for (size_t k = 0; k < g.ev_a.size() && k < g.ev_b.size(); k++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g.ev_a[k], g.ev_b[k]));
+        h->prof_cnt[g.fam[k]]++;
+        h->prof_ms[g.fam[k]] += ms;
+    }
+}
+
+void destroy_step_graphs(cpr_handle *h) {
+    for (auto &g : h->sg) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        for (auto e : g.ev_a) cudaEventDestroy(e);
+        for (auto e : g.ev_b) cudaEventDestroy(e);
+        g = cpr_handle::StepGraph{};
+    }
+    h->sg_epoch = -1;
 }
 
 void prof_flush(cpr_handle *h) {
@@ -318,6 +357,9 @@ void cpr_destroy(cpr_handle *h) {
     }
     cudaStream_t s = h->stream;
     bool own = h->own_stream;
+    destroy_step_graphs(h);
+    for (auto e : h->step_done)
+        if (e) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (int k = 0; k < cpr_handle::kProfSlots; k++) {
         if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);

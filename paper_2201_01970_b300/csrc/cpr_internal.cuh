@@ -87,22 +87,25 @@ struct DCsr {
     DVec<double> val;
 };
 
-// One AMG level: A_l in natural numbering (the setup result, bit-identical to
-// the plain definition's), its coloring, C/F split and transfer operators,
-// the FP32 shadows and the V-cycle's work vectors.
+// One AMG level.  A, P, R hold the setup result in natural numbering
+// (bit-identical to the plain definition's; used for inspection).  The solve
+// uses copies renumbered into color order, so each color is a contiguous row
+// range [color_off[c], color_off[c+1]): Ao (A without its diagonal), diag and
+// dinv, Pp (rows in this level's order, columns in the next level's), Rp.
 struct Level {
     DCsr A, P, R;
     DVec<int> color, cf;
     int ncolors = 0, nc = 0;
-    std::vector<int> color_off;   // rows of color c: rows_by_color[color_off[c] .. color_off[c+1])
-    DVec<int> rows_by_color;
-    // color_coupled[c]: some row of color c couples to another row of color c
-    // in A_l (possible at theta > 0); such colors relax through the staging vector
-    std::vector<char> color_coupled;
-    DVec<double> dinv;            // 1 / a_ii
-    DVec<float> Aval32, Pval32, Rval32, dinv32;
-    DVec<double> x, b, r, xs;     // FP64 work vectors (xs: staging of coupled colors)
-    DVec<float> x32, b32, r32, xs32;
+    std::vector<int> color_off;
+    DVec<int> rows_by_color;      // order: internal row t is natural row rows_by_color[t]
+    DVec<int> iperm;              // natural row i is internal row iperm[i]
+    DCsr Ao, Pp, Rp;
+    DVec<double> diag, dinv;      // internal numbering
+    DVec<float> Aoval32, Ppval32, Rpval32, diag32, dinv32;
+    int gA = 8, gP = 4, gR = 8;   // lanes per row of the solve kernels
+    // work vectors (internal numbering); s0, s1: staging of the color being relaxed
+    DVec<double> x, b, r, s0, s1;
+    DVec<float> x32, b32, r32, s0_32, s1_32;
 };
 
 // Split multicolor BILU(0) factors.
@@ -135,7 +138,7 @@ struct cpr_handle {
     cpr::DVec<float> w32;
     std::vector<cpr::Level> lev;
     int cn = 0;                     // coarsest size
-    cpr::DVec<double> cinv;         // dense inverse of the coarsest A, column-major
+    cpr::DVec<double> cinv;         // dense inverse of the coarsest A, row-major
     cpr::Bilu bilu;
     // --- Krylov workspace ---
     int m_alloc = 0;
@@ -145,6 +148,8 @@ struct cpr_handle {
     cpr::DVec<int> dint;            // device ints (step index, flags)
     cpr::DVec<float> t32a, t32b;    // FP32 vectors of length 3*nb inside B
     cpr::DVec<double> t64a;         // FP64 vector of length 3*nb inside B
+    cpr::DVec<double> ep64;         // e_P = B_P r_P in natural numbering
+    cpr::DVec<float> ep32;
     cpr::DVec<double> dev_b, dev_x; // device copies of host b / x
     double *pinned = nullptr;       // pinned host scalars
     cpr::DVec<int> err;             // device error flag
@@ -160,6 +165,18 @@ struct cpr_handle {
     int ev_n = 0;
     long prof_cnt[CPR_PROF_NFAMILIES] = {};
     double prof_ms[CPR_PROF_NFAMILIES] = {};
+    // --- graphs of one Arnoldi step (two instances, used on alternate steps) ---
+    int epoch = 0;                   // bumped whenever B or the workspace changes
+    struct StepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<cudaEvent_t> ev_a, ev_b;   // event-record nodes (profiling)
+        std::vector<int> fam;
+    } sg[2];
+    int sg_epoch = -1;
+    bool sg_prof = false;
+    int capturing = -1;              // index of the step graph being captured, -1 = none
+    cudaEvent_t step_done[2] = {nullptr, nullptr};
 };
 
 namespace cpr {
@@ -180,6 +197,8 @@ void set_last_error(const std::string &what);
 void prof_begin(cpr_handle *h, int family);
 void prof_end(cpr_handle *h);
 void prof_flush(cpr_handle *h);
+void prof_collect_graph(cpr_handle *h, int which);
+void destroy_step_graphs(cpr_handle *h);
 
 // setup.cu
 void build_preconditioner(cpr_handle *h);

@@ -578,14 +578,52 @@ __global__ void k_scatter_color(int n, const int *color, int c, const int *pos, 
     if (i < n && color[i] == c) rows[base + pos[i]] = i;
 }
 
-// Count, per color, the couplings a_ij (i != j) between rows of that color.
-__global__ void k_same_color_edges(int n, const int *rowptr, const int *col, const int *color,
-                                   int *cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int c = color[i], k = 0;
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) k += col[p] != i && color[col[p]] == c;
-    if (k) atomicAdd(&cnt[c], k);
+__global__ void k_iperm(int n, const int *order, int *iperm) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) iperm[order[t]] = t;
+}
+
+// Row lengths of the renumbered copy: row t is natural row order[t] (order ==
+// nullptr: identity), without its diagonal entry when skip_diag.
+__global__ void k_perm_count(int n, const int *order, const int *rowptr, const int *col,
+                             bool skip_diag, int *cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = order ? order[t] : t;
+    int c = rowptr[i + 1] - rowptr[i];
+    if (skip_diag)
+        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) c -= col[p] == i;
+    cnt[t] = c;
+}
+
+// Fill the renumbered copy; columns mapped through icol (nullptr: unchanged);
+// entries keep the natural (ascending-column) order of their row.
+__global__ void k_perm_fill(int n, const int *order, const int *rowptr, const int *col,
+                            const double *val, bool skip_diag, const int *icol, const int *nrow,
+                            int *ncol, double *nval) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = order ? order[t] : t;
+    int q = nrow[t];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+        int j = col[p];
+        if (skip_diag && j == i) continue;
+        ncol[q] = icol ? icol[j] : j;
+        nval[q] = val[p];
+        q++;
+    }
+}
+
+__global__ void k_perm_diag(int n, const int *order, const int *rowptr, const int *col,
+                            const double *val, double *diag, double *dinv) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int i = order[t];
+    double d = 0.0;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
+        if (col[p] == i) d = val[p];
+    diag[t] = d;
+    dinv[t] = 1.0 / d;
 }
 
 __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const double *val,
@@ -683,6 +721,14 @@ __global__ void __launch_bounds__(1024) k_dense_lu_inverse(int n, double *a, int
             x[i] = s / (d == 0.0 ? 1.0 : d);
         }
     }
+}
+
+// out (row-major) = in^T, n x n.
+__global__ void k_transpose_dense(int n, const double *in, double *out) {
+    long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (e >= (long)n * n) return;
+    int i = (int)(e / n), j = (int)(e % n);
+    out[e] = in[(size_t)j * n + i];
 }
 
 // ------------------------------------------------------------------ BILU(0)
@@ -975,6 +1021,34 @@ void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
     }
 }
 
+// dst = src with rows taken in `order` and columns mapped through icol.
+void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool skip_diag, DCsr &dst,
+              cudaStream_t s) {
+    int n = src.n;
+    DVec<int> cnt;
+    cnt.alloc(std::max(n, 1), s);
+    k_perm_count<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, skip_diag, cnt.p);
+    CK_LAUNCH();
+    dst.n = n;
+    dst.ncol = ncol;
+    dst.rowptr.alloc(n + 1, s);
+    exclusive_scan(cnt.p, dst.rowptr.p, n, s);
+    dst.nnz = read_int(dst.rowptr.p + n, s);
+    dst.col.alloc(std::max(dst.nnz, 1), s);
+    dst.val.alloc(std::max(dst.nnz, 1), s);
+    k_perm_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p, skip_diag,
+                                                      icol, dst.rowptr.p, dst.col.p, dst.val.p);
+    CK_LAUNCH();
+}
+
+// Lanes per row for a row length: the power of two >= the mean length, 4..32.
+int lanes_for(long nnz, int n) {
+    double avg = n ? (double)nnz / n : 1.0;
+    int g = 4;
+    while (g < 32 && g < avg) g <<= 1;
+    return g;
+}
+
 void copy_ints(DVec<int> &dst, const int *src, size_t n, cudaStream_t s) {
     dst.alloc(std::max<size_t>(n, 1), s);
     if (n) CK(cudaMemcpyAsync(dst.p, src, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
@@ -1041,8 +1115,9 @@ void build_preconditioner(cpr_handle *h) {
             diag.alloc(n, s);
             k_diagpos<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, diag.p);
             CK_LAUNCH();
-            L.dinv.alloc(n, s);
-            k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, diag.p, L.A.val.p, L.dinv.p, h->err.p);
+            DVec<double> dtmp;
+            dtmp.alloc(n, s);
+            k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, diag.p, L.A.val.p, dtmp.p, h->err.p);
             CK_LAUNCH();
             check_err(h, "zero diagonal on an AMG level");
         }
@@ -1125,17 +1200,6 @@ void build_preconditioner(cpr_handle *h) {
             Graph G = sym_union(Sc, s);
             L.ncolors = jp_color(h, G, 0, l, L.color);
             rows_by_color(h, n, L.color.p, L.ncolors, L.color_off, L.rows_by_color);
-            DVec<int> same;
-            same.alloc(L.ncolors, s);
-            same.zero();
-            k_same_color_edges<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.color.p,
-                                                                     same.p);
-            CK_LAUNCH();
-            std::vector<int> hs(L.ncolors);
-            CK(cudaMemcpyAsync(hs.data(), same.p, sizeof(int) * L.ncolors, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            L.color_coupled.assign(L.ncolors, 0);
-            for (int c = 0; c < L.ncolors; c++) L.color_coupled[c] = hs[c] != 0;
         }
         h->lev.emplace_back();
         h->lev[l + 1].A = std::move(Ac);
@@ -1155,9 +1219,13 @@ void build_preconditioner(cpr_handle *h) {
         h->cinv.alloc((size_t)n * n, s);
         k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
         CK_LAUNCH();
-        k_dense_lu_inverse<<<1, 1024, 0, s>>>(n, a.p, piv.p, h->cinv.p, h->err.p);
+        DVec<double> colmajor;
+        colmajor.alloc((size_t)n * n, s);
+        k_dense_lu_inverse<<<1, 1024, 0, s>>>(n, a.p, piv.p, colmajor.p, h->err.p);
         CK_LAUNCH();
         check_err(h, "singular coarsest matrix");
+        k_transpose_dense<<<grid_for((long)n * n, kBlock), kBlock, 0, s>>>(n, colmajor.p, h->cinv.p);
+        CK_LAUNCH();
     }
 
     // ---- second stage: multicolor BILU(0) ----
@@ -1203,7 +1271,36 @@ void build_preconditioner(cpr_handle *h) {
         CK_LAUNCH();
     }
 
-    // ---- FP32 shadows and work vectors ----
+    // ---- solve copies in color order, FP32 shadows, work vectors ----
+    int L = (int)h->lev.size();
+    for (int l = 0; l < L; l++) {
+        Level &Lv = h->lev[l];
+        int n = Lv.A.n;
+        bool coarsest = l == L - 1;
+        if (!coarsest) {
+            Lv.iperm.alloc(n, s);
+            k_iperm<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.iperm.p);
+            CK_LAUNCH();
+        }
+    }
+    for (int l = 0; l < L - 1; l++) {
+        Level &Lv = h->lev[l];
+        Level &Nx = h->lev[l + 1];
+        int n = Lv.A.n;
+        const int *next_iperm = (l + 1 == L - 1) ? nullptr : Nx.iperm.p;
+        const int *next_order = (l + 1 == L - 1) ? nullptr : Nx.rows_by_color.p;
+        perm_csr(Lv.A, Lv.rows_by_color.p, Lv.iperm.p, n, true, Lv.Ao, s);
+        perm_csr(Lv.P, Lv.rows_by_color.p, next_iperm, Lv.P.ncol, false, Lv.Pp, s);
+        perm_csr(Lv.R, next_order, Lv.iperm.p, n, false, Lv.Rp, s);
+        Lv.diag.alloc(n, s);
+        Lv.dinv.alloc(n, s);
+        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
+                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p);
+        CK_LAUNCH();
+        Lv.gA = lanes_for(Lv.Ao.nnz, n);
+        Lv.gP = lanes_for(Lv.Pp.nnz, n);
+        Lv.gR = lanes_for(Lv.Rp.nnz, Lv.Rp.n);
+    }
     if (f32) {
         to_f32(h->pcol0, h->pcol0_32, s);
         to_f32(h->w, h->w32, s);
@@ -1211,28 +1308,32 @@ void build_preconditioner(cpr_handle *h) {
         to_f32(h->bilu.Uval, h->bilu.Uval32, s);
         to_f32(h->bilu.Dinv, h->bilu.Dinv32, s);
     }
-    for (size_t l = 0; l < h->lev.size(); l++) {
-        Level &L = h->lev[l];
-        int n = L.A.n;
-        L.x.alloc(n, s);
-        L.b.alloc(n, s);
-        L.r.alloc(n, s);
-        L.xs.alloc(n, s);
+    for (int l = 0; l < L; l++) {
+        Level &Lv = h->lev[l];
+        int n = Lv.A.n;
+        Lv.x.alloc(n, s);
+        Lv.b.alloc(n, s);
+        Lv.r.alloc(n, s);
+        Lv.s0.alloc(n, s);
+        Lv.s1.alloc(n, s);
         if (f32) {
-            L.xs32.alloc(n, s);
-            to_f32(L.A.val, L.Aval32, s);
-            to_f32(L.dinv, L.dinv32, s);
-            if (L.P.nnz) {
-                to_f32(L.P.val, L.Pval32, s);
-                to_f32(L.R.val, L.Rval32, s);
+            if (l < L - 1) {
+                to_f32(Lv.Ao.val, Lv.Aoval32, s);
+                to_f32(Lv.diag, Lv.diag32, s);
+                to_f32(Lv.dinv, Lv.dinv32, s);
+                to_f32(Lv.Pp.val, Lv.Ppval32, s);
+                to_f32(Lv.Rp.val, Lv.Rpval32, s);
             }
-            L.x32.alloc(n, s);
-            L.b32.alloc(n, s);
-            L.r32.alloc(n, s);
+            Lv.x32.alloc(n, s);
+            Lv.b32.alloc(n, s);
+            Lv.r32.alloc(n, s);
+            Lv.s0_32.alloc(n, s);
+            Lv.s1_32.alloc(n, s);
         }
     }
     CK(cudaStreamSynchronize(s));
     h->have_B = true;
+    h->epoch++;
 }
 
 }  // namespace cpr

@@ -18,7 +18,7 @@ namespace cpr {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kRedBlocks = 296;   // 2 CTAs per SM on 148 SMs
+constexpr int kRedBlocks = 1184;  // 8 CTAs of 256 threads per SM on 148 SMs
 constexpr int kDotGroup = 8;      // vectors per register group in the CGS dot kernel
 
 // Layout of the device scalar block (doubles) for restart length m.
@@ -38,15 +38,16 @@ struct ScalLayout {
     __host__ __device__ int size() const { return norm0() + 5; }
 };
 // Device ints: [0] step j, [1] done, [2] steps in this cycle, [3] breakdown.
-enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_COUNT = 8 };
+enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_CNT_DOT = 5, I_CNT_UPD = 6, I_COUNT = 8 };
 
 __device__ __forceinline__ int step_of(const int *jptr) { return jptr ? *jptr : 0; }
 
 // --------------------------------------------------------------- BSR SpMV
 
-// y = A x, or y = b - A x.  G lanes per block row; lane t of a row handles the
-// (block, row-of-block) items t, t+G, ...: 3 contiguous values of the block
-// times 3 contiguous values of x.
+// y = A x, or y = b - A x.  G lanes per block row; each lane takes whole 3x3
+// blocks (blocks lane, lane+G, ...) and accumulates its three row sums with
+// one FMA per stored value -- B300's FP64 rate, not its bandwidth, bounds
+// this kernel, so no value costs more than one FP64 instruction.
 template <int G>
 __global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ x_base,
@@ -59,17 +60,20 @@ __global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *_
     bool active = row < nb;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     if (active) {
-        int s = rowptr[row], e = rowptr[row + 1];
-        int items = 3 * (e - s);
-        for (int t = lane; t < items; t += G) {
-            int blk = t / 3, r = t - 3 * blk;
-            int p = s + blk;
-            const double *v = val + 9 * (size_t)p + 3 * r;
+        int e = rowptr[row + 1];
+        for (int p = rowptr[row] + lane; p < e; p += G) {
+            const double *v = val + 9 * (size_t)p;
             const double *xj = x + 3 * (size_t)col[p];
-            double d = v[0] * xj[0] + v[1] * xj[1] + v[2] * xj[2];
-            if (r == 0) a0 += d;
-            else if (r == 1) a1 += d;
-            else a2 += d;
+            double x0 = xj[0], x1 = xj[1], x2 = xj[2];
+            a0 = fma(v[0], x0, a0);
+            a0 = fma(v[1], x1, a0);
+            a0 = fma(v[2], x2, a0);
+            a1 = fma(v[3], x0, a1);
+            a1 = fma(v[4], x1, a1);
+            a1 = fma(v[5], x2, a1);
+            a2 = fma(v[6], x0, a2);
+            a2 = fma(v[7], x1, a2);
+            a2 = fma(v[8], x2, a2);
         }
     }
 #pragma unroll
@@ -94,19 +98,22 @@ __global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *_
 
 // --------------------------------------------------- restriction / prolongation
 
-// r_P[i] = w_i . v_i (Pi_P^T with decoupling weights); v = v_base + j * ld.
+// r_P = Pi_P^T v with decoupling weights: r_P[t] = w_i . v_i for block row
+// i = order[t] (order: level 0's color order, nullptr = identity); v = v_base + j*ld.
 template <class T>
-__global__ void k_restrict(int nb, const double *v_base, long ld, const int *jptr, const T *w,
-                           T *rp, const int *done) {
+__global__ void k_restrict(int nb, const int *order, const double *v_base, long ld, const int *jptr,
+                           const T *w, T *rp, const int *done) {
     if (done && *done) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    int i = order ? order[t] : t;
     const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
-    rp[i] = (w[3 * i] * (T)v[0] + w[3 * i + 1] * (T)v[1]) + w[3 * i + 2] * (T)v[2];
+    rp[t] = (w[3 * i] * (T)v[0] + w[3 * i + 1] * (T)v[1]) + w[3 * i + 2] * (T)v[2];
 }
 
 // Second residual of Alg. 1: r = v - A z with z = Pi_P e_P, so only column 0 of
-// every block (the frozen copy c0) takes part.  G lanes per block row.
+// every block (the frozen copy c0, 3 values per block) takes part.  G lanes
+// per block row, whole blocks per lane, one FMA per stored value.
 template <class T, int G>
 __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
                                 const T *__restrict__ c0, const T *__restrict__ ep,
@@ -118,15 +125,13 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
     bool active = row < nb;
     T a0 = 0, a1 = 0, a2 = 0;
     if (active) {
-        int s = rowptr[row], e = rowptr[row + 1];
-        int items = 3 * (e - s);
-        for (int t = lane; t < items; t += G) {
-            int blk = t / 3, rr = t - 3 * blk;
-            int p = s + blk;
-            T d = c0[3 * (size_t)p + rr] * ep[col[p]];
-            if (rr == 0) a0 += d;
-            else if (rr == 1) a1 += d;
-            else a2 += d;
+        int e = rowptr[row + 1];
+        for (int p = rowptr[row] + lane; p < e; p += G) {
+            T ej = ep[col[p]];
+            const T *c = c0 + 3 * (size_t)p;
+            a0 = fma(c[0], ej, a0);
+            a1 = fma(c[1], ej, a1);
+            a2 = fma(c[2], ej, a2);
         }
     }
 #pragma unroll
@@ -144,82 +149,121 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
 }
 
 // ------------------------------------------------------ multi-color GS (Alg. 6)
+//
+// Levels are renumbered so that each color is a contiguous row range.  A
+// color's rows relax Jacobi-style: their new values go to a staging buffer
+// (s0/s1, alternating), every x_j is read as of the start of the color, and the
+// next kernel commits the staged range into x while reading that range from
+// the staging buffer ("pending" range [p0, p1)).  G lanes share a row.
 
-// First color of a sweep from x = 0: every neighbour is still zero.
 template <class T>
-__global__ void k_mcgs_first(const int *rows, int cnt, const T *b, const T *dinv, T *x,
-                             const int *done) {
+__device__ __forceinline__ T group_sum(T v, int G) {
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ T xval(const T *x, const T *sp, int p0, int p1, int j) {
+    return (j >= p0 && j < p1) ? sp[j] : x[j];
+}
+
+// First color of a sweep that starts from x = 0: the staged rows get b/a_ii,
+// every other row of x is zeroed.
+template <class T>
+__global__ void k_smooth_first(int n, int c0, int c1, const T *b, const T *dinv, T *x, T *sc,
+                               const int *done) {
     if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = rows[t];
-    x[i] = b[i] * dinv[i];
+    if (t >= n) return;
+    if (t >= c0 && t < c1) sc[t] = b[t] * dinv[t];
+    else x[t] = (T)0;
 }
 
-// Rows of one color: x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii, every x_j
-// as of the start of the color (Jacobi within a color).  The new values go to
-// xout: x itself when no two rows of the color are coupled, otherwise a
-// staging vector that k_mcgs_commit copies back after all rows have read x.
-template <class T>
-__global__ void k_mcgs_color(const int *rows, int cnt, const int *__restrict__ rowptr,
-                             const int *__restrict__ col, const T *__restrict__ val, const T *b,
-                             const T *dinv, const T *x, T *xout, const int *done) {
+// Relax rows [c0, c1) into sc; commit the pending range [p0, p1) of sp into x.
+template <class T, int G>
+__global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__restrict__ rowptr,
+                               const int *__restrict__ col, const T *__restrict__ val,
+                               const T *__restrict__ b, const T *__restrict__ dinv, T *x,
+                               const T *sp, T *sc, const int *done) {
     if (done && *done) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = rows[t];
-    T s = b[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
-        int j = col[p];
-        if (j != i) s -= val[p] * x[j];
-    }
-    xout[i] = s * dinv[i];
-}
-
-template <class T>
-__global__ void k_mcgs_commit(const int *rows, int cnt, const T *xs, T *x, const int *done) {
-    if (done && *done) return;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = rows[t];
-    x[i] = xs[i];
-}
-
-// r = b - A x on a scalar CSR level.
-template <class T>
-__global__ void k_csr_resid(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                            const T *__restrict__ val, const T *b, const T *x, T *r,
-                            const int *done) {
-    if (done && *done) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T s = b[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) s -= val[p] * x[col[p]];
-    r[i] = s;
-}
-
-// y = M x (add = false) or y += M x (add = true) for a scalar CSR operator (R or P).
-template <class T>
-__global__ void k_csr_spmv(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-                           const T *__restrict__ val, const T *x, T *y, bool add, const int *done) {
-    if (done && *done) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nthr = (long)gridDim.x * blockDim.x;
+    for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
+    long g = tid / G;
+    int lane = (int)(tid % G);
+    bool active = g < c1 - c0;
+    int i = c0 + (int)g;
     T s = 0;
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * x[col[p]];
-    y[i] = add ? y[i] + s : s;
+    if (active)
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+    s = group_sum(s, G);
+    if (active && lane == 0) sc[i] = (b[i] - s) * dinv[i];
 }
 
-// Coarsest level: x = A_L^-1 b with the FP64 inverse (column-major).
+// r = b - A x with x's pending range read from sp (and committed into x).
+template <class T, int G>
+__global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ rowptr,
+                               const int *__restrict__ col, const T *__restrict__ val,
+                               const T *__restrict__ diag, const T *__restrict__ b, T *x, const T *sp,
+                               T *r, const int *done) {
+    if (done && *done) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nthr = (long)gridDim.x * blockDim.x;
+    long g = tid / G;
+    int lane = (int)(tid % G);
+    bool active = g < n;
+    int i = (int)g;
+    T s = 0;
+    if (active)
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+    s = group_sum(s, G);
+    if (active && lane == 0) r[i] = b[i] - s - diag[i] * xval(x, sp, p0, p1, i);
+    // commit after every read of this kernel's own rows is done is not
+    // guaranteed across CTAs, so readers above take the pending range from sp
+    for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
+}
+
+// y = M x (R: restriction) or y += M x (P: prolongation), with x's pending
+// range [p0, p1) read from sp.
+template <class T, int G>
+__global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                           const T *__restrict__ val, const T *x, const T *sp, int p0, int p1, T *y,
+                           bool add, const int *done) {
+    if (done && *done) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long g = tid / G;
+    int lane = (int)(tid % G);
+    bool active = g < n;
+    int i = (int)g;
+    T s = 0;
+    if (active)
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+    s = group_sum(s, G);
+    if (active && lane == 0) y[i] = add ? y[i] + s : s;
+}
+
+// Level 0's result in natural numbering: out[order[t]] = x[t] (pending range from sp).
+template <class T>
+__global__ void k_commit_natural(int n, const int *order, const T *x, const T *sp, int p0, int p1,
+                                 T *out, const int *done) {
+    if (done && *done) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    out[order[t]] = xval(x, sp, p0, p1, t);
+}
+
+// Coarsest level: x = A_L^-1 b, one warp per row of the row-major inverse.
 template <class T>
 __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b, T *x,
                                const int *done) {
     if (done && *done) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i = (int)(tid >> 5), lane = (int)(tid & 31);
     double s = 0.0;
-    for (int j = 0; j < n; j++) s += inv[(size_t)j * n + i] * (double)b[j];
-    x[i] = (T)s;
+    if (i < n)
+        for (int j = lane; j < n; j += 32) s += inv[(size_t)i * n + j] * (double)b[j];
+    s = group_sum(s, 32);
+    if (i < n && lane == 0) x[i] = (T)s;
 }
 
 // ------------------------------------------------------------- BILU(0) sweeps
@@ -288,6 +332,13 @@ __global__ void k_cast(long n, const double *a, T *b) {
         b[i] = (T)a[i];
 }
 
+// y[t] = (T) x[order[t]] (order == nullptr: identity).
+template <class T>
+__global__ void k_gather_cast(int n, const int *order, const double *x, T *y) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) y[t] = (T)x[order ? order[t] : t];
+}
+
 template <class T>
 __global__ void k_widen(long n, const T *a, double *b) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -331,9 +382,22 @@ __global__ void k_dot_partial(long n, const double *a, const double *b, double *
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// CGS dots of Alg. 2: part[blk * ldp + i] = sum_q V_i[q] w[q] for i = 0..j.
+// Last-block-done: returns true in the one block that arrives last, after
+// every block's partials are visible (the partial writes are fenced first).
+__device__ bool arrive_last(int *counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    return last;
+}
+
+// CGS dots of Alg. 2, h_ij = (w, v_i) for i = 0..j: per-block partials, then the
+// last block sums each column over the blocks in a fixed order (deterministic).
 __global__ void k_cgs_dots(long N, const double *__restrict__ V, const double *__restrict__ w,
-                           const int *jptr, double *part, int ldp, const int *done) {
+                           const int *jptr, double *part, int ldp, double *hcol, int *counter,
+                           const int *done) {
     if (*done) return;
     int nvec = *jptr + 1;
     for (int g0 = 0; g0 < nvec; g0 += kDotGroup) {
@@ -352,27 +416,29 @@ __global__ void k_cgs_dots(long N, const double *__restrict__ V, const double *_
             if (threadIdx.x == 0 && g0 + k < nvec) part[(size_t)blockIdx.x * ldp + g0 + k] = s;
         }
     }
+    if (!arrive_last(counter)) return;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < nvec; i += nw) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)b * ldp + i);
+        s = warp_sum(s);
+        if (lane == 0) hcol[i] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0;
 }
 
-// hcol[i] = sum over blocks of part[.][i] (fixed order).
-__global__ void k_reduce_cols(const double *part, int nblk, int ldp, const int *jptr, double *hcol,
-                              const int *done) {
-    if (*done) return;
-    int nvec = *jptr + 1;
-    int i = threadIdx.x;
-    if (i >= nvec) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += part[(size_t)b * ldp + i];
-    hcol[i] = s;
-}
-
-// w -= sum_{i<=j} h_i V_i, and per-block partial sums of ||w||^2 into part.
-__global__ void k_cgs_update(long N, const double *__restrict__ V, double *__restrict__ w,
-                             const int *jptr, const double *hcol, double *part, const int *done) {
-    if (*done) return;
+// w -= sum_{i<=j} h_i V_i with per-block partials of ||w||^2; the last block
+// sums them (fixed order) and performs the Givens step of column j (Saad's
+// form): apply the previous rotations, form the new one, update g, estimate
+// |g_{j+1}| / ||r_0|| and take the stop decision of Alg. 2.
+__global__ void k_cgs_update_givens(long N, const double *__restrict__ V, double *__restrict__ w,
+                                    double *part, int *counter, double *sc, int m, int *di) {
+    if (di[I_DONE]) return;
+    ScalLayout SL{m};
     __shared__ double sh[kMaxRestart + 1];
-    int nvec = *jptr + 1;
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = hcol[i];
+    int j = di[I_J];
+    int nvec = j + 1;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = sc[SL.hcol() + i];
     __syncthreads();
     double s = 0.0;
     for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
@@ -383,42 +449,41 @@ __global__ void k_cgs_update(long N, const double *__restrict__ V, double *__res
     }
     s = block_sum(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// One Givens step (Saad's form) for column j of the Hessenberg matrix, the
-// residual estimate |g_{j+1}| / ||r_0|| and the stop decision of Alg. 2.
-__global__ void k_givens(const double *part, int nblk, double *sc, int m, int *di) {
-    if (di[I_DONE]) return;
-    ScalLayout L{m};
-    int j = di[I_J];
+    if (!arrive_last(counter)) return;
+    if (threadIdx.x >= 32) return;
+    int lane = threadIdx.x;
     double hn2 = 0.0;
-    for (int b = 0; b < nblk; b++) hn2 += part[b];
+    for (int b = lane; b < (int)gridDim.x; b += 32) hn2 += __ldcg(part + b);
+    hn2 = warp_sum(hn2);
+    if (lane != 0) return;
+    *counter = 0;
+    double *sc_ = sc;
     double hn = sqrt(hn2);
-    for (int i = 0; i <= j; i++) sc[L.H(i, j)] = sc[L.hcol() + i];
-    sc[L.H(j + 1, j)] = hn;
+    for (int i = 0; i <= j; i++) sc_[SL.H(i, j)] = sc_[SL.hcol() + i];
+    sc_[SL.H(j + 1, j)] = hn;
     for (int i = 0; i < j; i++) {
-        double a = sc[L.H(i, j)], c = sc[L.H(i + 1, j)];
-        sc[L.H(i, j)] = sc[L.cs() + i] * a + sc[L.sn() + i] * c;
-        sc[L.H(i + 1, j)] = -sc[L.sn() + i] * a + sc[L.cs() + i] * c;
+        double a = sc_[SL.H(i, j)], c = sc_[SL.H(i + 1, j)];
+        sc_[SL.H(i, j)] = sc_[SL.cs() + i] * a + sc_[SL.sn() + i] * c;
+        sc_[SL.H(i + 1, j)] = -sc_[SL.sn() + i] * a + sc_[SL.cs() + i] * c;
     }
-    double a = sc[L.H(j, j)], c = sc[L.H(j + 1, j)];
+    double a = sc_[SL.H(j, j)], c = sc_[SL.H(j + 1, j)];
     double den = sqrt(a * a + c * c);
     double cj = den == 0.0 ? 1.0 : a / den, sj = den == 0.0 ? 0.0 : c / den;
-    sc[L.cs() + j] = cj;
-    sc[L.sn() + j] = sj;
-    sc[L.H(j, j)] = den;
-    sc[L.H(j + 1, j)] = 0.0;
-    double gj = sc[L.g() + j];
-    sc[L.g() + j + 1] = -sj * gj;
-    sc[L.g() + j] = cj * gj;
-    double est = fabs(sc[L.g() + j + 1]) / sc[L.norm0()];
-    sc[L.est()] = est;
-    sc[L.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
+    sc_[SL.cs() + j] = cj;
+    sc_[SL.sn() + j] = sj;
+    sc_[SL.H(j, j)] = den;
+    sc_[SL.H(j + 1, j)] = 0.0;
+    double gj = sc_[SL.g() + j];
+    sc_[SL.g() + j + 1] = -sj * gj;
+    sc_[SL.g() + j] = cj * gj;
+    double est = fabs(sc_[SL.g() + j + 1]) / sc_[SL.norm0()];
+    sc_[SL.est()] = est;
+    sc_[SL.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
     di[I_K] = j + 1;
     di[I_J] = j + 1;
     bool brk = !isfinite(hn) || !isfinite(est);
     if (brk) di[I_BREAK] = 1;
-    if (brk || hn == 0.0 || est < sc[L.rtol()] || j + 1 >= m) di[I_DONE] = 1;
+    if (brk || hn == 0.0 || est < sc_[SL.rtol()] || j + 1 >= m) di[I_DONE] = 1;
 }
 
 // V_{j+1} = w / h_{j+1,j} (after k_givens advanced the step index to j+1).
@@ -438,7 +503,9 @@ __global__ void k_cycle_start_scal(const double *part, int nblk, double *sc, int
                                    int first, double rtol) {
     ScalLayout L{m};
     double s = 0.0;
-    for (int b = 0; b < nblk; b++) s += part[b];
+    for (int b = threadIdx.x; b < nblk; b += 32) s += part[b];
+    s = warp_sum(s);
+    if (threadIdx.x != 0) return;
     double beta = sqrt(s);
     if (first) {
         sc[L.norm0()] = beta;
@@ -494,95 +561,146 @@ template <class T>
 struct Vals;
 template <>
 struct Vals<double> {
-    static const double *A(const Level &L) { return L.A.val.p; }
-    static const double *P(const Level &L) { return L.P.val.p; }
-    static const double *R(const Level &L) { return L.R.val.p; }
+    static const double *Ao(const Level &L) { return L.Ao.val.p; }
+    static const double *P(const Level &L) { return L.Pp.val.p; }
+    static const double *R(const Level &L) { return L.Rp.val.p; }
+    static const double *diag(const Level &L) { return L.diag.p; }
     static const double *dinv(const Level &L) { return L.dinv.p; }
     static double *x(Level &L) { return L.x.p; }
     static double *b(Level &L) { return L.b.p; }
     static double *r(Level &L) { return L.r.p; }
-    static double *xs(Level &L) { return L.xs.p; }
+    static double *s(Level &L, int k) { return k ? L.s1.p : L.s0.p; }
     static const double *w(const cpr_handle *h) { return h->w.p; }
     static const double *c0(const cpr_handle *h) { return h->pcol0.p; }
     static const double *Lv(const cpr_handle *h) { return h->bilu.Lval.p; }
     static const double *Uv(const cpr_handle *h) { return h->bilu.Uval.p; }
     static const double *Dv(const cpr_handle *h) { return h->bilu.Dinv.p; }
     static double *tmp(cpr_handle *h) { return h->t64a.p; }
+    static double *ep(cpr_handle *h) { return h->ep64.p; }
 };
 template <>
 struct Vals<float> {
-    static const float *A(const Level &L) { return L.Aval32.p; }
-    static const float *P(const Level &L) { return L.Pval32.p; }
-    static const float *R(const Level &L) { return L.Rval32.p; }
+    static const float *Ao(const Level &L) { return L.Aoval32.p; }
+    static const float *P(const Level &L) { return L.Ppval32.p; }
+    static const float *R(const Level &L) { return L.Rpval32.p; }
+    static const float *diag(const Level &L) { return L.diag32.p; }
     static const float *dinv(const Level &L) { return L.dinv32.p; }
     static float *x(Level &L) { return L.x32.p; }
     static float *b(Level &L) { return L.b32.p; }
     static float *r(Level &L) { return L.r32.p; }
-    static float *xs(Level &L) { return L.xs32.p; }
+    static float *s(Level &L, int k) { return k ? L.s1_32.p : L.s0_32.p; }
     static const float *w(const cpr_handle *h) { return h->w32.p; }
     static const float *c0(const cpr_handle *h) { return h->pcol0_32.p; }
     static const float *Lv(const cpr_handle *h) { return h->bilu.Lval32.p; }
     static const float *Uv(const cpr_handle *h) { return h->bilu.Uval32.p; }
     static const float *Dv(const cpr_handle *h) { return h->bilu.Dinv32.p; }
     static float *tmp(cpr_handle *h) { return h->t32a.p; }
+    static float *ep(cpr_handle *h) { return h->ep32.p; }
 };
 
+// The staged ("pending") range of a level: rows [p0, p1) whose newest values
+// are in staging buffer k rather than in x.
+struct Pending {
+    int p0 = 0, p1 = 0, k = 0;
+};
+
+template <int G, class F>
+void with_lanes(int g, F f);
+
+#define CPR_LANES_DISPATCH(g, CALL) \
+    switch (g) {                    \
+    case 4: { constexpr int G = 4; CALL; break; }   \
+    case 8: { constexpr int G = 8; CALL; break; }   \
+    case 16: { constexpr int G = 16; CALL; break; } \
+    default: { constexpr int G = 32; CALL; break; } \
+    }
+
+inline unsigned blocks_for(long threads) { return (unsigned)std::max<long>(1, (threads + kBlock - 1) / kBlock); }
+
 // One smoothing sweep over the colors of level L (ascending or descending).
+// From zero: the first color writes b/a_ii into staging and zeroes x.
 template <class T>
-void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, const int *done) {
+void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pending &pd,
+                const int *done) {
     cudaStream_t s = h->stream;
+    int n = L.A.n;
     for (int t = 0; t < L.ncolors; t++) {
         int c = descending ? L.ncolors - 1 - t : t;
-        int cnt = L.color_off[c + 1] - L.color_off[c];
-        if (!cnt) continue;
-        const int *rows = L.rows_by_color.p + L.color_off[c];
+        int c0 = L.color_off[c], c1 = L.color_off[c + 1];
+        int k = 1 - pd.k;
         if (from_zero && t == 0) {
-            k_mcgs_first<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, Vals<T>::b(L),
-                                                                     Vals<T>::dinv(L), Vals<T>::x(L), done);
+            k_smooth_first<T><<<blocks_for(n), kBlock, 0, s>>>(n, c0, c1, Vals<T>::b(L), Vals<T>::dinv(L),
+                                                               Vals<T>::x(L), Vals<T>::s(L, k), done);
+            CK_LAUNCH();
         } else {
-            bool coupled = L.color_coupled[c] != 0;
-            T *xout = coupled ? Vals<T>::xs(L) : Vals<T>::x(L);
-            k_mcgs_color<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, L.A.rowptr.p, L.A.col.p,
-                                                                     Vals<T>::A(L), Vals<T>::b(L),
-                                                                     Vals<T>::dinv(L), Vals<T>::x(L), xout,
-                                                                     done);
-            if (coupled) {
-                CK_LAUNCH();
-                k_mcgs_commit<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(rows, cnt, Vals<T>::xs(L),
-                                                                          Vals<T>::x(L), done);
-            }
+            long thr = std::max<long>((long)(c1 - c0) * L.gA, pd.p1 - pd.p0);
+            CPR_LANES_DISPATCH(L.gA, (k_smooth_color<T, G><<<blocks_for(thr), kBlock, 0, s>>>(
+                                         c0, c1, pd.p0, pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L),
+                                         Vals<T>::b(L), Vals<T>::dinv(L), Vals<T>::x(L),
+                                         Vals<T>::s(L, pd.k), Vals<T>::s(L, k), done)));
+            CK_LAUNCH();
         }
-        CK_LAUNCH();
+        pd = Pending{c0, c1, k};
     }
 }
 
-// V(pre, post) cycle on level l: x_l = B_l b_l from x_l = 0 (reading: pre-smoothing
-// with colors ascending, post-smoothing descending).
+// V(pre, post) cycle on level l from x_l = 0 (pre-smoothing colors ascending,
+// post-smoothing descending).  On return the level's result is x with the
+// range `out` still staged.
 template <class T>
-void vcycle(cpr_handle *h, int l, const int *done) {
+void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
     cudaStream_t s = h->stream;
     Level &L = h->lev[l];
     int n = L.A.n;
     if (l == (int)h->lev.size() - 1) {
-        k_coarse_solve<T><<<grid_for(n, 128), 128, 0, s>>>(n, h->cinv.p, Vals<T>::b(L), Vals<T>::x(L), done);
+        k_coarse_solve<T><<<blocks_for((long)n * 32), kBlock, 0, s>>>(n, h->cinv.p, Vals<T>::b(L),
+                                                                       Vals<T>::x(L), done);
         CK_LAUNCH();
+        out = Pending{};
         return;
     }
-    k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, Vals<T>::x(L), done);
+    Pending pd;
+    if (h->opt.pre == 0) {
+        k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, Vals<T>::x(L), done);
+        CK_LAUNCH();
+    }
+    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done);
+    long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
+    CPR_LANES_DISPATCH(L.gA, (k_resid_commit<T, G><<<blocks_for(thr), kBlock, 0, s>>>(
+                                 n, pd.p0, pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L),
+                                 Vals<T>::b(L), Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     CK_LAUNCH();
-    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, done);
-    k_csr_resid<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, Vals<T>::A(L),
-                                                          Vals<T>::b(L), Vals<T>::x(L), Vals<T>::r(L), done);
-    CK_LAUNCH();
+    pd = Pending{};
     Level &C = h->lev[l + 1];
-    k_csr_spmv<T><<<grid_for(L.R.n, kBlock), kBlock, 0, s>>>(L.R.n, L.R.rowptr.p, L.R.col.p, Vals<T>::R(L),
-                                                             Vals<T>::r(L), Vals<T>::b(C), false, done);
+    CPR_LANES_DISPATCH(L.gR, (k_transfer<T, G><<<blocks_for((long)L.Rp.n * L.gR), kBlock, 0, s>>>(
+                                 L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L),
+                                 0, 0, Vals<T>::b(C), false, done)));
     CK_LAUNCH();
-    vcycle<T>(h, l + 1, done);
-    k_csr_spmv<T><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.P.rowptr.p, L.P.col.p, Vals<T>::P(L),
-                                                         Vals<T>::x(C), Vals<T>::x(L), true, done);
+    Pending cp;
+    vcycle<T>(h, l + 1, cp, done);
+    CPR_LANES_DISPATCH(L.gP, (k_transfer<T, G><<<blocks_for((long)n * L.gP), kBlock, 0, s>>>(
+                                 n, L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
+                                 Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
     CK_LAUNCH();
-    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, done);
+    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done);
+    out = pd;
+}
+
+// e_P = B_P r_P on level 0: r_P arrives in level 0's b (color order); the
+// result leaves in natural numbering in ep.
+template <class T>
+void vcycle_top(cpr_handle *h, T *ep, const int *done) {
+    Level &L0 = h->lev[0];
+    Pending pd;
+    vcycle<T>(h, 0, pd, done);
+    int n = L0.A.n;
+    if (h->lev.size() == 1) {
+        CK(cudaMemcpyAsync(ep, Vals<T>::x(L0), sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
+        return;
+    }
+    k_commit_natural<T><<<blocks_for(n), kBlock, 0, h->stream>>>(n, L0.rows_by_color.p, Vals<T>::x(L0),
+                                                                  Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
+    CK_LAUNCH();
 }
 
 // BILU(0) solve in place on y (forward by ascending colors, backward by
@@ -609,7 +727,8 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     }
 }
 
-constexpr int kSpmvLanes = 8;
+constexpr int kSpmvLanes = 8;      // outer BSR SpMV (lanes per block row)
+constexpr int kResidLanes = 8;     // second residual
 
 template <class T>
 void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
@@ -617,24 +736,25 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     cudaStream_t s = h->stream;
     int nb = h->nb;
     Level &L0 = h->lev[0];
+    const int *order0 = h->lev.size() > 1 ? L0.rows_by_color.p : nullptr;
     // r_P = Pi_P^T v
-    k_restrict<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, v_base, v_ld, jptr, Vals<T>::w(h),
+    k_restrict<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
                                                           Vals<T>::b(L0), done);
     CK_LAUNCH();
-    // e_P = B_P r_P
+    // e_P = B_P r_P (natural numbering)
     prof_begin(h, CPR_PROF_VCYCLE);
-    vcycle<T>(h, 0, done);
+    vcycle_top<T>(h, Vals<T>::ep(h), done);
     prof_end(h);
     // r = v - A Pi_P e_P
-    long threads = (long)nb * kSpmvLanes;
+    long threads = (long)nb * kResidLanes;
     prof_begin(h, CPR_PROF_RESID2);
-    k_prolong_resid<T, kSpmvLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-        nb, h->rowptr.p, h->col.p, Vals<T>::c0(h), Vals<T>::x(L0), v_base, v_ld, jptr, Vals<T>::tmp(h), done);
+    k_prolong_resid<T, kResidLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        nb, h->rowptr.p, h->col.p, Vals<T>::c0(h), Vals<T>::ep(h), v_base, v_ld, jptr, Vals<T>::tmp(h), done);
     CK_LAUNCH();
     prof_end(h);
     // z = Pi_P e_P + (LU)^-1 r
     prof_begin(h, CPR_PROF_BILU);
-    bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::x(L0), z_base, z_ld, jptr, done);
+    bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::ep(h), z_base, z_ld, jptr, done);
     prof_end(h);
 }
 
@@ -682,9 +802,14 @@ void ensure_workspace(cpr_handle *h) {
         h->red.alloc((size_t)kRedBlocks * (kMaxRestart + 3), s);
         h->dint.alloc(I_COUNT, s);
         h->dint.zero();
+        h->epoch++;
     }
     if (h->opt.precond_fp32 && h->t32a.n != (size_t)N) h->t32a.alloc(N, s);
+    if (h->opt.precond_fp32 && h->ep32.n != (size_t)h->nb) h->ep32.alloc(h->nb, s);
+    if (!h->opt.precond_fp32 && h->ep64.n != (size_t)h->nb) h->ep64.alloc(h->nb, s);
     if (!h->pinned) CK(cudaMallocHost((void **)&h->pinned, 64 * sizeof(double)));
+    for (auto &e : h->step_done)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
@@ -696,17 +821,20 @@ void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, do
 void vcycle_apply(cpr_handle *h, const double *b, double *x) {
     cudaStream_t s = h->stream;
     Level &L0 = h->lev[0];
-    long n = L0.A.n;
+    int n = L0.A.n;
+    const int *order0 = h->lev.size() > 1 ? L0.rows_by_color.p : nullptr;
     if (h->opt.precond_fp32) {
-        k_cast<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, b, L0.b32.p);
-        vcycle<float>(h, 0, nullptr);
-        k_widen<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, L0.x32.p, x);
+        k_gather_cast<float><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b32.p);
+        CK_LAUNCH();
+        vcycle_top<float>(h, h->ep32.p, nullptr);
+        k_widen<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, h->ep32.p, x);
+        CK_LAUNCH();
     } else {
-        CK(cudaMemcpyAsync(L0.b.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        vcycle<double>(h, 0, nullptr);
-        CK(cudaMemcpyAsync(x, L0.x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        k_gather_cast<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b.p);
+        CK_LAUNCH();
+        vcycle_top<double>(h, h->ep64.p, nullptr);
+        CK(cudaMemcpyAsync(x, h->ep64.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     }
-    CK_LAUNCH();
 }
 
 void bilu_apply(cpr_handle *h, const double *r, double *z) {
@@ -720,6 +848,60 @@ void bilu_apply(cpr_handle *h, const double *r, double *z) {
         CK(cudaMemcpyAsync(h->t64a.p, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         bilu_solve<double>(h, h->t64a.p, nullptr, z, 0, nullptr, nullptr);
     }
+}
+
+// The launches of one Arnoldi step j (j read from device memory).
+void record_step(cpr_handle *h) {
+    cudaStream_t s = h->stream;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
+    ScalLayout SL{m};
+    int *di = h->dint.p;
+    double *sc = h->dscal.p;
+    const int *done = di + I_DONE;
+    int ldp = kMaxRestart + 2;
+    // z_j = B v_j ; w = A z_j
+    if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+    else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+    prof_begin(h, CPR_PROF_SPMV);
+    spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
+    prof_end(h);
+    // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||, Givens
+    prof_begin(h, CPR_PROF_CGS);
+    k_cgs_dots<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, sc + SL.hcol(),
+                                             di + I_CNT_DOT, done);
+    CK_LAUNCH();
+    k_cgs_update_givens<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, h->red.p + (size_t)kRedBlocks * ldp,
+                                                      di + I_CNT_UPD, sc, m, di);
+    CK_LAUNCH();
+    prof_end(h);
+    k_next_basis<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->wv.p, h->V.p, sc, m, di);
+    CK_LAUNCH();
+}
+
+// (Re)capture the two step graphs when B, the workspace or profiling changed.
+void ensure_step_graphs(cpr_handle *h) {
+    if (h->sg_epoch == h->epoch && h->sg_prof == h->prof && h->sg[0].exec && h->sg[1].exec) return;
+    destroy_step_graphs(h);
+    for (int k = 0; k < 2; k++) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = k;
+        try {
+            record_step(h);
+        } catch (...) {
+            h->capturing = -1;
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        h->capturing = -1;
+        CK(cudaStreamEndCapture(h->stream, &g));
+        h->sg[k].graph = g;
+        CK(cudaGraphInstantiate(&h->sg[k].exec, g, 0));
+    }
+    h->sg_epoch = h->epoch;
+    h->sg_prof = h->prof;
 }
 
 // Flexible GMRES(m), right-preconditioned with B (Alg. 2): CGS Arnoldi, Givens
@@ -741,7 +923,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
         // r = b - A x, beta = ||r||, V_0 = r / beta
         spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
         norm_partials(h, h->r.p, N);
-        k_cycle_start_scal<<<1, 1, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, cycle == 0, rtol);
+        k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, cycle == 0, rtol);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -762,38 +944,46 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
         k_scale_into<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->r.p, h->V.p, sc, m);
         CK_LAUNCH();
         cycles++;
-        int *pin_i = reinterpret_cast<int *>(h->pinned + 8);
-        for (int j = 0; j < m; j++) {
-            // z_j = B v_j ; w = A z_j
-            if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
-            else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
-            prof_begin(h, CPR_PROF_SPMV);
-            spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s,
-                        done);
-            prof_end(h);
-            prof_begin(h, CPR_PROF_CGS);
-            // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||
-            k_cgs_dots<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, done);
-            CK_LAUNCH();
-            k_reduce_cols<<<1, 128, 0, s>>>(h->red.p, kRedBlocks, ldp, di + I_J, sc + SL.hcol(), done);
-            CK_LAUNCH();
-            k_cgs_update<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, sc + SL.hcol(),
-                                                       h->red.p + (size_t)kRedBlocks * ldp, done);
-            CK_LAUNCH();
-            prof_end(h);
-            k_givens<<<1, 1, 0, s>>>(h->red.p + (size_t)kRedBlocks * ldp, kRedBlocks, sc, m, di);
-            CK_LAUNCH();
-            k_next_basis<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->wv.p, h->V.p, sc, m, di);
-            CK_LAUNCH();
-            CK(cudaMemcpyAsync(pin_i, di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            iters++;
-            if (pin_i[I_BREAK]) {
-                rc = CPR_ERR_BREAKDOWN;
-                break;
+        ensure_step_graphs(h);
+        int *pin = reinterpret_cast<int *>(h->pinned + 8);   // two slots of 4 ints
+        int launched = 0, steps = 0;
+        bool stop = false;
+        // Step j's graph is launched before the host reads step j-1's flags;
+        // a step launched after convergence finds `done` set and does nothing.
+        auto check = [&](int step) {
+            const int *f = pin + 4 * (step & 1);
+            bool real = f[I_K] == step + 1;
+            if (real) {
+                steps = step + 1;
+                if (h->prof) prof_collect_graph(h, step & 1);
             }
-            if (pin_i[I_DONE]) break;
+            if (f[I_BREAK]) {
+                rc = CPR_ERR_BREAKDOWN;
+                stop = true;
+            } else if (f[I_DONE]) {
+                stop = true;
+            }
+        };
+        for (int j = 0; j < m && !stop; j++) {
+            CK(cudaGraphLaunch(h->sg[j & 1].exec, s));
+            CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(h->step_done[j & 1], s));
+            launched = j + 1;
+            if (j >= 1) {
+                CK(cudaEventSynchronize(h->step_done[(j - 1) & 1]));
+                check(j - 1);
+            }
         }
+        CK(cudaStreamSynchronize(s));
+        if (!stop) check(launched - 1);
+        else if (launched - 1 >= steps && rc != CPR_ERR_BREAKDOWN) {
+            const int *f = pin + 4 * ((launched - 1) & 1);
+            if (f[I_K] == launched) {
+                steps = launched;
+                if (h->prof) prof_collect_graph(h, (launched - 1) & 1);
+            }
+        }
+        iters += steps;
         if (rc == CPR_ERR_BREAKDOWN) break;
         // y = H^-1 g, x += Z y
         k_solve_y<<<1, 1, 0, s>>>(sc, m, di);
@@ -805,7 +995,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
         // true residual after the last cycle
         spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
         norm_partials(h, h->r.p, N);
-        k_cycle_start_scal<<<1, 1, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, 0, rtol);
+        k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, 0, rtol);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
