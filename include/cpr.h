@@ -189,7 +189,9 @@ int cpr_copy_level(const cpr_handle *h, int level, int32_t *rowptr, int32_t *col
 int cpr_copy_weights(const cpr_handle *h, double *w);
 
 /* bcolor: nb block colors; lu: 9*nnzb factor blocks in A's pattern (L_ij below
- * the diagonal in (color, index) order, U_ij above it, U_ii^-1 on it). */
+ * the diagonal in (color, index) order, U_ij above it, U_ii^-1 on it).  In
+ * FP32-preconditioner mode the factorization itself runs in FP32 and lu
+ * receives those factors widened to FP64. */
 int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolors);
 
 /* ------------------------------------------------------------------------

@@ -457,9 +457,16 @@ int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolor
     return guarded([&] {
         cudaStream_t s = h->stream;
         if (bcolor) CK(cudaMemcpyAsync(bcolor, h->bilu.color.p, sizeof(int) * h->nb, cudaMemcpyDeviceToHost, s));
-        if (lu) CK(cudaMemcpyAsync(lu, h->bilu.lu.p, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyDeviceToHost, s));
+        std::vector<float> tmp;
+        if (lu && h->opt.precond_fp32) {
+            tmp.resize(9 * (size_t)h->nnzb);
+            CK(cudaMemcpyAsync(tmp.data(), h->bilu.lu32.p, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, s));
+        } else if (lu) {
+            CK(cudaMemcpyAsync(lu, h->bilu.lu.p, sizeof(double) * 9 * (size_t)h->nnzb, cudaMemcpyDeviceToHost, s));
+        }
         if (nbcolors) *nbcolors = h->bilu.ncolors;
         CK(cudaStreamSynchronize(s));
+        for (size_t k = 0; k < tmp.size(); k++) lu[k] = tmp[k];
         return CPR_OK;
     });
 }

@@ -1,5 +1,6 @@
 // Shared host utilities: errors, scans, small device reads.
 #include <cstdio>
+#include <mutex>
 
 #include "cpr_internal.cuh"
 
@@ -17,6 +18,25 @@ void check_cuda(cudaError_t e, const char *expr, const char *file, int line) {
     char buf[512];
     snprintf(buf, sizeof(buf), "%s failed at %s:%d: %s", expr, file, line, cudaGetErrorString(e));
     fail(code, buf);
+}
+
+cudaMemPool_t library_pool() {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(CPR_ERR_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CK(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t keep = UINT64_MAX;
+        CK(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    return pools[dev];
 }
 
 int grid_for(long n, int block, int cap) {

@@ -33,7 +33,12 @@ void count_launch();
 
 // ------------------------------------------------------------ device buffers
 
-// Stream-ordered device allocation (cudaMallocAsync pool); move-only.
+// The library's stream-ordered memory pool on the current device.  Its release
+// threshold is unlimited: memory freed by one setup is reused by the next
+// instead of going back to the driver at every synchronisation.
+cudaMemPool_t library_pool();
+
+// Stream-ordered device allocation from the library pool; move-only.
 template <class T>
 struct DVec {
     T *p = nullptr;
@@ -60,7 +65,7 @@ struct DVec {
         s = stream;
         n = count;
         if (count) {
-            cudaError_t e = cudaMallocAsync((void **)&p, count * sizeof(T), stream);
+            cudaError_t e = cudaMallocFromPoolAsync((void **)&p, count * sizeof(T), library_pool(), stream);
             if (e == cudaErrorMemoryAllocation) {
                 cudaGetLastError();
                 p = nullptr;
@@ -114,7 +119,8 @@ struct Bilu {
     int ncolors = 0;
     std::vector<int> color_off;
     DVec<int> rows_by_color;
-    DVec<double> lu;               // factor array in A's pattern (inspection)
+    DVec<double> lu;               // factor array in A's pattern (FP64 mode)
+    DVec<float> lu32;              // factor array in A's pattern (FP32 mode: factored in FP32)
     DVec<int> Lrowptr, Lcol, Urowptr, Ucol;
     DVec<double> Lval, Uval, Dinv;
     DVec<float> Lval32, Uval32, Dinv32;

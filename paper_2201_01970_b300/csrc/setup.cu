@@ -12,7 +12,11 @@
 // every decision of a round reads the state at the start of the round.
 #include <algorithm>
 #include <climits>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <type_traits>
 
 #include "cpr_internal.cuh"
 
@@ -211,11 +215,47 @@ __global__ void k_scatter_t(int n, const int *rowptr, const int *col, const doub
     }
 }
 
-// Sort each row by column (insertion sort; rows of transposes are short).
+// Sort each row by column: rows of up to 32 entries in registers, longer
+// rows by insertion sort in place (rows of transposes are short).
+constexpr int kRegSort = 32;
 __global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
+    int L = b - a;
+    if (L <= 1) return;
+    if (L <= kRegSort) {
+        int c[kRegSort];
+        double v[kRegSort];
+#pragma unroll
+        for (int k = 0; k < kRegSort; k++)
+            if (k < L) {
+                c[k] = col[a + k];
+                v[k] = val ? val[a + k] : 0.0;
+            }
+        // odd-even transposition sort over the first L entries
+        for (int pass = 0; pass < L; pass++) {
+#pragma unroll
+            for (int k = 0; k + 1 < kRegSort; k++) {
+                if ((k & 1) != (pass & 1) || k + 1 >= L) continue;
+                if (c[k] > c[k + 1]) {
+                    int tc = c[k];
+                    c[k] = c[k + 1];
+                    c[k + 1] = tc;
+                    double tv = v[k];
+                    v[k] = v[k + 1];
+                    v[k + 1] = tv;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRegSort; k++)
+            if (k < L) {
+                col[a + k] = c[k];
+                if (val) val[a + k] = v[k];
+            }
+        return;
+    }
     for (int p = a + 1; p < b; p++) {
         int c = col[p];
         double v = val ? val[p] : 0.0;
@@ -254,17 +294,17 @@ __global__ void k_union(int n, const int *sr, const int *sc, const int *tr, cons
 // ------------------------------------------------------------ Jones-Plassmann
 
 constexpr unsigned long long kUncolored = ~0ull;
+constexpr int kSmallLevel = 4096;    // levels up to this size run their rounds in one CTA
 
-// One JP round r.  A vertex uncolored at the start of the round (never colored,
-// or colored in this very round by someone else) whose key (degree, hash,
-// index) beats every neighbour uncolored at the start of the round takes the
-// smallest color not held by a neighbour colored in an earlier round.  state
-// packs (round << 32 | color) into one 64-bit word, written in one store.
-__global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hbase,
-                           unsigned long long *state, unsigned r, int *remaining, int *maxcolor) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (state[i] != kUncolored) return;
+// One JP round r for vertex i.  A vertex uncolored at the start of the round
+// (never colored, or colored in this very round by someone else) whose key
+// (degree, hash, index) beats every neighbour uncolored at the start of the
+// round takes the smallest color not held by a neighbour colored in an
+// earlier round.  state packs (round << 32 | color) into one 64-bit word,
+// written in one store.  Returns the color taken, or -1.
+__device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase,
+                         unsigned long long *state, unsigned r) {
+    if (state[i] != kUncolored) return -1;
     int a = grow[i], b = grow[i + 1];
     int di = b - a;
     uint32_t hi = fmix32((uint32_t)i ^ hbase);
@@ -276,7 +316,7 @@ __global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hba
         bool unc = sj == kUncolored || (unsigned)(sj >> 32) == r;
         if (!unc) continue;
         int dj = grow[j + 1] - grow[j];
-        if (!key_greater(di, hi, i, dj, fmix32((uint32_t)j ^ hbase), j)) return;
+        if (!key_greater(di, hi, i, dj, fmix32((uint32_t)j ^ hbase), j)) return -1;
     }
     int c = 0;
     for (int base = 0;; base += 64) {
@@ -293,8 +333,45 @@ __global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hba
         }
     }
     state[i] = ((unsigned long long)r << 32) | (unsigned)c;
-    atomicSub(remaining, 1);
-    atomicMax(maxcolor, c);
+    return c;
+}
+
+__global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hbase,
+                           unsigned long long *state, unsigned r, int *remaining, int *maxcolor) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = jp_vertex(i, grow, gcol, hbase, state, r);
+    if (c >= 0) {
+        atomicSub(remaining, 1);
+        atomicMax(maxcolor, c);
+    }
+}
+
+// All JP rounds of a small graph in one CTA, rounds separated by barriers
+// (the same rounds as k_jp_round, without host round trips).
+__global__ void __launch_bounds__(1024) k_jp_small(int n, const int *grow, const int *gcol, uint32_t hbase,
+                                                   unsigned long long *state, int *maxcolor) {
+    __shared__ int rem;
+    __shared__ int mx;
+    if (threadIdx.x == 0) {
+        rem = n;
+        mx = 0;
+    }
+    __syncthreads();
+    for (unsigned r = 0; r < (unsigned)n + 8; r++) {
+        int left = rem;
+        __syncthreads();
+        if (left == 0) break;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = jp_vertex(i, grow, gcol, hbase, state, r);
+            if (c >= 0) {
+                atomicSub(&rem, 1);
+                atomicMax(&mx, c);
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *maxcolor = mx;
 }
 
 __global__ void k_state_to_color(int n, const unsigned long long *state, int *color) {
@@ -314,12 +391,9 @@ __global__ void k_pmis_init(int n, const int *sr, const int *tr, int *cf, int *u
 
 // An undecided point whose key (lambda = |S^T_i|, hash, index) beats every
 // undecided point of S_i u S^T_i is selected (cf is not written in this pass).
-__global__ void k_pmis_select(int n, const int *sr, const int *sc, const int *tr, const int *tc,
-                              uint32_t hbase, const int *cf, int *sel) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    sel[i] = 0;
-    if (cf[i] != -1) return;
+__device__ int pmis_select(int i, const int *sr, const int *sc, const int *tr, const int *tc,
+                           uint32_t hbase, const int *cf) {
+    if (cf[i] != -1) return 0;
     int li = tr[i + 1] - tr[i];
     uint32_t hi = fmix32((uint32_t)i ^ hbase);
     for (int pass = 0; pass < 2; pass++) {
@@ -329,31 +403,59 @@ __global__ void k_pmis_select(int n, const int *sr, const int *sc, const int *tr
             int j = Cc[p];
             if (cf[j] != -1) continue;
             int lj = tr[j + 1] - tr[j];
-            if (!key_greater(li, hi, i, lj, fmix32((uint32_t)j ^ hbase), j)) return;
+            if (!key_greater(li, hi, i, lj, fmix32((uint32_t)j ^ hbase), j)) return 0;
         }
     }
-    sel[i] = 1;
+    return 1;
 }
 
 // Selected points become C; undecided points with a C point in S_i become F.
-__global__ void k_pmis_commit(int n, const int *sr, const int *sc, int *cf, const int *sel,
-                              int *undecided) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Returns 1 if point i was decided in this call.
+__device__ int pmis_commit(int i, const int *sr, const int *sc, int *cf, const int *sel) {
     if (sel[i]) {
         cf[i] = 1;
-        atomicSub(undecided, 1);
-        return;
+        return 1;
     }
-    if (cf[i] != -1) return;
+    if (cf[i] != -1) return 0;
     volatile int *vcf = cf;
     for (int p = sr[i]; p < sr[i + 1]; p++) {
         int j = sc[p];
         if (sel[j] || vcf[j] == 1) {
             cf[i] = 0;
-            atomicSub(undecided, 1);
-            return;
+            return 1;
         }
+    }
+    return 0;
+}
+
+__global__ void k_pmis_select(int n, const int *sr, const int *sc, const int *tr, const int *tc,
+                              uint32_t hbase, const int *cf, int *sel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
+}
+
+__global__ void k_pmis_commit(int n, const int *sr, const int *sc, int *cf, const int *sel,
+                              int *undecided) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && pmis_commit(i, sr, sc, cf, sel)) atomicSub(undecided, 1);
+}
+
+// All PMIS rounds of a small level in one CTA (the same rounds as above).
+__global__ void __launch_bounds__(1024) k_pmis_small(int n, const int *sr, const int *sc, const int *tr,
+                                                     const int *tc, uint32_t hbase, int *cf, int *sel,
+                                                     const int *undecided0) {
+    __shared__ int und;
+    if (threadIdx.x == 0) und = *undecided0;
+    __syncthreads();
+    for (int round = 0; round < n + 8; round++) {
+        int left = und;
+        __syncthreads();
+        if (left == 0) break;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (pmis_commit(i, sr, sc, cf, sel)) atomicSub(&und, 1);
+        __syncthreads();
     }
 }
 
@@ -429,123 +531,190 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
     }
 }
 
-// -------------------------------------------------------------------- SpGEMM
 
-__global__ void k_spgemm_count(int n, const int *ar, const int *ac, const int *br, int *cnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    long c = 0;
-    for (int p = ar[i]; p < ar[i + 1]; p++) {
+// ------------------------------------------------- SpGEMM with per-warp hashing
+//
+// One warp per row of C = A B.  Symbolic: the row's candidate columns (B_k for
+// k in A_i) go into a shared-memory hash set.  Numeric: the warp extracts and
+// sorts the row's columns, then adds a_ik b_kJ into a shared accumulator with k
+// in ascending order (one k at a time, lanes over B_k's distinct columns), so
+// every C entry is summed in the same order as Gustavson's row-by-row product.
+// Rows with more than kHashMax distinct columns take an exact slow path.
+
+constexpr int kHashCap = 1024;     // hash slots per warp (power of two)
+constexpr int kHashMax = 512;      // distinct columns handled in shared memory
+constexpr int kHashWarps = 4;
+constexpr int kEmpty = -1;
+
+// Insert every candidate column of row i into a table of *cap slots (sized
+// from the row's candidate count, 32..kHashCap); returns the distinct count,
+// or kHashMax+1 when the row is too large for the shared path.
+__device__ int hash_row(int i, const int *ar, const int *ac, const int *br, const int *bc, int *tab,
+                        int *cnt, int lane, int *cap_out) {
+    int a = ar[i], b = ar[i + 1];
+    int cand = 0;
+    for (int p = a + lane; p < b; p += 32) {
         int k = ac[p];
-        c += br[k + 1] - br[k];
+        cand += br[k + 1] - br[k];
     }
-    cnt[i] = (int)min(c, (long)INT_MAX / 4);
-}
-
-__global__ void k_spgemm_fill(int n, const int *ar, const int *ac, const int *br, const int *bc,
-                              const int *off, int *cand) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int o = off[i];
-    for (int p = ar[i]; p < ar[i + 1]; p++) {
+    for (int sh = 16; sh > 0; sh >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, sh);
+    int cap = 32;
+    while (cap < kHashCap && cap < 2 * cand) cap <<= 1;
+    *cap_out = cap;
+    for (int t = lane; t < cap; t += 32) tab[t] = kEmpty;
+    if (lane == 0) *cnt = 0;
+    __syncwarp();
+    bool overflow = false;
+    int limit = min(kHashMax, cap / 2 + cap / 4);
+    for (int p = a + lane; p < b; p += 32) {
         int k = ac[p];
-        for (int q = br[k]; q < br[k + 1]; q++) cand[o++] = bc[q];
-    }
-}
-
-constexpr int kSortCap = 1024;
-constexpr int kSortWarps = 4;
-
-// One warp per row: sort the row's candidate columns and keep each once
-// (bitonic sort in shared memory, or repeated minimum selection for rows
-// longer than kSortCap).  Unique columns go to uout at the row's offset.
-__global__ void __launch_bounds__(kSortWarps * 32) k_sort_unique(int n, const int *off,
-                                                                 const int *cand, int *uout,
-                                                                 int *ucnt) {
-    __shared__ int sbuf[kSortWarps][kSortCap];
-    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    int row = blockIdx.x * kSortWarps + wl;
-    if (row >= n) return;
-    int a = off[row], L = off[row + 1] - a;
-    const int *d = cand + a;
-    int *o = uout + a;
-    int *buf = sbuf[wl];
-    unsigned lt = (1u << lane) - 1u;
-    int cnt = 0;
-    if (L <= kSortCap) {
-        int P = 1;
-        while (P < L) P <<= 1;
-        for (int k = lane; k < P; k += 32) buf[k] = k < L ? d[k] : INT_MAX;
-        __syncwarp();
-        for (int size = 2; size <= P; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = lane; t < P / 2; t += 32) {
-                    int x = (t / stride) * 2 * stride + (t % stride);
-                    int y = x + stride;
-                    bool up = (x & size) == 0;
-                    int u = buf[x], v = buf[y];
-                    if ((u > v) == up) {
-                        buf[x] = v;
-                        buf[y] = u;
-                    }
+        for (int q = br[k]; q < br[k + 1] && !overflow; q++) {
+            int J = bc[q];
+            unsigned slot = ((unsigned)J * 2654435761u) & (cap - 1);
+            for (int probe = 0; probe < cap; probe++) {
+                int prev = atomicCAS(&tab[slot], kEmpty, J);
+                if (prev == kEmpty) {
+                    if (atomicAdd(cnt, 1) >= limit) overflow = true;
+                    break;
                 }
-                __syncwarp();
+                if (prev == J) break;
+                slot = (slot + 1) & (cap - 1);
             }
-        for (int base = 0; base < L; base += 32) {
-            int k = base + lane;
-            int v = k < L ? buf[k] : INT_MAX;
-            bool keep = k < L && (k == 0 || buf[k - 1] != v);
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            if (keep) o[cnt + __popc(mask & lt)] = v;
-            cnt += __popc(mask);
-        }
-    } else {
-        long last = -1;
-        for (;;) {
-            int m = INT_MAX;
-            for (int k = lane; k < L; k += 32) {
-                int v = d[k];
-                if (v > last && v < m) m = v;
-            }
-            for (int sh = 16; sh > 0; sh >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, sh));
-            if (m == INT_MAX) break;
-            if (lane == 0) o[cnt] = m;
-            cnt++;
-            last = m;
         }
     }
-    if (lane == 0) ucnt[row] = cnt;
+    __syncwarp();
+    int c = *cnt;
+    return c > limit ? kHashMax + 1 : c;
 }
 
-__global__ void k_gather_unique(int n, const int *off, const int *uout, const int *crow,
-                                int *ccol) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Exact slow path for a large row: the next distinct column above `last`,
+// found by one pass over all candidates (warp minimum).
+__device__ int next_col(int i, long last, const int *ar, const int *ac, const int *br, const int *bc,
+                        int lane) {
+    int m = INT_MAX;
+    for (int p = ar[i] + lane; p < ar[i + 1]; p += 32) {
+        int k = ac[p];
+        for (int q = br[k]; q < br[k + 1]; q++) {
+            int J = bc[q];
+            if (J > last && J < m) m = J;
+        }
+    }
+    for (int sh = 16; sh > 0; sh >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, sh));
+    return m;
+}
+
+__global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowcount(int n, const int *ar, const int *ac,
+                                                                     const int *br, const int *bc, int *ucnt) {
+    __shared__ int tab[kHashWarps][kHashCap];
+    __shared__ int cnt[kHashWarps];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int i = blockIdx.x * kHashWarps + wl;
     if (i >= n) return;
-    int a = off[i], c = crow[i], L = crow[i + 1] - c;
-    for (int k = 0; k < L; k++) ccol[c + k] = uout[a + k];
+    int cap;
+    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap);
+    if (c > kHashMax) {
+        c = 0;
+        for (long last = -1;;) {
+            int J = next_col(i, last, ar, ac, br, bc, lane);
+            if (J == INT_MAX) break;
+            c++;
+            last = J;
+        }
+    }
+    if (lane == 0) ucnt[i] = c;
 }
 
-// C = A B values, one warp per row, lanes over the row's entries: for entry
-// (i, J) the products a_ik b_kJ are added in ascending k, as Gustavson's
-// row-by-row accumulation adds them.
-__global__ void k_spgemm_numeric(int n, const int *ar, const int *ac, const double *av,
-                                 const int *br, const int *bc, const double *bv, const int *cr,
-                                 const int *cc, double *cv) {
-    int lane = threadIdx.x & 31;
-    long row = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= n) return;
-    int a = ar[row], b = ar[row + 1];
-    for (int e = cr[row] + lane; e < cr[row + 1]; e += 32) {
-        int J = cc[e];
-        double acc = 0.0;
-        for (int p = a; p < b; p++) {
-            int k = ac[p];
-            int lo = br[k], hi = br[k + 1];
-            int q = find_col(bc, lo, hi, J);
-            if (q < hi && bc[q] == J) acc = __dadd_rn(acc, __dmul_rn(av[p], bv[q]));
+__global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowfill(int n, const int *ar, const int *ac,
+                                                                    const double *av, const int *br,
+                                                                    const int *bc, const double *bv,
+                                                                    const int *cr, int *cc, double *cv) {
+    __shared__ int tab[kHashWarps][kHashCap];
+    __shared__ int keys[kHashWarps][kHashMax];
+    __shared__ double acc[kHashWarps][kHashMax];
+    __shared__ int cnt[kHashWarps];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int i = blockIdx.x * kHashWarps + wl;
+    if (i >= n) return;
+    unsigned lt = (1u << lane) - 1u;
+    int cap;
+    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap);
+    int base = cr[i];
+    int a = ar[i], b = ar[i + 1];
+    if (c > kHashMax) {
+        // slow path: columns by repeated minimum, values pulled per column
+        int e = 0;
+        for (long last = -1;;) {
+            int J = next_col(i, last, ar, ac, br, bc, lane);
+            if (J == INT_MAX) break;
+            if (lane == 0) cc[base + e] = J;
+            e++;
+            last = J;
         }
-        cv[e] = acc;
+        __syncwarp();
+        for (int q = base + lane; q < base + e; q += 32) {
+            int J = cc[q];
+            double s = 0.0;
+            for (int p = a; p < b; p++) {
+                int k = ac[p];
+                int lo = br[k], hi = br[k + 1];
+                int f = find_col(bc, lo, hi, J);
+                if (f < hi && bc[f] == J) s = __dadd_rn(s, __dmul_rn(av[p], bv[f]));
+            }
+            cv[q] = s;
+        }
+        return;
     }
+    // compact the hash table into keys[0..c), then sort (bitonic)
+    int *K = keys[wl];
+    int w = 0;
+    for (int t0 = 0; t0 < cap; t0 += 32) {
+        int v = tab[wl][t0 + lane];
+        bool keep = v != kEmpty;
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) K[w + __popc(m & lt)] = v;
+        w += __popc(m);
+    }
+    int P = 1;
+    while (P < c) P <<= 1;
+    for (int t = c + lane; t < P; t += 32) K[t] = INT_MAX;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < P / 2; t += 32) {
+                int x = (t / stride) * 2 * stride + (t % stride);
+                int y = x + stride;
+                bool up = (x & size) == 0;
+                int u = K[x], v = K[y];
+                if ((u > v) == up) {
+                    K[x] = v;
+                    K[y] = u;
+                }
+            }
+            __syncwarp();
+        }
+    double *S = acc[wl];
+    for (int t = lane; t < c; t += 32) {
+        S[t] = 0.0;
+        cc[base + t] = K[t];
+    }
+    __syncwarp();
+    // ascending k; the columns of one B row are distinct, so lanes never collide
+    for (int p = a; p < b; p++) {
+        int k = ac[p];
+        double av_p = av[p];
+        for (int q = br[k] + lane; q < br[k + 1]; q += 32) {
+            int J = bc[q];
+            int lo = 0, hi = c;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (K[mid] < J) lo = mid + 1;
+                else hi = mid;
+            }
+            S[lo] = __dadd_rn(S[lo], __dmul_rn(av_p, bv[q]));
+        }
+        __syncwarp();
+    }
+    for (int t = lane; t < c; t += 32) cv[base + t] = S[t];
 }
 
 // -------------------------------------------------------- level helpers
@@ -562,9 +731,22 @@ __global__ void k_check_diag(int n, const int *diag, const double *val, double *
     dinv[i] = 1.0 / d;
 }
 
-__global__ void k_color_hist(int n, const int *color, int *hist) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicAdd(&hist[color[i]], 1);
+// Per-color row counts: a block-local histogram in shared memory (colors
+// below 1024), then one global atomic per block and color.
+__global__ void k_color_hist(int n, int ncolors, const int *color, int *hist) {
+    __shared__ int sh[1024];
+    bool local = ncolors <= 1024;
+    if (local)
+        for (int c = threadIdx.x; c < ncolors; c += blockDim.x) sh[c] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (local) atomicAdd(&sh[color[i]], 1);
+        else atomicAdd(&hist[color[i]], 1);
+    }
+    __syncthreads();
+    if (local)
+        for (int c = threadIdx.x; c < ncolors; c += blockDim.x)
+            if (sh[c]) atomicAdd(&hist[c], sh[c]);
 }
 
 __global__ void k_flag_color(int n, const int *color, int c, int *flag) {
@@ -633,21 +815,29 @@ __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const d
     for (int p = rowptr[i]; p < rowptr[i + 1]; p++) a[(size_t)i * n + col[p]] = val[p];
 }
 
-// Dense LU with partial pivoting (largest |a|, lowest index on ties) of the
-// coarsest matrix, then its inverse column by column, stored column-major
-// (inv[j*n + i] = (A^-1)_ij).  One CTA.
-__global__ void __launch_bounds__(1024) k_dense_lu_inverse(int n, double *a, int *piv,
-                                                           double *inv, int *err) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
-    __shared__ int pivot_row;
-    int tid = threadIdx.x, nt = blockDim.x;
+// Dense LU with partial pivoting of the coarsest matrix (largest |a|, lowest
+// position on ties), one CTA.  Rows are never moved: perm[k] is the storage row
+// at position k.  The factors leave in position order in `lu` (row-major, row k
+// = position k).  The matrix is staged in shared memory when it fits.
+constexpr int kLuThreads = 256;
+__global__ void __launch_bounds__(kLuThreads) k_dense_lu(int n, const double *a_g, double *lu, int *perm,
+                                                         int use_smem, int *err) {
+    extern __shared__ double sm[];
+    __shared__ double wv[kLuThreads / 32];
+    __shared__ int wi[kLuThreads / 32];
+    __shared__ int prow;
+    __shared__ double pinv;
+    double *a = use_smem ? sm : lu;
+    int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    for (long e = tid; e < (long)n * n; e += nt) a[e] = a_g[e];
+    for (int i = tid; i < n; i += nt) perm[i] = i;
+    __syncthreads();
     for (int k = 0; k < n; k++) {
         double best = -1.0;
         int bi = INT_MAX;
         for (int i = k + tid; i < n; i += nt) {
-            double v = fabs(a[(size_t)i * n + k]);
-            if (v > best || (v == best && i < bi)) {
+            double v = fabs(a[(size_t)perm[i] * n + k]);
+            if (v > best) {
                 best = v;
                 bi = i;
             }
@@ -660,75 +850,79 @@ __global__ void __launch_bounds__(1024) k_dense_lu_inverse(int n, double *a, int
                 bi = oi;
             }
         }
-        if ((tid & 31) == 0) {
-            sv[tid >> 5] = best;
-            si[tid >> 5] = bi;
+        if (lane == 0) {
+            wv[wid] = best;
+            wi[wid] = bi;
         }
         __syncthreads();
         if (tid == 0) {
-            double bv = sv[0];
-            int bidx = si[0];
-            for (int w = 1; w < (nt + 31) / 32; w++)
-                if (sv[w] > bv || (sv[w] == bv && si[w] < bidx)) {
-                    bv = sv[w];
-                    bidx = si[w];
+            double bv = wv[0];
+            int b = wi[0];
+            for (int w = 1; w < nt / 32; w++)
+                if (wv[w] > bv || (wv[w] == bv && wi[w] < b)) {
+                    bv = wv[w];
+                    b = wi[w];
                 }
             if (!(bv > 0.0)) {
                 set_err(err, CPR_ERR_SINGULAR);
-                bidx = k;
+                b = k;
             }
-            pivot_row = bidx;
-            piv[k] = bidx;
+            int t = perm[k];
+            perm[k] = perm[b];
+            perm[b] = t;
+            prow = perm[k];
+            double pv = a[(size_t)prow * n + k];
+            pinv = pv == 0.0 ? 1.0 : 1.0 / pv;
         }
         __syncthreads();
-        int p = pivot_row;
-        if (p != k)
-            for (int j = tid; j < n; j += nt) {
-                double t = a[(size_t)k * n + j];
-                a[(size_t)k * n + j] = a[(size_t)p * n + j];
-                a[(size_t)p * n + j] = t;
-            }
-        __syncthreads();
-        double pk = a[(size_t)k * n + k];
-        if (pk == 0.0) pk = 1.0;
-        for (int i = k + 1 + tid; i < n; i += nt) a[(size_t)i * n + k] /= pk;
-        __syncthreads();
-        int m = n - k - 1;
-        for (long e = tid; e < (long)m * m; e += nt) {
-            int i = k + 1 + (int)(e / m), j = k + 1 + (int)(e % m);
-            a[(size_t)i * n + j] -= a[(size_t)i * n + k] * a[(size_t)k * n + j];
+        const double *pr = a + (size_t)prow * n;
+        for (int i = k + 1 + wid; i < n; i += nt / 32) {
+            double *ri = a + (size_t)perm[i] * n;
+            double l = ri[k] * pinv;
+            for (int j = k + 1 + lane; j < n; j += 32) ri[j] -= l * pr[j];
+            __syncwarp();
+            if (lane == 0) ri[k] = l;
         }
         __syncthreads();
     }
-    for (int j = tid; j < n; j += nt) {
-        double *x = inv + (size_t)j * n;
-        for (int i = 0; i < n; i++) x[i] = i == j ? 1.0 : 0.0;
-        for (int k = 0; k < n; k++) {
-            int p = piv[k];
-            double t = x[k];
-            x[k] = x[p];
-            x[p] = t;
-        }
-        for (int i = 0; i < n; i++) {
-            double s = x[i];
-            for (int q = 0; q < i; q++) s -= a[(size_t)i * n + q] * x[q];
-            x[i] = s;
-        }
-        for (int i = n - 1; i >= 0; i--) {
-            double s = x[i];
-            for (int q = i + 1; q < n; q++) s -= a[(size_t)i * n + q] * x[q];
-            double d = a[(size_t)i * n + i];
-            x[i] = s / (d == 0.0 ? 1.0 : d);
+    // factors in position order (in place is safe only through the staging copy)
+    if (use_smem) {
+        for (long e = tid; e < (long)n * n; e += nt) {
+            int k = (int)(e / n), q = (int)(e % n);
+            lu[e] = a[(size_t)perm[k] * n + q];
         }
     }
 }
 
-// out (row-major) = in^T, n x n.
-__global__ void k_transpose_dense(int n, const double *in, double *out) {
+// out[k*n + q] = in[perm[k]*n + q] (rows gathered into position order).
+__global__ void k_gather_rows(int n, const double *in, const int *perm, double *out) {
     long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (e >= (long)n * n) return;
-    int i = (int)(e / n), j = (int)(e % n);
-    out[e] = in[(size_t)j * n + i];
+    int k = (int)(e / n), q = (int)(e % n);
+    out[e] = in[(size_t)perm[k] * n + q];
+}
+
+// Column j of A^-1 from the LU factors (one CTA per column): x = P e_j
+// (x_k = 1 where perm[k] = j), then column-oriented forward (unit L) and
+// backward (U) substitution in shared memory; written row-major (inv[i*n + j]).
+__global__ void k_dense_inv_cols(int n, const double *lu, const int *perm, double *inv) {
+    extern __shared__ double x[];
+    int j = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < n; i += nt) x[i] = perm[i] == j ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < n; k++) {
+        double xk = x[k];
+        for (int i = k + 1 + tid; i < n; i += nt) x[i] -= lu[(size_t)i * n + k] * xk;
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        if (tid == 0) x[k] /= lu[(size_t)k * n + k];
+        __syncthreads();
+        double xk = x[k];
+        for (int i = tid; i < k; i += nt) x[i] -= lu[(size_t)i * n + k] * xk;
+        __syncthreads();
+    }
+    for (int i = tid; i < n; i += nt) inv[(size_t)i * n + j] = x[i];
 }
 
 // ------------------------------------------------------------------ BILU(0)
@@ -760,13 +954,47 @@ __device__ __forceinline__ bool mat3_inv_rn(const double *a, double *inv) {
     return true;
 }
 
+template <class T>
+__device__ __forceinline__ void mat3_mul_t(const T *a, const T *b, T *c);
+template <>
+__device__ __forceinline__ void mat3_mul_t<double>(const double *a, const double *b, double *c) {
+    mat3_mul_rn(a, b, c);
+}
+template <>
+__device__ __forceinline__ void mat3_mul_t<float>(const float *a, const float *b, float *c) {
+    for (int r = 0; r < 3; r++)
+        for (int s = 0; s < 3; s++) c[3 * r + s] = fmaf(a[3 * r + 2], b[6 + s], fmaf(a[3 * r + 1], b[3 + s], a[3 * r] * b[s]));
+}
+__device__ __forceinline__ double sub_t(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_t(float a, float b) { return a - b; }
+__device__ __forceinline__ bool mat3_inv_t(const double *a, double *inv) { return mat3_inv_rn(a, inv); }
+__device__ __forceinline__ bool mat3_inv_t(const float *a, float *inv) {
+    float c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    float det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    if (det == 0.0f || !isfinite(det)) return false;
+    float r = 1.0f / det;
+    inv[0] = c00 * r;
+    inv[1] = (a[2] * a[7] - a[1] * a[8]) * r;
+    inv[2] = (a[1] * a[5] - a[2] * a[4]) * r;
+    inv[3] = c01 * r;
+    inv[4] = (a[0] * a[8] - a[2] * a[6]) * r;
+    inv[5] = (a[2] * a[3] - a[0] * a[5]) * r;
+    inv[6] = c02 * r;
+    inv[7] = (a[1] * a[6] - a[0] * a[7]) * r;
+    inv[8] = (a[0] * a[4] - a[1] * a[3]) * r;
+    return true;
+}
+
 // Factor the block rows of one color; rows of lower colors are final.  For
 // row i, the entries k before i in (color, index) order are eliminated in that
 // order: L_ik = A_ik U_kk^-1, then A_ij -= L_ik U_kj for j after k in row k
 // that lies in row i's pattern.  Same-color rows are never adjacent (the
 // block coloring is at theta = 0), so "after k" means "higher color than k".
+// FP64: every operation rounded as the plain definition orders it; FP32 (the
+// FP32-preconditioner mode, whose B only ever uses FP32 factors): FMA allowed.
+template <class T>
 __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr, const int *col,
-                                    const int *color, const int *diag, double *lu, int *err) {
+                                    const int *color, const int *diag, T *lu, int *err) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     int i = rows[t];
@@ -789,24 +1017,24 @@ __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr,
         }
         if (best < 0) break;
         int k = bk;
-        double L[9];
-        mat3_mul_rn(lu + 9 * (size_t)best, lu + 9 * (size_t)diag[k], L);
+        T L[9];
+        mat3_mul_t<T>(lu + 9 * (size_t)best, lu + 9 * (size_t)diag[k], L);
         for (int e = 0; e < 9; e++) lu[9 * (size_t)best + e] = L[e];
         for (int q = rowptr[k]; q < rowptr[k + 1]; q++) {
             int j = col[q];
             if (j == k || color[j] <= color[k]) continue;
             int r = find_col(col, a, b, j);
             if (r >= b || col[r] != j) continue;
-            double P[9];
-            mat3_mul_rn(L, lu + 9 * (size_t)q, P);
-            for (int e = 0; e < 9; e++) lu[9 * (size_t)r + e] = __dsub_rn(lu[9 * (size_t)r + e], P[e]);
+            T P[9];
+            mat3_mul_t<T>(L, lu + 9 * (size_t)q, P);
+            for (int e = 0; e < 9; e++) lu[9 * (size_t)r + e] = sub_t(lu[9 * (size_t)r + e], P[e]);
         }
         last_c = bc;
         last_k = bk;
     }
-    double inv[9];
-    double *D = lu + 9 * (size_t)diag[i];
-    if (!mat3_inv_rn(D, inv)) {
+    T inv[9];
+    T *D = lu + 9 * (size_t)diag[i];
+    if (!mat3_inv_t(D, inv)) {
         set_err(err, CPR_ERR_SINGULAR);
         return;
     }
@@ -829,27 +1057,41 @@ __global__ void k_bilu_split_count(int nb, const int *rowptr, const int *col, co
     ucnt[i] = u;
 }
 
-__global__ void k_bilu_split_fill(int nb, const int *rowptr, const int *col, const int *color,
-                                  const double *lu, const int *lr, int *lc, double *lv,
-                                  const int *ur, int *uc, double *uv, double *dinv) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
-    int ql = lr[i], qu = ur[i], ci = color[i];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
-        int j = col[p];
-        const double *src = lu + 9 * (size_t)p;
-        double *dst;
-        if (j == i) {
-            dst = dinv + 9 * (size_t)i;
-        } else if (color[j] < ci) {
-            lc[ql] = j;
-            dst = lv + 9 * (size_t)ql++;
-        } else {
-            uc[qu] = j;
-            dst = uv + 9 * (size_t)qu++;
-        }
-        for (int e = 0; e < 9; e++) dst[e] = src[e];
+// One thread per block entry p (row found by binary search in rowptr): copy its
+// 9 values to L, U or D^-1; consecutive threads copy consecutive blocks.
+template <class T>
+__global__ void k_bilu_split_fill(long nnzb, int nb, const int *rowptr, const int *col,
+                                  const int *color, const T *lu, const int *lr, int *lc, T *lv,
+                                  const int *ur, int *uc, T *uv, T *dinv) {
+    long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (p >= nnzb) return;
+    int lo = 0, hi = nb;   // row i: rowptr[i] <= p < rowptr[i+1]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (rowptr[mid] <= p) lo = mid;
+        else hi = mid;
     }
+    int i = lo, j = col[p], ci = color[i];
+    T *dst;
+    if (j == i) {
+        dst = dinv + 9 * (size_t)i;
+    } else {
+        bool lower = color[j] < ci;
+        int k = 0;
+        for (int q = rowptr[i]; q < p; q++) {
+            int jq = col[q];
+            if (jq != i && (color[jq] < ci) == lower) k++;
+        }
+        if (lower) {
+            lc[lr[i] + k] = j;
+            dst = lv + 9 * (size_t)(lr[i] + k);
+        } else {
+            uc[ur[i] + k] = j;
+            dst = uv + 9 * (size_t)(ur[i] + k);
+        }
+    }
+    const T *src = lu + 9 * (size_t)p;
+    for (int e = 0; e < 9; e++) dst[e] = src[e];
 }
 
 __global__ void k_d2f(long n, const double *a, float *b) {
@@ -935,6 +1177,14 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
     int init[2] = {n, 0};
     CK(cudaMemcpyAsync(counters.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
     uint32_t hb = hash_base(h->opt.seed, salt, level);
+    if (n <= kSmallLevel) {
+        k_jp_small<<<1, 1024, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, counters.p + 1);
+        CK_LAUNCH();
+        color.alloc(n, s);
+        k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
+        CK_LAUNCH();
+        return read_int(counters.p + 1, s) + 1;
+    }
     unsigned r = 0;
     for (;;) {
         for (int k = 0; k < 4; k++, r++) {
@@ -958,7 +1208,7 @@ void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vec
     DVec<int> hist, flag, pos;
     hist.alloc(ncolors, s);
     hist.zero();
-    k_color_hist<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, color, hist.p);
+    k_color_hist<<<grid_for(n, kBlock, 148 * 4), kBlock, 0, s>>>(n, ncolors, color, hist.p);
     CK_LAUNCH();
     std::vector<int> hh(ncolors);
     CK(cudaMemcpyAsync(hh.data(), hist.p, sizeof(int) * ncolors, cudaMemcpyDeviceToHost, s));
@@ -980,36 +1230,21 @@ void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vec
 // C = A B (structural pattern, sorted; values in Gustavson order).
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     int n = A.n;
-    DVec<int> cnt, off, cand, uout, ucnt;
-    cnt.alloc(n, s);
-    k_spgemm_count<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, cnt.p);
+    DVec<int> ucnt;
+    ucnt.alloc(std::max(n, 1), s);
+    unsigned blocks = (unsigned)((n + kHashWarps - 1) / kHashWarps);
+    k_spgemm_rowcount<<<blocks, kHashWarps * 32, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, ucnt.p);
     CK_LAUNCH();
-    off.alloc(n + 1, s);
-    exclusive_scan(cnt.p, off.p, n, s);
-    int total = read_int(off.p + n, s);
-    if (total < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
-    cand.alloc(std::max(total, 1), s);
-    uout.alloc(std::max(total, 1), s);
-    k_spgemm_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
-                                                        off.p, cand.p);
-    CK_LAUNCH();
-    ucnt.alloc(n, s);
-    k_sort_unique<<<(n + kSortWarps - 1) / kSortWarps, kSortWarps * 32, 0, s>>>(n, off.p, cand.p,
-                                                                                uout.p, ucnt.p);
-    CK_LAUNCH();
-    cand.release();
     C.n = n;
     C.ncol = B.ncol;
     C.rowptr.alloc(n + 1, s);
     exclusive_scan(ucnt.p, C.rowptr.p, n, s);
     C.nnz = read_int(C.rowptr.p + n, s);
+    if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
-    k_gather_unique<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, off.p, uout.p, C.rowptr.p, C.col.p);
-    CK_LAUNCH();
-    long threads = (long)n * 32;
-    k_spgemm_numeric<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-        n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
+    k_spgemm_rowfill<<<blocks, kHashWarps * 32, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p,
+                                                       B.val.p, C.rowptr.p, C.col.p, C.val.p);
     CK_LAUNCH();
 }
 
@@ -1041,11 +1276,13 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
     CK_LAUNCH();
 }
 
-// Lanes per row for a row length: the power of two >= the mean length, 4..32.
+// Lanes per row for a mean row length: about four entries per lane (1..32
+// lanes), so short rows keep many rows, and several independent loads per
+// lane, in flight.
 int lanes_for(long nnz, int n) {
     double avg = n ? (double)nnz / n : 1.0;
-    int g = 4;
-    while (g < 32 && g < avg) g <<= 1;
+    int g = 1;
+    while (g < 32 && 4 * g < avg) g <<= 1;
     return g;
 }
 
@@ -1075,10 +1312,33 @@ void free_preconditioner(cpr_handle *h) {
     h->have_B = false;
 }
 
+// Wall-clock phase marks of one setup, printed to stderr when the environment
+// variable CPR_SETUP_TIMING is set (diagnostics only).
+struct PhaseClock {
+    bool on = getenv("CPR_SETUP_TIMING") != nullptr;
+    cudaStream_t s;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    std::string line;
+    void mark(const char *name) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        auto t = std::chrono::steady_clock::now();
+        char buf[96];
+        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(t - t0).count());
+        line += buf;
+        t0 = t;
+    }
+    ~PhaseClock() {
+        if (on) fprintf(stderr, "[cpr setup ms]%s\n", line.c_str());
+    }
+};
+
 // Build B from the handle's current A (Sec. 3.1; the setup lines of Alg. 6 per level).
 void build_preconditioner(cpr_handle *h) {
     free_preconditioner(h);
     cudaStream_t s = h->stream;
+    PhaseClock clk;
+    clk.s = s;
     const cpr_opts &o = h->opt;
     int nb = h->nb, nnzb = h->nnzb;
     bool f32 = o.precond_fp32 != 0;
@@ -1106,6 +1366,7 @@ void build_preconditioner(cpr_handle *h) {
         CK_LAUNCH();
     }
 
+    clk.mark("decouple");
     // ---- the AMG hierarchy ----
     for (int l = 0;; l++) {
         int n = h->lev[l].A.n;
@@ -1123,6 +1384,7 @@ void build_preconditioner(cpr_handle *h) {
         }
         if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
         Level &L = h->lev[l];
+        clk.mark("diag");
         // classical strength and PMIS
         Graph S = build_pattern(n, s, [&](const int *srow, int *out) {
             k_strength_rs<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
@@ -1140,7 +1402,11 @@ void build_preconditioner(cpr_handle *h) {
         CK_LAUNCH();
         uint32_t hb = hash_base(o.seed, 1, l);
         int rounds = 0;
-        while (read_int(und.p, s) > 0) {
+        if (n <= kSmallLevel) {
+            k_pmis_small<<<1, 1024, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, hb, L.cf.p, sel.p, und.p);
+            CK_LAUNCH();
+        }
+        while (n > kSmallLevel && read_int(und.p, s) > 0) {
             for (int k = 0; k < 3; k++, rounds++) {
                 k_pmis_select<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p,
                                                                     tcol.p, hb, L.cf.p, sel.p);
@@ -1151,6 +1417,7 @@ void build_preconditioner(cpr_handle *h) {
             }
             if (rounds > n + 8) fail(CPR_ERR_CUDA, "C/F splitting did not terminate");
         }
+        clk.mark("pmis");
         DVec<int> flag, cidx;
         flag.alloc(n, s);
         cidx.alloc(n + 1, s);
@@ -1185,11 +1452,13 @@ void build_preconditioner(cpr_handle *h) {
             L.R.nnz = L.P.nnz;
             transpose(n, nc, L.P.nnz, L.P.rowptr.p, L.P.col.p, L.P.val.p, L.R.rowptr, L.R.col, &L.R.val, s);
         }
+        clk.mark("interp");
         // Galerkin coarse matrix A_{l+1} = R (A P)
         DCsr AP, Ac;
         spgemm(L.A, L.P, AP, s);
         spgemm(L.R, AP, Ac, s);
         AP = DCsr{};
+        clk.mark("rap");
         // the smoother's coloring: Eq. 5.1 strength, symmetrised, JP
         {
             Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
@@ -1201,6 +1470,7 @@ void build_preconditioner(cpr_handle *h) {
             L.ncolors = jp_color(h, G, 0, l, L.color);
             rows_by_color(h, n, L.color.p, L.ncolors, L.color_off, L.rows_by_color);
         }
+        clk.mark("color");
         h->lev.emplace_back();
         h->lev[l + 1].A = std::move(Ac);
     }
@@ -1219,15 +1489,28 @@ void build_preconditioner(cpr_handle *h) {
         h->cinv.alloc((size_t)n * n, s);
         k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
         CK_LAUNCH();
-        DVec<double> colmajor;
-        colmajor.alloc((size_t)n * n, s);
-        k_dense_lu_inverse<<<1, 1024, 0, s>>>(n, a.p, piv.p, colmajor.p, h->err.p);
+        int use_smem = (size_t)n * n * sizeof(double) <= 200 * 1024 ? 1 : 0;
+        size_t smem = use_smem ? (size_t)n * n * sizeof(double) : 0;
+        if (use_smem) CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        DVec<double> lu;
+        lu.alloc((size_t)n * n, s);
+        if (!use_smem) {
+            // global path: factor a copy in storage order, then gather rows into position order
+            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+        }
+        k_dense_lu<<<1, kLuThreads, smem, s>>>(n, a.p, lu.p, piv.p, use_smem, h->err.p);
         CK_LAUNCH();
         check_err(h, "singular coarsest matrix");
-        k_transpose_dense<<<grid_for((long)n * n, kBlock), kBlock, 0, s>>>(n, colmajor.p, h->cinv.p);
+        if (!use_smem) {
+            k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, s>>>(n, lu.p, piv.p, a.p);
+            CK_LAUNCH();
+            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+        }
+        k_dense_inv_cols<<<n, 256, sizeof(double) * n, s>>>(n, lu.p, piv.p, h->cinv.p);
         CK_LAUNCH();
     }
 
+    clk.mark("coarse");
     // ---- second stage: multicolor BILU(0) ----
     {
         Bilu &B = h->bilu;
@@ -1236,19 +1519,11 @@ void build_preconditioner(cpr_handle *h) {
             CK_LAUNCH();
         });
         Graph G = sym_union(S, s);
+        clk.mark("bilu_graph");
         B.ncolors = jp_color(h, G, 2, 0, B.color);
+        clk.mark("bilu_jp");
         rows_by_color(h, nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color);
-        B.lu.alloc(9 * (size_t)nnzb, s);
-        CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
-        for (int c = 0; c < B.ncolors; c++) {
-            int cnt = B.color_off[c + 1] - B.color_off[c];
-            if (!cnt) continue;
-            k_bilu_factor_color<<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                                  h->rowptr.p, h->col.p, B.color.p,
-                                                                  bdiag.p, B.lu.p, h->err.p);
-            CK_LAUNCH();
-        }
-        check_err(h, "singular pivot block in BILU(0)");
+        clk.mark("bilu_rows");
         DVec<int> lcnt, ucnt;
         lcnt.alloc(nb, s);
         ucnt.alloc(nb, s);
@@ -1262,15 +1537,42 @@ void build_preconditioner(cpr_handle *h) {
         int nl = read_int(B.Lrowptr.p + nb, s), nu = read_int(B.Urowptr.p + nb, s);
         B.Lcol.alloc(std::max(nl, 1), s);
         B.Ucol.alloc(std::max(nu, 1), s);
-        B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
-        B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
-        B.Dinv.alloc(9 * (size_t)nb, s);
-        k_bilu_split_fill<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, B.color.p,
-                                                                 B.lu.p, B.Lrowptr.p, B.Lcol.p, B.Lval.p,
-                                                                 B.Urowptr.p, B.Ucol.p, B.Uval.p, B.Dinv.p);
-        CK_LAUNCH();
+        clk.mark("bilu_split_count");
+        auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
+            using T = std::remove_pointer_t<decltype(lu)>;
+            for (int c = 0; c < B.ncolors; c++) {
+                int cnt = B.color_off[c + 1] - B.color_off[c];
+                if (!cnt) continue;
+                k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
+                                                                         h->rowptr.p, h->col.p, B.color.p,
+                                                                         bdiag.p, lu, h->err.p);
+                CK_LAUNCH();
+            }
+            check_err(h, "singular pivot block in BILU(0)");
+            k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
+                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p, B.Ucol.p,
+                Uv, Dv);
+            CK_LAUNCH();
+        };
+        if (f32) {
+            B.lu32.alloc(9 * (size_t)nnzb, s);
+            k_d2f<<<grid_for(9L * nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(9L * nnzb, h->val.p, B.lu32.p);
+            CK_LAUNCH();
+            B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
+            B.Uval32.alloc(9 * (size_t)std::max(nu, 1), s);
+            B.Dinv32.alloc(9 * (size_t)nb, s);
+            factor_and_split(B.lu32.p, B.Lval32.p, B.Uval32.p, B.Dinv32.p);
+        } else {
+            B.lu.alloc(9 * (size_t)nnzb, s);
+            CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
+            B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
+            B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
+            B.Dinv.alloc(9 * (size_t)nb, s);
+            factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
+        }
     }
 
+    clk.mark("bilu");
     // ---- solve copies in color order, FP32 shadows, work vectors ----
     int L = (int)h->lev.size();
     for (int l = 0; l < L; l++) {
@@ -1304,9 +1606,6 @@ void build_preconditioner(cpr_handle *h) {
     if (f32) {
         to_f32(h->pcol0, h->pcol0_32, s);
         to_f32(h->w, h->w32, s);
-        to_f32(h->bilu.Lval, h->bilu.Lval32, s);
-        to_f32(h->bilu.Uval, h->bilu.Uval32, s);
-        to_f32(h->bilu.Dinv, h->bilu.Dinv32, s);
     }
     for (int l = 0; l < L; l++) {
         Level &Lv = h->lev[l];
@@ -1332,6 +1631,7 @@ void build_preconditioner(cpr_handle *h) {
         }
     }
     CK(cudaStreamSynchronize(s));
+    clk.mark("layout");
     h->have_B = true;
     h->epoch++;
 }

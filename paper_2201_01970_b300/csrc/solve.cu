@@ -162,6 +162,17 @@ __device__ __forceinline__ T group_sum(T v, int G) {
     return v;
 }
 
+// sum_{p in row i, strided by G from lane} val[p] * xv(col[p]), with the loads
+// of four entries issued before their products are accumulated.
+template <class T, int G, class XV>
+__device__ __forceinline__ T row_dot(const int *__restrict__ col, const T *__restrict__ val, int p0, int p1,
+                                     int lane, XV xv) {
+    T s = 0;
+#pragma unroll 4
+    for (int p = p0 + lane; p < p1; p += G) s += val[p] * xv(col[p]);
+    return s;
+}
+
 template <class T>
 __device__ __forceinline__ T xval(const T *x, const T *sp, int p0, int p1, int j) {
     return (j >= p0 && j < p1) ? sp[j] : x[j];
@@ -195,7 +206,7 @@ __global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__rest
     int i = c0 + (int)g;
     T s = 0;
     if (active)
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
     if (active && lane == 0) sc[i] = (b[i] - s) * dinv[i];
 }
@@ -215,7 +226,7 @@ __global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ ro
     int i = (int)g;
     T s = 0;
     if (active)
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
     if (active && lane == 0) r[i] = b[i] - s - diag[i] * xval(x, sp, p0, p1, i);
     // commit after every read of this kernel's own rows is done is not
@@ -237,7 +248,7 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
     int i = (int)g;
     T s = 0;
     if (active)
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += G) s += val[p] * xval(x, sp, p0, p1, col[p]);
+        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
     if (active && lane == 0) y[i] = add ? y[i] + s : s;
 }
@@ -266,6 +277,7 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b
     if (i < n && lane == 0) x[i] = (T)s;
 }
 
+
 // ------------------------------------------------------------- BILU(0) sweeps
 
 // Forward substitution for one color, in place: y_i = r_i - sum_{lower} L_ij y_j.
@@ -278,6 +290,7 @@ __global__ void k_bilu_fwd(const int *rows, int cnt, const int *__restrict__ lr,
     if (t >= cnt) return;
     int i = rows[t];
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+#pragma unroll 4
     for (int p = lr[i]; p < lr[i + 1]; p++) {
         const T *L = lv + 9 * (size_t)p;
         const T *yj = y + 3 * (size_t)lc[p];
@@ -303,6 +316,7 @@ __global__ void k_bilu_bwd(const int *rows, int cnt, const int *__restrict__ ur,
     if (t >= cnt) return;
     int i = rows[t];
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+#pragma unroll 4
     for (int p = ur[i]; p < ur[i + 1]; p++) {
         const T *U = uv + 9 * (size_t)p;
         const T *zj = y + 3 * (size_t)uc[p];
@@ -609,6 +623,8 @@ void with_lanes(int g, F f);
 
 #define CPR_LANES_DISPATCH(g, CALL) \
     switch (g) {                    \
+    case 1: { constexpr int G = 1; CALL; break; }   \
+    case 2: { constexpr int G = 2; CALL; break; }   \
     case 4: { constexpr int G = 4; CALL; break; }   \
     case 8: { constexpr int G = 8; CALL; break; }   \
     case 16: { constexpr int G = 16; CALL; break; } \
@@ -727,8 +743,8 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     }
 }
 
-constexpr int kSpmvLanes = 8;      // outer BSR SpMV (lanes per block row)
-constexpr int kResidLanes = 8;     // second residual
+constexpr int kSpmvLanes = 4;      // outer BSR SpMV (lanes per block row)
+constexpr int kResidLanes = 2;     // second residual
 
 template <class T>
 void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
