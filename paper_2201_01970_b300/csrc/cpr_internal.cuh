@@ -113,14 +113,19 @@ struct Level {
     DVec<float> x32, b32, r32, s0_32, s1_32;
 };
 
-// Split multicolor BILU(0) factors.
+// Multicolor BILU(0).  The factor array lu (lu32 in FP32 mode) is in A's
+// pattern and natural numbering (inspection).  The sweeps use block rows
+// renumbered into color order (position t holds natural row rows_by_color[t],
+// each color a contiguous range [color_off[c], color_off[c+1])): L (lower
+// colors), U (higher colors) and D^-1 with rows and columns in positions.
 struct Bilu {
     DVec<int> color;
     int ncolors = 0;
     std::vector<int> color_off;
-    DVec<int> rows_by_color;
-    DVec<double> lu;               // factor array in A's pattern (FP64 mode)
-    DVec<float> lu32;              // factor array in A's pattern (FP32 mode: factored in FP32)
+    DVec<int> rows_by_color;       // position -> natural block row
+    DVec<int> iperm;               // natural block row -> position
+    DVec<double> lu;
+    DVec<float> lu32;
     DVec<int> Lrowptr, Lcol, Urowptr, Ucol;
     DVec<double> Lval, Uval, Dinv;
     DVec<float> Lval32, Uval32, Dinv32;
@@ -138,8 +143,12 @@ struct cpr_handle {
     cpr::DVec<double> val;
     // --- the preconditioner B (frozen between setups) ---
     bool have_B = false;
-    cpr::DVec<double> pcol0;        // column 0 of every block of the A that B was built from
+    // column 0 of every block of the A that B was built from (Alg. 1 line 3),
+    // rows and columns in BILU positions
+    cpr::DVec<int> c0rowptr, c0col;
+    cpr::DVec<double> pcol0;
     cpr::DVec<float> pcol0_32;
+    cpr::DVec<int> ep_map;          // level-0 solve row -> BILU position (final V-cycle commit)
     cpr::DVec<double> w;            // decoupling weights, 3 per block row
     cpr::DVec<float> w32;
     std::vector<cpr::Level> lev;
@@ -154,7 +163,7 @@ struct cpr_handle {
     cpr::DVec<int> dint;            // device ints (step index, flags)
     cpr::DVec<float> t32a, t32b;    // FP32 vectors of length 3*nb inside B
     cpr::DVec<double> t64a;         // FP64 vector of length 3*nb inside B
-    cpr::DVec<double> ep64;         // e_P = B_P r_P in natural numbering
+    cpr::DVec<double> ep64;         // e_P = B_P r_P in BILU positions
     cpr::DVec<float> ep32;
     cpr::DVec<double> dev_b, dev_x; // device copies of host b / x
     double *pinned = nullptr;       // pinned host scalars

@@ -48,19 +48,25 @@ void *scratch_address() {
     return g_scratch_addr[dev];
 }
 
+// y (block rows in the factors' color order) <- r (natural order).
 template <class T>
-__global__ void k_load(long n, const double *r, T *y) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        y[i] = (T)r[i];
+__global__ void k_load(int nb, const int *order, const double *r, T *y) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const double *src = r + 3 * (size_t)order[t];
+    y[3 * (size_t)t] = (T)src[0];
+    y[3 * (size_t)t + 1] = (T)src[1];
+    y[3 * (size_t)t + 2] = (T)src[2];
 }
 
-// Forward substitution of one color on the scratch vector (as cpr_bilu_apply's).
+// Forward substitution of one color's positions [c0, c0 + cnt) on the scratch
+// vector (as cpr_bilu_apply's).
 template <class T>
-__global__ void k_fwd(const int *rows, int cnt, const int *__restrict__ lr, const int *__restrict__ lc,
+__global__ void k_fwd(int c0, int cnt, const int *__restrict__ lr, const int *__restrict__ lc,
                       const T *__restrict__ lv, T *y) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    int i = rows[t];
+    int i = c0 + t;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
     for (int p = lr[i]; p < lr[i + 1]; p++) {
         const T *L = lv + 9 * (size_t)p;
@@ -75,13 +81,14 @@ __global__ void k_fwd(const int *rows, int cnt, const int *__restrict__ lr, cons
     y[3 * (size_t)i + 2] = s2;
 }
 
-// Backward substitution of one color; writes z (FP64) as well.
+// Backward substitution of one color's positions; writes z (FP64, natural
+// block row order[i]) as well.
 template <class T>
-__global__ void k_bwd(const int *rows, int cnt, const int *__restrict__ ur, const int *__restrict__ uc,
-                      const T *__restrict__ uv, const T *__restrict__ dinv, T *y, double *z) {
+__global__ void k_bwd(int c0, int cnt, const int *__restrict__ ur, const int *__restrict__ uc,
+                      const T *__restrict__ uv, const T *__restrict__ dinv, T *y, const int *order, double *z) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    int i = rows[t];
+    int i = c0 + t;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
     for (int p = ur[i]; p < ur[i + 1]; p++) {
         const T *U = uv + 9 * (size_t)p;
@@ -98,32 +105,32 @@ __global__ void k_bwd(const int *rows, int cnt, const int *__restrict__ ur, cons
     y[3 * (size_t)i] = z0;
     y[3 * (size_t)i + 1] = z1;
     y[3 * (size_t)i + 2] = z2;
-    z[3 * (size_t)i] = (double)z0;
-    z[3 * (size_t)i + 1] = (double)z1;
-    z[3 * (size_t)i + 2] = (double)z2;
+    double *zi = z + 3 * (size_t)order[i];
+    zi[0] = (double)z0;
+    zi[1] = (double)z1;
+    zi[2] = (double)z2;
 }
 
 template <class T>
 void sweeps(cpr_handle *h, const double *r, double *z, T *y, const T *lv, const T *uv, const T *dv) {
     cudaStream_t s = h->stream;
     Bilu &B = h->bilu;
-    long N = 3L * h->nb;
+    int nb = h->nb;
     // every entry of y that the sweeps read is written here first, so no part
     // of the scratch has to start at zero
-    k_load<T><<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, r, y);
+    k_load<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, r, y);
     CK_LAUNCH();
     for (int c = 0; c < B.ncolors; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                         B.Lrowptr.p, B.Lcol.p, lv, y);
+        k_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p, lv, y);
         CK_LAUNCH();
     }
     for (int c = B.ncolors - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                         B.Urowptr.p, B.Ucol.p, uv, dv, y, z);
+        k_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p, uv, dv, y,
+                                                         B.rows_by_color.p, z);
         CK_LAUNCH();
     }
 }

@@ -113,19 +113,43 @@ __global__ void k_decouple(int nb, const int *diag, const double *val, int mode,
     w[3 * i + 2] = __ddiv_rn(c20, det);
 }
 
-// A_P[i][j] = w_i . A_ij e_1 on the block pattern; also the column-0 slices of A.
+// A_P[i][j] = w_i . A_ij e_1 on the block pattern.
 __global__ void k_pressure_matrix(int nb, const int *rowptr, const double *val, const double *w,
-                                  double *apval, double *pcol0) {
+                                  double *apval) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     double w0 = w[3 * i], w1 = w[3 * i + 1], w2 = w[3 * i + 2];
     for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
         const double *a = val + 9 * (size_t)p;
         apval[p] = __dadd_rn(__dadd_rn(__dmul_rn(w0, a[0]), __dmul_rn(w1, a[3])), __dmul_rn(w2, a[6]));
-        pcol0[3 * (size_t)p] = a[0];
-        pcol0[3 * (size_t)p + 1] = a[3];
-        pcol0[3 * (size_t)p + 2] = a[6];
     }
+}
+
+// Column 0 of every block of A (the copy B keeps for Alg. 1 line 3), with rows
+// taken in position order and columns renumbered to positions.  Count pass
+// (crow == nullptr: row lengths) or fill pass.
+__global__ void k_col0_perm(int nb, const int *order, const int *iperm, const int *rowptr, const int *col,
+                            const double *val, const int *crow, int *ccol, double *cval, int *cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    int i = order[t];
+    if (!crow) {
+        cnt[t] = rowptr[i + 1] - rowptr[i];
+        return;
+    }
+    int q = crow[t];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++, q++) {
+        const double *a = val + 9 * (size_t)p;
+        ccol[q] = iperm[col[p]];
+        cval[3 * (size_t)q] = a[0];
+        cval[3 * (size_t)q + 1] = a[3];
+        cval[3 * (size_t)q + 2] = a[6];
+    }
+}
+
+__global__ void k_compose(int n, const int *first, const int *second, int *out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = second[first ? first[t] : t];
 }
 
 // -------------------------------------------------------- strength (Eq. 5.1)
@@ -1041,11 +1065,12 @@ __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr,
     for (int e = 0; e < 9; e++) D[e] = inv[e];
 }
 
-// Split the factor array into L (lower colors), U (higher colors) and D^-1.
-__global__ void k_bilu_split_count(int nb, const int *rowptr, const int *col, const int *color,
-                                   int *lcnt, int *ucnt) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb) return;
+// Row lengths of L (lower colors) and U (higher colors) per position t.
+__global__ void k_bilu_split_count(int nb, const int *order, const int *rowptr, const int *col,
+                                   const int *color, int *lcnt, int *ucnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    int i = order[t];
     int l = 0, u = 0, ci = color[i];
     for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
         int j = col[p];
@@ -1053,16 +1078,17 @@ __global__ void k_bilu_split_count(int nb, const int *rowptr, const int *col, co
         if (color[j] < ci) l++;
         else u++;
     }
-    lcnt[i] = l;
-    ucnt[i] = u;
+    lcnt[t] = l;
+    ucnt[t] = u;
 }
 
-// One thread per block entry p (row found by binary search in rowptr): copy its
-// 9 values to L, U or D^-1; consecutive threads copy consecutive blocks.
+// One thread per block entry p of the natural factor array (its row found by
+// binary search in rowptr): copy its 9 values to L, U or D^-1 at the row's
+// position, with the column renumbered to its position.
 template <class T>
 __global__ void k_bilu_split_fill(long nnzb, int nb, const int *rowptr, const int *col,
-                                  const int *color, const T *lu, const int *lr, int *lc, T *lv,
-                                  const int *ur, int *uc, T *uv, T *dinv) {
+                                  const int *color, const int *iperm, const T *lu, const int *lr, int *lc,
+                                  T *lv, const int *ur, int *uc, T *uv, T *dinv) {
     long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (p >= nnzb) return;
     int lo = 0, hi = nb;   // row i: rowptr[i] <= p < rowptr[i+1]
@@ -1071,10 +1097,10 @@ __global__ void k_bilu_split_fill(long nnzb, int nb, const int *rowptr, const in
         if (rowptr[mid] <= p) lo = mid;
         else hi = mid;
     }
-    int i = lo, j = col[p], ci = color[i];
+    int i = lo, j = col[p], ci = color[i], t = iperm[i];
     T *dst;
     if (j == i) {
-        dst = dinv + 9 * (size_t)i;
+        dst = dinv + 9 * (size_t)t;
     } else {
         bool lower = color[j] < ci;
         int k = 0;
@@ -1083,11 +1109,11 @@ __global__ void k_bilu_split_fill(long nnzb, int nb, const int *rowptr, const in
             if (jq != i && (color[jq] < ci) == lower) k++;
         }
         if (lower) {
-            lc[lr[i] + k] = j;
-            dst = lv + 9 * (size_t)(lr[i] + k);
+            lc[lr[t] + k] = iperm[j];
+            dst = lv + 9 * (size_t)(lr[t] + k);
         } else {
-            uc[ur[i] + k] = j;
-            dst = uv + 9 * (size_t)(ur[i] + k);
+            uc[ur[t] + k] = iperm[j];
+            dst = uv + 9 * (size_t)(ur[t] + k);
         }
     }
     const T *src = lu + 9 * (size_t)p;
@@ -1304,6 +1330,9 @@ void free_preconditioner(cpr_handle *h) {
     h->lev.clear();
     h->pcol0.release();
     h->pcol0_32.release();
+    h->c0rowptr.release();
+    h->c0col.release();
+    h->ep_map.release();
     h->w.release();
     h->w32.release();
     h->cinv.release();
@@ -1360,9 +1389,8 @@ void build_preconditioner(cpr_handle *h) {
         copy_ints(L0.A.rowptr, h->rowptr.p, nb + 1, s);
         copy_ints(L0.A.col, h->col.p, nnzb, s);
         L0.A.val.alloc(nnzb, s);
-        h->pcol0.alloc(3 * (size_t)nnzb, s);
         k_pressure_matrix<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->val.p, h->w.p,
-                                                                 L0.A.val.p, h->pcol0.p);
+                                                                 L0.A.val.p);
         CK_LAUNCH();
     }
 
@@ -1524,11 +1552,14 @@ void build_preconditioner(cpr_handle *h) {
         clk.mark("bilu_jp");
         rows_by_color(h, nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color);
         clk.mark("bilu_rows");
+        B.iperm.alloc(nb, s);
+        k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
+        CK_LAUNCH();
         DVec<int> lcnt, ucnt;
         lcnt.alloc(nb, s);
         ucnt.alloc(nb, s);
-        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, B.color.p,
-                                                                  lcnt.p, ucnt.p);
+        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
+                                                                  B.color.p, lcnt.p, ucnt.p);
         CK_LAUNCH();
         B.Lrowptr.alloc(nb + 1, s);
         B.Urowptr.alloc(nb + 1, s);
@@ -1550,8 +1581,8 @@ void build_preconditioner(cpr_handle *h) {
             }
             check_err(h, "singular pivot block in BILU(0)");
             k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
-                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p, B.Ucol.p,
-                Uv, Dv);
+                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
+                B.Ucol.p, Uv, Dv);
             CK_LAUNCH();
         };
         if (f32) {
@@ -1570,8 +1601,20 @@ void build_preconditioner(cpr_handle *h) {
             B.Dinv.alloc(9 * (size_t)nb, s);
             factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
         }
+        // the frozen column-0 copy of A in positions
+        DVec<int> ccnt;
+        ccnt.alloc(nb, s);
+        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                           h->val.p, nullptr, nullptr, nullptr, ccnt.p);
+        CK_LAUNCH();
+        h->c0rowptr.alloc(nb + 1, s);
+        exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
+        h->c0col.alloc(nnzb, s);
+        h->pcol0.alloc(3 * (size_t)nnzb, s);
+        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                           h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
+        CK_LAUNCH();
     }
-
     clk.mark("bilu");
     // ---- solve copies in color order, FP32 shadows, work vectors ----
     int L = (int)h->lev.size();
@@ -1602,6 +1645,13 @@ void build_preconditioner(cpr_handle *h) {
         Lv.gA = lanes_for(Lv.Ao.nnz, n);
         Lv.gP = lanes_for(Lv.Pp.nnz, n);
         Lv.gR = lanes_for(Lv.Rp.nnz, Lv.Rp.n);
+    }
+    {
+        // final V-cycle commit: level-0 solve row -> BILU position
+        const int *order0 = L > 1 ? h->lev[0].rows_by_color.p : nullptr;
+        h->ep_map.alloc(nb, s);
+        k_compose<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, order0, h->bilu.iperm.p, h->ep_map.p);
+        CK_LAUNCH();
     }
     if (f32) {
         to_f32(h->pcol0, h->pcol0_32, s);

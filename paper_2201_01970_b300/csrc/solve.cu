@@ -112,11 +112,12 @@ __global__ void k_restrict(int nb, const int *order, const double *v_base, long 
 }
 
 // Second residual of Alg. 1: r = v - A z with z = Pi_P e_P, so only column 0 of
-// every block (the frozen copy c0, 3 values per block) takes part.  G lanes
-// per block row, whole blocks per lane, one FMA per stored value.
+// every block (the frozen copy c0, 3 values per block) takes part.  Rows and
+// columns are BILU positions (position t is natural block row border[t]); r
+// leaves in positions.  G lanes per block row, whole blocks per lane.
 template <class T, int G>
 __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
-                                const T *__restrict__ c0, const T *__restrict__ ep,
+                                const T *__restrict__ c0, const T *__restrict__ ep, const int *__restrict__ border,
                                 const double *v_base, long ld, const int *jptr, T *__restrict__ r,
                                 const int *done) {
     if (done && *done) return;
@@ -141,7 +142,7 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
         a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
     }
     if (active && lane == 0) {
-        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)row;
+        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)border[row];
         r[3 * (size_t)row] = (T)v[0] - a0;
         r[3 * (size_t)row + 1] = (T)v[1] - a1;
         r[3 * (size_t)row + 2] = (T)v[2] - a2;
@@ -253,7 +254,7 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
     if (active && lane == 0) y[i] = add ? y[i] + s : s;
 }
 
-// Level 0's result in natural numbering: out[order[t]] = x[t] (pending range from sp).
+// Level 0's result renumbered: out[map[t]] = x[t] (pending range from sp).
 template <class T>
 __global__ void k_commit_natural(int n, const int *order, const T *x, const T *sp, int p0, int p1,
                                  T *out, const int *done) {
@@ -280,15 +281,16 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b
 
 // ------------------------------------------------------------- BILU(0) sweeps
 
-// Forward substitution for one color, in place: y_i = r_i - sum_{lower} L_ij y_j.
+// Forward substitution for the color of positions [c0, c0 + cnt), in place:
+// y_i = r_i - sum_{lower} L_ij y_j (everything in BILU positions).
 template <class T>
-__global__ void k_bilu_fwd(const int *rows, int cnt, const int *__restrict__ lr,
+__global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
                            const int *__restrict__ lc, const T *__restrict__ lv, T *y,
                            const int *done) {
     if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    int i = rows[t];
+    int i = c0 + t;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
 #pragma unroll 4
     for (int p = lr[i]; p < lr[i + 1]; p++) {
@@ -304,17 +306,18 @@ __global__ void k_bilu_fwd(const int *rows, int cnt, const int *__restrict__ lr,
     y[3 * (size_t)i + 2] = s2;
 }
 
-// Backward substitution for one color, in place: z_i = U_ii^-1 (y_i - sum_{upper} U_ij z_j).
-// The result, plus Pi_P e_P when ep != nullptr, is also written to out (FP64).
+// Backward substitution for the color of positions [c0, c0 + cnt), in place:
+// z_i = U_ii^-1 (y_i - sum_{upper} U_ij z_j).  The result, plus Pi_P e_P when
+// ep != nullptr, is also written to out (FP64, natural block row border[i]).
 template <class T>
-__global__ void k_bilu_bwd(const int *rows, int cnt, const int *__restrict__ ur,
+__global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
                            const int *__restrict__ uc, const T *__restrict__ uv,
-                           const T *__restrict__ dinv, T *y, const T *ep, double *out_base, long ld,
-                           const int *jptr, const int *done) {
+                           const T *__restrict__ dinv, T *y, const T *ep, const int *__restrict__ border,
+                           double *out_base, long ld, const int *jptr, const int *done) {
     if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
-    int i = rows[t];
+    int i = c0 + t;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
 #pragma unroll 4
     for (int p = ur[i]; p < ur[i + 1]; p++) {
@@ -332,7 +335,7 @@ __global__ void k_bilu_bwd(const int *rows, int cnt, const int *__restrict__ ur,
     y[3 * (size_t)i] = z0;
     y[3 * (size_t)i + 1] = z1;
     y[3 * (size_t)i + 2] = z2;
-    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
+    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)border[i];
     out[0] = (double)z0 + (ep ? (double)ep[i] : 0.0);
     out[1] = (double)z1;
     out[2] = (double)z2;
@@ -351,6 +354,24 @@ template <class T>
 __global__ void k_gather_cast(int n, const int *order, const double *x, T *y) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) y[t] = (T)x[order ? order[t] : t];
+}
+
+// x[i] = (double) y[map[i]] (natural i from positions).
+template <class T>
+__global__ void k_gather_widen(int n, const int *map, const T *y, double *x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (double)y[map[i]];
+}
+
+// y[t] = (T) r[order[t]] for the 3 values of block row t.
+template <class T>
+__global__ void k_gather3(int nb, const int *order, const double *r, T *y) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    const double *src = r + 3 * (size_t)order[t];
+    y[3 * (size_t)t] = (T)src[0];
+    y[3 * (size_t)t + 1] = (T)src[1];
+    y[3 * (size_t)t + 2] = (T)src[2];
 }
 
 template <class T>
@@ -702,19 +723,15 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
     out = pd;
 }
 
-// e_P = B_P r_P on level 0: r_P arrives in level 0's b (color order); the
-// result leaves in natural numbering in ep.
+// e_P = B_P r_P on level 0: r_P arrives in level 0's b (level 0's color
+// order); the result leaves in BILU positions in ep.
 template <class T>
 void vcycle_top(cpr_handle *h, T *ep, const int *done) {
     Level &L0 = h->lev[0];
     Pending pd;
     vcycle<T>(h, 0, pd, done);
     int n = L0.A.n;
-    if (h->lev.size() == 1) {
-        CK(cudaMemcpyAsync(ep, Vals<T>::x(L0), sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
-        return;
-    }
-    k_commit_natural<T><<<blocks_for(n), kBlock, 0, h->stream>>>(n, L0.rows_by_color.p, Vals<T>::x(L0),
+    k_commit_natural<T><<<blocks_for(n), kBlock, 0, h->stream>>>(n, h->ep_map.p, Vals<T>::x(L0),
                                                                   Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
     CK_LAUNCH();
 }
@@ -729,16 +746,16 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     for (int c = 0; c < B.ncolors; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bilu_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                               B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), y, done);
+        k_bilu_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p,
+                                                               Vals<T>::Lv(h), y, done);
         CK_LAUNCH();
     }
     for (int c = B.ncolors - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bilu_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                               B.Urowptr.p, B.Ucol.p, Vals<T>::Uv(h),
-                                                               Vals<T>::Dv(h), y, ep, out_base, ld, jptr, done);
+        k_bilu_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p,
+                                                               Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep,
+                                                               B.rows_by_color.p, out_base, ld, jptr, done);
         CK_LAUNCH();
     }
 }
@@ -757,7 +774,7 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     k_restrict<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
                                                           Vals<T>::b(L0), done);
     CK_LAUNCH();
-    // e_P = B_P r_P (natural numbering)
+    // e_P = B_P r_P (BILU positions)
     prof_begin(h, CPR_PROF_VCYCLE);
     vcycle_top<T>(h, Vals<T>::ep(h), done);
     prof_end(h);
@@ -765,7 +782,8 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     long threads = (long)nb * kResidLanes;
     prof_begin(h, CPR_PROF_RESID2);
     k_prolong_resid<T, kResidLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-        nb, h->rowptr.p, h->col.p, Vals<T>::c0(h), Vals<T>::ep(h), v_base, v_ld, jptr, Vals<T>::tmp(h), done);
+        nb, h->c0rowptr.p, h->c0col.p, Vals<T>::c0(h), Vals<T>::ep(h), h->bilu.rows_by_color.p, v_base, v_ld,
+        jptr, Vals<T>::tmp(h), done);
     CK_LAUNCH();
     prof_end(h);
     // z = Pi_P e_P + (LU)^-1 r
@@ -843,25 +861,27 @@ void vcycle_apply(cpr_handle *h, const double *b, double *x) {
         k_gather_cast<float><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b32.p);
         CK_LAUNCH();
         vcycle_top<float>(h, h->ep32.p, nullptr);
-        k_widen<float><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, h->ep32.p, x);
+        k_gather_widen<float><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->bilu.iperm.p, h->ep32.p, x);
         CK_LAUNCH();
     } else {
         k_gather_cast<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b.p);
         CK_LAUNCH();
         vcycle_top<double>(h, h->ep64.p, nullptr);
-        CK(cudaMemcpyAsync(x, h->ep64.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        k_gather_widen<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->bilu.iperm.p, h->ep64.p, x);
+        CK_LAUNCH();
     }
 }
 
 void bilu_apply(cpr_handle *h, const double *r, double *z) {
     cudaStream_t s = h->stream;
-    long N = 3L * h->nb;
+    int nb = h->nb;
     if (h->opt.precond_fp32) {
-        k_cast<float><<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, r, h->t32a.p);
+        k_gather3<float><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->bilu.rows_by_color.p, r, h->t32a.p);
         CK_LAUNCH();
         bilu_solve<float>(h, h->t32a.p, nullptr, z, 0, nullptr, nullptr);
     } else {
-        CK(cudaMemcpyAsync(h->t64a.p, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        k_gather3<double><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->bilu.rows_by_color.p, r, h->t64a.p);
+        CK_LAUNCH();
         bilu_solve<double>(h, h->t64a.p, nullptr, z, 0, nullptr, nullptr);
     }
 }
