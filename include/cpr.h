@@ -126,6 +126,31 @@ const char *cpr_strerror(int code);
 const char *cpr_last_error_detail(void);
 
 /* ------------------------------------------------------------------------
+ * Batched solves: many independent systems of uneven size in one handle.
+ * The systems' matrices are concatenated into one block-diagonal matrix, so
+ * the preconditioner's setup and every preconditioner kernel run once over all
+ * systems (B is the block-diagonal CPR preconditioner); FGMRES (Alg. 2) runs
+ * per system in lockstep, each with its own Hessenberg matrix, rotations and
+ * stop decision, and each Arnoldi step of the whole batch is one graph launch.
+ * cpr_solve and the component calls reject a batch handle; cpr_destroy frees it.
+ * ---------------------------------------------------------------------- */
+
+/* Build a batch handle from nsys systems A[0..nsys-1] (host or device pointers,
+ * each following the conventions above). */
+int cpr_batch_setup(cpr_handle **h, int nsys, const cpr_bsr3 *A, const cpr_opts *opts);
+
+/* New matrices with unchanged sizes (Alg. 3 decides reuse, with It^(k-1) the
+ * largest step count of the previous batch solve). */
+int cpr_batch_update(cpr_handle *h, const cpr_bsr3 *A);
+
+/* Solve every system: b[k], x[k] (host or device; x[k] is the initial guess and
+ * receives the solution); st, when not NULL, holds nsys entries. */
+int cpr_batch_solve(cpr_handle *h, const double *const *b, double *const *x, double rtol, cpr_stats *st);
+
+/* Number of systems of a batch handle (0 for a single-system handle). */
+int cpr_batch_size(const cpr_handle *h);
+
+/* ------------------------------------------------------------------------
  * Component entry points: one application of a part of B.  All vectors are
  * DEVICE pointers with the handle's sizes; work is ordered on the handle's
  * stream and the call returns after it completes.  In FP32 mode the inputs

@@ -94,6 +94,10 @@ def lib():
         L.cpr_copy_level.argtypes = [vp, C.c_int] + [vp] * 8
         L.cpr_copy_weights.argtypes = [vp, vp]
         L.cpr_copy_bilu.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
+        L.cpr_batch_setup.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(Bsr3), C.POINTER(Opts)]
+        L.cpr_batch_update.argtypes = [vp, C.POINTER(Bsr3)]
+        L.cpr_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(Stats)]
+        L.cpr_batch_size.argtypes = [vp]
         L.cpr_launch_count.restype = C.c_uint64
         L.cpr_profile.argtypes = [vp, C.c_int]
         L.cpr_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]
@@ -251,6 +255,50 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver(Solver):
+    """A batch handle: many independent systems (block-diagonal preconditioner,
+    per-system FGMRES in lockstep)."""
+
+    def __init__(self, systems, **opts):
+        if "stream" not in opts:
+            opts["stream"] = _torch_stream()
+        self.opts = default_opts(**opts)
+        self._h = C.c_void_p()
+        descs, self._keep = [], []
+        for A in systems:
+            d, keep = _as_bsr3(A)
+            descs.append(d)
+            self._keep.append(keep)
+        arr = (Bsr3 * len(descs))(*descs)
+        _check(lib().cpr_batch_setup(C.byref(self._h), len(descs), arr, C.byref(self.opts)),
+               "cpr_batch_setup")
+        self.sizes = [d.nb for d in descs]
+        self.nb = sum(self.sizes)
+
+    def update(self, systems) -> None:
+        descs = [_as_bsr3(A)[0] for A in systems]
+        arr = (Bsr3 * len(descs))(*descs)
+        _check(lib().cpr_batch_update(self._h, arr), "cpr_batch_update")
+
+    def solve(self, bs, xs=None, rtol: float = 1e-6):
+        """Solve every system; returns (xs, list of stats dicts)."""
+        n = len(bs)
+        if xs is None:
+            xs = []
+            for b in bs:
+                if isinstance(b, np.ndarray):
+                    xs.append(np.zeros_like(b, dtype=np.float64))
+                else:
+                    import torch
+                    xs.append(torch.zeros_like(b))
+        bp = (C.c_void_p * n)(*[_ptr(b) for b in bs])
+        xp = (C.c_void_p * n)(*[_ptr(x) for x in xs])
+        st = (Stats * n)()
+        rc = lib().cpr_batch_solve(self._h, bp, xp, float(rtol), st)
+        _check(rc, "cpr_batch_solve", allow_not_converged=True)
+        return xs, [s_.as_dict() for s_ in st]
 
 
 PROF_SPMV, PROF_VCYCLE, PROF_BILU, PROF_CGS, PROF_RESID2 = range(5)

@@ -309,7 +309,7 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
 }
 
 int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
-    if (!h || !b || !x || !(rtol > 0.0)) return CPR_ERR_INVALID;
+    if (!h || !b || !x || !(rtol > 0.0) || h->batch) return CPR_ERR_INVALID;
     return guarded([&] {
         double t0 = now_ms();
         cudaStream_t s = h->stream;
@@ -358,6 +358,12 @@ void cpr_destroy(cpr_handle *h) {
     cudaStream_t s = h->stream;
     bool own = h->own_stream;
     destroy_step_graphs(h);
+    for (auto &g : h->sgb) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    delete h->batch;
+    h->batch = nullptr;
     for (auto e : h->step_done)
         if (e) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);

@@ -131,6 +131,20 @@ struct Bilu {
     DVec<float> Lval32, Uval32, Dinv32;
 };
 
+// Many independent systems concatenated into one block-diagonal operator: the
+// preconditioner runs on the concatenation, the Krylov process per system.
+struct BatchInfo {
+    int nsys = 0;
+    std::vector<int> boff;        // block-row offset of each system (nsys + 1)
+    int nchunk = 0;               // vector chunks, each inside one system
+    DVec<int> chunk_sys, chunk_beg, chunk_end;
+    DVec<int> sys_chunk_off;      // chunks of system s: [sys_chunk_off[s], sys_chunk_off[s+1])
+    DVec<double> scal;            // per-system scalar blocks (Hessenberg, rotations, g, y, norms)
+    DVec<int> sint;               // per-system ints: done, steps this cycle, breakdown, converged, total steps
+    DVec<double> part, part2;     // chunk partial sums
+    DVec<double> b, x;            // concatenated right-hand sides and iterates
+};
+
 }  // namespace cpr
 
 // The opaque handle of the C ABI.
@@ -191,6 +205,9 @@ struct cpr_handle {
     int sg_epoch = -1;
     bool sg_prof = false;
     int capturing = -1;              // index of the step graph being captured, -1 = none
+    StepGraph sgb[2];                // the batched step graphs
+    int sgb_epoch = -1;
+    cpr::BatchInfo *batch = nullptr;
     cudaEvent_t step_done[2] = {nullptr, nullptr};
 };
 
@@ -227,6 +244,8 @@ void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, do
 void vcycle_apply(cpr_handle *h, const double *b, double *x);
 void bilu_apply(cpr_handle *h, const double *r, double *z);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
+void batch_prepare(cpr_handle *h);
+int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st);
 void bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val, const double *x,
                const double *b, double *y, cudaStream_t s);
 

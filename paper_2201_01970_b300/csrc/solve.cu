@@ -1048,4 +1048,406 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
     return rc;
 }
 
+
+// ===================================================================== batch
+//
+// FGMRES(m) for many systems at once (Alg. 2 per system, in lockstep): the
+// systems' vectors are segments of one concatenated vector and B is the
+// block-diagonal CPR preconditioner of the concatenated operator.  Dots and
+// norms are reduced per system over fixed chunks in a fixed order; every
+// system keeps its own Hessenberg matrix, rotations, residual estimate and
+// stop decision.  A stopped system's rows keep flowing through the shared
+// kernels, but nothing of it is updated any more.
+
+namespace {
+
+constexpr int kChunk = 4096;   // vector elements per chunk
+enum { S_DONE = 0, S_K = 1, S_BREAK = 2, S_CONV = 3, S_ITERS = 4, S_NINT = 5 };
+
+__global__ void k_bdots(const double *__restrict__ V, const double *__restrict__ w, long N,
+                        const int *jptr, const int *cbeg, const int *cend, double *part, int ldp,
+                        const int *done) {
+    if (*done) return;
+    int c = blockIdx.x;
+    int nvec = *jptr + 1;
+    int beg = cbeg[c], end = cend[c];
+    for (int g0 = 0; g0 < nvec; g0 += kDotGroup) {
+        double acc[kDotGroup];
+#pragma unroll
+        for (int k = 0; k < kDotGroup; k++) acc[k] = 0.0;
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            double wq = w[q];
+#pragma unroll
+            for (int k = 0; k < kDotGroup; k++)
+                if (g0 + k < nvec) acc[k] += V[(size_t)(g0 + k) * N + q] * wq;
+        }
+#pragma unroll
+        for (int k = 0; k < kDotGroup; k++) {
+            double sm = block_sum(acc[k]);
+            if (threadIdx.x == 0 && g0 + k < nvec) part[(size_t)c * ldp + g0 + k] = sm;
+        }
+    }
+}
+
+// hcol of system s = sum over its chunks (fixed order), one block per system.
+__global__ void k_bdots_reduce(const int *sco, const double *part, int ldp, const int *jptr, double *scal,
+                               int ssz, int m, const int *sint, const int *done) {
+    if (*done) return;
+    int sys = blockIdx.x;
+    if (sint[S_NINT * sys + S_DONE]) return;
+    ScalLayout SL{m};
+    int nvec = *jptr + 1;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int c0 = sco[sys], c1 = sco[sys + 1];
+    for (int i = wid; i < nvec; i += nw) {
+        double sm = 0.0;
+        for (int c = c0 + lane; c < c1; c += 32) sm += part[(size_t)c * ldp + i];
+        sm = warp_sum(sm);
+        if (lane == 0) scal[(size_t)sys * ssz + SL.hcol() + i] = sm;
+    }
+}
+
+// w -= sum_i h_i V_i on each chunk with its system's h; chunk partials of ||w||^2.
+__global__ void k_bupdate(const double *__restrict__ V, double *__restrict__ w, long N, const int *jptr,
+                          const int *csys, const int *cbeg, const int *cend, const double *scal, int ssz, int m,
+                          const int *sint, double *part2, const int *done) {
+    if (*done) return;
+    __shared__ double sh[kMaxRestart + 1];
+    int c = blockIdx.x, sys = csys[c];
+    if (sint[S_NINT * sys + S_DONE]) {
+        if (threadIdx.x == 0) part2[c] = 0.0;
+        return;
+    }
+    ScalLayout SL{m};
+    int nvec = *jptr + 1;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = scal[(size_t)sys * ssz + SL.hcol() + i];
+    __syncthreads();
+    double sm = 0.0;
+    for (int q = cbeg[c] + threadIdx.x; q < cend[c]; q += blockDim.x) {
+        double wq = w[q];
+        for (int i = 0; i < nvec; i++) wq -= sh[i] * V[(size_t)i * N + q];
+        w[q] = wq;
+        sm += wq * wq;
+    }
+    sm = block_sum(sm);
+    if (threadIdx.x == 0) part2[c] = sm;
+}
+
+// One Givens step per running system (thread per system), then the shared
+// step counter advances; `done` is raised when every system has stopped.
+__global__ void k_bgivens(int nsys, const int *sco, const double *part2, double *scal, int ssz, int m,
+                          int *sint, int *di) {
+    if (di[I_DONE]) return;
+    ScalLayout SL{m};
+    int j = di[I_J];
+    __shared__ int running;
+    if (threadIdx.x == 0) running = 0;
+    __syncthreads();
+    for (int sys = threadIdx.x; sys < nsys; sys += blockDim.x) {
+        int *si = sint + S_NINT * sys;
+        if (si[S_DONE]) continue;
+        double *sc = scal + (size_t)sys * ssz;
+        double hn2 = 0.0;
+        for (int c = sco[sys]; c < sco[sys + 1]; c++) hn2 += part2[c];
+        double hn = sqrt(hn2);
+        for (int i = 0; i <= j; i++) sc[SL.H(i, j)] = sc[SL.hcol() + i];
+        sc[SL.H(j + 1, j)] = hn;
+        for (int i = 0; i < j; i++) {
+            double a = sc[SL.H(i, j)], cc = sc[SL.H(i + 1, j)];
+            sc[SL.H(i, j)] = sc[SL.cs() + i] * a + sc[SL.sn() + i] * cc;
+            sc[SL.H(i + 1, j)] = -sc[SL.sn() + i] * a + sc[SL.cs() + i] * cc;
+        }
+        double a = sc[SL.H(j, j)], cc = sc[SL.H(j + 1, j)];
+        double den = sqrt(a * a + cc * cc);
+        double cj = den == 0.0 ? 1.0 : a / den, sj = den == 0.0 ? 0.0 : cc / den;
+        sc[SL.cs() + j] = cj;
+        sc[SL.sn() + j] = sj;
+        sc[SL.H(j, j)] = den;
+        sc[SL.H(j + 1, j)] = 0.0;
+        double gj = sc[SL.g() + j];
+        sc[SL.g() + j + 1] = -sj * gj;
+        sc[SL.g() + j] = cj * gj;
+        double est = fabs(sc[SL.g() + j + 1]) / sc[SL.norm0()];
+        sc[SL.est()] = est;
+        sc[SL.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
+        si[S_K] = j + 1;
+        bool brk = !isfinite(hn) || !isfinite(est);
+        if (brk) si[S_BREAK] = 1;
+        if (brk || hn == 0.0 || est < sc[SL.rtol()] || j + 1 >= m) si[S_DONE] = 1;
+        else atomicAdd(&running, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        di[I_J] = j + 1;
+        di[I_K] = j + 1;
+        if (running == 0) di[I_DONE] = 1;
+    }
+}
+
+// V_{j+1} = w / h_{j+1,j} per chunk, for systems still running.
+__global__ void k_bnext(const double *w, double *V, long N, const int *csys, const int *cbeg, const int *cend,
+                        const double *scal, int ssz, int m, const int *sint, const int *di) {
+    if (di[I_DONE]) return;
+    int c = blockIdx.x, sys = csys[c];
+    if (sint[S_NINT * sys + S_DONE]) return;
+    ScalLayout SL{m};
+    double f = scal[(size_t)sys * ssz + SL.inv_hn()];
+    double *v = V + (size_t)di[I_J] * N;
+    for (int q = cbeg[c] + threadIdx.x; q < cend[c]; q += blockDim.x) v[q] = w[q] * f;
+}
+
+__global__ void k_bnorm_part(const double *r, const int *cbeg, const int *cend, double *part2) {
+    int c = blockIdx.x;
+    double sm = 0.0;
+    for (int q = cbeg[c] + threadIdx.x; q < cend[c]; q += blockDim.x) sm += r[q] * r[q];
+    sm = block_sum(sm);
+    if (threadIdx.x == 0) part2[c] = sm;
+}
+
+// Start of a cycle for every system: beta = ||r_s||; a system whose true
+// residual already meets rtol (or whose r_0 is zero or non-finite) stops.
+__global__ void k_bcycle_start(int nsys, const int *sco, const double *part2, double *scal, int ssz, int m,
+                               int *sint, int *di, int first, double rtol, int *nrunning) {
+    ScalLayout SL{m};
+    __shared__ int running;
+    if (threadIdx.x == 0) running = 0;
+    __syncthreads();
+    for (int sys = threadIdx.x; sys < nsys; sys += blockDim.x) {
+        double *sc = scal + (size_t)sys * ssz;
+        int *si = sint + S_NINT * sys;
+        double ss = 0.0;
+        for (int c = sco[sys]; c < sco[sys + 1]; c++) ss += part2[c];
+        double beta = sqrt(ss);
+        if (first) {
+            sc[SL.norm0()] = beta;
+            sc[SL.rtol()] = rtol;
+            si[S_CONV] = 0;
+            si[S_ITERS] = 0;
+            si[S_BREAK] = 0;
+        }
+        sc[SL.rnorm()] = beta;
+        double n0 = sc[SL.norm0()];
+        bool conv = si[S_CONV] || n0 == 0.0 || (!first && beta / n0 < rtol);
+        if (!isfinite(beta)) si[S_BREAK] = 1;
+        si[S_CONV] = conv;
+        for (int i = 0; i <= m; i++) sc[SL.g() + i] = 0.0;
+        sc[SL.g()] = beta;
+        sc[SL.inv_hn()] = beta > 0.0 ? 1.0 / beta : 0.0;
+        si[S_K] = 0;
+        si[S_DONE] = conv || si[S_BREAK];
+        if (!si[S_DONE]) atomicAdd(&running, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        di[I_J] = 0;
+        di[I_K] = 0;
+        di[I_BREAK] = 0;
+        di[I_DONE] = running == 0;
+        *nrunning = running;
+    }
+}
+
+__global__ void k_bscale(const double *r, double *V, const int *csys, const int *cbeg, const int *cend,
+                         const double *scal, int ssz, int m) {
+    int c = blockIdx.x, sys = csys[c];
+    ScalLayout SL{m};
+    double f = scal[(size_t)sys * ssz + SL.inv_hn()];
+    for (int q = cbeg[c] + threadIdx.x; q < cend[c]; q += blockDim.x) V[q] = r[q] * f;
+}
+
+// y_s = H_s^-1 g_s for every system (thread per system); steps are counted.
+__global__ void k_bsolve_y(int nsys, double *scal, int ssz, int m, int *sint) {
+    ScalLayout SL{m};
+    for (int sys = blockIdx.x * blockDim.x + threadIdx.x; sys < nsys; sys += gridDim.x * blockDim.x) {
+        double *sc = scal + (size_t)sys * ssz;
+        int k = sint[S_NINT * sys + S_K];
+        sint[S_NINT * sys + S_ITERS] += k;
+        for (int i = k - 1; i >= 0; i--) {
+            double v = sc[SL.g() + i];
+            for (int q = i + 1; q < k; q++) v -= sc[SL.H(i, q)] * sc[SL.y() + q];
+            sc[SL.y() + i] = v / sc[SL.H(i, i)];
+        }
+    }
+}
+
+__global__ void k_bupdate_x(const double *__restrict__ Z, double *x, long N, const int *csys, const int *cbeg,
+                            const int *cend, const double *scal, int ssz, int m, const int *sint) {
+    __shared__ double sy[kMaxRestart];
+    int c = blockIdx.x, sys = csys[c];
+    int k = sint[S_NINT * sys + S_K];
+    if (k == 0) return;
+    ScalLayout SL{m};
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = scal[(size_t)sys * ssz + SL.y() + i];
+    __syncthreads();
+    for (int q = cbeg[c] + threadIdx.x; q < cend[c]; q += blockDim.x) {
+        double v = x[q];
+        for (int i = 0; i < k; i++) v += sy[i] * Z[(size_t)i * N + q];
+        x[q] = v;
+    }
+}
+
+void record_step_batch(cpr_handle *h) {
+    cudaStream_t s = h->stream;
+    BatchInfo &B = *h->batch;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
+    ScalLayout SL{m};
+    int ssz = SL.size();
+    int *di = h->dint.p;
+    const int *done = di + I_DONE;
+    int ldp = kMaxRestart + 2;
+    if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+    else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
+    spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
+    k_bdots<<<B.nchunk, kBlock, 0, s>>>(h->V.p, h->wv.p, N, di + I_J, B.chunk_beg.p, B.chunk_end.p, B.part.p, ldp,
+                                        done);
+    CK_LAUNCH();
+    k_bdots_reduce<<<B.nsys, kBlock, 0, s>>>(B.sys_chunk_off.p, B.part.p, ldp, di + I_J, B.scal.p, ssz, m,
+                                             B.sint.p, done);
+    CK_LAUNCH();
+    k_bupdate<<<B.nchunk, kBlock, 0, s>>>(h->V.p, h->wv.p, N, di + I_J, B.chunk_sys.p, B.chunk_beg.p,
+                                          B.chunk_end.p, B.scal.p, ssz, m, B.sint.p, B.part2.p, done);
+    CK_LAUNCH();
+    k_bgivens<<<1, 1024, 0, s>>>(B.nsys, B.sys_chunk_off.p, B.part2.p, B.scal.p, ssz, m, B.sint.p, di);
+    CK_LAUNCH();
+    k_bnext<<<B.nchunk, kBlock, 0, s>>>(h->wv.p, h->V.p, N, B.chunk_sys.p, B.chunk_beg.p, B.chunk_end.p, B.scal.p,
+                                        ssz, m, B.sint.p, di);
+    CK_LAUNCH();
+}
+
+}  // namespace
+
+// Chunk tables and per-system buffers for the handle's batch description.
+void batch_prepare(cpr_handle *h) {
+    BatchInfo &B = *h->batch;
+    cudaStream_t s = h->stream;
+    std::vector<int> csys, cbeg, cend, sco(B.nsys + 1, 0);
+    for (int sys = 0; sys < B.nsys; sys++) {
+        int beg = 3 * B.boff[sys], end = 3 * B.boff[sys + 1];
+        sco[sys] = (int)csys.size();
+        for (int q = beg; q < end; q += kChunk) {
+            csys.push_back(sys);
+            cbeg.push_back(q);
+            cend.push_back(std::min(end, q + kChunk));
+        }
+    }
+    sco[B.nsys] = (int)csys.size();
+    B.nchunk = (int)csys.size();
+    auto up = [&](DVec<int> &d, const std::vector<int> &v) {
+        d.alloc(std::max<size_t>(v.size(), 1), s);
+        CK(cudaMemcpyAsync(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+    };
+    up(B.chunk_sys, csys);
+    up(B.chunk_beg, cbeg);
+    up(B.chunk_end, cend);
+    up(B.sys_chunk_off, sco);
+    int m = h->opt.restart;
+    ScalLayout SL{m};
+    B.scal.alloc((size_t)B.nsys * SL.size(), s);
+    B.scal.zero();
+    B.sint.alloc((size_t)B.nsys * S_NINT, s);
+    B.sint.zero();
+    B.part.alloc((size_t)B.nchunk * (kMaxRestart + 2), s);
+    B.part2.alloc(B.nchunk, s);
+    B.b.alloc(3L * h->nb, s);
+    B.x.alloc(3L * h->nb, s);
+    CK(cudaStreamSynchronize(s));
+}
+
+// Lockstep FGMRES for every system of the batch; B.b and B.x hold the
+// concatenated right-hand sides and initial guesses; st[s] gets system s's stats.
+int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st) {
+    cudaStream_t s = h->stream;
+    BatchInfo &B = *h->batch;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
+    ScalLayout SL{m};
+    int ssz = SL.size();
+    int *di = h->dint.p;
+    double *x = B.x.p;
+    int *pin = reinterpret_cast<int *>(h->pinned + 8);
+    int rc = CPR_NOT_CONVERGED;
+    if (h->sgb_epoch != h->epoch || !h->sgb[0].exec || !h->sgb[1].exec) {
+        for (auto &g : h->sgb) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+            g = cpr_handle::StepGraph{};
+        }
+        bool prof = h->prof;
+        h->prof = false;
+        for (int k = 0; k < 2; k++) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                record_step_batch(h);
+            } catch (...) {
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+                h->prof = prof;
+                throw;
+            }
+            CK(cudaStreamEndCapture(s, &g));
+            h->sgb[k].graph = g;
+            CK(cudaGraphInstantiate(&h->sgb[k].exec, g, 0));
+        }
+        h->prof = prof;
+        h->sgb_epoch = h->epoch;
+    }
+    int cycles = 0;
+    for (int cycle = 0; cycle <= h->opt.max_restarts; cycle++) {
+        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, B.b.p, h->r.p, s, nullptr);
+        k_bnorm_part<<<B.nchunk, kBlock, 0, s>>>(h->r.p, B.chunk_beg.p, B.chunk_end.p, B.part2.p);
+        CK_LAUNCH();
+        k_bcycle_start<<<1, 1024, 0, s>>>(B.nsys, B.sys_chunk_off.p, B.part2.p, B.scal.p, ssz, m, B.sint.p, di,
+                                          cycle == 0, rtol, di + I_ZERO);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(pin + 8, di + I_ZERO, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (pin[8] == 0 || cycle == h->opt.max_restarts) break;
+        k_bscale<<<B.nchunk, kBlock, 0, s>>>(h->r.p, h->V.p, B.chunk_sys.p, B.chunk_beg.p, B.chunk_end.p, B.scal.p,
+                                             ssz, m);
+        CK_LAUNCH();
+        cycles++;
+        bool stop = false;
+        for (int j = 0; j < m && !stop; j++) {
+            CK(cudaGraphLaunch(h->sgb[j & 1].exec, s));
+            CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(h->step_done[j & 1], s));
+            if (j >= 1) {
+                CK(cudaEventSynchronize(h->step_done[(j - 1) & 1]));
+                stop = pin[4 * ((j - 1) & 1) + I_DONE] != 0;
+            }
+        }
+        CK(cudaStreamSynchronize(s));
+        k_bsolve_y<<<grid_for(B.nsys, 128), 128, 0, s>>>(B.nsys, B.scal.p, ssz, m, B.sint.p);
+        CK_LAUNCH();
+        k_bupdate_x<<<B.nchunk, kBlock, 0, s>>>(h->Z.p, x, N, B.chunk_sys.p, B.chunk_beg.p, B.chunk_end.p, B.scal.p,
+                                                ssz, m, B.sint.p);
+        CK_LAUNCH();
+    }
+    std::vector<int> si((size_t)B.nsys * S_NINT);
+    std::vector<double> sc((size_t)B.nsys * ssz);
+    CK(cudaMemcpyAsync(si.data(), B.sint.p, sizeof(int) * si.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sc.data(), B.scal.p, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool all = true, brk = false;
+    long total = 0;
+    for (int sys = 0; sys < B.nsys; sys++) {
+        const int *q = &si[(size_t)sys * S_NINT];
+        const double *c = &sc[(size_t)sys * ssz];
+        all = all && q[S_CONV];
+        brk = brk || q[S_BREAK];
+        total = std::max<long>(total, q[S_ITERS]);
+        if (st) {
+            st[sys].iters = q[S_ITERS];
+            st[sys].restarts = cycles;
+            st[sys].converged = q[S_CONV];
+            st[sys].rel_res = c[SL.norm0()] > 0.0 ? c[SL.rnorm()] / c[SL.norm0()] : 0.0;
+        }
+    }
+    h->last_iters = total;
+    rc = brk ? CPR_ERR_BREAKDOWN : (all ? CPR_OK : CPR_NOT_CONVERGED);
+    return rc;
+}
+
 }  // namespace cpr
