@@ -260,6 +260,88 @@ def e2e_arm(cpr, torch, seq_host, K, W, stream):
             "d2h_bytes_per_step": int(xh.nbytes)}
 
 
+def batched_arm(cpr, torch, K, stream, nsys=64):
+    """64 independent systems (16^3 .. 64x64x16): one batched FP32-preconditioner
+    solve vs the same systems solved one after another with plain FP64 CPR."""
+    specs = bs.batch_specs(nsys)
+    Js = [bs.jacobian(g) for g in specs]
+
+    class DJ:
+        def __init__(self, J):
+            self.nb = J.nb
+            self.rowptr = torch.from_numpy(J.rowptr).cuda()
+            self.col = torch.from_numpy(J.col).cuda()
+            self.val = torch.from_numpy(J.val).cuda()
+
+    dj = [DJ(J) for J in Js]
+    bvec = [torch.from_numpy(J.b).cuda() for J in Js]
+    bt = cpr.BatchSolver(dj, precond_fp32=1, mu=MU, stream=stream.cuda_stream)
+    xs = [torch.zeros_like(b) for b in bvec]
+    for _ in range(2):
+        bt.solve(bvec, xs, rtol=RTOL)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(K):
+        for x in xs:
+            x.zero_()
+        _, sts = bt.solve(bvec, xs, rtol=RTOL)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / K
+    ok = all(st["converged"] for st in sts)
+    iters = [st["iters"] for st in sts]
+    bt.close()
+    # the same systems, one handle each, FP64 preconditioner, solved in turn
+    singles = [cpr.Solver(d, precond_fp32=0, mu=MU, stream=stream.cuda_stream) for d in dj]
+    for sv, b, x in zip(singles, bvec, xs):
+        x.zero_()
+        sv.solve(b, x, rtol=RTOL)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(max(1, K // 2)):
+        for sv, b, x in zip(singles, bvec, xs):
+            x.zero_()
+            sv.solve(b, x, rtol=RTOL)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = ev0.elapsed_time(ev1) / max(1, K // 2)
+    for sv in singles:
+        sv.close()
+    cells = sum(g.ncells for g in specs)
+    return {"workload": f"{nsys} systems, 16^3..64x64x16 cells ({cells} cells), FP32 preconditioner",
+            "value": nsys / (ms / 1000.0), "unit": UNIT, "ms_per_batch": ms, "all_converged": ok,
+            "iters_max": max(iters), "iters_mean": statistics.mean(iters),
+            "fp64_one_by_one": {"value": nsys / (ms_seq / 1000.0), "unit": UNIT, "ms": ms_seq},
+            "speedup_vs_fp64_one_by_one": ms_seq / ms}
+
+
+def serve_arm(full: bool):
+    """Continuous-batching service: 32 ensemble members x 5 drifting Newton
+    Jacobians, Poisson arrivals at 200 requests/s, 4 slots, resident
+    hierarchies with the adaptive rule per member, FP32 preconditioner; beside
+    it the same requests served one at a time by plain FP64 CPR (setup every
+    request, mu = 0)."""
+    from paper_2201_01970_b300 import serve
+    members = bs.ensemble_specs(32, full=full)
+    reqs = serve.poisson_requests(members, steps=5, rate=200.0, seed=0)
+    srv = serve.Server(slots=4, precond_fp32=1, mu=MU)
+    m = srv.run(reqs, realtime=True)
+    srv.close()
+    ok = all(r.stats.get("converged") for r in reqs)
+    base = serve.poisson_requests(members, steps=5, rate=200.0, seed=0)
+    srv = serve.Server(slots=1, precond_fp32=0, mu=0)
+    mb = srv.run(base, realtime=False)
+    srv.close()
+    cells = sum(g.ncells for g in members)
+    m.update({"workload": f"32 members ({'32x32x8..128x128x32' if full else '32x32x8..64x64x16'}, "
+                          f"{cells} cells), 5 Newton steps each, Poisson 200/s",
+              "all_converged": ok,
+              "plain_fp64_cpr_serial": {"value": mb["value"], "unit": "solves/s", "p50_ms": mb["p50_ms"],
+                                        "p99_ms": mb["p99_ms"]}})
+    return m
+
+
 def cpu_baseline(seq_host):
     """The FP64 oracle, single-threaded on the host: one update (full setup, as
     It > mu) and one solve of the same workload's second Jacobian."""
@@ -333,6 +415,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving ensemble over the full 32x32x8..128x128x32 range")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
                     help="precision arms to time (the JSON line needs both)")
     ap.add_argument("--profile-region", action="store_true",
@@ -387,6 +473,8 @@ def main():
         return
 
     e2e = None if args.no_e2e else e2e_arm(cpr, torch, seq_host, max(3, K // 2), 1, stream)
+    batched = None if args.no_batch else batched_arm(cpr, torch, max(3, K // 2), stream)
+    serving = None if args.no_serve else serve_arm(args.serve_full)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(seq_host)
@@ -470,6 +558,10 @@ def main():
     }
     if e2e is not None:
         line["e2e"] = e2e
+    if batched is not None:
+        line["batched"] = batched
+    if serving is not None:
+        line["serving"] = serving
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

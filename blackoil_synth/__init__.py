@@ -66,6 +66,31 @@ CONFIGS = {
 }
 
 
+def batch_specs(nsys: int = 64, seed: int = 0) -> list[GridSpec]:
+    """Independent systems for batched solves: nx, ny drawn uniformly from
+    16..64 with nz = 16 (16^3 to 64x64x16 cells), ln k ~ N(0, 1.5), corner wells."""
+    rng = np.random.Generator(np.random.PCG64([seed, 64]))
+    out = []
+    for k in range(nsys):
+        nx, ny = (int(v) for v in rng.integers(16, 65, 2))
+        out.append(GridSpec(nx, ny, 16, 0.0, 1.5, 1.0, None, "corners", seed=1000 + k))
+    return out
+
+
+def ensemble_specs(nmembers: int = 32, seed: int = 0, full: bool = True) -> list[GridSpec]:
+    """Ensemble members for the serving workload: grids from 32x32x8 to
+    128x128x32 (nx = ny from {32, 48, 64, 96, 128}, nz from {8, 16, 32}), or,
+    with full=False, from 32x32x8 to 64x64x16; ln k ~ N(0, 1), corner wells."""
+    rng = np.random.Generator(np.random.PCG64([seed, 32]))
+    sizes, layers = ([32, 48, 64, 96, 128], [8, 16, 32]) if full else ([32, 48, 64], [8, 16])
+    out = []
+    for k in range(nmembers):
+        n = int(rng.choice(sizes))
+        nz = int(rng.choice(layers))
+        out.append(GridSpec(n, n, nz, 0.0, 1.0, 1.0, None, "corners", seed=2000 + k))
+    return out
+
+
 def well_columns(g: GridSpec) -> list[tuple[int, int]]:
     """(i, j) surface locations of the wells; each perforates every layer."""
     if g.wells == "none":
