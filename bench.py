@@ -112,6 +112,37 @@ def bilu_bytes(nb, nnzb, sv):
     return (nnzb - nb) * (9 * sv + 4) + nb * 9 * sv + 16 * nb + 6 * 3 * nb * sv + nb * sv + 24 * nb
 
 
+def smooth0_bytes(level, sv, pre=1, post=1):
+    """Mean algorithmic bytes of one k_smooth_color launch on the finest level:
+    per row of the color its row pointer, b, 1/a_ii and the staged result; per
+    off-diagonal entry its column, value and the gathered x; plus the commit of
+    the previous color's staged rows (read staged, write x).  Averaged over the
+    launches of a V(pre,post) cycle: pre-sweeps ascend the colors (the very first
+    color is a separate from-zero kernel), post-sweeps descend, and the first
+    post-sweep color has nothing staged to commit."""
+    rp, color = level["rowptr"], level["color"]
+    off = np.diff(rp) - 1
+    nc = int(color.max()) + 1
+    rows = np.bincount(color, minlength=nc)
+    nnz = np.bincount(color, weights=off, minlength=nc)
+    sweeps = [(list(range(nc)), k == 0) for k in range(pre)] + \
+             [(list(range(nc - 1, -1, -1)), False) for _ in range(post)]
+    launches, prev = [], None
+    for si, (cols, from_zero) in enumerate(sweeps):
+        if si == pre:
+            prev = None                      # the residual kernel committed the pre-sweep's last color
+        for t, c in enumerate(cols):
+            if from_zero and t == 0:
+                prev = c
+                continue
+            by = rows[c] * (4 + 3 * sv) + nnz[c] * (4 + 2 * sv)
+            if prev is not None:
+                by += rows[prev] * 2 * sv
+            launches.append(by)
+            prev = c
+    return float(np.mean(launches))
+
+
 def spmv_bytes(nb, nnzb):
     """FP64 BSR: 72 B of values + 4 B of column per block; x, y and rowptr per block row."""
     return 76 * nnzb + 52 * nb
@@ -198,7 +229,6 @@ def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_reg
 
     for k in range(W):
         step(k)
-    solver.profile(True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
     launches0 = cpr.launch_count()
     barrier(world)
@@ -216,11 +246,25 @@ def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_reg
     launches = cpr.launch_count() - launches0
     per = [ev[i].elapsed_time(ev[i + 1]) for i in range(K)]
     total = ev[0].elapsed_time(ev[K])
-    fam = {f: solver.profile_read(f) for f in range(5)}
+    # Per-family times: a second timed region of the same steps with CUDA-event
+    # brackets around each family (the brackets add event nodes to the step
+    # graphs, so the headline above is taken without them).
+    P = min(K, 4)
+    solver.profile(True)
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    pe[0].record(stream)
+    for i in range(P):
+        step(W + K + i)
+    pe[1].record(stream)
+    torch.cuda.synchronize()
+    fam = {f: solver.profile_read(f) for f in range(6)}
+    solver.profile(False)
+    prof_ms = pe[0].elapsed_time(pe[1]) / P
     levels = [solver.level(l) for l in range(solver.nlev)]
     solver.close()
     return {"per_ms": per, "total_ms": total, "stats": stats, "fam": fam, "levels": levels,
-            "launches": launches}
+            "launches": launches, "profiled_ms_per_step": prof_ms, "profiled_steps": P}
 
 
 def e2e_arm(cpr, torch, seq_host, K, W, stream):
@@ -342,6 +386,58 @@ def serve_arm(full: bool):
     return m
 
 
+def adaptive_sweep(cpr, torch, stream, mus=(0, 10, 20, 30, 40), nseq=10):
+    """Alg. 3 on a 10-Jacobian drifting Newton sequence of the 60x220x85 banded
+    workload, per threshold mu and per preconditioner precision: total device
+    time of the sequence (update + solve per step; the first setup, done at
+    construction, is outside the timed region for every mu alike), setups
+    taken and iterations per step."""
+    g = bs.CONFIGS["60x220x85"]
+    seq = list(bs.jacobian_sequence(g, nseq, drift=0.05))
+
+    class DJ:
+        def __init__(self, J):
+            self.nb = J.nb
+            self.rowptr = torch.from_numpy(J.rowptr).cuda()
+            self.col = torch.from_numpy(J.col).cuda()
+            self.val = torch.from_numpy(J.val).cuda()
+
+    dev = [DJ(J) for J in seq]
+    rhs = [torch.from_numpy(J.b).cuda() for J in seq]
+    x = torch.zeros_like(rhs[0])
+    runs = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def one(fp32, mu):
+        s = cpr.Solver(dev[0], precond_fp32=int(fp32), mu=mu, stream=stream.cuda_stream)
+        sts = []
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(nseq):
+            if k:
+                s.update(dev[k])
+            with torch.cuda.stream(stream):
+                x.zero_()
+            _, st = s.solve(rhs[k], x, rtol=RTOL)
+            sts.append(st)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        return ev0.elapsed_time(ev1), sts
+
+    one(True, 0)                                  # warm-up: pool, graphs, first-touch
+    for fp32 in (True, False):
+        for mu in mus:
+            ms, sts = one(fp32, mu)
+            runs.append({"precond": "fp32" if fp32 else "fp64", "mu": mu, "total_ms": ms,
+                         "ms_per_step": ms / nseq,
+                         "setups": int(sum(st["setup_called"] for st in sts[1:])),
+                         "iters": [st["iters"] for st in sts],
+                         "all_converged": all(st["converged"] for st in sts)})
+    return {"workload": f"60x220x85 banded, {nseq}-Jacobian drifting sequence, rtol {RTOL}",
+            "nb": seq[0].nb, "nnzb": seq[0].nnzb, "runs": runs}
+
+
 def cpu_baseline(seq_host):
     """The FP64 oracle, single-threaded on the host: one update (full setup, as
     It > mu) and one solve of the same workload's second Jacobian."""
@@ -421,6 +517,8 @@ def main():
                     help="serving ensemble over the full 32x32x8..128x128x32 range")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
                     help="precision arms to time (the JSON line needs both)")
+    ap.add_argument("--adaptive-sweep", action="store_true",
+                    help="only run Alg. 3's mu sweep on the 60x220x85 sequence and print it")
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the first timed region with cudaProfilerStart/Stop (for ncu)")
     args = ap.parse_args()
@@ -439,6 +537,11 @@ def main():
     barrier(world)
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
+    if args.adaptive_sweep:
+        res = adaptive_sweep(cpr, torch, stream)
+        if rank == 0:
+            print(json.dumps({"adaptive_sweep": res}), flush=True)
+        return
 
     seq_host = host_sequence(seed_offset=rank)
 
@@ -511,6 +614,11 @@ def main():
         if n:
             cb = sum(cgs_bytes(N, cycle_steps(st["iters"], 30)) for st in r["stats"])
             out["cgs"] = {"steps": n, "avg_us": 1000 * ms / n, "gbs": cb / (ms * 1e-3) / 1e9}
+        n, ms = fam[cpr.PROF_SMOOTH0]
+        if n:
+            sb = smooth0_bytes(lv[0], sv)
+            out["smooth0"] = {"launches": n, "avg_us": 1000 * ms / n, "bytes_per_launch": sb,
+                              "gbs": sb / (ms / n * 1e-3) / 1e9}
         n, ms = fam[cpr.PROF_RESID2]
         if n:
             rb = nnzb * (3 * sv + 4) + nb * (4 + 3 * 8 + 3 * sv) + nnzb * sv
@@ -520,12 +628,19 @@ def main():
 
     f32 = fam_report(r32, 4)
     f64 = fam_report(r64, 8)
-    sp = f64.get("spmv", {})
-    roof = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV, w = A z_j)", "bound": "hbm",
-            "achieved": sp.get("gbs"), "peak": hbm, "unit": "GB/s",
-            "frac": (sp.get("gbs") / hbm) if sp.get("gbs") else None,
+    sm0 = f32.get("smooth0", {})
+    roof = {"kernel": "k_smooth_color on the finest pressure level (multi-color GS color sweep, FP32)",
+            "bound": "hbm", "achieved": sm0.get("gbs"), "peak": hbm, "unit": "GB/s",
+            "frac": (sm0.get("gbs") / hbm) if sm0.get("gbs") else None,
             "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
-            "bytes_per_launch": spmv_bytes(nb, nnzb)}
+            "bytes_per_launch": sm0.get("bytes_per_launch")}
+    sp = f64.get("spmv", {})
+    fp64_peak = 296 * 2 * 2.032e9 / 1e12      # DFMA thread-instructions/cycle x 2 flop x max SM clock
+    spmv_tflops = (18.0 * nnzb / (sp["avg_us"] * 1e-6) / 1e12) if sp.get("avg_us") else None
+    roof_alu = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV)", "bound": "alu", "achieved": spmv_tflops,
+                "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
+                "hbm_gbs": sp.get("gbs"), "hbm_frac": (sp.get("gbs") / hbm) if sp.get("gbs") else None}
 
     def pct(a, q):
         return float(np.percentile(np.array(a), q))
@@ -544,6 +659,8 @@ def main():
         "p50_ms": pct(r32["per_ms"], 50), "p99_ms": pct(r32["per_ms"], 99),
         "iters_mean": statistics.mean(iters32),
         "setups_in_timed_region": sum(s["setup_called"] for s in r32["stats"]),
+        "setup_ms_mean": statistics.mean([s["setup_ms"] for s in r32["stats"] if s["setup_called"]] or [0.0]),
+        "solve_phase_ms_mean": statistics.mean([s["solve_ms"] for s in r32["stats"]]),
         "fp64": {"value": v64, "unit": UNIT, "ms_per_step": t64 / K, "p50_ms": pct(r64["per_ms"], 50),
                  "p99_ms": pct(r64["per_ms"], 99), "iters_mean": statistics.mean(iters64),
                  "setups_in_timed_region": sum(s["setup_called"] for s in r64["stats"])},
@@ -551,8 +668,12 @@ def main():
         "vcycle_gbs": {"fp32": f32.get("vcycle", {}).get("gbs"), "fp64": f64.get("vcycle", {}).get("gbs"),
                        "frac_fp32": (f32.get("vcycle", {}).get("gbs") or 0) / hbm,
                        "frac_fp64": (f64.get("vcycle", {}).get("gbs") or 0) / hbm},
-        "families": {"fp32": f32, "fp64": f64},
+        "families": {"fp32": f32, "fp64": f64,
+                     "note": "CUDA-event brackets per family, from a separate timed region of "
+                             f"{r32['profiled_steps']} steps per arm (bracketed step: "
+                             f"{r32['profiled_ms_per_step']:.2f} ms fp32, {r64['profiled_ms_per_step']:.2f} ms fp64)"},
         "roofline": roof,
+        "roofline_fp64_spmv": roof_alu,
         "gpu_launches": int(r32["launches"]),
         "clocks": clocks,
     }

@@ -90,10 +90,11 @@ typedef struct {
 void cpr_default_opts(cpr_opts *o);
 
 /*
- * Build the handle and the preconditioner B^(1) from A^(1) (Alg. 2 line 1 with
+ * Build the handle and the preconditioner B^(1) from A^(1) (Alg. 2's first setup, with
  * k = 1; Alg. 1's setup: decoupling, AMG hierarchy with Eq. 5.1 colorings,
  * BILU(0)), all on the device.  opts may be NULL for defaults.
- * Returns CPR_ERR_INVALID, _OOM, _SINGULAR or _CUDA on failure (*h = NULL).
+ * Returns CPR_ERR_INVALID (also for an empty system, nb < 1), _OOM, _SINGULAR
+ * or _CUDA on failure (*h = NULL).
  */
 int cpr_setup(cpr_handle **h, const cpr_bsr3 *A, const cpr_opts *opts);
 
@@ -102,7 +103,7 @@ int cpr_setup(cpr_handle **h, const cpr_bsr3 *A, const cpr_opts *opts);
  * operator becomes A^(k); B is kept iff the previous solve took
  * It^(k-1) <= mu steps and the size and pattern are unchanged (Remark 4.2),
  * otherwise B is rebuilt from A^(k).  A kept B keeps the copy of A it was
- * built from for its own second residual (Alg. 1 line 3).
+ * built from for its own second residual (the second residual of Alg. 1).
  */
 int cpr_update(cpr_handle *h, const cpr_bsr3 *A);
 
@@ -232,8 +233,9 @@ uint64_t cpr_launch_count(void);
 #define CPR_PROF_VCYCLE 1    /* one whole V-cycle application (all its launches) */
 #define CPR_PROF_BILU 2      /* one whole BILU(0) forward+backward application */
 #define CPR_PROF_CGS 3       /* one CGS orthogonalisation (dots, reduction, update) */
-#define CPR_PROF_RESID2 4    /* one second-residual launch (Alg. 1 line 3) */
-#define CPR_PROF_NFAMILIES 5
+#define CPR_PROF_RESID2 4    /* one second-residual launch (Alg. 1, second residual) */
+#define CPR_PROF_SMOOTH0 5   /* one multi-color GS color launch on the finest pressure level */
+#define CPR_PROF_NFAMILIES 6
 
 /* enable != 0: time the families above during later solves (adds two event
  * records per bracketed region); 0: stop.  Both reset the accumulators. */

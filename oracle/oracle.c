@@ -26,7 +26,7 @@
  *  R6 second stage: block ILU(0) in (color, index) order of a coloring of the
  *     block graph at theta = 0.
  *  R7 It of Alg. 3 is the number of inner (Arnoldi) steps of the last solve;
- *     a reused B keeps its own copy of A for line 3 of Alg. 1.
+ *     a reused B keeps its own copy of A for the second residual of Alg. 1.
  *  Hash: MurmurHash3's 32-bit finalizer (fmix32), a published mixing function.
  */
 #include "oracle.h"
@@ -59,7 +59,7 @@ struct o_handle {
     int nb, nnzb;
     int *rowptr, *col;
     double *val;   /* outer operator A^(k) */
-    double *pval;  /* the copy of A inside B (Alg. 1 line 3), frozen with B (R7) */
+    double *pval;  /* the copy of A inside B (the second residual of Alg. 1), frozen with B (R7) */
     double *w;     /* decoupling weights, 3 per block row (R1) */
     int nlev;
     level_t lev[MAXLEV];

@@ -301,7 +301,7 @@ class BatchSolver(Solver):
         return xs, [s_.as_dict() for s_ in st]
 
 
-PROF_SPMV, PROF_VCYCLE, PROF_BILU, PROF_CGS, PROF_RESID2 = range(5)
+PROF_SPMV, PROF_VCYCLE, PROF_BILU, PROF_CGS, PROF_RESID2, PROF_SMOOTH0 = range(6)
 
 
 def launch_count() -> int:

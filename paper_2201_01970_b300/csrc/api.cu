@@ -116,38 +116,51 @@ void prof_begin(cpr_handle *h, int family) {
         cudaEvent_t a;
         CK(cudaEventCreate(&a));
         CK(cudaEventRecordWithFlags(a, h->stream, cudaEventRecordExternal));
+        h->prof_open.push_back((int)g.ev_a.size());
         g.ev_a.push_back(a);
+        g.ev_b.push_back(nullptr);
         g.fam.push_back(family);
         return;
     }
-    if (h->ev_n == cpr_handle::kProfSlots) prof_flush(h);
-    int k = h->ev_n;
+    if (h->ev_n == cpr_handle::kProfSlots) {
+        if (!h->prof_open.empty()) {      // no slot free inside an open bracket: drop this one
+            h->prof_open.push_back(-1);
+            return;
+        }
+        prof_flush(h);
+    }
+    int k = h->ev_n++;
     if (!h->ev_a[k]) {
         CK(cudaEventCreate(&h->ev_a[k]));
         CK(cudaEventCreate(&h->ev_b[k]));
     }
     h->ev_fam[k] = family;
+    h->prof_open.push_back(k);
     CK(cudaEventRecord(h->ev_a[k], h->stream));
 }
 
+// Closes the innermost open bracket.
 void prof_end(cpr_handle *h) {
-    if (!h->prof) return;
+    if (!h->prof || h->prof_open.empty()) return;
+    int k = h->prof_open.back();
+    h->prof_open.pop_back();
+    if (k < 0) return;
     if (h->capturing >= 0) {
         auto &g = h->sg[h->capturing];
         cudaEvent_t b;
         CK(cudaEventCreate(&b));
         CK(cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal));
-        g.ev_b.push_back(b);
+        g.ev_b[k] = b;
         return;
     }
-    CK(cudaEventRecord(h->ev_b[h->ev_n], h->stream));
-    h->ev_n++;
+    CK(cudaEventRecord(h->ev_b[k], h->stream));
 }
 
 // Accumulate the event-node brackets of step graph `which` (its last launch has completed).
 void prof_collect_graph(cpr_handle *h, int which) {
     auto &g = h->sg[which];
     for (size_t k = 0; k < g.ev_a.size() && k < g.ev_b.size(); k++) {
+        if (!g.ev_b[k]) continue;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g.ev_a[k], g.ev_b[k]));
         h->prof_cnt[g.fam[k]]++;
@@ -160,17 +173,19 @@ void destroy_step_graphs(cpr_handle *h) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         if (g.graph) cudaGraphDestroy(g.graph);
         for (auto e : g.ev_a) cudaEventDestroy(e);
-        for (auto e : g.ev_b) cudaEventDestroy(e);
+        for (auto e : g.ev_b)
+            if (e) cudaEventDestroy(e);
         g = cpr_handle::StepGraph{};
     }
     h->sg_epoch = -1;
 }
 
+// Accumulates the closed eager brackets (called with no bracket open).
 void prof_flush(cpr_handle *h) {
     if (!h->ev_n) return;
-    CK(cudaEventSynchronize(h->ev_b[h->ev_n - 1]));
     for (int k = 0; k < h->ev_n; k++) {
         float ms = 0.f;
+        CK(cudaEventSynchronize(h->ev_b[k]));
         CK(cudaEventElapsedTime(&ms, h->ev_a[k], h->ev_b[k]));
         h->prof_cnt[h->ev_fam[k]]++;
         h->prof_ms[h->ev_fam[k]] += ms;
@@ -187,6 +202,7 @@ int cpr_profile(cpr_handle *h, int enable) {
     if (!h) return CPR_ERR_INVALID;
     return guarded([&] {
         prof_flush(h);
+        h->prof_open.clear();
         h->prof = enable != 0;
         for (int f = 0; f < CPR_PROF_NFAMILIES; f++) {
             h->prof_cnt[f] = 0;

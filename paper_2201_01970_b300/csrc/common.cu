@@ -1,6 +1,7 @@
 // Shared host utilities: errors, scans, small device reads.
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "cpr_internal.cuh"
 
@@ -9,7 +10,26 @@ namespace cpr {
 void fail(int code, const std::string &what) { throw Error{code, what}; }
 
 static unsigned long long g_launches = 0;
-void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+static thread_local bool t_capturing = false;
+void count_launch() {
+    if (!t_capturing) __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED);
+}
+void count_launches(unsigned long long n) { __atomic_add_fetch(&g_launches, n, __ATOMIC_RELAXED); }
+void set_capturing(bool on) { t_capturing = on; }
+
+unsigned long long graph_kernel_nodes(cudaGraph_t g) {
+    size_t n = 0;
+    CK(cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) CK(cudaGraphGetNodes(g, nodes.data(), &n));
+    unsigned long long k = 0;
+    for (size_t i = 0; i < n; i++) {
+        cudaGraphNodeType t;
+        CK(cudaGraphNodeGetType(nodes[i], &t));
+        if (t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
 unsigned long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 void check_cuda(cudaError_t e, const char *expr, const char *file, int line) {

@@ -24,7 +24,10 @@ struct Error {
 [[noreturn]] void fail(int code, const std::string &what);
 void check_cuda(cudaError_t e, const char *expr, const char *file, int line);
 #define CK(x) ::cpr::check_cuda((x), #x, __FILE__, __LINE__)
-void count_launch();
+void count_launch();                      // one kernel launched (not counted while capturing)
+void count_launches(unsigned long long n); // n kernels launched through a graph
+void set_capturing(bool on);              // this thread is capturing a graph
+unsigned long long graph_kernel_nodes(cudaGraph_t g);
 #define CK_LAUNCH()                                                                   \
     do {                                                                              \
         ::cpr::count_launch();                                                        \
@@ -157,7 +160,7 @@ struct cpr_handle {
     cpr::DVec<double> val;
     // --- the preconditioner B (frozen between setups) ---
     bool have_B = false;
-    // column 0 of every block of the A that B was built from (Alg. 1 line 3),
+    // column 0 of every block of the A that B was built from (Alg. 1, second residual),
     // rows and columns in BILU positions
     cpr::DVec<int> c0rowptr, c0col;
     cpr::DVec<double> pcol0;
@@ -192,6 +195,7 @@ struct cpr_handle {
     cudaEvent_t ev_a[kProfSlots] = {}, ev_b[kProfSlots] = {};
     int ev_fam[kProfSlots] = {};
     int ev_n = 0;
+    std::vector<int> prof_open;      // open (possibly nested) brackets: slot or graph-event index, -1 = dropped
     long prof_cnt[CPR_PROF_NFAMILIES] = {};
     double prof_ms[CPR_PROF_NFAMILIES] = {};
     // --- graphs of one Arnoldi step (two instances, used on alternate steps) ---
@@ -201,6 +205,7 @@ struct cpr_handle {
         cudaGraphExec_t exec = nullptr;
         std::vector<cudaEvent_t> ev_a, ev_b;   // event-record nodes (profiling)
         std::vector<int> fam;
+        unsigned long long kernels = 0;        // kernel nodes: launches per graph launch
     } sg[2];
     int sg_epoch = -1;
     bool sg_prof = false;

@@ -125,7 +125,7 @@ __global__ void k_pressure_matrix(int nb, const int *rowptr, const double *val, 
     }
 }
 
-// Column 0 of every block of A (the copy B keeps for Alg. 1 line 3), with rows
+// Column 0 of every block of A (the copy B keeps for the second residual of Alg. 1), with rows
 // taken in position order and columns renumbered to positions.  Count pass
 // (crow == nullptr: row lengths) or fill pass.
 __global__ void k_col0_perm(int nb, const int *order, const int *iperm, const int *rowptr, const int *col,
@@ -570,11 +570,59 @@ constexpr int kHashMax = 512;      // distinct columns handled in shared memory
 constexpr int kHashWarps = 4;
 constexpr int kEmpty = -1;
 
+// Per-warp scratch for enumerating the products of one chunk of 32 A entries:
+// product t of the chunk belongs to entry e with off[e] <= t < off[e + 1] and
+// reads B entry st[e] + t - off[e].
+struct ProdChunk {
+    int off[33];
+    int st[32];
+    double av[32];
+};
+
+// Loads one chunk of row entries [a0, min(a0 + 32, b)) and scans their B row
+// lengths; returns the chunk's product count.
+__device__ __forceinline__ int load_chunk(int a0, int b, const int *ac, const double *av, const int *br,
+                                          ProdChunk &pc, int lane) {
+    int p = a0 + lane, len = 0, st = 0;
+    double v = 0.0;
+    if (p < b) {
+        int k = ac[p];
+        st = br[k];
+        len = br[k + 1] - st;
+        if (av) v = av[p];
+    }
+    int inc = len;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    pc.off[lane] = inc - len;
+    pc.st[lane] = st;
+    pc.av[lane] = v;
+    int tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane == 31) pc.off[32] = tot;
+    __syncwarp();
+    return tot;
+}
+
+// The chunk entry that product t belongs to (the last e with off[e] <= t).
+__device__ __forceinline__ int chunk_owner(const ProdChunk &pc, int t) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pc.off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Insert every candidate column of row i into a table of *cap slots (sized
 // from the row's candidate count, 32..kHashCap); returns the distinct count,
-// or kHashMax+1 when the row is too large for the shared path.
+// or kHashMax+1 when the row is too large for the shared path.  All products
+// of a chunk of 32 A entries are enumerated at once (one per lane), so the
+// row costs one chain of dependent loads per chunk, not one per A entry.
 __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, const int *bc, int *tab,
-                        int *cnt, int lane, int *cap_out) {
+                        int *cnt, int lane, int *cap_out, ProdChunk &pc) {
     int a = ar[i], b = ar[i + 1];
     int cand = 0;
     for (int p = a + lane; p < b; p += 32) {
@@ -590,10 +638,11 @@ __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, cons
     __syncwarp();
     bool overflow = false;
     int limit = min(kHashMax, cap / 2 + cap / 4);
-    for (int p = a + lane; p < b; p += 32) {
-        int k = ac[p];
-        for (int q = br[k]; q < br[k + 1] && !overflow; q++) {
-            int J = bc[q];
+    for (int a0 = a; a0 < b; a0 += 32) {
+        int tot = load_chunk(a0, b, ac, nullptr, br, pc, lane);
+        for (int t = lane; t < tot && !overflow; t += 32) {
+            int e = chunk_owner(pc, t);
+            int J = bc[pc.st[e] + t - pc.off[e]];
             unsigned slot = ((unsigned)J * 2654435761u) & (cap - 1);
             for (int probe = 0; probe < cap; probe++) {
                 int prev = atomicCAS(&tab[slot], kEmpty, J);
@@ -605,6 +654,7 @@ __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, cons
                 slot = (slot + 1) & (cap - 1);
             }
         }
+        __syncwarp();
     }
     __syncwarp();
     int c = *cnt;
@@ -631,11 +681,12 @@ __global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowcount(int n, cons
                                                                      const int *br, const int *bc, int *ucnt) {
     __shared__ int tab[kHashWarps][kHashCap];
     __shared__ int cnt[kHashWarps];
+    __shared__ ProdChunk pcs[kHashWarps];
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     int i = blockIdx.x * kHashWarps + wl;
     if (i >= n) return;
     int cap;
-    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap);
+    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pcs[wl]);
     if (c > kHashMax) {
         c = 0;
         for (long last = -1;;) {
@@ -656,12 +707,14 @@ __global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowfill(int n, const
     __shared__ int keys[kHashWarps][kHashMax];
     __shared__ double acc[kHashWarps][kHashMax];
     __shared__ int cnt[kHashWarps];
+    __shared__ ProdChunk pcs[kHashWarps];
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     int i = blockIdx.x * kHashWarps + wl;
     if (i >= n) return;
     unsigned lt = (1u << lane) - 1u;
     int cap;
-    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap);
+    ProdChunk &pc = pcs[wl];
+    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pc);
     int base = cr[i];
     int a = ar[i], b = ar[i + 1];
     if (c > kHashMax) {
@@ -722,19 +775,35 @@ __global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowfill(int n, const
         cc[base + t] = K[t];
     }
     __syncwarp();
-    // ascending k; the columns of one B row are distinct, so lanes never collide
-    for (int p = a; p < b; p++) {
-        int k = ac[p];
-        double av_p = av[p];
-        for (int q = br[k] + lane; q < br[k + 1]; q += 32) {
-            int J = bc[q];
-            int lo = 0, hi = c;
-            while (lo < hi) {
-                int mid = (lo + hi) >> 1;
-                if (K[mid] < J) lo = mid + 1;
-                else hi = mid;
+    // Products in (A entry, B entry) order, one per lane; each lane finds its
+    // column's slot, then the lanes add in ascending A entry (ascending k)
+    // order.  The columns of one B row are distinct, so lanes of one A entry
+    // never collide, and every C entry is summed in Gustavson's order.
+    for (int a0 = a; a0 < b; a0 += 32) {
+        int tot = load_chunk(a0, b, ac, av, br, pc, lane);
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+            int t = t0 + lane;
+            int e = 32, slot = 0;
+            double prod = 0.0;
+            if (t < tot) {
+                e = chunk_owner(pc, t);
+                int q = pc.st[e] + t - pc.off[e];
+                int J = bc[q];
+                int lo = 0, hi = c;
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (K[mid] < J) lo = mid + 1;
+                    else hi = mid;
+                }
+                slot = lo;
+                prod = __dmul_rn(pc.av[e], bv[q]);
             }
-            S[lo] = __dadd_rn(S[lo], __dmul_rn(av_p, bv[q]));
+            int e_first = __shfl_sync(0xffffffffu, e, 0);
+            int e_last = __shfl_sync(0xffffffffu, e, min(31, tot - 1 - t0));
+            for (int ee = e_first; ee <= e_last; ee++) {
+                if (e == ee) S[slot] = __dadd_rn(S[slot], prod);
+                __syncwarp();
+            }
         }
         __syncwarp();
     }
@@ -1362,7 +1431,7 @@ struct PhaseClock {
     }
 };
 
-// Build B from the handle's current A (Sec. 3.1; the setup lines of Alg. 6 per level).
+// Build B from the handle's current A (Sec. 3.1; the setup steps of Alg. 6 per level).
 void build_preconditioner(cpr_handle *h) {
     free_preconditioner(h);
     cudaStream_t s = h->stream;
@@ -1517,9 +1586,12 @@ void build_preconditioner(cpr_handle *h) {
         h->cinv.alloc((size_t)n * n, s);
         k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
         CK_LAUNCH();
-        int use_smem = (size_t)n * n * sizeof(double) <= 200 * 1024 ? 1 : 0;
+        constexpr int kLuSmemMax = 200 * 1024;
+        int use_smem = (size_t)n * n * sizeof(double) <= kLuSmemMax ? 1 : 0;
         size_t smem = use_smem ? (size_t)n * n * sizeof(double) : 0;
-        if (use_smem) CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // always the same ceiling: handles set up concurrently on other host
+        // threads must never see a smaller limit than the one they launch with
+        if (use_smem) CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuSmemMax));
         DVec<double> lu;
         lu.alloc((size_t)n * n, s);
         if (!use_smem) {

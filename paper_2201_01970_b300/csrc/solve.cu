@@ -19,7 +19,10 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kRedBlocks = 1184;  // 8 CTAs of 256 threads per SM on 148 SMs
-constexpr int kDotGroup = 8;      // vectors per register group in the CGS dot kernel
+constexpr int kDotGroup = 8;      // vectors per register group in the batched dot kernel
+constexpr int kCgsBlocks = 296;   // CGS update: 2 CTAs of 256 threads per SM on 148 SMs (102 registers)
+constexpr int kCgsDotBlocks = 444; // CGS dots: 3 CTAs per SM (80 registers), more loads in flight
+constexpr int kCgsGroup = 16;     // basis vectors per pass of the CGS dot kernel
 
 // Layout of the device scalar block (doubles) for restart length m.
 struct ScalLayout {
@@ -47,7 +50,9 @@ __device__ __forceinline__ int step_of(const int *jptr) { return jptr ? *jptr : 
 // y = A x, or y = b - A x.  G lanes per block row; each lane takes whole 3x3
 // blocks (blocks lane, lane+G, ...) and accumulates its three row sums with
 // one FMA per stored value -- B300's FP64 rate, not its bandwidth, bounds
-// this kernel, so no value costs more than one FP64 instruction.
+// this kernel, so no value costs more than one FP64 instruction.  G = 1 (one
+// thread per block row, no cross-lane FP64 additions at all) measured fastest
+// on B300 at 128x128x32: 119 us against 135 (G = 2), 137 (G = 4), 152 (G = 8).
 template <int G>
 __global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *__restrict__ col,
                             const double *__restrict__ val, const double *__restrict__ x_base,
@@ -428,59 +433,164 @@ __device__ bool arrive_last(int *counter) {
     return last;
 }
 
-// CGS dots of Alg. 2, h_ij = (w, v_i) for i = 0..j: per-block partials, then the
-// last block sums each column over the blocks in a fixed order (deterministic).
-__global__ void k_cgs_dots(long N, const double *__restrict__ V, const double *__restrict__ w,
-                           const int *jptr, double *part, int ldp, double *hcol, int *counter,
-                           const int *done) {
+// Transpose-reduction of 16 per-lane partials over a warp: four halving steps
+// in which each lane keeps one half of its vectors and adds its partner's copy
+// of that half, then one plain step.  Afterwards lanes L and L^1 both hold the
+// warp's sum for vector (L >> 1) & 15.  16 additions per lane instead of the
+// 80 of sixteen butterfly sums; FP64 additions are scarce on B300.
+__device__ __forceinline__ double warp_transpose_sum16(double (&a)[16], int lane) {
+    const unsigned full = 0xffffffffu;
+    bool up = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        double keep = up ? a[k + 8] : a[k], send = up ? a[k] : a[k + 8];
+        a[k] = keep + __shfl_xor_sync(full, send, 16);
+    }
+    up = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        double keep = up ? a[k + 4] : a[k], send = up ? a[k] : a[k + 4];
+        a[k] = keep + __shfl_xor_sync(full, send, 8);
+    }
+    up = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        double keep = up ? a[k + 2] : a[k], send = up ? a[k] : a[k + 2];
+        a[k] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    up = lane & 2;
+    {
+        double keep = up ? a[1] : a[0], send = up ? a[0] : a[1];
+        a[0] = keep + __shfl_xor_sync(full, send, 2);
+    }
+    return a[0] + __shfl_xor_sync(full, a[0], 1);
+}
+
+// CGS dots of Alg. 2, h_ij = (w, v_i) for i = 0..j, sixteen basis vectors per
+// pass over w: per-block partials (warp transpose-sums, then warps summed in
+// order), then the last block sums each column over the blocks in a fixed
+// order (deterministic).
+// acc[k] += sum_q V_{g0+k}[q] w[q] for k < NV over this thread's q.
+template <int NV>
+__device__ __forceinline__ void cgs_dots_pass(long N, const double *__restrict__ Vg, const double *__restrict__ w,
+                                              double (&acc)[kCgsGroup]) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+        double v[NV];
+#pragma unroll
+        for (int k = 0; k < NV; k++) v[k] = Vg[(size_t)k * N + q];
+        double wq = w[q];
+#pragma unroll
+        for (int k = 0; k < NV; k++) acc[k] = fma(v[k], wq, acc[k]);
+    }
+}
+
+#define CPR_NV_DISPATCH(nv, CALL)                                                                   \
+    switch (nv) {                                                                                   \
+    case 1: { constexpr int NV = 1; CALL; break; }   case 2: { constexpr int NV = 2; CALL; break; }   \
+    case 3: { constexpr int NV = 3; CALL; break; }   case 4: { constexpr int NV = 4; CALL; break; }   \
+    case 5: { constexpr int NV = 5; CALL; break; }   case 6: { constexpr int NV = 6; CALL; break; }   \
+    case 7: { constexpr int NV = 7; CALL; break; }   case 8: { constexpr int NV = 8; CALL; break; }   \
+    case 9: { constexpr int NV = 9; CALL; break; }   case 10: { constexpr int NV = 10; CALL; break; } \
+    case 11: { constexpr int NV = 11; CALL; break; } case 12: { constexpr int NV = 12; CALL; break; } \
+    case 13: { constexpr int NV = 13; CALL; break; } case 14: { constexpr int NV = 14; CALL; break; } \
+    case 15: { constexpr int NV = 15; CALL; break; } default: { constexpr int NV = 16; CALL; break; } \
+    }
+
+__global__ void __launch_bounds__(kBlock) k_cgs_dots(long N, const double *__restrict__ V,
+                                                     const double *__restrict__ w, const int *jptr,
+                                                     double *part, int ldp, double *hcol, int *counter,
+                                                     const int *done) {
     if (*done) return;
+    __shared__ double red[kBlock / 32][kCgsGroup];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int nvec = *jptr + 1;
-    for (int g0 = 0; g0 < nvec; g0 += kDotGroup) {
-        double acc[kDotGroup];
+    for (int g0 = 0; g0 < nvec; g0 += kCgsGroup) {
+        double acc[kCgsGroup];
 #pragma unroll
-        for (int k = 0; k < kDotGroup; k++) acc[k] = 0.0;
-        for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
-            double wq = w[q];
-#pragma unroll
-            for (int k = 0; k < kDotGroup; k++)
-                if (g0 + k < nvec) acc[k] += V[(size_t)(g0 + k) * N + q] * wq;
+        for (int k = 0; k < kCgsGroup; k++) acc[k] = 0.0;
+        const double *Vg = V + (size_t)g0 * N;
+        CPR_NV_DISPATCH(min(nvec - g0, kCgsGroup), (cgs_dots_pass<NV>(N, Vg, w, acc)));
+        double v = warp_transpose_sum16(acc, lane);
+        if (!(lane & 1)) red[wid][(lane >> 1) & 15] = v;
+        __syncthreads();
+        if (threadIdx.x < kCgsGroup && g0 + (int)threadIdx.x < nvec) {
+            double t = 0.0;
+            for (int k = 0; k < kBlock / 32; k++) t += red[k][threadIdx.x];
+            part[(size_t)blockIdx.x * ldp + g0 + threadIdx.x] = t;
         }
-#pragma unroll
-        for (int k = 0; k < kDotGroup; k++) {
-            double s = block_sum(acc[k]);
-            if (threadIdx.x == 0 && g0 + k < nvec) part[(size_t)blockIdx.x * ldp + g0 + k] = s;
-        }
+        __syncthreads();
     }
     if (!arrive_last(counter)) return;
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i < nvec; i += nw) {
-        double s = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(part + (size_t)b * ldp + i);
-        s = warp_sum(s);
-        if (lane == 0) hcol[i] = s;
+    for (int i = wid; i < nvec; i += kBlock / 32) {
+        double t = 0.0;
+#pragma unroll 4
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + (size_t)b * ldp + i);
+        t = warp_sum(t);
+        if (lane == 0) hcol[i] = t;
     }
     if (threadIdx.x == 0) *counter = 0;
 }
 
+// wq -= sum_{k < NV} h[k] V_k[q], h in registers.
+template <int NV>
+__device__ __forceinline__ double cgs_update_chunk(long N, const double *__restrict__ Vg, const double (&h)[NV],
+                                                   long q, double wq) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = Vg[(size_t)k * N + q];
+#pragma unroll
+    for (int k = 0; k < NV; k++) wq = fma(-h[k], v[k], wq);
+    return wq;
+}
+
+// w -= V h over this thread's q for NA + NB basis vectors (NB from V_16 on);
+// returns the thread's part of ||w||^2.
+template <int NA, int NB>
+__device__ __forceinline__ double cgs_update_loop(long N, const double *__restrict__ V, const double *h,
+                                                  double *__restrict__ w) {
+    double ha[NA], hb[NB > 0 ? NB : 1];
+#pragma unroll
+    for (int k = 0; k < NA; k++) ha[k] = h[k];
+#pragma unroll
+    for (int k = 0; k < NB; k++) hb[k] = h[kCgsGroup + k];
+    double s = 0.0;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+        double wq = w[q];
+        wq = cgs_update_chunk<NA>(N, V, ha, q, wq);
+        if constexpr (NB > 0)
+            wq = cgs_update_chunk<NB>(N, V + (size_t)kCgsGroup * N, reinterpret_cast<const double(&)[NB]>(hb), q, wq);
+        w[q] = wq;
+        s = fma(wq, wq, s);
+    }
+    return s;
+}
+
 // w -= sum_{i<=j} h_i V_i with per-block partials of ||w||^2; the last block
 // sums them (fixed order) and performs the Givens step of column j (Saad's
-// form): apply the previous rotations, form the new one, update g, estimate
-// |g_{j+1}| / ||r_0|| and take the stop decision of Alg. 2.
-__global__ void k_cgs_update_givens(long N, const double *__restrict__ V, double *__restrict__ w,
-                                    double *part, int *counter, double *sc, int m, int *di) {
+// form) in shared memory: apply the previous rotations, form the new one,
+// update g, estimate |g_{j+1}| / ||r_0|| and take the stop decision of Alg. 2.
+__global__ void __launch_bounds__(kBlock) k_cgs_update_givens(long N, const double *__restrict__ V,
+                                                              double *__restrict__ w, double *part,
+                                                              int *counter, double *sc, int m, int *di) {
     if (di[I_DONE]) return;
     ScalLayout SL{m};
-    __shared__ double sh[kMaxRestart + 1];
+    __shared__ double sh[kMaxRestart + 2], rc[kMaxRestart], rs[kMaxRestart];
     int j = di[I_J];
     int nvec = j + 1;
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) sh[i] = sc[SL.hcol() + i];
     __syncthreads();
     double s = 0.0;
-    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
-        double wq = w[q];
-        for (int i = 0; i < nvec; i++) wq -= sh[i] * V[(size_t)i * N + q];
-        w[q] = wq;
-        s += wq * wq;
+    if (nvec <= kCgsGroup) {
+        CPR_NV_DISPATCH(nvec, (s = cgs_update_loop<NV, 0>(N, V, sh, w)));
+    } else if (nvec <= 2 * kCgsGroup) {
+        CPR_NV_DISPATCH(nvec - kCgsGroup, (s = cgs_update_loop<kCgsGroup, NV>(N, V, sh, w)));
+    } else {
+        for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < N; q += (long)gridDim.x * blockDim.x) {
+            double wq = w[q];
+            for (int i = 0; i < nvec; i++) wq = fma(-sh[i], V[(size_t)i * N + q], wq);
+            w[q] = wq;
+            s = fma(wq, wq, s);
+        }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -488,37 +598,45 @@ __global__ void k_cgs_update_givens(long N, const double *__restrict__ V, double
     if (threadIdx.x >= 32) return;
     int lane = threadIdx.x;
     double hn2 = 0.0;
+#pragma unroll 4
     for (int b = lane; b < (int)gridDim.x; b += 32) hn2 += __ldcg(part + b);
     hn2 = warp_sum(hn2);
-    if (lane != 0) return;
-    *counter = 0;
-    double *sc_ = sc;
-    double hn = sqrt(hn2);
-    for (int i = 0; i <= j; i++) sc_[SL.H(i, j)] = sc_[SL.hcol() + i];
-    sc_[SL.H(j + 1, j)] = hn;
-    for (int i = 0; i < j; i++) {
-        double a = sc_[SL.H(i, j)], c = sc_[SL.H(i + 1, j)];
-        sc_[SL.H(i, j)] = sc_[SL.cs() + i] * a + sc_[SL.sn() + i] * c;
-        sc_[SL.H(i + 1, j)] = -sc_[SL.sn() + i] * a + sc_[SL.cs() + i] * c;
+    for (int i = lane; i < j; i += 32) {
+        rc[i] = sc[SL.cs() + i];
+        rs[i] = sc[SL.sn() + i];
     }
-    double a = sc_[SL.H(j, j)], c = sc_[SL.H(j + 1, j)];
-    double den = sqrt(a * a + c * c);
-    double cj = den == 0.0 ? 1.0 : a / den, sj = den == 0.0 ? 0.0 : c / den;
-    sc_[SL.cs() + j] = cj;
-    sc_[SL.sn() + j] = sj;
-    sc_[SL.H(j, j)] = den;
-    sc_[SL.H(j + 1, j)] = 0.0;
-    double gj = sc_[SL.g() + j];
-    sc_[SL.g() + j + 1] = -sj * gj;
-    sc_[SL.g() + j] = cj * gj;
-    double est = fabs(sc_[SL.g() + j + 1]) / sc_[SL.norm0()];
-    sc_[SL.est()] = est;
-    sc_[SL.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
-    di[I_K] = j + 1;
-    di[I_J] = j + 1;
-    bool brk = !isfinite(hn) || !isfinite(est);
-    if (brk) di[I_BREAK] = 1;
-    if (brk || hn == 0.0 || est < sc_[SL.rtol()] || j + 1 >= m) di[I_DONE] = 1;
+    __syncwarp();
+    double hn = sqrt(hn2);
+    if (lane == 0) {
+        *counter = 0;
+        sh[j + 1] = hn;
+        for (int i = 0; i < j; i++) {
+            double a = sh[i], c = sh[i + 1];
+            sh[i] = rc[i] * a + rs[i] * c;
+            sh[i + 1] = -rs[i] * a + rc[i] * c;
+        }
+        double a = sh[j], c = sh[j + 1];
+        double den = sqrt(a * a + c * c);
+        double cj = den == 0.0 ? 1.0 : a / den, sj = den == 0.0 ? 0.0 : c / den;
+        sc[SL.cs() + j] = cj;
+        sc[SL.sn() + j] = sj;
+        sh[j] = den;
+        sh[j + 1] = 0.0;
+        double gj = sc[SL.g() + j];
+        double gn = -sj * gj;
+        sc[SL.g() + j + 1] = gn;
+        sc[SL.g() + j] = cj * gj;
+        double est = fabs(gn) / sc[SL.norm0()];
+        sc[SL.est()] = est;
+        sc[SL.inv_hn()] = hn > 0.0 ? 1.0 / hn : 0.0;
+        di[I_K] = j + 1;
+        di[I_J] = j + 1;
+        bool brk = !isfinite(hn) || !isfinite(est);
+        if (brk) di[I_BREAK] = 1;
+        if (brk || hn == 0.0 || est < sc[SL.rtol()] || j + 1 >= m) di[I_DONE] = 1;
+    }
+    __syncwarp();
+    for (int i = lane; i <= j + 1; i += 32) sc[SL.H(i, j)] = sh[i];
 }
 
 // V_{j+1} = w / h_{j+1,j} (after k_givens advanced the step index to j+1).
@@ -671,11 +789,14 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
             CK_LAUNCH();
         } else {
             long thr = std::max<long>((long)(c1 - c0) * L.gA, pd.p1 - pd.p0);
+            bool fine = &L == &h->lev[0];
+            if (fine) prof_begin(h, CPR_PROF_SMOOTH0);
             CPR_LANES_DISPATCH(L.gA, (k_smooth_color<T, G><<<blocks_for(thr), kBlock, 0, s>>>(
                                          c0, c1, pd.p0, pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L),
                                          Vals<T>::b(L), Vals<T>::dinv(L), Vals<T>::x(L),
                                          Vals<T>::s(L, pd.k), Vals<T>::s(L, k), done)));
             CK_LAUNCH();
+            if (fine) prof_end(h);
         }
         pd = Pending{c0, c1, k};
     }
@@ -760,7 +881,10 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     }
 }
 
-constexpr int kSpmvLanes = 4;      // outer BSR SpMV (lanes per block row)
+#ifndef CPR_SPMV_LANES
+#define CPR_SPMV_LANES 1
+#endif
+constexpr int kSpmvLanes = CPR_SPMV_LANES;  // outer BSR SpMV (lanes per block row)
 constexpr int kResidLanes = 2;     // second residual
 
 template <class T>
@@ -904,10 +1028,10 @@ void record_step(cpr_handle *h) {
     prof_end(h);
     // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||, Givens
     prof_begin(h, CPR_PROF_CGS);
-    k_cgs_dots<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, sc + SL.hcol(),
+    k_cgs_dots<<<kCgsDotBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, sc + SL.hcol(),
                                              di + I_CNT_DOT, done);
     CK_LAUNCH();
-    k_cgs_update_givens<<<kRedBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, h->red.p + (size_t)kRedBlocks * ldp,
+    k_cgs_update_givens<<<kCgsBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, h->red.p + (size_t)kCgsDotBlocks * ldp,
                                                       di + I_CNT_UPD, sc, m, di);
     CK_LAUNCH();
     prof_end(h);
@@ -923,17 +1047,21 @@ void ensure_step_graphs(cpr_handle *h) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         h->capturing = k;
+        set_capturing(true);
         try {
             record_step(h);
         } catch (...) {
             h->capturing = -1;
+            set_capturing(false);
             cudaStreamEndCapture(h->stream, &g);
             if (g) cudaGraphDestroy(g);
             throw;
         }
         h->capturing = -1;
+        set_capturing(false);
         CK(cudaStreamEndCapture(h->stream, &g));
         h->sg[k].graph = g;
+        h->sg[k].kernels = graph_kernel_nodes(g);
         CK(cudaGraphInstantiate(&h->sg[k].exec, g, 0));
     }
     h->sg_epoch = h->epoch;
@@ -1002,6 +1130,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
         };
         for (int j = 0; j < m && !stop; j++) {
             CK(cudaGraphLaunch(h->sg[j & 1].exec, s));
+            count_launches(h->sg[j & 1].kernels);
             CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
             CK(cudaEventRecord(h->step_done[j & 1], s));
             launched = j + 1;
@@ -1378,16 +1507,20 @@ int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st) {
         for (int k = 0; k < 2; k++) {
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            set_capturing(true);
             try {
                 record_step_batch(h);
             } catch (...) {
+                set_capturing(false);
                 cudaStreamEndCapture(s, &g);
                 if (g) cudaGraphDestroy(g);
                 h->prof = prof;
                 throw;
             }
+            set_capturing(false);
             CK(cudaStreamEndCapture(s, &g));
             h->sgb[k].graph = g;
+            h->sgb[k].kernels = graph_kernel_nodes(g);
             CK(cudaGraphInstantiate(&h->sgb[k].exec, g, 0));
         }
         h->prof = prof;
@@ -1411,6 +1544,7 @@ int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st) {
         bool stop = false;
         for (int j = 0; j < m && !stop; j++) {
             CK(cudaGraphLaunch(h->sgb[j & 1].exec, s));
+            count_launches(h->sgb[j & 1].kernels);
             CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
             CK(cudaEventRecord(h->step_done[j & 1], s));
             if (j >= 1) {

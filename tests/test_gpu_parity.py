@@ -201,6 +201,11 @@ def test_edge_cases(torch, cpr):
     g = cpr.Solver(J1)
     x, st = g.solve(J1.b.copy())
     assert st["converged"] and rel(x, np.linalg.solve(J1.to_dense(), J1.b)) < 1e-12
+    # an empty system is rejected
+    J0 = bs.Jacobian(0, np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0), np.zeros(0))
+    with pytest.raises(cpr.CprError) as e:
+        cpr.Solver(J0)
+    assert e.value.code == cpr.CPR_ERR_INVALID
     J = bs.tiny()
     g = cpr.Solver(DevJ(torch, J))
     # zero right-hand side: no iterations, x = 0
