@@ -386,7 +386,7 @@ def serve_arm(full: bool):
     return m
 
 
-def adaptive_sweep(cpr, torch, stream, mus=(0, 10, 20, 30, 40), nseq=10):
+def adaptive_sweep(cpr, torch, stream, mus=(0, 10, 20, 30, 40, 50, 60, 100), nseq=10):
     """Alg. 3 on a 10-Jacobian drifting Newton sequence of the 60x220x85 banded
     workload, per threshold mu and per preconditioner precision: total device
     time of the sequence (update + solve per step; the first setup, done at

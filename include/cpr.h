@@ -72,6 +72,10 @@ typedef struct {
     int max_levels;     /* default 20 */
     uint64_t seed;      /* hash seed of coloring and C/F splitting; default 0 */
     void *stream;       /* cudaStream_t; NULL = the handle creates its own */
+    int pdl;            /* 1: the kernels of a B application use programmatic dependent launch,
+                           each loading its setup-time operands while its predecessor runs;
+                           0 (default, measured as fast on B300): plain stream order.  Results
+                           are identical either way. */
 } cpr_opts;
 
 typedef struct {

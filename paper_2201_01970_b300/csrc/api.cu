@@ -36,7 +36,8 @@ void check_opts(const cpr_opts &o) {
     bool ok = o.restart >= 1 && o.restart <= kMaxRestart && o.max_restarts >= 1 && o.pre >= 0 &&
               o.post >= 0 && o.coarse_max >= 1 && o.coarse_max <= kMaxCoarse && o.max_levels >= 1 &&
               o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
-              o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1);
+              o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
+              (o.pdl == 0 || o.pdl == 1);
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -233,6 +234,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->max_levels = 20;
     o->seed = 0;
     o->stream = nullptr;
+    o->pdl = 0;
 }
 
 const char *cpr_strerror(int code) {

@@ -239,16 +239,16 @@ __global__ void k_scatter_t(int n, const int *rowptr, const int *col, const doub
     }
 }
 
-// Sort each row by column: rows of up to 32 entries in registers, longer
-// rows by insertion sort in place (rows of transposes are short).
+// Sort each row by column: rows of up to 32 entries in registers (one thread
+// per row); longer rows are left to k_sort_long_rows.
 constexpr int kRegSort = 32;
 __global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
     int L = b - a;
-    if (L <= 1) return;
-    if (L <= kRegSort) {
+    if (L <= 1 || L > kRegSort) return;
+    {
         int c[kRegSort];
         double v[kRegSort];
 #pragma unroll
@@ -280,17 +280,70 @@ __global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
             }
         return;
     }
-    for (int p = a + 1; p < b; p++) {
-        int c = col[p];
-        double v = val ? val[p] : 0.0;
-        int q = p - 1;
-        while (q >= a && col[q] > c) {
-            col[q + 1] = col[q];
-            if (val) val[q + 1] = val[q];
-            q--;
+}
+
+// Rows longer than kRegSort: one warp per row, bitonic sort of (column, value)
+// pairs in shared memory (rows up to kLongSort entries), grid-stride over rows.
+// Rows beyond kLongSort (none in practice) take a serial insertion sort.
+constexpr int kLongSort = 1024;
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_long_rows(int n, const int *rowptr, int *col,
+                                                                     double *val) {
+    __shared__ int sk[kSortWarps][kLongSort];
+    __shared__ double sv[kSortWarps][kLongSort];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int *K = sk[wl];
+    double *Vv = sv[wl];
+    for (int i = blockIdx.x * kSortWarps + wl; i < n; i += gridDim.x * kSortWarps) {
+        int a = rowptr[i], b = rowptr[i + 1];
+        int L = b - a;
+        if (L <= kRegSort) continue;
+        if (L > kLongSort) {
+            if (lane == 0)
+                for (int p = a + 1; p < b; p++) {
+                    int c = col[p];
+                    double v = val ? val[p] : 0.0;
+                    int q = p - 1;
+                    while (q >= a && col[q] > c) {
+                        col[q + 1] = col[q];
+                        if (val) val[q + 1] = val[q];
+                        q--;
+                    }
+                    col[q + 1] = c;
+                    if (val) val[q + 1] = v;
+                }
+            __syncwarp();
+            continue;
         }
-        col[q + 1] = c;
-        if (val) val[q + 1] = v;
+        int P = 64;
+        while (P < L) P <<= 1;
+        for (int t = lane; t < P; t += 32) {
+            K[t] = t < L ? col[a + t] : INT_MAX;
+            Vv[t] = (t < L && val) ? val[a + t] : 0.0;
+        }
+        __syncwarp();
+        for (int size = 2; size <= P; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < P / 2; t += 32) {
+                    int x = (t / stride) * 2 * stride + (t % stride);
+                    int y = x + stride;
+                    bool up = (x & size) == 0;
+                    int u = K[x], v = K[y];
+                    if ((u > v) == up) {
+                        K[x] = v;
+                        K[y] = u;
+                        double tv = Vv[x];
+                        Vv[x] = Vv[y];
+                        Vv[y] = tv;
+                    }
+                }
+                __syncwarp();
+            }
+        for (int t = lane; t < L; t += 32) {
+            col[a + t] = K[t];
+            if (val) val[a + t] = Vv[t];
+        }
+        __syncwarp();
     }
 }
 
@@ -1246,6 +1299,9 @@ void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, cons
     CK_LAUNCH();
     if (ncol) {
         k_sort_rows<<<grid_for(ncol, kBlock), kBlock, 0, s>>>(ncol, trow.p, tcol.p, tval ? tval->p : nullptr);
+        CK_LAUNCH();
+        k_sort_long_rows<<<grid_for(ncol, kSortWarps, 148 * 8), kSortWarps * 32, 0, s>>>(
+            ncol, trow.p, tcol.p, tval ? tval->p : nullptr);
         CK_LAUNCH();
     }
 }

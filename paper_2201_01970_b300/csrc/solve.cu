@@ -45,6 +45,57 @@ enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_CNT_DOT = 5, I_C
 
 __device__ __forceinline__ int step_of(const int *jptr) { return jptr ? *jptr : 0; }
 
+// ------------------------------------------------ programmatic dependent launch
+//
+// The kernels of one B application run as a chain in which each kernel's
+// inputs are the previous kernels' outputs, but most of what they read -- the
+// matrices' patterns and values, 1/a_ii, the permutations -- was fixed at
+// setup.  Each kernel loads that static part first, then waits for its
+// predecessor (griddepcontrol.wait: the predecessor has completed and its
+// writes are visible), then lets its own successor launch.  The successor's
+// static loads thus overlap this kernel's dependent work, and since a kernel
+// lets its successor start only after its own wait returned, everything
+// before the current kernel has completed when a prologue runs.  Without the
+// launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr int kPre = 4;   // row entries per lane loaded before the dependency wait
+
+// The first kPre entries of a lane's share of row i (entries e0+lane, +G, ...).
+template <class T, int G>
+struct RowPre {
+    int e0 = 0, e1 = 0;
+    int c[kPre];
+    T v[kPre];
+    __device__ __forceinline__ void load(const int *__restrict__ rowptr, const int *__restrict__ col,
+                                         const T *__restrict__ val, int i, int lane, bool active) {
+        if (active) {
+            e0 = rowptr[i];
+            e1 = rowptr[i + 1];
+        }
+#pragma unroll
+        for (int u = 0; u < kPre; u++) {
+            int p = e0 + lane + u * G;
+            bool in = p < e1;
+            c[u] = in ? col[p] : 0;
+            v[u] = in ? val[p] : (T)0;
+        }
+    }
+    // sum over the lane's entries in ascending order of v_p * xv(col_p)
+    template <class XV>
+    __device__ __forceinline__ T dot(const int *__restrict__ col, const T *__restrict__ val, int lane,
+                                     XV xv) const {
+        T s = 0;
+#pragma unroll
+        for (int u = 0; u < kPre; u++)
+            if (e0 + lane + u * G < e1) s += v[u] * xv(c[u]);
+#pragma unroll 4
+        for (int p = e0 + lane + kPre * G; p < e1; p += G) s += val[p] * xv(col[p]);
+        return s;
+    }
+};
+
 // --------------------------------------------------------------- BSR SpMV
 
 // y = A x, or y = b - A x.  G lanes per block row; each lane takes whole 3x3
@@ -108,12 +159,21 @@ __global__ void k_bsr3_spmv(int nb, const int *__restrict__ rowptr, const int *_
 template <class T>
 __global__ void k_restrict(int nb, const int *order, const double *v_base, long ld, const int *jptr,
                            const T *w, T *rp, const int *done) {
-    if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nb) return;
-    int i = order ? order[t] : t;
+    bool active = t < nb;
+    int i = 0;
+    T w0 = 0, w1 = 0, w2 = 0;
+    if (active) {
+        i = order ? order[t] : t;
+        w0 = w[3 * i];
+        w1 = w[3 * i + 1];
+        w2 = w[3 * i + 2];
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (!active || (done && *done)) return;
     const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
-    rp[t] = (w[3 * i] * (T)v[0] + w[3 * i + 1] * (T)v[1]) + w[3 * i + 2] * (T)v[2];
+    rp[t] = (w0 * (T)v[0] + w1 * (T)v[1]) + w2 * (T)v[2];
 }
 
 // Second residual of Alg. 1: r = v - A z with z = Pi_P e_P, so only column 0 of
@@ -125,14 +185,40 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
                                 const T *__restrict__ c0, const T *__restrict__ ep, const int *__restrict__ border,
                                 const double *v_base, long ld, const int *jptr, T *__restrict__ r,
                                 const int *done) {
-    if (done && *done) return;
     long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     int row = (int)(tid / G), lane = (int)(tid % G);
     bool active = row < nb;
+    int e0 = 0, e1 = 0, brow = 0;
+    int cj[kPre];
+    T cv[kPre][3];
+    if (active) {
+        e0 = rowptr[row];
+        e1 = rowptr[row + 1];
+        brow = border[row];
+    }
+#pragma unroll
+    for (int u = 0; u < kPre; u++) {
+        int p = e0 + lane + u * G;
+        bool in = p < e1;
+        cj[u] = in ? col[p] : 0;
+        cv[u][0] = in ? c0[3 * (size_t)p] : (T)0;
+        cv[u][1] = in ? c0[3 * (size_t)p + 1] : (T)0;
+        cv[u][2] = in ? c0[3 * (size_t)p + 2] : (T)0;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
     T a0 = 0, a1 = 0, a2 = 0;
     if (active) {
-        int e = rowptr[row + 1];
-        for (int p = rowptr[row] + lane; p < e; p += G) {
+#pragma unroll
+        for (int u = 0; u < kPre; u++)
+            if (e0 + lane + u * G < e1) {
+                T ej = ep[cj[u]];
+                a0 = fma(cv[u][0], ej, a0);
+                a1 = fma(cv[u][1], ej, a1);
+                a2 = fma(cv[u][2], ej, a2);
+            }
+        for (int p = e0 + lane + kPre * G; p < e1; p += G) {
             T ej = ep[col[p]];
             const T *c = c0 + 3 * (size_t)p;
             a0 = fma(c[0], ej, a0);
@@ -147,7 +233,7 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
         a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
     }
     if (active && lane == 0) {
-        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)border[row];
+        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)brow;
         r[3 * (size_t)row] = (T)v[0] - a0;
         r[3 * (size_t)row + 1] = (T)v[1] - a1;
         r[3 * (size_t)row + 2] = (T)v[2] - a2;
@@ -168,17 +254,6 @@ __device__ __forceinline__ T group_sum(T v, int G) {
     return v;
 }
 
-// sum_{p in row i, strided by G from lane} val[p] * xv(col[p]), with the loads
-// of four entries issued before their products are accumulated.
-template <class T, int G, class XV>
-__device__ __forceinline__ T row_dot(const int *__restrict__ col, const T *__restrict__ val, int p0, int p1,
-                                     int lane, XV xv) {
-    T s = 0;
-#pragma unroll 4
-    for (int p = p0 + lane; p < p1; p += G) s += val[p] * xv(col[p]);
-    return s;
-}
-
 template <class T>
 __device__ __forceinline__ T xval(const T *x, const T *sp, int p0, int p1, int j) {
     return (j >= p0 && j < p1) ? sp[j] : x[j];
@@ -189,10 +264,13 @@ __device__ __forceinline__ T xval(const T *x, const T *sp, int p0, int p1, int j
 template <class T>
 __global__ void k_smooth_first(int n, int c0, int c1, const T *b, const T *dinv, T *x, T *sc,
                                const int *done) {
-    if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    if (t >= c0 && t < c1) sc[t] = b[t] * dinv[t];
+    bool mine = t >= c0 && t < c1;
+    T di = mine ? dinv[t] : (T)0;
+    pdl_wait();
+    pdl_trigger();
+    if (t >= n || (done && *done)) return;
+    if (mine) sc[t] = b[t] * di;
     else x[t] = (T)0;
 }
 
@@ -200,41 +278,49 @@ __global__ void k_smooth_first(int n, int c0, int c1, const T *b, const T *dinv,
 template <class T, int G>
 __global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__restrict__ rowptr,
                                const int *__restrict__ col, const T *__restrict__ val,
-                               const T *__restrict__ b, const T *__restrict__ dinv, T *x,
+                               const T *b, const T *__restrict__ dinv, T *x,
                                const T *sp, T *sc, const int *done) {
-    if (done && *done) return;
     long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long nthr = (long)gridDim.x * blockDim.x;
-    for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
     long g = tid / G;
     int lane = (int)(tid % G);
     bool active = g < c1 - c0;
     int i = c0 + (int)g;
+    RowPre<T, G> rp;
+    rp.load(rowptr, col, val, i, lane, active);
+    T di = active ? dinv[i] : (T)0;
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
+    for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
     T s = 0;
-    if (active)
-        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
+    if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
-    if (active && lane == 0) sc[i] = (b[i] - s) * dinv[i];
+    if (active && lane == 0) sc[i] = (b[i] - s) * di;
 }
 
 // r = b - A x with x's pending range read from sp (and committed into x).
 template <class T, int G>
 __global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ rowptr,
                                const int *__restrict__ col, const T *__restrict__ val,
-                               const T *__restrict__ diag, const T *__restrict__ b, T *x, const T *sp,
+                               const T *__restrict__ diag, const T *b, T *x, const T *sp,
                                T *r, const int *done) {
-    if (done && *done) return;
     long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long nthr = (long)gridDim.x * blockDim.x;
     long g = tid / G;
     int lane = (int)(tid % G);
     bool active = g < n;
     int i = (int)g;
+    RowPre<T, G> rp;
+    rp.load(rowptr, col, val, i, lane, active);
+    T dg = active ? diag[i] : (T)0;
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
     T s = 0;
-    if (active)
-        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
+    if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
-    if (active && lane == 0) r[i] = b[i] - s - diag[i] * xval(x, sp, p0, p1, i);
+    if (active && lane == 0) r[i] = b[i] - s - dg * xval(x, sp, p0, p1, i);
     // commit after every read of this kernel's own rows is done is not
     // guaranteed across CTAs, so readers above take the pending range from sp
     for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
@@ -246,15 +332,18 @@ template <class T, int G>
 __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
                            const T *__restrict__ val, const T *x, const T *sp, int p0, int p1, T *y,
                            bool add, const int *done) {
-    if (done && *done) return;
     long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long g = tid / G;
     int lane = (int)(tid % G);
     bool active = g < n;
     int i = (int)g;
+    RowPre<T, G> rp;
+    rp.load(rowptr, col, val, i, lane, active);
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
     T s = 0;
-    if (active)
-        s = row_dot<T, G>(col, val, rowptr[i], rowptr[i + 1], lane, [&](int j) { return xval(x, sp, p0, p1, j); });
+    if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
     if (active && lane == 0) y[i] = add ? y[i] + s : s;
 }
@@ -263,22 +352,37 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
 template <class T>
 __global__ void k_commit_natural(int n, const int *order, const T *x, const T *sp, int p0, int p1,
                                  T *out, const int *done) {
-    if (done && *done) return;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    out[order[t]] = xval(x, sp, p0, p1, t);
+    int o = t < n ? order[t] : 0;
+    pdl_wait();
+    pdl_trigger();
+    if (t >= n || (done && *done)) return;
+    out[o] = xval(x, sp, p0, p1, t);
 }
 
 // Coarsest level: x = A_L^-1 b, one warp per row of the row-major inverse.
 template <class T>
 __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b, T *x,
                                const int *done) {
-    if (done && *done) return;
+    constexpr int kPreC = 8;   // row entries per lane loaded before the wait (n <= 256)
     long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     int i = (int)(tid >> 5), lane = (int)(tid & 31);
+    double a[kPreC];
+#pragma unroll
+    for (int u = 0; u < kPreC; u++) {
+        int j = lane + 32 * u;
+        a[u] = (i < n && j < n) ? inv[(size_t)i * n + j] : 0.0;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
     double s = 0.0;
-    if (i < n)
-        for (int j = lane; j < n; j += 32) s += inv[(size_t)i * n + j] * (double)b[j];
+    if (i < n) {
+#pragma unroll
+        for (int u = 0; u < kPreC; u++)
+            if (lane + 32 * u < n) s += a[u] * (double)b[lane + 32 * u];
+        for (int j = lane + 32 * kPreC; j < n; j += 32) s += inv[(size_t)i * n + j] * (double)b[j];
+    }
     s = group_sum(s, 32);
     if (i < n && lane == 0) x[i] = (T)s;
 }
@@ -292,13 +396,40 @@ template <class T>
 __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
                            const int *__restrict__ lc, const T *__restrict__ lv, T *y,
                            const int *done) {
-    if (done && *done) return;
+    constexpr int kPreB = 2;   // blocks loaded before the wait
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
+    bool active = t < cnt;
     int i = c0 + t;
+    int e0 = 0, e1 = 0;
+    if (active) {
+        e0 = lr[i];
+        e1 = lr[i + 1];
+    }
+    int cj[kPreB];
+    T Lp[kPreB][9];
+#pragma unroll
+    for (int u = 0; u < kPreB; u++) {
+        bool in = e0 + u < e1;
+        cj[u] = in ? lc[e0 + u] : 0;
+#pragma unroll
+        for (int k = 0; k < 9; k++) Lp[u][k] = in ? lv[9 * (size_t)(e0 + u) + k] : (T)0;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (!active || (done && *done)) return;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+#pragma unroll
+    for (int u = 0; u < kPreB; u++)
+        if (e0 + u < e1) {
+            const T *L = Lp[u];
+            const T *yj = y + 3 * (size_t)cj[u];
+            T y0 = yj[0], y1 = yj[1], y2 = yj[2];
+            s0 -= L[0] * y0 + L[1] * y1 + L[2] * y2;
+            s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
+            s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
+        }
 #pragma unroll 4
-    for (int p = lr[i]; p < lr[i + 1]; p++) {
+    for (int p = e0 + kPreB; p < e1; p++) {
         const T *L = lv + 9 * (size_t)p;
         const T *yj = y + 3 * (size_t)lc[p];
         T y0 = yj[0], y1 = yj[1], y2 = yj[2];
@@ -319,13 +450,44 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
                            const int *__restrict__ uc, const T *__restrict__ uv,
                            const T *__restrict__ dinv, T *y, const T *ep, const int *__restrict__ border,
                            double *out_base, long ld, const int *jptr, const int *done) {
-    if (done && *done) return;
+    constexpr int kPreB = 2;   // blocks loaded before the wait
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
+    bool active = t < cnt;
     int i = c0 + t;
+    int e0 = 0, e1 = 0, bi = 0;
+    T D[9];
+    if (active) {
+        e0 = ur[i];
+        e1 = ur[i + 1];
+        bi = border[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) D[k] = active ? dinv[9 * (size_t)i + k] : (T)0;
+    int cj[kPreB];
+    T Up[kPreB][9];
+#pragma unroll
+    for (int u = 0; u < kPreB; u++) {
+        bool in = e0 + u < e1;
+        cj[u] = in ? uc[e0 + u] : 0;
+#pragma unroll
+        for (int k = 0; k < 9; k++) Up[u][k] = in ? uv[9 * (size_t)(e0 + u) + k] : (T)0;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (!active || (done && *done)) return;
     T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+#pragma unroll
+    for (int u = 0; u < kPreB; u++)
+        if (e0 + u < e1) {
+            const T *U = Up[u];
+            const T *zj = y + 3 * (size_t)cj[u];
+            T z0 = zj[0], z1 = zj[1], z2 = zj[2];
+            s0 -= U[0] * z0 + U[1] * z1 + U[2] * z2;
+            s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
+            s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
+        }
 #pragma unroll 4
-    for (int p = ur[i]; p < ur[i + 1]; p++) {
+    for (int p = e0 + kPreB; p < e1; p++) {
         const T *U = uv + 9 * (size_t)p;
         const T *zj = y + 3 * (size_t)uc[p];
         T z0 = zj[0], z1 = zj[1], z2 = zj[2];
@@ -333,14 +495,13 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
         s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
         s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
     }
-    const T *D = dinv + 9 * (size_t)i;
     T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
     T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
     T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
     y[3 * (size_t)i] = z0;
     y[3 * (size_t)i + 1] = z1;
     y[3 * (size_t)i + 2] = z2;
-    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)border[i];
+    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
     out[0] = (double)z0 + (ep ? (double)ep[i] : 0.0);
     out[1] = (double)z1;
     out[2] = (double)z2;
@@ -772,6 +933,30 @@ void with_lanes(int g, F f);
 
 inline unsigned blocks_for(long threads) { return (unsigned)std::max<long>(1, (threads + kBlock - 1) / kBlock); }
 
+// Launch one kernel of the B-application chain: with programmatic dependent
+// launch when the handle asks for it (the kernel's prologue may then overlap
+// its predecessor), else in plain stream order.
+template <class... KArgs, class... Args>
+void launch_b(const cpr_handle *h, void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s,
+              Args &&...args) {
+    if (h->opt.pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(block);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    } else {
+        kern<<<grid, block, 0, s>>>(std::forward<Args>(args)...);
+    }
+    CK_LAUNCH();
+}
+
 // One smoothing sweep over the colors of level L (ascending or descending).
 // From zero: the first color writes b/a_ii into staging and zeroes x.
 template <class T>
@@ -784,18 +969,16 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
         int c0 = L.color_off[c], c1 = L.color_off[c + 1];
         int k = 1 - pd.k;
         if (from_zero && t == 0) {
-            k_smooth_first<T><<<blocks_for(n), kBlock, 0, s>>>(n, c0, c1, Vals<T>::b(L), Vals<T>::dinv(L),
-                                                               Vals<T>::x(L), Vals<T>::s(L, k), done);
-            CK_LAUNCH();
+            launch_b(h, k_smooth_first<T>, blocks_for(n), kBlock, s, n, c0, c1, Vals<T>::b(L), Vals<T>::dinv(L),
+                     Vals<T>::x(L), Vals<T>::s(L, k), done);
         } else {
             long thr = std::max<long>((long)(c1 - c0) * L.gA, pd.p1 - pd.p0);
             bool fine = &L == &h->lev[0];
             if (fine) prof_begin(h, CPR_PROF_SMOOTH0);
-            CPR_LANES_DISPATCH(L.gA, (k_smooth_color<T, G><<<blocks_for(thr), kBlock, 0, s>>>(
-                                         c0, c1, pd.p0, pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L),
-                                         Vals<T>::b(L), Vals<T>::dinv(L), Vals<T>::x(L),
-                                         Vals<T>::s(L, pd.k), Vals<T>::s(L, k), done)));
-            CK_LAUNCH();
+            CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_smooth_color<T, G>, blocks_for(thr), kBlock, s, c0, c1, pd.p0,
+                                               pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::b(L),
+                                               Vals<T>::dinv(L), Vals<T>::x(L), Vals<T>::s(L, pd.k),
+                                               Vals<T>::s(L, k), done)));
             if (fine) prof_end(h);
         }
         pd = Pending{c0, c1, k};
@@ -811,9 +994,8 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
     Level &L = h->lev[l];
     int n = L.A.n;
     if (l == (int)h->lev.size() - 1) {
-        k_coarse_solve<T><<<blocks_for((long)n * 32), kBlock, 0, s>>>(n, h->cinv.p, Vals<T>::b(L),
-                                                                       Vals<T>::x(L), done);
-        CK_LAUNCH();
+        launch_b(h, k_coarse_solve<T>, blocks_for((long)n * 32), kBlock, s, n, h->cinv.p, Vals<T>::b(L),
+                 Vals<T>::x(L), done);
         out = Pending{};
         return;
     }
@@ -824,22 +1006,19 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
     }
     for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done);
     long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
-    CPR_LANES_DISPATCH(L.gA, (k_resid_commit<T, G><<<blocks_for(thr), kBlock, 0, s>>>(
-                                 n, pd.p0, pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L),
-                                 Vals<T>::b(L), Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
-    CK_LAUNCH();
+    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+                                       L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), Vals<T>::b(L),
+                                       Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     pd = Pending{};
     Level &C = h->lev[l + 1];
-    CPR_LANES_DISPATCH(L.gR, (k_transfer<T, G><<<blocks_for((long)L.Rp.n * L.gR), kBlock, 0, s>>>(
-                                 L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L),
-                                 0, 0, Vals<T>::b(C), false, done)));
-    CK_LAUNCH();
+    CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s, L.Rp.n,
+                                       L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L), 0, 0,
+                                       Vals<T>::b(C), false, done)));
     Pending cp;
     vcycle<T>(h, l + 1, cp, done);
-    CPR_LANES_DISPATCH(L.gP, (k_transfer<T, G><<<blocks_for((long)n * L.gP), kBlock, 0, s>>>(
-                                 n, L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
-                                 Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
-    CK_LAUNCH();
+    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+                                       L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
+                                       Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
     for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done);
     out = pd;
 }
@@ -852,9 +1031,8 @@ void vcycle_top(cpr_handle *h, T *ep, const int *done) {
     Pending pd;
     vcycle<T>(h, 0, pd, done);
     int n = L0.A.n;
-    k_commit_natural<T><<<blocks_for(n), kBlock, 0, h->stream>>>(n, h->ep_map.p, Vals<T>::x(L0),
-                                                                  Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
-    CK_LAUNCH();
+    launch_b(h, k_commit_natural<T>, blocks_for(n), kBlock, h->stream, n, h->ep_map.p, Vals<T>::x(L0),
+             Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
 }
 
 // BILU(0) solve in place on y (forward by ascending colors, backward by
@@ -864,20 +1042,19 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
                 const int *done) {
     cudaStream_t s = h->stream;
     Bilu &B = h->bilu;
-    for (int c = 0; c < B.ncolors; c++) {
+    // the lowest color has no lower neighbours (L holds lower colors only), so
+    // its forward substitution leaves y unchanged and is skipped
+    for (int c = 1; c < B.ncolors; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bilu_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p,
-                                                               Vals<T>::Lv(h), y, done);
-        CK_LAUNCH();
+        launch_b(h, k_bilu_fwd<T>, grid_for(cnt, kBlock), kBlock, s, B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p,
+                 Vals<T>::Lv(h), y, done);
     }
     for (int c = B.ncolors - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bilu_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p,
-                                                               Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep,
-                                                               B.rows_by_color.p, out_base, ld, jptr, done);
-        CK_LAUNCH();
+        launch_b(h, k_bilu_bwd<T>, grid_for(cnt, kBlock), kBlock, s, B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p,
+                 Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base, ld, jptr, done);
     }
 }
 
@@ -895,9 +1072,8 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     Level &L0 = h->lev[0];
     const int *order0 = h->lev.size() > 1 ? L0.rows_by_color.p : nullptr;
     // r_P = Pi_P^T v
-    k_restrict<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
-                                                          Vals<T>::b(L0), done);
-    CK_LAUNCH();
+    launch_b(h, k_restrict<T>, grid_for(nb, kBlock), kBlock, s, nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
+             Vals<T>::b(L0), done);
     // e_P = B_P r_P (BILU positions)
     prof_begin(h, CPR_PROF_VCYCLE);
     vcycle_top<T>(h, Vals<T>::ep(h), done);
@@ -905,10 +1081,9 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     // r = v - A Pi_P e_P
     long threads = (long)nb * kResidLanes;
     prof_begin(h, CPR_PROF_RESID2);
-    k_prolong_resid<T, kResidLanes><<<(unsigned)((threads + kBlock - 1) / kBlock), kBlock, 0, s>>>(
-        nb, h->c0rowptr.p, h->c0col.p, Vals<T>::c0(h), Vals<T>::ep(h), h->bilu.rows_by_color.p, v_base, v_ld,
-        jptr, Vals<T>::tmp(h), done);
-    CK_LAUNCH();
+    launch_b(h, k_prolong_resid<T, kResidLanes>, (unsigned)((threads + kBlock - 1) / kBlock), kBlock, s, nb,
+             h->c0rowptr.p, h->c0col.p, Vals<T>::c0(h), Vals<T>::ep(h), h->bilu.rows_by_color.p, v_base, v_ld,
+             jptr, Vals<T>::tmp(h), done);
     prof_end(h);
     // z = Pi_P e_P + (LU)^-1 r
     prof_begin(h, CPR_PROF_BILU);
