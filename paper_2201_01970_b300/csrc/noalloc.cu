@@ -12,6 +12,7 @@
 #include <mutex>
 
 #include "cpr_internal.cuh"
+#include "sweeps.cuh"
 
 namespace cpr {
 namespace {
@@ -59,78 +60,31 @@ __global__ void k_load(int nb, const int *order, const double *r, T *y) {
     y[3 * (size_t)t + 2] = (T)src[2];
 }
 
-// Forward substitution of one color's positions [c0, c0 + cnt) on the scratch
-// vector (as cpr_bilu_apply's).
-template <class T>
-__global__ void k_fwd(int c0, int cnt, const int *__restrict__ lr, const int *__restrict__ lc,
-                      const T *__restrict__ lv, T *y) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = c0 + t;
-    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
-    for (int p = lr[i]; p < lr[i + 1]; p++) {
-        const T *L = lv + 9 * (size_t)p;
-        const T *yj = y + 3 * (size_t)lc[p];
-        T y0 = yj[0], y1 = yj[1], y2 = yj[2];
-        s0 -= L[0] * y0 + L[1] * y1 + L[2] * y2;
-        s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
-        s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
-    }
-    y[3 * (size_t)i] = s0;
-    y[3 * (size_t)i + 1] = s1;
-    y[3 * (size_t)i + 2] = s2;
-}
-
-// Backward substitution of one color's positions; writes z (FP64, natural
-// block row order[i]) as well.
-template <class T>
-__global__ void k_bwd(int c0, int cnt, const int *__restrict__ ur, const int *__restrict__ uc,
-                      const T *__restrict__ uv, const T *__restrict__ dinv, T *y, const int *order, double *z) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cnt) return;
-    int i = c0 + t;
-    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
-    for (int p = ur[i]; p < ur[i + 1]; p++) {
-        const T *U = uv + 9 * (size_t)p;
-        const T *zj = y + 3 * (size_t)uc[p];
-        T z0 = zj[0], z1 = zj[1], z2 = zj[2];
-        s0 -= U[0] * z0 + U[1] * z1 + U[2] * z2;
-        s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
-        s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
-    }
-    const T *D = dinv + 9 * (size_t)i;
-    T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
-    T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
-    T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
-    y[3 * (size_t)i] = z0;
-    y[3 * (size_t)i + 1] = z1;
-    y[3 * (size_t)i + 2] = z2;
-    double *zi = z + 3 * (size_t)order[i];
-    zi[0] = (double)z0;
-    zi[1] = (double)z1;
-    zi[2] = (double)z2;
-}
-
 template <class T>
 void sweeps(cpr_handle *h, const double *r, double *z, T *y, const T *lv, const T *uv, const T *dv) {
     cudaStream_t s = h->stream;
     Bilu &B = h->bilu;
     int nb = h->nb;
+    // the same sweep kernels, lane split and color order as cpr_bilu_apply, so
+    // the two entries agree bit for bit
+    constexpr int G = sizeof(T) == 4 ? 4 : 1;
     // every entry of y that the sweeps read is written here first, so no part
     // of the scratch has to start at zero
     k_load<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, r, y);
     CK_LAUNCH();
-    for (int c = 0; c < B.ncolors; c++) {
+    for (int c = 1; c < B.ncolors; c++) {   // the lowest color has no lower neighbours
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_fwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p, lv, y);
+        k_bilu_fwd<T, G><<<grid_for((long)cnt * G, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Lrowptr.p,
+                                                                           B.Lcol.p, lv, y, nullptr);
         CK_LAUNCH();
     }
     for (int c = B.ncolors - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        k_bwd<T><<<grid_for(cnt, kBlock), kBlock, 0, s>>>(B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p, uv, dv, y,
-                                                         B.rows_by_color.p, z);
+        k_bilu_bwd<T, G><<<grid_for((long)cnt * G, kBlock), kBlock, 0, s>>>(
+            B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p, uv, dv, y, nullptr, B.rows_by_color.p, z, 0, nullptr,
+            nullptr);
         CK_LAUNCH();
     }
 }

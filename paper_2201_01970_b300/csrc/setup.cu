@@ -207,6 +207,55 @@ __global__ void k_strength_rs(int n, const int *rowptr, const int *col, const do
     if (!srowptr) out[i] = c;
 }
 
+// Warp-per-row form of the classical strength kernel for levels with long
+// rows (coarse levels average 16-40 entries per row): a row's entries are
+// loaded by all lanes at once instead of one after another by one thread.
+// Same arithmetic (a maximum and comparisons, all exact) and the same output
+// order (ballot compaction in entry order).
+__global__ void k_strength_rs_warp(int n, const int *rowptr, const int *col, const double *val,
+                                   double theta, const int *srowptr, int *out) {
+    int lane = threadIdx.x & 31;
+    int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;
+    int a = rowptr[i], b = rowptr[i + 1];
+    unsigned lt = (1u << lane) - 1u;
+    double aii = 0.0;
+    bool found = false;
+    for (int p = a + lane; p < b; p += 32)
+        if (col[p] == i) {
+            aii = val[p];
+            found = true;
+        }
+    unsigned fm = __ballot_sync(0xffffffffu, found);
+    aii = fm ? __shfl_sync(0xffffffffu, aii, __ffs(fm) - 1) : 0.0;
+    double s = aii < 0.0 ? -1.0 : 1.0;
+    double m = -INFINITY;
+    bool have = false;
+    for (int p = a + lane; p < b; p += 32)
+        if (col[p] != i) {
+            m = fmax(m, -s * val[p]);
+            have = true;
+        }
+    for (int sh = 16; sh > 0; sh >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, sh));
+    have = __any_sync(0xffffffffu, have);
+    int q = srowptr ? srowptr[i] : 0, c = 0;
+    if (have && m > 0.0) {
+        double t = __dmul_rn(theta, m);
+        for (int p0 = a; p0 < b; p0 += 32) {
+            int p = p0 + lane, j = 0;
+            bool keep = false;
+            if (p < b) {
+                j = col[p];
+                keep = j != i && -s * val[p] >= t;
+            }
+            unsigned bm = __ballot_sync(0xffffffffu, keep);
+            if (keep && srowptr) out[q + c + __popc(bm & lt)] = j;
+            c += __popc(bm);
+        }
+    }
+    if (!srowptr && lane == 0) out[i] = c;
+}
+
 // Off-diagonal block pattern (the BILU graph at theta = 0).
 __global__ void k_offdiag_pattern(int n, const int *rowptr, const int *col, const int *srowptr,
                                   int *out) {
@@ -240,13 +289,14 @@ __global__ void k_scatter_t(int n, const int *rowptr, const int *col, const doub
 }
 
 // Sort each row by column: rows of up to 32 entries in registers (one thread
-// per row); longer rows are left to k_sort_long_rows.
+// per row); longer rows are listed (in any order) for k_sort_long_rows.
 constexpr int kRegSort = 32;
-__global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
+__global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val, int *longrows, int *nlong) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
     int L = b - a;
+    if (L > kRegSort) longrows[atomicAdd(nlong, 1)] = i;
     if (L <= 1 || L > kRegSort) return;
     {
         int c[kRegSort];
@@ -282,22 +332,24 @@ __global__ void k_sort_rows(int n, const int *rowptr, int *col, double *val) {
     }
 }
 
-// Rows longer than kRegSort: one warp per row, bitonic sort of (column, value)
-// pairs in shared memory (rows up to kLongSort entries), grid-stride over rows.
-// Rows beyond kLongSort (none in practice) take a serial insertion sort.
+// The listed rows (longer than kRegSort): one warp per row, bitonic sort of
+// (column, value) pairs in shared memory (rows up to kLongSort entries),
+// grid-stride over the list.  Rows beyond kLongSort (none in practice) take a
+// serial insertion sort.
 constexpr int kLongSort = 1024;
 constexpr int kSortWarps = 4;
-__global__ void __launch_bounds__(kSortWarps * 32) k_sort_long_rows(int n, const int *rowptr, int *col,
-                                                                     double *val) {
+__global__ void __launch_bounds__(kSortWarps * 32) k_sort_long_rows(const int *longrows, const int *nlong,
+                                                                     const int *rowptr, int *col, double *val) {
     __shared__ int sk[kSortWarps][kLongSort];
     __shared__ double sv[kSortWarps][kLongSort];
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     int *K = sk[wl];
     double *Vv = sv[wl];
-    for (int i = blockIdx.x * kSortWarps + wl; i < n; i += gridDim.x * kSortWarps) {
+    int nl = *nlong;
+    for (int w = blockIdx.x * kSortWarps + wl; w < nl; w += gridDim.x * kSortWarps) {
+        int i = longrows[w];
         int a = rowptr[i], b = rowptr[i + 1];
         int L = b - a;
-        if (L <= kRegSort) continue;
         if (L > kLongSort) {
             if (lane == 0)
                 for (int p = a + 1; p < b; p++) {
@@ -616,11 +668,16 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 // sorts the row's columns, then adds a_ik b_kJ into a shared accumulator with k
 // in ascending order (one k at a time, lanes over B_k's distinct columns), so
 // every C entry is summed in the same order as Gustavson's row-by-row product.
-// Rows with more than kHashMax distinct columns take an exact slow path.
+// Rows with more distinct columns than the table holds take an exact slow path.
 
-constexpr int kHashCap = 1024;     // hash slots per warp (power of two)
-constexpr int kHashMax = 512;      // distinct columns handled in shared memory
-constexpr int kHashWarps = 4;
+// Two table sizes.  Rows with at most kSmallCand candidate products (all but
+// a few rows at the fine levels: level 0's A P has ~11 per row) run with
+// small per-warp tables at full occupancy; the other rows, listed by a
+// candidate-count pass, run with large tables.
+//   CAP: hash slots per warp (power of two); HMAX: distinct columns handled
+//   in shared memory, a power of two (larger rows take the exact slow path);
+//   WARPS per block.
+constexpr int kSmallCand = 32;
 constexpr int kEmpty = -1;
 
 // Per-warp scratch for enumerating the products of one chunk of 32 A entries:
@@ -670,10 +727,12 @@ __device__ __forceinline__ int chunk_owner(const ProdChunk &pc, int t) {
 }
 
 // Insert every candidate column of row i into a table of *cap slots (sized
-// from the row's candidate count, 32..kHashCap); returns the distinct count,
-// or kHashMax+1 when the row is too large for the shared path.  All products
+// from the row's candidate count, 32..CAP); returns the distinct count, or
+// HMAX+1 when the row is too large for the shared path.  All products
 // of a chunk of 32 A entries are enumerated at once (one per lane), so the
 // row costs one chain of dependent loads per chunk, not one per A entry.
+// With SKIP, a row with more than HMAX candidates is left alone (returns -1).
+template <int CAP, int HMAX, bool SKIP>
 __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, const int *bc, int *tab,
                         int *cnt, int lane, int *cap_out, ProdChunk &pc) {
     int a = ar[i], b = ar[i + 1];
@@ -683,14 +742,15 @@ __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, cons
         cand += br[k + 1] - br[k];
     }
     for (int sh = 16; sh > 0; sh >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, sh);
+    if (SKIP && cand > HMAX) return -1;
     int cap = 32;
-    while (cap < kHashCap && cap < 2 * cand) cap <<= 1;
+    while (cap < CAP && cap < 2 * cand) cap <<= 1;
     *cap_out = cap;
     for (int t = lane; t < cap; t += 32) tab[t] = kEmpty;
     if (lane == 0) *cnt = 0;
     __syncwarp();
     bool overflow = false;
-    int limit = min(kHashMax, cap / 2 + cap / 4);
+    int limit = min(HMAX, cap / 2 + cap / 4);
     for (int a0 = a; a0 < b; a0 += 32) {
         int tot = load_chunk(a0, b, ac, nullptr, br, pc, lane);
         for (int t = lane; t < tot && !overflow; t += 32) {
@@ -711,7 +771,7 @@ __device__ int hash_row(int i, const int *ar, const int *ac, const int *br, cons
     }
     __syncwarp();
     int c = *cnt;
-    return c > limit ? kHashMax + 1 : c;
+    return c > limit ? HMAX + 1 : c;
 }
 
 // Exact slow path for a large row: the next distinct column above `last`,
@@ -730,17 +790,36 @@ __device__ int next_col(int i, long last, const int *ar, const int *ac, const in
     return m;
 }
 
-__global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowcount(int n, const int *ar, const int *ac,
-                                                                     const int *br, const int *bc, int *ucnt) {
-    __shared__ int tab[kHashWarps][kHashCap];
-    __shared__ int cnt[kHashWarps];
-    __shared__ ProdChunk pcs[kHashWarps];
-    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    int i = blockIdx.x * kHashWarps + wl;
+// Rows of A B with more than kSmallCand candidate products (sum over k in
+// A_i of |B_k|), appended to a list in any order.
+__global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *big, int *nbig) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    int c = 0;
+    for (int p = ar[i]; p < ar[i + 1]; p++) {
+        int k = ac[p];
+        c += br[k + 1] - br[k];
+    }
+    if (c > kSmallCand) big[atomicAdd(nbig, 1)] = i;
+}
+
+// One warp per row: rows 0..n-1, or the n rows listed in `rows`.  With SKIP,
+// rows with more than HMAX candidates are left to the large-table launch.
+template <int CAP, int HMAX, int WARPS, bool SKIP>
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowcount(int n, const int *rows, const int *ar,
+                                                                const int *ac, const int *br, const int *bc,
+                                                                int *ucnt) {
+    __shared__ int tab[WARPS][CAP];
+    __shared__ int cnt[WARPS];
+    __shared__ ProdChunk pcs[WARPS];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int w = blockIdx.x * WARPS + wl;
+    if (w >= n) return;
+    int i = rows ? rows[w] : w;
     int cap;
-    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pcs[wl]);
-    if (c > kHashMax) {
+    int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pcs[wl]);
+    if (c < 0) return;
+    if (c > HMAX) {
         c = 0;
         for (long last = -1;;) {
             int J = next_col(i, last, ar, ac, br, bc, lane);
@@ -752,25 +831,29 @@ __global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowcount(int n, cons
     if (lane == 0) ucnt[i] = c;
 }
 
-__global__ void __launch_bounds__(kHashWarps * 32) k_spgemm_rowfill(int n, const int *ar, const int *ac,
-                                                                    const double *av, const int *br,
-                                                                    const int *bc, const double *bv,
-                                                                    const int *cr, int *cc, double *cv) {
-    __shared__ int tab[kHashWarps][kHashCap];
-    __shared__ int keys[kHashWarps][kHashMax];
-    __shared__ double acc[kHashWarps][kHashMax];
-    __shared__ int cnt[kHashWarps];
-    __shared__ ProdChunk pcs[kHashWarps];
+template <int CAP, int HMAX, int WARPS, bool SKIP>
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int *rows, const int *ar,
+                                                               const int *ac, const double *av, const int *br,
+                                                               const int *bc, const double *bv,
+                                                               const int *cr, int *cc, double *cv) {
+    static_assert((HMAX & (HMAX - 1)) == 0, "HMAX bounds the bitonic sort: a power of two");
+    __shared__ int tab[WARPS][CAP];
+    __shared__ int keys[WARPS][HMAX];
+    __shared__ double acc[WARPS][HMAX];
+    __shared__ int cnt[WARPS];
+    __shared__ ProdChunk pcs[WARPS];
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    int i = blockIdx.x * kHashWarps + wl;
-    if (i >= n) return;
+    int wr = blockIdx.x * WARPS + wl;
+    if (wr >= n) return;
+    int i = rows ? rows[wr] : wr;
     unsigned lt = (1u << lane) - 1u;
     int cap;
     ProdChunk &pc = pcs[wl];
-    int c = hash_row(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pc);
+    int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pc);
+    if (c < 0) return;
     int base = cr[i];
     int a = ar[i], b = ar[i + 1];
-    if (c > kHashMax) {
+    if (c > HMAX) {
         // slow path: columns by repeated minimum, values pulled per column
         int e = 0;
         for (long last = -1;;) {
@@ -1298,10 +1381,15 @@ void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, cons
                                                       tval ? tval->p : nullptr);
     CK_LAUNCH();
     if (ncol) {
-        k_sort_rows<<<grid_for(ncol, kBlock), kBlock, 0, s>>>(ncol, trow.p, tcol.p, tval ? tval->p : nullptr);
+        DVec<int> longrows, nlong;
+        longrows.alloc(ncol, s);
+        nlong.alloc(1, s);
+        CK(cudaMemsetAsync(nlong.p, 0, sizeof(int), s));
+        k_sort_rows<<<grid_for(ncol, kBlock), kBlock, 0, s>>>(ncol, trow.p, tcol.p, tval ? tval->p : nullptr,
+                                                              longrows.p, nlong.p);
         CK_LAUNCH();
-        k_sort_long_rows<<<grid_for(ncol, kSortWarps, 148 * 8), kSortWarps * 32, 0, s>>>(
-            ncol, trow.p, tcol.p, tval ? tval->p : nullptr);
+        k_sort_long_rows<<<grid_for(ncol, kSortWarps, 148 * 4), kSortWarps * 32, 0, s>>>(
+            longrows.p, nlong.p, trow.p, tcol.p, tval ? tval->p : nullptr);
         CK_LAUNCH();
     }
 }
@@ -1379,13 +1467,34 @@ void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vec
 }
 
 // C = A B (structural pattern, sorted; values in Gustavson order).
+// C = A B (structural pattern, sorted; values in Gustavson order).  Rows with
+// at most kSmallCand candidates run with small tables, the listed rest with
+// large ones; every row is written by exactly one of the two launches.
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
+    constexpr int kSW = 16, kBW = 4;   // warps per block, small and large tables
     int n = A.n;
-    DVec<int> ucnt;
+    DVec<int> ucnt, big, nbig;
     ucnt.alloc(std::max(n, 1), s);
-    unsigned blocks = (unsigned)((n + kHashWarps - 1) / kHashWarps);
-    k_spgemm_rowcount<<<blocks, kHashWarps * 32, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p, ucnt.p);
+    big.alloc(std::max(n, 1), s);
+    nbig.alloc(1, s);
+    CK(cudaMemsetAsync(nbig.p, 0, sizeof(int), s));
+    k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, big.p,
+                                                                      nbig.p);
     CK_LAUNCH();
+    int nb = read_int(nbig.p, s);
+    bool small = nb < n;
+    unsigned sblocks = (unsigned)((n + kSW - 1) / kSW), bblocks = (unsigned)((nb + kBW - 1) / kBW);
+    if (small) {
+        k_spgemm_rowcount<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(n, nullptr, A.rowptr.p,
+                                                                                  A.col.p, B.rowptr.p,
+                                                                                  B.col.p, ucnt.p);
+        CK_LAUNCH();
+    }
+    if (nb) {
+        k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(nb, big.p, A.rowptr.p, A.col.p,
+                                                                               B.rowptr.p, B.col.p, ucnt.p);
+        CK_LAUNCH();
+    }
     C.n = n;
     C.ncol = B.ncol;
     C.rowptr.alloc(n + 1, s);
@@ -1394,9 +1503,16 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
-    k_spgemm_rowfill<<<blocks, kHashWarps * 32, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p,
-                                                       B.val.p, C.rowptr.p, C.col.p, C.val.p);
-    CK_LAUNCH();
+    if (small) {
+        k_spgemm_rowfill<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(
+            n, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
+        CK_LAUNCH();
+    }
+    if (nb) {
+        k_spgemm_rowfill<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(
+            nb, big.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
+        CK_LAUNCH();
+    }
 }
 
 void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
@@ -1539,9 +1655,14 @@ void build_preconditioner(cpr_handle *h) {
         Level &L = h->lev[l];
         clk.mark("diag");
         // classical strength and PMIS
+        bool long_rows = L.A.nnz > 16L * n;   // warp per row pays once rows average over 16 entries
         Graph S = build_pattern(n, s, [&](const int *srow, int *out) {
-            k_strength_rs<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
-                                                                o.theta_amg, srow, out);
+            if (long_rows)
+                k_strength_rs_warp<<<grid_for((long)n * 32, kBlock), kBlock, 0, s>>>(
+                    n, L.A.rowptr.p, L.A.col.p, L.A.val.p, o.theta_amg, srow, out);
+            else
+                k_strength_rs<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
+                                                                    o.theta_amg, srow, out);
             CK_LAUNCH();
         });
         DVec<int> trow, tcol;
@@ -1615,8 +1736,8 @@ void build_preconditioner(cpr_handle *h) {
         // the smoother's coloring: Eq. 5.1 strength, symmetrised, JP
         {
             Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
-                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p,
-                                                                   L.A.val.p, o.theta_color, srow, out);
+                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
+                                                                   o.theta_color, srow, out);
                 CK_LAUNCH();
             });
             Graph G = sym_union(Sc, s);

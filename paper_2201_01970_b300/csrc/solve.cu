@@ -12,6 +12,7 @@
 #include <cmath>
 
 #include "cpr_internal.cuh"
+#include "sweeps.cuh"
 
 namespace cpr {
 
@@ -43,22 +44,6 @@ struct ScalLayout {
 // Device ints: [0] step j, [1] done, [2] steps in this cycle, [3] breakdown.
 enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_CNT_DOT = 5, I_CNT_UPD = 6, I_COUNT = 8 };
 
-__device__ __forceinline__ int step_of(const int *jptr) { return jptr ? *jptr : 0; }
-
-// ------------------------------------------------ programmatic dependent launch
-//
-// The kernels of one B application run as a chain in which each kernel's
-// inputs are the previous kernels' outputs, but most of what they read -- the
-// matrices' patterns and values, 1/a_ii, the permutations -- was fixed at
-// setup.  Each kernel loads that static part first, then waits for its
-// predecessor (griddepcontrol.wait: the predecessor has completed and its
-// writes are visible), then lets its own successor launch.  The successor's
-// static loads thus overlap this kernel's dependent work, and since a kernel
-// lets its successor start only after its own wait returned, everything
-// before the current kernel has completed when a prologue runs.  Without the
-// launch attribute both instructions are no-ops.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 constexpr int kPre = 4;   // row entries per lane loaded before the dependency wait
 
@@ -248,11 +233,6 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
 // next kernel commits the staged range into x while reading that range from
 // the staging buffer ("pending" range [p0, p1)).  G lanes share a row.
 
-template <class T>
-__device__ __forceinline__ T group_sum(T v, int G) {
-    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
-    return v;
-}
 
 template <class T>
 __device__ __forceinline__ T xval(const T *x, const T *sp, int p0, int p1, int j) {
@@ -389,123 +369,10 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b
 
 
 // ------------------------------------------------------------- BILU(0) sweeps
+// (k_bilu_fwd / k_bilu_bwd live in sweeps.cuh)
 
-// Forward substitution for the color of positions [c0, c0 + cnt), in place:
-// y_i = r_i - sum_{lower} L_ij y_j (everything in BILU positions).
-template <class T>
-__global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
-                           const int *__restrict__ lc, const T *__restrict__ lv, T *y,
-                           const int *done) {
-    constexpr int kPreB = 2;   // blocks loaded before the wait
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = t < cnt;
-    int i = c0 + t;
-    int e0 = 0, e1 = 0;
-    if (active) {
-        e0 = lr[i];
-        e1 = lr[i + 1];
-    }
-    int cj[kPreB];
-    T Lp[kPreB][9];
-#pragma unroll
-    for (int u = 0; u < kPreB; u++) {
-        bool in = e0 + u < e1;
-        cj[u] = in ? lc[e0 + u] : 0;
-#pragma unroll
-        for (int k = 0; k < 9; k++) Lp[u][k] = in ? lv[9 * (size_t)(e0 + u) + k] : (T)0;
-    }
-    pdl_wait();
-    pdl_trigger();
-    if (!active || (done && *done)) return;
-    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
-#pragma unroll
-    for (int u = 0; u < kPreB; u++)
-        if (e0 + u < e1) {
-            const T *L = Lp[u];
-            const T *yj = y + 3 * (size_t)cj[u];
-            T y0 = yj[0], y1 = yj[1], y2 = yj[2];
-            s0 -= L[0] * y0 + L[1] * y1 + L[2] * y2;
-            s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
-            s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
-        }
-#pragma unroll 4
-    for (int p = e0 + kPreB; p < e1; p++) {
-        const T *L = lv + 9 * (size_t)p;
-        const T *yj = y + 3 * (size_t)lc[p];
-        T y0 = yj[0], y1 = yj[1], y2 = yj[2];
-        s0 -= L[0] * y0 + L[1] * y1 + L[2] * y2;
-        s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
-        s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
-    }
-    y[3 * (size_t)i] = s0;
-    y[3 * (size_t)i + 1] = s1;
-    y[3 * (size_t)i + 2] = s2;
-}
 
-// Backward substitution for the color of positions [c0, c0 + cnt), in place:
-// z_i = U_ii^-1 (y_i - sum_{upper} U_ij z_j).  The result, plus Pi_P e_P when
-// ep != nullptr, is also written to out (FP64, natural block row border[i]).
-template <class T>
-__global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
-                           const int *__restrict__ uc, const T *__restrict__ uv,
-                           const T *__restrict__ dinv, T *y, const T *ep, const int *__restrict__ border,
-                           double *out_base, long ld, const int *jptr, const int *done) {
-    constexpr int kPreB = 2;   // blocks loaded before the wait
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = t < cnt;
-    int i = c0 + t;
-    int e0 = 0, e1 = 0, bi = 0;
-    T D[9];
-    if (active) {
-        e0 = ur[i];
-        e1 = ur[i + 1];
-        bi = border[i];
-    }
-#pragma unroll
-    for (int k = 0; k < 9; k++) D[k] = active ? dinv[9 * (size_t)i + k] : (T)0;
-    int cj[kPreB];
-    T Up[kPreB][9];
-#pragma unroll
-    for (int u = 0; u < kPreB; u++) {
-        bool in = e0 + u < e1;
-        cj[u] = in ? uc[e0 + u] : 0;
-#pragma unroll
-        for (int k = 0; k < 9; k++) Up[u][k] = in ? uv[9 * (size_t)(e0 + u) + k] : (T)0;
-    }
-    pdl_wait();
-    pdl_trigger();
-    if (!active || (done && *done)) return;
-    T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
-#pragma unroll
-    for (int u = 0; u < kPreB; u++)
-        if (e0 + u < e1) {
-            const T *U = Up[u];
-            const T *zj = y + 3 * (size_t)cj[u];
-            T z0 = zj[0], z1 = zj[1], z2 = zj[2];
-            s0 -= U[0] * z0 + U[1] * z1 + U[2] * z2;
-            s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
-            s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
-        }
-#pragma unroll 4
-    for (int p = e0 + kPreB; p < e1; p++) {
-        const T *U = uv + 9 * (size_t)p;
-        const T *zj = y + 3 * (size_t)uc[p];
-        T z0 = zj[0], z1 = zj[1], z2 = zj[2];
-        s0 -= U[0] * z0 + U[1] * z1 + U[2] * z2;
-        s1 -= U[3] * z0 + U[4] * z1 + U[5] * z2;
-        s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
-    }
-    T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
-    T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
-    T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
-    y[3 * (size_t)i] = z0;
-    y[3 * (size_t)i + 1] = z1;
-    y[3 * (size_t)i + 2] = z2;
-    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
-    out[0] = (double)z0 + (ep ? (double)ep[i] : 0.0);
-    out[1] = (double)z1;
-    out[2] = (double)z2;
-}
+
 
 // ------------------------------------------------------------- small kernels
 
@@ -1044,17 +911,21 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     Bilu &B = h->bilu;
     // the lowest color has no lower neighbours (L holds lower colors only), so
     // its forward substitution leaves y unchanged and is skipped
+    // FP32: 4 lanes share a block row (FP32 shuffles are cheap); FP64: one
+    // thread per block row, no cross-lane FP64 additions
+    constexpr int G = sizeof(T) == 4 ? 4 : 1;
     for (int c = 1; c < B.ncolors; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        launch_b(h, k_bilu_fwd<T>, grid_for(cnt, kBlock), kBlock, s, B.color_off[c], cnt, B.Lrowptr.p, B.Lcol.p,
-                 Vals<T>::Lv(h), y, done);
+        launch_b(h, k_bilu_fwd<T, G>, grid_for((long)cnt * G, kBlock), kBlock, s, B.color_off[c], cnt,
+                 B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), y, done);
     }
     for (int c = B.ncolors - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
-        launch_b(h, k_bilu_bwd<T>, grid_for(cnt, kBlock), kBlock, s, B.color_off[c], cnt, B.Urowptr.p, B.Ucol.p,
-                 Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base, ld, jptr, done);
+        launch_b(h, k_bilu_bwd<T, G>, grid_for((long)cnt * G, kBlock), kBlock, s, B.color_off[c], cnt,
+                 B.Urowptr.p, B.Ucol.p, Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base, ld,
+                 jptr, done);
     }
 }
 
