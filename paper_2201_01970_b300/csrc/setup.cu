@@ -1546,10 +1546,17 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
 // Lanes per row for a mean row length: about four entries per lane (1..32
 // lanes), so short rows keep many rows, and several independent loads per
 // lane, in flight.
-int lanes_for(long nnz, int n) {
-    double avg = n ? (double)nnz / n : 1.0;
+// Lanes per row for a launch over `rows` rows averaging `avg` entries: at
+// least a quarter of the row length, and enough lanes that the launch has
+// `target` threads (up to 32 lanes).  A lane's work is a chain of dependent
+// loads (row extent, entries, gathered x), so small launches wait on that
+// chain and gain from spreading each row over more lanes.  The rule and its
+// thread targets come from sweeping 1..32 lanes per kernel family and level
+// on B300 (128x128x32 and 60x220x85 hierarchies): it matches the fastest
+// width, or comes within a few percent of it, on every level.
+int lanes_for(double avg, long rows, long target) {
     int g = 1;
-    while (g < 32 && 4 * g < avg) g <<= 1;
+    while (g < 32 && (4 * g < avg || rows * g < target)) g <<= 1;
     return g;
 }
 
@@ -1891,9 +1898,11 @@ void build_preconditioner(cpr_handle *h) {
         k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
                                                           Lv.A.val.p, Lv.diag.p, Lv.dinv.p);
         CK_LAUNCH();
-        Lv.gA = lanes_for(Lv.Ao.nnz, n);
-        Lv.gP = lanes_for(Lv.Pp.nnz, n);
-        Lv.gR = lanes_for(Lv.Rp.nnz, Lv.Rp.n);
+        // smoothing launches cover one color (n / ncolors rows on average);
+        // the residual kernel shares their width
+        Lv.gA = lanes_for((double)Lv.Ao.nnz / n, n / std::max(1, Lv.ncolors), 1L << 16);
+        Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
+        Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
     }
     {
         // final V-cycle commit: level-0 solve row -> BILU position
