@@ -262,9 +262,13 @@ def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_reg
     solver.profile(False)
     prof_ms = pe[0].elapsed_time(pe[1]) / P
     levels = [solver.level(l) for l in range(solver.nlev)]
+    # in-graph device time of each V-cycle part (between solves)
+    parts = solver.profile_vcycle_levels(20)
+    for l, d in enumerate(parts["levels"]):
+        d.update(n=levels[l]["n"], nnz=levels[l]["nnz"], ncolors=levels[l]["ncolors"])
     solver.close()
     return {"per_ms": per, "total_ms": total, "stats": stats, "fam": fam, "levels": levels,
-            "launches": launches, "profiled_ms_per_step": prof_ms, "profiled_steps": P}
+            "launches": launches, "profiled_ms_per_step": prof_ms, "profiled_steps": P, "parts": parts}
 
 
 def e2e_arm(cpr, torch, seq_host, K, W, stream):
@@ -629,18 +633,27 @@ def main():
     f32 = fam_report(r32, 4)
     f64 = fam_report(r64, 8)
     sm0 = f32.get("smooth0", {})
-    roof = {"kernel": "k_smooth_color on the finest pressure level (multi-color GS color sweep, FP32)",
-            "bound": "hbm", "achieved": sm0.get("gbs"), "peak": hbm, "unit": "GB/s",
-            "frac": (sm0.get("gbs") / hbm) if sm0.get("gbs") else None,
-            "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
-            "bytes_per_launch": sm0.get("bytes_per_launch")}
-    sp = f64.get("spmv", {})
-    fp64_peak = 296 * 2 * 2.032e9 / 1e12      # DFMA thread-instructions/cycle x 2 flop x max SM clock
+    sp = f32.get("spmv", {})
+    # The outer BSR SpMV is the largest single kernel of the step (launch-list
+    # share); its bound is B300's FP64 pipe.  Peak: the FP64 FMA rate ncu
+    # reports for this GPU (296 DFMA thread-instructions per cycle) x 2 flops x
+    # the maximum SM clock.  traffic: dram__bytes_read.sum + dram__bytes_write.sum
+    # of one launch of this kernel from the ncu capture summarised in
+    # profiles/hot_kernels_128x128x32_fp32.md (350.85 MB read + 11.30 MB written).
+    fp64_peak = 296 * 2 * 2.032e9 / 1e12
     spmv_tflops = (18.0 * nnzb / (sp["avg_us"] * 1e-6) / 1e12) if sp.get("avg_us") else None
-    roof_alu = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV)", "bound": "alu", "achieved": spmv_tflops,
-                "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
-                "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
-                "hbm_gbs": sp.get("gbs"), "hbm_frac": (sp.get("gbs") / hbm) if sp.get("gbs") else None}
+    roof = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV, w = A z)", "bound": "alu",
+            "achieved": spmv_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
+            "peak_kind": "FP64 FMA rate x max SM clock (derived, ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak)",
+            "traffic": 362.16e6 if WORKLOAD == "128x128x32" else None,
+            "flops_per_launch": 18.0 * nnzb, "bytes_per_launch": spmv_bytes(nb, nnzb),
+            "hbm_gbs": sp.get("gbs"), "hbm_frac_of_measured": (sp.get("gbs") / hbm) if sp.get("gbs") else None}
+    roof_sm = {"kernel": "k_smooth_color on the finest pressure level (multi-color GS color sweep, FP32)",
+               "bound": "hbm", "achieved": sm0.get("gbs"), "peak": hbm, "unit": "GB/s",
+               "frac": (sm0.get("gbs") / hbm) if sm0.get("gbs") else None,
+               "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+               "bytes_per_launch": sm0.get("bytes_per_launch")}
 
     def pct(a, q):
         return float(np.percentile(np.array(a), q))
@@ -668,12 +681,14 @@ def main():
         "vcycle_gbs": {"fp32": f32.get("vcycle", {}).get("gbs"), "fp64": f64.get("vcycle", {}).get("gbs"),
                        "frac_fp32": (f32.get("vcycle", {}).get("gbs") or 0) / hbm,
                        "frac_fp64": (f64.get("vcycle", {}).get("gbs") or 0) / hbm},
+        "vcycle_parts_us": {"note": "each part captured 20x into its own CUDA graph, device time per repetition",
+                            "fp32": r32["parts"], "fp64": r64["parts"]},
         "families": {"fp32": f32, "fp64": f64,
                      "note": "CUDA-event brackets per family, from a separate timed region of "
                              f"{r32['profiled_steps']} steps per arm (bracketed step: "
                              f"{r32['profiled_ms_per_step']:.2f} ms fp32, {r64['profiled_ms_per_step']:.2f} ms fp64)"},
         "roofline": roof,
-        "roofline_fp64_spmv": roof_alu,
+        "roofline_smoother_level0": roof_sm,
         "gpu_launches": int(r32["launches"]),
         "clocks": clocks,
     }

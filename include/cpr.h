@@ -248,6 +248,23 @@ int cpr_profile(cpr_handle *h, int enable);
 /* Accumulated bracket count and device milliseconds of one family. */
 int cpr_profile_read(const cpr_handle *h, int family, long *count, double *ms);
 
+/*
+ * Device time of the parts of one B application, each captured `reps` times
+ * into a CUDA graph of its own and timed with CUDA events on the handle's
+ * stream (best of three graph launches; microseconds per repetition):
+ *   us[0] one V-cycle (Alg. 6 on every level, Alg. 1's B_P),
+ *   us[1] one BILU(0) forward + backward application,
+ *   us[2] the coarsest level's dense solve,
+ *   us[3 + 5 l + q] level l < levels-1: q = 0 pre-smoothing sweep over its
+ *         colors, 1 residual, 2 restriction, 3 prolongation, 4 post-smoothing.
+ * The parts run on whatever the work vectors hold, so call this between
+ * solves only (every B application rewrites those vectors before reading
+ * them).  n_us must be at least 3 + 5 * (levels - 1).  Returns the count of
+ * values written, or CPR_ERR_INVALID / CPR_ERR_CUDA.  No counterpart in the
+ * paper: a measurement hook.
+ */
+int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ def lib():
         L.cpr_launch_count.restype = C.c_uint64
         L.cpr_profile.argtypes = [vp, C.c_int]
         L.cpr_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]
+        L.cpr_profile_vcycle_levels.argtypes = [vp, C.c_int, vp, C.c_int]
         _lib = L
     return _lib
 
@@ -235,6 +236,18 @@ class Solver:
 
     def profile(self, enable: bool = True) -> None:
         _check(lib().cpr_profile(self._h, int(enable)), "cpr_profile")
+
+    def profile_vcycle_levels(self, reps: int = 20) -> dict:
+        """In-graph device microseconds of the V-cycle, the BILU application,
+        the coarse solve and every level's pre/resid/R/P/post parts."""
+        nl = self.nlev
+        us = np.zeros(3 + 5 * max(nl - 1, 0))
+        rc = lib().cpr_profile_vcycle_levels(self._h, reps, _ptr(us), len(us))
+        if rc < 0:
+            _check(rc, "cpr_profile_vcycle_levels")
+        parts = ("pre", "resid", "R", "P", "post")
+        return {"vcycle_us": us[0], "bilu_us": us[1], "coarse_us": us[2],
+                "levels": [dict(zip(parts, us[3 + 5 * l: 8 + 5 * l])) for l in range(nl - 1)]}
 
     def profile_read(self, family: int):
         n, ms = C.c_long(), C.c_double()

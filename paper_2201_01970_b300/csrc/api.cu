@@ -413,6 +413,16 @@ int cpr_vcycle(cpr_handle *h, const double *b, double *x) {
     });
 }
 
+int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
+    if (!h || !us || reps < 1 || h->lev.empty()) return CPR_ERR_INVALID;
+    int written = 0;
+    int rc = guarded([&] {
+        written = profile_vcycle_levels(h, reps, us, n_us);
+        return CPR_OK;
+    });
+    return rc == CPR_OK ? written : rc;
+}
+
 int cpr_bilu_apply(cpr_handle *h, const double *r, double *z) {
     if (!h || !r || !z) return CPR_ERR_INVALID;
     return guarded([&] {

@@ -248,6 +248,7 @@ void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, do
              long z_ld);
 void vcycle_apply(cpr_handle *h, const double *b, double *x);
 void bilu_apply(cpr_handle *h, const double *r, double *z);
+int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
 void batch_prepare(cpr_handle *h);
 int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st);

@@ -803,53 +803,45 @@ __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br
     if (c > kSmallCand) big[atomicAdd(nbig, 1)] = i;
 }
 
-// One warp per row: rows 0..n-1, or the n rows listed in `rows`.  With SKIP,
-// rows with more than HMAX candidates are left to the large-table launch.
+// One warp per row, grid-stride: rows 0..n-1, or the *nrows rows listed in
+// `rows` (a count on the device, so the launch needs no read-back).  With
+// SKIP, rows with more than HMAX candidates are left to the large-table launch.
 template <int CAP, int HMAX, int WARPS, bool SKIP>
-__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowcount(int n, const int *rows, const int *ar,
-                                                                const int *ac, const int *br, const int *bc,
-                                                                int *ucnt) {
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowcount(int n, const int *rows, const int *nrows,
+                                                                const int *ar, const int *ac, const int *br,
+                                                                const int *bc, int *ucnt) {
     __shared__ int tab[WARPS][CAP];
     __shared__ int cnt[WARPS];
     __shared__ ProdChunk pcs[WARPS];
     int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    int w = blockIdx.x * WARPS + wl;
-    if (w >= n) return;
-    int i = rows ? rows[w] : w;
-    int cap;
-    int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pcs[wl]);
-    if (c < 0) return;
-    if (c > HMAX) {
-        c = 0;
-        for (long last = -1;;) {
-            int J = next_col(i, last, ar, ac, br, bc, lane);
-            if (J == INT_MAX) break;
-            c++;
-            last = J;
+    int nn = rows ? *nrows : n;
+    for (int w = blockIdx.x * WARPS + wl; w < nn; w += gridDim.x * WARPS) {
+        int i = rows ? rows[w] : w;
+        int cap;
+        int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pcs[wl]);
+        if (c < 0) continue;
+        if (c > HMAX) {
+            c = 0;
+            for (long last = -1;;) {
+                int J = next_col(i, last, ar, ac, br, bc, lane);
+                if (J == INT_MAX) break;
+                c++;
+                last = J;
+            }
         }
+        if (lane == 0) ucnt[i] = c;
+        __syncwarp();
     }
-    if (lane == 0) ucnt[i] = c;
 }
 
-template <int CAP, int HMAX, int WARPS, bool SKIP>
-__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int *rows, const int *ar,
-                                                               const int *ac, const double *av, const int *br,
-                                                               const int *bc, const double *bv,
-                                                               const int *cr, int *cc, double *cv) {
-    static_assert((HMAX & (HMAX - 1)) == 0, "HMAX bounds the bitonic sort: a power of two");
-    __shared__ int tab[WARPS][CAP];
-    __shared__ int keys[WARPS][HMAX];
-    __shared__ double acc[WARPS][HMAX];
-    __shared__ int cnt[WARPS];
-    __shared__ ProdChunk pcs[WARPS];
-    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    int wr = blockIdx.x * WARPS + wl;
-    if (wr >= n) return;
-    int i = rows ? rows[wr] : wr;
+// Numeric row i of C = A B with this warp's shared tables (see below).
+template <int CAP, int HMAX, bool SKIP>
+__device__ void spgemm_fill_row(int i, const int *ar, const int *ac, const double *av, const int *br,
+                                const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *tab,
+                                int *keys, double *acc, int *cnt, ProdChunk &pc, int lane) {
     unsigned lt = (1u << lane) - 1u;
     int cap;
-    ProdChunk &pc = pcs[wl];
-    int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab[wl], &cnt[wl], lane, &cap, pc);
+    int c = hash_row<CAP, HMAX, SKIP>(i, ar, ac, br, bc, tab, cnt, lane, &cap, pc);
     if (c < 0) return;
     int base = cr[i];
     int a = ar[i], b = ar[i + 1];
@@ -878,10 +870,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
         return;
     }
     // compact the hash table into keys[0..c), then sort (bitonic)
-    int *K = keys[wl];
+    int *K = keys;
     int w = 0;
     for (int t0 = 0; t0 < cap; t0 += 32) {
-        int v = tab[wl][t0 + lane];
+        int v = tab[t0 + lane];
         bool keep = v != kEmpty;
         unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) K[w + __popc(m & lt)] = v;
@@ -905,7 +897,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
             }
             __syncwarp();
         }
-    double *S = acc[wl];
+    double *S = acc;
     for (int t = lane; t < c; t += 32) {
         S[t] = 0.0;
         cc[base + t] = K[t];
@@ -944,6 +936,26 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
         __syncwarp();
     }
     for (int t = lane; t < c; t += 32) cv[base + t] = S[t];
+}
+
+template <int CAP, int HMAX, int WARPS, bool SKIP>
+__global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int *rows, const int *nrows,
+                                                               const int *ar, const int *ac, const double *av,
+                                                               const int *br, const int *bc, const double *bv,
+                                                               const int *cr, int *cc, double *cv) {
+    static_assert((HMAX & (HMAX - 1)) == 0, "HMAX bounds the bitonic sort: a power of two");
+    __shared__ int tab[WARPS][CAP];
+    __shared__ int keys[WARPS][HMAX];
+    __shared__ double acc[WARPS][HMAX];
+    __shared__ int cnt[WARPS];
+    __shared__ ProdChunk pcs[WARPS];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int nn = rows ? *nrows : n;
+    for (int w = blockIdx.x * WARPS + wl; w < nn; w += gridDim.x * WARPS) {
+        spgemm_fill_row<CAP, HMAX, SKIP>(rows ? rows[w] : w, ar, ac, av, br, bc, bv, cr, cc, cv, tab[wl], keys[wl],
+                                         acc[wl], &cnt[wl], pcs[wl], lane);
+        __syncwarp();
+    }
 }
 
 // -------------------------------------------------------- level helpers
@@ -1481,20 +1493,15 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, big.p,
                                                                       nbig.p);
     CK_LAUNCH();
-    int nb = read_int(nbig.p, s);
-    bool small = nb < n;
-    unsigned sblocks = (unsigned)((n + kSW - 1) / kSW), bblocks = (unsigned)((nb + kBW - 1) / kBW);
-    if (small) {
-        k_spgemm_rowcount<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(n, nullptr, A.rowptr.p,
-                                                                                  A.col.p, B.rowptr.p,
-                                                                                  B.col.p, ucnt.p);
-        CK_LAUNCH();
-    }
-    if (nb) {
-        k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(nb, big.p, A.rowptr.p, A.col.p,
-                                                                               B.rowptr.p, B.col.p, ucnt.p);
-        CK_LAUNCH();
-    }
+    // the listed rows run on a fixed grid that reads their count on the device
+    unsigned sblocks = (unsigned)((n + kSW - 1) / kSW);
+    unsigned bblocks = (unsigned)grid_for(n, kBW, 148 * 8);
+    k_spgemm_rowcount<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(n, nullptr, nullptr, A.rowptr.p,
+                                                                              A.col.p, B.rowptr.p, B.col.p, ucnt.p);
+    CK_LAUNCH();
+    k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(n, big.p, nbig.p, A.rowptr.p, A.col.p,
+                                                                           B.rowptr.p, B.col.p, ucnt.p);
+    CK_LAUNCH();
     C.n = n;
     C.ncol = B.ncol;
     C.rowptr.alloc(n + 1, s);
@@ -1503,16 +1510,14 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
-    if (small) {
-        k_spgemm_rowfill<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(
-            n, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
-        CK_LAUNCH();
-    }
-    if (nb) {
-        k_spgemm_rowfill<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(
-            nb, big.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
-        CK_LAUNCH();
-    }
+    k_spgemm_rowfill<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(
+        n, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+        C.val.p);
+    CK_LAUNCH();
+    k_spgemm_rowfill<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(
+        n, big.p, nbig.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+        C.val.p);
+    CK_LAUNCH();
 }
 
 void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
@@ -1535,9 +1540,12 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
     dst.ncol = ncol;
     dst.rowptr.alloc(n + 1, s);
     exclusive_scan(cnt.p, dst.rowptr.p, n, s);
-    dst.nnz = read_int(dst.rowptr.p + n, s);
-    dst.col.alloc(std::max(dst.nnz, 1), s);
-    dst.val.alloc(std::max(dst.nnz, 1), s);
+    // no read-back: the copy keeps every entry (less one diagonal per row when
+    // skip_diag, each level row holding exactly one), so the source's count
+    // bounds the allocation and the host count is exact for level matrices
+    dst.nnz = skip_diag ? std::max(src.nnz - n, 0) : src.nnz;
+    dst.col.alloc(std::max(src.nnz, 1), s);
+    dst.val.alloc(std::max(src.nnz, 1), s);
     k_perm_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p, skip_diag,
                                                       icol, dst.rowptr.p, dst.col.p, dst.val.p);
     CK_LAUNCH();
@@ -1655,8 +1663,7 @@ void build_preconditioner(cpr_handle *h) {
             DVec<double> dtmp;
             dtmp.alloc(n, s);
             k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, diag.p, L.A.val.p, dtmp.p, h->err.p);
-            CK_LAUNCH();
-            check_err(h, "zero diagonal on an AMG level");
+            CK_LAUNCH();   // a zero diagonal is reported by the check at the end of the setup
         }
         if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
         Level &L = h->lev[l];
@@ -1783,8 +1790,7 @@ void build_preconditioner(cpr_handle *h) {
             CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
         }
         k_dense_lu<<<1, kLuThreads, smem, s>>>(n, a.p, lu.p, piv.p, use_smem, h->err.p);
-        CK_LAUNCH();
-        check_err(h, "singular coarsest matrix");
+        CK_LAUNCH();   // a zero pivot is reported by the check at the end of the setup
         if (!use_smem) {
             k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, s>>>(n, lu.p, piv.p, a.p);
             CK_LAUNCH();
@@ -1835,7 +1841,7 @@ void build_preconditioner(cpr_handle *h) {
                                                                          bdiag.p, lu, h->err.p);
                 CK_LAUNCH();
             }
-            check_err(h, "singular pivot block in BILU(0)");
+            // a singular pivot block is reported by the check at the end of the setup
             k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
                 nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
                 B.Ucol.p, Uv, Dv);
@@ -1938,7 +1944,11 @@ void build_preconditioner(cpr_handle *h) {
             Lv.s1_32.alloc(n, s);
         }
     }
-    CK(cudaStreamSynchronize(s));
+    // Kernels that meet a zero or non-finite pivot (an AMG level's diagonal,
+    // the coarsest matrix, a BILU(0) block) record CPR_ERR_SINGULAR and go on
+    // with a unit stand-in, so the setup runs to completion without host
+    // round trips and fails here.
+    check_err(h, "zero or non-finite pivot: an AMG level's diagonal, the coarsest matrix or a BILU(0) block");
     clk.mark("layout");
     h->have_B = true;
     h->epoch++;

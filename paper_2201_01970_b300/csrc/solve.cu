@@ -161,6 +161,35 @@ __global__ void k_restrict(int nb, const int *order, const double *v_base, long 
     rp[t] = (w0 * (T)v[0] + w1 * (T)v[1]) + w2 * (T)v[2];
 }
 
+// k_restrict fused with level 0's first pre-smoothing color (from x = 0): the
+// rows of color 0, [c0, c1), get r_P / a_ii in the staging vector sc, every
+// other row of x is zeroed.
+template <class T>
+__global__ void k_restrict_first(int nb, const int *order, const double *v_base, long ld, const int *jptr,
+                                 const T *w, T *rp, const T *__restrict__ dinv, T *x, T *sc, int c0, int c1,
+                                 const int *done) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = t < nb;
+    int i = 0;
+    T w0 = 0, w1 = 0, w2 = 0;
+    bool mine = active && t >= c0 && t < c1;
+    T di = mine ? dinv[t] : (T)0;
+    if (active) {
+        i = order ? order[t] : t;
+        w0 = w[3 * i];
+        w1 = w[3 * i + 1];
+        w2 = w[3 * i + 2];
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (!active || (done && *done)) return;
+    const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
+    T r = (w0 * (T)v[0] + w1 * (T)v[1]) + w2 * (T)v[2];
+    rp[t] = r;
+    if (mine) sc[t] = r * di;
+    else x[t] = (T)0;
+}
+
 // Second residual of Alg. 1: r = v - A z with z = Pi_P e_P, so only column 0 of
 // every block (the frozen copy c0, 3 values per block) takes part.  Rows and
 // columns are BILU positions (position t is natural block row border[t]); r
@@ -326,6 +355,36 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
     if (active && lane == 0) y[i] = add ? y[i] + s : s;
+}
+
+// Restriction fused with the first pre-smoothing color of the coarser level
+// (k_transfer with add = false, then k_smooth_first's work for row i): b_C =
+// R r, and from x_C = 0 the rows of color 0, [c0, c1), get b_C / a_ii in the
+// staging vector sc while every other row of x_C is zeroed.
+template <class T, int G>
+__global__ void k_transfer_first(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                 const T *__restrict__ val, const T *x, T *y, const T *__restrict__ dinv,
+                                 T *xc, T *sc, int c0, int c1, const int *done) {
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long g = tid / G;
+    int lane = (int)(tid % G);
+    bool active = g < n;
+    int i = (int)g;
+    RowPre<T, G> rp;
+    rp.load(rowptr, col, val, i, lane, active);
+    bool mine = active && i >= c0 && i < c1;
+    T di = mine ? dinv[i] : (T)0;
+    pdl_wait();
+    pdl_trigger();
+    if (done && *done) return;
+    T s = 0;
+    if (active) s = rp.dot(col, val, lane, [&](int j) { return x[j]; });
+    s = group_sum(s, G);
+    if (active && lane == 0) {
+        y[i] = s;
+        if (mine) sc[i] = s * di;
+        else xc[i] = (T)0;
+    }
 }
 
 // Level 0's result renumbered: out[map[t]] = x[t] (pending range from sp).
@@ -828,14 +887,16 @@ void launch_b(const cpr_handle *h, void (*kern)(KArgs...), unsigned grid, unsign
 // From zero: the first color writes b/a_ii into staging and zeroes x.
 template <class T>
 void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pending &pd,
-                const int *done) {
+                const int *done, bool first_done = false) {
     cudaStream_t s = h->stream;
     int n = L.A.n;
     for (int t = 0; t < L.ncolors; t++) {
         int c = descending ? L.ncolors - 1 - t : t;
         int c0 = L.color_off[c], c1 = L.color_off[c + 1];
         int k = 1 - pd.k;
-        if (from_zero && t == 0) {
+        if (from_zero && t == 0 && first_done) {
+            // the producer of b already did this color's from-zero work
+        } else if (from_zero && t == 0) {
             launch_b(h, k_smooth_first<T>, blocks_for(n), kBlock, s, n, c0, c1, Vals<T>::b(L), Vals<T>::dinv(L),
                      Vals<T>::x(L), Vals<T>::s(L, k), done);
         } else {
@@ -854,9 +915,10 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
 
 // V(pre, post) cycle on level l from x_l = 0 (pre-smoothing colors ascending,
 // post-smoothing descending).  On return the level's result is x with the
-// range `out` still staged.
+// range `out` still staged.  first_done: the kernel that wrote b_l also did
+// the first pre-smoothing color (x_l zeroed, color 0 staged in s1).
 template <class T>
-void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
+void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done = false) {
     cudaStream_t s = h->stream;
     Level &L = h->lev[l];
     int n = L.A.n;
@@ -871,18 +933,26 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
         k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, Vals<T>::x(L), done);
         CK_LAUNCH();
     }
-    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done);
+    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0);
     long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
     CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
                                        L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), Vals<T>::b(L),
                                        Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     pd = Pending{};
     Level &C = h->lev[l + 1];
-    CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s, L.Rp.n,
-                                       L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L), 0, 0,
-                                       Vals<T>::b(C), false, done)));
+    bool fuse = l + 1 < (int)h->lev.size() - 1 && h->opt.pre > 0;   // C is smoothed from zero
+    if (fuse) {
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer_first<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+                                           L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
+                                           Vals<T>::b(C), Vals<T>::dinv(C), Vals<T>::x(C), Vals<T>::s(C, 1),
+                                           C.color_off[0], C.color_off[1], done)));
+    } else {
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+                                           L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
+                                           Vals<T>::r(L), 0, 0, Vals<T>::b(C), false, done)));
+    }
     Pending cp;
-    vcycle<T>(h, l + 1, cp, done);
+    vcycle<T>(h, l + 1, cp, done, fuse);
     CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
                                        L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
                                        Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
@@ -893,10 +963,10 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done) {
 // e_P = B_P r_P on level 0: r_P arrives in level 0's b (level 0's color
 // order); the result leaves in BILU positions in ep.
 template <class T>
-void vcycle_top(cpr_handle *h, T *ep, const int *done) {
+void vcycle_top(cpr_handle *h, T *ep, const int *done, bool first_done = false) {
     Level &L0 = h->lev[0];
     Pending pd;
-    vcycle<T>(h, 0, pd, done);
+    vcycle<T>(h, 0, pd, done, first_done);
     int n = L0.A.n;
     launch_b(h, k_commit_natural<T>, blocks_for(n), kBlock, h->stream, n, h->ep_map.p, Vals<T>::x(L0),
              Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
@@ -943,11 +1013,18 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     Level &L0 = h->lev[0];
     const int *order0 = h->lev.size() > 1 ? L0.rows_by_color.p : nullptr;
     // r_P = Pi_P^T v
-    launch_b(h, k_restrict<T>, grid_for(nb, kBlock), kBlock, s, nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
-             Vals<T>::b(L0), done);
+    // level 0 is smoothed from zero unless it is the coarsest level
+    bool fuse = h->lev.size() > 1 && h->opt.pre > 0;
+    if (fuse)
+        launch_b(h, k_restrict_first<T>, grid_for(nb, kBlock), kBlock, s, nb, order0, v_base, v_ld, jptr,
+                 Vals<T>::w(h), Vals<T>::b(L0), Vals<T>::dinv(L0), Vals<T>::x(L0), Vals<T>::s(L0, 1),
+                 L0.color_off[0], L0.color_off[1], done);
+    else
+        launch_b(h, k_restrict<T>, grid_for(nb, kBlock), kBlock, s, nb, order0, v_base, v_ld, jptr, Vals<T>::w(h),
+                 Vals<T>::b(L0), done);
     // e_P = B_P r_P (BILU positions)
     prof_begin(h, CPR_PROF_VCYCLE);
-    vcycle_top<T>(h, Vals<T>::ep(h), done);
+    vcycle_top<T>(h, Vals<T>::ep(h), done, fuse);
     prof_end(h);
     // r = v - A Pi_P e_P
     long threads = (long)nb * kResidLanes;
@@ -1040,6 +1117,125 @@ void vcycle_apply(cpr_handle *h, const double *b, double *x) {
         k_gather_widen<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->bilu.iperm.p, h->ep64.p, x);
         CK_LAUNCH();
     }
+}
+
+namespace {
+
+// Capture `reps` repetitions of body() into one graph on the handle's stream
+// and return the device microseconds per repetition (best of three launches).
+template <class F>
+double graph_us(cpr_handle *h, int reps, F body) {
+    cudaStream_t s = h->stream;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaStreamSynchronize(s));
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int r = 0; r < reps; r++) body();
+    } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    CK(cudaStreamEndCapture(s, &g));
+    float best = 1e30f;
+    try {
+        CK(cudaGraphInstantiate(&ge, g, 0));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaGraphLaunch(ge, s));
+        for (int t = 0; t < 3; t++) {
+            CK(cudaEventRecord(e0, s));
+            CK(cudaGraphLaunch(ge, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            best = std::min(best, ms);
+        }
+    } catch (...) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ge) cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return 1000.0 * best / reps;
+}
+
+// The launches of one part of level l's V-cycle work, as vcycle() issues
+// them: 0 pre-smoothing sweep, 1 residual, 2 restriction, 3 prolongation,
+// 4 post-smoothing sweep.
+template <class T>
+void level_part(cpr_handle *h, int l, int part) {
+    cudaStream_t s = h->stream;
+    Level &L = h->lev[l];
+    int n = L.A.n;
+    Pending pd;
+    if (part == 0) {
+        mcgs_sweep<T>(h, L, false, true, pd, nullptr);
+    } else if (part == 1) {
+        pd = Pending{L.color_off[L.ncolors - 1], L.color_off[L.ncolors], 0};
+        long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
+        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+                                           L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L),
+                                           Vals<T>::b(L), Vals<T>::x(L), Vals<T>::s(L, 0), Vals<T>::r(L),
+                                           (const int *)nullptr)));
+    } else if (part == 2) {
+        Level &C = h->lev[l + 1];
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+                                           L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
+                                           Vals<T>::r(L), 0, 0, Vals<T>::b(C), false, (const int *)nullptr)));
+    } else if (part == 3) {
+        Level &C = h->lev[l + 1];
+        CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+                                           L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
+                                           Vals<T>::s(C, 0), 0, 0, Vals<T>::x(L), true, (const int *)nullptr)));
+    } else {
+        mcgs_sweep<T>(h, L, true, false, pd, nullptr);
+    }
+}
+
+template <class T>
+int profile_levels_t(cpr_handle *h, int reps, double *us, int n_us) {
+    int L = (int)h->lev.size();
+    int need = 3 + 5 * (L - 1);
+    if (n_us < need) fail(CPR_ERR_INVALID, "output array shorter than 3 + 5 * (levels - 1)");
+    DVec<double> out;
+    out.alloc(3 * (size_t)h->nb, h->stream);
+    us[0] = graph_us(h, reps, [&] { vcycle_top<T>(h, Vals<T>::ep(h), nullptr); });
+    us[1] = graph_us(h, reps, [&] { bilu_solve<T>(h, Vals<T>::tmp(h), nullptr, out.p, 0, nullptr, nullptr); });
+    Level &C = h->lev.back();
+    us[2] = graph_us(h, reps, [&] {
+        launch_b(h, k_coarse_solve<T>, blocks_for((long)C.A.n * 32), kBlock, h->stream, C.A.n, h->cinv.p,
+                 Vals<T>::b(C), Vals<T>::x(C), (const int *)nullptr);
+    });
+    for (int l = 0; l < L - 1; l++)
+        for (int part = 0; part < 5; part++)
+            us[3 + 5 * l + part] = graph_us(h, reps, [&] { level_part<T>(h, l, part); });
+    return need;
+}
+
+}  // namespace
+
+int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
+    bool prof = h->prof;
+    h->prof = false;   // no event nodes inside these graphs
+    int r;
+    try {
+        r = h->opt.precond_fp32 ? profile_levels_t<float>(h, reps, us, n_us)
+                                : profile_levels_t<double>(h, reps, us, n_us);
+    } catch (...) {
+        h->prof = prof;
+        throw;
+    }
+    h->prof = prof;
+    return r;
 }
 
 void bilu_apply(cpr_handle *h, const double *r, double *z) {

@@ -288,3 +288,19 @@ def test_dependent_launch_changes_no_result(torch, cpr, fp32):
         s.close()
     assert its[0] == its[1]
     assert np.array_equal(xs[0], xs[2]) and np.array_equal(xs[1], xs[3])
+
+
+def test_vcycle_part_timing_hook(torch, cpr):
+    """cpr_profile_vcycle_levels times every part and leaves the handle usable:
+    a solve after it matches a solve before it bit for bit."""
+    J = ragged()
+    b = dev(torch, J.b)
+    s = cpr.Solver(DevJ(torch, J), precond_fp32=1)
+    x0, _ = s.solve(b, rtol=1e-8)
+    t = s.profile_vcycle_levels(3)
+    assert len(t["levels"]) == s.nlev - 1
+    assert t["vcycle_us"] > 0 and t["bilu_us"] > 0 and t["coarse_us"] > 0
+    assert all(v > 0 for lv in t["levels"] for v in lv.values())
+    x1, _ = s.solve(b, rtol=1e-8)
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+    s.close()
