@@ -241,9 +241,14 @@ uint64_t cpr_launch_count(void);
 #define CPR_PROF_SMOOTH0 5   /* one multi-color GS color launch on the finest pressure level */
 #define CPR_PROF_NFAMILIES 6
 
-/* enable != 0: time the families above during later solves (adds two event
- * records per bracketed region); 0: stop.  Both reset the accumulators. */
-int cpr_profile(cpr_handle *h, int enable);
+#define CPR_PROF_ALL ((1 << CPR_PROF_NFAMILIES) - 1)
+
+/* mask != 0: time the families whose bits (1 << family) are set during later
+ * solves, each bracketed region with two event records on the handle's stream
+ * (inside the step graphs an event node costs a few microseconds, so nested
+ * families -- the level-0 sweeps inside the V-cycle -- are best timed in
+ * separate passes); 0: stop.  Both reset the accumulators. */
+int cpr_profile(cpr_handle *h, int mask);
 
 /* Accumulated bracket count and device milliseconds of one family. */
 int cpr_profile_read(const cpr_handle *h, int family, long *count, double *ms);

@@ -234,8 +234,12 @@ class Solver:
         _check(lib().cpr_copy_bilu(self._h, _ptr(bc), _ptr(lu), C.byref(nc)), "cpr_copy_bilu")
         return bc, nc.value, lu
 
-    def profile(self, enable: bool = True) -> None:
-        _check(lib().cpr_profile(self._h, int(enable)), "cpr_profile")
+    def profile(self, enable: bool = True, families=None) -> None:
+        """Bracket the given PROF_* families (all when None) in later solves."""
+        mask = 0
+        if enable:
+            mask = (1 << 6) - 1 if families is None else sum(1 << f for f in families)
+        _check(lib().cpr_profile(self._h, mask), "cpr_profile")
 
     def profile_vcycle_levels(self, reps: int = 20) -> dict:
         """In-graph device microseconds of the V-cycle, the BILU application,

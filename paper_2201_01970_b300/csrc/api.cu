@@ -112,6 +112,10 @@ void set_last_error(const std::string &what) { g_last_error = what; }
 
 void prof_begin(cpr_handle *h, int family) {
     if (!h->prof) return;
+    if (!(h->prof_mask & (1u << family))) {   // family not selected: an empty bracket for prof_end to close
+        h->prof_open.push_back(-1);
+        return;
+    }
     if (h->capturing >= 0) {
         auto &g = h->sg[h->capturing];
         cudaEvent_t a;
@@ -204,7 +208,8 @@ int cpr_profile(cpr_handle *h, int enable) {
     return guarded([&] {
         prof_flush(h);
         h->prof_open.clear();
-        h->prof = enable != 0;
+        h->prof_mask = (unsigned)enable & ((1u << CPR_PROF_NFAMILIES) - 1u);
+        h->prof = h->prof_mask != 0;
         for (int f = 0; f < CPR_PROF_NFAMILIES; f++) {
             h->prof_cnt[f] = 0;
             h->prof_ms[f] = 0.0;

@@ -130,6 +130,32 @@ __global__ void k_tile_scan(const int *in, int n, const int *tile_off, int *out)
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanBlock - 1) out[n] = excl;
 }
+// Whole scan in one CTA for up to kScanSingleMax elements: tiles in order,
+// each scanned by the block and offset by the running total (one launch
+// instead of three).
+constexpr int kScanSingleMax = 16 * kScanTile;
+__global__ void __launch_bounds__(kScanBlock) k_scan_single(const int *in, int n, int *out) {
+    int carry = 0;
+    for (long base = 0; base < n; base += kScanTile) {
+        int v[kScanItems];
+        int s = 0;
+        for (int k = 0; k < kScanItems; k++) {
+            long i = base + (long)threadIdx.x * kScanItems + k;
+            v[k] = i < n ? in[i] : 0;
+            s += v[k];
+        }
+        int total;
+        int excl = block_exclusive_scan(s, &total) + carry;
+        for (int k = 0; k < kScanItems; k++) {
+            long i = base + (long)threadIdx.x * kScanItems + k;
+            if (i < n) out[i] = excl;
+            excl += v[k];
+        }
+        carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
 }  // namespace
 
 void exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
@@ -140,6 +166,11 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
     int tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
         k_tile_scan<<<1, kScanBlock, 0, s>>>(in, n, nullptr, out);
+        CK_LAUNCH();
+        return;
+    }
+    if (n <= kScanSingleMax) {
+        k_scan_single<<<1, kScanBlock, 0, s>>>(in, n, out);
         CK_LAUNCH();
         return;
     }

@@ -191,6 +191,7 @@ struct cpr_handle {
     double setup_ms = 0.0;
     // --- event brackets of kernel families (cpr_profile) ---
     bool prof = false;
+    unsigned prof_mask = 0;           // families bracketed while prof is on (bit f = family f)
     static constexpr int kProfSlots = 512;
     cudaEvent_t ev_a[kProfSlots] = {}, ev_b[kProfSlots] = {};
     int ev_fam[kProfSlots] = {};
@@ -208,7 +209,7 @@ struct cpr_handle {
         unsigned long long kernels = 0;        // kernel nodes: launches per graph launch
     } sg[2];
     int sg_epoch = -1;
-    bool sg_prof = false;
+    unsigned sg_prof = 0;            // prof_mask the step graphs were captured with (0: none)
     int capturing = -1;              // index of the step graph being captured, -1 = none
     StepGraph sgb[2];                // the batched step graphs
     int sgb_epoch = -1;

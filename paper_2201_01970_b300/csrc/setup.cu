@@ -1001,6 +1001,43 @@ __global__ void k_scatter_color(int n, const int *color, int c, const int *pos, 
     if (i < n && color[i] == c) rows[base + pos[i]] = i;
 }
 
+// Counting sort of rows by color (index order kept within a color), for up to
+// kSortColors colors: tiles of kColorTile rows.  cnt is color-major,
+// cnt[c * ntiles + tile], so one exclusive scan of it gives every (color,
+// tile) its first output position directly.
+constexpr int kColorTile = 1024;
+constexpr int kSortColors = 64;
+
+__global__ void __launch_bounds__(kColorTile) k_color_tile_counts(int n, int ncolors, int ntiles,
+                                                                   const int *color, int *cnt) {
+    __shared__ int sh[kSortColors];
+    for (int c = threadIdx.x; c < ncolors; c += blockDim.x) sh[c] = 0;
+    __syncthreads();
+    int i = blockIdx.x * kColorTile + threadIdx.x;
+    if (i < n) atomicAdd(&sh[color[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncolors; c += blockDim.x) cnt[(size_t)c * ntiles + blockIdx.x] = sh[c];
+}
+
+// rows[pos(color_i, tile) + rank of i among the tile's rows of that color] = i
+__global__ void __launch_bounds__(kColorTile) k_color_tile_scatter(int n, int ncolors, int ntiles,
+                                                                    const int *color, const int *pos, int *rows) {
+    __shared__ int wc[kColorTile / 32][kSortColors];   // per-warp color counts
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kColorTile / 32) * kSortColors; k += blockDim.x) (&wc[0][0])[k] = 0;
+    __syncthreads();
+    int i = blockIdx.x * kColorTile + threadIdx.x;
+    int c = i < n ? color[i] : -1;
+    unsigned same = __match_any_sync(0xffffffffu, c);
+    int in_warp = __popc(same & ((1u << lane) - 1u));
+    if (c >= 0 && in_warp == 0) wc[w][c] = __popc(same);
+    __syncthreads();
+    if (c < 0) return;
+    int before = 0;
+    for (int v = 0; v < w; v++) before += wc[v][c];
+    rows[pos[(size_t)c * ntiles + blockIdx.x] + before + in_warp] = i;
+}
+
 __global__ void k_iperm(int n, const int *order, int *iperm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) iperm[order[t]] = t;
@@ -1467,6 +1504,18 @@ void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vec
     off.assign(ncolors + 1, 0);
     for (int c = 0; c < ncolors; c++) off[c + 1] = off[c] + hh[c];
     rows.alloc(n, s);
+    if (ncolors <= kSortColors) {
+        int ntiles = (n + kColorTile - 1) / kColorTile;
+        DVec<int> cnt;
+        cnt.alloc((size_t)ncolors * ntiles, s);
+        pos.alloc((size_t)ncolors * ntiles + 1, s);
+        k_color_tile_counts<<<ntiles, kColorTile, 0, s>>>(n, ncolors, ntiles, color, cnt.p);
+        CK_LAUNCH();
+        exclusive_scan(cnt.p, pos.p, ncolors * ntiles, s);
+        k_color_tile_scatter<<<ntiles, kColorTile, 0, s>>>(n, ncolors, ntiles, color, pos.p, rows.p);
+        CK_LAUNCH();
+        return;
+    }
     flag.alloc(n, s);
     pos.alloc(n + 1, s);
     for (int c = 0; c < ncolors; c++) {
@@ -1478,7 +1527,6 @@ void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vec
     }
 }
 
-// C = A B (structural pattern, sorted; values in Gustavson order).
 // C = A B (structural pattern, sorted; values in Gustavson order).  Rows with
 // at most kSmallCand candidates run with small tables, the listed rest with
 // large ones; every row is written by exactly one of the two launches.

@@ -1283,7 +1283,8 @@ void record_step(cpr_handle *h) {
 
 // (Re)capture the two step graphs when B, the workspace or profiling changed.
 void ensure_step_graphs(cpr_handle *h) {
-    if (h->sg_epoch == h->epoch && h->sg_prof == h->prof && h->sg[0].exec && h->sg[1].exec) return;
+    unsigned pm = h->prof ? h->prof_mask : 0u;
+    if (h->sg_epoch == h->epoch && h->sg_prof == pm && h->sg[0].exec && h->sg[1].exec) return;
     destroy_step_graphs(h);
     for (int k = 0; k < 2; k++) {
         cudaGraph_t g = nullptr;
@@ -1307,7 +1308,7 @@ void ensure_step_graphs(cpr_handle *h) {
         CK(cudaGraphInstantiate(&h->sg[k].exec, g, 0));
     }
     h->sg_epoch = h->epoch;
-    h->sg_prof = h->prof;
+    h->sg_prof = pm;
 }
 
 // Flexible GMRES(m), right-preconditioned with B (Alg. 2): CGS Arnoldi, Givens
