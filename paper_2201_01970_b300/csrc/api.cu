@@ -395,9 +395,14 @@ void cpr_destroy(cpr_handle *h) {
         if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
     }
     h->pinned = nullptr;
-    delete h;  // DVec destructors free on the stream
+    cudaStream_t side = h->side;
+    delete h;  // DVec destructors free on the stream each buffer was allocated on
     if (s) cudaStreamSynchronize(s);
     if (own && s) cudaStreamDestroy(s);
+    if (side) {
+        cudaStreamSynchronize(side);
+        cudaStreamDestroy(side);
+    }
 }
 
 int cpr_apply(cpr_handle *h, const double *v, double *z) {

@@ -40,23 +40,29 @@ void check_cuda(cudaError_t e, const char *expr, const char *file, int line) {
     fail(code, buf);
 }
 
+// Two pools per device: 0 for the handle's own stream, 1 for the setup's side
+// worker thread (selected per host thread), so buffers allocated and freed on
+// the side stream never interleave with the main stream's in one pool.
+static thread_local int t_pool = 0;
+void use_side_pool(bool on) { t_pool = on ? 1 : 0; }
+
 cudaMemPool_t library_pool() {
     static std::mutex mu;
-    static cudaMemPool_t pools[64] = {};
+    static cudaMemPool_t pools[64][2] = {};
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) fail(CPR_ERR_INVALID, "device index out of range");
     std::lock_guard<std::mutex> lock(mu);
-    if (!pools[dev]) {
+    if (!pools[dev][t_pool]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
         props.location.type = cudaMemLocationTypeDevice;
         props.location.id = dev;
-        CK(cudaMemPoolCreate(&pools[dev], &props));
+        CK(cudaMemPoolCreate(&pools[dev][t_pool], &props));
         uint64_t keep = UINT64_MAX;
-        CK(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+        CK(cudaMemPoolSetAttribute(pools[dev][t_pool], cudaMemPoolAttrReleaseThreshold, &keep));
     }
-    return pools[dev];
+    return pools[dev][t_pool];
 }
 
 int grid_for(long n, int block, int cap) {

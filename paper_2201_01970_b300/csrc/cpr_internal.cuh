@@ -40,6 +40,7 @@ unsigned long long graph_kernel_nodes(cudaGraph_t g);
 // threshold is unlimited: memory freed by one setup is reused by the next
 // instead of going back to the driver at every synchronisation.
 cudaMemPool_t library_pool();
+void use_side_pool(bool on);   // this host thread allocates from the side pool
 
 // Stream-ordered device allocation from the library pool; move-only.
 template <class T>
@@ -154,6 +155,7 @@ struct BatchInfo {
 struct cpr_handle {
     cpr_opts opt{};
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;      // setup's side worker stream (created on first use)
     bool own_stream = false;
     int nb = 0, nnzb = 0;
     cpr::DVec<int> rowptr, col;     // outer operator A^(k) (copy)

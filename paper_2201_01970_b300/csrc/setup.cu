@@ -16,6 +16,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <condition_variable>
+#include <deque>
+#include <exception>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <type_traits>
 
 #include "cpr_internal.cuh"
@@ -1454,8 +1460,7 @@ Graph sym_union(const Graph &S, cudaStream_t s) {
 }
 
 // Jones-Plassmann coloring of graph G; returns the number of colors.
-int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &color) {
-    cudaStream_t s = h->stream;
+int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &color, cudaStream_t s) {
     int n = G.n;
     DVec<unsigned long long> state;
     state.alloc(n, s);
@@ -1490,9 +1495,8 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
 }
 
 // Rows grouped by color, index-ascending within a color.
-void rows_by_color(cpr_handle *h, int n, const int *color, int ncolors, std::vector<int> &off,
-                   DVec<int> &rows) {
-    cudaStream_t s = h->stream;
+void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, DVec<int> &rows,
+                   cudaStream_t s) {
     DVec<int> hist, flag, pos;
     hist.alloc(ncolors, s);
     hist.zero();
@@ -1647,6 +1651,80 @@ void free_preconditioner(cpr_handle *h) {
 
 // Wall-clock phase marks of one setup, printed to stderr when the environment
 // variable CPR_SETUP_TIMING is set (diagnostics only).
+// Setup work that needs only its own inputs -- the BILU(0) second stage
+// (needs A) and each level's smoother coloring (needs A_l) -- runs on a
+// worker host thread with its own stream while this thread builds the AMG
+// chain.  Both chains are long sequences of small kernels with host
+// read-backs, so running them side by side keeps the GPU and the host busy.
+// A task starts behind an event of the main stream; join() makes the main
+// stream wait for everything the worker issued and rethrows its error.
+class SideWorker {
+  public:
+    SideWorker(cpr_handle *h) : h_(h) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        th_ = std::thread([this, dev] { run(dev); });
+    }
+    ~SideWorker() {
+        if (th_.joinable()) {   // unwinding: let the side work finish before the caller's buffers go
+            stop();
+            th_.join();
+            cudaStreamSynchronize(h_->side);
+        }
+    }
+    cudaStream_t stream() const { return h_->side; }
+    // Run f on the worker.  Callers post right after a host read-back of the
+    // main stream, so everything f reads from it is already complete and no
+    // cross-stream event is needed.
+    void post(std::function<void()> f) {
+        std::lock_guard<std::mutex> lk(mu_);
+        q_.push_back(std::move(f));
+        cv_.notify_one();
+    }
+    // Wait for the worker and for everything it issued on the side stream.
+    void join() {
+        stop();
+        th_.join();
+        if (err_) std::rethrow_exception(err_);
+        CK(cudaStreamSynchronize(h_->side));
+    }
+
+  private:
+    void stop() {
+        std::lock_guard<std::mutex> lk(mu_);
+        done_ = true;
+        cv_.notify_one();
+    }
+    void run(int dev) {
+        cudaSetDevice(dev);
+        use_side_pool(true);
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [this] { return done_ || !q_.empty(); });
+                if (q_.empty()) return;
+                f = std::move(q_.front());
+                q_.pop_front();
+            }
+            if (err_) continue;   // after a failure, drain without running
+            try {
+                f();
+            } catch (...) {
+                err_ = std::current_exception();
+            }
+        }
+    }
+    cpr_handle *h_;
+    std::thread th_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::function<void()>> q_;
+    bool done_ = false;
+    std::exception_ptr err_;
+};
+
 struct PhaseClock {
     bool on = getenv("CPR_SETUP_TIMING") != nullptr;
     cudaStream_t s;
@@ -1675,6 +1753,8 @@ void build_preconditioner(cpr_handle *h) {
     const cpr_opts &o = h->opt;
     int nb = h->nb, nnzb = h->nnzb;
     bool f32 = o.precond_fp32 != 0;
+    // levels are referenced by the side worker while this thread appends: no reallocation
+    h->lev.reserve((size_t)std::max(1, o.max_levels) + 1);
 
     // ---- decoupling and the pressure matrix A_P (level 0) ----
     DVec<int> bdiag;
@@ -1699,6 +1779,80 @@ void build_preconditioner(cpr_handle *h) {
     }
 
     clk.mark("decouple");
+    // ---- second stage: multicolor BILU(0), on the side worker ----
+    SideWorker side(h);
+    side.post([h, nb, nnzb, f32, &bdiag, &side] {
+        cudaStream_t s = side.stream();
+        Bilu &B = h->bilu;
+        Graph S = build_pattern(nb, s, [&](const int *srow, int *out) {
+            k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, srow, out);
+            CK_LAUNCH();
+        });
+        Graph G = sym_union(S, s);
+        B.ncolors = jp_color(h, G, 2, 0, B.color, s);
+        rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
+        B.iperm.alloc(nb, s);
+        k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
+        CK_LAUNCH();
+        DVec<int> lcnt, ucnt;
+        lcnt.alloc(nb, s);
+        ucnt.alloc(nb, s);
+        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
+                                                                  B.color.p, lcnt.p, ucnt.p);
+        CK_LAUNCH();
+        B.Lrowptr.alloc(nb + 1, s);
+        B.Urowptr.alloc(nb + 1, s);
+        exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
+        exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
+        int nl = read_int(B.Lrowptr.p + nb, s), nu = read_int(B.Urowptr.p + nb, s);
+        B.Lcol.alloc(std::max(nl, 1), s);
+        B.Ucol.alloc(std::max(nu, 1), s);
+        auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
+            using T = std::remove_pointer_t<decltype(lu)>;
+            for (int c = 0; c < B.ncolors; c++) {
+                int cnt = B.color_off[c + 1] - B.color_off[c];
+                if (!cnt) continue;
+                k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
+                                                                         h->rowptr.p, h->col.p, B.color.p,
+                                                                         bdiag.p, lu, h->err.p);
+                CK_LAUNCH();
+            }
+            // a singular pivot block is reported by the check at the end of the setup
+            k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
+                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
+                B.Ucol.p, Uv, Dv);
+            CK_LAUNCH();
+        };
+        if (f32) {
+            B.lu32.alloc(9 * (size_t)nnzb, s);
+            k_d2f<<<grid_for(9L * nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(9L * nnzb, h->val.p, B.lu32.p);
+            CK_LAUNCH();
+            B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
+            B.Uval32.alloc(9 * (size_t)std::max(nu, 1), s);
+            B.Dinv32.alloc(9 * (size_t)nb, s);
+            factor_and_split(B.lu32.p, B.Lval32.p, B.Uval32.p, B.Dinv32.p);
+        } else {
+            B.lu.alloc(9 * (size_t)nnzb, s);
+            CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
+            B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
+            B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
+            B.Dinv.alloc(9 * (size_t)nb, s);
+            factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
+        }
+        // the frozen column-0 copy of A in positions
+        DVec<int> ccnt;
+        ccnt.alloc(nb, s);
+        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                           h->val.p, nullptr, nullptr, nullptr, ccnt.p);
+        CK_LAUNCH();
+        h->c0rowptr.alloc(nb + 1, s);
+        exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
+        h->c0col.alloc(nnzb, s);
+        h->pcol0.alloc(3 * (size_t)nnzb, s);
+        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                           h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
+        CK_LAUNCH();
+    });
     // ---- the AMG hierarchy ----
     for (int l = 0;; l++) {
         int n = h->lev[l].A.n;
@@ -1766,6 +1920,21 @@ void build_preconditioner(cpr_handle *h) {
             break;
         }
         L.nc = nc;
+        // the smoother's coloring of this level (Eq. 5.1 strength, symmetrised,
+        // JP), on the side worker: it needs only A_l, and
+        // level l is smoothed now that it is not the coarsest
+        side.post([h, l, n, &side] {
+            cudaStream_t s = side.stream();
+            Level &L = h->lev[l];
+            Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
+                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
+                                                                   h->opt.theta_color, srow, out);
+                CK_LAUNCH();
+            });
+            Graph G = sym_union(Sc, s);
+            L.ncolors = jp_color(h, G, 0, l, L.color, s);
+            rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
+        });
         // direct interpolation P and R = P^T
         {
             DVec<int> cnt;
@@ -1795,18 +1964,6 @@ void build_preconditioner(cpr_handle *h) {
         spgemm(L.R, AP, Ac, s);
         AP = DCsr{};
         clk.mark("rap");
-        // the smoother's coloring: Eq. 5.1 strength, symmetrised, JP
-        {
-            Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
-                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
-                                                                   o.theta_color, srow, out);
-                CK_LAUNCH();
-            });
-            Graph G = sym_union(Sc, s);
-            L.ncolors = jp_color(h, G, 0, l, L.color);
-            rows_by_color(h, n, L.color.p, L.ncolors, L.color_off, L.rows_by_color);
-        }
-        clk.mark("color");
         h->lev.emplace_back();
         h->lev[l + 1].A = std::move(Ac);
     }
@@ -1849,83 +2006,8 @@ void build_preconditioner(cpr_handle *h) {
     }
 
     clk.mark("coarse");
-    // ---- second stage: multicolor BILU(0) ----
-    {
-        Bilu &B = h->bilu;
-        Graph S = build_pattern(nb, s, [&](const int *srow, int *out) {
-            k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, srow, out);
-            CK_LAUNCH();
-        });
-        Graph G = sym_union(S, s);
-        clk.mark("bilu_graph");
-        B.ncolors = jp_color(h, G, 2, 0, B.color);
-        clk.mark("bilu_jp");
-        rows_by_color(h, nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color);
-        clk.mark("bilu_rows");
-        B.iperm.alloc(nb, s);
-        k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
-        CK_LAUNCH();
-        DVec<int> lcnt, ucnt;
-        lcnt.alloc(nb, s);
-        ucnt.alloc(nb, s);
-        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
-                                                                  B.color.p, lcnt.p, ucnt.p);
-        CK_LAUNCH();
-        B.Lrowptr.alloc(nb + 1, s);
-        B.Urowptr.alloc(nb + 1, s);
-        exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
-        exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
-        int nl = read_int(B.Lrowptr.p + nb, s), nu = read_int(B.Urowptr.p + nb, s);
-        B.Lcol.alloc(std::max(nl, 1), s);
-        B.Ucol.alloc(std::max(nu, 1), s);
-        clk.mark("bilu_split_count");
-        auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
-            using T = std::remove_pointer_t<decltype(lu)>;
-            for (int c = 0; c < B.ncolors; c++) {
-                int cnt = B.color_off[c + 1] - B.color_off[c];
-                if (!cnt) continue;
-                k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                                         h->rowptr.p, h->col.p, B.color.p,
-                                                                         bdiag.p, lu, h->err.p);
-                CK_LAUNCH();
-            }
-            // a singular pivot block is reported by the check at the end of the setup
-            k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
-                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
-                B.Ucol.p, Uv, Dv);
-            CK_LAUNCH();
-        };
-        if (f32) {
-            B.lu32.alloc(9 * (size_t)nnzb, s);
-            k_d2f<<<grid_for(9L * nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(9L * nnzb, h->val.p, B.lu32.p);
-            CK_LAUNCH();
-            B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
-            B.Uval32.alloc(9 * (size_t)std::max(nu, 1), s);
-            B.Dinv32.alloc(9 * (size_t)nb, s);
-            factor_and_split(B.lu32.p, B.Lval32.p, B.Uval32.p, B.Dinv32.p);
-        } else {
-            B.lu.alloc(9 * (size_t)nnzb, s);
-            CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
-            B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
-            B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
-            B.Dinv.alloc(9 * (size_t)nb, s);
-            factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
-        }
-        // the frozen column-0 copy of A in positions
-        DVec<int> ccnt;
-        ccnt.alloc(nb, s);
-        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                           h->val.p, nullptr, nullptr, nullptr, ccnt.p);
-        CK_LAUNCH();
-        h->c0rowptr.alloc(nb + 1, s);
-        exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
-        h->c0col.alloc(nnzb, s);
-        h->pcol0.alloc(3 * (size_t)nnzb, s);
-        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                           h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
-        CK_LAUNCH();
-    }
-    clk.mark("bilu");
+    side.join();
+    clk.mark("side_join");
     // ---- solve copies in color order, FP32 shadows, work vectors ----
     int L = (int)h->lev.size();
     for (int l = 0; l < L; l++) {
