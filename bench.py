@@ -644,19 +644,19 @@ def main():
     f64 = fam_report(r64, 8)
     sm0 = f32.get("smooth0", {})
     sp = f32.get("spmv", {})
-    # The outer BSR SpMV is the largest single kernel of the step (launch-list
-    # share); its bound is B300's FP64 pipe.  Peak: the FP64 FMA rate ncu
-    # reports for this GPU (296 DFMA thread-instructions per cycle) x 2 flops x
-    # the maximum SM clock.  traffic: dram__bytes_read.sum + dram__bytes_write.sum
-    # of one launch of this kernel from the ncu capture summarised in
-    # profiles/hot_kernels_128x128x32_fp32.md (350.85 MB read + 11.30 MB written).
+    # The outer SpMV is the largest single kernel of the step (launch-list
+    # share); its bound is B300's FP64 pipe (91 % active under ncu).  Peak: the
+    # FP64 FMA rate ncu reports for this GPU (296 DFMA thread-instructions per
+    # cycle) x 2 flops x the maximum SM clock.  traffic: dram__bytes_read.sum +
+    # dram__bytes_write.sum of one launch of k_sell_spmv from the ncu capture
+    # summarised in profiles/spmv_sell_128x128x32.md (290.51 MB read + 9.96 MB written).
     fp64_peak = 296 * 2 * 2.032e9 / 1e12
     spmv_tflops = (18.0 * nnzb / (sp["avg_us"] * 1e-6) / 1e12) if sp.get("avg_us") else None
-    roof = {"kernel": "k_bsr3_spmv (outer FP64 BSR SpMV, w = A z)", "bound": "alu",
+    roof = {"kernel": "k_sell_spmv (outer FP64 SpMV on the sliced-ELL copy, w = A z)", "bound": "alu",
             "achieved": spmv_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
             "peak_kind": "FP64 FMA rate x max SM clock (derived, ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak)",
-            "traffic": 362.16e6 if WORKLOAD == "128x128x32" else None,
+            "traffic": 300.47e6 if WORKLOAD == "128x128x32" else None,
             "flops_per_launch": 18.0 * nnzb, "bytes_per_launch": spmv_bytes(nb, nnzb),
             "hbm_gbs": sp.get("gbs"), "hbm_frac_of_measured": (sp.get("gbs") / hbm) if sp.get("gbs") else None}
     roof_sm = {"kernel": "k_smooth_color on the finest pressure level (multi-color GS color sweep, FP32)",

@@ -282,6 +282,7 @@ int cpr_setup(cpr_handle **out, const cpr_bsr3 *A, const cpr_opts *opts) {
         h->nnzb = A->nnzb;
         h->val.alloc(9 * (size_t)A->nnzb, h->stream);
         copy_in(h->val.p, A->val, sizeof(double) * 9 * (size_t)A->nnzb, h->stream);
+        refresh_outer(h, true);
         h->updates = 1;
         build_timed(h);
         return CPR_OK;
@@ -318,6 +319,7 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
             h->val.alloc(9 * (size_t)A->nnzb, s);
         }
         copy_in(h->val.p, A->val, sizeof(double) * 9 * (size_t)A->nnzb, s);
+        refresh_outer(h, !same);
         h->updates++;
         // Alg. 3: reuse B^(k-1) iff k > 1 and It^(k-1) <= mu (and Remark 4.2: same size/pattern)
         bool reuse = same && h->have_B && h->last_iters >= 0 && h->last_iters <= h->opt.mu;

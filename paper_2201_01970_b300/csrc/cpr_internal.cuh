@@ -156,6 +156,14 @@ struct cpr_handle {
     cpr_opts opt{};
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;      // setup's side worker stream (created on first use)
+    // Sliced-ELL copy of the outer operator for the SpMV: slices of 32 block
+    // rows; slot k of a slice holds each of its rows' k-th block (column -1
+    // past a row's end), the nine values of a slot lane-contiguous per block
+    // entry, so a warp's loads are contiguous.  Refreshed with every new A.
+    cpr::DVec<int> sell_off, sell_col, sell_pos;
+    cpr::DVec<double> sell_val;
+    int sell_slices = 0;
+    bool sell_ok = false;
     bool own_stream = false;
     int nb = 0, nnzb = 0;
     cpr::DVec<int> rowptr, col;     // outer operator A^(k) (copy)
@@ -251,6 +259,7 @@ void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, do
              long z_ld);
 void vcycle_apply(cpr_handle *h, const double *b, double *x);
 void bilu_apply(cpr_handle *h, const double *r, double *z);
+void refresh_outer(cpr_handle *h, bool pattern_changed);
 int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
 void batch_prepare(cpr_handle *h);

@@ -254,6 +254,84 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
     }
 }
 
+// The same product on the sliced-ELL copy: one warp per slice of 32 block
+// rows, lane = row.  A row's blocks are taken in the same order with the same
+// FMA sequence as k_bsr3_spmv<1>, so the result is bit-identical; the value
+// loads of a warp are 256 contiguous bytes per block entry.
+__global__ void __launch_bounds__(256) k_sell_spmv(int nslices, int nb, const int *__restrict__ off,
+                                                   const int *__restrict__ col, const double *__restrict__ val,
+                                                   const double *__restrict__ x_base, long xld, const int *jptr,
+                                                   const double *__restrict__ b, double *__restrict__ y,
+                                                   const int *done) {
+    if (done && *done) return;
+    int slice = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (slice >= nslices) return;
+    const double *x = x_base + (size_t)step_of(jptr) * xld;
+    int row = slice * 32 + lane;
+    int k0 = off[slice], k1 = off[slice + 1];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int k = k0; k < k1; k++) {
+        int c = col[(size_t)k * 32 + lane];
+        if (c < 0) continue;
+        const double *v = val + (size_t)k * 288 + lane;
+        const double *xj = x + 3 * (size_t)c;
+        double x0 = xj[0], x1 = xj[1], x2 = xj[2];
+        a0 = fma(v[0], x0, a0);
+        a0 = fma(v[32], x1, a0);
+        a0 = fma(v[64], x2, a0);
+        a1 = fma(v[96], x0, a1);
+        a1 = fma(v[128], x1, a1);
+        a1 = fma(v[160], x2, a1);
+        a2 = fma(v[192], x0, a2);
+        a2 = fma(v[224], x1, a2);
+        a2 = fma(v[256], x2, a2);
+    }
+    if (row < nb) {
+        size_t q = 3 * (size_t)row;
+        if (b) {
+            y[q] = b[q] - a0;
+            y[q + 1] = b[q + 1] - a1;
+            y[q + 2] = b[q + 2] - a2;
+        } else {
+            y[q] = a0;
+            y[q + 1] = a1;
+            y[q + 2] = a2;
+        }
+    }
+}
+
+// Sliced-ELL build: slot count per slice (its longest row), then each block's
+// slot (pos) and column, then the values.
+__global__ void k_sell_width(int nb, int nslices, const int *rowptr, int *width) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int w = 0;
+    for (int i = s * 32; i < min(nb, s * 32 + 32); i++) w = max(w, rowptr[i + 1] - rowptr[i]);
+    width[s] = w;
+}
+
+__global__ void k_sell_pattern(int nb, const int *rowptr, const int *col, const int *off, int *scol, int *pos) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    int s = i >> 5, lane = i & 31;
+    int slot = off[s];
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++, slot++) {
+        scol[(size_t)slot * 32 + lane] = col[p];
+        pos[p] = slot * 32 + lane;
+    }
+}
+
+__global__ void k_sell_values(long nnzb, const int *pos, const double *val, double *sval) {
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < nnzb; p += (long)gridDim.x * blockDim.x) {
+        int q = pos[p];
+        double *d = sval + (size_t)(q >> 5) * 288 + (q & 31);
+        const double *v = val + 9 * (size_t)p;
+#pragma unroll
+        for (int e = 0; e < 9; e++) d[32 * e] = v[e];
+    }
+}
+
 // ------------------------------------------------------ multi-color GS (Alg. 6)
 //
 // Levels are renumbered so that each color is a contiguous row range.  A
@@ -1048,6 +1126,20 @@ void spmv_launch(int nb, const int *rowptr, const int *col, const double *val, c
     CK_LAUNCH();
 }
 
+// y = A x (or b - A x) with the handle's outer operator: the sliced-ELL copy
+// when it is current, else the BSR arrays.
+void spmv_h(cpr_handle *h, const double *x, long xld, const int *jptr, const double *b, double *y,
+            cudaStream_t s, const int *done) {
+    if (!h->sell_ok) {
+        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, xld, jptr, b, y, s, done);
+        return;
+    }
+    unsigned blocks = (unsigned)((h->sell_slices + 7) / 8);
+    k_sell_spmv<<<blocks, 256, 0, s>>>(h->sell_slices, h->nb, h->sell_off.p, h->sell_col.p, h->sell_val.p, x, xld,
+                                       jptr, b, y, done);
+    CK_LAUNCH();
+}
+
 // ||a||^2 partials into h->red, then a one-thread kernel consumes them.
 void norm_partials(cpr_handle *h, const double *a, long n) {
     k_dot_partial<<<kRedBlocks, kBlock, 0, h->stream>>>(n, a, a, h->red.p);
@@ -1057,6 +1149,36 @@ void norm_partials(cpr_handle *h, const double *a, long n) {
 }  // namespace
 
 // ================================================================== public
+
+// Rebuild the sliced-ELL copy of the outer operator after a new A: its
+// pattern when the pattern changed (or was never built), always its values.
+void refresh_outer(cpr_handle *h, bool pattern_changed) {
+    cudaStream_t s = h->stream;
+    int nb = h->nb;
+    long nnzb = h->nnzb;
+    if (pattern_changed || !h->sell_ok) {
+        h->sell_ok = false;
+        int nsl = (nb + 31) / 32;
+        DVec<int> width;
+        width.alloc(nsl, s);
+        k_sell_width<<<grid_for(nsl, kBlock), kBlock, 0, s>>>(nb, nsl, h->rowptr.p, width.p);
+        CK_LAUNCH();
+        h->sell_off.alloc(nsl + 1, s);
+        exclusive_scan(width.p, h->sell_off.p, nsl, s);
+        int slots = read_int(h->sell_off.p + nsl, s);
+        h->sell_col.alloc(32 * (size_t)std::max(slots, 1), s);
+        CK(cudaMemsetAsync(h->sell_col.p, 0xff, sizeof(int) * 32 * (size_t)std::max(slots, 1), s));
+        h->sell_pos.alloc(std::max<long>(nnzb, 1), s);
+        k_sell_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, h->sell_off.p,
+                                                              h->sell_col.p, h->sell_pos.p);
+        CK_LAUNCH();
+        h->sell_val.alloc(288 * (size_t)std::max(slots, 1), s);
+        h->sell_slices = nsl;
+    }
+    k_sell_values<<<grid_for(nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(nnzb, h->sell_pos.p, h->val.p, h->sell_val.p);
+    CK_LAUNCH();
+    h->sell_ok = true;
+}
 
 void bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val, const double *x,
                const double *b, double *y, cudaStream_t s) {
@@ -1266,7 +1388,7 @@ void record_step(cpr_handle *h) {
     if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
     else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
     prof_begin(h, CPR_PROF_SPMV);
-    spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
+    spmv_h(h, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
     prof_end(h);
     // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||, Givens
     prof_begin(h, CPR_PROF_CGS);
@@ -1328,7 +1450,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
     int ldp = kMaxRestart + 2;
     for (int cycle = 0; cycle < h->opt.max_restarts; cycle++) {
         // r = b - A x, beta = ||r||, V_0 = r / beta
-        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
+        spmv_h(h, x, 0, nullptr, b, h->r.p, s, nullptr);
         norm_partials(h, h->r.p, N);
         k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, cycle == 0, rtol);
         CK_LAUNCH();
@@ -1401,7 +1523,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
     }
     if (rc == CPR_NOT_CONVERGED && cycles == h->opt.max_restarts) {
         // true residual after the last cycle
-        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, b, h->r.p, s, nullptr);
+        spmv_h(h, x, 0, nullptr, b, h->r.p, s, nullptr);
         norm_partials(h, h->r.p, N);
         k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, 0, rtol);
         CK_LAUNCH();
@@ -1670,7 +1792,7 @@ void record_step_batch(cpr_handle *h) {
     int ldp = kMaxRestart + 2;
     if (h->opt.precond_fp32) apply_B_t<float>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
     else apply_B_t<double>(h, h->V.p, N, di + I_J, h->Z.p, N, done);
-    spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
+    spmv_h(h, h->Z.p, N, di + I_J, nullptr, h->wv.p, s, done);
     k_bdots<<<B.nchunk, kBlock, 0, s>>>(h->V.p, h->wv.p, N, di + I_J, B.chunk_beg.p, B.chunk_end.p, B.part.p, ldp,
                                         done);
     CK_LAUNCH();
@@ -1771,7 +1893,7 @@ int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st) {
     }
     int cycles = 0;
     for (int cycle = 0; cycle <= h->opt.max_restarts; cycle++) {
-        spmv_launch(h->nb, h->rowptr.p, h->col.p, h->val.p, x, 0, nullptr, B.b.p, h->r.p, s, nullptr);
+        spmv_h(h, x, 0, nullptr, B.b.p, h->r.p, s, nullptr);
         k_bnorm_part<<<B.nchunk, kBlock, 0, s>>>(h->r.p, B.chunk_beg.p, B.chunk_end.p, B.part2.p);
         CK_LAUNCH();
         k_bcycle_start<<<1, 1024, 0, s>>>(B.nsys, B.sys_chunk_off.p, B.part2.p, B.scal.p, ssz, m, B.sint.p, di,
