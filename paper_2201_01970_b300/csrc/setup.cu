@@ -676,14 +676,17 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 // every C entry is summed in the same order as Gustavson's row-by-row product.
 // Rows with more distinct columns than the table holds take an exact slow path.
 
-// Two table sizes.  Rows with at most kSmallCand candidate products (all but
-// a few rows at the fine levels: level 0's A P has ~11 per row) run with
-// small per-warp tables at full occupancy; the other rows, listed by a
-// candidate-count pass, run with large tables.
+// Three table sizes.  Rows with at most kSmallCand candidate products (all
+// but a few rows of A P at the fine levels: level 0's has ~11 per row) run
+// with small per-warp tables at full occupancy; rows up to kMidCand (most of
+// R (A P): ~70 per coarse row at level 0) with medium tables, still at full
+// occupancy; the rest with large tables.  A candidate-count pass lists the
+// medium and large rows.
 //   CAP: hash slots per warp (power of two); HMAX: distinct columns handled
 //   in shared memory, a power of two (larger rows take the exact slow path);
 //   WARPS per block.
 constexpr int kSmallCand = 32;
+constexpr int kMidCand = 160;   // rows above kSmallCand and up to this: 256-slot tables
 constexpr int kEmpty = -1;
 
 // Per-warp scratch for enumerating the products of one chunk of 32 A entries:
@@ -796,9 +799,11 @@ __device__ int next_col(int i, long last, const int *ar, const int *ac, const in
     return m;
 }
 
-// Rows of A B with more than kSmallCand candidate products (sum over k in
-// A_i of |B_k|), appended to a list in any order.
-__global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *big, int *nbig) {
+// Rows of A B by candidate product count (sum over k in A_i of |B_k|):
+// above kSmallCand and up to kMidCand into `mid`, above kMidCand into `big`,
+// each list in any order.
+__global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *mid, int *nmid, int *big,
+                              int *nbig) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = 0;
@@ -806,7 +811,8 @@ __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br
         int k = ac[p];
         c += br[k + 1] - br[k];
     }
-    if (c > kSmallCand) big[atomicAdd(nbig, 1)] = i;
+    if (c > kMidCand) big[atomicAdd(nbig, 1)] = i;
+    else if (c > kSmallCand) mid[atomicAdd(nmid, 1)] = i;
 }
 
 // One warp per row, grid-stride: rows 0..n-1, or the *nrows rows listed in
@@ -1535,23 +1541,28 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
 // at most kSmallCand candidates run with small tables, the listed rest with
 // large ones; every row is written by exactly one of the two launches.
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
-    constexpr int kSW = 16, kBW = 4;   // warps per block, small and large tables
+    constexpr int kSW = 16, kMW = 8, kBW = 4;   // warps per block: small, medium and large tables
     int n = A.n;
-    DVec<int> ucnt, big, nbig;
+    DVec<int> ucnt, mid, big, cnts;
     ucnt.alloc(std::max(n, 1), s);
+    mid.alloc(std::max(n, 1), s);
     big.alloc(std::max(n, 1), s);
-    nbig.alloc(1, s);
-    CK(cudaMemsetAsync(nbig.p, 0, sizeof(int), s));
-    k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, big.p,
-                                                                      nbig.p);
+    cnts.alloc(2, s);
+    cnts.zero();
+    k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, mid.p,
+                                                                      cnts.p, big.p, cnts.p + 1);
     CK_LAUNCH();
-    // the listed rows run on a fixed grid that reads their count on the device
+    // the listed rows run on fixed grids that read their counts on the device
     unsigned sblocks = (unsigned)((n + kSW - 1) / kSW);
+    unsigned mblocks = (unsigned)grid_for(n, kMW, 148 * 8);
     unsigned bblocks = (unsigned)grid_for(n, kBW, 148 * 8);
     k_spgemm_rowcount<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(n, nullptr, nullptr, A.rowptr.p,
                                                                               A.col.p, B.rowptr.p, B.col.p, ucnt.p);
     CK_LAUNCH();
-    k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(n, big.p, nbig.p, A.rowptr.p, A.col.p,
+    k_spgemm_rowcount<256, 128, kMW, false><<<mblocks, kMW * 32, 0, s>>>(n, mid.p, cnts.p, A.rowptr.p, A.col.p,
+                                                                          B.rowptr.p, B.col.p, ucnt.p);
+    CK_LAUNCH();
+    k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(n, big.p, cnts.p + 1, A.rowptr.p, A.col.p,
                                                                            B.rowptr.p, B.col.p, ucnt.p);
     CK_LAUNCH();
     C.n = n;
@@ -1566,8 +1577,11 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
         n, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
         C.val.p);
     CK_LAUNCH();
+    k_spgemm_rowfill<256, 128, kMW, false><<<mblocks, kMW * 32, 0, s>>>(
+        n, mid.p, cnts.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
+    CK_LAUNCH();
     k_spgemm_rowfill<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(
-        n, big.p, nbig.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+        n, big.p, cnts.p + 1, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
         C.val.p);
     CK_LAUNCH();
 }
