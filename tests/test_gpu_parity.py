@@ -269,6 +269,27 @@ def test_full_size_128x128x32(torch, cpr):
     print("128x128x32:", sg)
 
 
+def test_full_size_fp32_mode_128x128x32(torch, cpr):
+    """The benchmark's configuration (FP32 preconditioner, 128x128x32): the FP32
+    mode has no oracle of its own, so check what must hold at any precision --
+    convergence of the true FP64 residual below rtol -- and that the FP32 B
+    costs at most a few more inner steps than the FP64 B on the same system."""
+    J = bs.jacobian("128x128x32")
+    dj = DevJ(torch, J)
+    b = dev(torch, J.b)
+    its = {}
+    for fp32 in (0, 1):
+        g = cpr.Solver(dj, precond_fp32=fp32, mu=30)
+        x, st = g.solve(b, rtol=1e-6)
+        x = x.cpu().numpy()
+        assert st["converged"]
+        true_rel = np.linalg.norm(J.b - oracle.bsr3_spmv(J, x)) / np.linalg.norm(J.b)
+        assert true_rel < 1e-6
+        its[fp32] = st["iters"]
+        g.close()
+    assert its[1] <= its[0] + 4, its
+
+
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_dependent_launch_changes_no_result(torch, cpr, fp32):
     """Programmatic dependent launch only moves the loads of setup-time
