@@ -391,6 +391,8 @@ void cpr_destroy(cpr_handle *h) {
     h->batch = nullptr;
     for (auto e : h->step_done)
         if (e) cudaEventDestroy(e);
+    for (auto e : h->ev_coarse)
+        if (e) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (int k = 0; k < cpr_handle::kProfSlots; k++) {
         if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);

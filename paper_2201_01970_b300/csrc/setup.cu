@@ -430,6 +430,7 @@ __global__ void k_union(int n, const int *sr, const int *sc, const int *tr, cons
 
 constexpr unsigned long long kUncolored = ~0ull;
 constexpr int kSmallLevel = 4096;    // levels up to this size run their rounds in one CTA
+constexpr int kJpBatch = 8;          // JP rounds launched per host check of the remaining count
 
 // One JP round r for vertex i.  A vertex uncolored at the start of the round
 // (never colored, or colored in this very round by someone else) whose key
@@ -474,7 +475,9 @@ __device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase
 __global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hbase,
                            unsigned long long *state, unsigned r, int *remaining, int *maxcolor) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    // rounds are launched in batches between host checks: once every vertex
+    // is colored the rest of the batch returns at once (the count only falls)
+    if (i >= n || *(volatile int *)remaining == 0) return;
     int c = jp_vertex(i, grow, gcol, hbase, state, r);
     if (c >= 0) {
         atomicSub(remaining, 1);
@@ -1486,7 +1489,7 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
     }
     unsigned r = 0;
     for (;;) {
-        for (int k = 0; k < 4; k++, r++) {
+        for (int k = 0; k < kJpBatch; k++, r++) {
             k_jp_round<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, r,
                                                              counters.p, counters.p + 1);
             CK_LAUNCH();
@@ -1494,6 +1497,7 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
         if (read_int(counters.p, s) == 0) break;
         if (r > (unsigned)n + 8) fail(CPR_ERR_CUDA, "coloring did not terminate");
     }
+    if (getenv("CPR_SETUP_TIMING")) fprintf(stderr, "[cpr setup] jp n=%d rounds<=%u\n", n, r);
     color.alloc(n, s);
     k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
     CK_LAUNCH();
@@ -1672,12 +1676,40 @@ void free_preconditioner(cpr_handle *h) {
 // read-backs, so running them side by side keeps the GPU and the host busy.
 // A task starts behind an event of the main stream; join() makes the main
 // stream wait for everything the worker issued and rethrows its error.
+// Phase times of a setup (CPR_SETUP_TIMING set): each mark waits for its
+// stream, so the marks serialise what they time.
+struct PhaseClock {
+    bool on = getenv("CPR_SETUP_TIMING") != nullptr;
+    cudaStream_t s;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    std::string line;
+    const char *tag = "";
+    void mark(const char *name) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        auto t = std::chrono::steady_clock::now();
+        char buf[96];
+        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(t - t0).count());
+        line += buf;
+        t0 = t;
+    }
+    ~PhaseClock() {
+        if (on) fprintf(stderr, "[cpr setup ms]%s%s\n", tag, line.c_str());
+    }
+};
+
 class SideWorker {
   public:
     SideWorker(cpr_handle *h) : h_(h) {
         int dev = 0;
         CK(cudaGetDevice(&dev));
-        if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        if (!h->side) {
+            int lo = 0, hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+        }
+        clk_.s = h->side;
+        clk_.tag = " side:";
         th_ = std::thread([this, dev] { run(dev); });
     }
     ~SideWorker() {
@@ -1688,13 +1720,31 @@ class SideWorker {
         }
     }
     cudaStream_t stream() const { return h_->side; }
-    // Run f on the worker.  Callers post right after a host read-back of the
-    // main stream, so everything f reads from it is already complete and no
-    // cross-stream event is needed.
-    void post(std::function<void()> f) {
+    void mark(const char *name) {   // phase times of the worker's own tasks
+        if (std::this_thread::get_id() == th_.get_id()) clk_.mark(name);
+    }
+    // Queue f(stream) for the worker.  Callers post right after a host
+    // read-back of the main stream, so everything f reads from it is already
+    // complete and no cross-stream event is needed.
+    using Task = std::function<void(cudaStream_t)>;
+    void post(Task f) {
         std::lock_guard<std::mutex> lk(mu_);
         q_.push_back(std::move(f));
         cv_.notify_one();
+    }
+    // Run tasks the worker has not started yet on the calling thread and
+    // stream s, newest first, while the worker goes on from the oldest.
+    void help(cudaStream_t s) {
+        for (;;) {
+            Task f;
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                if (q_.empty() || err_) return;
+                f = std::move(q_.back());
+                q_.pop_back();
+            }
+            f(s);
+        }
     }
     // Wait for the worker and for everything it issued on the side stream.
     void join() {
@@ -1714,49 +1764,33 @@ class SideWorker {
         cudaSetDevice(dev);
         use_side_pool(true);
         for (;;) {
-            std::function<void()> f;
+            Task f;
             {
                 std::unique_lock<std::mutex> lk(mu_);
                 cv_.wait(lk, [this] { return done_ || !q_.empty(); });
                 if (q_.empty()) return;
                 f = std::move(q_.front());
                 q_.pop_front();
+                if (err_) continue;   // after a failure, drain without running
             }
-            if (err_) continue;   // after a failure, drain without running
             try {
-                f();
+                f(h_->side);
             } catch (...) {
+                std::lock_guard<std::mutex> lk(mu_);
                 err_ = std::current_exception();
             }
         }
     }
     cpr_handle *h_;
+    PhaseClock clk_;
     std::thread th_;
     std::mutex mu_;
     std::condition_variable cv_;
-    std::deque<std::function<void()>> q_;
+    std::deque<Task> q_;
     bool done_ = false;
     std::exception_ptr err_;
 };
 
-struct PhaseClock {
-    bool on = getenv("CPR_SETUP_TIMING") != nullptr;
-    cudaStream_t s;
-    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
-    std::string line;
-    void mark(const char *name) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        auto t = std::chrono::steady_clock::now();
-        char buf[96];
-        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(t - t0).count());
-        line += buf;
-        t0 = t;
-    }
-    ~PhaseClock() {
-        if (on) fprintf(stderr, "[cpr setup ms]%s\n", line.c_str());
-    }
-};
 
 // Build B from the handle's current A (Sec. 3.1; the setup steps of Alg. 6 per level).
 void build_preconditioner(cpr_handle *h) {
@@ -1795,15 +1829,16 @@ void build_preconditioner(cpr_handle *h) {
     clk.mark("decouple");
     // ---- second stage: multicolor BILU(0), on the side worker ----
     SideWorker side(h);
-    side.post([h, nb, nnzb, f32, &bdiag, &side] {
-        cudaStream_t s = side.stream();
+    side.post([h, nb, nnzb, f32, &bdiag, &side](cudaStream_t s) {
         Bilu &B = h->bilu;
         Graph S = build_pattern(nb, s, [&](const int *srow, int *out) {
             k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, srow, out);
             CK_LAUNCH();
         });
         Graph G = sym_union(S, s);
+        side.mark("bilu_graph");
         B.ncolors = jp_color(h, G, 2, 0, B.color, s);
+        side.mark("bilu_jp");
         rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
         B.iperm.alloc(nb, s);
         k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
@@ -1821,6 +1856,7 @@ void build_preconditioner(cpr_handle *h) {
         int nl = read_int(B.Lrowptr.p + nb, s), nu = read_int(B.Urowptr.p + nb, s);
         B.Lcol.alloc(std::max(nl, 1), s);
         B.Ucol.alloc(std::max(nu, 1), s);
+        side.mark("bilu_order");
         auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
             using T = std::remove_pointer_t<decltype(lu)>;
             for (int c = 0; c < B.ncolors; c++) {
@@ -1853,6 +1889,7 @@ void build_preconditioner(cpr_handle *h) {
             B.Dinv.alloc(9 * (size_t)nb, s);
             factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
         }
+        side.mark("bilu_factor");
         // the frozen column-0 copy of A in positions
         DVec<int> ccnt;
         ccnt.alloc(nb, s);
@@ -1866,6 +1903,7 @@ void build_preconditioner(cpr_handle *h) {
         k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
                                                            h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
         CK_LAUNCH();
+        side.mark("col0");
     });
     // ---- the AMG hierarchy ----
     for (int l = 0;; l++) {
@@ -1937,8 +1975,8 @@ void build_preconditioner(cpr_handle *h) {
         // the smoother's coloring of this level (Eq. 5.1 strength, symmetrised,
         // JP), on the side worker: it needs only A_l, and
         // level l is smoothed now that it is not the coarsest
-        side.post([h, l, n, &side] {
-            cudaStream_t s = side.stream();
+        side.post([h, l, n, &side](cudaStream_t s) {
+            side.mark("idle");
             Level &L = h->lev[l];
             Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
                 k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
@@ -1946,8 +1984,11 @@ void build_preconditioner(cpr_handle *h) {
                 CK_LAUNCH();
             });
             Graph G = sym_union(Sc, s);
+            side.mark("c_graph");
             L.ncolors = jp_color(h, G, 0, l, L.color, s);
+            side.mark("c_jp");
             rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
+            side.mark("c_order");
         });
         // direct interpolation P and R = P^T
         {
@@ -1982,19 +2023,48 @@ void build_preconditioner(cpr_handle *h) {
         h->lev[l + 1].A = std::move(Ac);
     }
 
-    // ---- coarsest level: dense inverse ----
+    side.help(s);
+    clk.mark("side_help");
+    side.join();
+    clk.mark("side_join");
+    // ---- coarsest level: dense inverse, on the side stream ----
+    // The factorisation is FP64 work on one SM (about 0.8 ms at n = 200) that
+    // only the solve reads, so it runs on the side stream beside the layout
+    // below.  The guard makes the main stream wait for it before the final
+    // error check, and on every unwinding path, so no buffer is released or
+    // reused while the side stream still writes it.
+    struct CoarseJoin {
+        cudaStream_t s = nullptr, q = nullptr;
+        cudaEvent_t e = nullptr;
+        void finish() {
+            if (!q) return;
+            cudaEventRecord(e, q);
+            cudaStreamWaitEvent(s, e, 0);
+            q = nullptr;
+        }
+        ~CoarseJoin() { finish(); }
+    } coarse_join;
     {
+        for (auto &e : h->ev_coarse)
+            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         Level &C = h->lev.back();
         int n = C.A.n;
         if (n > kMaxCoarse) fail(CPR_ERR_INVALID, "coarsest level larger than the dense-solve limit");
         h->cn = n;
+        h->cinv.alloc((size_t)n * n, s);    // a handle buffer: allocated and released on the main stream
+        cudaStream_t q = h->side;
+        CK(cudaEventRecord(h->ev_coarse[0], s));
+        CK(cudaStreamWaitEvent(q, h->ev_coarse[0], 0));
+        coarse_join.s = s;
+        coarse_join.e = h->ev_coarse[1];
+        coarse_join.q = q;
+        // temporaries live and die on the side stream
         DVec<double> a;
         DVec<int> piv;
-        a.alloc((size_t)n * n, s);
+        a.alloc((size_t)n * n, q);
         a.zero();
-        piv.alloc(n, s);
-        h->cinv.alloc((size_t)n * n, s);
-        k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
+        piv.alloc(n, q);
+        k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, q>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
         CK_LAUNCH();
         constexpr int kLuSmemMax = 200 * 1024;
         int use_smem = (size_t)n * n * sizeof(double) <= kLuSmemMax ? 1 : 0;
@@ -2003,25 +2073,23 @@ void build_preconditioner(cpr_handle *h) {
         // threads must never see a smaller limit than the one they launch with
         if (use_smem) CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuSmemMax));
         DVec<double> lu;
-        lu.alloc((size_t)n * n, s);
+        lu.alloc((size_t)n * n, q);
         if (!use_smem) {
             // global path: factor a copy in storage order, then gather rows into position order
-            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, q));
         }
-        k_dense_lu<<<1, kLuThreads, smem, s>>>(n, a.p, lu.p, piv.p, use_smem, h->err.p);
+        k_dense_lu<<<1, kLuThreads, smem, q>>>(n, a.p, lu.p, piv.p, use_smem, h->err.p);
         CK_LAUNCH();   // a zero pivot is reported by the check at the end of the setup
         if (!use_smem) {
-            k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, s>>>(n, lu.p, piv.p, a.p);
+            k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, q>>>(n, lu.p, piv.p, a.p);
             CK_LAUNCH();
-            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, q));
         }
-        k_dense_inv_cols<<<n, 256, sizeof(double) * n, s>>>(n, lu.p, piv.p, h->cinv.p);
+        k_dense_inv_cols<<<n, 256, sizeof(double) * n, q>>>(n, lu.p, piv.p, h->cinv.p);
         CK_LAUNCH();
     }
 
     clk.mark("coarse");
-    side.join();
-    clk.mark("side_join");
     // ---- solve copies in color order, FP32 shadows, work vectors ----
     int L = (int)h->lev.size();
     for (int l = 0; l < L; l++) {
@@ -2088,6 +2156,7 @@ void build_preconditioner(cpr_handle *h) {
             Lv.s1_32.alloc(n, s);
         }
     }
+    coarse_join.finish();
     // Kernels that meet a zero or non-finite pivot (an AMG level's diagonal,
     // the coarsest matrix, a BILU(0) block) record CPR_ERR_SINGULAR and go on
     // with a unit stand-in, so the setup runs to completion without host
