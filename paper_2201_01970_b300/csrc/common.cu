@@ -1,4 +1,5 @@
 // Shared host utilities: errors, scans, small device reads.
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -136,31 +137,44 @@ __global__ void k_tile_scan(const int *in, int n, const int *tile_off, int *out)
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanBlock - 1) out[n] = excl;
 }
-// Whole scan in one CTA for up to kScanSingleMax elements: tiles in order,
-// each scanned by the block and offset by the running total (one launch
-// instead of three).
-constexpr int kScanSingleMax = 16 * kScanTile;
+// Whole scan in one CTA for up to kScanSingleMax elements (one launch
+// instead of three): a coalesced copy of the input into shared memory
+// (skewed by one word per 32 against bank conflicts), one contiguous chunk
+// per thread summed there, one block scan of the chunk sums, the chunk's
+// prefixes written back in place, and a coalesced copy out.
+constexpr int kScanSingleMax = 8 * kScanTile;
+constexpr int kScanSingleSmem = (kScanSingleMax + kScanSingleMax / 32) * (int)sizeof(int);
+__device__ __forceinline__ int skew32(int i) { return i + (i >> 5); }
 __global__ void __launch_bounds__(kScanBlock) k_scan_single(const int *in, int n, int *out) {
-    int carry = 0;
-    for (long base = 0; base < n; base += kScanTile) {
-        int v[kScanItems];
-        int s = 0;
-        for (int k = 0; k < kScanItems; k++) {
-            long i = base + (long)threadIdx.x * kScanItems + k;
-            v[k] = i < n ? in[i] : 0;
-            s += v[k];
-        }
-        int total;
-        int excl = block_exclusive_scan(s, &total) + carry;
-        for (int k = 0; k < kScanItems; k++) {
-            long i = base + (long)threadIdx.x * kScanItems + k;
-            if (i < n) out[i] = excl;
-            excl += v[k];
-        }
-        carry += total;
-        __syncthreads();
+    extern __shared__ int sm[];
+    for (int i = threadIdx.x; i < n; i += kScanBlock) sm[skew32(i)] = in[i];
+    __syncthreads();
+    int chunk = (n + kScanBlock - 1) / kScanBlock;
+    int b = threadIdx.x * chunk, e = min(b + chunk, n);
+    int s = 0;
+#pragma unroll 8
+    for (int i = b; i < e; i++) s += sm[skew32(i)];
+    int total;
+    int excl = block_exclusive_scan(s, &total);
+    for (int i = b; i < e; i++) {
+        int v = sm[skew32(i)];
+        sm[skew32(i)] = excl;
+        excl += v;
     }
-    if (threadIdx.x == 0) out[n] = carry;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kScanBlock) out[i] = sm[skew32(i)];
+    if (threadIdx.x == 0) out[n] = total;
+}
+
+// The shared-memory ceiling of k_scan_single, set once per device.
+void scan_single_attr() {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    CK(cudaFuncSetAttribute(k_scan_single, cudaFuncAttributeMaxDynamicSharedMemorySize, kScanSingleSmem));
+    done.fetch_or(bit, std::memory_order_release);
 }
 }  // namespace
 
@@ -176,7 +190,8 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
         return;
     }
     if (n <= kScanSingleMax) {
-        k_scan_single<<<1, kScanBlock, 0, s>>>(in, n, out);
+        scan_single_attr();
+        k_scan_single<<<1, kScanBlock, kScanSingleSmem, s>>>(in, n, out);
         CK_LAUNCH();
         return;
     }

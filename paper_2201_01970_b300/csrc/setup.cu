@@ -431,6 +431,7 @@ __global__ void k_union(int n, const int *sr, const int *sc, const int *tr, cons
 constexpr unsigned long long kUncolored = ~0ull;
 constexpr int kSmallLevel = 4096;    // levels up to this size run their rounds in one CTA
 constexpr int kJpBatch = 8;          // JP rounds launched per host check of the remaining count
+constexpr int kPmisBatch = 6;        // PMIS rounds launched per host check of the undecided count
 
 // One JP round r for vertex i.  A vertex uncolored at the start of the round
 // (never colored, or colored in this very round by someone else) whose key
@@ -566,16 +567,22 @@ __device__ int pmis_commit(int i, const int *sr, const int *sc, int *cf, const i
     return 0;
 }
 
+// Rounds are launched in batches between host checks.  Once every point is
+// decided the count is 0 and both kernels return at once.  The count reaches 0
+// only with the last decision, and a point with a decision pending still
+// counts itself, so no commit that is due is skipped.
 __global__ void k_pmis_select(int n, const int *sr, const int *sc, const int *tr, const int *tc,
-                              uint32_t hbase, const int *cf, int *sel) {
+                              uint32_t hbase, const int *cf, int *sel, const int *undecided) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
+    if (i >= n || *(volatile const int *)undecided == 0) return;
+    sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
 }
 
 __global__ void k_pmis_commit(int n, const int *sr, const int *sc, int *cf, const int *sel,
                               int *undecided) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && pmis_commit(i, sr, sc, cf, sel)) atomicSub(undecided, 1);
+    if (i >= n || *(volatile int *)undecided == 0) return;
+    if (pmis_commit(i, sr, sc, cf, sel)) atomicSub(undecided, 1);
 }
 
 // All PMIS rounds of a small level in one CTA (the same rounds as above).
@@ -1948,16 +1955,19 @@ void build_preconditioner(cpr_handle *h) {
             k_pmis_small<<<1, 1024, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, hb, L.cf.p, sel.p, und.p);
             CK_LAUNCH();
         }
-        while (n > kSmallLevel && read_int(und.p, s) > 0) {
-            for (int k = 0; k < 3; k++, rounds++) {
-                k_pmis_select<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p,
-                                                                    tcol.p, hb, L.cf.p, sel.p);
-                CK_LAUNCH();
-                k_pmis_commit<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, L.cf.p,
-                                                                    sel.p, und.p);
-                CK_LAUNCH();
-            }
-            if (rounds > n + 8) fail(CPR_ERR_CUDA, "C/F splitting did not terminate");
+        if (n > kSmallLevel) {
+            do {
+                for (int k = 0; k < kPmisBatch; k++, rounds++) {
+                    k_pmis_select<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p,
+                                                                        tcol.p, hb, L.cf.p, sel.p, und.p);
+                    CK_LAUNCH();
+                    k_pmis_commit<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, L.cf.p,
+                                                                        sel.p, und.p);
+                    CK_LAUNCH();
+                }
+                if (rounds > n + 8) fail(CPR_ERR_CUDA, "C/F splitting did not terminate");
+            } while (read_int(und.p, s) > 0);
+            if (getenv("CPR_SETUP_TIMING")) fprintf(stderr, "[cpr setup] pmis n=%d rounds<=%d\n", n, rounds);
         }
         clk.mark("pmis");
         DVec<int> flag, cidx;
