@@ -473,17 +473,41 @@ __device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase
     return c;
 }
 
-__global__ void k_jp_round(int n, const int *grow, const int *gcol, uint32_t hbase,
-                           unsigned long long *state, unsigned r, int *remaining, int *maxcolor) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    // rounds are launched in batches between host checks: once every vertex
-    // is colored the rest of the batch returns at once (the count only falls)
-    if (i >= n || *(volatile int *)remaining == 0) return;
-    int c = jp_vertex(i, grow, gcol, hbase, state, r);
-    if (c >= 0) {
-        atomicSub(remaining, 1);
-        atomicMax(maxcolor, c);
+// One JP round over a worklist: the vertices still uncolored when the round
+// starts (round 0: all n, list_in == nullptr).  A vertex's decision depends
+// only on the states left by earlier rounds, so the order of the list does not
+// matter; the losers are appended to list_out (warp-aggregated).  Counts cycle
+// through three slots: this round reads cnt[r % 3], appends to cnt[(r+1) % 3]
+// (zeroed by the previous round) and zeroes cnt[(r+2) % 3] for the next one.
+// Rounds are launched in batches between host checks; once the list is empty
+// the rest of the batch returns at once.
+__global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, const int *grow,
+                           const int *gcol, uint32_t hbase, unsigned long long *state, unsigned r,
+                           int *maxcolor) {
+    int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
+    int *out_cnt = &cnt[(r + 1) % 3];
+    int lane = threadIdx.x & 31;
+    int cmax = -1;
+    // t0 is uniform over the block, so whole warps run each pass together
+    for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
+        int t = t0 + threadIdx.x, i = 0;
+        bool lost = false;
+        if (t < m) {
+            i = list_in ? list_in[t] : t;
+            int c = jp_vertex(i, grow, gcol, hbase, state, r);
+            if (c >= 0) cmax = max(cmax, c);
+            else lost = true;
+        }
+        unsigned b = __ballot_sync(0xffffffffu, lost);
+        if (b) {
+            int leader = __ffs(b) - 1, base = 0;
+            if (lane == leader) base = atomicAdd(out_cnt, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (lost) list_out[base + __popc(b & ((1u << lane) - 1u))] = i;
+        }
     }
+    if (cmax >= 0) atomicMax(maxcolor, cmax);
 }
 
 // All JP rounds of a small graph in one CTA, rounds separated by barriers
@@ -1078,21 +1102,37 @@ __global__ void k_perm_count(int n, const int *order, const int *rowptr, const i
     cnt[t] = c;
 }
 
-// Fill the renumbered copy; columns mapped through icol (nullptr: unchanged);
-// entries keep the natural (ascending-column) order of their row.
+// Fill the renumbered copy, G lanes per row; columns mapped through icol
+// (nullptr: unchanged); entries keep the natural (ascending-column) order of
+// their row.  With skip_diag the diagonal is dropped: the diagonals before a
+// lane's entry are counted from a ballot of the lane's group.
+template <int G>
 __global__ void k_perm_fill(int n, const int *order, const int *rowptr, const int *col,
                             const double *val, bool skip_diag, const int *icol, const int *nrow,
                             int *ncol, double *nval) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int i = order ? order[t] : t;
-    int q = nrow[t];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
-        int j = col[p];
-        if (skip_diag && j == i) continue;
-        ncol[q] = icol ? icol[j] : j;
-        nval[q] = val[p];
-        q++;
+    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    if (t >= n) return;   // whole groups: G divides the block
+    int wl = threadIdx.x & 31;
+    unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
+    unsigned below = gmask & ((1u << wl) - 1u);
+    int i = order ? order[t] : (int)t;
+    int a = rowptr[i], b = rowptr[i + 1];
+    int q = nrow[t] - a;   // source entry p lands at q + p, less the diagonals before it
+    int skipped = 0;
+    for (int p0 = a; p0 < b; p0 += G) {
+        int p = p0 + lane;
+        bool in = p < b;
+        int j = in ? col[p] : 0;
+        bool d = skip_diag && in && j == i;
+        unsigned m = __ballot_sync(gmask, d);
+        if (in && !d) {
+            int o = q + p - skipped - __popc(m & below);
+            ncol[o] = icol ? icol[j] : j;
+            nval[o] = val[p];
+        }
+        skipped += __popc(m);
     }
 }
 
@@ -1481,34 +1521,38 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
     DVec<unsigned long long> state;
     state.alloc(n, s);
     CK(cudaMemsetAsync(state.p, 0xff, sizeof(unsigned long long) * n, s));
-    DVec<int> counters;  // remaining, max color
-    counters.alloc(2, s);
-    int init[2] = {n, 0};
-    CK(cudaMemcpyAsync(counters.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    DVec<int> counters;  // list counts (three slots), max color
+    counters.alloc(4, s);
+    CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
     uint32_t hb = hash_base(h->opt.seed, salt, level);
     if (n <= kSmallLevel) {
-        k_jp_small<<<1, 1024, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, counters.p + 1);
+        k_jp_small<<<1, 1024, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, counters.p + 3);
         CK_LAUNCH();
         color.alloc(n, s);
         k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
         CK_LAUNCH();
-        return read_int(counters.p + 1, s) + 1;
+        return read_int(counters.p + 3, s) + 1;
     }
+    DVec<int> lists;   // two worklists, used alternately
+    lists.alloc(2 * (size_t)n, s);
+    int grid = grid_for(n, kBlock, 148 * 8);
     unsigned r = 0;
     for (;;) {
         for (int k = 0; k < kJpBatch; k++, r++) {
-            k_jp_round<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, r,
-                                                             counters.p, counters.p + 1);
+            const int *in = r == 0 ? nullptr : lists.p + (size_t)(r % 2) * n;
+            int *out = lists.p + (size_t)((r + 1) % 2) * n;
+            k_jp_round<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.rowptr.p, G.col.p, hb, state.p, r,
+                                               counters.p + 3);
             CK_LAUNCH();
         }
-        if (read_int(counters.p, s) == 0) break;
+        if (read_int(counters.p + r % 3, s) == 0) break;
         if (r > (unsigned)n + 8) fail(CPR_ERR_CUDA, "coloring did not terminate");
     }
     if (getenv("CPR_SETUP_TIMING")) fprintf(stderr, "[cpr setup] jp n=%d rounds<=%u\n", n, r);
     color.alloc(n, s);
     k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
     CK_LAUNCH();
-    return read_int(counters.p + 1, s) + 1;
+    return read_int(counters.p + 3, s) + 1;
 }
 
 // Rows grouped by color, index-ascending within a color.
@@ -1582,6 +1626,9 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     exclusive_scan(ucnt.p, C.rowptr.p, n, s);
     C.nnz = read_int(C.rowptr.p + n, s);
     if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
+    if (getenv("CPR_SETUP_TIMING"))
+        fprintf(stderr, "[cpr setup] spgemm n=%d annz=%d bnnz=%d cnnz=%d mid=%d big=%d\n", n, A.nnz, B.nnz, C.nnz,
+                read_int(cnts.p, s), read_int(cnts.p + 1, s));
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
     k_spgemm_rowfill<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(
@@ -1606,6 +1653,8 @@ void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
 }
 
 // dst = src with rows taken in `order` and columns mapped through icol.
+int lanes_for(double avg, long rows, long target);
+
 void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool skip_diag, DCsr &dst,
               cudaStream_t s) {
     int n = src.n;
@@ -1623,8 +1672,18 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
     dst.nnz = skip_diag ? std::max(src.nnz - n, 0) : src.nnz;
     dst.col.alloc(std::max(src.nnz, 1), s);
     dst.val.alloc(std::max(src.nnz, 1), s);
-    k_perm_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p, skip_diag,
-                                                      icol, dst.rowptr.p, dst.col.p, dst.val.p);
+    // lanes per row: a few entries per lane, at least 2^17 threads
+    int g = std::min(8, lanes_for((double)src.nnz / std::max(n, 1), n, 1L << 17));
+    auto fill = [&](auto kern, int G) {
+        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p,
+                                                             skip_diag, icol, dst.rowptr.p, dst.col.p, dst.val.p);
+    };
+    switch (g) {
+    case 1: fill(k_perm_fill<1>, 1); break;
+    case 2: fill(k_perm_fill<2>, 2); break;
+    case 4: fill(k_perm_fill<4>, 4); break;
+    default: fill(k_perm_fill<8>, 8); break;
+    }
     CK_LAUNCH();
 }
 
@@ -1940,8 +1999,10 @@ void build_preconditioner(cpr_handle *h) {
                                                                     o.theta_amg, srow, out);
             CK_LAUNCH();
         });
+        clk.mark("strength");
         DVec<int> trow, tcol;
         transpose(n, n, S.nnz, S.rowptr.p, S.col.p, nullptr, trow, tcol, nullptr, s);
+        clk.mark("st");
         L.cf.alloc(n, s);
         DVec<int> sel, und;
         sel.alloc(n, s);
@@ -2026,6 +2087,7 @@ void build_preconditioner(cpr_handle *h) {
         // Galerkin coarse matrix A_{l+1} = R (A P)
         DCsr AP, Ac;
         spgemm(L.A, L.P, AP, s);
+        clk.mark("ap");
         spgemm(L.R, AP, Ac, s);
         AP = DCsr{};
         clk.mark("rap");
@@ -2102,6 +2164,7 @@ void build_preconditioner(cpr_handle *h) {
     clk.mark("coarse");
     // ---- solve copies in color order, FP32 shadows, work vectors ----
     int L = (int)h->lev.size();
+    clk.mark("coarse_post");
     for (int l = 0; l < L; l++) {
         Level &Lv = h->lev[l];
         int n = Lv.A.n;
@@ -2132,6 +2195,7 @@ void build_preconditioner(cpr_handle *h) {
         Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
         Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
     }
+    clk.mark("perm");
     {
         // final V-cycle commit: level-0 solve row -> BILU position
         const int *order0 = L > 1 ? h->lev[0].rows_by_color.p : nullptr;
