@@ -393,20 +393,22 @@ void cpr_destroy(cpr_handle *h) {
         if (e) cudaEventDestroy(e);
     for (auto e : h->ev_coarse)
         if (e) cudaEventDestroy(e);
+    for (auto e : h->ev_color) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);
     for (int k = 0; k < cpr_handle::kProfSlots; k++) {
         if (h->ev_a[k]) cudaEventDestroy(h->ev_a[k]);
         if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
     }
     h->pinned = nullptr;
-    cudaStream_t side = h->side;
+    cudaStream_t side = h->side, lu = h->lu_stream;
     delete h;  // DVec destructors free on the stream each buffer was allocated on
     if (s) cudaStreamSynchronize(s);
     if (own && s) cudaStreamDestroy(s);
-    if (side) {
-        cudaStreamSynchronize(side);
-        cudaStreamDestroy(side);
-    }
+    for (cudaStream_t q : {side, lu})
+        if (q) {
+            cudaStreamSynchronize(q);
+            cudaStreamDestroy(q);
+        }
 }
 
 int cpr_apply(cpr_handle *h, const double *v, double *z) {

@@ -156,7 +156,9 @@ struct cpr_handle {
     cpr_opts opt{};
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;      // setup's side worker stream (created on first use)
-    cudaEvent_t ev_coarse[2] = {nullptr, nullptr};  // main -> side -> main around the coarse factorisation
+    cudaStream_t lu_stream = nullptr; // setup's coarse factorisation stream (created on first use)
+    cudaEvent_t ev_coarse[2] = {nullptr, nullptr};  // main -> LU stream -> main around the coarse factorisation
+    std::vector<cudaEvent_t> ev_color;              // per level: its coloring's stream work is complete
     // Sliced-ELL copy of the outer operator for the SpMV: slices of 32 block
     // rows; slot k of a slice holds each of its rows' k-th block (column -1
     // past a row's end), the nine values of a slot lane-contiguous per block

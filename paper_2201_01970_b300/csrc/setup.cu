@@ -710,15 +710,19 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 // every C entry is summed in the same order as Gustavson's row-by-row product.
 // Rows with more distinct columns than the table holds take an exact slow path.
 
-// Three table sizes.  Rows with at most kSmallCand candidate products (all
-// but a few rows of A P at the fine levels: level 0's has ~11 per row) run
-// with small per-warp tables at full occupancy; rows up to kMidCand (most of
-// R (A P): ~70 per coarse row at level 0) with medium tables, still at full
-// occupancy; the rest with large tables.  A candidate-count pass lists the
-// medium and large rows.
+// Four tiers.  Rows with at most kTinyCand candidate products (most rows of
+// A P at the fine levels: level 0's has ~11 per row) take one thread each:
+// the products, in (A entry, B entry) order, are insertion-sorted by column in
+// the thread's own arrays (stable, so each column's products stay in
+// ascending k) and each column's run is summed in that order.  Rows up to
+// kSmallCand run with small per-warp tables at full occupancy; rows up to
+// kMidCand (most of R (A P): ~33 per coarse row at level 0, ~70 at level 1)
+// with medium tables, still at full occupancy; the rest with large tables.
+// A candidate-count pass lists the small, medium and large rows.
 //   CAP: hash slots per warp (power of two); HMAX: distinct columns handled
 //   in shared memory, a power of two (larger rows take the exact slow path);
 //   WARPS per block.
+constexpr int kTinyCand = 24;
 constexpr int kSmallCand = 32;
 constexpr int kMidCand = 160;   // rows above kSmallCand and up to this: 256-slot tables
 constexpr int kEmpty = -1;
@@ -833,11 +837,11 @@ __device__ int next_col(int i, long last, const int *ar, const int *ac, const in
     return m;
 }
 
-// Rows of A B by candidate product count (sum over k in A_i of |B_k|):
-// above kSmallCand and up to kMidCand into `mid`, above kMidCand into `big`,
-// each list in any order.
-__global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *mid, int *nmid, int *big,
-                              int *nbig) {
+// Rows of A B by candidate product count (sum over k in A_i of |B_k|): above
+// kTinyCand and up to kSmallCand into `small`, up to kMidCand into `mid`,
+// above kMidCand into `big`, each list in any order.  cnt: small, mid, big.
+__global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *small, int *mid, int *big,
+                              int *cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = 0;
@@ -845,8 +849,59 @@ __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br
         int k = ac[p];
         c += br[k + 1] - br[k];
     }
-    if (c > kMidCand) big[atomicAdd(nbig, 1)] = i;
-    else if (c > kSmallCand) mid[atomicAdd(nmid, 1)] = i;
+    if (c > kMidCand) big[atomicAdd(&cnt[2], 1)] = i;
+    else if (c > kSmallCand) mid[atomicAdd(&cnt[1], 1)] = i;
+    else if (c > kTinyCand) small[atomicAdd(&cnt[0], 1)] = i;
+}
+
+// The tiny tier: one thread per row with at most kTinyCand candidates (other
+// rows are skipped).  Without cr, counts the row's distinct columns into
+// ucnt; with cr, writes the row's columns (ascending) and values.
+__global__ void k_spgemm_tiny(int n, const int *ar, const int *ac, const double *av, const int *br,
+                              const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *ucnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = ar[i], b = ar[i + 1];
+    int cand = 0;
+    for (int p = a; p < b; p++) {
+        int k = ac[p];
+        cand += br[k + 1] - br[k];
+    }
+    if (cand > kTinyCand) return;
+    int J[kTinyCand];
+    double V[kTinyCand];
+    int m = 0;
+    for (int p = a; p < b; p++) {
+        int k = ac[p];
+        double x = cr ? av[p] : 0.0;
+        for (int q = br[k]; q < br[k + 1]; q++) {
+            int j = bc[q];
+            double v = cr ? __dmul_rn(x, bv[q]) : 0.0;
+            int pos = m++;
+            while (pos > 0 && J[pos - 1] > j) {   // stable: equal columns keep their k order
+                J[pos] = J[pos - 1];
+                V[pos] = V[pos - 1];
+                pos--;
+            }
+            J[pos] = j;
+            V[pos] = v;
+        }
+    }
+    if (!cr) {
+        int c = 0;
+        for (int t = 0; t < m; t++) c += t == 0 || J[t] != J[t - 1];
+        ucnt[i] = c;
+        return;
+    }
+    int o = cr[i];
+    for (int t = 0; t < m;) {
+        int j = J[t];
+        double sum = 0.0;
+        for (; t < m && J[t] == j; t++) sum = __dadd_rn(sum, V[t]);
+        cc[o] = j;
+        cv[o] = sum;
+        o++;
+    }
 }
 
 // One warp per row, grid-stride: rows 0..n-1, or the *nrows rows listed in
@@ -1593,31 +1648,36 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
 }
 
 // C = A B (structural pattern, sorted; values in Gustavson order).  Rows with
-// at most kSmallCand candidates run with small tables, the listed rest with
-// large ones; every row is written by exactly one of the two launches.
+// at most kTinyCand candidates run one per thread, the listed rest with
+// small, medium or large tables; every row is written by exactly one launch.
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     constexpr int kSW = 16, kMW = 8, kBW = 4;   // warps per block: small, medium and large tables
     int n = A.n;
-    DVec<int> ucnt, mid, big, cnts;
+    DVec<int> ucnt, small, mid, big, cnts;
     ucnt.alloc(std::max(n, 1), s);
+    small.alloc(std::max(n, 1), s);
     mid.alloc(std::max(n, 1), s);
     big.alloc(std::max(n, 1), s);
-    cnts.alloc(2, s);
+    cnts.alloc(3, s);
     cnts.zero();
-    k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, mid.p,
-                                                                      cnts.p, big.p, cnts.p + 1);
+    k_spgemm_cand<<<grid_for(std::max(n, 1), kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, small.p,
+                                                                      mid.p, big.p, cnts.p);
     CK_LAUNCH();
     // the listed rows run on fixed grids that read their counts on the device
-    unsigned sblocks = (unsigned)((n + kSW - 1) / kSW);
+    unsigned tblocks = (unsigned)grid_for(std::max(n, 1), kBlock);
+    unsigned sblocks = (unsigned)grid_for(n, kSW, 148 * 8);
     unsigned mblocks = (unsigned)grid_for(n, kMW, 148 * 8);
     unsigned bblocks = (unsigned)grid_for(n, kBW, 148 * 8);
-    k_spgemm_rowcount<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(n, nullptr, nullptr, A.rowptr.p,
-                                                                              A.col.p, B.rowptr.p, B.col.p, ucnt.p);
+    k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr, nullptr,
+                                             nullptr, nullptr, ucnt.p);
     CK_LAUNCH();
-    k_spgemm_rowcount<256, 128, kMW, false><<<mblocks, kMW * 32, 0, s>>>(n, mid.p, cnts.p, A.rowptr.p, A.col.p,
+    k_spgemm_rowcount<64, kSmallCand, kSW, false><<<sblocks, kSW * 32, 0, s>>>(n, small.p, cnts.p, A.rowptr.p,
+                                                                               A.col.p, B.rowptr.p, B.col.p, ucnt.p);
+    CK_LAUNCH();
+    k_spgemm_rowcount<256, 128, kMW, false><<<mblocks, kMW * 32, 0, s>>>(n, mid.p, cnts.p + 1, A.rowptr.p, A.col.p,
                                                                           B.rowptr.p, B.col.p, ucnt.p);
     CK_LAUNCH();
-    k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(n, big.p, cnts.p + 1, A.rowptr.p, A.col.p,
+    k_spgemm_rowcount<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(n, big.p, cnts.p + 2, A.rowptr.p, A.col.p,
                                                                            B.rowptr.p, B.col.p, ucnt.p);
     CK_LAUNCH();
     C.n = n;
@@ -1627,19 +1687,23 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     C.nnz = read_int(C.rowptr.p + n, s);
     if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
     if (getenv("CPR_SETUP_TIMING"))
-        fprintf(stderr, "[cpr setup] spgemm n=%d annz=%d bnnz=%d cnnz=%d mid=%d big=%d\n", n, A.nnz, B.nnz, C.nnz,
-                read_int(cnts.p, s), read_int(cnts.p + 1, s));
+        fprintf(stderr, "[cpr setup] spgemm n=%d annz=%d bnnz=%d cnnz=%d small=%d mid=%d big=%d\n", n, A.nnz,
+                B.nnz, C.nnz, read_int(cnts.p, s), read_int(cnts.p + 1, s), read_int(cnts.p + 2, s));
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
-    k_spgemm_rowfill<64, kSmallCand, kSW, true><<<sblocks, kSW * 32, 0, s>>>(
-        n, nullptr, nullptr, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+    k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
+                                             C.rowptr.p, C.col.p, C.val.p, nullptr);
+    CK_LAUNCH();
+    k_spgemm_rowfill<64, kSmallCand, kSW, false><<<sblocks, kSW * 32, 0, s>>>(
+        n, small.p, cnts.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
         C.val.p);
     CK_LAUNCH();
     k_spgemm_rowfill<256, 128, kMW, false><<<mblocks, kMW * 32, 0, s>>>(
-        n, mid.p, cnts.p, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p);
+        n, mid.p, cnts.p + 1, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+        C.val.p);
     CK_LAUNCH();
     k_spgemm_rowfill<1024, 512, kBW, false><<<bblocks, kBW * 32, 0, s>>>(
-        n, big.p, cnts.p + 1, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
+        n, big.p, cnts.p + 2, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p,
         C.val.p);
     CK_LAUNCH();
 }
@@ -1812,6 +1876,33 @@ class SideWorker {
             f(s);
         }
     }
+    // Task `key` has finished; the task recorded an event for its stream work.
+    void finished(int key) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if ((size_t)key >= finished_.size()) finished_.resize(key + 1, 0);
+        finished_[key] = 1;
+        cvd_.notify_all();
+    }
+    // Wait until task `key` has finished, running queued tasks (newest first)
+    // on this thread and stream s meanwhile.
+    void wait(int key, cudaStream_t s) {
+        for (;;) {
+            Task f;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                for (;;) {
+                    if (err_) std::rethrow_exception(err_);
+                    if ((size_t)key < finished_.size() && finished_[key]) return;
+                    if (!q_.empty()) break;
+                    if (!busy_) fail(CPR_ERR_CUDA, "setup waited on a side task that was never posted");
+                    cvd_.wait(lk);
+                }
+                f = std::move(q_.back());
+                q_.pop_back();
+            }
+            f(s);
+        }
+    }
     // Wait for the worker and for everything it issued on the side stream.
     void join() {
         stop();
@@ -1838,6 +1929,7 @@ class SideWorker {
                 f = std::move(q_.front());
                 q_.pop_front();
                 if (err_) continue;   // after a failure, drain without running
+                busy_ = true;
             }
             try {
                 f(h_->side);
@@ -1845,15 +1937,19 @@ class SideWorker {
                 std::lock_guard<std::mutex> lk(mu_);
                 err_ = std::current_exception();
             }
+            std::lock_guard<std::mutex> lk(mu_);
+            busy_ = false;
+            cvd_.notify_all();
         }
     }
     cpr_handle *h_;
     PhaseClock clk_;
     std::thread th_;
     std::mutex mu_;
-    std::condition_variable cv_;
+    std::condition_variable cv_, cvd_;
     std::deque<Task> q_;
-    bool done_ = false;
+    std::vector<char> finished_;
+    bool done_ = false, busy_ = false;
     std::exception_ptr err_;
 };
 
@@ -1869,6 +1965,13 @@ void build_preconditioner(cpr_handle *h) {
     bool f32 = o.precond_fp32 != 0;
     // levels are referenced by the side worker while this thread appends: no reallocation
     h->lev.reserve((size_t)std::max(1, o.max_levels) + 1);
+    // one event per level coloring: the layout of a level waits on its own and
+    // the next level's coloring, not on the whole side worker
+    while (h->ev_color.size() < (size_t)std::max(1, o.max_levels) + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->ev_color.push_back(e);
+    }
 
     // ---- decoupling and the pressure matrix A_P (level 0) ----
     DVec<int> bdiag;
@@ -2059,7 +2162,9 @@ void build_preconditioner(cpr_handle *h) {
             L.ncolors = jp_color(h, G, 0, l, L.color, s);
             side.mark("c_jp");
             rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
+            CK(cudaEventRecord(h->ev_color[l], s));
             side.mark("c_order");
+            side.finished(l);
         });
         // direct interpolation P and R = P^T
         {
@@ -2095,16 +2200,12 @@ void build_preconditioner(cpr_handle *h) {
         h->lev[l + 1].A = std::move(Ac);
     }
 
-    side.help(s);
-    clk.mark("side_help");
-    side.join();
-    clk.mark("side_join");
-    // ---- coarsest level: dense inverse, on the side stream ----
+    // ---- coarsest level: dense inverse, on a stream of its own ----
     // The factorisation is FP64 work on one SM (about 0.8 ms at n = 200) that
-    // only the solve reads, so it runs on the side stream beside the layout
-    // below.  The guard makes the main stream wait for it before the final
-    // error check, and on every unwinding path, so no buffer is released or
-    // reused while the side stream still writes it.
+    // only the solve reads, so it runs beside the layout below.  The guard
+    // makes the main stream wait for it before the final error check, and on
+    // every unwinding path, so no buffer is released or reused while that
+    // stream still writes it.
     struct CoarseJoin {
         cudaStream_t s = nullptr, q = nullptr;
         cudaEvent_t e = nullptr;
@@ -2119,18 +2220,19 @@ void build_preconditioner(cpr_handle *h) {
     {
         for (auto &e : h->ev_coarse)
             if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (!h->lu_stream) CK(cudaStreamCreateWithFlags(&h->lu_stream, cudaStreamNonBlocking));
         Level &C = h->lev.back();
         int n = C.A.n;
         if (n > kMaxCoarse) fail(CPR_ERR_INVALID, "coarsest level larger than the dense-solve limit");
         h->cn = n;
         h->cinv.alloc((size_t)n * n, s);    // a handle buffer: allocated and released on the main stream
-        cudaStream_t q = h->side;
+        cudaStream_t q = h->lu_stream;
         CK(cudaEventRecord(h->ev_coarse[0], s));
         CK(cudaStreamWaitEvent(q, h->ev_coarse[0], 0));
         coarse_join.s = s;
         coarse_join.e = h->ev_coarse[1];
         coarse_join.q = q;
-        // temporaries live and die on the side stream
+        // temporaries live and die on that stream
         DVec<double> a;
         DVec<int> piv;
         a.alloc((size_t)n * n, q);
@@ -2160,22 +2262,14 @@ void build_preconditioner(cpr_handle *h) {
         k_dense_inv_cols<<<n, 256, sizeof(double) * n, q>>>(n, lu.p, piv.p, h->cinv.p);
         CK_LAUNCH();
     }
-
     clk.mark("coarse");
+
     // ---- solve copies in color order, FP32 shadows, work vectors ----
+    // Level l's copies need the colorings of levels l and l+1 (the coarsest
+    // level is not colored), so each level is laid out as soon as those two
+    // side tasks have finished, while the worker goes on with the rest.
     int L = (int)h->lev.size();
-    clk.mark("coarse_post");
-    for (int l = 0; l < L; l++) {
-        Level &Lv = h->lev[l];
-        int n = Lv.A.n;
-        bool coarsest = l == L - 1;
-        if (!coarsest) {
-            Lv.iperm.alloc(n, s);
-            k_iperm<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.iperm.p);
-            CK_LAUNCH();
-        }
-    }
-    for (int l = 0; l < L - 1; l++) {
+    auto layout = [&](int l) {
         Level &Lv = h->lev[l];
         Level &Nx = h->lev[l + 1];
         int n = Lv.A.n;
@@ -2194,8 +2288,29 @@ void build_preconditioner(cpr_handle *h) {
         Lv.gA = lanes_for((double)Lv.Ao.nnz / n, n / std::max(1, Lv.ncolors), 1L << 16);
         Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
         Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
+        if (f32) {
+            to_f32(Lv.Ao.val, Lv.Aoval32, s);
+            to_f32(Lv.diag, Lv.diag32, s);
+            to_f32(Lv.dinv, Lv.dinv32, s);
+            to_f32(Lv.Pp.val, Lv.Ppval32, s);
+            to_f32(Lv.Rp.val, Lv.Rpval32, s);
+        }
+    };
+    for (int l = 0; l < L - 1; l++) {
+        side.wait(l, s);
+        CK(cudaStreamWaitEvent(s, h->ev_color[l], 0));
+        Level &Lv = h->lev[l];
+        Lv.iperm.alloc(Lv.A.n, s);
+        k_iperm<<<grid_for(Lv.A.n, kBlock), kBlock, 0, s>>>(Lv.A.n, Lv.rows_by_color.p, Lv.iperm.p);
+        CK_LAUNCH();
+        if (l > 0) layout(l - 1);
     }
+    if (L > 1) layout(L - 2);
     clk.mark("perm");
+    side.help(s);
+    clk.mark("side_help");
+    side.join();
+    clk.mark("side_join");
     {
         // final V-cycle commit: level-0 solve row -> BILU position
         const int *order0 = L > 1 ? h->lev[0].rows_by_color.p : nullptr;
@@ -2216,13 +2331,6 @@ void build_preconditioner(cpr_handle *h) {
         Lv.s0.alloc(n, s);
         Lv.s1.alloc(n, s);
         if (f32) {
-            if (l < L - 1) {
-                to_f32(Lv.Ao.val, Lv.Aoval32, s);
-                to_f32(Lv.diag, Lv.diag32, s);
-                to_f32(Lv.dinv, Lv.dinv32, s);
-                to_f32(Lv.Pp.val, Lv.Ppval32, s);
-                to_f32(Lv.Rp.val, Lv.Rpval32, s);
-            }
             Lv.x32.alloc(n, s);
             Lv.b32.alloc(n, s);
             Lv.r32.alloc(n, s);
