@@ -405,27 +405,6 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_long_rows(const int *l
     }
 }
 
-// ------------------------------------------------------------------ union
-
-// Pattern of S united with T = S^T (both sorted): count (urow == nullptr) or fill.
-__global__ void k_union(int n, const int *sr, const int *sc, const int *tr, const int *tc,
-                        const int *urow, int *out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int p = sr[i], pe = sr[i + 1], q = tr[i], qe = tr[i + 1];
-    int o = urow ? urow[i] : 0, c = 0;
-    while (p < pe || q < qe) {
-        int a = p < pe ? sc[p] : INT_MAX;
-        int b = q < qe ? tc[q] : INT_MAX;
-        int m = a < b ? a : b;
-        if (a == m) p++;
-        if (b == m) q++;
-        if (urow) out[o + c] = m;
-        c++;
-    }
-    if (!urow) out[i] = c;
-}
-
 // ------------------------------------------------------------ Jones-Plassmann
 
 constexpr unsigned long long kUncolored = ~0ull;
@@ -433,36 +412,47 @@ constexpr int kSmallLevel = 4096;    // levels up to this size run their rounds 
 constexpr int kJpBatch = 8;          // JP rounds launched per host check of the remaining count
 constexpr int kPmisBatch = 6;        // PMIS rounds launched per host check of the undecided count
 
+// The symmetric graph G = S u S^T that JP colors, held as two disjoint
+// adjacency lists: S (no diagonal, rows sorted) and T, the entries of S^T
+// that S lacks (rows in any order; empty when S is symmetric).  The degree in
+// the key is |S_i u S^T_i| = |S_i| + |T_i|.
+struct JpGraph {
+    const int *sr, *sc, *tr, *tc, *deg;
+};
+
 // One JP round r for vertex i.  A vertex uncolored at the start of the round
 // (never colored, or colored in this very round by someone else) whose key
 // (degree, hash, index) beats every neighbour uncolored at the start of the
 // round takes the smallest color not held by a neighbour colored in an
 // earlier round.  state packs (round << 32 | color) into one 64-bit word,
 // written in one store.  Returns the color taken, or -1.
-__device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase,
-                         unsigned long long *state, unsigned r) {
+__device__ int jp_vertex(int i, const JpGraph &g, uint32_t hbase, unsigned long long *state, unsigned r) {
     if (state[i] != kUncolored) return -1;
-    int a = grow[i], b = grow[i + 1];
-    int di = b - a;
+    int di = g.deg[i];
     uint32_t hi = fmix32((uint32_t)i ^ hbase);
     volatile unsigned long long *vs = state;
-    for (int p = a; p < b; p++) {
-        int j = gcol[p];
-        if (j == i) continue;
-        unsigned long long sj = vs[j];
-        bool unc = sj == kUncolored || (unsigned)(sj >> 32) == r;
-        if (!unc) continue;
-        int dj = grow[j + 1] - grow[j];
-        if (!key_greater(di, hi, i, dj, fmix32((uint32_t)j ^ hbase), j)) return -1;
+    for (int pass = 0; pass < 2; pass++) {
+        const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
+        for (int p = R[i]; p < R[i + 1]; p++) {
+            int j = C[p];
+            if (j == i) continue;
+            unsigned long long sj = vs[j];
+            bool unc = sj == kUncolored || (unsigned)(sj >> 32) == r;
+            if (!unc) continue;
+            if (!key_greater(di, hi, i, g.deg[j], fmix32((uint32_t)j ^ hbase), j)) return -1;
+        }
     }
     int c = 0;
     for (int base = 0;; base += 64) {
         unsigned long long mask = 0;
-        for (int p = a; p < b; p++) {
-            unsigned long long sj = vs[gcol[p]];
-            if (sj == kUncolored || (unsigned)(sj >> 32) >= r) continue;
-            int cj = (int)(unsigned)sj;
-            if (cj >= base && cj < base + 64) mask |= 1ull << (cj - base);
+        for (int pass = 0; pass < 2; pass++) {
+            const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
+            for (int p = R[i]; p < R[i + 1]; p++) {
+                unsigned long long sj = vs[C[p]];
+                if (sj == kUncolored || (unsigned)(sj >> 32) >= r) continue;
+                int cj = (int)(unsigned)sj;
+                if (cj >= base && cj < base + 64) mask |= 1ull << (cj - base);
+            }
         }
         if (mask != ~0ull) {
             c = base + __ffsll((long long)~mask) - 1;
@@ -473,6 +463,37 @@ __device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase
     return c;
 }
 
+// Whether row j of S (sorted) holds column i.
+__device__ __forceinline__ bool row_has(const int *sr, const int *sc, int j, int i) {
+    int lo = sr[j], hi = sr[j + 1], end = hi;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (sc[mid] < i) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < end && sc[lo] == i;
+}
+
+// T, the one-way part of S^T: entry (i, j) of S puts i into row j of T
+// unless j's own row of S already holds i.  Without tcol, counts per T row;
+// with it, scatters (rows in any order).  One thread per row of S, so the
+// entry count of S need not be known on the host.
+__global__ void k_oneway_t(int n, const int *sr, const int *sc, int *cnt_or_cursor, int *tcol) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = sr[i]; p < sr[i + 1]; p++) {
+        int j = sc[p];
+        if (row_has(sr, sc, j, i)) continue;
+        int q = atomicAdd(&cnt_or_cursor[j], 1);
+        if (tcol) tcol[q] = i;
+    }
+}
+
+__global__ void k_sym_degree(int n, const int *sr, const int *tr, int *deg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) deg[i] = (sr[i + 1] - sr[i]) + (tr[i + 1] - tr[i]);
+}
+
 // One JP round over a worklist: the vertices still uncolored when the round
 // starts (round 0: all n, list_in == nullptr).  A vertex's decision depends
 // only on the states left by earlier rounds, so the order of the list does not
@@ -481,9 +502,8 @@ __device__ int jp_vertex(int i, const int *grow, const int *gcol, uint32_t hbase
 // (zeroed by the previous round) and zeroes cnt[(r+2) % 3] for the next one.
 // Rounds are launched in batches between host checks; once the list is empty
 // the rest of the batch returns at once.
-__global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, const int *grow,
-                           const int *gcol, uint32_t hbase, unsigned long long *state, unsigned r,
-                           int *maxcolor) {
+__global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, JpGraph g, uint32_t hbase,
+                           unsigned long long *state, unsigned r, int *maxcolor) {
     int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
     int *out_cnt = &cnt[(r + 1) % 3];
@@ -495,7 +515,7 @@ __global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, c
         bool lost = false;
         if (t < m) {
             i = list_in ? list_in[t] : t;
-            int c = jp_vertex(i, grow, gcol, hbase, state, r);
+            int c = jp_vertex(i, g, hbase, state, r);
             if (c >= 0) cmax = max(cmax, c);
             else lost = true;
         }
@@ -512,8 +532,8 @@ __global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, c
 
 // All JP rounds of a small graph in one CTA, rounds separated by barriers
 // (the same rounds as k_jp_round, without host round trips).
-__global__ void __launch_bounds__(1024) k_jp_small(int n, const int *grow, const int *gcol, uint32_t hbase,
-                                                   unsigned long long *state, int *maxcolor) {
+__global__ void __launch_bounds__(1024) k_jp_small(int n, JpGraph g, uint32_t hbase, unsigned long long *state,
+                                                   int *maxcolor) {
     __shared__ int rem;
     __shared__ int mx;
     if (threadIdx.x == 0) {
@@ -526,7 +546,7 @@ __global__ void __launch_bounds__(1024) k_jp_small(int n, const int *grow, const
         __syncthreads();
         if (left == 0) break;
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            int c = jp_vertex(i, grow, gcol, hbase, state, r);
+            int c = jp_vertex(i, g, hbase, state, r);
             if (c >= 0) {
                 atomicSub(&rem, 1);
                 atomicMax(&mx, c);
@@ -710,8 +730,12 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 // every C entry is summed in the same order as Gustavson's row-by-row product.
 // Rows with more distinct columns than the table holds take an exact slow path.
 
-// Four tiers.  Rows with at most kTinyCand candidate products (most rows of
-// A P at the fine levels: level 0's has ~11 per row) take one thread each:
+// Five tiers.  Rows with at most kMergeRow entries in A (every row of A P at
+// level 0 and most rows of R (A P) at the fine levels) take one thread each,
+// which merges the row's B rows (each sorted) held as list heads in
+// registers: the smallest head column is the next C column, and its products
+// are added in list order, i.e. ascending k.  Longer rows with at most
+// kTinyCand candidate products take one thread each too:
 // the products, in (A entry, B entry) order, are insertion-sorted by column in
 // the thread's own arrays (stable, so each column's products stay in
 // ascending k) and each column's run is summed in that order.  Rows up to
@@ -722,6 +746,7 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 //   CAP: hash slots per warp (power of two); HMAX: distinct columns handled
 //   in shared memory, a power of two (larger rows take the exact slow path);
 //   WARPS per block.
+constexpr int kMergeRow = 8;
 constexpr int kTinyCand = 24;
 constexpr int kSmallCand = 32;
 constexpr int kMidCand = 160;   // rows above kSmallCand and up to this: 256-slot tables
@@ -837,13 +862,14 @@ __device__ int next_col(int i, long last, const int *ar, const int *ac, const in
     return m;
 }
 
-// Rows of A B by candidate product count (sum over k in A_i of |B_k|): above
-// kTinyCand and up to kSmallCand into `small`, up to kMidCand into `mid`,
-// above kMidCand into `big`, each list in any order.  cnt: small, mid, big.
+// Rows of A B with more than kMergeRow entries in A, by candidate product
+// count (sum over k in A_i of |B_k|): above kTinyCand and up to kSmallCand
+// into `small`, up to kMidCand into `mid`, above kMidCand into `big`, each
+// list in any order.  cnt: small, mid, big.
 __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *small, int *mid, int *big,
                               int *cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || ar[i + 1] - ar[i] <= kMergeRow) return;
     int c = 0;
     for (int p = ar[i]; p < ar[i + 1]; p++) {
         int k = ac[p];
@@ -854,14 +880,61 @@ __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br
     else if (c > kTinyCand) small[atomicAdd(&cnt[0], 1)] = i;
 }
 
-// The tiny tier: one thread per row with at most kTinyCand candidates (other
-// rows are skipped).  Without cr, counts the row's distinct columns into
-// ucnt; with cr, writes the row's columns (ascending) and values.
+// The merge tier: one thread per row with at most kMergeRow entries in A
+// (other rows are skipped).  Without cr, counts the row's distinct columns
+// into ucnt; with cr, writes the row's columns (ascending) and values.
+__global__ void k_spgemm_merge(int n, const int *ar, const int *ac, const double *av, const int *br,
+                               const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *ucnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = ar[i], b = ar[i + 1];
+    if (b - a > kMergeRow) return;
+    int q[kMergeRow], e[kMergeRow], hd[kMergeRow];
+    double x[kMergeRow];
+#pragma unroll
+    for (int t = 0; t < kMergeRow; t++) {
+        bool in = a + t < b;
+        int k = in ? ac[a + t] : 0;
+        q[t] = in ? br[k] : 0;
+        e[t] = in ? br[k + 1] : 0;
+        x[t] = in && cr ? av[a + t] : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < kMergeRow; t++) hd[t] = q[t] < e[t] ? bc[q[t]] : INT_MAX;
+    int o = cr ? cr[i] : 0, c = 0;
+    for (;;) {
+        int J = INT_MAX;
+#pragma unroll
+        for (int t = 0; t < kMergeRow; t++) J = min(J, hd[t]);
+        if (J == INT_MAX) break;
+        double sum = 0.0;
+#pragma unroll
+        for (int t = 0; t < kMergeRow; t++)
+            if (hd[t] == J) {   // a B row holds each column once
+                if (cr) sum = __dadd_rn(sum, __dmul_rn(x[t], bv[q[t]]));
+                q[t]++;
+                hd[t] = q[t] < e[t] ? bc[q[t]] : INT_MAX;
+            }
+        if (cr) {
+            cc[o] = J;
+            cv[o] = sum;
+            o++;
+        }
+        c++;
+    }
+    if (!cr) ucnt[i] = c;
+}
+
+// The tiny tier: one thread per row with more than kMergeRow entries in A and
+// at most kTinyCand candidates (other rows are skipped).  Without cr, counts
+// the row's distinct columns into ucnt; with cr, writes the row's columns
+// (ascending) and values.
 __global__ void k_spgemm_tiny(int n, const int *ar, const int *ac, const double *av, const int *br,
                               const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *ucnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = ar[i], b = ar[i + 1];
+    if (b - a <= kMergeRow) return;
     int cand = 0;
     for (int p = a; p < b; p++) {
         int k = ac[p];
@@ -1527,6 +1600,23 @@ Graph build_pattern(int n, cudaStream_t s, CountFill cf) {
     return g;
 }
 
+// The same with at most ub entries allocated and no read-back of the count
+// (nnz = -1: known on the device only).
+template <class CountFill>
+Graph build_pattern_ub(int n, long ub, cudaStream_t s, CountFill cf) {
+    Graph g;
+    g.n = n;
+    g.nnz = -1;
+    DVec<int> cnt;
+    cnt.alloc(std::max(n, 1), s);
+    cf(nullptr, cnt.p);
+    g.rowptr.alloc(n + 1, s);
+    exclusive_scan(cnt.p, g.rowptr.p, n, s);
+    g.col.alloc(std::max<long>(ub, 1), s);
+    cf(g.rowptr.p, g.col.p);
+    return g;
+}
+
 // Transpose (pattern, or with values when val != nullptr); rows of the result sorted.
 void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, const double *val,
                DVec<int> &trow, DVec<int> &tcol, DVec<double> *tval, cudaStream_t s) {
@@ -1560,18 +1650,40 @@ void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, cons
     }
 }
 
-Graph sym_union(const Graph &S, cudaStream_t s) {
-    DVec<int> trow, tcol;
-    transpose(S.n, S.n, S.nnz, S.rowptr.p, S.col.p, nullptr, trow, tcol, nullptr, s);
-    int n = S.n;
-    return build_pattern(n, s, [&](const int *urow, int *out) {
-        k_union<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, urow, out);
-        CK_LAUNCH();
-    });
+// G = S u S^T for JP: S itself, its one-way transpose part T (rows unsorted)
+// and the union degrees.  S may carry only a bound of its entry count (ub):
+// nothing here reads the count back.
+struct SymGraph {
+    int n = 0;
+    Graph S;
+    DVec<int> trow, tcol, deg;
+    JpGraph dev() const { return JpGraph{S.rowptr.p, S.col.p, trow.p, tcol.p, deg.p}; }
+};
+
+SymGraph sym_graph(Graph &&S, long ub, cudaStream_t s) {
+    SymGraph g;
+    int n = g.n = S.n;
+    g.S = std::move(S);
+    DVec<int> cnt, cursor;
+    cnt.alloc(std::max(n, 1), s);
+    cnt.zero();
+    k_oneway_t<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, g.S.rowptr.p, g.S.col.p, cnt.p, nullptr);
+    CK_LAUNCH();
+    g.trow.alloc(n + 1, s);
+    exclusive_scan(cnt.p, g.trow.p, n, s);
+    cursor.alloc(std::max(n, 1), s);
+    if (n) CK(cudaMemcpyAsync(cursor.p, g.trow.p, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    g.tcol.alloc(std::max<long>(ub, 1), s);
+    k_oneway_t<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, g.S.rowptr.p, g.S.col.p, cursor.p, g.tcol.p);
+    CK_LAUNCH();
+    g.deg.alloc(std::max(n, 1), s);
+    k_sym_degree<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, g.S.rowptr.p, g.trow.p, g.deg.p);
+    CK_LAUNCH();
+    return g;
 }
 
 // Jones-Plassmann coloring of graph G; returns the number of colors.
-int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &color, cudaStream_t s) {
+int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &color, cudaStream_t s) {
     int n = G.n;
     DVec<unsigned long long> state;
     state.alloc(n, s);
@@ -1581,7 +1693,7 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
     uint32_t hb = hash_base(h->opt.seed, salt, level);
     if (n <= kSmallLevel) {
-        k_jp_small<<<1, 1024, 0, s>>>(n, G.rowptr.p, G.col.p, hb, state.p, counters.p + 3);
+        k_jp_small<<<1, 1024, 0, s>>>(n, G.dev(), hb, state.p, counters.p + 3);
         CK_LAUNCH();
         color.alloc(n, s);
         k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
@@ -1596,8 +1708,7 @@ int jp_color(cpr_handle *h, const Graph &G, int salt, int level, DVec<int> &colo
         for (int k = 0; k < kJpBatch; k++, r++) {
             const int *in = r == 0 ? nullptr : lists.p + (size_t)(r % 2) * n;
             int *out = lists.p + (size_t)((r + 1) % 2) * n;
-            k_jp_round<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.rowptr.p, G.col.p, hb, state.p, r,
-                                               counters.p + 3);
+            k_jp_round<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.dev(), hb, state.p, r, counters.p + 3);
             CK_LAUNCH();
         }
         if (read_int(counters.p + r % 3, s) == 0) break;
@@ -1647,9 +1758,10 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
     }
 }
 
-// C = A B (structural pattern, sorted; values in Gustavson order).  Rows with
-// at most kTinyCand candidates run one per thread, the listed rest with
-// small, medium or large tables; every row is written by exactly one launch.
+// C = A B (structural pattern, sorted; values in Gustavson order; the rows of
+// B sorted).  Rows with at most kMergeRow entries in A, or at most kTinyCand
+// candidates, run one per thread, the listed rest with small, medium or large
+// tables; every row is written by exactly one launch.
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     constexpr int kSW = 16, kMW = 8, kBW = 4;   // warps per block: small, medium and large tables
     int n = A.n;
@@ -1668,6 +1780,9 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     unsigned sblocks = (unsigned)grid_for(n, kSW, 148 * 8);
     unsigned mblocks = (unsigned)grid_for(n, kMW, 148 * 8);
     unsigned bblocks = (unsigned)grid_for(n, kBW, 148 * 8);
+    k_spgemm_merge<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr,
+                                              nullptr, nullptr, nullptr, ucnt.p);
+    CK_LAUNCH();
     k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr, nullptr,
                                              nullptr, nullptr, ucnt.p);
     CK_LAUNCH();
@@ -1691,6 +1806,9 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
                 B.nnz, C.nnz, read_int(cnts.p, s), read_int(cnts.p + 1, s), read_int(cnts.p + 2, s));
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
+    k_spgemm_merge<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
+                                              C.rowptr.p, C.col.p, C.val.p, nullptr);
+    CK_LAUNCH();
     k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
                                              C.rowptr.p, C.col.p, C.val.p, nullptr);
     CK_LAUNCH();
@@ -2000,11 +2118,13 @@ void build_preconditioner(cpr_handle *h) {
     SideWorker side(h);
     side.post([h, nb, nnzb, f32, &bdiag, &side](cudaStream_t s) {
         Bilu &B = h->bilu;
-        Graph S = build_pattern(nb, s, [&](const int *srow, int *out) {
-            k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, srow, out);
-            CK_LAUNCH();
-        });
-        Graph G = sym_union(S, s);
+        // every row holds exactly one diagonal block: nnzb - nb entries
+        SymGraph G = sym_graph(build_pattern_ub(nb, (long)nnzb - nb, s, [&](const int *srow, int *out) {
+                                   k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p,
+                                                                                            h->col.p, srow, out);
+                                   CK_LAUNCH();
+                               }),
+                               (long)nnzb - nb, s);
         side.mark("bilu_graph");
         B.ncolors = jp_color(h, G, 2, 0, B.color, s);
         side.mark("bilu_jp");
@@ -2152,12 +2272,14 @@ void build_preconditioner(cpr_handle *h) {
         side.post([h, l, n, &side](cudaStream_t s) {
             side.mark("idle");
             Level &L = h->lev[l];
-            Graph Sc = build_pattern(n, s, [&](const int *srow, int *out) {
-                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
-                                                                   h->opt.theta_color, srow, out);
-                CK_LAUNCH();
-            });
-            Graph G = sym_union(Sc, s);
+            // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
+            long ub = L.A.nnz;
+            SymGraph G = sym_graph(build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
+                                       k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(
+                                           n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out);
+                                       CK_LAUNCH();
+                                   }),
+                                   ub, s);
             side.mark("c_graph");
             L.ncolors = jp_color(h, G, 0, l, L.color, s);
             side.mark("c_jp");
