@@ -76,6 +76,12 @@ typedef struct {
                            each loading its setup-time operands while its predecessor runs;
                            0 (default, measured as fast on B300): plain stream order.  Results
                            are identical either way. */
+    int tail;           /* 1: the last one or two smoothed AMG levels (never level 0) and the
+                           coarse solve run as one kernel on one thread-block cluster when
+                           they are small enough (at most 4096 rows per level, 16 colors, a
+                           coarse level of at most 1024 rows) and the cycle is V(1,1);
+                           0 (default, measured faster on B300): one kernel per phase.
+                           Results are identical either way. */
 } cpr_opts;
 
 typedef struct {
@@ -88,6 +94,7 @@ typedef struct {
     double rel_res;     /* ||b - A x|| / ||b - A x_0||, true FP64 residual */
     double setup_ms;    /* wall time of the last build of B (0 if reused) */
     double solve_ms;    /* wall time of this cpr_solve */
+    int tail_levels;    /* smoothed levels run by the cluster tail kernel (0: none) */
 } cpr_stats;
 
 /* Fill *o with the defaults listed above. */

@@ -31,13 +31,14 @@ class Opts(C.Structure):
                 ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
-                ("stream", C.c_void_p), ("pdl", C.c_int)]
+                ("stream", C.c_void_p), ("pdl", C.c_int), ("tail", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("setup_called", C.c_int),
                 ("setup_count", C.c_int), ("levels", C.c_int), ("converged", C.c_int),
-                ("rel_res", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double)]
+                ("rel_res", C.c_double), ("setup_ms", C.c_double), ("solve_ms", C.c_double),
+                ("tail_levels", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

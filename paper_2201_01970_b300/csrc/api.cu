@@ -37,7 +37,7 @@ void check_opts(const cpr_opts &o) {
               o.post >= 0 && o.coarse_max >= 1 && o.coarse_max <= kMaxCoarse && o.max_levels >= 1 &&
               o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
               o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
-              (o.pdl == 0 || o.pdl == 1);
+              (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1);
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -240,6 +240,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->seed = 0;
     o->stream = nullptr;
     o->pdl = 0;
+    o->tail = 0;
 }
 
 const char *cpr_strerror(int code) {
@@ -366,6 +367,7 @@ int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats 
         local.setup_called = h->setup_called;
         local.setup_count = h->setup_count;
         local.levels = (int)h->lev.size();
+        local.tail_levels = h->tail_top >= 0 ? (int)h->lev.size() - 1 - h->tail_top : 0;
         local.setup_ms = h->setup_called ? h->setup_ms : 0.0;
         local.solve_ms = now_ms() - t0;
         if (st) *st = local;

@@ -228,6 +228,7 @@ struct cpr_handle {
     int sgb_epoch = -1;
     cpr::BatchInfo *batch = nullptr;
     cudaEvent_t step_done[2] = {nullptr, nullptr};
+    int tail_top = -1;               // first level run by the cluster tail kernel, -1 = none
 };
 
 namespace cpr {
@@ -263,6 +264,7 @@ void apply_B(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, do
 void vcycle_apply(cpr_handle *h, const double *b, double *x);
 void bilu_apply(cpr_handle *h, const double *r, double *z);
 void refresh_outer(cpr_handle *h, bool pattern_changed);
+void choose_tail(cpr_handle *h);   // decide which levels the cluster tail kernel runs
 int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
 void batch_prepare(cpr_handle *h);

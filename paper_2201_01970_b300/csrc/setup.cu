@@ -1901,6 +1901,7 @@ void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr
 }
 
 void free_preconditioner(cpr_handle *h) {
+    h->tail_top = -1;
     h->lev.clear();
     h->pcol0.release();
     h->pcol0_32.release();
@@ -2461,6 +2462,7 @@ void build_preconditioner(cpr_handle *h) {
         }
     }
     coarse_join.finish();
+    choose_tail(h);
     // Kernels that meet a zero or non-finite pivot (an AMG level's diagonal,
     // the coarsest matrix, a BILU(0) block) record CPR_ERR_SINGULAR and go on
     // with a unit stand-in, so the setup runs to completion without host

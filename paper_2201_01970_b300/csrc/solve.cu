@@ -12,7 +12,10 @@
 #include <cmath>
 
 #include "cpr_internal.cuh"
+#include <atomic>
+
 #include "sweeps.cuh"
+#include "tail.cuh"
 
 namespace cpr {
 
@@ -991,6 +994,80 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
     }
 }
 
+// The cluster tail from level h->tail_top down: one launch of one cluster.
+template <class T>
+void launch_tail(cpr_handle *h, const int *done) {
+    TailArgs<T> a{};
+    int L = (int)h->lev.size(), t = h->tail_top;
+    a.nlev = L - 1 - t;
+    int off = 0;
+    for (int q = 0; q < a.nlev; q++) {
+        Level &Lv = h->lev[t + q];
+        TailLevel<T> &d = a.lev[q];
+        d.n = Lv.A.n;
+        d.ncolors = Lv.ncolors;
+        d.gA = Lv.gA;
+        d.gP = Lv.gP;
+        d.gR = Lv.gR;
+        for (int c = 0; c <= Lv.ncolors; c++) d.color_off[c] = Lv.color_off[c];
+        d.arow = Lv.Ao.rowptr.p;
+        d.acol = Lv.Ao.col.p;
+        d.aval = Vals<T>::Ao(Lv);
+        d.diag = Vals<T>::diag(Lv);
+        d.dinv = Vals<T>::dinv(Lv);
+        d.prow = Lv.Pp.rowptr.p;
+        d.pcol = Lv.Pp.col.p;
+        d.pval = Vals<T>::P(Lv);
+        d.rrow = Lv.Rp.rowptr.p;
+        d.rcol = Lv.Rp.col.p;
+        d.rval = Vals<T>::R(Lv);
+        d.ox = off;
+        d.os = off + d.n;
+        d.orr = off + 2 * d.n;
+        d.ob = off + 3 * d.n;
+        off += 4 * d.n;
+    }
+    a.nc = h->lev.back().A.n;
+    a.obc = off;
+    a.oxc = off + a.nc;
+    off += 2 * a.nc;
+    a.cinv = h->cinv.p;
+    a.b_top = Vals<T>::b(h->lev[t]);
+    a.x_top = Vals<T>::x(h->lev[t]);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kTailCTAs);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = (size_t)off * sizeof(T);
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kTailCTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, k_tail_vcycle<T>, a, done));
+    CK_LAUNCH();
+}
+
+// Shared-memory ceiling of both tail kernels, set once per device.
+void tail_attr() {
+    static std::atomic<unsigned long long> set{0};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned long long bit = 1ull << (dev & 63);
+    if (set.load(std::memory_order_acquire) & bit) return;
+    CK(cudaFuncSetAttribute(k_tail_vcycle<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemMax));
+    CK(cudaFuncSetAttribute(k_tail_vcycle<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTailSmemMax));
+    // the replicas are small: leave the rest of the SM's memory to L1, which
+    // holds this CTA's rows of the tail matrices (prefetched at kernel start)
+    CK(cudaFuncSetAttribute(k_tail_vcycle<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            cudaSharedmemCarveoutMaxL1));
+    CK(cudaFuncSetAttribute(k_tail_vcycle<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            cudaSharedmemCarveoutMaxL1));
+    set.fetch_or(bit, std::memory_order_release);
+}
+
 // V(pre, post) cycle on level l from x_l = 0 (pre-smoothing colors ascending,
 // post-smoothing descending).  On return the level's result is x with the
 // range `out` still staged.  first_done: the kernel that wrote b_l also did
@@ -1000,6 +1077,11 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
     cudaStream_t s = h->stream;
     Level &L = h->lev[l];
     int n = L.A.n;
+    if (l == h->tail_top) {   // this level and everything below in one cluster
+        launch_tail<T>(h, done);
+        out = Pending{};
+        return;
+    }
     if (l == (int)h->lev.size() - 1) {
         launch_b(h, k_coarse_solve<T>, blocks_for((long)n * 32), kBlock, s, n, h->cinv.p, Vals<T>::b(L),
                  Vals<T>::x(L), done);
@@ -1018,7 +1100,8 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
                                        Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     pd = Pending{};
     Level &C = h->lev[l + 1];
-    bool fuse = l + 1 < (int)h->lev.size() - 1 && h->opt.pre > 0;   // C is smoothed from zero
+    // C is smoothed from zero by the next kernel unless the cluster tail takes it
+    bool fuse = l + 1 < (int)h->lev.size() - 1 && h->opt.pre > 0 && l + 1 != h->tail_top;
     if (fuse) {
         CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer_first<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
                                            L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
@@ -1344,6 +1427,50 @@ int profile_levels_t(cpr_handle *h, int reps, double *us, int n_us) {
 }
 
 }  // namespace
+
+// The cluster tail covers the last one or two smoothed levels (never level
+// 0) when they and the coarse level are small enough for one cluster's shared
+// memory, the cycle is V(1,1), and the cluster can be scheduled.
+void choose_tail(cpr_handle *h) {
+    h->tail_top = -1;
+    const cpr_opts &o = h->opt;
+    int L = (int)h->lev.size();
+    if (!o.tail || o.pre != 1 || o.post != 1 || L < 3) return;
+    int nc = h->lev[L - 1].A.n;
+    if (nc > kTailMaxCoarse) return;
+    size_t elt = o.precond_fp32 ? sizeof(float) : sizeof(double);
+    size_t elems = 2 * (size_t)nc;
+    int top = -1;
+    for (int l = L - 2; l >= 1 && L - 1 - l <= kTailMaxLevels; l--) {
+        const Level &Lv = h->lev[l];
+        if (Lv.A.n > kTailMaxRows || Lv.ncolors < 1 || Lv.ncolors > kTailMaxColors) break;
+        size_t e = elems + 4 * (size_t)Lv.A.n;
+        if (e * elt > (size_t)kTailSmemMax) break;
+        elems = e;
+        top = l;
+    }
+    if (top < 0) return;
+    tail_attr();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kTailCTAs);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = elems * elt;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kTailCTAs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    cudaError_t e = o.precond_fp32 ? cudaOccupancyMaxActiveClusters(&nclusters, k_tail_vcycle<float>, &cfg)
+                                   : cudaOccupancyMaxActiveClusters(&nclusters, k_tail_vcycle<double>, &cfg);
+    if (e != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        return;
+    }
+    h->tail_top = top;
+}
 
 int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
     bool prof = h->prof;

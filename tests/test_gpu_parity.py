@@ -291,6 +291,32 @@ def test_full_size_fp32_mode_128x128x32(torch, cpr):
 
 
 @pytest.mark.parametrize("fp32", [0, 1])
+def test_cluster_tail_changes_no_result(torch, cpr, fp32):
+    """The cluster tail (the last smoothed levels and the coarse solve in one
+    launch on one thread-block cluster) computes every product as the
+    kernel-per-phase V-cycle does, so B z and a whole solve agree bit for bit.
+    The ragged case puts two levels in the tail, 20x20x5 one, and 128x128x32
+    its levels 4 (2,044 rows) and 5 (459)."""
+    rng = np.random.default_rng(5)
+    for J, want in ((ragged(), 2), (bs.jacobian("20x20x5"), 1), (bs.jacobian("128x128x32"), 2)):
+        dj = DevJ(torch, J)
+        v = rng.standard_normal(J.n)
+        out = {}
+        for tail in (0, 1):
+            g = cpr.Solver(dj, precond_fp32=fp32, tail=tail)
+            z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
+            g.apply(dev(torch, v), z)
+            x, st = g.solve(dev(torch, J.b), rtol=1e-8)
+            out[tail] = (z.cpu().numpy(), x.cpu().numpy(), st)
+            g.close()
+        assert out[0][2]["tail_levels"] == 0
+        assert out[1][2]["tail_levels"] == want
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        np.testing.assert_array_equal(out[0][1], out[1][1])
+        assert out[0][2]["iters"] == out[1][2]["iters"]
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
 def test_dependent_launch_changes_no_result(torch, cpr, fp32):
     """Programmatic dependent launch only moves the loads of setup-time
     operands ahead of the wait on the previous kernel: solves with it on and
