@@ -730,26 +730,37 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
 // every C entry is summed in the same order as Gustavson's row-by-row product.
 // Rows with more distinct columns than the table holds take an exact slow path.
 
-// Five tiers.  Rows with at most kMergeRow entries in A (every row of A P at
-// level 0 and most rows of R (A P) at the fine levels) take one thread each,
-// which merges the row's B rows (each sorted) held as list heads in
-// registers: the smallest head column is the next C column, and its products
-// are added in list order, i.e. ascending k.  Longer rows with at most
-// kTinyCand candidate products take one thread each too:
-// the products, in (A entry, B entry) order, are insertion-sorted by column in
-// the thread's own arrays (stable, so each column's products stay in
-// ascending k) and each column's run is summed in that order.  Rows up to
-// kSmallCand run with small per-warp tables at full occupancy; rows up to
-// kMidCand (most of R (A P): ~33 per coarse row at level 0, ~70 at level 1)
-// with medium tables, still at full occupancy; the rest with large tables.
-// A candidate-count pass lists the small, medium and large rows.
+// Six tiers, chosen per row from its length in A and its candidate product
+// count (sum over k in A_i of |B_k|).  The first three take one thread per
+// row.  Rows with at most 8 (or 9 to 16) entries in A and few candidates
+// (every row of A P at levels 0 and 1, most rows of R (A P) at level 0) are
+// merged from their B rows (each sorted) held as list heads in registers:
+// the smallest head column is the next C column, and its products are added
+// in list order, i.e. ascending k.  Other rows with at most kTinyCand
+// candidates insertion-sort their products by column in the thread's own
+// arrays (stable, so each column's products stay in ascending k) and sum each
+// column's run in that order.  Rows up to kSmallCand candidates run with small
+// per-warp tables at full occupancy, rows up to kMidCand (most of R (A P) at
+// the coarser levels) with medium tables, still at full occupancy, the rest
+// with large tables.  A merge costs the thread one step per C column and list
+// head, so long merges go to the tables, whose warps split a row's products.
 //   CAP: hash slots per warp (power of two); HMAX: distinct columns handled
 //   in shared memory, a power of two (larger rows take the exact slow path);
 //   WARPS per block.
-constexpr int kMergeRow = 8;
+constexpr int kMerge8Cand = 64;    // merge tier 0: at most 8 entries in A and this many candidates
+constexpr int kMerge16Cand = 48;   // merge tier 1: 9 to 16 entries in A and this many candidates
 constexpr int kTinyCand = 24;
 constexpr int kSmallCand = 32;
-constexpr int kMidCand = 160;   // rows above kSmallCand and up to this: 256-slot tables
+constexpr int kMidCand = 160;      // rows above kSmallCand and up to this: 256-slot tables
+enum { kTierMerge8, kTierMerge16, kTierTiny, kTierSmall, kTierMid, kTierBig };
+
+__device__ __forceinline__ int spgemm_tier(int len, int cand) {
+    if (len <= 8 && cand <= kMerge8Cand) return kTierMerge8;
+    if (len <= 16 && cand <= kMerge16Cand) return kTierMerge16;
+    if (cand <= kTinyCand) return kTierTiny;
+    if (cand <= kSmallCand) return kTierSmall;
+    return cand <= kMidCand ? kTierMid : kTierBig;
+}
 constexpr int kEmpty = -1;
 
 // Per-warp scratch for enumerating the products of one chunk of 32 A entries:
@@ -862,54 +873,58 @@ __device__ int next_col(int i, long last, const int *ar, const int *ac, const in
     return m;
 }
 
-// Rows of A B with more than kMergeRow entries in A, by candidate product
-// count (sum over k in A_i of |B_k|): above kTinyCand and up to kSmallCand
-// into `small`, up to kMidCand into `mid`, above kMidCand into `big`, each
-// list in any order.  cnt: small, mid, big.
+// The rows of the three table tiers: `small`, `mid` and `big`, each list in
+// any order.  cnt: their lengths.
 __global__ void k_spgemm_cand(int n, const int *ar, const int *ac, const int *br, int *small, int *mid, int *big,
                               int *cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || ar[i + 1] - ar[i] <= kMergeRow) return;
+    if (i >= n) return;
     int c = 0;
     for (int p = ar[i]; p < ar[i + 1]; p++) {
         int k = ac[p];
         c += br[k + 1] - br[k];
     }
-    if (c > kMidCand) big[atomicAdd(&cnt[2], 1)] = i;
-    else if (c > kSmallCand) mid[atomicAdd(&cnt[1], 1)] = i;
-    else if (c > kTinyCand) small[atomicAdd(&cnt[0], 1)] = i;
+    int tier = spgemm_tier(ar[i + 1] - ar[i], c);
+    if (tier == kTierBig) big[atomicAdd(&cnt[2], 1)] = i;
+    else if (tier == kTierMid) mid[atomicAdd(&cnt[1], 1)] = i;
+    else if (tier == kTierSmall) small[atomicAdd(&cnt[0], 1)] = i;
 }
 
-// The merge tier: one thread per row with at most kMergeRow entries in A
-// (other rows are skipped).  Without cr, counts the row's distinct columns
-// into ucnt; with cr, writes the row's columns (ascending) and values.
+// A merge tier (ML list heads: tier kTierMerge8 or kTierMerge16), one thread
+// per row of that tier (other rows are skipped).  Without cr, counts the
+// row's distinct columns into ucnt; with cr, writes the row's columns
+// (ascending) and values.
+template <int ML, int TIER>
 __global__ void k_spgemm_merge(int n, const int *ar, const int *ac, const double *av, const int *br,
                                const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *ucnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = ar[i], b = ar[i + 1];
-    if (b - a > kMergeRow) return;
-    int q[kMergeRow], e[kMergeRow], hd[kMergeRow];
-    double x[kMergeRow];
+    if (b - a > ML) return;
+    int q[ML], e[ML], hd[ML];
+    double x[ML];
+    int cand = 0;
 #pragma unroll
-    for (int t = 0; t < kMergeRow; t++) {
+    for (int t = 0; t < ML; t++) {
         bool in = a + t < b;
         int k = in ? ac[a + t] : 0;
         q[t] = in ? br[k] : 0;
         e[t] = in ? br[k + 1] : 0;
         x[t] = in && cr ? av[a + t] : 0.0;
+        cand += e[t] - q[t];
     }
+    if (spgemm_tier(b - a, cand) != TIER) return;
 #pragma unroll
-    for (int t = 0; t < kMergeRow; t++) hd[t] = q[t] < e[t] ? bc[q[t]] : INT_MAX;
+    for (int t = 0; t < ML; t++) hd[t] = q[t] < e[t] ? bc[q[t]] : INT_MAX;
     int o = cr ? cr[i] : 0, c = 0;
     for (;;) {
         int J = INT_MAX;
 #pragma unroll
-        for (int t = 0; t < kMergeRow; t++) J = min(J, hd[t]);
+        for (int t = 0; t < ML; t++) J = min(J, hd[t]);
         if (J == INT_MAX) break;
         double sum = 0.0;
 #pragma unroll
-        for (int t = 0; t < kMergeRow; t++)
+        for (int t = 0; t < ML; t++)
             if (hd[t] == J) {   // a B row holds each column once
                 if (cr) sum = __dadd_rn(sum, __dmul_rn(x[t], bv[q[t]]));
                 q[t]++;
@@ -925,22 +940,20 @@ __global__ void k_spgemm_merge(int n, const int *ar, const int *ac, const double
     if (!cr) ucnt[i] = c;
 }
 
-// The tiny tier: one thread per row with more than kMergeRow entries in A and
-// at most kTinyCand candidates (other rows are skipped).  Without cr, counts
-// the row's distinct columns into ucnt; with cr, writes the row's columns
-// (ascending) and values.
+// The tiny tier: one thread per row of tier kTierTiny (other rows are
+// skipped).  Without cr, counts the row's distinct columns into ucnt; with
+// cr, writes the row's columns (ascending) and values.
 __global__ void k_spgemm_tiny(int n, const int *ar, const int *ac, const double *av, const int *br,
                               const int *bc, const double *bv, const int *cr, int *cc, double *cv, int *ucnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = ar[i], b = ar[i + 1];
-    if (b - a <= kMergeRow) return;
     int cand = 0;
     for (int p = a; p < b; p++) {
         int k = ac[p];
         cand += br[k + 1] - br[k];
     }
-    if (cand > kTinyCand) return;
+    if (spgemm_tier(b - a, cand) != kTierTiny) return;
     int J[kTinyCand];
     double V[kTinyCand];
     int m = 0;
@@ -1759,9 +1772,9 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
 }
 
 // C = A B (structural pattern, sorted; values in Gustavson order; the rows of
-// B sorted).  Rows with at most kMergeRow entries in A, or at most kTinyCand
-// candidates, run one per thread, the listed rest with small, medium or large
-// tables; every row is written by exactly one launch.
+// B sorted).  Each row belongs to exactly one tier (spgemm_tier) and is
+// written by exactly one launch: the three per-thread tiers over all rows,
+// the table tiers over their lists.
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     constexpr int kSW = 16, kMW = 8, kBW = 4;   // warps per block: small, medium and large tables
     int n = A.n;
@@ -1780,8 +1793,11 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     unsigned sblocks = (unsigned)grid_for(n, kSW, 148 * 8);
     unsigned mblocks = (unsigned)grid_for(n, kMW, 148 * 8);
     unsigned bblocks = (unsigned)grid_for(n, kBW, 148 * 8);
-    k_spgemm_merge<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr,
-                                              nullptr, nullptr, nullptr, ucnt.p);
+    k_spgemm_merge<8, kTierMerge8><<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p,
+                                                     nullptr, nullptr, nullptr, nullptr, ucnt.p);
+    CK_LAUNCH();
+    k_spgemm_merge<16, kTierMerge16><<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p,
+                                                            B.col.p, nullptr, nullptr, nullptr, nullptr, ucnt.p);
     CK_LAUNCH();
     k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr, nullptr,
                                              nullptr, nullptr, ucnt.p);
@@ -1806,8 +1822,12 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
                 B.nnz, C.nnz, read_int(cnts.p, s), read_int(cnts.p + 1, s), read_int(cnts.p + 2, s));
     C.col.alloc(std::max(C.nnz, 1), s);
     C.val.alloc(std::max(C.nnz, 1), s);
-    k_spgemm_merge<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
-                                              C.rowptr.p, C.col.p, C.val.p, nullptr);
+    k_spgemm_merge<8, kTierMerge8><<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p,
+                                                     B.val.p, C.rowptr.p, C.col.p, C.val.p, nullptr);
+    CK_LAUNCH();
+    k_spgemm_merge<16, kTierMerge16><<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p,
+                                                            B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p,
+                                                            nullptr);
     CK_LAUNCH();
     k_spgemm_tiny<<<tblocks, kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p,
                                              C.rowptr.p, C.col.p, C.val.p, nullptr);
