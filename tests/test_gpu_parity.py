@@ -56,10 +56,20 @@ def ragged():
     return bs.jacobian(bs.GridSpec(37, 23, 9, 0.0, 1.5, 0.3, None, "five_spot", seed=5))
 
 
+def tall_well():
+    """4x4x600 with corner wells perforating all 600 layers: a 601-block well
+    row at level 0 and Galerkin rows of 1,119 (level 1) and 467 (level 2)
+    columns, past the 512 distinct columns the shared-memory SpGEMM tables
+    hold (the exact slow path), long transpose rows and warp-per-row
+    strength."""
+    return bs.jacobian(bs.GridSpec(4, 4, 600, wells="corners", seed=3))
+
+
 CASES = {
     "tiny": lambda: bs.tiny(),
     "20x20x5": lambda: bs.jacobian("20x20x5"),
     "37x23x9": ragged,
+    "tall_well": tall_well,
 }
 
 
