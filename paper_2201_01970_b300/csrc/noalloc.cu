@@ -67,7 +67,7 @@ void sweeps(cpr_handle *h, const double *r, double *z, T *y, const T *lv, const 
     int nb = h->nb;
     // the same sweep kernels, lane split and color order as cpr_bilu_apply, so
     // the two entries agree bit for bit
-    constexpr int G = sizeof(T) == 4 ? 4 : 1;
+    constexpr int G = sizeof(T) == 4 ? kBiluLanesF32 : 1;
     // every entry of y that the sweeps read is written here first, so no part
     // of the scratch has to start at zero
     k_load<T><<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, r, y);

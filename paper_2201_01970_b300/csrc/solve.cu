@@ -1142,9 +1142,7 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     Bilu &B = h->bilu;
     // the lowest color has no lower neighbours (L holds lower colors only), so
     // its forward substitution leaves y unchanged and is skipped
-    // FP32: 4 lanes share a block row (FP32 shuffles are cheap); FP64: one
-    // thread per block row, no cross-lane FP64 additions
-    constexpr int G = sizeof(T) == 4 ? 4 : 1;
+    constexpr int G = sizeof(T) == 4 ? kBiluLanesF32 : 1;
     for (int c = 1; c < B.ncolors; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
