@@ -586,6 +586,9 @@ def main():
         if rank == 0:
             print(json.dumps({"partial": args.arm, "ms_per_step": r["total_ms"] / K,
                               "launches_per_step": r["launches"] / K,
+                              "setup_ms_mean": statistics.mean([st["setup_ms"] for st in r["stats"]
+                                                                if st["setup_called"]] or [0.0]),
+                              "solve_phase_ms_mean": statistics.mean([st["solve_ms"] for st in r["stats"]]),
                               "iters": [st["iters"] for st in r["stats"]]}), flush=True)
         return
 
