@@ -40,7 +40,8 @@ class Opts(C.Structure):
     _fields_ = [("theta_color", C.c_double), ("theta_amg", C.c_double), ("mu", C.c_int),
                 ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
-                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64)]
+                ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
+                ("bilu_order", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -87,6 +88,8 @@ def lib():
         L.o_decouple.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _f64p, _f64p]
         L.o_bilu0.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_uint64, _i32p, _f64p]
         L.o_bilu0_solve.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _f64p, _f64p]
+        L.o_bilu0_natural.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p]
+        L.o_natural_levels.argtypes = [C.c_int, _i32p, _i32p, _i32p]
         L.o_fgmres_identity.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
                                         C.c_int, C.c_int, C.POINTER(Stats), vp]
         L.o_default_opts.argtypes = [C.POINTER(Opts)]
@@ -243,6 +246,24 @@ def bilu0(J, seed=0):
     if nc < 0:
         raise RuntimeError(f"oracle BILU(0) failed ({nc})")
     return bcolor, nc, lu
+
+
+def bilu0_natural(J):
+    """Natural-order block ILU(0) (the level-scheduled BILU of Sec. 6): factor
+    array in A's pattern, as bilu0's."""
+    lu = np.zeros(9 * J.nnzb)
+    rc = lib().o_bilu0_natural(J.nb, _i32(J.rowptr), _i32(J.col), _f64(J.val), lu)
+    if rc < 0:
+        raise RuntimeError(f"oracle natural-order BILU(0) failed ({rc})")
+    return lu
+
+
+def natural_levels(J):
+    """Level sets of the natural-order block triangular solves: (level per
+    block row, number of levels)."""
+    level = np.zeros(J.nb, np.int32)
+    nlev = lib().o_natural_levels(J.nb, _i32(J.rowptr), _i32(J.col), level)
+    return level, nlev
 
 
 def bilu0_solve(J, bcolor, nbcolors, lu, r):

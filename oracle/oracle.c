@@ -895,6 +895,44 @@ int o_bilu0(int nb, const int *rowptr, const int *col, const double *val, uint64
     return rc == O_OK ? nc : rc;
 }
 
+/*
+ * Natural-order block ILU(0), the factorization level scheduling runs in
+ * parallel (Sec. 6's second stage): with every block row in one color the
+ * (color, index) order above is the index order, so the lower part of row i is
+ * its blocks j < i, eliminated in ascending j.  Returns 1 (one color) or an
+ * error code.
+ */
+int o_bilu0_natural(int nb, const int *rowptr, const int *col, const double *val, double *lu) {
+    int *one = xcalloc((size_t)nb, sizeof(int));
+    int rc = bilu0_factor(nb, rowptr, col, val, one, 1, lu);
+    free(one);
+    return rc == O_OK ? 1 : rc;
+}
+
+/*
+ * Level sets of the natural-order block triangular solves: level(i) is 0 when
+ * block row i has no neighbour j < i in the symmetrised block pattern, else
+ * 1 + the largest level among those neighbours.  Rows of one level are never
+ * adjacent, and every neighbour j < i of i lies in a lower level.  Returns the
+ * number of levels.
+ */
+int o_natural_levels(int nb, const int *rowptr, const int *col, int *level) {
+    o_csr A = csr_view(nb, nb, rowptr, col, NULL);
+    o_csr G = sym_union(&A);
+    int nlev = 0;
+    for (int i = 0; i < nb; i++) {
+        int lv = 0;
+        for (int p = G.rowptr[i]; p < G.rowptr[i + 1]; p++) {
+            int j = G.col[p];
+            if (j < i && level[j] + 1 > lv) lv = level[j] + 1;
+        }
+        level[i] = lv;
+        if (lv + 1 > nlev) nlev = lv + 1;
+    }
+    csr_release(&G);
+    return nlev;
+}
+
 /* ------------------------------------------------------------- hierarchy */
 
 void o_default_opts(o_opts *o) {
@@ -910,6 +948,7 @@ void o_default_opts(o_opts *o) {
     o->coarse_max = 256;
     o->max_levels = 20;
     o->seed = 0;
+    o->bilu_order = 0;
 }
 
 static void free_setup(o_handle *h) {
@@ -1019,7 +1058,8 @@ static int build_preconditioner(o_handle *h) {
     if (rc != O_OK) return rc;
     /* second stage */
     h->bcolor = xcalloc((size_t)nb, sizeof(int));
-    h->nbcolors = bilu_coloring(nb, h->rowptr, h->col, o->seed, h->bcolor);
+    /* natural order: one color, so the (color, index) order is the index order */
+    h->nbcolors = o->bilu_order ? 1 : bilu_coloring(nb, h->rowptr, h->col, o->seed, h->bcolor);
     h->lu = xcalloc(9 * (size_t)nnzb, sizeof(double));
     rc = bilu0_factor(nb, h->rowptr, h->col, h->pval, h->bcolor, h->nbcolors, h->lu);
     return rc;

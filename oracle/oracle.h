@@ -32,6 +32,8 @@ typedef struct {
     int coarse_max;       /* coarsest level size for the dense LU (256) */
     int max_levels;       /* (20) */
     uint64_t seed;        /* hash seed of coloring and C/F splitting */
+    int bilu_order;       /* 0: multicolor BILU(0) in (JP color, index) order (reading R6);
+                             1: natural order, the level-scheduled BILU of Sec. 6 (0) */
 } o_opts;
 
 typedef struct {
@@ -72,6 +74,8 @@ int    o_decouple(int nb, const int *rowptr, const int *col, const double *val, 
                   double *w, double *apval);
 int    o_bilu0(int nb, const int *rowptr, const int *col, const double *val, uint64_t seed,
                int *bcolor, double *lu);
+int    o_bilu0_natural(int nb, const int *rowptr, const int *col, const double *val, double *lu);
+int    o_natural_levels(int nb, const int *rowptr, const int *col, int *level);
 void   o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,
                      const int *bcolor, int nbcolors, const double *r, double *z);
 int    o_fgmres_identity(int nb, const int *rowptr, const int *col, const double *val,

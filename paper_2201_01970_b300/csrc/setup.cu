@@ -1817,7 +1817,8 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     exclusive_scan(ucnt.p, C.rowptr.p, n, s);
     C.nnz = read_int(C.rowptr.p + n, s);
     if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
-    if (getenv("CPR_SETUP_TIMING"))
+    // the tier counts are read back: printed at CPR_SETUP_TIMING=2 only
+    if (const char *t = getenv("CPR_SETUP_TIMING"); t && atoi(t) >= 2)
         fprintf(stderr, "[cpr setup] spgemm n=%d annz=%d bnnz=%d cnnz=%d small=%d mid=%d big=%d\n", n, A.nnz,
                 B.nnz, C.nnz, read_int(cnts.p, s), read_int(cnts.p + 1, s), read_int(cnts.p + 2, s));
     C.col.alloc(std::max(C.nnz, 1), s);
@@ -1936,8 +1937,54 @@ void free_preconditioner(cpr_handle *h) {
     h->have_B = false;
 }
 
-// Wall-clock phase marks of one setup, printed to stderr when the environment
-// variable CPR_SETUP_TIMING is set (diagnostics only).
+// Phase marks of a setup, printed to stderr when CPR_SETUP_TIMING is set
+// (diagnostics only).  A mark records a timing event on its clock's stream
+// and the host time; each prints as name=host/device, both in ms since the
+// setup began: when the host issued the mark and when the stream reached it.
+// Marks do not synchronise, so both chains run as they do untimed.
+struct PhaseClock {
+    bool on = getenv("CPR_SETUP_TIMING") != nullptr;
+    cudaStream_t s = nullptr;
+    const char *tag = "";
+    const PhaseClock *origin = nullptr;   // the clock whose start is time zero (this one when null)
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    cudaEvent_t e0 = nullptr;
+    struct Mark {
+        const char *name;
+        double host;
+        cudaEvent_t ev;
+    };
+    std::vector<Mark> marks;
+    void start(cudaStream_t stream) {
+        s = stream;
+        if (on && !e0 && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+    }
+    void mark(const char *name) {
+        if (!on) return;
+        const PhaseClock &o = origin ? *origin : *this;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, s);
+        marks.push_back(
+            {name, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - o.t0).count(), e});
+    }
+    ~PhaseClock() {
+        if (!on) return;
+        const PhaseClock &o = origin ? *origin : *this;
+        std::string line;
+        for (auto &m : marks) {
+            float d = -1.0f;
+            if (cudaEventSynchronize(m.ev) == cudaSuccess && o.e0) cudaEventElapsedTime(&d, o.e0, m.ev);
+            char buf[96];
+            snprintf(buf, sizeof(buf), " %s=%.2f/%.2f", m.name, m.host, d);
+            line += buf;
+            cudaEventDestroy(m.ev);
+        }
+        if (e0) cudaEventDestroy(e0);
+        fprintf(stderr, "[cpr setup ms host/dev]%s%s\n", tag, line.c_str());
+    }
+};
+
 // Setup work that needs only its own inputs -- the BILU(0) second stage
 // (needs A) and each level's smoother coloring (needs A_l) -- runs on a
 // worker host thread with its own stream while this thread builds the AMG
@@ -1945,31 +1992,9 @@ void free_preconditioner(cpr_handle *h) {
 // read-backs, so running them side by side keeps the GPU and the host busy.
 // A task starts behind an event of the main stream; join() makes the main
 // stream wait for everything the worker issued and rethrows its error.
-// Phase times of a setup (CPR_SETUP_TIMING set): each mark waits for its
-// stream, so the marks serialise what they time.
-struct PhaseClock {
-    bool on = getenv("CPR_SETUP_TIMING") != nullptr;
-    cudaStream_t s;
-    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
-    std::string line;
-    const char *tag = "";
-    void mark(const char *name) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        auto t = std::chrono::steady_clock::now();
-        char buf[96];
-        snprintf(buf, sizeof(buf), " %s=%.2f", name, std::chrono::duration<double, std::milli>(t - t0).count());
-        line += buf;
-        t0 = t;
-    }
-    ~PhaseClock() {
-        if (on) fprintf(stderr, "[cpr setup ms]%s%s\n", tag, line.c_str());
-    }
-};
-
 class SideWorker {
   public:
-    SideWorker(cpr_handle *h) : h_(h) {
+    SideWorker(cpr_handle *h, const PhaseClock *origin) : h_(h) {
         int dev = 0;
         CK(cudaGetDevice(&dev));
         if (!h->side) {
@@ -1979,6 +2004,7 @@ class SideWorker {
         }
         clk_.s = h->side;
         clk_.tag = " side:";
+        clk_.origin = origin;
         th_ = std::thread([this, dev] { run(dev); });
     }
     ~SideWorker() {
@@ -2098,7 +2124,7 @@ void build_preconditioner(cpr_handle *h) {
     free_preconditioner(h);
     cudaStream_t s = h->stream;
     PhaseClock clk;
-    clk.s = s;
+    clk.start(s);
     const cpr_opts &o = h->opt;
     int nb = h->nb, nnzb = h->nnzb;
     bool f32 = o.precond_fp32 != 0;
@@ -2136,7 +2162,7 @@ void build_preconditioner(cpr_handle *h) {
 
     clk.mark("decouple");
     // ---- second stage: multicolor BILU(0), on the side worker ----
-    SideWorker side(h);
+    SideWorker side(h, &clk);
     side.post([h, nb, nnzb, f32, &bdiag, &side](cudaStream_t s) {
         Bilu &B = h->bilu;
         // every row holds exactly one diagonal block: nnzb - nb entries

@@ -396,6 +396,74 @@ def test_bilu0_block_diagonal_is_exact():
     assert np.allclose(z, np.linalg.solve(Jd.to_dense(), r), rtol=1e-12)
 
 
+def _block_mask(J):
+    mask = np.zeros((J.n, J.n), bool)
+    for i in range(J.nb):
+        for p in range(J.rowptr[i], J.rowptr[i + 1]):
+            j = J.col[p]
+            mask[3 * i:3 * i + 3, 3 * j:3 * j + 3] = True
+    return mask
+
+
+def test_bilu0_natural_defining_property(tiny):
+    """Natural-order block ILU(0) (the level-scheduled BILU of Sec. 6): L is
+    block lower and U block upper in the natural numbering, (L U)_ij = A_ij on
+    A's block pattern, and the solve applies (L U)^-1."""
+    J = tiny
+    lu = oracle.bilu0_natural(J)
+    one = np.zeros(J.nb, np.int32)
+    L, U = _bilu_dense_factors(J, one, 1, lu)
+    nz_l = np.abs(L.reshape(J.nb, 3, J.nb, 3)).sum(axis=(1, 3)) > 0
+    nz_u = np.abs(U.reshape(J.nb, 3, J.nb, 3)).sum(axis=(1, 3)) > 0
+    assert not np.triu(nz_l, 1).any() and not np.tril(nz_u, -1).any()   # block lower / upper
+    assert np.array_equal(np.diag(L), np.ones(J.n))
+    LU = L @ U
+    A = J.to_dense()
+    mask = _block_mask(J)
+    assert np.allclose(LU[mask], A[mask], rtol=1e-11, atol=1e-11 * np.abs(A).max())
+    # with wells the pattern is not closed under elimination: the fill ILU(0) drops is real
+    assert not np.allclose(LU, A, rtol=1e-6, atol=1e-9 * np.abs(A).max())
+    r = np.random.default_rng(2).standard_normal(J.n)
+    z = oracle.bilu0_solve(J, one, 1, lu, r)
+    assert np.allclose(z, np.linalg.solve(LU, r), rtol=1e-10, atol=1e-12)
+
+
+def test_bilu0_natural_on_a_chain_is_the_exact_lu():
+    """A 1-D grid gives a block-tridiagonal A, whose natural-order elimination
+    creates no fill: ILU(0) is the exact block LU and B = A^-1."""
+    J = bs.tiny(7, 1, 1, wells="none")
+    lu = oracle.bilu0_natural(J)
+    r = np.random.default_rng(3).standard_normal(J.n)
+    z = oracle.bilu0_solve(J, np.zeros(J.nb, np.int32), 1, lu, r)
+    assert np.allclose(z, np.linalg.solve(J.to_dense(), r), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("wells", ["none", "corners"])
+def test_natural_levels(wells):
+    """Level sets of the natural-order sweeps equal the topological generations
+    (Kahn's layering, networkx) of the DAG with an edge j -> i for every
+    neighbour j < i in the symmetrised block pattern; without wells, on an
+    nx x ny x nz 7-point grid, level(x, y, z) = x + y + z."""
+    nx_, ny_, nz_ = 5, 4, 3
+    J = bs.tiny(nx_, ny_, nz_, wells=wells)
+    level, nlev = oracle.natural_levels(J)
+    D = nx.DiGraph()
+    D.add_nodes_from(range(J.nb))
+    for i in range(J.nb):
+        for p in range(J.rowptr[i], J.rowptr[i + 1]):
+            j = int(J.col[p])
+            if j != i:
+                D.add_edge(min(i, j), max(i, j))
+    gens = list(nx.topological_generations(D))
+    assert nlev == len(gens)
+    for g, nodes in enumerate(gens):
+        assert all(level[v] == g for v in nodes)
+    if wells == "none":
+        c = np.arange(J.nb)
+        assert np.array_equal(level, c % nx_ + (c // nx_) % ny_ + c // (nx_ * ny_))
+        assert nlev == nx_ + ny_ + nz_ - 2
+
+
 # ------------------------------------------------------ CPR, Eq. 3.1, FGMRES
 
 def test_cpr_apply_is_eq31_with_exact_pressure_solve(tiny):
