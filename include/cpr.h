@@ -82,6 +82,13 @@ typedef struct {
                            coarse level of at most 1024 rows) and the cycle is V(1,1);
                            0 (default, measured faster on B300): one kernel per phase.
                            Results are identical either way. */
+    int bilu_order;     /* second stage's BILU(0) order.  0 (default): multicolor, blocks in
+                           (JP color, index) order, one launch per color.  1: natural block
+                           order, as the paper's level-scheduled BILU (Sec. 6): the same
+                           factors as sequential block ILU(0) in index order, run one level
+                           set at a time (level = 1 + the largest level among a row's
+                           neighbours of lower index), so a sweep has as many launches as
+                           there are levels (nx + ny + nz - 2 on a 7-point grid). */
 } cpr_opts;
 
 typedef struct {

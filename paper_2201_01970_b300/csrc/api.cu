@@ -37,7 +37,8 @@ void check_opts(const cpr_opts &o) {
               o.post >= 0 && o.coarse_max >= 1 && o.coarse_max <= kMaxCoarse && o.max_levels >= 1 &&
               o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
               o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
-              (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1);
+              (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1) &&
+              (o.bilu_order == 0 || o.bilu_order == 1);
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -224,6 +225,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->stream = nullptr;
     o->pdl = 0;
     o->tail = 0;
+    o->bilu_order = 0;
 }
 
 const char *cpr_strerror(int code) {

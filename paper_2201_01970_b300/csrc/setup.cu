@@ -562,6 +562,55 @@ __global__ void k_state_to_color(int n, const unsigned long long *state, int *co
     if (i < n) color[i] = (int)(unsigned)state[i];
 }
 
+// One round of the level sets of natural-order block ILU(0) over a worklist
+// (round 0: all n rows, list_in == nullptr).  A row whose neighbours of lower
+// index in G (the symmetrised block graph) all have levels takes 1 + the
+// largest of them, or 0 with none; the others are appended to list_out.  A
+// level, once written, is final, so a row may read one written earlier in
+// this same round: rounds decide only when a row is reached, never its value.
+// Count slots cycle as in k_jp_round.
+__global__ void k_level_round(int n, const int *list_in, int *list_out, int *cnt, JpGraph g, int *level,
+                              unsigned r, int *maxlevel) {
+    int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
+    int *out_cnt = &cnt[(r + 1) % 3];
+    int lane = threadIdx.x & 31;
+    int lmax = -1;
+    for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
+        int t = t0 + threadIdx.x, i = 0;
+        bool wait = false;
+        if (t < m) {
+            i = list_in ? list_in[t] : t;
+            int lv = 0;
+            for (int pass = 0; pass < 2 && !wait; pass++) {
+                const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
+                for (int p = R[i]; p < R[i + 1]; p++) {
+                    int j = C[p];
+                    if (j >= i) continue;
+                    int lj = *(volatile const int *)&level[j];
+                    if (lj < 0) {
+                        wait = true;
+                        break;
+                    }
+                    lv = max(lv, lj + 1);
+                }
+            }
+            if (!wait) {
+                level[i] = lv;
+                lmax = max(lmax, lv);
+            }
+        }
+        unsigned b = __ballot_sync(0xffffffffu, wait);
+        if (b) {
+            int leader = __ffs(b) - 1, base = 0;
+            if (lane == leader) base = atomicAdd(out_cnt, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (wait) list_out[base + __popc(b & ((1u << lane) - 1u))] = i;
+        }
+    }
+    if (lmax >= 0) atomicMax(maxlevel, lmax);
+}
+
 // ---------------------------------------------------------------------- PMIS
 
 __global__ void k_pmis_init(int n, const int *sr, const int *tr, int *cf, int *undecided) {
@@ -1225,6 +1274,43 @@ __global__ void __launch_bounds__(kColorTile) k_color_tile_scatter(int n, int nc
     rows[pos[(size_t)c * ntiles + blockIdx.x] + before + in_warp] = i;
 }
 
+// The same counting sort for more than kSortColors colors (the level sets of
+// the natural-order BILU(0)): tiles of kColorTileMany rows, the per-tile and
+// per-warp counts in dynamic shared memory (ncolors and
+// (kColorTileMany / 32) * ncolors ints).
+constexpr int kColorTileMany = 256;
+constexpr int kSortColorsMany = 1024;
+
+__global__ void __launch_bounds__(kColorTileMany) k_color_tile_counts_many(int n, int ncolors, int ntiles,
+                                                                           const int *color, int *cnt) {
+    extern __shared__ int sh_many[];
+    for (int c = threadIdx.x; c < ncolors; c += blockDim.x) sh_many[c] = 0;
+    __syncthreads();
+    int i = blockIdx.x * kColorTileMany + threadIdx.x;
+    if (i < n && (unsigned)color[i] < (unsigned)ncolors) atomicAdd(&sh_many[color[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncolors; c += blockDim.x) cnt[(size_t)c * ntiles + blockIdx.x] = sh_many[c];
+}
+
+__global__ void __launch_bounds__(kColorTileMany) k_color_tile_scatter_many(int n, int ncolors, int ntiles,
+                                                                            const int *color, const int *pos,
+                                                                            int *rows) {
+    extern __shared__ int wc_many[];   // [warp][color]
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < (kColorTileMany / 32) * ncolors; k += blockDim.x) wc_many[k] = 0;
+    __syncthreads();
+    int i = blockIdx.x * kColorTileMany + threadIdx.x;
+    int c = i < n && (unsigned)color[i] < (unsigned)ncolors ? color[i] : -1;
+    unsigned same = __match_any_sync(0xffffffffu, c);
+    int in_warp = __popc(same & ((1u << lane) - 1u));
+    if (c >= 0 && in_warp == 0) wc_many[w * ncolors + c] = __popc(same);
+    __syncthreads();
+    if (c < 0) return;
+    int before = 0;
+    for (int v = 0; v < w; v++) before += wc_many[v * ncolors + c];
+    rows[pos[(size_t)c * ntiles + blockIdx.x] + before + in_warp] = i;
+}
+
 __global__ void k_iperm(int n, const int *order, int *iperm) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) iperm[order[t]] = t;
@@ -1471,11 +1557,13 @@ __device__ __forceinline__ bool mat3_inv_t(const float *a, float *inv) {
 // order: L_ik = A_ik U_kk^-1, then A_ij -= L_ik U_kj for j after k in row k
 // that lies in row i's pattern.  Same-color rows are never adjacent (the
 // block coloring is at theta = 0), so "after k" means "higher color than k".
-// FP64: every operation rounded as the plain definition orders it; FP32 (the
+// With natural set, the colors are the natural-order level sets and the k
+// before i are taken in index order alone: the operations, and their order,
+// of sequential block ILU(0) in index order.  FP64: every operation rounded as the plain definition orders it; FP32 (the
 // FP32-preconditioner mode, whose B only ever uses FP32 factors): FMA allowed.
 template <class T>
 __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr, const int *col,
-                                    const int *color, const int *diag, T *lu, int *err) {
+                                    const int *color, const int *diag, T *lu, int *err, int natural) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cnt) return;
     int i = rows[t];
@@ -1488,6 +1576,7 @@ __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr,
             int k = col[p];
             int ck = color[k];
             if (ck >= ci) continue;
+            if (natural) ck = 0;   // lower neighbours eliminated by index alone
             bool after_last = ck > last_c || (ck == last_c && k > last_k);
             bool before_best = ck < bc || (ck == bc && k < bk);
             if (after_last && before_best) {
@@ -1734,6 +1823,34 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
     return read_int(counters.p + 3, s) + 1;
 }
 
+// Level sets of natural-order block ILU(0) over G (k_level_round), with
+// batches of rounds between host checks; returns the number of levels.
+int level_sets(const SymGraph &G, DVec<int> &level, cudaStream_t s) {
+    constexpr int kLevelBatch = 16;
+    int n = G.n;
+    level.alloc(n, s);
+    CK(cudaMemsetAsync(level.p, 0xff, sizeof(int) * n, s));
+    DVec<int> counters, lists;
+    counters.alloc(4, s);
+    CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
+    lists.alloc(2 * (size_t)n, s);
+    int grid = grid_for(n, kBlock, 148 * 8);
+    unsigned r = 0;
+    for (;;) {
+        for (int k = 0; k < kLevelBatch; k++, r++) {
+            const int *in = r == 0 ? nullptr : lists.p + (size_t)(r % 2) * n;
+            int *out = lists.p + (size_t)((r + 1) % 2) * n;
+            k_level_round<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.dev(), level.p, r, counters.p + 3);
+            CK_LAUNCH();
+        }
+        if (read_int(counters.p + r % 3, s) == 0) break;
+        // every round settles at least the lowest unsettled row
+        if (r > (unsigned)n + kLevelBatch) fail(CPR_ERR_CUDA, "level sets did not terminate");
+    }
+    if (getenv("CPR_SETUP_TIMING")) fprintf(stderr, "[cpr setup] levels n=%d rounds<=%u\n", n, r);
+    return read_int(counters.p + 3, s) + 1;
+}
+
 // Rows grouped by color, index-ascending within a color.
 void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, DVec<int> &rows,
                    cudaStream_t s) {
@@ -1757,6 +1874,20 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
         CK_LAUNCH();
         exclusive_scan(cnt.p, pos.p, ncolors * ntiles, s);
         k_color_tile_scatter<<<ntiles, kColorTile, 0, s>>>(n, ncolors, ntiles, color, pos.p, rows.p);
+        CK_LAUNCH();
+        return;
+    }
+    if (ncolors <= kSortColorsMany) {
+        int ntiles = (n + kColorTileMany - 1) / kColorTileMany;
+        DVec<int> cnt;
+        cnt.alloc((size_t)ncolors * ntiles, s);
+        pos.alloc((size_t)ncolors * ntiles + 1, s);
+        k_color_tile_counts_many<<<ntiles, kColorTileMany, sizeof(int) * ncolors, s>>>(n, ncolors, ntiles, color,
+                                                                                      cnt.p);
+        CK_LAUNCH();
+        exclusive_scan(cnt.p, pos.p, ncolors * ntiles, s);
+        k_color_tile_scatter_many<<<ntiles, kColorTileMany, sizeof(int) * (kColorTileMany / 32) * ncolors, s>>>(
+            n, ncolors, ntiles, color, pos.p, rows.p);
         CK_LAUNCH();
         return;
     }
@@ -2173,7 +2304,8 @@ void build_preconditioner(cpr_handle *h) {
                                }),
                                (long)nnzb - nb, s);
         side.mark("bilu_graph");
-        B.ncolors = jp_color(h, G, 2, 0, B.color, s);
+        // multicolor (JP at theta = 0), or the natural order's level sets
+        B.ncolors = h->opt.bilu_order ? level_sets(G, B.color, s) : jp_color(h, G, 2, 0, B.color, s);
         side.mark("bilu_jp");
         rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
         B.iperm.alloc(nb, s);
@@ -2200,7 +2332,8 @@ void build_preconditioner(cpr_handle *h) {
                 if (!cnt) continue;
                 k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
                                                                          h->rowptr.p, h->col.p, B.color.p,
-                                                                         bdiag.p, lu, h->err.p);
+                                                                         bdiag.p, lu, h->err.p,
+                                                                         h->opt.bilu_order);
                 CK_LAUNCH();
             }
             // a singular pivot block is reported by the check at the end of the setup

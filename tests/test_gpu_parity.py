@@ -300,6 +300,57 @@ def test_full_size_fp32_mode_128x128x32(torch, cpr):
     assert its[1] <= its[0] + 4, its
 
 
+@pytest.mark.parametrize("case", list(CASES))
+def test_natural_order_bilu_matches_oracle(torch, cpr, case):
+    """bilu_order = 1, the paper's level-scheduled BILU (Sec. 6): the level
+    sets and the FP64 factors equal the oracle's natural-order block ILU(0) bit
+    for bit (the factor kernel takes each row's lower neighbours in index
+    order), B z and the BILU application match it, and a whole solve takes the
+    oracle's iteration count within one."""
+    J = CASES[case]()
+    kw = dict(coarse_max=16 if case == "tiny" else 256, bilu_order=1)
+    o = oracle.Solver(J, **kw)
+    g = cpr.Solver(DevJ(torch, J), **kw)
+    level, nlev = oracle.natural_levels(J)
+    gbc, gnc, glu = g.bilu()
+    assert gnc == nlev
+    np.testing.assert_array_equal(gbc, level)
+    np.testing.assert_array_equal(glu, oracle.bilu0_natural(J))
+    np.testing.assert_array_equal(glu, o.bilu()[2])
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(J.n)
+    z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
+    g.bilu_apply(dev(torch, v), z)
+    assert rel(z.cpu().numpy(), o.bilu_apply(v)) < APPLY_TOL
+    g.apply(dev(torch, v), z)
+    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    xo, so = o.solve(J.b, rtol=1e-6)
+    xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
+    assert sg["converged"] and so["converged"]
+    assert abs(sg["iters"] - so["iters"]) <= 1, (sg, so)
+    if sg["iters"] == so["iters"]:
+        assert rel(xg.cpu().numpy(), xo) < SOLVE_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_natural_order_bilu_full_size(torch, cpr, fp32):
+    """128x128x32 with the level-scheduled BILU, in both precisions: the
+    oracle's level sets (the grid's nx + ny + nz - 2 and the well rows, which
+    are numbered last) and convergence of the true FP64 residual."""
+    J = bs.jacobian("128x128x32")
+    g = cpr.Solver(DevJ(torch, J), precond_fp32=fp32, bilu_order=1)
+    gbc, gnc, _ = g.bilu()
+    level, nlev = oracle.natural_levels(J)
+    assert gnc == nlev
+    np.testing.assert_array_equal(gbc, level)
+    x, st = g.solve(dev(torch, J.b), rtol=1e-6)
+    assert st["converged"]
+    x = x.cpu().numpy()
+    assert np.linalg.norm(J.b - oracle.bsr3_spmv(J, x)) / np.linalg.norm(J.b) < 1e-6
+    g.close()
+
+
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_cluster_tail_changes_no_result(torch, cpr, fp32):
     """The cluster tail (the last smoothed levels and the coarse solve in one
