@@ -89,6 +89,10 @@ typedef struct {
                            set at a time (level = 1 + the largest level among a row's
                            neighbours of lower index), so a sweep has as many launches as
                            there are levels (nx + ny + nz - 2 on a 7-point grid). */
+    int reuse_refresh;  /* what a B kept by Alg. 3 applies.  0 (default): B as built, with the
+                           copy of A^(k-1) it was built from in its second residual (Alg. 1).
+                           1: the second residual takes the current A^(k); the decoupling,
+                           the AMG hierarchy and the BILU(0) factors stay those of A^(k-1). */
 } cpr_opts;
 
 typedef struct {

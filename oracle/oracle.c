@@ -949,6 +949,7 @@ void o_default_opts(o_opts *o) {
     o->max_levels = 20;
     o->seed = 0;
     o->bilu_order = 0;
+    o->reuse_refresh = 0;
 }
 
 static void free_setup(o_handle *h) {
@@ -1365,7 +1366,11 @@ int o_update(o_handle *h, int nb, const int *rowptr, const int *col, const doubl
     h->updates++;
     int reuse = same && h->updates > 1 && h->last_iters >= 0 && h->last_iters <= h->opt.mu;
     h->setup_called = !reuse;
-    if (reuse) return O_OK;
+    if (reuse) {
+        /* reuse_refresh: the second residual's copy of A becomes A^(k) */
+        if (h->opt.reuse_refresh) memcpy(h->pval, h->val, sizeof(double) * 9 * (size_t)h->nnzb);
+        return O_OK;
+    }
     rc = build_preconditioner(h);
     if (rc != O_OK) return rc;
     h->setup_count++;

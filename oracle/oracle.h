@@ -34,6 +34,8 @@ typedef struct {
     uint64_t seed;        /* hash seed of coloring and C/F splitting */
     int bilu_order;       /* 0: multicolor BILU(0) in (JP color, index) order (reading R6);
                              1: natural order, the level-scheduled BILU of Sec. 6 (0) */
+    int reuse_refresh;    /* 1: a B kept by Alg. 3 takes A^(k) for its second residual;
+                             0: it keeps the copy of A it was built from (0) */
 } o_opts;
 
 typedef struct {

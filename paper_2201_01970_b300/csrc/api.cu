@@ -38,7 +38,7 @@ void check_opts(const cpr_opts &o) {
               o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
               o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
               (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1) &&
-              (o.bilu_order == 0 || o.bilu_order == 1);
+              (o.bilu_order == 0 || o.bilu_order == 1) && (o.reuse_refresh == 0 || o.reuse_refresh == 1);
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -226,6 +226,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->pdl = 0;
     o->tail = 0;
     o->bilu_order = 0;
+    o->reuse_refresh = 0;
 }
 
 const char *cpr_strerror(int code) {
@@ -310,6 +311,7 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
         // Alg. 3: reuse B^(k-1) iff k > 1 and It^(k-1) <= mu (and Remark 4.2: same size/pattern)
         bool reuse = same && h->have_B && h->last_iters >= 0 && h->last_iters <= h->opt.mu;
         if (reuse) {
+            if (h->opt.reuse_refresh) refresh_second_residual(h);
             h->setup_called = 0;
             h->setup_ms = 0.0;
             return CPR_OK;

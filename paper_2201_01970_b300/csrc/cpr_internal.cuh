@@ -255,6 +255,7 @@ void destroy_step_graphs(cpr_handle *h);
 // setup.cu
 void build_preconditioner(cpr_handle *h);
 void free_preconditioner(cpr_handle *h);
+void refresh_second_residual(cpr_handle *h);   // reuse_refresh: the kept B's copy of A := the current A
 void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr, cudaStream_t s);
 
 // solve.cu

@@ -2068,6 +2068,24 @@ void free_preconditioner(cpr_handle *h) {
     h->have_B = false;
 }
 
+// A kept B takes the current A for its second residual (reuse_refresh): the
+// column-0 copy, and its FP32 shadow, are refilled in place.  Pattern and
+// positions are A's and B's, both unchanged, so the step graphs captured for
+// B stay valid.
+void refresh_second_residual(cpr_handle *h) {
+    cudaStream_t s = h->stream;
+    const Bilu &B = h->bilu;
+    int nb = h->nb;
+    k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                       h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
+    CK_LAUNCH();
+    size_t n = std::min(h->pcol0.n, h->pcol0_32.n);
+    if (h->pcol0_32.p && n) {
+        k_d2f<<<grid_for((long)n, kBlock, 148 * 16), kBlock, 0, s>>>((long)n, h->pcol0.p, h->pcol0_32.p);
+        CK_LAUNCH();
+    }
+}
+
 // Phase marks of a setup, printed to stderr when CPR_SETUP_TIMING is set
 // (diagnostics only).  A mark records a timing event on its clock's stream
 // and the host time; each prints as name=host/device, both in ms since the

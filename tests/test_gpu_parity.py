@@ -351,6 +351,49 @@ def test_natural_order_bilu_full_size(torch, cpr, fp32):
     g.close()
 
 
+def test_reuse_refresh_matches_oracle(torch, cpr):
+    """A B kept by Alg. 3 (mu large) applied to A^(k): with reuse_refresh = 0
+    its second residual keeps A^(k-1), with 1 it takes A^(k); B z and the next
+    solve match the oracle's either way, the two differ, and the FP32 mode's
+    B z moves the same way."""
+    J0, J1 = list(bs.jacobian_sequence(bs.CONFIGS["20x20x5"], 2, drift=0.05))
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(J0.n)
+    out = {}
+    for refresh in (0, 1):
+        kw = dict(mu=10 ** 6, reuse_refresh=refresh)
+        o = oracle.Solver(J0, **kw)
+        g = cpr.Solver(DevJ(torch, J0), **kw)
+        o.solve(J0.b, rtol=1e-6)
+        g.solve(dev(torch, J0.b), rtol=1e-6)
+        o.update(J1)
+        g.update(DevJ(torch, J1))
+        z = torch.zeros(J0.n, dtype=torch.float64, device="cuda")
+        g.apply(dev(torch, v), z)
+        zo = o.cpr_apply(v)
+        assert rel(z.cpu().numpy(), zo) < APPLY_TOL
+        xo, so = o.solve(J1.b, rtol=1e-6)
+        xg, sg = g.solve(dev(torch, J1.b), rtol=1e-6)
+        assert sg["setup_called"] == 0 and so["setup_called"] == 0
+        assert sg["converged"] and abs(sg["iters"] - so["iters"]) <= 1, (sg, so)
+        if sg["iters"] == so["iters"]:
+            assert rel(xg.cpu().numpy(), xo) < SOLVE_TOL
+        g.close()
+        g32 = cpr.Solver(DevJ(torch, J0), precond_fp32=1, **kw)
+        g32.solve(dev(torch, J0.b), rtol=1e-6)
+        g32.update(DevJ(torch, J1))
+        z32 = torch.zeros_like(z)
+        g32.apply(dev(torch, v), z32)
+        x32, s32 = g32.solve(dev(torch, J1.b), rtol=1e-6)
+        assert s32["setup_called"] == 0 and s32["converged"]
+        g32.close()
+        out[refresh] = (zo, z32.cpu().numpy())
+    assert rel(out[1][0], out[0][0]) > 1e-6
+    # the FP32 B moves with the FP64 one (its own rounding is ~1e-7)
+    d64, d32 = out[1][0] - out[0][0], out[1][1] - out[0][1]
+    assert rel(d32, d64) < 1e-2
+
+
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_cluster_tail_changes_no_result(torch, cpr, fp32):
     """The cluster tail (the last smoothed levels and the coarse solve in one

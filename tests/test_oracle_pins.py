@@ -492,6 +492,39 @@ def test_cpr_apply_is_eq31_with_exact_pressure_solve(tiny):
     s.close()
 
 
+@pytest.mark.parametrize("refresh", [0, 1])
+def test_kept_b_second_residual(refresh):
+    """Alg. 3 keeps B^(k-1) for A^(k).  Eq. 3.1 in dense form with B_P = A_P^-1,
+    W and M = L U all from A^(k-1): reuse_refresh = 0 keeps A^(k-1) in the
+    second residual, reuse_refresh = 1 takes A^(k) there."""
+    g = bs.GridSpec(4, 4, 2, 0.0, 1.0, 1.0, None, "corners", seed=4)
+    J0, J1 = list(bs.jacobian_sequence(g, 2, drift=0.05))
+    s = oracle.Solver(J0, coarse_max=10 ** 6, mu=10 ** 6, reuse_refresh=refresh)
+    A0 = J0.to_dense()
+    w = s.weights()
+    W = np.zeros((J0.n, J0.nb))
+    Pi = np.zeros((J0.n, J0.nb))
+    for i in range(J0.nb):
+        W[3 * i:3 * i + 3, i] = w[3 * i:3 * i + 3]
+        Pi[3 * i, i] = 1.0
+    bc, nbc, lu = s.bilu()
+    L, U = _bilu_dense_factors(J0, bc, nbc, lu)
+    Minv = np.linalg.inv(L @ U)
+    C1 = Pi @ np.linalg.inv(W.T @ A0 @ Pi) @ W.T
+    _, st = s.solve(J0.b)
+    s.update(J1)
+    _, st = s.solve(J1.b)
+    assert st["setup_called"] == 0 and st["converged"]
+    Ares = J1.to_dense() if refresh else A0
+    B = C1 + Minv @ (np.eye(J0.n) - Ares @ C1)
+    Bo = np.column_stack([s.cpr_apply(e) for e in np.eye(J0.n)])
+    assert np.allclose(Bo, B, rtol=1e-9, atol=1e-9 * np.abs(B).max())
+    # the two readings differ: the drift reaches the second residual
+    Bother = C1 + Minv @ (np.eye(J0.n) - (A0 if refresh else J1.to_dense()) @ C1)
+    assert not np.allclose(Bo, Bother, rtol=1e-6, atol=1e-6 * np.abs(B).max())
+    s.close()
+
+
 def test_vcycle_two_level_composition(tiny):
     """V(1,0) with an exact coarse solve: x = S b + P A_c^-1 R (b - A S b)."""
     J = tiny
