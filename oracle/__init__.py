@@ -41,7 +41,7 @@ class Opts(C.Structure):
                 ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
-                ("bilu_order", C.c_int), ("reuse_refresh", C.c_int)]
+                ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int)]
 
 
 class Stats(C.Structure):

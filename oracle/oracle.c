@@ -51,6 +51,7 @@ typedef struct {
     int *cf;       /* 1 = C point, 0 = F point */
     int nc;        /* number of C points = size of level l+1 */
     o_csr P, R;    /* interpolation (n_l x n_{l+1}) and R = P^T */
+    o_csr S;       /* classical strength set the interpolation used (kept for resetup = 1) */
     double *x, *b, *r, *tmp; /* V-cycle work vectors */
 } level_t;
 
@@ -950,6 +951,7 @@ void o_default_opts(o_opts *o) {
     o->seed = 0;
     o->bilu_order = 0;
     o->reuse_refresh = 0;
+    o->resetup = 0;
 }
 
 static void free_setup(o_handle *h) {
@@ -958,6 +960,7 @@ static void free_setup(o_handle *h) {
         csr_release(&L->A);
         csr_release(&L->P);
         csr_release(&L->R);
+        csr_release(&L->S);
         free(L->color);
         free(L->cf);
         free(L->x);
@@ -993,7 +996,36 @@ static int check_diag(const o_csr *A) {
 }
 
 /* Build B from the current A (Alg. 1's preconditioner, Sec. 3.1, Alg. 6). */
-static int build_preconditioner(o_handle *h) {
+/*
+ * Build B from the handle's A.  numeric = 0: the full setup.  numeric = 1 (the
+ * numeric-only resetup of resetup = 1): the discrete structure of the last
+ * setup is kept -- the number of levels, each level's classical strength set,
+ * C/F split and smoother coloring, and the BILU(0) block coloring -- and
+ * every value is recomputed from A: decoupling weights and A_P, direct
+ * interpolation over the kept strength sets and C/F splits, R = P^T, the
+ * Galerkin products, the coarsest LU and the BILU(0) factors.  With the same
+ * pattern the products have the same patterns, so the structure fits.
+ */
+static int build_preconditioner(o_handle *h, int numeric) {
+    int knlev = h->nlev, knbc = h->nbcolors;
+    o_csr kS[MAXLEV];
+    int *kcf[MAXLEV], knc[MAXLEV], *kcolor[MAXLEV], kncol[MAXLEV];
+    int *kbcolor = NULL;
+    if (numeric) {
+        for (int l = 0; l < knlev; l++) {
+            level_t *L = &h->lev[l];
+            kS[l] = L->S;
+            kcf[l] = L->cf;
+            knc[l] = L->nc;
+            kcolor[l] = L->color;
+            kncol[l] = L->ncolors;
+            memset(&L->S, 0, sizeof(L->S));
+            L->cf = NULL;
+            L->color = NULL;
+        }
+        kbcolor = h->bcolor;
+        h->bcolor = NULL;
+    }
     free_setup(h);
     const o_opts *o = &h->opt;
     int nb = h->nb, nnzb = h->nnzb;
@@ -1021,32 +1053,53 @@ static int build_preconditioner(o_handle *h) {
         L->b = xcalloc((size_t)n, sizeof(double));
         L->r = xcalloc((size_t)n, sizeof(double));
         L->tmp = xcalloc((size_t)n, sizeof(double));
-        if (n <= o->coarse_max || l + 1 >= o->max_levels || l + 1 >= MAXLEV) break;
-        o_csr S = strength_rs(&L->A, o->theta_amg);
-        L->cf = xcalloc((size_t)n, sizeof(int));
-        int nc = pmis(&S, o->seed, 1, l, L->cf);
-        if (nc == 0 || (double)nc > 0.95 * (double)n) {
-            csr_release(&S);
-            free(L->cf);
-            L->cf = NULL;
-            break;
+        int nc;
+        if (numeric) {
+            if (l == knlev - 1) break;   /* the kept coarsest level */
+            L->S = kS[l];
+            L->cf = kcf[l];
+            nc = knc[l];
+            kS[l].rowptr = NULL;
+            kcf[l] = NULL;
+        } else {
+            if (n <= o->coarse_max || l + 1 >= o->max_levels || l + 1 >= MAXLEV) break;
+            L->S = strength_rs(&L->A, o->theta_amg);
+            L->cf = xcalloc((size_t)n, sizeof(int));
+            nc = pmis(&L->S, o->seed, 1, l, L->cf);
+            if (nc == 0 || (double)nc > 0.95 * (double)n) {
+                csr_release(&L->S);
+                free(L->cf);
+                L->cf = NULL;
+                break;
+            }
         }
         L->nc = nc;
-        L->P = interp_direct(&L->A, &S, L->cf);
-        csr_release(&S);
+        L->P = interp_direct(&L->A, &L->S, L->cf);
         L->R = transpose(&L->P);
         o_csr AP = spgemm(&L->A, &L->P);
         h->lev[l + 1].A = spgemm(&L->R, &AP);
         csr_release(&AP);
-        /* the smoother's coloring (Eq. 5.1, Alg. 4-6 intent, reading R3) */
-        o_csr Sc = strength_color(&L->A, o->theta_color);
-        o_csr G = sym_union(&Sc);
-        L->color = xcalloc((size_t)n, sizeof(int));
-        L->ncolors = jp_color(&G, o->seed, 0, l, L->color);
-        csr_release(&Sc);
-        csr_release(&G);
+        if (numeric) {
+            L->color = kcolor[l];
+            L->ncolors = kncol[l];
+            kcolor[l] = NULL;
+        } else {
+            /* the smoother's coloring (Eq. 5.1, Alg. 4-6 intent, reading R3) */
+            o_csr Sc = strength_color(&L->A, o->theta_color);
+            o_csr G = sym_union(&Sc);
+            L->color = xcalloc((size_t)n, sizeof(int));
+            L->ncolors = jp_color(&G, o->seed, 0, l, L->color);
+            csr_release(&Sc);
+            csr_release(&G);
+        }
         l++;
     }
+    if (numeric)
+        for (int k = 0; k < knlev; k++) {   /* the kept structure not taken over (the coarsest level's) */
+            if (kS[k].rowptr) csr_release(&kS[k]);
+            free(kcf[k]);
+            free(kcolor[k]);
+        }
     /* coarsest level: dense LU */
     level_t *C = &h->lev[h->nlev - 1];
     int n = C->A.n;
@@ -1058,9 +1111,14 @@ static int build_preconditioner(o_handle *h) {
     rc = dense_lu(n, h->clu, h->cpiv);
     if (rc != O_OK) return rc;
     /* second stage */
-    h->bcolor = xcalloc((size_t)nb, sizeof(int));
-    /* natural order: one color, so the (color, index) order is the index order */
-    h->nbcolors = o->bilu_order ? 1 : bilu_coloring(nb, h->rowptr, h->col, o->seed, h->bcolor);
+    if (numeric) {
+        h->bcolor = kbcolor;
+        h->nbcolors = knbc;
+    } else {
+        h->bcolor = xcalloc((size_t)nb, sizeof(int));
+        /* natural order: one color, so the (color, index) order is the index order */
+        h->nbcolors = o->bilu_order ? 1 : bilu_coloring(nb, h->rowptr, h->col, o->seed, h->bcolor);
+    }
     h->lu = xcalloc(9 * (size_t)nnzb, sizeof(double));
     rc = bilu0_factor(nb, h->rowptr, h->col, h->pval, h->bcolor, h->nbcolors, h->lu);
     return rc;
@@ -1333,7 +1391,7 @@ int o_setup(o_handle **out, int nb, const int *rowptr, const int *col, const dou
     if (opt) h->opt = *opt;
     else o_default_opts(&h->opt);
     int rc = load_matrix(h, nb, rowptr, col, val);
-    if (rc == O_OK) rc = build_preconditioner(h);
+    if (rc == O_OK) rc = build_preconditioner(h, 0);
     if (rc != O_OK) {
         o_destroy(h);
         *out = NULL;
@@ -1371,7 +1429,8 @@ int o_update(o_handle *h, int nb, const int *rowptr, const int *col, const doubl
         if (h->opt.reuse_refresh) memcpy(h->pval, h->val, sizeof(double) * 9 * (size_t)h->nnzb);
         return O_OK;
     }
-    rc = build_preconditioner(h);
+    /* resetup = 1: with the pattern unchanged, only the values are rebuilt */
+    rc = build_preconditioner(h, h->opt.resetup && same && h->nlev > 0);
     if (rc != O_OK) return rc;
     h->setup_count++;
     h->last_iters = -1;

@@ -36,6 +36,9 @@ typedef struct {
                              1: natural order, the level-scheduled BILU of Sec. 6 (0) */
     int reuse_refresh;    /* 1: a B kept by Alg. 3 takes A^(k) for its second residual;
                              0: it keeps the copy of A it was built from (0) */
+    int resetup;          /* when Alg. 3 rebuilds B and the pattern is unchanged: 0 full setup;
+                             1 numeric only, keeping the last setup's levels, strength sets,
+                             C/F splits and colorings (0) */
 } o_opts;
 
 typedef struct {

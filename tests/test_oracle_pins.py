@@ -525,6 +525,72 @@ def test_kept_b_second_residual(refresh):
     s.close()
 
 
+def _level_dense(lv, which):
+    M = lv[which]
+    return csr_dense(M.rowptr, M.col, M.val, M.n, M.ncol)
+
+
+def test_numeric_resetup():
+    """resetup = 1: when Alg. 3 rebuilds B for a Jacobian of the
+    same pattern, the levels, C/F splits, interpolation patterns and colorings
+    of the last setup are kept and every value is recomputed.  Pins: A_P =
+    W^T A^(k) Pi with W_i solving D_i^T w_i = e_1 on A^(k)'s blocks; every
+    A_{l+1} = R A_l P (dense); C rows of P are unit rows; and a numeric
+    resetup with unchanged values equals the full setup bit for bit."""
+    g = bs.GridSpec(6, 6, 4, 0.0, 1.0, 1.0, None, "corners", seed=6)
+    J0, J1 = list(bs.jacobian_sequence(g, 2, drift=0.05))
+    kw = dict(coarse_max=20, mu=0)
+    full0 = oracle.Solver(J0, **kw)
+    assert full0.nlev >= 3
+    s = oracle.Solver(J0, resetup=1, **kw)
+    s.solve(J0.b)
+    s.update(J1)
+    _, st = s.solve(J1.b)
+    assert st["setup_called"] == 1 and st["converged"]
+    assert s.nlev == full0.nlev
+    # level 0: the decoupling of A^(k)
+    blocks = J1.val.reshape(-1, 3, 3)
+    w = s.weights()
+    W = np.zeros((J1.n, J1.nb))
+    Pi = np.zeros((J1.n, J1.nb))
+    for i in range(J1.nb):
+        p = J1.rowptr[i] + list(J1.col[J1.rowptr[i]:J1.rowptr[i + 1]]).index(i)
+        assert np.allclose(blocks[p].T @ w[3 * i:3 * i + 3], [1, 0, 0], atol=1e-12)
+        W[3 * i:3 * i + 3, i] = w[3 * i:3 * i + 3]
+        Pi[3 * i, i] = 1.0
+    AP = W.T @ J1.to_dense() @ Pi
+    l0 = s.level(0)
+    assert np.allclose(_level_dense(l0, "A"), AP, rtol=1e-12, atol=1e-12 * np.abs(AP).max())
+    for l in range(s.nlev - 1):
+        a, k = s.level(l), full0.level(l)
+        # the kept structure
+        np.testing.assert_array_equal(a["cf"], k["cf"])
+        np.testing.assert_array_equal(a["color"], k["color"])
+        np.testing.assert_array_equal(a["P"].rowptr, k["P"].rowptr)
+        np.testing.assert_array_equal(a["P"].col, k["P"].col)
+        P = _level_dense(a, "P")
+        for i in np.flatnonzero(a["cf"] == 1):
+            assert np.count_nonzero(P[i]) == 1 and P[i].max() == 1.0
+        # new values, Galerkin-consistent
+        assert not np.array_equal(a["P"].val, k["P"].val)
+        Ac = P.T @ _level_dense(a, "A") @ P
+        An = _level_dense(s.level(l + 1), "A")
+        assert np.allclose(An, Ac, rtol=1e-11, atol=1e-11 * np.abs(Ac).max())
+    # unchanged values: the numeric resetup is the full setup
+    t = oracle.Solver(J0, resetup=1, **kw)
+    t.solve(J0.b)
+    t.update(J0)
+    for l in range(full0.nlev):
+        a, k = t.level(l), full0.level(l)
+        for key in ("rowptr", "col", "val"):
+            np.testing.assert_array_equal(getattr(a["A"], key), getattr(k["A"], key))
+        if l < full0.nlev - 1:
+            np.testing.assert_array_equal(a["P"].val, k["P"].val)
+    np.testing.assert_array_equal(t.bilu()[2], full0.bilu()[2])
+    for o in (full0, s, t):
+        o.close()
+
+
 def test_vcycle_two_level_composition(tiny):
     """V(1,0) with an exact coarse solve: x = S b + P A_c^-1 R (b - A S b)."""
     J = tiny
