@@ -278,14 +278,13 @@ def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_reg
             "launches": launches, "profiled_ms_per_step": prof_ms, "profiled_steps": P, "parts": parts}
 
 
-def bilu_natural_arm(cpr, torch, seq_dev, rhs_dev, K, W, stream):
-    """The same update+solve steps with the paper's level-scheduled second
-    stage (bilu_order = 1: natural-order BILU(0), one launch per level set)
-    instead of the multicolor one, in both precisions."""
+def option_arm(cpr, torch, seq_dev, rhs_dev, K, W, stream, note, **opts):
+    """The headline's update+solve steps with extra solver options, in both
+    precisions."""
     S = len(seq_dev)
     out = {}
     for name, fp32 in (("fp32", 1), ("fp64", 0)):
-        solver = cpr.Solver(seq_dev[0], precond_fp32=fp32, mu=MU, bilu_order=1, stream=stream.cuda_stream)
+        solver = cpr.Solver(seq_dev[0], precond_fp32=fp32, mu=MU, stream=stream.cuda_stream, **opts)
         x = torch.zeros_like(rhs_dev[0])
         stats = []
 
@@ -316,9 +315,8 @@ def bilu_natural_arm(cpr, torch, seq_dev, rhs_dev, K, W, stream):
                      "setup_ms_mean": statistics.mean([st["setup_ms"] for st in stats if st["setup_called"]]
                                                       or [0.0]),
                      "solve_phase_ms_mean": statistics.mean(st["solve_ms"] for st in stats),
-                     "level_sets": nlev}
-    out["note"] = (f"{K} timed steps after {W} warm-up, same sequence and rule as the headline; "
-                   "the second stage swept one level set per launch")
+                     "setups": sum(st["setup_called"] for st in stats), "bilu_colors": nlev}
+    out["note"] = f"{K} timed steps after {W} warm-up, same sequence and rule as the headline; {note}"
     return out
 
 
@@ -573,6 +571,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bilu-natural", action="store_true",
                     help="skip the level-scheduled (natural-order) BILU(0) line")
+    ap.add_argument("--no-resetup-numeric", action="store_true",
+                    help="skip the numeric-only resetup line")
     ap.add_argument("--serve-full", action="store_true",
                     help="serving ensemble over the full 32x32x8..128x128x32 range")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
@@ -641,8 +641,13 @@ def main():
     e2e = None if args.no_e2e else e2e_arm(cpr, torch, seq_host, max(3, K // 2), 1, stream)
     batched = None if args.no_batch else batched_arm(cpr, torch, max(3, K // 2), stream)
     serving = None if args.no_serve else serve_arm(args.serve_full)
-    natural = None if args.no_bilu_natural else bilu_natural_arm(cpr, torch, seq_dev, rhs_dev, max(3, K // 3), W,
-                                                                   stream)
+    natural = None if args.no_bilu_natural else option_arm(
+        cpr, torch, seq_dev, rhs_dev, max(3, K // 3), W, stream,
+        "bilu_order = 1: the paper's level-scheduled second stage, one launch per level set", bilu_order=1)
+    numeric = None if args.no_resetup_numeric else option_arm(
+        cpr, torch, seq_dev, rhs_dev, K, W, stream,
+        "resetup = 1: each rebuild keeps the first setup's levels, strength sets, C/F splits and colorings "
+        "and recomputes the values", resetup=1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(seq_host)
@@ -762,6 +767,8 @@ def main():
         line["serving"] = serving
     if natural is not None:
         line["bilu_natural"] = natural
+    if numeric is not None:
+        line["resetup_numeric"] = numeric
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -93,6 +93,12 @@ typedef struct {
                            copy of A^(k-1) it was built from in its second residual (Alg. 1).
                            1: the second residual takes the current A^(k); the decoupling,
                            the AMG hierarchy and the BILU(0) factors stay those of A^(k-1). */
+    int resetup;        /* what Alg. 3's rebuild of B does when the pattern is unchanged.
+                           0 (default): the full setup.  1: numeric only -- the last setup's
+                           number of levels, classical strength sets, C/F splits, smoother
+                           colorings and BILU(0) ordering are kept, and every value (weights,
+                           A_P, interpolation, Galerkin products, coarse LU, BILU(0) factors)
+                           is recomputed from A^(k).  Not in the paper. */
 } cpr_opts;
 
 typedef struct {

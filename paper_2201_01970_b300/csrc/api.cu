@@ -38,7 +38,8 @@ void check_opts(const cpr_opts &o) {
               o.theta_color >= 0.0 && o.theta_color <= 1.0 && o.theta_amg >= 0.0 && o.theta_amg <= 1.0 &&
               o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
               (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1) &&
-              (o.bilu_order == 0 || o.bilu_order == 1) && (o.reuse_refresh == 0 || o.reuse_refresh == 1);
+              (o.bilu_order == 0 || o.bilu_order == 1) && (o.reuse_refresh == 0 || o.reuse_refresh == 1) &&
+              (o.resetup == 0 || o.resetup == 1);
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -77,9 +78,9 @@ __global__ void k_has_nonfinite(long n, const double *a, int *flag) {
         if (!isfinite(a[i])) atomicExch(flag, 1);
 }
 
-void build_timed(cpr_handle *h) {
+void build_timed(cpr_handle *h, bool numeric = false) {
     double t0 = now_ms();
-    build_preconditioner(h);
+    build_preconditioner(h, numeric);
     h->setup_ms = now_ms() - t0;
     h->setup_count++;
     h->setup_called = 1;
@@ -227,6 +228,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->tail = 0;
     o->bilu_order = 0;
     o->reuse_refresh = 0;
+    o->resetup = 0;
 }
 
 const char *cpr_strerror(int code) {
@@ -316,7 +318,8 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
             h->setup_ms = 0.0;
             return CPR_OK;
         }
-        build_timed(h);
+        // resetup = 1: same pattern, so only the values are rebuilt
+        build_timed(h, h->opt.resetup && same && h->have_B);
         return CPR_OK;
     });
 }

@@ -105,6 +105,8 @@ struct Level {
     DCsr A, P, R;
     DVec<int> color, cf;
     int ncolors = 0, nc = 0;
+    DVec<int> Srow, Scol;         // classical strength set the interpolation used (kept for resetup = 1)
+    int Snnz = 0;
     std::vector<int> color_off;
     DVec<int> rows_by_color;      // order: internal row t is natural row rows_by_color[t]
     DVec<int> iperm;              // natural row i is internal row iperm[i]
@@ -253,7 +255,9 @@ void prof_collect_graph(cpr_handle *h, int which);
 void destroy_step_graphs(cpr_handle *h);
 
 // setup.cu
-void build_preconditioner(cpr_handle *h);
+// numeric: keep the last setup's discrete structure (levels, strength sets,
+// C/F splits, colorings, BILU(0) ordering) and recompute every value from A.
+void build_preconditioner(cpr_handle *h, bool numeric = false);
 void free_preconditioner(cpr_handle *h);
 void refresh_second_residual(cpr_handle *h);   // reuse_refresh: the kept B's copy of A := the current A
 void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr, cudaStream_t s);
