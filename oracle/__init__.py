@@ -41,7 +41,8 @@ class Opts(C.Structure):
                 ("restart", C.c_int), ("max_restarts", C.c_int), ("precond_fp32", C.c_int),
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
-                ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int)]
+                ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int),
+                ("amg", C.c_int), ("amli_iters", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -90,6 +91,7 @@ def lib():
         L.o_bilu0_solve.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _f64p, _f64p]
         L.o_bilu0_natural.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p]
         L.o_natural_levels.argtypes = [C.c_int, _i32p, _i32p, _i32p]
+        L.o_aggregate.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_int, _i32p]
         L.o_fgmres_identity.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
                                         C.c_int, C.c_int, C.POINTER(Stats), vp]
         L.o_default_opts.argtypes = [C.POINTER(Opts)]
@@ -264,6 +266,14 @@ def natural_levels(J):
     level = np.zeros(J.nb, np.int32)
     nlev = lib().o_natural_levels(J.nb, _i32(J.rowptr), _i32(J.col), level)
     return level, nlev
+
+
+def aggregate(n, rowptr, col, val, beta=0.25, passes=2):
+    """Pairwise aggregation of a scalar CSR matrix: (aggregate per node, number
+    of aggregates); passes = 1 for one matching pass, 2 for the double pass."""
+    agg = np.zeros(n, np.int32)
+    na = lib().o_aggregate(n, _i32(rowptr), _i32(col), _f64(val), beta, passes, agg)
+    return agg, na
 
 
 def bilu0_solve(J, bcolor, nbcolors, lu, r):

@@ -53,6 +53,7 @@ typedef struct {
     o_csr P, R;    /* interpolation (n_l x n_{l+1}) and R = P^T */
     o_csr S;       /* classical strength set the interpolation used (kept for resetup = 1) */
     double *x, *b, *r, *tmp; /* V-cycle work vectors */
+    double *gv, *gw, *gres;  /* amg = 1: the GCR vectors of a coarse correction on this level */
 } level_t;
 
 struct o_handle {
@@ -741,6 +742,198 @@ void o_mcgs_sweep(int n, const int *rowptr, const int *col, const double *val, c
     free(tmp);
 }
 
+/* --------------------------------------- UA-AMG: pairwise aggregation (f2) */
+
+/* A binary min-heap of (key, node) pairs with lazy deletion. */
+typedef struct {
+    long *key;
+    int *node;
+    int size, cap;
+} heap_t;
+
+static void heap_push(heap_t *q, long key, int node) {
+    if (q->size == q->cap) {
+        q->cap = q->cap ? 2 * q->cap : 64;
+        q->key = realloc(q->key, sizeof(long) * (size_t)q->cap);
+        q->node = realloc(q->node, sizeof(int) * (size_t)q->cap);
+        if (!q->key || !q->node) abort();
+    }
+    int c = q->size++;
+    while (c > 0) {
+        int p = (c - 1) / 2;
+        if (q->key[p] < key || (q->key[p] == key && q->node[p] < node)) break;
+        q->key[c] = q->key[p];
+        q->node[c] = q->node[p];
+        c = p;
+    }
+    q->key[c] = key;
+    q->node[c] = node;
+}
+
+static void heap_pop(heap_t *q, long *key, int *node) {
+    *key = q->key[0];
+    *node = q->node[0];
+    long k = q->key[--q->size];
+    int v = q->node[q->size];
+    int c = 0;
+    for (;;) {
+        int l = 2 * c + 1, r = l + 1, m = c;
+        long mk = k;
+        int mv = v;
+        if (l < q->size && (q->key[l] < mk || (q->key[l] == mk && q->node[l] < mv))) {
+            m = l;
+            mk = q->key[l];
+            mv = q->node[l];
+        }
+        if (r < q->size && (q->key[r] < mk || (q->key[r] == mk && q->node[r] < mv))) m = r;
+        if (m == c) break;
+        q->key[c] = q->key[m];
+        q->node[c] = q->node[m];
+        c = m;
+    }
+    if (q->size) {
+        q->key[c] = k;
+        q->node[c] = v;
+    }
+}
+
+/*
+ * One pass of pairwise matching (reading R15: the pairwise aggregation Sec. 6
+ * names as NPAIR, taken on the symmetrised couplings c_ij = (a_ij + a_ji) / 2
+ * so that a nonsymmetric A is matched as its symmetric part).
+ *  - j != i is a strong neighbour of i when c_ij < 0 and
+ *    -c_ij >= beta * max_{k != i} (-c_ik).
+ *  - m_i = the number of unmatched nodes that have i as a strong neighbour.
+ *  - The unmatched node i of smallest (m_i, i) is matched with its unmatched
+ *    strong neighbour j of smallest (c_ij, j), or stays alone if it has none.
+ *    Both leave the pool, and each of their strong neighbours' m drops by one.
+ * agg[i] = aggregate index, numbered in the order the aggregates form.
+ * Returns the number of aggregates.
+ */
+static int pairwise_pass(const o_csr *A, double beta, int *agg) {
+    int n = A->n;
+    o_csr T = transpose(A);
+    /* S with its couplings: row i holds the strong neighbours of i */
+    int *srow = xcalloc((size_t)n + 1, sizeof(int));
+    int cap = A->nnz + T.nnz + 1;
+    int *scol = xcalloc((size_t)cap, sizeof(int));
+    double *sval = xcalloc((size_t)cap, sizeof(double));
+    int *ccol = xcalloc((size_t)n + 1, sizeof(int));
+    double *cval = xcalloc((size_t)n + 1, sizeof(double));
+    int nnz = 0;
+    for (int i = 0; i < n; i++) {
+        /* merge row i of A and of A^T: the couplings of i, off the diagonal */
+        int p = A->rowptr[i], pe = A->rowptr[i + 1], q = T.rowptr[i], qe = T.rowptr[i + 1], nc = 0;
+        double maxneg = 0.0;
+        while (p < pe || q < qe) {
+            int a = p < pe ? A->col[p] : n, b = q < qe ? T.col[q] : n;
+            int j = a < b ? a : b;
+            double c = 0.0;
+            if (a == j) c += A->val[p++];
+            if (b == j) c += T.val[q++];
+            if (j == i) continue;
+            c = 0.5 * c;
+            ccol[nc] = j;
+            cval[nc++] = c;
+            if (-c > maxneg) maxneg = -c;
+        }
+        for (int t = 0; t < nc; t++)
+            if (cval[t] < 0.0 && maxneg > 0.0 && -cval[t] >= beta * maxneg) {
+                scol[nnz] = ccol[t];
+                sval[nnz++] = cval[t];
+            }
+        srow[i + 1] = nnz;
+    }
+    int *m = xcalloc((size_t)n, sizeof(int));
+    for (int k = 0; k < nnz; k++) m[scol[k]]++;
+    char *done = xcalloc((size_t)n, 1);
+    heap_t h = {0};
+    for (int i = 0; i < n; i++) heap_push(&h, m[i], i);
+    int na = 0;
+    while (h.size) {
+        long key;
+        int i;
+        heap_pop(&h, &key, &i);
+        if (done[i] || key != m[i]) continue;   /* a stale entry */
+        int j = -1;
+        double cj = 0.0;
+        for (int t = srow[i]; t < srow[i + 1]; t++) {
+            int k = scol[t];
+            if (done[k]) continue;
+            if (j < 0 || sval[t] < cj || (sval[t] == cj && k < j)) {
+                j = k;
+                cj = sval[t];
+            }
+        }
+        int pair[2] = {i, j};
+        for (int u = 0; u < 2 && pair[u] >= 0; u++) {
+            int v = pair[u];
+            done[v] = 1;
+            agg[v] = na;
+            for (int t = srow[v]; t < srow[v + 1]; t++) {
+                int k = scol[t];
+                if (done[k]) continue;
+                m[k]--;
+                heap_push(&h, m[k], k);
+            }
+        }
+        na++;
+    }
+    free(h.key);
+    free(h.node);
+    free(done);
+    free(m);
+    free(ccol);
+    free(cval);
+    free(srow);
+    free(scol);
+    free(sval);
+    csr_release(&T);
+    return na;
+}
+
+/* Unsmoothed aggregation's P (n x nc): row i is the unit row of aggregate agg[i]. */
+static o_csr agg_to_p(int n, int nc, const int *agg) {
+    o_csr P = csr_alloc(n, nc, n, 1);
+    for (int i = 0; i < n; i++) {
+        P.col[i] = agg[i];
+        P.val[i] = 1.0;
+        P.rowptr[i + 1] = i + 1;
+    }
+    return P;
+}
+
+/*
+ * Double pairwise aggregation: a pass on A, then a pass on the pair
+ * operator P1^T A P1, so aggregates hold at most four nodes.  agg[i] = the
+ * final aggregate of node i; returns their number.
+ */
+static int aggregate_double(const o_csr *A, double beta, int *agg) {
+    int n = A->n;
+    int *a1 = xcalloc((size_t)n, sizeof(int));
+    int n1 = pairwise_pass(A, beta, a1);
+    o_csr P1 = agg_to_p(n, n1, a1);
+    o_csr R1 = transpose(&P1);
+    o_csr AP = spgemm(A, &P1);
+    o_csr A1 = spgemm(&R1, &AP);
+    int *a2 = xcalloc((size_t)n1, sizeof(int));
+    int n2 = pairwise_pass(&A1, beta, a2);
+    for (int i = 0; i < n; i++) agg[i] = a2[a1[i]];
+    free(a1);
+    free(a2);
+    csr_release(&P1);
+    csr_release(&R1);
+    csr_release(&AP);
+    csr_release(&A1);
+    return n2;
+}
+
+int o_aggregate(int n, const int *rowptr, const int *col, const double *val, double beta, int passes,
+                int *agg) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    return passes == 1 ? pairwise_pass(&A, beta, agg) : aggregate_double(&A, beta, agg);
+}
+
 /* ----------------------------------------------------------------- BILU(0) */
 
 /* Positions of rows in (color, index) order; order[t] = row at position t. */
@@ -952,6 +1145,8 @@ void o_default_opts(o_opts *o) {
     o->bilu_order = 0;
     o->reuse_refresh = 0;
     o->resetup = 0;
+    o->amg = 0;
+    o->amli_iters = 2;
 }
 
 static void free_setup(o_handle *h) {
@@ -967,6 +1162,9 @@ static void free_setup(o_handle *h) {
         free(L->b);
         free(L->r);
         free(L->tmp);
+        free(L->gv);
+        free(L->gw);
+        free(L->gres);
         memset(L, 0, sizeof(*L));
     }
     h->nlev = 0;
@@ -1063,9 +1261,14 @@ static int build_preconditioner(o_handle *h, int numeric) {
             kcf[l] = NULL;
         } else {
             if (n <= o->coarse_max || l + 1 >= o->max_levels || l + 1 >= MAXLEV) break;
-            L->S = strength_rs(&L->A, o->theta_amg);
             L->cf = xcalloc((size_t)n, sizeof(int));
-            nc = pmis(&L->S, o->seed, 1, l, L->cf);
+            if (o->amg == 1) {
+                /* UA-AMG: cf holds each node's aggregate */
+                nc = aggregate_double(&L->A, o->theta_amg, L->cf);
+            } else {
+                L->S = strength_rs(&L->A, o->theta_amg);
+                nc = pmis(&L->S, o->seed, 1, l, L->cf);
+            }
             if (nc == 0 || (double)nc > 0.95 * (double)n) {
                 csr_release(&L->S);
                 free(L->cf);
@@ -1074,7 +1277,8 @@ static int build_preconditioner(o_handle *h, int numeric) {
             }
         }
         L->nc = nc;
-        L->P = interp_direct(&L->A, &L->S, L->cf);
+        if (o->amg == 1) L->P = agg_to_p(n, nc, L->cf);
+        else L->P = interp_direct(&L->A, &L->S, L->cf);
         L->R = transpose(&L->P);
         o_csr AP = spgemm(&L->A, &L->P);
         h->lev[l + 1].A = spgemm(&L->R, &AP);
@@ -1099,6 +1303,14 @@ static int build_preconditioner(o_handle *h, int numeric) {
             if (kS[k].rowptr) csr_release(&kS[k]);
             free(kcf[k]);
             free(kcolor[k]);
+        }
+    /* amg = 1: the coarse corrections onto levels 1 .. nlev-2 run GCR there */
+    if (o->amg == 1)
+        for (int k = 1; k < h->nlev - 1; k++) {
+            size_t nk = (size_t)h->lev[k].A.n, m = (size_t)(o->amli_iters > 0 ? o->amli_iters : 1);
+            h->lev[k].gv = xcalloc(m * nk, sizeof(double));
+            h->lev[k].gw = xcalloc(m * nk, sizeof(double));
+            h->lev[k].gres = xcalloc(nk, sizeof(double));
         }
     /* coarsest level: dense LU */
     level_t *C = &h->lev[h->nlev - 1];
@@ -1160,6 +1372,96 @@ static void vcycle(o_handle *h, int l, const double *b, double *x) {
         mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 1, L->tmp);
 }
 
+static void kcycle(o_handle *h, int l, const double *b, double *x);
+
+/*
+ * The coarse correction of the nonlinear AMLI-cycle (reading R15): amli_iters
+ * steps of flexible GCR on A_k e = r from e = 0, each step preconditioned by
+ * the cycle of level k.  Step t takes v_t = cycle(res), w_t = A_k v_t,
+ * makes w_t orthogonal to the earlier w_s (v_t follows), then
+ * alpha_t = (w_t, res) / (w_t, w_t), e += alpha_t v_t, res -= alpha_t w_t.
+ */
+static void amli_coarse(o_handle *h, int k, const double *r, double *e) {
+    level_t *L = &h->lev[k];
+    int n = L->A.n, m = h->opt.amli_iters > 0 ? h->opt.amli_iters : 1;
+    double *res = L->gres;
+    for (int i = 0; i < n; i++) {
+        e[i] = 0.0;
+        res[i] = r[i];
+    }
+    for (int t = 0; t < m; t++) {
+        double *v = L->gv + (size_t)t * n, *w = L->gw + (size_t)t * n;
+        kcycle(h, k, res, v);
+        for (int i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int p = L->A.rowptr[i]; p < L->A.rowptr[i + 1]; p++) s += L->A.val[p] * v[L->A.col[p]];
+            w[i] = s;
+        }
+        for (int u = 0; u < t; u++) {
+            const double *vu = L->gv + (size_t)u * n, *wu = L->gw + (size_t)u * n;
+            double den = dot(n, wu, wu);
+            if (den == 0.0) continue;
+            double beta = dot(n, w, wu) / den;
+            for (int i = 0; i < n; i++) {
+                w[i] -= beta * wu[i];
+                v[i] -= beta * vu[i];
+            }
+        }
+        double ww = dot(n, w, w);
+        if (ww == 0.0) break;
+        double alpha = dot(n, w, res) / ww;
+        for (int i = 0; i < n; i++) {
+            e[i] += alpha * v[i];
+            res[i] -= alpha * w[i];
+        }
+    }
+}
+
+/*
+ * The nonlinear AMLI-cycle for A_l e = b from zero (amg = 1): the V-cycle's
+ * smoothing and transfers, with the coarse problem solved exactly on the
+ * coarsest level and by amli_coarse elsewhere.
+ */
+static void kcycle(o_handle *h, int l, const double *b, double *x) {
+    level_t *L = &h->lev[l];
+    int n = L->A.n;
+    if (l == h->nlev - 1) {
+        dense_lu_solve(n, h->clu, h->cpiv, b, x);
+        return;
+    }
+    for (int i = 0; i < n; i++) x[i] = 0.0;
+    for (int s = 0; s < h->opt.pre; s++) mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 0, L->tmp);
+    for (int i = 0; i < n; i++) {
+        double s = b[i];
+        for (int p = L->A.rowptr[i]; p < L->A.rowptr[i + 1]; p++)
+            s -= L->A.val[p] * x[L->A.col[p]];
+        L->r[i] = s;
+    }
+    level_t *Lc = &h->lev[l + 1];
+    for (int I = 0; I < L->R.n; I++) {
+        double s = 0.0;
+        for (int p = L->R.rowptr[I]; p < L->R.rowptr[I + 1]; p++)
+            s += L->R.val[p] * L->r[L->R.col[p]];
+        Lc->b[I] = s;
+    }
+    if (l + 1 == h->nlev - 1) dense_lu_solve(Lc->A.n, h->clu, h->cpiv, Lc->b, Lc->x);
+    else amli_coarse(h, l + 1, Lc->b, Lc->x);
+    for (int i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int p = L->P.rowptr[i]; p < L->P.rowptr[i + 1]; p++)
+            s += L->P.val[p] * Lc->x[L->P.col[p]];
+        x[i] += s;
+    }
+    for (int s = 0; s < h->opt.post; s++)
+        mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 1, L->tmp);
+}
+
+/* B_P: the V-cycle (amg = 0) or the nonlinear AMLI-cycle (amg = 1). */
+static void pressure_cycle(o_handle *h, const double *b, double *x) {
+    if (h->opt.amg == 1) kcycle(h, 0, b, x);
+    else vcycle(h, 0, b, x);
+}
+
 /*
  * One CPR application z = B v (Alg. 1 from x = 0, Eq. 3.1):
  *   r_P = Pi_P^T v (decoupled restriction), e_P = B_P r_P (AMG V-cycle),
@@ -1170,7 +1472,7 @@ static void cpr_apply(o_handle *h, const double *v, double *z) {
     for (int i = 0; i < nb; i++)
         h->rp[i] = (h->w[3 * i] * v[3 * i] + h->w[3 * i + 1] * v[3 * i + 1]) +
                    h->w[3 * i + 2] * v[3 * i + 2];
-    vcycle(h, 0, h->rp, h->ep);
+    pressure_cycle(h, h->rp, h->ep);
     for (int i = 0; i < nb; i++) {
         z[3 * i] = h->ep[i];
         z[3 * i + 1] = 0.0;
@@ -1182,7 +1484,7 @@ static void cpr_apply(o_handle *h, const double *v, double *z) {
 }
 
 void o_cpr_apply(o_handle *h, const double *v, double *z) { cpr_apply(h, v, z); }
-void o_vcycle(o_handle *h, const double *b, double *x) { vcycle(h, 0, b, x); }
+void o_vcycle(o_handle *h, const double *b, double *x) { pressure_cycle(h, b, x); }
 void o_bilu_apply(o_handle *h, const double *r, double *z) {
     o_bilu0_solve(h->nb, h->rowptr, h->col, h->lu, h->bcolor, h->nbcolors, r, z);
 }

@@ -39,6 +39,10 @@ typedef struct {
     int resetup;          /* when Alg. 3 rebuilds B and the pattern is unchanged: 0 full setup;
                              1 numeric only, keeping the last setup's levels, strength sets,
                              C/F splits and colorings (0) */
+    int amg;              /* first stage: 0 classical AMG V-cycle (reading R5); 1 the paper's
+                             UA-AMG, double pairwise aggregation and the nonlinear AMLI-cycle
+                             (Sec. 6, reading R15) (0) */
+    int amli_iters;       /* amg = 1: GCR steps of each coarse correction (2) */
 } o_opts;
 
 typedef struct {
@@ -81,6 +85,8 @@ int    o_bilu0(int nb, const int *rowptr, const int *col, const double *val, uin
                int *bcolor, double *lu);
 int    o_bilu0_natural(int nb, const int *rowptr, const int *col, const double *val, double *lu);
 int    o_natural_levels(int nb, const int *rowptr, const int *col, int *level);
+int    o_aggregate(int n, const int *rowptr, const int *col, const double *val, double beta,
+                   int passes, int *agg);
 void   o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,
                      const int *bcolor, int nbcolors, const double *r, double *z);
 int    o_fgmres_identity(int nb, const int *rowptr, const int *col, const double *val,

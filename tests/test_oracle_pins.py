@@ -611,6 +611,144 @@ def test_vcycle_two_level_composition(tiny):
     s.close()
 
 
+# -------------------------------------------- UA-AMG and the AMLI-cycle (f2)
+
+def _chain(n):
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+                vals.append(v)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    return A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data
+
+
+def test_pairwise_aggregation_on_a_chain():
+    """A 1-D Laplacian: the end node has the fewest nodes depending on it, so
+    matching runs left to right in pairs {2k, 2k+1}; the pair operator is again
+    a chain, so the second pass gives aggregates of four consecutive nodes."""
+    rp, cl, v = _chain(16)
+    agg1, n1 = oracle.aggregate(16, rp, cl, v, passes=1)
+    assert n1 == 8 and np.array_equal(agg1, np.arange(16) // 2)
+    agg2, n2 = oracle.aggregate(16, rp, cl, v, passes=2)
+    assert n2 == 4 and np.array_equal(agg2, np.arange(16) // 4)
+
+
+@pytest.mark.parametrize("which", ["laplacian", "pressure"])
+def test_pairwise_aggregation_properties(which):
+    """Every node in exactly one aggregate; one pass forms pairs or singletons,
+    each pair strongly coupled (c_ij < 0 and -c_ij >= 0.25 max_k -c_ik, from one
+    of its nodes, c the symmetric part); two passes give at most four nodes,
+    each aggregate connected in the symmetrised pattern; the count at least
+    halves twice on the Laplacian."""
+    if which == "laplacian":
+        rp, cl, v = bs.laplacian_2d(12, 10)
+    else:
+        rp, cl, v = _pressure_level0(bs.jacobian(bs.GridSpec(8, 8, 3, seed=2)))
+    n = len(rp) - 1
+    A = sp.csr_matrix((v, cl, rp), shape=(n, n))
+    C = ((A + A.T) * 0.5).toarray()
+    np.fill_diagonal(C, 0.0)
+    maxneg = np.maximum((-C).max(axis=1), 0.0)
+
+    def strong(i, j):
+        return C[i, j] < 0 and -C[i, j] >= 0.25 * maxneg[i]
+
+    agg1, n1 = oracle.aggregate(n, rp, cl, v, passes=1)
+    sizes = np.bincount(agg1, minlength=n1)
+    assert sizes.sum() == n and sizes.min() >= 1 and sizes.max() <= 2
+    for a in np.flatnonzero(sizes == 2):
+        i, j = np.flatnonzero(agg1 == a)
+        assert strong(i, j) or strong(j, i)
+    agg2, n2 = oracle.aggregate(n, rp, cl, v, passes=2)
+    sizes = np.bincount(agg2, minlength=n2)
+    assert sizes.sum() == n and sizes.min() >= 1 and sizes.max() <= 4
+    G = nx.Graph((i, int(j)) for i in range(n) for j in cl[rp[i]:rp[i + 1]] if j != i)
+    for a in range(n2):
+        assert nx.is_connected(G.subgraph(np.flatnonzero(agg2 == a).tolist()))
+    if which == "laplacian":
+        assert n2 <= n // 3
+
+
+def test_ua_hierarchy_is_galerkin():
+    """amg = 1: P_l has one unit entry per row (the node's aggregate, at most
+    four nodes each) and A_{l+1} = P_l^T A_l P_l."""
+    J = bs.jacobian(bs.GridSpec(10, 10, 4, seed=1))
+    s = oracle.Solver(J, amg=1, coarse_max=30)
+    assert s.nlev >= 3
+    for l in range(s.nlev - 1):
+        L0, L1 = s.level(l), s.level(l + 1)
+        P = L0["P"].dense()
+        assert np.array_equal(P.sum(axis=1), np.ones(P.shape[0])) and set(np.unique(P)) <= {0.0, 1.0}
+        assert np.array_equal(np.argmax(P, axis=1), L0["cf"])
+        assert np.bincount(L0["cf"]).max() <= 4
+        A, Ac = L0["A"].dense(), L1["A"].dense()
+        assert np.allclose(Ac, P.T @ A @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    s.close()
+
+
+def _two_level_dense(lv, lvc, Acinv):
+    """x = S b + P Ac^-1 P^T (b - A S b) as a matrix (pre = 1, post = 0)."""
+    a = lv["A"]
+    A, P = a.dense(), lv["P"].dense()
+    n = A.shape[0]
+    S = np.column_stack([oracle.mcgs_sweep(a.rowptr, a.col, a.val, lv["color"], lv["ncolors"], e,
+                                           np.zeros(n)) for e in np.eye(n)])
+    return S + P @ Acinv @ P.T @ (np.eye(n) - A @ S)
+
+
+def test_amli_cycle_two_levels_is_the_two_level_cycle():
+    """With the coarsest level next, the AMLI-cycle's coarse problem is solved
+    exactly: x = S b + P A_c^-1 P^T (b - A S b)."""
+    J = bs.tiny()
+    s = oracle.Solver(J, amg=1, coarse_max=12, max_levels=2, pre=1, post=0)
+    assert s.nlev == 2
+    L0, L1 = s.level(0), s.level(1)
+    B = _two_level_dense(L0, L1, np.linalg.inv(L1["A"].dense()))
+    b = np.random.default_rng(5).standard_normal(J.nb)
+    assert np.allclose(s.vcycle(b), B @ b, rtol=1e-10, atol=1e-10 * np.abs(B @ b).max())
+    s.close()
+
+
+def test_amli_cycle_coarse_correction_minimises_the_residual():
+    """Three levels, two GCR steps on level 1 with the (linear) two-level cycle
+    B_1 of levels 1-2 as preconditioner: the correction e minimises
+    ||r_1 - A_1 e|| over span{B_1 r_1, B_1 A_1 B_1 r_1} (least squares here),
+    and x = S_0 b + P_0 e.  The cycle is homogeneous and not additive."""
+    J = bs.jacobian(bs.GridSpec(6, 6, 3, seed=4))
+    s = oracle.Solver(J, amg=1, coarse_max=8, max_levels=3, pre=1, post=0, amli_iters=2)
+    assert s.nlev == 3
+    L0, L1, L2 = s.level(0), s.level(1), s.level(2)
+    B1 = _two_level_dense(L1, L2, np.linalg.inv(L2["A"].dense()))
+    a0 = L0["A"]
+    A0, P0, A1 = a0.dense(), L0["P"].dense(), L1["A"].dense()
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(J.nb)
+    S0b = oracle.mcgs_sweep(a0.rowptr, a0.col, a0.val, L0["color"], L0["ncolors"], b, np.zeros(J.nb))
+    r1 = P0.T @ (b - A0 @ S0b)
+    V = np.column_stack([B1 @ r1, B1 @ A1 @ B1 @ r1])
+    y = np.linalg.lstsq(A1 @ V, r1, rcond=None)[0]
+    ref = S0b + P0 @ (V @ y)
+    x = s.vcycle(b)
+    assert np.allclose(x, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+    assert np.array_equal(s.vcycle(4.0 * b), 4.0 * x)
+    b2 = rng.standard_normal(J.nb)
+    assert not np.allclose(s.vcycle(b + b2), x + s.vcycle(b2), rtol=1e-6, atol=1e-9)
+    s.close()
+
+
+def test_cpr_solve_with_ua_amg():
+    """The CPR solve with the UA-AMG first stage reaches the direct solution."""
+    J = bs.jacobian(bs.GridSpec(8, 8, 4, seed=3))
+    s = oracle.Solver(J, amg=1, coarse_max=16)
+    x, st = s.solve(J.b, rtol=1e-10)
+    assert st["converged"]
+    assert np.allclose(x, np.linalg.solve(J.to_dense(), J.b), rtol=1e-7, atol=1e-9)
+    s.close()
+
+
 @pytest.mark.parametrize("coarse_max", [10 ** 6, 8])
 def test_whole_solve_reaches_direct_solution(tiny, coarse_max):
     J = tiny
