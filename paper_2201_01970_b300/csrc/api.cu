@@ -32,6 +32,9 @@ double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// The Python binding mirrors cpr_opts field by field; its test checks the same size.
+static_assert(sizeof(cpr_opts) == 96, "cpr_opts changed: update the binding's Opts and this check");
+
 void check_opts(const cpr_opts &o) {
     bool ok = o.restart >= 1 && o.restart <= kMaxRestart && o.max_restarts >= 1 && o.pre >= 0 &&
               o.post >= 0 && o.coarse_max >= 1 && o.coarse_max <= kMaxCoarse && o.max_levels >= 1 &&
