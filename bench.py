@@ -210,6 +210,39 @@ def host_sequence(seed_offset=0):
 
 # --------------------------------------------------------------- our arm
 
+def setup_profile(cpr, torch, J, stream, warm=4):
+    """Setup alone (FP32 mode): `warm` setups, then one more bracketed by
+    cudaProfilerStart/Stop (ncu --profile-from-start off) and recorded by the
+    setup's phase clock (CPR_SETUP_TIMING: per mark, host and device ms)."""
+    class DJ:
+        nb = J.nb
+        rowptr = torch.from_numpy(J.rowptr).cuda()
+        col = torch.from_numpy(J.col).cuda()
+        val = torch.from_numpy(J.val).cuda()
+
+    walls = []
+    for _ in range(warm):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        cpr.Solver(DJ, precond_fp32=1, stream=stream.cuda_stream).close()
+        torch.cuda.synchronize()
+        walls.append((time.perf_counter() - t) * 1e3)
+    os.environ["CPR_SETUP_TIMING"] = "1"
+    launches0 = cpr.launch_count()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    t = time.perf_counter()
+    solver = cpr.Solver(DJ, precond_fp32=1, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t) * 1e3
+    torch.cuda.profiler.stop()
+    del os.environ["CPR_SETUP_TIMING"]
+    launches = cpr.launch_count() - launches0
+    solver.close()
+    return {"workload": f"{WORKLOAD} FP32-mode setup", "warm_wall_ms": walls, "profiled_wall_ms": wall,
+            "launches": launches}
+
+
 def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_region=False):
     """Time K update+solve steps of one precision arm; returns a dict."""
     S = len(seq_dev)
@@ -571,6 +604,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bilu-natural", action="store_true",
                     help="skip the level-scheduled (natural-order) BILU(0) line")
+    ap.add_argument("--setup-profile", action="store_true",
+                    help="only time setups of the workload, the last one bracketed for ncu and phase-marked")
     ap.add_argument("--no-resetup-numeric", action="store_true",
                     help="skip the numeric-only resetup line")
     ap.add_argument("--serve-full", action="store_true",
@@ -601,6 +636,11 @@ def main():
         res = adaptive_sweep(cpr, torch, stream)
         if rank == 0:
             print(json.dumps({"adaptive_sweep": res}), flush=True)
+        return
+    if args.setup_profile:
+        res = setup_profile(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
+        if rank == 0:
+            print(json.dumps({"setup_profile": res}), flush=True)
         return
 
     seq_host = host_sequence(seed_offset=rank)
