@@ -42,7 +42,7 @@ class Opts(C.Structure):
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
                 ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int),
-                ("amg", C.c_int), ("amli_iters", C.c_int)]
+                ("amg", C.c_int), ("amli_iters", C.c_int), ("coloring", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -91,6 +91,7 @@ def lib():
         L.o_bilu0_solve.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _f64p, _f64p]
         L.o_bilu0_natural.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p]
         L.o_natural_levels.argtypes = [C.c_int, _i32p, _i32p, _i32p]
+        L.o_vertices_grouping.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, _i32p]
         L.o_aggregate.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_int, _i32p]
         L.o_fgmres_identity.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
                                         C.c_int, C.c_int, C.POINTER(Stats), vp]
@@ -266,6 +267,14 @@ def natural_levels(J):
     level = np.zeros(J.nb, np.int32)
     nlev = lib().o_natural_levels(J.nb, _i32(J.rowptr), _i32(J.col), level)
     return level, nlev
+
+
+def vertices_grouping(n, rowptr, col, val, theta):
+    """The paper's VerticesSplitting/Grouping (Alg. 4-5) on the Eq. 5.1 strong
+    connections of a scalar CSR matrix: (group per vertex, number of groups)."""
+    color = np.zeros(n, np.int32)
+    c = lib().o_vertices_grouping(n, _i32(rowptr), _i32(col), _f64(val), theta, color)
+    return color, c
 
 
 def aggregate(n, rowptr, col, val, beta=0.25, passes=2):

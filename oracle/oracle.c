@@ -742,6 +742,118 @@ void o_mcgs_sweep(int n, const int *rowptr, const int *col, const double *val, c
     free(tmp);
 }
 
+/* ------------------------ Alg. 4-5: VerticesSplitting / VerticesGrouping (f1) */
+
+/*
+ * One call of VerticesSplitting (Alg. 4) on the vertices with inV set, over
+ * the strong-connection matrix S (Eq. 5.1, rows as computed, not
+ * symmetrised), with these readings (R16):
+ *  - "any take" picks, among the candidates with the largest |S_i|, the one
+ *    of lowest index;
+ *  - the candidates are the second-circle set W^ restricted to V when that
+ *    is not empty, else V;
+ *  - a vertex's color is undetermined while it is in V;
+ *  - S^_i = (union of S_k over k in S_i) minus (S_i and i), restricted to V;
+ *  - W-bar takes only the members of S_i that are still in V.
+ * The vertices put in W get `c`; the others of V are left with inV set for
+ * the next call.  Returns the size of W.
+ */
+static int vertices_splitting(const o_csr *S, char *inV, int *color, int c, char *inW, char *inHat) {
+    int n = S->n, nW = 0, left = 0;
+    for (int i = 0; i < n; i++) {
+        inW[i] = 0;
+        inHat[i] = 0;
+        left += inV[i];
+    }
+    char *inBar = xcalloc((size_t)n, 1);   /* W-bar: out of V for this call, kept for the next */
+    int nhat = 0;
+    while (left > 0) {
+        int best = -1, bdeg = -1;
+        for (int pass = nhat > 0 ? 0 : 1; pass < 2 && best < 0; pass++)
+            for (int i = 0; i < n; i++) {
+                if (!inV[i] || inBar[i] || inW[i] || (pass == 0 && !inHat[i])) continue;
+                int d = S->rowptr[i + 1] - S->rowptr[i];
+                if (d > bdeg) {
+                    best = i;
+                    bdeg = d;
+                }
+            }
+        int i = best;
+        int free_of_w = 1;
+        for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++)
+            if (inW[S->col[p]]) free_of_w = 0;
+        if (inHat[i]) {
+            inHat[i] = 0;
+            nhat--;
+        }
+        left--;
+        if (free_of_w) {
+            inW[i] = 1;
+            color[i] = c;
+            nW++;
+            for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++) {
+                int j = S->col[p];
+                if (!inV[j] || inBar[j] || inW[j]) continue;
+                inBar[j] = 1;
+                left--;
+                if (inHat[j]) {
+                    inHat[j] = 0;
+                    nhat--;
+                }
+            }
+            /* the second circle of i */
+            for (int p = S->rowptr[i]; p < S->rowptr[i + 1]; p++) {
+                int k = S->col[p];
+                for (int q = S->rowptr[k]; q < S->rowptr[k + 1]; q++) {
+                    int j = S->col[q];
+                    if (j == i || !inV[j] || inBar[j] || inW[j] || inHat[j]) continue;
+                    int in_si = 0;
+                    for (int t = S->rowptr[i]; t < S->rowptr[i + 1]; t++)
+                        if (S->col[t] == j) in_si = 1;
+                    if (in_si) continue;
+                    inHat[j] = 1;
+                    nhat++;
+                }
+            }
+        } else {
+            inBar[i] = 1;
+        }
+    }
+    /* V for the next call: W-bar */
+    for (int i = 0; i < n; i++) inV[i] = inBar[i];
+    free(inBar);
+    return nW;
+}
+
+/* VerticesGrouping (Alg. 5): repeated splitting until every vertex has a group. */
+static int vertices_grouping(const o_csr *S, int *color) {
+    int n = S->n, c = 0, left = n;
+    char *inV = xcalloc((size_t)n, 1), *inW = xcalloc((size_t)n, 1), *inHat = xcalloc((size_t)n, 1);
+    for (int i = 0; i < n; i++) {
+        inV[i] = 1;
+        color[i] = -1;
+    }
+    while (left > 0) {
+        left -= vertices_splitting(S, inV, color, c, inW, inHat);
+        c++;
+    }
+    for (int i = 0; i < n; i++)
+        if (color[i] < 0) abort();   /* every vertex leaves V through W or W-bar */
+    free(inV);
+    free(inW);
+    free(inHat);
+    return c;
+}
+
+int o_vertices_grouping(int n, const int *rowptr, const int *col, const double *val, double theta,
+                        int *color) {
+    o_csr A = csr_view(n, n, rowptr, col, val);
+    o_csr S = strength_color(&A, theta);
+    int c = vertices_grouping(&S, color);
+    csr_release(&S);
+    return c;
+}
+
 /* --------------------------------------- UA-AMG: pairwise aggregation (f2) */
 
 /* A binary min-heap of (key, node) pairs with lazy deletion. */
@@ -1147,6 +1259,7 @@ void o_default_opts(o_opts *o) {
     o->resetup = 0;
     o->amg = 0;
     o->amli_iters = 2;
+    o->coloring = 0;
 }
 
 static void free_setup(o_handle *h) {
@@ -1288,13 +1401,17 @@ static int build_preconditioner(o_handle *h, int numeric) {
             L->ncolors = kncol[l];
             kcolor[l] = NULL;
         } else {
-            /* the smoother's coloring (Eq. 5.1, Alg. 4-6 intent, reading R3) */
+            /* the smoother's coloring (Eq. 5.1): JP (reading R3), or Alg. 4-5 literally */
             o_csr Sc = strength_color(&L->A, o->theta_color);
-            o_csr G = sym_union(&Sc);
             L->color = xcalloc((size_t)n, sizeof(int));
-            L->ncolors = jp_color(&G, o->seed, 0, l, L->color);
+            if (o->coloring == 1) {
+                L->ncolors = vertices_grouping(&Sc, L->color);
+            } else {
+                o_csr G = sym_union(&Sc);
+                L->ncolors = jp_color(&G, o->seed, 0, l, L->color);
+                csr_release(&G);
+            }
             csr_release(&Sc);
-            csr_release(&G);
         }
         l++;
     }

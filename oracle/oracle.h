@@ -43,6 +43,8 @@ typedef struct {
                              UA-AMG, double pairwise aggregation and the nonlinear AMLI-cycle
                              (Sec. 6, reading R15) (0) */
     int amli_iters;       /* amg = 1: GCR steps of each coarse correction (2) */
+    int coloring;         /* smoother coloring: 0 JP on S u S^T (reading R3); 1 the paper's
+                             VerticesSplitting/Grouping, Alg. 4-5 (reading R16) (0) */
 } o_opts;
 
 typedef struct {
@@ -85,6 +87,8 @@ int    o_bilu0(int nb, const int *rowptr, const int *col, const double *val, uin
                int *bcolor, double *lu);
 int    o_bilu0_natural(int nb, const int *rowptr, const int *col, const double *val, double *lu);
 int    o_natural_levels(int nb, const int *rowptr, const int *col, int *level);
+int    o_vertices_grouping(int n, const int *rowptr, const int *col, const double *val,
+                           double theta, int *color);
 int    o_aggregate(int n, const int *rowptr, const int *col, const double *val, double beta,
                    int passes, int *agg);
 void   o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,

@@ -611,6 +611,80 @@ def test_vcycle_two_level_composition(tiny):
     s.close()
 
 
+# ------------------------------- Alg. 4-5: VerticesSplitting/Grouping (f1)
+
+def _grid5(nx_, ny_):
+    n = nx_ * ny_
+    A = np.zeros((n, n))
+    for j in range(ny_):
+        for i in range(nx_):
+            c = i + nx_ * j
+            for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < nx_ and 0 <= jj < ny_:
+                    A[c, ii + nx_ * jj] = -1.0
+            A[c, c] = -A[c].sum() + 0.5
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    return M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data
+
+
+def test_vertices_grouping_gives_red_black_on_the_five_point_grid():
+    """Alg. 4-5 at theta = 0 on the 4x4 five-point grid of Fig. 2(a): the first
+    split collects one checkerboard class, which leaves the other independent,
+    so c = 2 and the groups are the red-black grouping (red = (i + j) even)."""
+    rp, cl, v = _grid5(4, 4)
+    color, c = oracle.vertices_grouping(16, rp, cl, v, 0.0)
+    assert c == 2
+    np.testing.assert_array_equal(color, read_grid("redblack_4x4.txt").ravel())
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.05, 0.1, 0.3, 1.0])
+def test_vertices_grouping_properties(theta):
+    """Alg. 4-5 on a black-oil pressure matrix: every vertex in one group, no two
+    vertices of a group strongly connected (Eq. 5.1, either direction); at
+    theta = 0 each A_{V_l V_l} is diagonal (Prop. 5.2); c <= the largest
+    degree of S u S^T plus one (Prop. 5.1's bound); theta = 1 gives one group."""
+    rp, cl, v = _pressure_level0(bs.jacobian("20x20x5"))
+    n = len(rp) - 1
+    color, c = oracle.vertices_grouping(n, rp, cl, v, theta)
+    assert color.min() == 0 and color.max() == c - 1 and len(np.unique(color)) == c
+    Ad = np.abs(sp.csr_matrix((v, cl, rp), shape=(n, n)).toarray())
+    Sd = Ad > theta * Ad.sum(axis=1, keepdims=True)     # Eq. 5.1, the row sum with the diagonal
+    np.fill_diagonal(Sd, False)
+    G = Sd | Sd.T
+    same = color[:, None] == color[None, :]
+    assert not (G & same).any()
+    if theta == 0.0:
+        A = sp.csr_matrix((v, cl, rp), shape=(n, n)).toarray()
+        np.fill_diagonal(A, 0.0)
+        assert not (A[same] != 0.0).any()
+    assert c <= G.sum(axis=1).max() + 1
+    if theta == 1.0:
+        assert c == 1
+
+
+def test_vertices_grouping_against_jp():
+    """the paper's grouping and the JP coloring as the PGS-SCM
+    smoother of the CPR solve on 20x20x5, at theta in {0, 0.05, 0.1, 0.3}: both
+    converge; the level-0 group counts and iteration counts are printed
+    (pytest -s) for the comparison in the design notes."""
+    J = bs.jacobian("20x20x5")
+    rows = []
+    for theta in (0.0, 0.05, 0.1, 0.3):
+        r = [theta]
+        for coloring in (0, 1):
+            s = oracle.Solver(J, theta_color=theta, coloring=coloring)
+            _, st = s.solve(J.b, rtol=1e-6)
+            assert st["converged"]
+            r += [s.level(0)["ncolors"], st["iters"]]
+            s.close()
+        rows.append(r)
+    print("\ntheta  JP colors/iters  Alg.4-5 colors/iters")
+    for theta, c0, i0, c1, i1 in rows:
+        print(f"{theta:5.2f}  {c0:3d} / {i0:3d}        {c1:3d} / {i1:3d}")
+
+
 # -------------------------------------------- UA-AMG and the AMLI-cycle (f2)
 
 def _chain(n):
