@@ -210,6 +210,33 @@ def host_sequence(seed_offset=0):
 
 # --------------------------------------------------------------- our arm
 
+def theta_sweep(cpr, torch, J, stream, thetas=(0.0, 0.05, 0.1, 0.2, 0.3, 0.5)):
+    """The Eq. 5.1 threshold of the smoother's coloring (FP32 mode): per theta,
+    the colors of every smoothed level, the in-graph V-cycle and per-level
+    pre+post smoothing times, and one solve's iterations and time.  theta
+    changes only the coloring; the AMG hierarchy is the same."""
+    class DJ:
+        nb = J.nb
+        rowptr = torch.from_numpy(J.rowptr).cuda()
+        col = torch.from_numpy(J.col).cuda()
+        val = torch.from_numpy(J.val).cuda()
+
+    b = torch.from_numpy(J.b).cuda()
+    out = []
+    for th in thetas:
+        g = cpr.Solver(DJ, precond_fp32=1, theta_color=th, stream=stream.cuda_stream)
+        _, st = g.solve(b, rtol=RTOL)          # first solve: captures the step graphs
+        x = torch.zeros_like(b)
+        _, st = g.solve(b, x, rtol=RTOL)
+        parts = g.profile_vcycle_levels(20)
+        out.append({"theta": th, "colors": [g.level(l)["ncolors"] for l in range(g.nlev - 1)],
+                    "vcycle_us": parts["vcycle_us"],
+                    "smooth_us": [p["pre"] + p["post"] for p in parts["levels"]],
+                    "iters": st["iters"], "solve_ms": st["solve_ms"], "converged": st["converged"]})
+        g.close()
+    return {"workload": f"{WORKLOAD}, FP32 preconditioner, rtol {RTOL}", "rows": out}
+
+
 def setup_profile(cpr, torch, J, stream, warm=4):
     """Setup alone (FP32 mode): `warm` setups, then one more bracketed by
     cudaProfilerStart/Stop (ncu --profile-from-start off) and recorded by the
@@ -604,6 +631,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-bilu-natural", action="store_true",
                     help="skip the level-scheduled (natural-order) BILU(0) line")
+    ap.add_argument("--theta-sweep", action="store_true",
+                    help="only sweep the smoother coloring's Eq. 5.1 threshold: colors, V-cycle time, iterations")
     ap.add_argument("--setup-profile", action="store_true",
                     help="only time setups of the workload, the last one bracketed for ncu and phase-marked")
     ap.add_argument("--no-resetup-numeric", action="store_true",
@@ -636,6 +665,11 @@ def main():
         res = adaptive_sweep(cpr, torch, stream)
         if rank == 0:
             print(json.dumps({"adaptive_sweep": res}), flush=True)
+        return
+    if args.theta_sweep:
+        res = theta_sweep(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
+        if rank == 0:
+            print(json.dumps({"theta_sweep": res}), flush=True)
         return
     if args.setup_profile:
         res = setup_profile(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
