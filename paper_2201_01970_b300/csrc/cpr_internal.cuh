@@ -165,7 +165,7 @@ struct cpr_handle {
     // rows; slot k of a slice holds each of its rows' k-th block (column -1
     // past a row's end), the nine values of a slot lane-contiguous per block
     // entry, so a warp's loads are contiguous.  Refreshed with every new A.
-    cpr::DVec<int> sell_off, sell_col, sell_pos;
+    cpr::DVec<int> sell_off, sell_col;
     cpr::DVec<double> sell_val;
     int sell_slices = 0;
     bool sell_ok = false;

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int nslices, int nb, const in
 }
 
 // Sliced-ELL build: slot count per slice (its longest row), then each block's
-// slot (pos) and column, then the values.
+// column in its slot, then the values.
 __global__ void k_sell_width(int nb, int nslices, const int *rowptr, int *width) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
@@ -314,24 +314,29 @@ __global__ void k_sell_width(int nb, int nslices, const int *rowptr, int *width)
     width[s] = w;
 }
 
-__global__ void k_sell_pattern(int nb, const int *rowptr, const int *col, const int *off, int *scol, int *pos) {
+__global__ void k_sell_pattern(int nb, const int *rowptr, const int *col, const int *off, int *scol) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nb) return;
     int s = i >> 5, lane = i & 31;
     int slot = off[s];
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++, slot++) {
-        scol[(size_t)slot * 32 + lane] = col[p];
-        pos[p] = slot * 32 + lane;
-    }
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++, slot++) scol[(size_t)slot * 32 + lane] = col[p];
 }
 
-__global__ void k_sell_values(long nnzb, const int *pos, const double *val, double *sval) {
-    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < nnzb; p += (long)gridDim.x * blockDim.x) {
-        int q = pos[p];
-        double *d = sval + (size_t)(q >> 5) * 288 + (q & 31);
-        const double *v = val + 9 * (size_t)p;
-#pragma unroll
-        for (int e = 0; e < 9; e++) d[32 * e] = v[e];
+// The values, one CTA per slice, in output order: element t of the slice's
+// slots is (slot k, entry e, lane l) with t = 288 k + 32 e + l, so a warp
+// writes 32 consecutive doubles, while its reads stay inside the slice's own
+// contiguous run of blocks (rows 32 s .. 32 s + 31), which L1 holds.  Padding
+// slots are not written: the SpMV skips them by their column (-1).
+__global__ void __launch_bounds__(256) k_sell_values(int nb, const int *rowptr, const int *off,
+                                                     const double *val, double *sval) {
+    int s = blockIdx.x, r0 = s * 32;
+    int w = off[s + 1] - off[s];
+    double *out = sval + (size_t)off[s] * 288;
+    for (int t = threadIdx.x; t < w * 288; t += blockDim.x) {
+        int k = t / 288, rem = t - k * 288, e = rem >> 5, r = r0 + (rem & 31);
+        if (r >= nb) continue;
+        int p = rowptr[r] + k;
+        if (p < rowptr[r + 1]) out[t] = val[9 * (size_t)p + e];
     }
 }
 
@@ -1236,7 +1241,6 @@ void norm_partials(cpr_handle *h, const double *a, long n) {
 void refresh_outer(cpr_handle *h, bool pattern_changed) {
     cudaStream_t s = h->stream;
     int nb = h->nb;
-    long nnzb = h->nnzb;
     if (pattern_changed || !h->sell_ok) {
         h->sell_ok = false;
         int nsl = (nb + 31) / 32;
@@ -1249,14 +1253,13 @@ void refresh_outer(cpr_handle *h, bool pattern_changed) {
         int slots = read_int(h->sell_off.p + nsl, s);
         h->sell_col.alloc(32 * (size_t)std::max(slots, 1), s);
         CK(cudaMemsetAsync(h->sell_col.p, 0xff, sizeof(int) * 32 * (size_t)std::max(slots, 1), s));
-        h->sell_pos.alloc(std::max<long>(nnzb, 1), s);
         k_sell_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, h->sell_off.p,
-                                                              h->sell_col.p, h->sell_pos.p);
+                                                              h->sell_col.p);
         CK_LAUNCH();
         h->sell_val.alloc(288 * (size_t)std::max(slots, 1), s);
         h->sell_slices = nsl;
     }
-    k_sell_values<<<grid_for(nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(nnzb, h->sell_pos.p, h->val.p, h->sell_val.p);
+    k_sell_values<<<h->sell_slices, 256, 0, s>>>(nb, h->rowptr.p, h->sell_off.p, h->val.p, h->sell_val.p);
     CK_LAUNCH();
     h->sell_ok = true;
 }
