@@ -10,6 +10,8 @@
  *   - the adaptive setup rule: Alg. 3 and Remark 4.2 (Sec. 4);
  *   - the AMG smoother: multi-color Gauss-Seidel over the colors of the
  *     strong-connection matrix, Eq. 5.1 and Alg. 6 (Sec. 5.2).
+ *   - the second stage's BILU(0): multicolor by default, or the natural-order,
+ *     level-scheduled BILU of Sec. 6 (cpr_opts.bilu_order).
  *
  * Conventions for every call below
  *   - Block rows: nb >= 1.  A 3x3 block is 9 doubles, row-major.  rowptr has
