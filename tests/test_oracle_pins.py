@@ -763,6 +763,33 @@ def test_ua_hierarchy_is_galerkin():
     s.close()
 
 
+def test_ua_numeric_resetup():
+    """amg = 1 with resetup = 1: a rebuild keeps the aggregates (so P) and
+    recomputes A_{l+1} = P^T A_l P; with unchanged values it equals the full
+    setup bit for bit, and on the next Jacobian the levels stay Galerkin."""
+    g = bs.GridSpec(10, 10, 4, seed=2)
+    J0, J1 = list(bs.jacobian_sequence(g, 2, drift=0.05))
+    kw = dict(amg=1, coarse_max=30, mu=0)
+    full = oracle.Solver(J0, **kw)
+    s = oracle.Solver(J0, resetup=1, **kw)
+    s.solve(J0.b)
+    s.update(J0)
+    for l in range(full.nlev):
+        np.testing.assert_array_equal(s.level(l)["A"].val, full.level(l)["A"].val)
+    s.update(J1)
+    _, st = s.solve(J1.b, rtol=1e-8)
+    assert st["setup_called"] == 1 and st["converged"] and s.nlev == full.nlev
+    for l in range(s.nlev - 1):
+        a = s.level(l)
+        np.testing.assert_array_equal(a["cf"], full.level(l)["cf"])
+        P = a["P"].dense()
+        Ac = P.T @ a["A"].dense() @ P
+        An = s.level(l + 1)["A"].dense()
+        assert np.allclose(An, Ac, rtol=1e-11, atol=1e-11 * np.abs(Ac).max())
+    full.close()
+    s.close()
+
+
 def _two_level_dense(lv, lvc, Acinv):
     """x = S b + P Ac^-1 P^T (b - A S b) as a matrix (pre = 1, post = 0)."""
     a = lv["A"]
