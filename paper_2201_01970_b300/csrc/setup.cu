@@ -1332,11 +1332,12 @@ __global__ void k_perm_count(int n, const int *order, const int *rowptr, const i
 // Fill the renumbered copy, G lanes per row; columns mapped through icol
 // (nullptr: unchanged); entries keep the natural (ascending-column) order of
 // their row.  With skip_diag the diagonal is dropped: the diagonals before a
-// lane's entry are counted from a ballot of the lane's group.
+// lane's entry are counted from a ballot of the lane's group.  nval32, when
+// set, receives the values rounded to FP32 as well.
 template <int G>
 __global__ void k_perm_fill(int n, const int *order, const int *rowptr, const int *col,
                             const double *val, bool skip_diag, const int *icol, const int *nrow,
-                            int *ncol, double *nval) {
+                            int *ncol, double *nval, float *nval32) {
     long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     long t = tid / G;
     int lane = (int)(tid % G);
@@ -1357,22 +1358,29 @@ __global__ void k_perm_fill(int n, const int *order, const int *rowptr, const in
         if (in && !d) {
             int o = q + p - skipped - __popc(m & below);
             ncol[o] = icol ? icol[j] : j;
-            nval[o] = val[p];
+            double v = val[p];
+            nval[o] = v;
+            if (nval32) nval32[o] = (float)v;
         }
         skipped += __popc(m);
     }
 }
 
 __global__ void k_perm_diag(int n, const int *order, const int *rowptr, const int *col,
-                            const double *val, double *diag, double *dinv) {
+                            const double *val, double *diag, double *dinv, float *diag32, float *dinv32) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     int i = order[t];
     double d = 0.0;
     for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
         if (col[p] == i) d = val[p];
+    double r = 1.0 / d;
     diag[t] = d;
-    dinv[t] = 1.0 / d;
+    dinv[t] = r;
+    if (diag32) {   // the FP32 shadows, rounded from the FP64 values
+        diag32[t] = (float)d;
+        dinv32[t] = (float)r;
+    }
 }
 
 __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const double *val,
@@ -1990,7 +1998,7 @@ void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
 int lanes_for(double avg, long rows, long target);
 
 void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool skip_diag, DCsr &dst,
-              cudaStream_t s) {
+              cudaStream_t s, DVec<float> *val32 = nullptr) {
     int n = src.n;
     DVec<int> cnt;
     cnt.alloc(std::max(n, 1), s);
@@ -2006,11 +2014,13 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
     dst.nnz = skip_diag ? std::max(src.nnz - n, 0) : src.nnz;
     dst.col.alloc(std::max(src.nnz, 1), s);
     dst.val.alloc(std::max(src.nnz, 1), s);
+    if (val32) val32->alloc(std::max(src.nnz, 1), s);   // the FP32 shadow, filled alongside
     // lanes per row: a few entries per lane, at least 2^17 threads
     int g = std::min(8, lanes_for((double)src.nnz / std::max(n, 1), n, 1L << 17));
     auto fill = [&](auto kern, int G) {
         kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p,
-                                                             skip_diag, icol, dst.rowptr.p, dst.col.p, dst.val.p);
+                                                             skip_diag, icol, dst.rowptr.p, dst.col.p, dst.val.p,
+                                                             val32 ? val32->p : nullptr);
     };
     switch (g) {
     case 1: fill(k_perm_fill<1>, 1); break;
@@ -2678,26 +2688,25 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         int n = Lv.A.n;
         const int *next_iperm = (l + 1 == L - 1) ? nullptr : Nx.iperm.p;
         const int *next_order = (l + 1 == L - 1) ? nullptr : Nx.rows_by_color.p;
-        perm_csr(Lv.A, Lv.rows_by_color.p, Lv.iperm.p, n, true, Lv.Ao, s);
-        perm_csr(Lv.P, Lv.rows_by_color.p, next_iperm, Lv.P.ncol, false, Lv.Pp, s);
-        perm_csr(Lv.R, next_order, Lv.iperm.p, n, false, Lv.Rp, s);
+        // the FP32 shadows are written by the same kernels
+        perm_csr(Lv.A, Lv.rows_by_color.p, Lv.iperm.p, n, true, Lv.Ao, s, f32 ? &Lv.Aoval32 : nullptr);
+        perm_csr(Lv.P, Lv.rows_by_color.p, next_iperm, Lv.P.ncol, false, Lv.Pp, s, f32 ? &Lv.Ppval32 : nullptr);
+        perm_csr(Lv.R, next_order, Lv.iperm.p, n, false, Lv.Rp, s, f32 ? &Lv.Rpval32 : nullptr);
         Lv.diag.alloc(n, s);
         Lv.dinv.alloc(n, s);
+        if (f32) {
+            Lv.diag32.alloc(n, s);
+            Lv.dinv32.alloc(n, s);
+        }
         k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
-                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p);
+                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p,
+                                                          f32 ? Lv.diag32.p : nullptr, f32 ? Lv.dinv32.p : nullptr);
         CK_LAUNCH();
         // smoothing launches cover one color (n / ncolors rows on average);
         // the residual kernel shares their width
         Lv.gA = lanes_for((double)Lv.Ao.nnz / n, n / std::max(1, Lv.ncolors), 1L << 16);
         Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
         Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
-        if (f32) {
-            to_f32(Lv.Ao.val, Lv.Aoval32, s);
-            to_f32(Lv.diag, Lv.diag32, s);
-            to_f32(Lv.dinv, Lv.dinv32, s);
-            to_f32(Lv.Pp.val, Lv.Ppval32, s);
-            to_f32(Lv.Rp.val, Lv.Rpval32, s);
-        }
     };
     for (int l = 0; l < L - 1; l++) {
         side.wait(l, s);
