@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
                 ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int),
-                ("amg", C.c_int), ("amli_iters", C.c_int), ("coloring", C.c_int)]
+                ("amg", C.c_int), ("amli_iters", C.c_int), ("coloring", C.c_int),
+                ("agg_match", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -92,7 +93,7 @@ def lib():
         L.o_bilu0_natural.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p]
         L.o_natural_levels.argtypes = [C.c_int, _i32p, _i32p, _i32p]
         L.o_vertices_grouping.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, _i32p]
-        L.o_aggregate.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_int, _i32p]
+        L.o_aggregate.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_double, C.c_int, C.c_int, _i32p]
         L.o_fgmres_identity.argtypes = [C.c_int, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
                                         C.c_int, C.c_int, C.POINTER(Stats), vp]
         L.o_default_opts.argtypes = [C.POINTER(Opts)]
@@ -277,11 +278,12 @@ def vertices_grouping(n, rowptr, col, val, theta):
     return color, c
 
 
-def aggregate(n, rowptr, col, val, beta=0.25, passes=2):
+def aggregate(n, rowptr, col, val, beta=0.25, passes=2, match=0):
     """Pairwise aggregation of a scalar CSR matrix: (aggregate per node, number
-    of aggregates); passes = 1 for one matching pass, 2 for the double pass."""
+    of aggregates); passes = 1 for one matching pass, 2 for the double pass;
+    match = 0 greedy, 1 handshake rounds."""
     agg = np.zeros(n, np.int32)
-    na = lib().o_aggregate(n, _i32(rowptr), _i32(col), _f64(val), beta, passes, agg)
+    na = lib().o_aggregate(n, _i32(rowptr), _i32(col), _f64(val), beta, passes, match, agg)
     return agg, na
 
 

@@ -922,7 +922,94 @@ static void heap_pop(heap_t *q, long *key, int *node) {
  * agg[i] = aggregate index, numbered in the order the aggregates form.
  * Returns the number of aggregates.
  */
-static int pairwise_pass(const o_csr *A, double beta, int *agg) {
+/*
+ * Handshake rounds (agg_match = 1: the parallel reading of the matching,
+ * R15).  Candidates are symmetric: j is a candidate of i when either is a
+ * strong neighbour of the other.  Each edge has one key for both ends,
+ * (c_ij, smaller hash, larger hash), unique per edge since the hash is a
+ * bijection of the index.  In a round every
+ * unmatched node points to its unmatched candidate of smallest key; mutual
+ * pointers pair up; an unmatched node with no unmatched candidate stays
+ * alone.  The smallest remaining edge is always mutual, so every round pairs
+ * or settles at least one node.  Aggregates are numbered by their smallest
+ * node.
+ */
+static int handshake_match(int n, const int *srow, const int *scol, const double *sval, uint32_t hb,
+                           int *agg) {
+    /* the symmetric candidate lists with their couplings */
+    int *crow = xcalloc((size_t)n + 1, sizeof(int));
+    for (int i = 0; i < n; i++)
+        for (int t = srow[i]; t < srow[i + 1]; t++) {
+            crow[i + 1]++;
+            crow[scol[t] + 1]++;
+        }
+    for (int i = 0; i < n; i++) crow[i + 1] += crow[i];
+    int *cc = xcalloc((size_t)crow[n] + 1, sizeof(int)), *fill = xcalloc((size_t)n, sizeof(int));
+    double *cv = xcalloc((size_t)crow[n] + 1, sizeof(double));
+    for (int i = 0; i < n; i++)
+        for (int t = srow[i]; t < srow[i + 1]; t++) {
+            int j = scol[t];
+            cc[crow[i] + fill[i]] = j;
+            cv[crow[i] + fill[i]++] = sval[t];
+            cc[crow[j] + fill[j]] = i;
+            cv[crow[j] + fill[j]++] = sval[t];
+        }
+    int *mate = xcalloc((size_t)n, sizeof(int)), *ptr = xcalloc((size_t)n, sizeof(int));
+    for (int i = 0; i < n; i++) mate[i] = -2;   /* -2 unmatched, -1 alone, else the partner */
+    int left = n;
+    while (left > 0) {
+        for (int i = 0; i < n; i++) {
+            ptr[i] = -1;
+            if (mate[i] != -2) continue;
+            double bc = 0.0;
+            uint32_t blo = 0, bhi = 0;
+            int bj = -1;
+            for (int t = crow[i]; t < crow[i + 1]; t++) {
+                int j = cc[t];
+                if (mate[j] != -2 || j == i) continue;
+                uint32_t hi_ = fmix32((uint32_t)i ^ hb), hj = fmix32((uint32_t)j ^ hb);
+                uint32_t lo = hi_ < hj ? hi_ : hj, hi = hi_ < hj ? hj : hi_;
+                int better = bj < 0 || cv[t] < bc ||
+                             (cv[t] == bc && (lo < blo || (lo == blo && (hi < bhi || (hi == bhi && j < bj)))));
+                if (better) {
+                    bj = j;
+                    bc = cv[t];
+                    blo = lo;
+                    bhi = hi;
+                }
+            }
+            ptr[i] = bj;
+        }
+        for (int i = 0; i < n; i++) {
+            if (mate[i] != -2) continue;
+            if (ptr[i] < 0) {
+                mate[i] = -1;
+                left--;
+            } else if (ptr[ptr[i]] == i && i < ptr[i]) {
+                mate[i] = ptr[i];
+                mate[ptr[i]] = i;
+                left -= 2;
+            }
+        }
+    }
+    int na = 0;
+    for (int i = 0; i < n; i++) agg[i] = -1;
+    for (int i = 0; i < n; i++) {
+        if (agg[i] >= 0) continue;
+        agg[i] = na;
+        if (mate[i] >= 0) agg[mate[i]] = na;
+        na++;
+    }
+    free(crow);
+    free(cc);
+    free(fill);
+    free(cv);
+    free(mate);
+    free(ptr);
+    return na;
+}
+
+static int pairwise_pass(const o_csr *A, double beta, int match, uint32_t hb, int *agg) {
     int n = A->n;
     o_csr T = transpose(A);
     /* S with its couplings: row i holds the strong neighbours of i */
@@ -955,6 +1042,16 @@ static int pairwise_pass(const o_csr *A, double beta, int *agg) {
                 sval[nnz++] = cval[t];
             }
         srow[i + 1] = nnz;
+    }
+    if (match == 1) {
+        int na = handshake_match(n, srow, scol, sval, hb, agg);
+        free(ccol);
+        free(cval);
+        free(srow);
+        free(scol);
+        free(sval);
+        csr_release(&T);
+        return na;
     }
     int *m = xcalloc((size_t)n, sizeof(int));
     for (int k = 0; k < nnz; k++) m[scol[k]]++;
@@ -1020,16 +1117,16 @@ static o_csr agg_to_p(int n, int nc, const int *agg) {
  * operator P1^T A P1, so aggregates hold at most four nodes.  agg[i] = the
  * final aggregate of node i; returns their number.
  */
-static int aggregate_double(const o_csr *A, double beta, int *agg) {
+static int aggregate_double(const o_csr *A, double beta, int match, uint32_t hb, int *agg) {
     int n = A->n;
     int *a1 = xcalloc((size_t)n, sizeof(int));
-    int n1 = pairwise_pass(A, beta, a1);
+    int n1 = pairwise_pass(A, beta, match, hb, a1);
     o_csr P1 = agg_to_p(n, n1, a1);
     o_csr R1 = transpose(&P1);
     o_csr AP = spgemm(A, &P1);
     o_csr A1 = spgemm(&R1, &AP);
     int *a2 = xcalloc((size_t)n1, sizeof(int));
-    int n2 = pairwise_pass(&A1, beta, a2);
+    int n2 = pairwise_pass(&A1, beta, match, hb ^ 0x9e3779b9u, a2);
     for (int i = 0; i < n; i++) agg[i] = a2[a1[i]];
     free(a1);
     free(a2);
@@ -1041,9 +1138,10 @@ static int aggregate_double(const o_csr *A, double beta, int *agg) {
 }
 
 int o_aggregate(int n, const int *rowptr, const int *col, const double *val, double beta, int passes,
-                int *agg) {
+                int match, int *agg) {
     o_csr A = csr_view(n, n, rowptr, col, val);
-    return passes == 1 ? pairwise_pass(&A, beta, agg) : aggregate_double(&A, beta, agg);
+    uint32_t hb = fmix32(3u * 1000003u);
+    return passes == 1 ? pairwise_pass(&A, beta, match, hb, agg) : aggregate_double(&A, beta, match, hb, agg);
 }
 
 /* ----------------------------------------------------------------- BILU(0) */
@@ -1260,6 +1358,7 @@ void o_default_opts(o_opts *o) {
     o->amg = 0;
     o->amli_iters = 2;
     o->coloring = 0;
+    o->agg_match = 0;
 }
 
 static void free_setup(o_handle *h) {
@@ -1377,7 +1476,9 @@ static int build_preconditioner(o_handle *h, int numeric) {
             L->cf = xcalloc((size_t)n, sizeof(int));
             if (o->amg == 1) {
                 /* UA-AMG: cf holds each node's aggregate */
-                nc = aggregate_double(&L->A, o->theta_amg, L->cf);
+                uint32_t s32 = (uint32_t)(o->seed ^ (o->seed >> 32));
+                nc = aggregate_double(&L->A, o->theta_amg, o->agg_match,
+                                      fmix32(s32 + 3u * 1000003u + (uint32_t)l), L->cf);
             } else {
                 L->S = strength_rs(&L->A, o->theta_amg);
                 nc = pmis(&L->S, o->seed, 1, l, L->cf);

@@ -45,6 +45,8 @@ typedef struct {
     int amli_iters;       /* amg = 1: GCR steps of each coarse correction (2) */
     int coloring;         /* smoother coloring: 0 JP on S u S^T (reading R3); 1 the paper's
                              VerticesSplitting/Grouping, Alg. 4-5 (reading R16) (0) */
+    int agg_match;        /* amg = 1 matching: 0 greedy by (m_i, i); 1 handshake rounds, the
+                             parallel reading (R15) (0) */
 } o_opts;
 
 typedef struct {
@@ -90,7 +92,7 @@ int    o_natural_levels(int nb, const int *rowptr, const int *col, int *level);
 int    o_vertices_grouping(int n, const int *rowptr, const int *col, const double *val,
                            double theta, int *color);
 int    o_aggregate(int n, const int *rowptr, const int *col, const double *val, double beta,
-                   int passes, int *agg);
+                   int passes, int match, int *agg);
 void   o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,
                      const int *bcolor, int nbcolors, const double *r, double *z);
 int    o_fgmres_identity(int nb, const int *rowptr, const int *col, const double *val,

@@ -746,6 +746,75 @@ def test_pairwise_aggregation_properties(which):
         assert n2 <= n // 3
 
 
+def test_handshake_matching_on_a_weighted_chain():
+    """agg_match = 1 (handshake rounds) on a chain whose couplings grow weaker
+    to the right, -(n - i) between i and i + 1: the strongest remaining edge is
+    always the leftmost, so the pairs are {2k, 2k + 1}, and the pair operator
+    is again such a chain, giving aggregates of four."""
+    n = 16
+    A = np.zeros((n, n))
+    for i in range(n - 1):
+        A[i, i + 1] = A[i + 1, i] = -(n - i)
+    A[np.arange(n), np.arange(n)] = -A.sum(axis=1) + 1.0
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    rp, cl, v = M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data
+    agg1, n1 = oracle.aggregate(n, rp, cl, v, passes=1, match=1)
+    assert n1 == 8 and np.array_equal(agg1, np.arange(n) // 2)
+    agg2, n2 = oracle.aggregate(n, rp, cl, v, passes=2, match=1)
+    assert n2 == 4 and np.array_equal(agg2, np.arange(n) // 4)
+
+
+@pytest.mark.parametrize("which", ["laplacian", "pressure"])
+def test_handshake_matching_properties(which):
+    """Handshake rounds: pairs are strongly coupled in at least one direction;
+    the matching is maximal (no two single nodes strongly coupled); two passes
+    give connected aggregates of at most four nodes."""
+    if which == "laplacian":
+        rp, cl, v = bs.laplacian_2d(12, 10)
+    else:
+        rp, cl, v = _pressure_level0(bs.jacobian(bs.GridSpec(8, 8, 3, seed=2)))
+    n = len(rp) - 1
+    A = sp.csr_matrix((v, cl, rp), shape=(n, n))
+    C = ((A + A.T) * 0.5).toarray()
+    np.fill_diagonal(C, 0.0)
+    maxneg = np.maximum((-C).max(axis=1), 0.0)
+    strong = (C < 0) & (-C >= 0.25 * maxneg[:, None])
+    cand = strong | strong.T
+    agg1, n1 = oracle.aggregate(n, rp, cl, v, passes=1, match=1)
+    sizes = np.bincount(agg1, minlength=n1)
+    assert sizes.sum() == n and sizes.max() <= 2
+    for a in np.flatnonzero(sizes == 2):
+        i, j = np.flatnonzero(agg1 == a)
+        assert cand[i, j]
+    single = sizes[agg1] == 1
+    assert not (cand & single[:, None] & single[None, :]).any()
+    agg2, n2 = oracle.aggregate(n, rp, cl, v, passes=2, match=1)
+    sizes = np.bincount(agg2, minlength=n2)
+    assert sizes.sum() == n and sizes.max() <= 4
+    G = nx.Graph((i, int(j)) for i in range(n) for j in cl[rp[i]:rp[i + 1]] if j != i)
+    for a in range(n2):
+        assert nx.is_connected(G.subgraph(np.flatnonzero(agg2 == a).tolist()))
+
+
+def test_ua_with_handshake_matching_solves():
+    """amg = 1 with agg_match = 1: Galerkin levels of unit-row P and a CPR
+    solve reaching the direct solution."""
+    J = bs.jacobian(bs.GridSpec(8, 8, 4, seed=3))
+    s = oracle.Solver(J, amg=1, agg_match=1, coarse_max=16)
+    assert s.nlev >= 2
+    for l in range(s.nlev - 1):
+        L0, L1 = s.level(l), s.level(l + 1)
+        P = L0["P"].dense()
+        assert np.array_equal(P.sum(axis=1), np.ones(P.shape[0]))
+        Ac = L1["A"].dense()
+        assert np.allclose(Ac, P.T @ L0["A"].dense() @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    x, st = s.solve(J.b, rtol=1e-10)
+    assert st["converged"]
+    assert np.allclose(x, np.linalg.solve(J.to_dense(), J.b), rtol=1e-7, atol=1e-9)
+    s.close()
+
+
 def test_ua_hierarchy_is_galerkin():
     """amg = 1: P_l has one unit entry per row (the node's aggregate, at most
     four nodes each) and A_{l+1} = P_l^T A_l P_l."""
