@@ -61,17 +61,17 @@ struct o_handle {
     int nb, nnzb;
     int *rowptr, *col;
     double *val;   /* outer operator A^(k) */
-    double *pval;  /* the copy of A inside B (the second residual of Alg. 1), frozen with B (R7) */
-    double *w;     /* decoupling weights, 3 per block row (R1) */
+    double *pval;  /* the copy of A inside B (the second residual of Alg. 1), frozen with B while Alg. 3 reuses it */
+    double *w;     /* decoupling weights w_i = D_i^-T e_1, 3 per block row */
     int nlev;
     level_t lev[MAXLEV];
     double *clu;   /* coarsest level: dense LU, row-major, with row pivots */
     int *cpiv;
-    int *bcolor;   /* BILU(0) block colors (R6) */
+    int *bcolor;   /* BILU(0) block colors (JP at theta = 0 on the block graph) */
     int nbcolors;
     double *lu;    /* L blocks (unit diagonal implied), U blocks, U_ii^-1 at the diagonal */
     double *work1, *work2, *work3, *rp, *ep; /* CPR apply work vectors */
-    long last_iters; /* It of the previous solve (R7); -1 = none since the last setup */
+    long last_iters; /* It of Alg. 3: the inner steps of the previous solve; -1 = none since the last setup */
     int setup_count, setup_called, updates;
 };
 
@@ -226,7 +226,8 @@ static void bsr3_resid(int nb, const int *rowptr, const int *col, const double *
 /* -------------------------------------------------------------- decoupling */
 
 /*
- * Pressure decoupling and the pressure matrix (Eq. 3.1, reading R1).
+ * Pressure decoupling and the pressure matrix (Eq. 3.1; mode 1 takes ABF weights in
+ * place of the paper's plain injection).
  * mode 1: w_i = D_i^-T e_1, i.e. the first row of D_i^-1 by the adjugate:
  *   w_i = (C00, C10, C20) / det(D_i),  det = D00 C00 + D10 C10 + D20 C20.
  * mode 0: w_i = e_1 (plain injection).
@@ -264,7 +265,8 @@ int o_decouple(int nb, const int *rowptr, const int *col, const double *val, int
 
 /* ------------------------------------------------- strength and coloring */
 
-/* Eq. 5.1: j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik| (reading R2). */
+/* Eq. 5.1: j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik|, the sum over the
+ * whole row, the diagonal included. */
 static o_csr strength_color(const o_csr *A, double theta) {
     int n = A->n;
     o_csr S = csr_alloc(n, n, A->nnz, 0);
@@ -312,7 +314,7 @@ o_csr *o_transpose(int n, int ncol, const int *rowptr, const int *col, const dou
     return csr_box(transpose(&A));
 }
 
-/* Pattern of S united with S^T (the undirected graph of R2), sorted rows. */
+/* Pattern of S united with S^T (the undirected graph the colorings use), sorted rows. */
 static o_csr sym_union(const o_csr *S) {
     o_csr T = transpose(S);
     int n = S->n;
@@ -342,7 +344,8 @@ o_csr *o_sym_union(int n, const int *rowptr, const int *col) {
 }
 
 /*
- * Jones-Plassmann coloring of an undirected graph G (reading R3).
+ * Jones-Plassmann coloring of an undirected graph G, standing in for the sequential
+ * Alg. 4-5.
  * key(i) = (deg_G(i), hash(i), i).  Each round, from the round-start state,
  * every uncolored vertex whose key beats all uncolored neighbours is selected;
  * each selected vertex takes the smallest color not held by a neighbour.
@@ -713,7 +716,7 @@ int o_dense_lu_solve(int n, const double *a, const double *b, double *x) {
  * One sweep of PGS-SCM (Alg. 6): colors in order (ascending, or descending
  * when `descending`), each row i of the color taking
  *   x_i <- (b_i - sum_{j != i} a_ij x_j) / a_ii
- * with every x_j read as of the start of the color (reading R4).
+ * with every x_j read as of the start of the color.
  */
 static void mcgs_sweep(const o_csr *A, const int *color, int ncolors, const double *b,
                        double *x, int descending, double *tmp) {
@@ -747,7 +750,7 @@ void o_mcgs_sweep(int n, const int *rowptr, const int *col, const double *val, c
 /*
  * One call of VerticesSplitting (Alg. 4) on the vertices with inV set, over
  * the strong-connection matrix S (Eq. 5.1, rows as computed, not
- * symmetrised), with these readings (R16):
+ * symmetrised), with these readings of its loosely defined parts:
  *  - "any take" picks, among the candidates with the largest |S_i|, the one
  *    of lowest index;
  *  - the candidates are the second-circle set W^ restricted to V when that
@@ -910,7 +913,7 @@ static void heap_pop(heap_t *q, long *key, int *node) {
 }
 
 /*
- * One pass of pairwise matching (reading R15: the pairwise aggregation Sec. 6
+ * One pass of pairwise matching (the pairwise aggregation Sec. 6
  * names as NPAIR, taken on the symmetrised couplings c_ij = (a_ij + a_ji) / 2
  * so that a nonsymmetric A is matched as its symmetric part).
  *  - j != i is a strong neighbour of i when c_ij < 0 and
@@ -923,8 +926,8 @@ static void heap_pop(heap_t *q, long *key, int *node) {
  * Returns the number of aggregates.
  */
 /*
- * Handshake rounds (agg_match = 1: the parallel reading of the matching,
- * R15).  Candidates are symmetric: j is a candidate of i when either is a
+ * Handshake rounds (agg_match = 1: the parallel reading of the matching).
+ * Candidates are symmetric: j is a candidate of i when either is a
  * strong neighbour of the other.  Each edge has one key for both ends,
  * (c_ij, smaller hash, larger hash), unique per edge since the hash is a
  * bijection of the index.  In a round every
@@ -1184,7 +1187,7 @@ static int find_col(const int *col, int lo, int hi, int j) {
 }
 
 /*
- * Block ILU(0) in (color, index) order (reading R6), row by row: for row i and
+ * Block ILU(0) in (color, index) order, row by row: for row i and
  * each k before i in that order (ascending), L_ik = A_ik U_kk^-1, then
  * A_ij -= L_ik U_kj for every j after k in row k that is also in row i's
  * pattern.  The factor array holds L_ik and U_ij in A's pattern and U_ii^-1 at
@@ -1502,7 +1505,7 @@ static int build_preconditioner(o_handle *h, int numeric) {
             L->ncolors = kncol[l];
             kcolor[l] = NULL;
         } else {
-            /* the smoother's coloring (Eq. 5.1): JP (reading R3), or Alg. 4-5 literally */
+            /* the smoother's coloring (Eq. 5.1): JP standing in for Alg. 4-5, or Alg. 4-5 */
             o_csr Sc = strength_color(&L->A, o->theta_color);
             L->color = xcalloc((size_t)n, sizeof(int));
             if (o->coloring == 1) {
@@ -1554,7 +1557,8 @@ static int build_preconditioner(o_handle *h, int numeric) {
     return rc;
 }
 
-/* V(pre, post) cycle for A_l e = b with zero initial guess (reading R5). */
+/* V(pre, post) cycle for A_l e = b from zero: pre-smoothing colors ascending,
+ * post-smoothing descending. */
 static void vcycle(o_handle *h, int l, const double *b, double *x) {
     level_t *L = &h->lev[l];
     int n = L->A.n;
@@ -1593,7 +1597,7 @@ static void vcycle(o_handle *h, int l, const double *b, double *x) {
 static void kcycle(o_handle *h, int l, const double *b, double *x);
 
 /*
- * The coarse correction of the nonlinear AMLI-cycle (reading R15): amli_iters
+ * The coarse correction of the nonlinear AMLI-cycle (Sec. 6): amli_iters
  * steps of flexible GCR on A_k e = r from e = 0, each step preconditioned by
  * the cycle of level k.  Step t takes v_t = cycle(res), w_t = A_k v_t,
  * makes w_t orthogonal to the earlier w_s (v_t follows), then

@@ -32,21 +32,21 @@ typedef struct {
     int coarse_max;       /* coarsest level size for the dense LU (256) */
     int max_levels;       /* (20) */
     uint64_t seed;        /* hash seed of coloring and C/F splitting */
-    int bilu_order;       /* 0: multicolor BILU(0) in (JP color, index) order (reading R6);
+    int bilu_order;       /* 0: multicolor BILU(0) in (JP color, index) order;
                              1: natural order, the level-scheduled BILU of Sec. 6 (0) */
     int reuse_refresh;    /* 1: a B kept by Alg. 3 takes A^(k) for its second residual;
                              0: it keeps the copy of A it was built from (0) */
     int resetup;          /* when Alg. 3 rebuilds B and the pattern is unchanged: 0 full setup;
                              1 numeric only, keeping the last setup's levels, strength sets,
                              C/F splits and colorings (0) */
-    int amg;              /* first stage: 0 classical AMG V-cycle (reading R5); 1 the paper's
+    int amg;              /* first stage: 0 classical AMG V-cycle; 1 the paper's
                              UA-AMG, double pairwise aggregation and the nonlinear AMLI-cycle
-                             (Sec. 6, reading R15) (0) */
+                             (Sec. 6) (0) */
     int amli_iters;       /* amg = 1: GCR steps of each coarse correction (2) */
-    int coloring;         /* smoother coloring: 0 JP on S u S^T (reading R3); 1 the paper's
-                             VerticesSplitting/Grouping, Alg. 4-5 (reading R16) (0) */
+    int coloring;         /* smoother coloring: 0 JP on S u S^T; 1 the paper's
+                             VerticesSplitting/Grouping, Alg. 4-5 (0) */
     int agg_match;        /* amg = 1 matching: 0 greedy by (m_i, i); 1 handshake rounds, the
-                             parallel reading (R15) (0) */
+                             parallel form (0) */
 } o_opts;
 
 typedef struct {

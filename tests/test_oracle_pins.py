@@ -496,7 +496,7 @@ def test_cpr_apply_is_eq31_with_exact_pressure_solve(tiny):
 def test_kept_b_second_residual(refresh):
     """Alg. 3 keeps B^(k-1) for A^(k).  Eq. 3.1 in dense form with B_P = A_P^-1,
     W and M = L U all from A^(k-1): reuse_refresh = 0 keeps A^(k-1) in the
-    second residual, reuse_refresh = 1 takes A^(k) there (SURVEY f4)."""
+    second residual, reuse_refresh = 1 takes A^(k) there."""
     g = bs.GridSpec(4, 4, 2, 0.0, 1.0, 1.0, None, "corners", seed=4)
     J0, J1 = list(bs.jacobian_sequence(g, 2, drift=0.05))
     s = oracle.Solver(J0, coarse_max=10 ** 6, mu=10 ** 6, reuse_refresh=refresh)
@@ -531,7 +531,7 @@ def _level_dense(lv, which):
 
 
 def test_numeric_resetup():
-    """resetup = 1 (SURVEY f4): when Alg. 3 rebuilds B for a Jacobian of the
+    """resetup = 1: when Alg. 3 rebuilds B for a Jacobian of the
     same pattern, the levels, C/F splits, interpolation patterns and colorings
     of the last setup are kept and every value is recomputed.  Pins: A_P =
     W^T A^(k) Pi with W_i solving D_i^T w_i = e_1 on A^(k)'s blocks; every
@@ -665,7 +665,7 @@ def test_vertices_grouping_properties(theta):
 
 
 def test_vertices_grouping_against_jp():
-    """the paper's grouping and the JP coloring as the PGS-SCM
+    """The paper's grouping (Alg. 4-5) and the JP coloring as the PGS-SCM
     smoother of the CPR solve on 20x20x5, at theta in {0, 0.05, 0.1, 0.3}: both
     converge; the level-0 group counts and iteration counts are printed
     (pytest -s) for the comparison in the design notes."""
