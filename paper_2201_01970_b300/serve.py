@@ -66,6 +66,17 @@ class Server:
     def _resident(self) -> int:
         return sum(self.bytes.values())
 
+    def _open(self, A):
+        """A new handle for a member, on a CUDA stream of its own (non-blocking:
+        members never wait on each other)."""
+        import torch
+        st = torch.cuda.Stream()
+        opts = dict(self.opts)
+        opts["stream"] = st.cuda_stream
+        h = Solver(A, **opts)
+        h._serve_stream = st
+        return h
+
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         """Replay the requests (arrival times honoured when `realtime`); returns metrics."""
         pending = sorted(requests, key=lambda r: (r.arrival, r.member, r.step))
@@ -84,12 +95,7 @@ class Server:
             try:
                 req.start = now()
                 if fresh:
-                    import torch
-                    st = torch.cuda.Stream()      # non-blocking: members never wait on each other
-                    opts = dict(self.opts)
-                    opts["stream"] = st.cuda_stream
-                    h = Solver(req.A, **opts)
-                    h._serve_stream = st
+                    h = self._open(req.A)
                     with lock:
                         self.handles[req.member] = h
                 else:
