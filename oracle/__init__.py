@@ -77,6 +77,8 @@ def lib():
         L.o_jp_color.argtypes = [C.c_int, _i32p, _i32p, C.c_uint64, C.c_int, C.c_int, _i32p]
         L.o_hash.argtypes = [C.c_uint64, C.c_int, C.c_int, C.c_int]
         L.o_hash.restype = C.c_uint32
+        L.o_fmix32.argtypes = [C.c_uint32]
+        L.o_fmix32.restype = C.c_uint32
         L.o_pmis.argtypes = [C.c_int, _i32p, _i32p, C.c_uint64, C.c_int, C.c_int, _i32p]
         L.o_interp_direct.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p]
         L.o_interp_direct.restype = vp
@@ -100,6 +102,7 @@ def lib():
         L.o_setup.argtypes = [C.POINTER(vp), C.c_int, _i32p, _i32p, _f64p, C.POINTER(Opts)]
         L.o_update.argtypes = [vp, C.c_int, _i32p, _i32p, _f64p]
         L.o_solve.argtypes = [vp, _f64p, _f64p, C.c_double, C.POINTER(Stats)]
+        L.o_solve_rows.argtypes = [vp, C.c_int, C.c_int, _f64p, _f64p, C.c_double, C.POINTER(Stats)]
         L.o_destroy.argtypes = [vp]
         L.o_num_levels.argtypes = [vp]
         L.o_last_iters.argtypes = [vp]
@@ -183,6 +186,10 @@ def jp_color(G: CSR, seed=0, salt=0, level=0):
     color = np.zeros(G.n, np.int32)
     nc = lib().o_jp_color(G.n, _i32(G.rowptr), _i32(G.col), seed, salt, level, color)
     return color, nc
+
+
+def fmix32(h) -> int:
+    return int(lib().o_fmix32(h))
 
 
 def hash32(seed, salt, level, i) -> int:
@@ -331,6 +338,16 @@ class Solver:
         rc = lib().o_solve(self._h, _f64(b), x, rtol, C.byref(st))
         if rc < 0:
             raise RuntimeError(f"oracle solve failed ({rc})")
+        return x, st.as_dict()
+
+    def solve_rows(self, r0, r1, b, x0=None, rtol=1e-6):
+        """FGMRES on block rows [r0, r1) of a block-diagonal A (one system of a
+        batch) with this handle's B restricted to them."""
+        x = np.zeros(3 * (r1 - r0)) if x0 is None else _f64(x0).copy()
+        st = Stats()
+        rc = lib().o_solve_rows(self._h, r0, r1, _f64(b), x, rtol, C.byref(st))
+        if rc < 0:
+            raise RuntimeError(f"oracle solve_rows failed ({rc})")
         return x, st.as_dict()
 
     # inspection

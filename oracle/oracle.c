@@ -153,6 +153,8 @@ static uint32_t fmix32(uint32_t h) {
     return h;
 }
 
+uint32_t o_fmix32(uint32_t h) { return fmix32(h); }
+
 /* Per-vertex hash weight: salt 0 = smoother coloring, 1 = PMIS, 2 = BILU coloring. */
 uint32_t o_hash(uint64_t seed, int salt, int level, int i) {
     uint32_t s32 = (uint32_t)(seed ^ (seed >> 32));
@@ -1851,6 +1853,61 @@ int o_fgmres_identity(int nb, const int *rowptr, const int *col, const double *v
                       o_stats *st, double *hist) {
     op_ctx ctx = {nb, rowptr, col, val};
     return fgmres(nb, rowptr, col, val, identity_pc, &ctx, b, x, rtol, m, max_restarts, st, hist);
+}
+
+/*
+ * FGMRES (Alg. 2) on one system of a block-diagonal concatenation: block rows
+ * [r0, r1) of the handle's A, which must couple to no block row outside the
+ * range, preconditioned by the handle's B restricted to those rows.  B is
+ * applied to the vector that equals v on the range and zero elsewhere; with
+ * a block-diagonal A every level, interpolation and factor of B is block
+ * diagonal too, so the other systems' rows stay exactly zero and the range
+ * gets what a batch of such systems gives that system.  b and x hold
+ * 3 (r1 - r0) values.  Restart length and restarts are the handle's.
+ */
+typedef struct {
+    o_handle *h;
+    int r0, r1;
+    double *vfull, *zfull;
+} rows_ctx;
+
+static void rows_pc(void *ctx, const double *v, double *z) {
+    rows_ctx *c = (rows_ctx *)ctx;
+    int n = 3 * c->h->nb, m = 3 * (c->r1 - c->r0);
+    for (int i = 0; i < n; i++) c->vfull[i] = 0.0;
+    memcpy(c->vfull + 3 * (size_t)c->r0, v, sizeof(double) * (size_t)m);
+    cpr_apply(c->h, c->vfull, c->zfull);
+    memcpy(z, c->zfull + 3 * (size_t)c->r0, sizeof(double) * (size_t)m);
+}
+
+int o_solve_rows(o_handle *h, int r0, int r1, const double *b, double *x, double rtol, o_stats *st) {
+    if (r0 < 0 || r1 > h->nb || r0 >= r1) return O_ERR_INVALID;
+    int ns = r1 - r0, base = h->rowptr[r0];
+    int *rp = xcalloc((size_t)ns + 1, sizeof(int));
+    int *cl = xcalloc((size_t)(h->rowptr[r1] - base) + 1, sizeof(int));
+    for (int i = 0; i <= ns; i++) rp[i] = h->rowptr[r0 + i] - base;
+    for (int p = base; p < h->rowptr[r1]; p++) {
+        if (h->col[p] < r0 || h->col[p] >= r1) {
+            free(rp);
+            free(cl);
+            return O_ERR_INVALID;
+        }
+        cl[p - base] = h->col[p] - r0;
+    }
+    rows_ctx ctx = {h, r0, r1, xcalloc(3 * (size_t)h->nb, sizeof(double)),
+                    xcalloc(3 * (size_t)h->nb, sizeof(double))};
+    int rc = fgmres(ns, rp, cl, h->val + 9 * (size_t)base, rows_pc, &ctx, b, x, rtol, h->opt.restart,
+                    h->opt.max_restarts, st, NULL);
+    if (st) {
+        st->setup_called = h->setup_called;
+        st->setup_count = h->setup_count;
+        st->levels = h->nlev;
+    }
+    free(rp);
+    free(cl);
+    free(ctx.vfull);
+    free(ctx.zfull);
+    return rc;
 }
 
 /* ------------------------------------------------------------------- API */

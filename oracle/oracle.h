@@ -72,6 +72,7 @@ o_csr *o_sym_union(int n, const int *rowptr, const int *col);
 int    o_jp_color(int n, const int *rowptr, const int *col, uint64_t seed, int salt, int level,
                   int *color);
 uint32_t o_hash(uint64_t seed, int salt, int level, int i);
+uint32_t o_fmix32(uint32_t h);   /* the finalizer itself, for checking against published values */
 o_csr *o_strength_rs(int n, const int *rowptr, const int *col, const double *val, double theta);
 int    o_pmis(int n, const int *srowptr, const int *scol, uint64_t seed, int salt, int level,
               int *cf);
@@ -105,6 +106,10 @@ int  o_setup(o_handle **h, int nb, const int *rowptr, const int *col, const doub
              const o_opts *opt);
 int  o_update(o_handle *h, int nb, const int *rowptr, const int *col, const double *val);
 int  o_solve(o_handle *h, const double *b, double *x, double rtol, o_stats *st);
+/* FGMRES on block rows [r0, r1) of a block-diagonal A (one system of a batch),
+ * preconditioned by the handle's B restricted to those rows; does not count as
+ * the handle's solve for Alg. 3. */
+int  o_solve_rows(o_handle *h, int r0, int r1, const double *b, double *x, double rtol, o_stats *st);
 void o_destroy(o_handle *h);
 
 /* ---- inspection ---- */

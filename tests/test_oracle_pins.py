@@ -15,6 +15,7 @@ import scipy.sparse.linalg as spla
 
 import blackoil_synth as bs
 import oracle
+from parity_helpers import block_diag
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -991,3 +992,100 @@ def test_pattern_change_forces_setup():
     x, st = s.solve(J2.b)
     assert st["setup_called"] == 1 and st["converged"]
     s.close()
+
+
+# ------------------------------------------------------- hash and V-cycle pins
+
+def test_fmix32_against_published_murmur3_vectors():
+    """MurmurHash3_x86_32 of the empty key is fmix32(seed) (no blocks, no tail,
+    length 0), so its published test vectors pin the finalizer: seed 1 gives
+    0x514E28B7, seed 0xFFFFFFFF gives 0x81F16F39, seed 0 gives 0.  The
+    per-vertex hash is then fmix32(i ^ fmix32(seed32 + 1000003 salt + level))."""
+    assert oracle.fmix32(1) == 0x514E28B7
+    assert oracle.fmix32(0xFFFFFFFF) == 0x81F16F39
+    assert oracle.fmix32(0) == 0
+    for i in (0, 1, 7, 123456):
+        assert oracle.hash32(1, 0, 0, i) == oracle.fmix32(i ^ 0x514E28B7)
+    # salt and level enter the base as seed32 + 1000003 * salt + level
+    assert oracle.hash32(0, 1, 5, 9) == oracle.fmix32(9 ^ oracle.fmix32(1000003 + 5))
+
+
+def _mcgs_dense(A, color, ncolors, b, x, descending):
+    """One multi-color Gauss-Seidel sweep (Alg. 6) from the matrix splitting:
+    the rows of each color take x_I <- (b_I - (A - D)_I x) / d_I with x as of
+    the start of the color (Jacobi within a color)."""
+    x = x.copy()
+    d = np.diag(A)
+    off = A - np.diag(d)
+    order = range(ncolors - 1, -1, -1) if descending else range(ncolors)
+    for c in order:
+        I = color == c
+        x[I] = (b[I] - off[I] @ x) / d[I]
+    return x
+
+
+def _vcycle_dense(levels, l, b, post_descending=True):
+    """V(1,1) from zero on dense level matrices: pre-smoothing colors ascending,
+    residual, R = P^T, the coarser level recursively (exact at the coarsest),
+    prolongation, post-smoothing colors descending."""
+    A = levels[l]["A"]
+    if l == len(levels) - 1:
+        return np.linalg.solve(A, b)
+    col, nc, P = levels[l]["color"], levels[l]["ncolors"], levels[l]["P"]
+    x = _mcgs_dense(A, col, nc, b, np.zeros_like(b), False)
+    xc = _vcycle_dense(levels, l + 1, P.T @ (b - A @ x), post_descending)
+    x = x + P @ xc
+    return _mcgs_dense(A, col, nc, b, x, post_descending)
+
+
+def test_vcycle_three_level_composition():
+    """The oracle's V(1,1) on three levels against the dense composition above:
+    colors ascending before the coarse correction and descending after it, the
+    middle level smoothed on both sides, an exact solve only on the coarsest.
+    Ascending post-smoothing would give a different result, by far more than
+    the tolerance, so the test fixes the order as well as the recursion."""
+    J = bs.tiny(6, 5, 3)
+    s = oracle.Solver(J, coarse_max=8, max_levels=3)
+    assert s.nlev == 3
+    levels = []
+    for l in range(3):
+        L = s.level(l)
+        d = {"A": L["A"].dense()}
+        if l < 2:
+            assert L["ncolors"] >= 2
+            d.update(color=L["color"], ncolors=L["ncolors"], P=L["P"].dense())
+        levels.append(d)
+    b = np.random.default_rng(5).standard_normal(J.nb)
+    ref = _vcycle_dense(levels, 0, b)
+    x = s.vcycle(b)
+    np.testing.assert_allclose(x, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    wrong = _vcycle_dense(levels, 0, b, post_descending=False)
+    assert np.abs(wrong - ref).max() > 1e-6 * np.abs(ref).max()
+    s.close()
+
+
+def test_solve_rows_on_a_block_diagonal_system():
+    """FGMRES on one system of a block-diagonal concatenation with the shared B
+    restricted to its rows: B of a vector supported on one system is zero on
+    the others (exactly), a coarse-LU-only B reaches that system's direct
+    solution, and with the default hierarchy the solve converges on the true
+    residual of the system alone."""
+    J1, J2 = bs.tiny(4, 4, 2, seed=1), bs.tiny(5, 3, 2, seed=2)
+    C = block_diag([J1, J2])
+    o = oracle.Solver(C, coarse_max=8)
+    v = np.zeros(C.n)
+    v[3 * J1.nb:] = np.random.default_rng(1).standard_normal(J2.n)
+    z = o.cpr_apply(v)
+    assert not z[:3 * J1.nb].any() and np.abs(z[3 * J1.nb:]).max() > 0
+    x, st = o.solve_rows(J1.nb, C.nb, J2.b, rtol=1e-6)
+    assert st["converged"]
+    assert np.linalg.norm(J2.b - oracle.bsr3_spmv(J2, x)) < 1e-6 * np.linalg.norm(J2.b)
+    o.close()
+    exact = oracle.Solver(C, coarse_max=4096)
+    assert exact.nlev == 1
+    x, st = exact.solve_rows(0, J1.nb, J1.b, rtol=1e-12)
+    ref = np.linalg.solve(J1.to_dense(), J1.b)
+    np.testing.assert_allclose(x, ref, rtol=1e-8, atol=1e-8 * np.abs(ref).max())
+    with pytest.raises(RuntimeError):
+        exact.solve_rows(0, J1.nb + 1, np.zeros(3 * J1.nb + 3))   # couples into the next system
+    exact.close()
