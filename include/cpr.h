@@ -32,6 +32,9 @@
  *     be destroyed, except for CPR_ERR_INVALID from cpr_update/cpr_solve,
  *     which leaves it unchanged.
  *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Devices: a handle belongs to the CUDA device that was current when it
+ *     was set up.  Every call on it runs on that device, whichever device the
+ *     caller has current, and leaves the caller's current device as it was.
  */
 #ifndef CPR_B300_H
 #define CPR_B300_H
@@ -49,7 +52,8 @@ extern "C" {
 #define CPR_ERR_OOM (-3)       /* device memory exhausted */
 #define CPR_ERR_SINGULAR (-4)  /* zero pivot: block diagonal, smoother diagonal or coarse LU */
 #define CPR_ERR_BREAKDOWN (-5) /* NaN/Inf in the iteration or the right-hand side */
-#define CPR_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define CPR_ERR_TIMEOUT (-6)   /* reserved for a bounded device-side wait that gives up; no kernel
+                                  of this library waits on another, so no call returns it today */
 
 typedef struct cpr_handle cpr_handle;
 
@@ -163,7 +167,9 @@ const char *cpr_last_error_detail(void);
  * systems (B is the block-diagonal CPR preconditioner); FGMRES (Alg. 2) runs
  * per system in lockstep, each with its own Hessenberg matrix, rotations and
  * stop decision, and each Arnoldi step of the whole batch is one graph launch.
- * cpr_solve and the component calls reject a batch handle; cpr_destroy frees it.
+ * cpr_solve rejects a batch handle.  The component and inspection calls below
+ * accept one and work on the concatenated system (vectors of 3 * total block
+ * rows, systems in order); cpr_destroy frees it.
  * ---------------------------------------------------------------------- */
 
 /* Build a batch handle from nsys systems A[0..nsys-1] (host or device pointers,
@@ -206,9 +212,11 @@ int cpr_bilu_apply(cpr_handle *h, const double *r, double *z);
  * variant only.  The sweeps' work vector (3*nb values) lives in a fixed
  * device array of 65,536 block rows (1.5 MiB) that every GPU loading this
  * library holds until the process exits; a handle with more block rows gets
- * CPR_ERR_INVALID.  The call allocates nothing and frees nothing.  The first
- * call on a device looks up that array's device address (with the device
- * current), so make the first call before any stream capture.  All calls share
+ * CPR_ERR_INVALID (for a batch handle the limit applies to the total of its
+ * systems).  The call allocates nothing and frees nothing.  The array is
+ * mapped onto a device, and its device address looked up, when the first
+ * handle is set up there (cpr_setup, where allocating is allowed): the call
+ * itself only reads that cached address.  All calls share
  * the one array and leave their last contents in it; nothing in it needs to
  * start at zero (each call writes every entry it reads first).  Calls whose
  * GPU work overlaps -- two streams, two handles, two threads -- race on the
@@ -256,6 +264,17 @@ int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolor
 
 /* Number of kernels this library has launched in this process so far. */
 uint64_t cpr_launch_count(void);
+
+/* A cap on the device memory this library holds, over all handles and devices
+ * of the process (bytes; 0 = no cap, the default).  An allocation that would
+ * pass it fails as a failed device allocation does: CPR_ERR_OOM from the call
+ * that needed it, with the handle left as CPR_ERR_OOM leaves it.  Lets a
+ * caller that shares the GPU bound the library's share of it.  Not in the
+ * paper. */
+void cpr_set_memory_limit(uint64_t bytes);
+
+/* Device bytes the library holds now, over all handles and devices. */
+uint64_t cpr_memory_in_use(void);
 
 /* Kernel families that cpr_profile brackets with CUDA events on the handle's
  * stream during cpr_solve. */

@@ -90,6 +90,9 @@ def lib():
         L.cpr_apply.argtypes = [vp, vp, vp]
         L.cpr_vcycle.argtypes = [vp, vp, vp]
         L.cpr_bilu_apply.argtypes = [vp, vp, vp]
+        L.cpr_bilu_apply_noalloc.argtypes = [vp, vp, vp]
+        L.cpr_set_memory_limit.argtypes = [C.c_uint64]
+        L.cpr_memory_in_use.restype = C.c_uint64
         L.cpr_bsr3_spmv.argtypes = [C.POINTER(Bsr3), vp, vp, vp, vp]
         L.cpr_num_levels.argtypes = [vp]
         L.cpr_get_level_info.argtypes = [vp, C.c_int, C.POINTER(LevelInfo)]
@@ -201,6 +204,10 @@ class Solver:
     def bilu_apply(self, r, z) -> None:
         _check(lib().cpr_bilu_apply(self._h, _ptr(r), _ptr(z)), "cpr_bilu_apply")
 
+    def bilu_apply_noalloc(self, r, z) -> None:
+        """cpr_bilu_apply_noalloc: z = R r with no device allocation in the call."""
+        _check(lib().cpr_bilu_apply_noalloc(self._h, _ptr(r), _ptr(z)), "cpr_bilu_apply_noalloc")
+
     # inspection (host numpy copies, natural numbering)
     @property
     def nlev(self) -> int:
@@ -295,6 +302,7 @@ class BatchSolver(Solver):
                "cpr_batch_setup")
         self.sizes = [d.nb for d in descs]
         self.nb = sum(self.sizes)
+        self.nnzb = sum(d.nnzb for d in descs)
 
     def update(self, systems) -> None:
         descs = [_as_bsr3(A)[0] for A in systems]
@@ -325,6 +333,16 @@ PROF_SPMV, PROF_VCYCLE, PROF_BILU, PROF_CGS, PROF_RESID2, PROF_SMOOTH0 = range(6
 
 def launch_count() -> int:
     return int(lib().cpr_launch_count())
+
+
+def set_memory_limit(nbytes: int) -> None:
+    """Cap the device memory the library holds (0: no cap); beyond it calls fail with CPR_ERR_OOM."""
+    lib().cpr_set_memory_limit(int(nbytes))
+
+
+def memory_in_use() -> int:
+    """Device bytes the library holds now, over all handles."""
+    return int(lib().cpr_memory_in_use())
 
 
 def bsr3_spmv(A, x, b=None, y=None, stream=None):

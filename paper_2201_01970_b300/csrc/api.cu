@@ -12,22 +12,6 @@ namespace {
 
 thread_local std::string g_last_error;
 
-template <class F>
-int guarded(F f) {
-    try {
-        return f();
-    } catch (const Error &e) {
-        g_last_error = e.what;
-        return e.code;
-    } catch (const std::bad_alloc &) {
-        g_last_error = "host allocation failed";
-        return CPR_ERR_OOM;
-    } catch (...) {
-        g_last_error = "unknown failure";
-        return CPR_ERR_CUDA;
-    }
-}
-
 double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -194,6 +178,7 @@ uint64_t cpr_launch_count(void) { return (uint64_t)cpr::launch_count(); }
 int cpr_profile(cpr_handle *h, int enable) {
     if (!h) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         prof_flush(h);
         h->prof_open.clear();
         h->prof_mask = (unsigned)enable & ((1u << CPR_PROF_NFAMILIES) - 1u);
@@ -254,11 +239,17 @@ const char *cpr_last_error_detail(void) { return g_last_error.c_str(); }
 int cpr_setup(cpr_handle **out, const cpr_bsr3 *A, const cpr_opts *opts) {
     if (!out) return CPR_ERR_INVALID;
     *out = nullptr;
-    cpr_handle *h = new cpr_handle();
+    cpr_handle *h = new (std::nothrow) cpr_handle();
+    if (!h) return CPR_ERR_OOM;
     int rc = guarded([&] {
         if (opts) h->opt = *opts;
         else cpr_default_opts(&h->opt);
         check_opts(h->opt);
+        Nvtx nv("cpr_setup");
+        CK(cudaGetDevice(&h->device));
+        // the allocation-free entry's scratch array is mapped here, where
+        // allocating is allowed, rather than at its first call
+        noalloc_prepare();
         if (h->opt.stream) {
             h->stream = (cudaStream_t)h->opt.stream;
         } else {
@@ -290,6 +281,8 @@ int cpr_setup(cpr_handle **out, const cpr_bsr3 *A, const cpr_opts *opts) {
 int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
     if (!h) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
+        Nvtx nv("cpr_update");
         cudaStream_t s = h->stream;
         DVec<int> rp, cl;
         load_pattern(h, A, rp, cl);
@@ -330,6 +323,8 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
 int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
     if (!h || !b || !x || !(rtol > 0.0) || h->batch) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
+        Nvtx nv("cpr_solve");
         double t0 = now_ms();
         cudaStream_t s = h->stream;
         size_t bytes = sizeof(double) * 3 * (size_t)h->nb;
@@ -370,6 +365,9 @@ int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats 
 
 void cpr_destroy(cpr_handle *h) {
     if (!h) return;
+    int prev = -1;
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != h->device) cudaSetDevice(h->device);
+    else prev = -1;
     if (h->stream) cudaStreamSynchronize(h->stream);
     try {
         free_preconditioner(h);
@@ -404,11 +402,13 @@ void cpr_destroy(cpr_handle *h) {
             cudaStreamSynchronize(q);
             cudaStreamDestroy(q);
         }
+    if (prev >= 0) cudaSetDevice(prev);
 }
 
 int cpr_apply(cpr_handle *h, const double *v, double *z) {
     if (!h || !v || !z) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         apply_B(h, v, 0, nullptr, z, 0);
         CK(cudaStreamSynchronize(h->stream));
         return CPR_OK;
@@ -418,6 +418,7 @@ int cpr_apply(cpr_handle *h, const double *v, double *z) {
 int cpr_vcycle(cpr_handle *h, const double *b, double *x) {
     if (!h || !b || !x) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         vcycle_apply(h, b, x);
         CK(cudaStreamSynchronize(h->stream));
         return CPR_OK;
@@ -428,6 +429,7 @@ int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
     if (!h || !us || reps < 1 || h->lev.empty()) return CPR_ERR_INVALID;
     int written = 0;
     int rc = guarded([&] {
+        DeviceGuard dg(h->device);
         written = profile_vcycle_levels(h, reps, us, n_us);
         return CPR_OK;
     });
@@ -437,6 +439,7 @@ int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
 int cpr_bilu_apply(cpr_handle *h, const double *r, double *z) {
     if (!h || !r || !z) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         bilu_apply(h, r, z);
         CK(cudaStreamSynchronize(h->stream));
         return CPR_OK;
@@ -468,6 +471,7 @@ int cpr_copy_level(const cpr_handle *h, int level, int32_t *rowptr, int32_t *col
                    int32_t *color, int32_t *cf, int32_t *prow, int32_t *pcol, double *pval) {
     if (!h || level < 0 || level >= (int)h->lev.size()) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         const Level &L = h->lev[level];
         cudaStream_t s = h->stream;
         auto d2h = [&](void *dst, const void *src, size_t bytes) {
@@ -491,6 +495,7 @@ int cpr_copy_level(const cpr_handle *h, int level, int32_t *rowptr, int32_t *col
 int cpr_copy_weights(const cpr_handle *h, double *w) {
     if (!h || !w) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         CK(cudaMemcpyAsync(w, h->w.p, sizeof(double) * 3 * (size_t)h->nb, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
         return CPR_OK;
@@ -500,6 +505,7 @@ int cpr_copy_weights(const cpr_handle *h, double *w) {
 int cpr_copy_bilu(const cpr_handle *h, int32_t *bcolor, double *lu, int *nbcolors) {
     if (!h) return CPR_ERR_INVALID;
     return guarded([&] {
+        DeviceGuard dg(h->device);
         cudaStream_t s = h->stream;
         if (bcolor) CK(cudaMemcpyAsync(bcolor, h->bilu.color.p, sizeof(int) * h->nb, cudaMemcpyDeviceToHost, s));
         std::vector<float> tmp;

@@ -53,19 +53,6 @@ void concat(int nsys, const cpr_bsr3 *A, cudaStream_t s, DVec<int> &rp, DVec<int
     CK(cudaStreamSynchronize(s));
 }
 
-template <class F>
-int guarded_b(F f) {
-    try {
-        return f();
-    } catch (const Error &e) {
-        set_last_error(e.what);
-        return e.code;
-    } catch (...) {
-        set_last_error("unknown failure");
-        return CPR_ERR_CUDA;
-    }
-}
-
 }  // namespace
 
 extern "C" {
@@ -78,7 +65,7 @@ int cpr_batch_setup(cpr_handle **out, int nsys, const cpr_bsr3 *A, const cpr_opt
     DVec<double> v;
     std::vector<int> boff;
     int nb = 0, nnzb = 0;
-    int rc = guarded_b([&] {
+    int rc = guarded([&] {
         concat(nsys, A, s, rp, cl, v, boff, nb, nnzb);
         return CPR_OK;
     });
@@ -87,7 +74,7 @@ int cpr_batch_setup(cpr_handle **out, int nsys, const cpr_bsr3 *A, const cpr_opt
     cpr_handle *h = nullptr;
     rc = cpr_setup(&h, &all, opts);
     if (rc != CPR_OK) return rc;
-    rc = guarded_b([&] {
+    rc = guarded([&] {
         h->batch = new BatchInfo();
         h->batch->nsys = nsys;
         h->batch->boff = boff;
@@ -104,25 +91,25 @@ int cpr_batch_setup(cpr_handle **out, int nsys, const cpr_bsr3 *A, const cpr_opt
 
 int cpr_batch_update(cpr_handle *h, const cpr_bsr3 *A) {
     if (!h || !h->batch || !A) return CPR_ERR_INVALID;
-    BatchInfo &B = *h->batch;
-    DVec<int> rp, cl;
-    DVec<double> v;
-    std::vector<int> boff;
-    int nb = 0, nnzb = 0;
-    int rc = guarded_b([&] {
+    return guarded([&] {
+        DeviceGuard dg(h->device);
+        BatchInfo &B = *h->batch;
+        DVec<int> rp, cl;
+        DVec<double> v;
+        std::vector<int> boff;
+        int nb = 0, nnzb = 0;
         concat(B.nsys, A, h->stream, rp, cl, v, boff, nb, nnzb);
         if (boff != B.boff) fail(CPR_ERR_INVALID, "the batch's system sizes changed");
-        return CPR_OK;
+        cpr_bsr3 all{nb, nnzb, rp.p, cl.p, v.p};
+        return cpr_update(h, &all);
     });
-    if (rc != CPR_OK) return rc;
-    cpr_bsr3 all{nb, nnzb, rp.p, cl.p, v.p};
-    return cpr_update(h, &all);
 }
 
 int cpr_batch_solve(cpr_handle *h, const double *const *b, double *const *x, double rtol, cpr_stats *st) {
     if (!h || !h->batch || !b || !x || !(rtol > 0.0)) return CPR_ERR_INVALID;
     BatchInfo &B = *h->batch;
-    return guarded_b([&] {
+    return guarded([&] {
+        DeviceGuard dg(h->device);
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t s = h->stream;
         for (int k = 0; k < B.nsys; k++) {

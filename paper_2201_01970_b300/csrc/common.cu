@@ -10,6 +10,32 @@ namespace cpr {
 
 void fail(int code, const std::string &what) { throw Error{code, what}; }
 
+DeviceGuard::DeviceGuard(int dev) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != dev) {
+        CK(cudaSetDevice(dev));
+        prev = cur;
+    }
+}
+DeviceGuard::~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+// Library-wide device bytes and their cap (0 = no cap).
+static std::atomic<unsigned long long> g_bytes{0}, g_cap{0};
+
+void reserve_bytes(size_t bytes) {
+    unsigned long long cap = g_cap.load(std::memory_order_relaxed);
+    unsigned long long now = g_bytes.fetch_add(bytes, std::memory_order_relaxed) + bytes;
+    if (cap && now > cap) {
+        g_bytes.fetch_sub(bytes, std::memory_order_relaxed);
+        fail(CPR_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes would pass the library's "
+                          "memory limit of " + std::to_string(cap) + " bytes");
+    }
+}
+void unreserve_bytes(size_t bytes) { g_bytes.fetch_sub(bytes, std::memory_order_relaxed); }
+
 static unsigned long long g_launches = 0;
 static thread_local bool t_capturing = false;
 void count_launch() {
@@ -212,20 +238,11 @@ int read_int(const int *dptr, cudaStream_t s) {
     return v;
 }
 
-static uint32_t fmix32_host(uint32_t h) {
-    h ^= h >> 16;
-    h *= 0x85ebca6bu;
-    h ^= h >> 13;
-    h *= 0xc2b2ae35u;
-    h ^= h >> 16;
-    return h;
-}
-
 // Hash weight of vertex i is fmix32(i ^ base), base = fmix32(seed32 + 1000003*salt + level);
 // salt 0 = smoother coloring, 1 = PMIS, 2 = BILU coloring (MurmurHash3's finalizer).
 uint32_t hash_base(uint64_t seed, int salt, int level) {
     uint32_t s32 = (uint32_t)(seed ^ (seed >> 32));
-    return fmix32_host(s32 + 1000003u * (uint32_t)salt + (uint32_t)level);
+    return fmix32(s32 + 1000003u * (uint32_t)salt + (uint32_t)level);
 }
 
 bool is_device_ptr(const void *p) {
@@ -240,3 +257,11 @@ bool is_device_ptr(const void *p) {
 }
 
 }  // namespace cpr
+
+extern "C" {
+
+void cpr_set_memory_limit(uint64_t bytes) { cpr::g_cap.store(bytes, std::memory_order_relaxed); }
+
+uint64_t cpr_memory_in_use(void) { return cpr::g_bytes.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -3,9 +3,11 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -22,6 +24,43 @@ struct Error {
 };
 
 [[noreturn]] void fail(int code, const std::string &what);
+
+// The text of the calling thread's last failure (cpr_last_error_detail).
+void set_last_error(const std::string &what);
+
+// Runs f() and maps every exception to a return code, so that nothing escapes
+// a C-ABI function: library errors keep their code, a failed host allocation
+// is CPR_ERR_OOM, anything else CPR_ERR_CUDA.
+template <class F>
+int guarded(F f) {
+    try {
+        return f();
+    } catch (const Error &e) {
+        set_last_error(e.what);
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return CPR_ERR_OOM;
+    } catch (...) {
+        set_last_error("unknown failure");
+        return CPR_ERR_CUDA;
+    }
+}
+
+// Makes `dev` the current device for one entry point's work and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
+// Device bytes held by the library in this process, against the cap set with
+// cpr_set_memory_limit: reserve_bytes fails with CPR_ERR_OOM beyond the cap.
+void reserve_bytes(size_t bytes);
+void unreserve_bytes(size_t bytes);
 void check_cuda(cudaError_t e, const char *expr, const char *file, int line);
 #define CK(x) ::cpr::check_cuda((x), #x, __FILE__, __LINE__)
 void count_launch();                      // one kernel launched (not counted while capturing)
@@ -33,6 +72,16 @@ unsigned long long graph_kernel_nodes(cudaGraph_t g);
         ::cpr::count_launch();                                                        \
         ::cpr::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);   \
     } while (0)
+
+// An NVTX range for the life of the object (visible in Nsight timelines; no
+// cost without a profiler attached).  Ranges name the entry points, the setup's
+// phases and, outside graph capture, the kernel families of a B application.
+struct Nvtx {
+    explicit Nvtx(const char *name) { nvtxRangePushA(name); }
+    ~Nvtx() { nvtxRangePop(); }
+    Nvtx(const Nvtx &) = delete;
+    Nvtx &operator=(const Nvtx &) = delete;
+};
 
 // ------------------------------------------------------------ device buffers
 
@@ -67,23 +116,29 @@ struct DVec {
     void alloc(size_t count, cudaStream_t stream) {
         release();
         s = stream;
-        n = count;
         if (count) {
+            reserve_bytes(count * sizeof(T));
             cudaError_t e = cudaMallocFromPoolAsync((void **)&p, count * sizeof(T), library_pool(), stream);
-            if (e == cudaErrorMemoryAllocation) {
-                cudaGetLastError();
+            if (e != cudaSuccess) {
+                unreserve_bytes(count * sizeof(T));
                 p = nullptr;
-                n = 0;
-                fail(CPR_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes");
+                if (e == cudaErrorMemoryAllocation) {
+                    cudaGetLastError();
+                    fail(CPR_ERR_OOM, "device allocation of " + std::to_string(count * sizeof(T)) + " bytes");
+                }
+                CK(e);
             }
-            CK(e);
         }
+        n = count;
     }
     void zero() {
         if (n) CK(cudaMemsetAsync(p, 0, n * sizeof(T), s));
     }
     void release() {
-        if (p) cudaFreeAsync(p, s);
+        if (p) {
+            cudaFreeAsync(p, s);
+            unreserve_bytes(n * sizeof(T));
+        }
         p = nullptr;
         n = 0;
     }
@@ -170,6 +225,7 @@ struct cpr_handle {
     int sell_slices = 0;
     bool sell_ok = false;
     bool own_stream = false;
+    int device = 0;                 // the CUDA device the handle was set up on
     int nb = 0, nnzb = 0;
     cpr::DVec<int> rowptr, col;     // outer operator A^(k) (copy)
     cpr::DVec<double> val;
@@ -239,13 +295,21 @@ constexpr int kMaxRestart = 64;
 constexpr int kMaxCoarse = 4096;
 
 int grid_for(long n, int block, int cap = 1 << 30);
+
+// MurmurHash3's 32-bit finalizer (Appleby's published mixing function): the
+// bijective hash of the coloring, C/F splitting and matching keys.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
 void exclusive_scan(const int *in, int *out, int n, cudaStream_t s);   // out has n+1 entries
 int read_int(const int *dptr, cudaStream_t s);
 uint32_t hash_base(uint64_t seed, int salt, int level);
 bool is_device_ptr(const void *p);
-
-// text of the calling thread's last failure (api.cu)
-void set_last_error(const std::string &what);
 
 // event brackets (api.cu)
 void prof_begin(cpr_handle *h, int family);
@@ -260,6 +324,10 @@ void destroy_step_graphs(cpr_handle *h);
 void build_preconditioner(cpr_handle *h, bool numeric = false);
 void free_preconditioner(cpr_handle *h);
 void refresh_second_residual(cpr_handle *h);   // reuse_refresh: the kept B's copy of A := the current A
+
+// noalloc.cu: resolve (and so load) the allocation-free entry's scratch array
+// on the current device
+void noalloc_prepare();
 void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr, cudaStream_t s);
 
 // solve.cu

@@ -4,11 +4,16 @@
 // at start-up and forbids allocation later, and host code that runs while
 // another component owns the allocator (an allocation there would fail, or
 // would synchronize the device).  The forward/backward sweeps need one work
-// vector of 3*nb values; here it lives in a file-scope device array that is
-// sized once, at load time, instead of in memory the handle allocates.
+// vector of 3*nb values; here it lives in a file-scope device array of a fixed
+// maximum size instead of in memory the handle allocates.
 //
-// The array holds kNoAllocMaxBlockRows block rows (1.5 MiB).  Every GPU that
-// loads this library keeps that much memory until the process exits.
+// The array holds kNoAllocMaxBlockRows block rows (1.5 MiB).  The library's
+// device code for this file is a module of its own, which CUDA maps onto a
+// device (and so allocates the array there) the first time its address is
+// looked up.  cpr_setup does that lookup on the handle's device, where an
+// allocation is allowed, and loads the entry's kernels there, so a later call
+// finds both in place; every device that has had a handle set up keeps the
+// 1.5 MiB until the process exits.
 #include <mutex>
 
 #include "cpr_internal.cuh"
@@ -29,11 +34,9 @@ static __device__ __align__(256) double g_bilu_scratch[3 * kNoAllocMaxBlockRows]
 std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (at that device's first call).
-void *scratch_address() {
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
+// Device address of the scratch array on device `dev` (which must be
+// current), looked up once per device.
+void *scratch_address(int dev) {
     if (dev < 0 || dev >= kMaxDevices) fail(CPR_ERR_INVALID, "device index out of range");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
@@ -90,26 +93,47 @@ void sweeps(cpr_handle *h, const double *r, double *z, T *y, const T *lv, const 
 }
 
 }  // namespace
+
+// Called by cpr_setup with the handle's device current: maps the array and,
+// with CUDA's lazy loading, loads the code of every kernel the entry launches,
+// so that neither happens inside a later call.
+void noalloc_prepare() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    scratch_address(dev);
+    static std::mutex mu;
+    static bool loaded[kMaxDevices] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (loaded[dev]) return;
+    cudaFuncAttributes a;
+    CK(cudaFuncGetAttributes(&a, k_load<float>));
+    CK(cudaFuncGetAttributes(&a, k_load<double>));
+    CK(cudaFuncGetAttributes(&a, k_bilu_fwd<float, kBiluLanesF32>));
+    CK(cudaFuncGetAttributes(&a, k_bilu_fwd<double, 1>));
+    CK(cudaFuncGetAttributes(&a, k_bilu_bwd<float, kBiluLanesF32>));
+    CK(cudaFuncGetAttributes(&a, k_bilu_bwd<double, 1>));
+    loaded[dev] = true;
+}
+
 }  // namespace cpr
 
 using namespace cpr;
 
 extern "C" int cpr_bilu_apply_noalloc(cpr_handle *h, const double *r, double *z) {
     if (!h || !r || !z) return CPR_ERR_INVALID;
-    try {
+    return guarded([&] {
+        // the handle's device, whichever device the caller has current
+        DeviceGuard dg(h->device);
         if (h->nb > kNoAllocMaxBlockRows)
             fail(CPR_ERR_INVALID, "cpr_bilu_apply_noalloc supports at most " +
                                       std::to_string(kNoAllocMaxBlockRows) + " block rows; this system has " +
                                       std::to_string(h->nb));
-        void *y = scratch_address();
+        void *y = scratch_address(h->device);
         if (h->opt.precond_fp32)
             sweeps<float>(h, r, z, (float *)y, h->bilu.Lval32.p, h->bilu.Uval32.p, h->bilu.Dinv32.p);
         else
             sweeps<double>(h, r, z, (double *)y, h->bilu.Lval.p, h->bilu.Uval.p, h->bilu.Dinv.p);
         CK(cudaStreamSynchronize(h->stream));
         return CPR_OK;
-    } catch (const Error &e) {
-        set_last_error(e.what);
-        return e.code;
-    }
+    });
 }

@@ -32,15 +32,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
-    h ^= h >> 16;
-    h *= 0x85ebca6bu;
-    h ^= h >> 13;
-    h *= 0xc2b2ae35u;
-    h ^= h >> 16;
-    return h;
-}
-
 __device__ __forceinline__ bool key_greater(int a1, uint32_t h1, int i1, int a2, uint32_t h2,
                                             int i2) {
     if (a1 != a2) return a1 > a2;
@@ -2315,6 +2306,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         kept_b.Ucol = std::move(B.Ucol);
     }
     free_preconditioner(h);
+    Nvtx nv(numeric ? "numeric resetup" : "setup");
     cudaStream_t s = h->stream;
     PhaseClock clk;
     clk.start(s);
@@ -2357,6 +2349,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     // ---- second stage: multicolor BILU(0), on the side worker ----
     SideWorker side(h, &clk);
     side.post([h, nb, nnzb, f32, &bdiag, &side, numeric, &kept_b](cudaStream_t s) {
+        Nvtx r("BILU(0) setup");
         Bilu &B = h->bilu;
         int nl = 0, nu = 0;
         if (numeric) {   // the kept ordering and L/U patterns
@@ -2455,6 +2448,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     // ---- the AMG hierarchy ----
     for (int l = 0;; l++) {
         int n = h->lev[l].A.n;
+        Nvtx r("AMG level");
         {
             Level &L = h->lev[l];
             DVec<int> diag;
@@ -2556,6 +2550,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             side.finished(l);
         } else {
             side.post([h, l, n, &side](cudaStream_t s) {
+                Nvtx r("level coloring");
                 side.mark("idle");
                 Level &L = h->lev[l];
                 // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
@@ -2631,6 +2626,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         ~CoarseJoin() { finish(); }
     } coarse_join;
     {
+        Nvtx r("coarse LU");
         for (auto &e : h->ev_coarse)
             if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         if (!h->lu_stream) CK(cudaStreamCreateWithFlags(&h->lu_stream, cudaStreamNonBlocking));
@@ -2683,6 +2679,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     // side tasks have finished, while the worker goes on with the rest.
     int L = (int)h->lev.size();
     auto layout = [&](int l) {
+        Nvtx r("level layout");
         Level &Lv = h->lev[l];
         Level &Nx = h->lev[l + 1];
         int n = Lv.A.n;

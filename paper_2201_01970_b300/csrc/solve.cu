@@ -1176,6 +1176,7 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     int nb = h->nb;
     Level &L0 = h->lev[0];
     const int *order0 = h->lev.size() > 1 ? L0.rows_by_color.p : nullptr;
+    Nvtx nv("B application");
     // r_P = Pi_P^T v
     // level 0 is smoothed from zero unless it is the coarsest level
     bool fuse = h->lev.size() > 1 && h->opt.pre > 0;
@@ -1188,7 +1189,10 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
                  Vals<T>::b(L0), done);
     // e_P = B_P r_P (BILU positions)
     prof_begin(h, CPR_PROF_VCYCLE);
-    vcycle_top<T>(h, Vals<T>::ep(h), done, fuse);
+    {
+        Nvtx r("V-cycle");
+        vcycle_top<T>(h, Vals<T>::ep(h), done, fuse);
+    }
     prof_end(h);
     // r = v - A Pi_P e_P
     long threads = (long)nb * kResidLanes;
@@ -1199,7 +1203,10 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     prof_end(h);
     // z = Pi_P e_P + (LU)^-1 r
     prof_begin(h, CPR_PROF_BILU);
-    bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::ep(h), z_base, z_ld, jptr, done);
+    {
+        Nvtx r("BILU(0) sweeps");
+        bilu_solve<T>(h, Vals<T>::tmp(h), Vals<T>::ep(h), z_base, z_ld, jptr, done);
+    }
     prof_end(h);
 }
 
@@ -1536,6 +1543,7 @@ void ensure_step_graphs(cpr_handle *h) {
     unsigned pm = h->prof ? h->prof_mask : 0u;
     if (h->sg_epoch == h->epoch && h->sg_prof == pm && h->sg[0].exec && h->sg[1].exec) return;
     destroy_step_graphs(h);
+    Nvtx nv("capture Arnoldi step graphs");
     for (int k = 0; k < 2; k++) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -1577,6 +1585,7 @@ int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st
     double norm0 = 0.0, rnorm = 0.0;
     int ldp = kMaxRestart + 2;
     for (int cycle = 0; cycle < h->opt.max_restarts; cycle++) {
+        Nvtx nv("FGMRES cycle");
         // r = b - A x, beta = ||r||, V_0 = r / beta
         spmv_h(h, x, 0, nullptr, b, h->r.p, s, nullptr);
         norm_partials(h, h->r.p, N);

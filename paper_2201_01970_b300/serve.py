@@ -7,7 +7,9 @@ member across its Newton steps.  A fixed number of slots run requests
 concurrently: a request is admitted as soon as a slot is free, its member has
 no request in flight (a member's steps run in order), and the member's
 footprint fits the HBM budget -- least-recently-used idle members are evicted
-(their handles destroyed) to make room.  Work of different members overlaps on
+(their handles destroyed) to make room.  A request whose member could not fit
+even on an empty device is rejected at once (its `error` says why) instead of
+waiting for room that never comes.  Work of different members overlaps on
 the device; every kernel is deterministic, so a request's result does not
 depend on what else runs beside it.
 """
@@ -43,6 +45,7 @@ class Request:
     start: float = 0.0
     end: float = 0.0
     stats: dict = field(default_factory=dict)
+    error: str | None = None   # set when the request was rejected, not served
 
     @property
     def latency_ms(self) -> float:
@@ -61,6 +64,7 @@ class Server:
         self.bytes: dict[int, int] = {}
         self.last_used: dict[int, float] = {}
         self.evictions = 0
+        self.rejected = 0
         self.peak_bytes = 0
 
     def _resident(self) -> int:
@@ -130,6 +134,15 @@ class Server:
                         need = 0 if req.member in self.handles else footprint_bytes(
                             req.A.nb, int(req.A.col.shape[0]), self.opts.get("restart", 30),
                             bool(self.opts.get("precond_fp32", 1)))
+                        if need > self.budget:
+                            # no eviction can make room: reject rather than wait forever
+                            req.error = (f"footprint {need} bytes exceeds the HBM budget of "
+                                         f"{self.budget} bytes")
+                            req.start = req.end = now()
+                            self.rejected += 1
+                            pending.pop(k)
+                            launched = True
+                            break
                         if self._resident() + need > self.budget:
                             idle = sorted((m for m in self.handles if m not in busy_members),
                                           key=lambda m: self.last_used.get(m, 0.0))
@@ -162,13 +175,14 @@ class Server:
             th.join()
         if errors:
             raise errors[0]
-        makespan = max(r.end for r in requests) if requests else 0.0
-        lat = np.array([r.latency_ms for r in requests])
-        return {"requests": len(requests), "makespan_s": makespan,
-                "value": len(requests) / makespan if makespan else 0.0, "unit": "solves/s",
+        served = [r for r in requests if r.error is None]
+        makespan = max(r.end for r in served) if served else 0.0
+        lat = np.array([r.latency_ms for r in served]) if served else np.zeros(1)
+        return {"requests": len(served), "rejected": self.rejected, "makespan_s": makespan,
+                "value": len(served) / makespan if makespan else 0.0, "unit": "solves/s",
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_iters": float(np.mean([r.stats.get("iters", 0) for r in requests])),
-                "setups": int(sum(r.stats.get("setup_called", 0) for r in requests)),
+                "mean_iters": float(np.mean([r.stats.get("iters", 0) for r in served] or [0])),
+                "setups": int(sum(r.stats.get("setup_called", 0) for r in served)),
                 "evictions": self.evictions, "peak_resident_bytes": self.peak_bytes,
                 "slots": self.slots}
 

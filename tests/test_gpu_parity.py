@@ -14,8 +14,7 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-APPLY_TOL = 1e-10
-SOLVE_TOL = 1e-8
+from parity_helpers import APPLY_TOL, SOLVE_TOL, assert_apply_close, compare_hierarchy, rel
 
 
 @pytest.fixture(scope="module")
@@ -47,11 +46,6 @@ class DevJ:
         self.val = dev(torch, J.val)
 
 
-def rel(a, b):
-    a, b = np.asarray(a, float), np.asarray(b, float)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
-
-
 def ragged():
     return bs.jacobian(bs.GridSpec(37, 23, 9, 0.0, 1.5, 0.3, None, "five_spot", seed=5))
 
@@ -71,31 +65,6 @@ CASES = {
     "37x23x9": ragged,
     "tall_well": tall_well,
 }
-
-
-def compare_hierarchy(o, g):
-    assert g.nlev == o.nlev
-    for l in range(o.nlev):
-        ol, gl = o.level(l), g.level(l)
-        A = ol["A"]
-        assert gl["n"] == A.n and gl["nnz"] == len(A.col), l
-        np.testing.assert_array_equal(gl["rowptr"], A.rowptr)
-        np.testing.assert_array_equal(gl["col"], A.col)
-        np.testing.assert_array_equal(gl["val"], A.val)
-        if l < o.nlev - 1:
-            assert gl["ncolors"] == ol["ncolors"]
-            np.testing.assert_array_equal(gl["color"], ol["color"])
-            np.testing.assert_array_equal(gl["cf"], ol["cf"])
-            P = ol["P"]
-            np.testing.assert_array_equal(gl["prow"], P.rowptr)
-            np.testing.assert_array_equal(gl["pcol"], P.col)
-            np.testing.assert_array_equal(gl["pval"], P.val)
-    np.testing.assert_array_equal(g.weights(), o.weights())
-    gbc, gnc, glu = g.bilu()
-    obc, onc, olu = o.bilu()
-    assert gnc == onc
-    np.testing.assert_array_equal(gbc, obc)
-    np.testing.assert_array_equal(glu, olu)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -118,21 +87,21 @@ def test_components_match_oracle(torch, cpr, case):
     v = rng.standard_normal(J.n)
     z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
     g.apply(dev(torch, v), z)
-    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    assert_apply_close(z.cpu().numpy(), o.cpr_apply(v), what="B v")
     z2 = torch.zeros_like(z)
     g.apply(dev(torch, v), z2)
     assert torch.equal(z, z2)                        # run-to-run deterministic
     bp = rng.standard_normal(J.nb)
     xp = torch.zeros(J.nb, dtype=torch.float64, device="cuda")
     g.vcycle(dev(torch, bp), xp)
-    assert rel(xp.cpu().numpy(), o.vcycle(bp)) < APPLY_TOL
+    assert_apply_close(xp.cpu().numpy(), o.vcycle(bp), what="B_P b")
     g.bilu_apply(dev(torch, v), z)
-    assert rel(z.cpu().numpy(), o.bilu_apply(v)) < APPLY_TOL
+    assert_apply_close(z.cpu().numpy(), o.bilu_apply(v), what="R v")
     x = rng.standard_normal(J.n)
     y = cpr.bsr3_spmv(DevJ(torch, J), dev(torch, x))
-    assert rel(y.cpu().numpy(), oracle.bsr3_spmv(J, x)) < 1e-13
+    assert_apply_close(y.cpu().numpy(), oracle.bsr3_spmv(J, x), tol=1e-13, what="A x")
     r = cpr.bsr3_spmv(DevJ(torch, J), dev(torch, x), b=dev(torch, J.b))
-    assert rel(r.cpu().numpy(), J.b - oracle.bsr3_spmv(J, x)) < 1e-12
+    assert_apply_close(r.cpu().numpy(), J.b - oracle.bsr3_spmv(J, x), tol=1e-12, what="b - A x")
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -270,7 +239,7 @@ def test_full_size_128x128x32(torch, cpr):
     v = rng.standard_normal(J.n)
     z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
     g.apply(dev(torch, v), z)
-    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    assert_apply_close(z.cpu().numpy(), o.cpr_apply(v), what="B v")
     xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
     xg = xg.cpu().numpy()
     assert sg["converged"]
@@ -321,9 +290,9 @@ def test_natural_order_bilu_matches_oracle(torch, cpr, case):
     v = rng.standard_normal(J.n)
     z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
     g.bilu_apply(dev(torch, v), z)
-    assert rel(z.cpu().numpy(), o.bilu_apply(v)) < APPLY_TOL
+    assert_apply_close(z.cpu().numpy(), o.bilu_apply(v), what="R v")
     g.apply(dev(torch, v), z)
-    assert rel(z.cpu().numpy(), o.cpr_apply(v)) < APPLY_TOL
+    assert_apply_close(z.cpu().numpy(), o.cpr_apply(v), what="B v")
     xo, so = o.solve(J.b, rtol=1e-6)
     xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
     assert sg["converged"] and so["converged"]
@@ -371,7 +340,7 @@ def test_reuse_refresh_matches_oracle(torch, cpr):
         z = torch.zeros(J0.n, dtype=torch.float64, device="cuda")
         g.apply(dev(torch, v), z)
         zo = o.cpr_apply(v)
-        assert rel(z.cpu().numpy(), zo) < APPLY_TOL
+        assert_apply_close(z.cpu().numpy(), zo, what="kept B v")
         xo, so = o.solve(J1.b, rtol=1e-6)
         xg, sg = g.solve(dev(torch, J1.b), rtol=1e-6)
         assert sg["setup_called"] == 0 and so["setup_called"] == 0

@@ -58,3 +58,32 @@ def test_admission_by_hbm_budget_evicts_and_stays_correct(serve):
         assert r.stats["converged"]
         res = np.linalg.norm(r.A.b - oracle.bsr3_spmv(r.A, r.x)) / np.linalg.norm(r.A.b)
         assert res < 1e-6
+
+
+def test_served_results_match_the_oracle(serve):
+    """Each served request (FP64 preconditioner) against the oracle solving the
+    same member's Newton sequence in order under Alg. 3 with the same mu: the
+    same setup decisions while the iteration counts agree, iterations within
+    one, and x within 1e-8 when the counts are equal."""
+    from parity_helpers import SOLVE_TOL, rel
+    members = _members()[:3]
+    reqs = serve.poisson_requests(members, steps=3, rate=2000.0, seed=3)
+    s = serve.Server(slots=3, precond_fp32=0, mu=8)
+    s.run(reqs, realtime=True)
+    s.close()
+    for m in range(len(members)):
+        mine = sorted((r for r in reqs if r.member == m), key=lambda r: r.step)
+        o = oracle.Solver(mine[0].A, mu=8)
+        prev_equal = True
+        for k, r in enumerate(mine):
+            if k:
+                o.update(r.A)
+            xo, so = o.solve(r.A.b, rtol=1e-6)
+            if prev_equal:
+                assert r.stats["setup_called"] == so["setup_called"], (m, k)
+            assert r.stats["converged"] and so["converged"]
+            assert abs(r.stats["iters"] - so["iters"]) <= 1, (m, k, r.stats, so)
+            prev_equal = r.stats["iters"] == so["iters"]
+            if prev_equal:
+                assert rel(r.x, xo) < SOLVE_TOL, (m, k)
+        o.close()

@@ -105,3 +105,21 @@ def test_a_failed_solve_is_raised():
     with pytest.raises(RuntimeError, match="solve failed"):
         srv.run(reqs, realtime=False)
     srv.close()
+
+
+def test_a_request_larger_than_the_budget_is_rejected():
+    """Admission by HBM footprint: a member whose handle could not fit even on
+    an empty device is rejected with a reason, and the other requests are
+    served as usual (the loop does not wait for room that never comes)."""
+    small = requests(members=2, steps=2)
+    big = serve.Request(9, 0, SimpleNamespace(nb=10 ** 6, col=np.zeros(7 * 10 ** 6, np.int32), member=9),
+                        np.zeros(3), 0.0)
+    budget = 4 * serve.footprint_bytes(100, 500)
+    assert serve.footprint_bytes(10 ** 6, 7 * 10 ** 6) > budget
+    srv = FakeServer(slots=2, hbm_budget=budget)
+    res = srv.run(small + [big], realtime=False)
+    assert res["rejected"] == 1 and res["requests"] == 4
+    assert big.error and "exceeds the HBM budget" in big.error and big.x is None
+    assert all(r.error is None and r.stats for r in small)
+    assert ("open", 9) not in FakeSolver.log
+    srv.close()
