@@ -36,6 +36,15 @@ NSEQ = 4            # Jacobians of the drifting sequence kept resident in HBM
 RTOL = 1e-6
 MU = 30
 
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel the line rates, from one ncu capture of the build named, at the
+# workload named; a kernel changed since then has no entry (traffic null).
+NCU_TRAFFIC = {
+    ("k_sell_spmv", "128x128x32"): {"bytes": 302.63e6 + 9.98e6,
+                                    "source": "ncu capture of one k_sell_spmv launch of the commit cdabb71 "
+                                              "build (profiles/spmv_sell_128x128x32.md)"},
+}
+
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -482,14 +491,14 @@ def serve_arm(full: bool):
     from paper_2201_01970_b300 import serve
     members = bs.ensemble_specs(32, full=full)
     reqs = serve.poisson_requests(members, steps=5, rate=200.0, seed=0)
-    # 16 concurrent solves: each member's system is small (8k-65k cells), so
-    # one solve leaves most of the GPU idle; a slot sweep (4/8/12/16) measured
-    # 81/120/137/152 solves/s on this ensemble
+    # 16 concurrent solves: most members' systems are small (8k-524k cells),
+    # so one solve leaves most of the GPU idle; a slot sweep (4/8/12/16) on the
+    # scaled ensemble measured 81/120/137/152 solves/s
     srv = serve.Server(slots=16, precond_fp32=1, mu=MU)
     m = srv.run(reqs, realtime=True)
     srv.close()
     ok = all(r.stats.get("converged") for r in reqs)
-    base = serve.poisson_requests(members, steps=5, rate=200.0, seed=0)
+    base = [serve.Request(r.member, r.step, r.A, r.b, r.arrival) for r in reqs]
     srv = serve.Server(slots=1, precond_fp32=0, mu=0)
     mb = srv.run(base, realtime=False)
     srv.close()
@@ -554,65 +563,143 @@ def adaptive_sweep(cpr, torch, stream, mus=(0, 10, 20, 30, 40, 50, 60, 100), nse
             "nb": seq[0].nb, "nnzb": seq[0].nnzb, "runs": runs}
 
 
-def cpu_baseline(seq_host):
-    """The FP64 oracle, single-threaded on the host: one update (full setup, as
-    It > mu) and one solve of the same workload's second Jacobian."""
+def host_cpu():
+    """(logical CPUs, CPU model) of this host."""
+    model = "unknown"
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return os.cpu_count() or 1, model
+
+
+def cpu_baseline(seq_host, omp_samples=5):
+    """The FP64 oracle on the host, in the two forms of the CPU baseline: the
+    single-threaded build (one update+solve: the full setup, as It > mu, then
+    the solve) and the OpenMP build over every host core (rows within a color,
+    SpMV rows, vector updates; bit-identical results), median of
+    `omp_samples` update+solves of the sequence.  Setup and solve are timed
+    separately.  Returns the line's object and the OpenMP solution of the
+    sequence's second Jacobian (for the error of the GPU solutions)."""
     import oracle
-    oracle.build()
+    nproc, model = host_cpu()
+    S = len(seq_host)
     o = oracle.Solver(seq_host[0], mu=MU)
-    _, st0 = o.solve(seq_host[0].b, rtol=RTOL)
     t0 = time.perf_counter()
     o.update(seq_host[1])
-    _, st = o.solve(seq_host[1].b, rtol=RTOL)
-    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    _, st1 = o.solve(seq_host[1].b, rtol=RTOL)
+    t2 = time.perf_counter()
     o.close()
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one update+solve of a {WORKLOAD} Jacobian (setup_called={st['setup_called']}, "
-                      f"{st['iters']} iterations, {dt:.1f} s)"}
+    single = {"value": 1.0 / (t2 - t0), "unit": UNIT, "cores": 1, "setup_s": t1 - t0, "solve_s": t2 - t1,
+              "iters": st1["iters"], "samples": 1}
+    p = oracle.Solver(seq_host[0], mu=MU, omp=True)
+    threads = oracle.threads(True)
+    setups, solves, x_ref, iters = [], [], None, []
+    for k in range(omp_samples):
+        J = seq_host[1 + k % (S - 1)]
+        t0 = time.perf_counter()
+        p.update(J)
+        t1 = time.perf_counter()
+        x, st = p.solve(J.b, rtol=RTOL)
+        t2 = time.perf_counter()
+        if not st["setup_called"]:
+            raise RuntimeError("the CPU baseline's update kept B; every timed step must set up")
+        setups.append(t1 - t0)
+        solves.append(t2 - t1)
+        iters.append(st["iters"])
+        if k == 0:
+            x_ref = x
+    p.close()
+    tot = [a + b for a, b in zip(setups, solves)]
+    med = statistics.median(tot)
+    out = {"value": 1.0 / med, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "nproc": nproc, "cpu_model": model,
+           "sample": f"OpenMP oracle, median of {omp_samples} update+solves (full setup each, It > mu) "
+                     f"of the {WORKLOAD} sequence; single-threaded oracle: one update+solve",
+           "setup_s_median": statistics.median(setups), "solve_s_median": statistics.median(solves),
+           "iters": iters, "single_thread": single,
+           "paper_context": "paper (Xeon 8260 / Tesla T4, SPE10 3P): over 6.5x with 16 OpenMP threads, "
+                            "over 9.5x in CUDA, each against one thread"}
+    return out, x_ref
+
+
+def gpu_error_vs_oracle(cpr, torch, J_dev, J, x_ref, stream):
+    """Relative error, against the FP64 oracle's solution x_ref, of the GPU
+    solutions of the same Jacobian from zero to rtol (fresh handles, so B is
+    built from this Jacobian on both sides), in both preconditioner precisions."""
+    out = {}
+    b = torch.from_numpy(J.b).cuda()
+    for name, fp32 in (("fp32", 1), ("fp64", 0)):
+        s = cpr.Solver(J_dev, precond_fp32=fp32, mu=MU, stream=stream.cuda_stream)
+        x = torch.zeros_like(b)
+        _, st = s.solve(b, x, rtol=RTOL)
+        torch.cuda.synchronize()
+        xg = x.cpu().numpy()
+        s.close()
+        out[name] = {"rel_error": float(np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref)),
+                     "iters": st["iters"]}
+    out["note"] = ("||x_gpu - x_oracle|| / ||x_oracle|| on the sequence's second Jacobian, both solved "
+                   f"from zero to rtol {RTOL} with B built from that Jacobian")
+    return out
 
 
 # ---------------------------------------------------------- reference arm
 
 def reference_arm(args, rank, world):
-    """The FP64 oracle as the reference implementation, on the host cores.
-    Each step is one update+solve of a bounded sample of the workload: the
-    full grid when K+W full steps fit the time budget, else a z-slab of it
-    (the first nz' layers, same generator), scaled to the full grid by cells."""
+    """The FP64 oracle as the reference implementation, on the host cores (its
+    OpenMP build, bit-identical to the single-threaded one).  Each step is one
+    update+solve of the workload's drifting sequence, as in our arm.  The first
+    warm-up step is timed: when all K+W steps of the full workload would not
+    end within the budget, every step runs on a z-slab of the workload (the
+    first nz' layers, same generator) instead, reported as that slab with its
+    own measured times (nothing is scaled)."""
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    budget = 170.0
-    g = bs.CONFIGS[WORKLOAD]
-    t_full_est = 16.0
-    nz = max(1, min(g.nz, int(g.nz * budget / (max(1, args.steps + args.warmup) * t_full_est))))
     import dataclasses
-    gs = dataclasses.replace(g, nz=nz)
-    seq = list(bs.jacobian_sequence(gs, NSEQ, drift=0.05))
-    scale = g.ncells / gs.ncells
-    o = oracle.Solver(seq[0], mu=MU)
-    times = []
-    for k in range(args.warmup + args.steps):
-        J = seq[(k + 1) % NSEQ]
-        t0 = time.perf_counter()
-        o.update(J)
-        _, st = o.solve(J.b, rtol=RTOL)
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            times.append(dt)
-    o.close()
-    per_solve_full = statistics.mean(times) * scale
-    value = 1.0 / per_solve_full
-    sample = (f"{g.nx}x{g.ny}x{nz} slab of the {WORKLOAD} workload per step"
-              + (f", times scaled by {scale:.2f} (cells)" if scale != 1 else ""))
+    import oracle
+    budget = 200.0
+    g = bs.CONFIGS[WORKLOAD]
+    nsteps = args.steps + args.warmup
+
+    def run(gs, first_only=False):
+        seq = list(bs.jacobian_sequence(gs, NSEQ, drift=0.05))
+        o = oracle.Solver(seq[0], mu=MU, omp=True)
+        times = []
+        for k in range(1 if first_only else nsteps):
+            J = seq[(k + 1) % NSEQ]
+            t0 = time.perf_counter()
+            o.update(J)
+            _, st = o.solve(J.b, rtol=RTOL)
+            times.append(time.perf_counter() - t0)
+        o.close()
+        return times
+
+    t_first = run(g, first_only=True)[0]
+    gs = g
+    if t_first * nsteps > budget:
+        nz = max(1, int(g.nz * budget / (t_first * nsteps)))
+        gs = dataclasses.replace(g, nz=nz)
+    times = run(gs)[args.warmup:]
+    per = statistics.mean(times)
+    value = 1.0 / per
+    nproc, model = host_cpu()
+    threads = oracle.threads(True)
+    wl = (f"{WORKLOAD} synthetic black-oil, drifting Newton sequence" if gs is g else
+          f"{g.nx}x{g.ny}x{gs.nz} z-slab of the {WORKLOAD} workload (the full grid would not fit "
+          f"{nsteps} steps in {budget:.0f} s: {t_first:.1f} s per step)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * per_solve_full,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * per,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD} synthetic black-oil, drifting Newton sequence",
-                       "mu": MU, "rtol": RTOL, "restart": 30},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "config": {"workload": wl, "mu": MU, "rtol": RTOL, "restart": 30},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "nproc": nproc, "cpu_model": model,
+                             "sample": f"each step one update+solve of the {wl} (OpenMP oracle, "
+                                       f"{threads} threads); first full-size step {t_first:.2f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -637,8 +724,9 @@ def main():
                     help="only time setups of the workload, the last one bracketed for ncu and phase-marked")
     ap.add_argument("--no-resetup-numeric", action="store_true",
                     help="skip the numeric-only resetup line")
-    ap.add_argument("--serve-full", action="store_true",
-                    help="serving ensemble over the full 32x32x8..128x128x32 range")
+    ap.add_argument("--serve-scaled", action="store_true",
+                    help="serving ensemble over the scaled 32x32x8..64x64x16 range instead of the full "
+                         "32x32x8..128x128x32 one")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
                     help="precision arms to time (the JSON line needs both)")
     ap.add_argument("--adaptive-sweep", action="store_true",
@@ -714,7 +802,7 @@ def main():
 
     e2e = None if args.no_e2e else e2e_arm(cpr, torch, seq_host, max(3, K // 2), 1, stream)
     batched = None if args.no_batch else batched_arm(cpr, torch, max(3, K // 2), stream)
-    serving = None if args.no_serve else serve_arm(args.serve_full)
+    serving = None if args.no_serve else serve_arm(not args.serve_scaled)
     natural = None if args.no_bilu_natural else option_arm(
         cpr, torch, seq_dev, rhs_dev, max(3, K // 3), W, stream,
         "bilu_order = 1: the paper's level-scheduled second stage, one launch per level set", bilu_order=1)
@@ -722,9 +810,10 @@ def main():
         cpr, torch, seq_dev, rhs_dev, K, W, stream,
         "resetup = 1: each rebuild keeps the first setup's levels, strength sets, C/F splits and colorings "
         "and recomputes the values", resetup=1)
-    cpu = None
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(seq_host)
+        cpu, x_ref = cpu_baseline(seq_host)
+        err = gpu_error_vs_oracle(cpr, torch, seq_dev[1], seq_host[1], x_ref, stream)
 
     t32 = max_over_ranks(r32["total_ms"], world)
     t64 = max_over_ranks(r64["total_ms"], world)
@@ -775,20 +864,27 @@ def main():
     sm0 = f32.get("smooth0", {})
     sp = f32.get("spmv", {})
     # The outer SpMV is the largest single kernel of the step (launch-list
-    # share); its bound is B300's FP64 pipe (91 % active under ncu).  Peak: the
-    # FP64 FMA rate ncu reports for this GPU (296 DFMA thread-instructions per
-    # cycle) x 2 flops x the maximum SM clock.  traffic: dram__bytes_read.sum +
-    # dram__bytes_write.sum of one launch of k_sell_spmv from the ncu capture
-    # summarised in profiles/spmv_sell_128x128x32.md (290.51 MB read + 9.96 MB written).
+    # share).  Its roofline is HBM: the algorithmic bytes of one launch,
+    # 76 nnzb + 52 nb (FP64 values and column of every block, x, y and the
+    # slice offsets), over its live average duration, against the measured
+    # copy bandwidth.  B300's FP64 pipe is its other limit (about 91 % busy
+    # under ncu), reported beside it: 18 nnzb flops against 296 DFMA
+    # thread-instructions per cycle x 2 x the maximum SM clock.
     fp64_peak = 296 * 2 * 2.032e9 / 1e12
     spmv_tflops = (18.0 * nnzb / (sp["avg_us"] * 1e-6) / 1e12) if sp.get("avg_us") else None
-    roof = {"kernel": "k_sell_spmv (outer FP64 SpMV on the sliced-ELL copy, w = A z)", "bound": "alu",
-            "achieved": spmv_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
-            "peak_kind": "FP64 FMA rate x max SM clock (derived, ncu sm__sass_thread_inst_executed_op_dfma_pred_on peak)",
-            "traffic": 300.47e6 if WORKLOAD == "128x128x32" else None,
-            "flops_per_launch": 18.0 * nnzb, "bytes_per_launch": spmv_bytes(nb, nnzb),
-            "hbm_gbs": sp.get("gbs"), "hbm_frac_of_measured": (sp.get("gbs") / hbm) if sp.get("gbs") else None}
+    tr = NCU_TRAFFIC.get(("k_sell_spmv", WORKLOAD))
+    roof = {"kernel": "k_sell_spmv (outer FP64 SpMV on the sliced-ELL copy, w = A z)", "bound": "hbm",
+            "achieved": sp.get("gbs"), "peak": hbm, "unit": "GB/s",
+            "frac": (sp.get("gbs") / hbm) if sp.get("gbs") else None,
+            "peak_kind": f"{peak_kind} hbm_gbs (of {peak_kind})",
+            "bytes_per_launch": spmv_bytes(nb, nnzb), "avg_us": sp.get("avg_us"),
+            "traffic": tr["bytes"] if tr else None,
+            "traffic_source": tr["source"] if tr else None,
+            "fp64_pipe": {"achieved": spmv_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                          "frac": spmv_tflops / fp64_peak if spmv_tflops else None,
+                          "flops_per_launch": 18.0 * nnzb,
+                          "peak_kind": "FP64 FMA rate x max SM clock (derived from the ncu peak of "
+                                       "sm__sass_thread_inst_executed_op_dfma_pred_on)"}}
     roof_sm = {"kernel": "k_smooth_color on the finest pressure level (multi-color GS color sweep, FP32)",
                "bound": "hbm", "achieved": sm0.get("gbs"), "peak": hbm, "unit": "GB/s",
                "frac": (sm0.get("gbs") / hbm) if sm0.get("gbs") else None,
@@ -830,6 +926,7 @@ def main():
                              "the level-0 sweeps (smooth0), nested in the V-cycle, in a further pass of their own"},
         "roofline": roof,
         "roofline_smoother_level0": roof_sm,
+        "vcycle_hbm_frac_fp32": (f32.get("vcycle", {}).get("gbs") or 0) / hbm,
         "gpu_launches": int(r32["launches"]),
         "clocks": clocks,
     }
@@ -845,6 +942,8 @@ def main():
         line["resetup_numeric"] = numeric
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if err is not None:
+        line["error_vs_oracle"] = err
     if rank == 0:
         print(json.dumps(line), flush=True)
 

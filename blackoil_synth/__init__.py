@@ -267,11 +267,15 @@ _PATTERN_CACHE: dict = {}
 
 
 def _pattern(g: GridSpec) -> _Pattern:
+    """The last grid's pattern is kept; safe to call from several threads (a
+    miss may build the pattern twice, never returns another grid's)."""
     key = (g.nx, g.ny, g.nz, g.wells)
-    if key not in _PATTERN_CACHE:
+    pat = _PATTERN_CACHE.get(key)
+    if pat is None:
+        pat = _Pattern(g)
         _PATTERN_CACHE.clear()
-        _PATTERN_CACHE[key] = _Pattern(g)
-    return _PATTERN_CACHE[key]
+        _PATTERN_CACHE[key] = pat
+    return pat
 
 
 def jacobian_sequence(g: GridSpec, nsteps: int, drift: float = 0.05):

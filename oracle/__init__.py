@@ -24,16 +24,25 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so in-tree (gcc, -ffp-contract=off: no fused multiply-add)."""
-    stale = (not os.path.exists(_LIB)
-             or os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_FLAGS = ["-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-Wno-unused-function"]
+
+
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile liboracle.so in-tree (gcc, -ffp-contract=off: no fused multiply-add).
+
+    omp=True builds liboracle_omp.so, the same source with OpenMP over the
+    loops marked independent (-fopenmp -march=native): the CPU baseline's
+    multi-threaded form, bit-identical to the single-threaded library."""
+    out = _LIB_OMP if omp else _LIB
+    stale = (not os.path.exists(out)
+             or os.path.getmtime(out) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        tmp = out + f".tmp{os.getpid()}"
+        extra = ["-fopenmp", "-march=native"] if omp else []
+        subprocess.check_call(["gcc", *_FLAGS, *extra, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Opts(C.Structure):
@@ -55,13 +64,13 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
+def lib(omp: bool = False):
+    """The oracle library: single-threaded, or the OpenMP build (omp=True)."""
+    if omp not in _libs:
+        L = C.CDLL(build(omp=omp))
         vp = C.c_void_p
         L.o_csr_n.argtypes = [vp]
         L.o_csr_ncol.argtypes = [vp]
@@ -114,8 +123,8 @@ def lib():
         L.o_cpr_apply.argtypes = [vp, _f64p, _f64p]
         L.o_vcycle.argtypes = [vp, _f64p, _f64p]
         L.o_bilu_apply.argtypes = [vp, _f64p, _f64p]
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
 
 
 def default_opts(**kw) -> Opts:
@@ -186,6 +195,11 @@ def jp_color(G: CSR, seed=0, salt=0, level=0):
     color = np.zeros(G.n, np.int32)
     nc = lib().o_jp_color(G.n, _i32(G.rowptr), _i32(G.col), seed, salt, level, color)
     return color, nc
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the chosen build's parallel loops run on."""
+    return int(lib(omp).o_threads())
 
 
 def fmix32(h) -> int:
@@ -315,19 +329,20 @@ def fgmres_identity(J, b, x0=None, rtol=1e-10, m=30, max_restarts=100):
 class Solver:
     """CPR-FGMRES with adaptive setup (Alg. 2 + Alg. 3), FP64 on the CPU."""
 
-    def __init__(self, J, **opts):
+    def __init__(self, J, omp: bool = False, **opts):
+        self._L = lib(omp)
         self.opts = default_opts(**opts)
         self._h = C.c_void_p()
         self._keep = (_i32(J.rowptr), _i32(J.col), _f64(J.val))
         self.nb = J.nb
         self.nnzb = J.nnzb
-        rc = lib().o_setup(C.byref(self._h), J.nb, *self._keep, C.byref(self.opts))
+        rc = self._L.o_setup(C.byref(self._h), J.nb, *self._keep, C.byref(self.opts))
         if rc != 0:
             raise RuntimeError(f"oracle setup failed ({rc})")
 
     def update(self, J):
         self._keep = (_i32(J.rowptr), _i32(J.col), _f64(J.val))
-        rc = lib().o_update(self._h, J.nb, *self._keep)
+        rc = self._L.o_update(self._h, J.nb, *self._keep)
         if rc != 0:
             raise RuntimeError(f"oracle update failed ({rc})")
         self.nb, self.nnzb = J.nb, J.nnzb
@@ -335,7 +350,7 @@ class Solver:
     def solve(self, b, x0=None, rtol=1e-6):
         x = np.zeros(3 * self.nb) if x0 is None else _f64(x0).copy()
         st = Stats()
-        rc = lib().o_solve(self._h, _f64(b), x, rtol, C.byref(st))
+        rc = self._L.o_solve(self._h, _f64(b), x, rtol, C.byref(st))
         if rc < 0:
             raise RuntimeError(f"oracle solve failed ({rc})")
         return x, st.as_dict()
@@ -345,7 +360,7 @@ class Solver:
         batch) with this handle's B restricted to them."""
         x = np.zeros(3 * (r1 - r0)) if x0 is None else _f64(x0).copy()
         st = Stats()
-        rc = lib().o_solve_rows(self._h, r0, r1, _f64(b), x, rtol, C.byref(st))
+        rc = self._L.o_solve_rows(self._h, r0, r1, _f64(b), x, rtol, C.byref(st))
         if rc < 0:
             raise RuntimeError(f"oracle solve_rows failed ({rc})")
         return x, st.as_dict()
@@ -353,11 +368,11 @@ class Solver:
     # inspection
     @property
     def nlev(self) -> int:
-        return lib().o_num_levels(self._h)
+        return self._L.o_num_levels(self._h)
 
     def level(self, l: int) -> dict:
         n, nnz, ncol, nc, nnzp = (C.c_int() for _ in range(5))
-        lib().o_level_info(self._h, l, C.byref(n), C.byref(nnz), C.byref(ncol), C.byref(nc),
+        self._L.o_level_info(self._h, l, C.byref(n), C.byref(nnz), C.byref(ncol), C.byref(nc),
                            C.byref(nnzp))
         n, nnz, ncolors, nc, nnzp = n.value, nnz.value, ncol.value, nc.value, nnzp.value
         rp = np.zeros(n + 1, np.int32)
@@ -369,7 +384,7 @@ class Solver:
         pcol = np.zeros(nnzp, np.int32)
         pval = np.zeros(nnzp)
         has_p = nnzp > 0 or nc > 0
-        lib().o_level_get(self._h, l, rp, cl, v, color.ctypes.data if ncolors else None,
+        self._L.o_level_get(self._h, l, rp, cl, v, color.ctypes.data if ncolors else None,
                           cf.ctypes.data if has_p else None, prow.ctypes.data if has_p else None,
                           pcol.ctypes.data if has_p else None, pval.ctypes.data if has_p else None)
         out = {"A": CSR(n, n, rp, cl, v), "ncolors": ncolors, "color": color if ncolors else None}
@@ -379,37 +394,37 @@ class Solver:
 
     def weights(self):
         w = np.zeros(3 * self.nb)
-        lib().o_get_weights(self._h, w)
+        self._L.o_get_weights(self._h, w)
         return w
 
     def bilu(self):
         bc = np.zeros(self.nb, np.int32)
         lu = np.zeros(9 * self.nnzb)
-        lib().o_bilu_get(self._h, bc, lu)
-        return bc, lib().o_bilu_ncolors(self._h), lu
+        self._L.o_bilu_get(self._h, bc, lu)
+        return bc, self._L.o_bilu_ncolors(self._h), lu
 
     def cpr_apply(self, v):
         z = np.zeros(3 * self.nb)
-        lib().o_cpr_apply(self._h, _f64(v), z)
+        self._L.o_cpr_apply(self._h, _f64(v), z)
         return z
 
     def vcycle(self, b):
         x = np.zeros(len(b))
-        lib().o_vcycle(self._h, _f64(b), x)
+        self._L.o_vcycle(self._h, _f64(b), x)
         return x
 
     def bilu_apply(self, r):
         z = np.zeros(3 * self.nb)
-        lib().o_bilu_apply(self._h, _f64(r), z)
+        self._L.o_bilu_apply(self._h, _f64(r), z)
         return z
 
     @property
     def last_iters(self) -> int:
-        return lib().o_last_iters(self._h)
+        return self._L.o_last_iters(self._h)
 
     def close(self):
         if self._h:
-            lib().o_destroy(self._h)
+            self._L.o_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

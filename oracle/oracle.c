@@ -38,6 +38,30 @@
 
 #define MAXLEV 32
 
+/*
+ * OMP_FOR marks loops whose iterations are independent: rows of one SpMV, the
+ * rows of one color of a multi-color sweep or BILU(0) solve, and element-wise
+ * vector updates.  Built with -fopenmp (the CPU baseline's multi-threaded
+ * form) they run across threads; every iteration still does its own
+ * arithmetic in the same order, so results are bit-identical to the
+ * single-threaded build.  Dot products stay serial for the same reason.
+ */
+#ifdef _OPENMP
+#include <omp.h>
+#define OMP_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OMP_FOR
+#endif
+
+/* Threads the marked loops use: OpenMP's count in the multi-threaded build, 1 otherwise. */
+int o_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 struct o_csr {
     int n, ncol, nnz;
     int *rowptr, *col;
@@ -205,6 +229,7 @@ static int mat3_inv(const double *a, double *inv) {
 /* y = A x for a 3x3 BSR matrix (Eq. 2.8 layout). */
 void o_bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val,
                  const double *x, double *y) {
+    OMP_FOR
     for (int i = 0; i < nb; i++) {
         double s[3] = {0.0, 0.0, 0.0};
         for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
@@ -222,6 +247,7 @@ void o_bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val,
 static void bsr3_resid(int nb, const int *rowptr, const int *col, const double *val,
                        const double *b, const double *x, double *r) {
     o_bsr3_spmv(nb, rowptr, col, val, x, r);
+    OMP_FOR
     for (int i = 0; i < 3 * nb; i++) r[i] = b[i] - r[i];
 }
 
@@ -724,6 +750,7 @@ static void mcgs_sweep(const o_csr *A, const int *color, int ncolors, const doub
                        double *x, int descending, double *tmp) {
     for (int t = 0; t < ncolors; t++) {
         int c = descending ? ncolors - 1 - t : t;
+        OMP_FOR
         for (int i = 0; i < A->n; i++) {
             if (color[i] != c) continue;
             double s = b[i], d = 0.0;
@@ -734,6 +761,7 @@ static void mcgs_sweep(const o_csr *A, const int *color, int ncolors, const doub
             }
             tmp[i] = s / d;
         }
+        OMP_FOR
         for (int i = 0; i < A->n; i++)
             if (color[i] == c) x[i] = tmp[i];
     }
@@ -1253,44 +1281,70 @@ static int bilu0_factor(int nb, const int *rowptr, const int *col, const double 
     return rc;
 }
 
-/* Solve (L U) z = r: forward then backward substitution in (color, index) order. */
+/* Row t (position in (color, index) order) of the forward substitution. */
+static void bilu_fwd_row(int t, const int *order, const int *pos, const int *rowptr, const int *col,
+                         const double *lu, const double *r, double *y) {
+    int i = order[t];
+    double s[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+        int j = col[p];
+        if (pos[j] >= t) continue;
+        const double *L = lu + 9 * (size_t)p;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) s[a] -= L[3 * a + b] * y[3 * j + b];
+    }
+    y[3 * i] = s[0];
+    y[3 * i + 1] = s[1];
+    y[3 * i + 2] = s[2];
+}
+
+/* Row t of the backward substitution. */
+static void bilu_bwd_row(int t, const int *order, const int *pos, const int *rowptr, const int *col,
+                         const double *lu, const double *y, double *z) {
+    int i = order[t];
+    double s[3] = {y[3 * i], y[3 * i + 1], y[3 * i + 2]};
+    const double *Dinv = NULL;
+    for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
+        int j = col[p];
+        if (j == i) {
+            Dinv = lu + 9 * (size_t)p;
+            continue;
+        }
+        if (pos[j] < t) continue;
+        const double *U = lu + 9 * (size_t)p;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) s[a] -= U[3 * a + b] * z[3 * j + b];
+    }
+    for (int a = 0; a < 3; a++)
+        z[3 * i + a] = (Dinv[3 * a] * s[0] + Dinv[3 * a + 1] * s[1]) + Dinv[3 * a + 2] * s[2];
+}
+
+/* Solve (L U) z = r: forward then backward substitution in (color, index)
+ * order.  With a proper coloring (more than one color) the rows of one color
+ * never reference each other, so each color's rows are independent; with one
+ * color (the natural order) the rows run strictly in sequence. */
 void o_bilu0_solve(int nb, const int *rowptr, const int *col, const double *lu,
                    const int *bcolor, int nbcolors, const double *r, double *z) {
     int *order = xcalloc((size_t)nb, sizeof(int));
     int *pos = xcalloc((size_t)nb, sizeof(int));
     color_order(nb, bcolor, nbcolors, order, pos);
     double *y = xcalloc(3 * (size_t)nb, sizeof(double));
-    for (int t = 0; t < nb; t++) {
-        int i = order[t];
-        double s[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
-        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
-            int j = col[p];
-            if (pos[j] >= t) continue;
-            const double *L = lu + 9 * (size_t)p;
-            for (int a = 0; a < 3; a++)
-                for (int b = 0; b < 3; b++) s[a] -= L[3 * a + b] * y[3 * j + b];
+    if (nbcolors > 1) {
+        int *off = xcalloc((size_t)nbcolors + 1, sizeof(int));
+        for (int i = 0; i < nb; i++) off[bcolor[i] + 1]++;
+        for (int c = 0; c < nbcolors; c++) off[c + 1] += off[c];
+        for (int c = 0; c < nbcolors; c++) {
+            OMP_FOR
+            for (int t = off[c]; t < off[c + 1]; t++) bilu_fwd_row(t, order, pos, rowptr, col, lu, r, y);
         }
-        y[3 * i] = s[0];
-        y[3 * i + 1] = s[1];
-        y[3 * i + 2] = s[2];
-    }
-    for (int t = nb - 1; t >= 0; t--) {
-        int i = order[t];
-        double s[3] = {y[3 * i], y[3 * i + 1], y[3 * i + 2]};
-        const double *Dinv = NULL;
-        for (int p = rowptr[i]; p < rowptr[i + 1]; p++) {
-            int j = col[p];
-            if (j == i) {
-                Dinv = lu + 9 * (size_t)p;
-                continue;
-            }
-            if (pos[j] < t) continue;
-            const double *U = lu + 9 * (size_t)p;
-            for (int a = 0; a < 3; a++)
-                for (int b = 0; b < 3; b++) s[a] -= U[3 * a + b] * z[3 * j + b];
+        for (int c = nbcolors - 1; c >= 0; c--) {
+            OMP_FOR
+            for (int t = off[c]; t < off[c + 1]; t++) bilu_bwd_row(t, order, pos, rowptr, col, lu, y, z);
         }
-        for (int a = 0; a < 3; a++)
-            z[3 * i + a] = (Dinv[3 * a] * s[0] + Dinv[3 * a + 1] * s[1]) + Dinv[3 * a + 2] * s[2];
+        free(off);
+    } else {
+        for (int t = 0; t < nb; t++) bilu_fwd_row(t, order, pos, rowptr, col, lu, r, y);
+        for (int t = nb - 1; t >= 0; t--) bilu_bwd_row(t, order, pos, rowptr, col, lu, y, z);
     }
     free(y);
     free(order);
@@ -1568,9 +1622,11 @@ static void vcycle(o_handle *h, int l, const double *b, double *x) {
         dense_lu_solve(n, h->clu, h->cpiv, b, x);
         return;
     }
+    OMP_FOR
     for (int i = 0; i < n; i++) x[i] = 0.0;
     for (int s = 0; s < h->opt.pre; s++) mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 0, L->tmp);
     /* r = b - A x, b_c = R r */
+    OMP_FOR
     for (int i = 0; i < n; i++) {
         double s = b[i];
         for (int p = L->A.rowptr[i]; p < L->A.rowptr[i + 1]; p++)
@@ -1578,6 +1634,7 @@ static void vcycle(o_handle *h, int l, const double *b, double *x) {
         L->r[i] = s;
     }
     level_t *Lc = &h->lev[l + 1];
+    OMP_FOR
     for (int I = 0; I < L->R.n; I++) {
         double s = 0.0;
         for (int p = L->R.rowptr[I]; p < L->R.rowptr[I + 1]; p++)
@@ -1586,6 +1643,7 @@ static void vcycle(o_handle *h, int l, const double *b, double *x) {
     }
     vcycle(h, l + 1, Lc->b, Lc->x);
     /* x += P x_c */
+    OMP_FOR
     for (int i = 0; i < n; i++) {
         double s = 0.0;
         for (int p = L->P.rowptr[i]; p < L->P.rowptr[i + 1]; p++)
@@ -1653,8 +1711,10 @@ static void kcycle(o_handle *h, int l, const double *b, double *x) {
         dense_lu_solve(n, h->clu, h->cpiv, b, x);
         return;
     }
+    OMP_FOR
     for (int i = 0; i < n; i++) x[i] = 0.0;
     for (int s = 0; s < h->opt.pre; s++) mcgs_sweep(&L->A, L->color, L->ncolors, b, x, 0, L->tmp);
+    OMP_FOR
     for (int i = 0; i < n; i++) {
         double s = b[i];
         for (int p = L->A.rowptr[i]; p < L->A.rowptr[i + 1]; p++)
@@ -1662,6 +1722,7 @@ static void kcycle(o_handle *h, int l, const double *b, double *x) {
         L->r[i] = s;
     }
     level_t *Lc = &h->lev[l + 1];
+    OMP_FOR
     for (int I = 0; I < L->R.n; I++) {
         double s = 0.0;
         for (int p = L->R.rowptr[I]; p < L->R.rowptr[I + 1]; p++)
@@ -1670,6 +1731,7 @@ static void kcycle(o_handle *h, int l, const double *b, double *x) {
     }
     if (l + 1 == h->nlev - 1) dense_lu_solve(Lc->A.n, h->clu, h->cpiv, Lc->b, Lc->x);
     else amli_coarse(h, l + 1, Lc->b, Lc->x);
+    OMP_FOR
     for (int i = 0; i < n; i++) {
         double s = 0.0;
         for (int p = L->P.rowptr[i]; p < L->P.rowptr[i + 1]; p++)
@@ -1693,10 +1755,12 @@ static void pressure_cycle(o_handle *h, const double *b, double *x) {
  */
 static void cpr_apply(o_handle *h, const double *v, double *z) {
     int nb = h->nb;
+    OMP_FOR
     for (int i = 0; i < nb; i++)
         h->rp[i] = (h->w[3 * i] * v[3 * i] + h->w[3 * i + 1] * v[3 * i + 1]) +
                    h->w[3 * i + 2] * v[3 * i + 2];
     pressure_cycle(h, h->rp, h->ep);
+    OMP_FOR
     for (int i = 0; i < nb; i++) {
         z[3 * i] = h->ep[i];
         z[3 * i + 1] = 0.0;
@@ -1704,6 +1768,7 @@ static void cpr_apply(o_handle *h, const double *v, double *z) {
     }
     bsr3_resid(nb, h->rowptr, h->col, h->pval, v, z, h->work1);
     o_bilu0_solve(nb, h->rowptr, h->col, h->lu, h->bcolor, h->nbcolors, h->work1, h->work2);
+    OMP_FOR
     for (int i = 0; i < 3 * nb; i++) z[i] += h->work2[i];
 }
 
@@ -1766,6 +1831,7 @@ static int fgmres(int nb, const int *rowptr, const int *col, const double *val, 
     }
     for (cycles = 0; cycles < max_restarts; cycles++) {
         double beta = rnorm;
+        OMP_FOR
         for (int i = 0; i < n; i++) V[i] = r[i] / beta;
         for (int i = 0; i <= m; i++) g[i] = 0.0;
         g[0] = beta;
@@ -1775,11 +1841,10 @@ static int fgmres(int nb, const int *rowptr, const int *col, const double *val, 
             pc(pctx, vj, zj);
             o_bsr3_spmv(nb, rowptr, col, val, zj, w);
             for (int i = 0; i <= j; i++) H[i * m + j] = dot(n, w, V + (size_t)i * n);
-            for (int i = 0; i <= j; i++) {
-                double hij = H[i * m + j];
-                const double *vi = V + (size_t)i * n;
-                for (int q = 0; q < n; q++) w[q] -= hij * vi[q];
-            }
+            /* w -= sum_i h_ij v_i, each entry taking i in ascending order */
+            OMP_FOR
+            for (int q = 0; q < n; q++)
+                for (int i = 0; i <= j; i++) w[q] -= H[i * m + j] * V[(size_t)i * n + q];
             double hn = sqrt(dot(n, w, w));
             H[(j + 1) * m + j] = hn;
             iters++;
@@ -1804,6 +1869,7 @@ static int fgmres(int nb, const int *rowptr, const int *col, const double *val, 
             g[j] = cs[j] * g[j];
             if (hist) hist[iters - 1] = fabs(g[j + 1]) / norm0;
             if (hn == 0.0) break;
+            OMP_FOR
             for (int q = 0; q < n; q++) V[(size_t)(j + 1) * n + q] = w[q] / hn;
             if (fabs(g[j + 1]) / norm0 < rtol) break;
         }
@@ -1813,10 +1879,9 @@ static int fgmres(int nb, const int *rowptr, const int *col, const double *val, 
             for (int q = i + 1; q < k; q++) s -= H[i * m + q] * y[q];
             y[i] = s / H[i * m + i];
         }
-        for (int i = 0; i < k; i++) {
-            const double *zi = Z + (size_t)i * n;
-            for (int q = 0; q < n; q++) x[q] += y[i] * zi[q];
-        }
+        OMP_FOR
+        for (int q = 0; q < n; q++)
+            for (int i = 0; i < k; i++) x[q] += y[i] * Z[(size_t)i * n + q];
         bsr3_resid(nb, rowptr, col, val, b, x, r);
         rnorm = sqrt(dot(n, r, r));
         if (!isfinite(rnorm)) {

@@ -193,13 +193,18 @@ class Server:
         self.bytes.clear()
 
 
-def poisson_requests(members: list, steps: int, rate: float, seed: int = 0, drift: float = 0.05):
+def poisson_requests(members: list, steps: int, rate: float, seed: int = 0, drift: float = 0.05,
+                     workers: int = 8):
     """Requests of `steps` drifting Jacobians per member, arrivals a Poisson
     process of `rate` per second (seeded exponential gaps); a member's steps
     arrive in order."""
     import blackoil_synth as bs
+    from concurrent.futures import ThreadPoolExecutor
     rng = np.random.Generator(np.random.PCG64([seed, 7]))
-    seqs = {m: list(bs.jacobian_sequence(g, steps, drift)) for m, g in enumerate(members)}
+    # members are generated independently (each from its own seed), on threads
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        lists = list(ex.map(lambda g: list(bs.jacobian_sequence(g, steps, drift)), members))
+    seqs = dict(enumerate(lists))
     order = [(m, k) for k in range(steps) for m in range(len(members))]
     rng.shuffle(order)
     # keep each member's steps in order

@@ -1089,3 +1089,23 @@ def test_solve_rows_on_a_block_diagonal_system():
     with pytest.raises(RuntimeError):
         exact.solve_rows(0, J1.nb + 1, np.zeros(3 * J1.nb + 3))   # couples into the next system
     exact.close()
+
+
+def test_openmp_build_is_bit_identical():
+    """The CPU baseline's multi-threaded oracle (OpenMP over rows within a
+    color, SpMV rows and element-wise vector updates) computes every value in
+    the single-threaded order: B v, the BILU(0) solve, the V-cycle and whole
+    solves agree bit for bit, multicolor and natural-order BILU alike."""
+    for J, kw in ((bs.jacobian("20x20x5"), {}), (bs.jacobian(bs.GridSpec(37, 23, 9, seed=5)), {}),
+                  (bs.jacobian("20x20x5"), {"bilu_order": 1})):
+        a, b = oracle.Solver(J, **kw), oracle.Solver(J, omp=True, **kw)
+        v = np.random.default_rng(2).standard_normal(J.n)
+        np.testing.assert_array_equal(a.cpr_apply(v), b.cpr_apply(v))
+        np.testing.assert_array_equal(a.bilu_apply(v), b.bilu_apply(v))
+        np.testing.assert_array_equal(a.vcycle(v[:J.nb]), b.vcycle(v[:J.nb]))
+        xa, sa = a.solve(J.b, rtol=1e-8)
+        xb, sb = b.solve(J.b, rtol=1e-8)
+        assert sa == sb
+        np.testing.assert_array_equal(xa, xb)
+        a.close()
+        b.close()
