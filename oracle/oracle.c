@@ -965,10 +965,13 @@ static void heap_pop(heap_t *q, long *key, int *node) {
  * pointers pair up; an unmatched node with no unmatched candidate stays
  * alone.  The smallest remaining edge is always mutual, so every round pairs
  * or settles at least one node.  Aggregates are numbered by their smallest
- * node.
+ * node.  With `attach` (agg_match = 2) a node left alone joins the pair of
+ * its best candidate, if it has one (see below): rounds alone leave many
+ * singletons on heterogeneous media, and they pile up level after level
+ * until coarsening stalls, which the greedy matching does not do.
  */
 static int handshake_match(int n, const int *srow, const int *scol, const double *sval, uint32_t hb,
-                           int *agg) {
+                           int attach, int *agg) {
     /* the symmetric candidate lists with their couplings */
     int *crow = xcalloc((size_t)n + 1, sizeof(int));
     for (int i = 0; i < n; i++)
@@ -1027,11 +1030,53 @@ static int handshake_match(int n, const int *srow, const int *scol, const double
     }
     int na = 0;
     for (int i = 0; i < n; i++) agg[i] = -1;
-    for (int i = 0; i < n; i++) {
-        if (agg[i] >= 0) continue;
-        agg[i] = na;
-        if (mate[i] >= 0) agg[mate[i]] = na;
-        na++;
+    if (attach) {
+        /* agg_match = 2: a node left alone that has a candidate joins the pair
+           of its candidate of smallest edge key (every candidate of a node left
+           alone is paired: an unmatched candidate would still have been one,
+           and the two would have pointed somewhere).  A pair may take several
+           such nodes.  Pairs and the nodes with no candidate at all are
+           numbered by their smallest node; a joining node takes its host
+           pair's number. */
+        int *host = xcalloc((size_t)n, sizeof(int));
+        for (int i = 0; i < n; i++) {
+            host[i] = -1;
+            if (mate[i] != -1) continue;
+            double bc = 0.0;
+            uint32_t blo = 0, bhi = 0;
+            int bj = -1;
+            for (int t = crow[i]; t < crow[i + 1]; t++) {
+                int j = cc[t];
+                if (j == i) continue;
+                uint32_t hi_ = fmix32((uint32_t)i ^ hb), hj = fmix32((uint32_t)j ^ hb);
+                uint32_t lo = hi_ < hj ? hi_ : hj, hi = hi_ < hj ? hj : hi_;
+                int better = bj < 0 || cv[t] < bc ||
+                             (cv[t] == bc && (lo < blo || (lo == blo && (hi < bhi || (hi == bhi && j < bj)))));
+                if (better) {
+                    bj = j;
+                    bc = cv[t];
+                    blo = lo;
+                    bhi = hi;
+                }
+            }
+            host[i] = bj;
+        }
+        for (int i = 0; i < n; i++) {
+            if (host[i] >= 0 || agg[i] >= 0) continue;
+            agg[i] = na;
+            if (mate[i] >= 0) agg[mate[i]] = na;
+            na++;
+        }
+        for (int i = 0; i < n; i++)
+            if (host[i] >= 0) agg[i] = agg[host[i]];
+        free(host);
+    } else {
+        for (int i = 0; i < n; i++) {
+            if (agg[i] >= 0) continue;
+            agg[i] = na;
+            if (mate[i] >= 0) agg[mate[i]] = na;
+            na++;
+        }
     }
     free(crow);
     free(cc);
@@ -1076,8 +1121,8 @@ static int pairwise_pass(const o_csr *A, double beta, int match, uint32_t hb, in
             }
         srow[i + 1] = nnz;
     }
-    if (match == 1) {
-        int na = handshake_match(n, srow, scol, sval, hb, agg);
+    if (match == 1 || match == 2) {
+        int na = handshake_match(n, srow, scol, sval, hb, match == 2, agg);
         free(ccol);
         free(cval);
         free(srow);

@@ -46,7 +46,8 @@ typedef struct {
     int coloring;         /* smoother coloring: 0 JP on S u S^T; 1 the paper's
                              VerticesSplitting/Grouping, Alg. 4-5 (0) */
     int agg_match;        /* amg = 1 matching: 0 greedy by (m_i, i); 1 handshake rounds, the
-                             parallel form (0) */
+                             parallel form; 2 handshake rounds, then every node left alone that
+                             has a candidate joins its best candidate's pair (0) */
 } o_opts;
 
 typedef struct {

@@ -798,6 +798,72 @@ def test_handshake_matching_properties(which):
         assert nx.is_connected(G.subgraph(np.flatnonzero(agg2 == a).tolist()))
 
 
+@pytest.mark.parametrize("which", ["laplacian", "pressure", "heterogeneous"])
+def test_handshake_with_attachment_properties(which):
+    """agg_match = 2: the handshake pairs of agg_match = 1, and every node left
+    alone that has a candidate joins the pair of its candidate of smallest edge
+    key (c_ij, smaller hash, larger hash, index), recomputed here by brute
+    force; nodes without a candidate stay alone; aggregates are numbered by
+    the smallest node of their pair (or the lone node)."""
+    if which == "laplacian":
+        rp, cl, v = bs.laplacian_2d(12, 10)
+    elif which == "pressure":
+        rp, cl, v = _pressure_level0(bs.jacobian(bs.GridSpec(8, 8, 3, seed=2)))
+    else:
+        rp, cl, v = _pressure_level0(bs.jacobian(bs.GridSpec(10, 9, 4, 0.0, 2.0, 0.1, None, "corners", seed=7)))
+    n = len(rp) - 1
+    A = sp.csr_matrix((v, cl, rp), shape=(n, n))
+    C = ((A + A.T) * 0.5).toarray()
+    np.fill_diagonal(C, 0.0)
+    maxneg = np.maximum((-C).max(axis=1), 0.0)
+    strong = (C < 0) & (-C >= 0.25 * maxneg[:, None])
+    cand = strong | strong.T
+    hb = oracle.fmix32(3 * 1000003)            # the pass hash o_aggregate uses
+    h = np.array([oracle.fmix32(i ^ hb) for i in range(n)], dtype=np.int64)
+    pairs, npairs = oracle.aggregate(n, rp, cl, v, passes=1, match=1)
+    agg, na = oracle.aggregate(n, rp, cl, v, passes=1, match=2)
+    psize = np.bincount(pairs, minlength=npairs)
+    lone = psize[pairs] == 1
+    host = {}
+    for i in np.flatnonzero(lone):
+        js = np.flatnonzero(cand[i])
+        if len(js):
+            key = [(C[i, j], min(h[i], h[j]), max(h[i], h[j]), j) for j in js]
+            host[i] = min(key)[3]
+            assert psize[pairs[host[i]]] == 2          # every candidate of a lone node is paired
+    leaders = sorted({int(np.flatnonzero(pairs == a).min()) for a in range(npairs)} - set(host))
+    assert na == len(leaders)
+    num = {ld: k for k, ld in enumerate(leaders)}
+    for i in range(n):
+        if i in host:
+            assert agg[i] == agg[host[i]]
+        else:
+            assert agg[i] == num[int(np.flatnonzero(pairs == pairs[i]).min())]
+    if which == "heterogeneous":
+        assert len(host) > 0                      # the case the attachment is for
+
+
+def test_ua_attachment_coarsens_and_solves():
+    """amg = 1 with agg_match = 2 on a heterogeneous anisotropic grid (the
+    benchmark generator's ln k ~ N(0, 2), kz/kx = 0.1): no singleton with a
+    candidate survives, each level coarsens by at least 3x, the levels are
+    Galerkin with unit-row P, and the CPR solve reaches the direct solution."""
+    J = bs.jacobian(bs.GridSpec(12, 12, 6, 0.0, 2.0, 0.1, None, "corners", seed=11))
+    s = oracle.Solver(J, amg=1, agg_match=2, coarse_max=16)
+    assert s.nlev >= 3
+    for l in range(s.nlev - 1):
+        L0, L1 = s.level(l), s.level(l + 1)
+        assert L1["A"].n * 3 <= L0["A"].n
+        P = L0["P"].dense()
+        assert np.array_equal(P.sum(axis=1), np.ones(P.shape[0]))
+        Ac = L1["A"].dense()
+        assert np.allclose(Ac, P.T @ L0["A"].dense() @ P, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    x, st = s.solve(J.b, rtol=1e-10)
+    assert st["converged"]
+    assert np.allclose(x, np.linalg.solve(J.to_dense(), J.b), rtol=1e-7, atol=1e-9)
+    s.close()
+
+
 def test_ua_with_handshake_matching_solves():
     """amg = 1 with agg_match = 1: Galerkin levels of unit-row P and a CPR
     solve reaching the direct solution."""
