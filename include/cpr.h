@@ -105,6 +105,23 @@ typedef struct {
                            colorings and BILU(0) ordering are kept, and every value (weights,
                            A_P, interpolation, Galerkin products, coarse LU, BILU(0) factors)
                            is recomputed from A^(k).  Not in the paper. */
+    int amg;            /* first stage's AMG.  0 (default): classical -- strength, PMIS C/F split,
+                           direct interpolation, R A P -- with a V(pre,post) cycle.  1: the paper's
+                           own first stage (Sec. 6): unsmoothed aggregation by double pairwise
+                           matching on the symmetric part of A_l (strong when c_ij < 0 and
+                           -c_ij >= theta_amg max_k -c_ik), matched in handshake rounds (each node
+                           points to its strongest unmatched candidate, mutual pointers pair; a node
+                           left alone joins its strongest candidate's pair), unit-entry P, and the
+                           nonlinear AMLI-cycle: the V-cycle's smoothing and transfers
+                           with each coarse problem above the coarsest solved by amli_iters steps
+                           of flexible GCR preconditioned by the cycle one level down. */
+    int amli_iters;     /* amg = 1: GCR steps of each coarse correction, 1..8; default 2 */
+    int coloring;       /* smoother coloring.  0 (default): Jones-Plassmann on S u S^T.  1: the
+                           paper's VerticesSplitting/Grouping (Alg. 4-5) on every smoothed level
+                           of at most coloring_rows rows (JP above): a sequential greedy, run by
+                           one thread block on the device. */
+    int coloring_rows;  /* coloring = 1: the largest level that takes Alg. 4-5; default 4096,
+                           at most 16384 */
 } cpr_opts;
 
 typedef struct {

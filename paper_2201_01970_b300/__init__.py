@@ -32,7 +32,8 @@ class Opts(C.Structure):
                 ("decouple", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
                 ("stream", C.c_void_p), ("pdl", C.c_int), ("tail", C.c_int), ("bilu_order", C.c_int),
-                ("reuse_refresh", C.c_int), ("resetup", C.c_int)]
+                ("reuse_refresh", C.c_int), ("resetup", C.c_int), ("amg", C.c_int),
+                ("amli_iters", C.c_int), ("coloring", C.c_int), ("coloring_rows", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -17,7 +17,7 @@ double now_ms() {
 }
 
 // The Python binding mirrors cpr_opts field by field; its test checks the same size.
-static_assert(sizeof(cpr_opts) == 96, "cpr_opts changed: update the binding's Opts and this check");
+static_assert(sizeof(cpr_opts) == 112, "cpr_opts changed: update the binding's Opts and this check");
 
 void check_opts(const cpr_opts &o) {
     bool ok = o.restart >= 1 && o.restart <= kMaxRestart && o.max_restarts >= 1 && o.pre >= 0 &&
@@ -26,7 +26,9 @@ void check_opts(const cpr_opts &o) {
               o.mu >= 0 && (o.decouple == 0 || o.decouple == 1) && (o.precond_fp32 == 0 || o.precond_fp32 == 1) &&
               (o.pdl == 0 || o.pdl == 1) && (o.tail == 0 || o.tail == 1) &&
               (o.bilu_order == 0 || o.bilu_order == 1) && (o.reuse_refresh == 0 || o.reuse_refresh == 1) &&
-              (o.resetup == 0 || o.resetup == 1);
+              (o.resetup == 0 || o.resetup == 1) && (o.amg == 0 || o.amg == 1) && o.amli_iters >= 1 &&
+              o.amli_iters <= kMaxAmli && (o.coloring == 0 || o.coloring == 1) && o.coloring_rows >= 0 &&
+              o.coloring_rows <= kMaxGroupingRows;
     if (!ok) fail(CPR_ERR_INVALID, "options out of range");
 }
 
@@ -217,6 +219,10 @@ void cpr_default_opts(cpr_opts *o) {
     o->bilu_order = 0;
     o->reuse_refresh = 0;
     o->resetup = 0;
+    o->amg = 0;
+    o->amli_iters = 2;
+    o->coloring = 0;
+    o->coloring_rows = 4096;
 }
 
 const char *cpr_strerror(int code) {

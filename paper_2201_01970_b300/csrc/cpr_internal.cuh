@@ -172,6 +172,11 @@ struct Level {
     // work vectors (internal numbering); s0, s1: staging of the color being relaxed
     DVec<double> x, b, r, s0, s1;
     DVec<float> x32, b32, r32, s0_32, s1_32;
+    // amg = 1, levels 1 .. L-2: the GCR vectors of this level's coarse
+    // correction (amli_iters x n each), its scalars and reduction partials
+    DVec<double> gv, gw, gscal, gpart;
+    DVec<float> gv32, gw32;
+    DVec<int> gcnt;
 };
 
 // Multicolor BILU(0).  The factor array lu (lu32 in FP32 mode) is in A's
@@ -293,6 +298,8 @@ namespace cpr {
 
 constexpr int kMaxRestart = 64;
 constexpr int kMaxCoarse = 4096;
+constexpr int kMaxAmli = 8;             // GCR steps of an AMLI coarse correction
+constexpr int kMaxGroupingRows = 16384; // largest level Alg. 4-5 colors on the device
 
 int grid_for(long n, int block, int cap = 1 << 30);
 

@@ -693,6 +693,217 @@ __global__ void k_is_c(int n, const int *cf, int *flag) {
     if (i < n) flag[i] = cf[i] == 1;
 }
 
+// ------------------------------------------------- pairwise aggregation (UA-AMG)
+//
+// One matching pass of the pairwise aggregation Sec. 6 names for its first
+// stage, taken on the symmetric part of A: c_ij = (a_ij + a_ji) / 2, and j is
+// a strong neighbour of i when c_ij < 0 and -c_ij >= beta max_{k != i}(-c_ik).
+// Nodes pair up in handshake rounds: every unmatched node points to its
+// unmatched candidate (a strong neighbour in either direction) of smallest
+// edge key (c_ij, smaller hash, larger hash, index); mutual pointers pair, and
+// a node with no unmatched candidate is left alone.  A node left alone that
+// has a candidate then joins the pair of its best candidate (rounds alone
+// leave many singletons on heterogeneous media, and coarsening stalls); the
+// others stay single.  Aggregates are numbered by the smaller node of their
+// pair (or the single node).  Every FP64 operation is the plain
+// definition's, in its order, so the result equals a sequential evaluation.
+
+// The symmetric couplings of row i, merged from row i of A and of A^T (both
+// sorted); f(j, c) is called for every j != i in ascending order.
+template <class F>
+__device__ __forceinline__ void pair_couplings(int i, int n, const int *ar, const int *ac, const double *av,
+                                               const int *tr, const int *tc, const double *tv, F f) {
+    int p = ar[i], pe = ar[i + 1], q = tr[i], qe = tr[i + 1];
+    while (p < pe || q < qe) {
+        int a = p < pe ? ac[p] : n, b = q < qe ? tc[q] : n;
+        int j = a < b ? a : b;
+        double c = 0.0;
+        if (a == j) c = __dadd_rn(c, av[p++]);
+        if (b == j) c = __dadd_rn(c, tv[q++]);
+        if (j == i) continue;
+        f(j, __dmul_rn(0.5, c));
+    }
+}
+
+// Strong neighbours of each row: counts (scol == nullptr) or columns and
+// couplings at srow[i].
+__global__ void k_pair_strong(int n, const int *ar, const int *ac, const double *av, const int *tr,
+                              const int *tc, const double *tv, double beta, const int *srow, int *cnt,
+                              int *scol, double *sval) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double maxneg = 0.0;
+    pair_couplings(i, n, ar, ac, av, tr, tc, tv, [&](int, double c) {
+        if (-c > maxneg) maxneg = -c;
+    });
+    double lim = __dmul_rn(beta, maxneg);
+    int o = scol ? srow[i] : 0;
+    pair_couplings(i, n, ar, ac, av, tr, tc, tv, [&](int j, double c) {
+        if (c < 0.0 && maxneg > 0.0 && -c >= lim) {
+            if (scol) {
+                scol[o] = j;
+                sval[o] = c;
+            }
+            o++;
+        }
+    });
+    if (!scol) cnt[i] = o;
+}
+
+constexpr int kUnmatched = -2, kAlone = -1;
+
+// The unmatched candidate of smallest edge key among S_i and (S^T)_i.
+__device__ int hs_best(int i, const int *sr, const int *sc, const double *sv, const int *tr, const int *tc,
+                       const double *tv, const int *mate, uint32_t hb) {
+    int bj = -1;
+    double bc = 0.0;
+    uint32_t blo = 0, bhi = 0;
+    uint32_t hi_ = fmix32((uint32_t)i ^ hb);
+    volatile const int *vm = mate;
+    for (int pass = 0; pass < 2; pass++) {
+        const int *R = pass ? tr : sr, *Cc = pass ? tc : sc;
+        const double *V = pass ? tv : sv;
+        for (int t = R[i]; t < R[i + 1]; t++) {
+            int j = Cc[t];
+            if (j == i || vm[j] != kUnmatched) continue;
+            uint32_t hj = fmix32((uint32_t)j ^ hb);
+            uint32_t lo = hi_ < hj ? hi_ : hj, hi = hi_ < hj ? hj : hi_;
+            double c = V[t];
+            bool better = bj < 0 || c < bc ||
+                          (c == bc && (lo < blo || (lo == blo && (hi < bhi || (hi == bhi && j < bj)))));
+            if (better) {
+                bj = j;
+                bc = c;
+                blo = lo;
+                bhi = hi;
+            }
+        }
+    }
+    return bj;
+}
+
+// A round: pointers from the round-start state, then the commits.  The count
+// of unmatched nodes reaches 0 with the last commit; then both kernels return
+// at once (rounds run in batches between host checks).
+__global__ void k_hs_point(int n, const int *sr, const int *sc, const double *sv, const int *tr, const int *tc,
+                           const double *tv, const int *mate, int *ptr, uint32_t hb, const int *left) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || *(volatile const int *)left == 0) return;
+    ptr[i] = mate[i] == kUnmatched ? hs_best(i, sr, sc, sv, tr, tc, tv, mate, hb) : -1;
+}
+
+__device__ __forceinline__ int hs_commit(int i, int *mate, const int *ptr) {
+    if (mate[i] != kUnmatched) return 0;
+    int p = ptr[i];
+    if (p < 0) {
+        mate[i] = kAlone;
+        return 1;
+    }
+    if (ptr[p] == i) {
+        mate[i] = p;
+        return 1;
+    }
+    return 0;
+}
+
+__global__ void k_hs_commit(int n, int *mate, const int *ptr, int *left) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || *(volatile int *)left == 0) return;
+    if (hs_commit(i, mate, ptr)) atomicSub(left, 1);
+}
+
+// All rounds of a small level in one CTA (the same rounds).
+__global__ void __launch_bounds__(1024) k_hs_small(int n, const int *sr, const int *sc, const double *sv,
+                                                   const int *tr, const int *tc, const double *tv, int *mate,
+                                                   int *ptr, uint32_t hb) {
+    __shared__ int left;
+    if (threadIdx.x == 0) left = n;
+    __syncthreads();
+    for (int round = 0; round < n + 8; round++) {
+        int l = left;
+        __syncthreads();
+        if (l == 0) break;
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            ptr[i] = mate[i] == kUnmatched ? hs_best(i, sr, sc, sv, tr, tc, tv, mate, hb) : -1;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (hs_commit(i, mate, ptr)) atomicSub(&left, 1);
+        __syncthreads();
+    }
+}
+
+// After the rounds, a node left alone that has a candidate joins the pair of
+// its candidate of smallest edge key (all its candidates are paired: an
+// unmatched one would have kept both nodes pointing); host[i] = that
+// candidate, or -1.
+__global__ void k_hs_host(int n, const int *sr, const int *sc, const double *sv, const int *tr, const int *tc,
+                          const double *tv, const int *mate, uint32_t hb, int *host) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int bj = -1;
+    if (mate[i] == kAlone) {
+        double bc = 0.0;
+        uint32_t blo = 0, bhi = 0;
+        uint32_t hi_ = fmix32((uint32_t)i ^ hb);
+        for (int pass = 0; pass < 2; pass++) {
+            const int *R = pass ? tr : sr, *Cc = pass ? tc : sc;
+            const double *V = pass ? tv : sv;
+            for (int t = R[i]; t < R[i + 1]; t++) {
+                int j = Cc[t];
+                if (j == i) continue;
+                uint32_t hj = fmix32((uint32_t)j ^ hb);
+                uint32_t lo = hi_ < hj ? hi_ : hj, hi = hi_ < hj ? hj : hi_;
+                double c = V[t];
+                bool better = bj < 0 || c < bc ||
+                              (c == bc && (lo < blo || (lo == blo && (hi < bhi || (hi == bhi && j < bj)))));
+                if (better) {
+                    bj = j;
+                    bc = c;
+                    blo = lo;
+                    bhi = hi;
+                }
+            }
+        }
+    }
+    host[i] = bj;
+}
+
+// Aggregates are numbered by their leader: the smaller node of a pair, or a
+// node left alone with no host.
+__global__ void k_hs_leader(int n, const int *mate, const int *host, int *flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = mate[i] >= 0 ? mate[i] > i : host[i] < 0;
+}
+
+__global__ void k_hs_number(int n, const int *mate, const int *host, const int *idx, int *agg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = host[i] >= 0 ? host[i] : i;   // a joining node takes its host pair's number
+    int m = mate[k];
+    agg[i] = idx[m >= 0 && m < k ? m : k];
+}
+
+__global__ void k_fill_int(int n, int *a, int v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+
+// Unsmoothed aggregation's P: row i is the unit row of aggregate agg[i].
+__global__ void k_unit_p(int n, const int *agg, int *rowptr, int *col, double *val) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    rowptr[i] = i;
+    if (i == n) return;
+    col[i] = agg[i];
+    val[i] = 1.0;
+}
+
+// agg[i] <- second[first[i]]: the two passes composed.
+__global__ void k_compose_agg(int n, const int *first, const int *second, int *agg) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) agg[i] = second[first[i]];
+}
+
 // ------------------------------------------------------ direct interpolation
 
 __global__ void k_interp_count(int n, const int *sr, const int *sc, const int *cf, int *cnt) {
@@ -1977,6 +2188,106 @@ void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     CK_LAUNCH();
 }
 
+constexpr int kHsBatch = 6;   // handshake rounds launched per host check of the unmatched count
+
+// P (n x na) of unsmoothed aggregation from the aggregate of every node.
+void unit_p(int n, int na, const int *agg, DCsr &P, cudaStream_t s) {
+    P.n = n;
+    P.ncol = na;
+    P.nnz = n;
+    P.rowptr.alloc(n + 1, s);
+    P.col.alloc(std::max(n, 1), s);
+    P.val.alloc(std::max(n, 1), s);
+    k_unit_p<<<grid_for(n + 1, kBlock), kBlock, 0, s>>>(n, agg, P.rowptr.p, P.col.p, P.val.p);
+    CK_LAUNCH();
+}
+
+// One pairwise matching pass on A; agg gets each node's aggregate, the
+// return value is the number of aggregates.
+int pairwise_pass(const DCsr &A, double beta, uint32_t hb, DVec<int> &agg, cudaStream_t s) {
+    int n = A.n;
+    DVec<int> tr, tc;
+    DVec<double> tv;
+    transpose(n, n, A.nnz, A.rowptr.p, A.col.p, A.val.p, tr, tc, &tv, s);
+    // the strong set S with its couplings, and S^T
+    DVec<int> cnt, sr, sc;
+    DVec<double> sv;
+    cnt.alloc(std::max(n, 1), s);
+    k_pair_strong<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, tr.p, tc.p, tv.p, beta,
+                                                        nullptr, cnt.p, nullptr, nullptr);
+    CK_LAUNCH();
+    sr.alloc(n + 1, s);
+    exclusive_scan(cnt.p, sr.p, n, s);
+    int snnz = read_int(sr.p + n, s);
+    sc.alloc(std::max(snnz, 1), s);
+    sv.alloc(std::max(snnz, 1), s);
+    k_pair_strong<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, tr.p, tc.p, tv.p, beta,
+                                                        sr.p, nullptr, sc.p, sv.p);
+    CK_LAUNCH();
+    DVec<int> str, stc;
+    DVec<double> stv;
+    transpose(n, n, snnz, sr.p, sc.p, sv.p, str, stc, &stv, s);
+    // handshake rounds
+    DVec<int> mate, ptr, left;
+    mate.alloc(std::max(n, 1), s);
+    ptr.alloc(std::max(n, 1), s);
+    k_fill_int<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, mate.p, kUnmatched);
+    CK_LAUNCH();
+    if (n <= kSmallLevel) {
+        k_hs_small<<<1, 1024, 0, s>>>(n, sr.p, sc.p, sv.p, str.p, stc.p, stv.p, mate.p, ptr.p, hb);
+        CK_LAUNCH();
+    } else {
+        left.alloc(1, s);
+        CK(cudaMemcpyAsync(left.p, &n, sizeof(int), cudaMemcpyHostToDevice, s));
+        int rounds = 0;
+        do {
+            for (int k = 0; k < kHsBatch; k++, rounds++) {
+                k_hs_point<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, sr.p, sc.p, sv.p, str.p, stc.p, stv.p, mate.p,
+                                                                 ptr.p, hb, left.p);
+                CK_LAUNCH();
+                k_hs_commit<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, mate.p, ptr.p, left.p);
+                CK_LAUNCH();
+            }
+            if (rounds > n + 8) fail(CPR_ERR_CUDA, "pairwise matching did not terminate");
+        } while (read_int(left.p, s) > 0);
+    }
+    DVec<int> host, flag, idx;
+    host.alloc(std::max(n, 1), s);
+    k_hs_host<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, sr.p, sc.p, sv.p, str.p, stc.p, stv.p, mate.p, hb, host.p);
+    CK_LAUNCH();
+    flag.alloc(std::max(n, 1), s);
+    idx.alloc(n + 1, s);
+    k_hs_leader<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, mate.p, host.p, flag.p);
+    CK_LAUNCH();
+    exclusive_scan(flag.p, idx.p, n, s);
+    int na = read_int(idx.p + n, s);
+    agg.alloc(std::max(n, 1), s);
+    k_hs_number<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, mate.p, host.p, idx.p, agg.p);
+    CK_LAUNCH();
+    return na;
+}
+
+// Double pairwise aggregation: a pass on A, then a pass on the pair operator
+// P1^T A P1 (hash hb ^ 0x9e3779b9), so aggregates hold at most four nodes.
+int aggregate_double(const DCsr &A, double beta, uint32_t hb, DVec<int> &agg, cudaStream_t s) {
+    int n = A.n;
+    DVec<int> a1, a2;
+    int n1 = pairwise_pass(A, beta, hb, a1, s);
+    DCsr P1, R1, AP, A1;
+    unit_p(n, n1, a1.p, P1, s);
+    R1.n = n1;
+    R1.ncol = n;
+    R1.nnz = n;
+    transpose(n, n1, n, P1.rowptr.p, P1.col.p, P1.val.p, R1.rowptr, R1.col, &R1.val, s);
+    spgemm(A, P1, AP, s);
+    spgemm(R1, AP, A1, s);
+    int n2 = pairwise_pass(A1, beta, hb ^ 0x9e3779b9u, a2, s);
+    agg.alloc(std::max(n, 1), s);
+    k_compose_agg<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, a1.p, a2.p, agg.p);
+    CK_LAUNCH();
+    return n2;
+}
+
 void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
     b.alloc(std::max<size_t>(a.n, 1), s);
     if (a.n) {
@@ -2466,7 +2777,23 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         Graph S;
         DVec<int> flag, cidx;
         int nc = 0;
-        if (numeric) {   // the kept strength set and C/F split; coarse indices from it
+        bool ua = o.amg == 1;
+        if (ua) {   // UA-AMG (Sec. 6): cf holds every node's aggregate
+            if (numeric) {
+                KeptLevel &K = kept[l];
+                if (K.cf.n != (size_t)n || K.rows_by_color.n != (size_t)n)
+                    fail(CPR_ERR_INVALID, "numeric resetup: the kept hierarchy does not fit A");
+                L.cf = std::move(K.cf);
+                nc = K.nc;
+            } else {
+                nc = aggregate_double(L.A, o.theta_amg, hash_base(o.seed, 3, l), L.cf, s);
+                clk.mark("aggregate");
+                if (nc == 0 || (double)nc > 0.95 * (double)n) {
+                    L.cf.release();
+                    break;
+                }
+            }
+        } else if (numeric) {   // the kept strength set and C/F split; coarse indices from it
             KeptLevel &K = kept[l];
             if (K.cf.n != (size_t)n || K.rows_by_color.n != (size_t)n)
                 fail(CPR_ERR_INVALID, "numeric resetup: the kept hierarchy does not fit A");
@@ -2570,8 +2897,13 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
                 side.finished(l);
             });
         }
-        // direct interpolation P and R = P^T
-        {
+        if (ua) {   // unsmoothed aggregation: unit rows, R = P^T
+            unit_p(n, nc, L.cf.p, L.P, s);
+            L.R.n = nc;
+            L.R.ncol = n;
+            L.R.nnz = n;
+            transpose(n, nc, n, L.P.rowptr.p, L.P.col.p, L.P.val.p, L.R.rowptr, L.R.col, &L.R.val, s);
+        } else {   // direct interpolation P and R = P^T
             DVec<int> cnt;
             cnt.alloc(n, s);
             k_interp_count<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, L.cf.p, cnt.p);
@@ -2745,6 +3077,23 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             Lv.r32.alloc(n, s);
             Lv.s0_32.alloc(n, s);
             Lv.s1_32.alloc(n, s);
+        }
+        // amg = 1: the GCR work of the coarse corrections on levels 1 .. L-2
+        if (o.amg == 1 && l >= 1 && l < L - 1) {
+            size_t m = (size_t)std::max(1, o.amli_iters);
+            if (f32) {
+                Lv.gv32.alloc(m * n, s);
+                Lv.gw32.alloc(m * n, s);
+            } else {
+                Lv.gv.alloc(m * n, s);
+                Lv.gw.alloc(m * n, s);
+            }
+            Lv.gscal.alloc(2 * m + 2, s);
+            Lv.gscal.zero();
+            // partials of the widest launch: the level's matrix-vector kernel, up to 32 lanes a row
+            Lv.gpart.alloc(2 * ((32 * (size_t)n + 255) / 256 + 1184), s);
+            Lv.gcnt.alloc(2, s);
+            Lv.gcnt.zero();
         }
     }
     coarse_join.finish();

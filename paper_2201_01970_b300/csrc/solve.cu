@@ -606,6 +606,143 @@ __device__ bool arrive_last(int *counter) {
     return last;
 }
 
+// ------------------------------------------- nonlinear AMLI-cycle (amg = 1)
+//
+// The coarse correction of Sec. 6's AMLI-cycle on level k: amli_iters steps
+// of flexible GCR on A_k e = r from e = 0, each preconditioned by the cycle of
+// level k.  Step t: v_t = cycle(res), w_t = A_k v_t, w_t and v_t made
+// orthogonal to the earlier w_u one u at a time (beta_u = (w_t, w_u) /
+// (w_u, w_u)), alpha_t = (w_t, res) / (w_t, w_t), e += alpha_t v_t,
+// res -= alpha_t w_t; a step with (w_t, w_t) = 0 ends the correction.  The
+// vectors are the preconditioner's type T; dot products accumulate in FP64 as
+// per-block partials that the last block sums in a fixed order, so the
+// scalars are deterministic.  Device scalars of a level (gscal): [0, m) the
+// (w_u, w_u), [m, 2m) the beta_u, 2m alpha, 2m+1 the stop flag.
+
+struct AmliScal {
+    int m;
+    __device__ int ww(int u) const { return u; }
+    __device__ int beta(int u) const { return m + u; }
+    __device__ int alpha() const { return 2 * m; }
+    __device__ int stop() const { return 2 * m + 1; }
+};
+
+// Block sums of (a, b) into part[2 blk], part[2 blk + 1]; the block that
+// arrives last gets the totals (fixed order), else returns false.
+__device__ bool amli_reduce(double a, double b, double *part, int *counter, double &sa, double &sb) {
+    a = block_sum(a);
+    __syncthreads();
+    b = block_sum(b);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+    if (!arrive_last(counter) || threadIdx.x >= 32) return false;
+    double ta = 0.0, tb = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) {
+        ta += __ldcg(part + 2 * k);
+        tb += __ldcg(part + 2 * k + 1);
+    }
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    if (threadIdx.x == 0) *counter = 0;
+    sa = ta;
+    sb = tb;
+    return threadIdx.x == 0;
+}
+
+// w_t = A v_t with v's pending range [p0, p1) read from sp and committed into
+// v.  t = 0: the partials of (w, w) and (w, res) give ww_0 and alpha (or the
+// stop flag); t > 0: the partials of (w, w_0) give beta_0.
+template <class T, int G>
+__global__ void k_amli_mv(int n, int p0, int p1, const int *__restrict__ rowptr, const int *__restrict__ col,
+                          const T *__restrict__ val, const T *__restrict__ diag, T *v, const T *sp, T *w,
+                          const T *y, int t, double *sc, int m, double *part, int *counter, const int *done) {
+    if (done && *done) return;
+    AmliScal L{m};
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long nthr = (long)gridDim.x * blockDim.x;
+    long g = tid / G;
+    int lane = (int)(tid % G);
+    bool active = g < n;
+    int i = (int)g;
+    RowPre<T, G> rp;
+    rp.load(rowptr, col, val, i, lane, active);
+    T dg = active ? diag[i] : (T)0;
+    T s = 0;
+    if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(v, sp, p0, p1, j); });
+    s = group_sum(s, G);
+    double da = 0.0, db = 0.0;
+    if (active && lane == 0) {
+        T wi = s + dg * xval(v, sp, p0, p1, i);
+        w[i] = wi;
+        da = t == 0 ? (double)wi * (double)wi : 0.0;
+        db = (double)wi * (double)y[i];
+    }
+    for (long q = tid; q < p1 - p0; q += nthr) v[p0 + q] = sp[p0 + q];
+    double ta, tb;
+    if (!amli_reduce(da, db, part, counter, ta, tb)) return;
+    if (t == 0) {
+        sc[L.ww(0)] = ta;
+        sc[L.stop()] = ta == 0.0 ? 1.0 : 0.0;
+        sc[L.alpha()] = ta == 0.0 ? 0.0 : tb / ta;
+    } else {
+        double den = sc[L.ww(0)];
+        sc[L.beta(0)] = den == 0.0 ? 0.0 : tb / den;
+    }
+}
+
+// w -= beta_u w_u, v -= beta_u v_u; then the partials of (w, w_{u+1}) give
+// beta_{u+1} (u + 1 < t), or those of (w, w) and (w, res) give ww_t and alpha
+// (u + 1 == t).
+template <class T>
+__global__ void k_amli_orth(int n, T *w, T *v, const T *wu, const T *vu, const T *y, int u, int t, double *sc, int m,
+                            double *part, int *counter, const int *done) {
+    if (done && *done) return;
+    AmliScal L{m};
+    T beta = (T)sc[L.beta(u)];
+    bool last = u + 1 == t;
+    double da = 0.0, db = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        T wi = w[i] - beta * wu[i];
+        w[i] = wi;
+        v[i] = v[i] - beta * vu[i];
+        if (last) da += (double)wi * (double)wi;
+        db += (double)wi * (double)y[i];
+    }
+    double ta, tb;
+    if (!amli_reduce(da, db, part, counter, ta, tb)) return;
+    if (last) {
+        sc[L.ww(t)] = ta;
+        bool stop = sc[L.stop()] != 0.0 || ta == 0.0;
+        sc[L.stop()] = stop ? 1.0 : 0.0;
+        sc[L.alpha()] = ta == 0.0 ? 0.0 : tb / ta;
+    } else {
+        double den = sc[L.ww(u + 1)];
+        sc[L.beta(u + 1)] = den == 0.0 ? 0.0 : tb / den;
+    }
+}
+
+// e += alpha v, res -= alpha w (t = 0: e = 0 + alpha v); nothing once a step
+// has stopped the correction (t = 0: e = 0).
+template <class T>
+__global__ void k_amli_update(int n, T *e, T *res, const T *v, const T *w, int t, const double *sc, int m,
+                              const int *done) {
+    if (done && *done) return;
+    AmliScal L{m};
+    bool stop = sc[L.stop()] != 0.0;
+    T alpha = (T)sc[L.alpha()];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        if (stop) {
+            if (t == 0) e[i] = (T)0;
+            continue;
+        }
+        T ei = t == 0 ? (T)0 : e[i];
+        e[i] = ei + alpha * v[i];
+        res[i] = res[i] - alpha * w[i];
+    }
+}
+
 // Transpose-reduction of 16 per-lane partials over a warp: four halving steps
 // in which each lane keeps one half of its vectors and adds its partner's copy
 // of that half, then one plain step.  Afterwards lanes L and L^1 both hold the
@@ -903,6 +1040,8 @@ struct Vals<double> {
     static const double *Dv(const cpr_handle *h) { return h->bilu.Dinv.p; }
     static double *tmp(cpr_handle *h) { return h->t64a.p; }
     static double *ep(cpr_handle *h) { return h->ep64.p; }
+    static double *gv(Level &L) { return L.gv.p; }
+    static double *gw(Level &L) { return L.gw.p; }
 };
 template <>
 struct Vals<float> {
@@ -922,6 +1061,8 @@ struct Vals<float> {
     static const float *Dv(const cpr_handle *h) { return h->bilu.Dinv32.p; }
     static float *tmp(cpr_handle *h) { return h->t32a.p; }
     static float *ep(cpr_handle *h) { return h->ep32.p; }
+    static float *gv(Level &L) { return L.gv32.p; }
+    static float *gw(Level &L) { return L.gw32.p; }
 };
 
 // The staged ("pending") range of a level: rows [p0, p1) whose newest values
@@ -973,7 +1114,7 @@ void launch_b(const cpr_handle *h, void (*kern)(KArgs...), unsigned grid, unsign
 // From zero: the first color writes b/a_ii into staging and zeroes x.
 template <class T>
 void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pending &pd,
-                const int *done, bool first_done = false) {
+                const int *done, bool first_done, const T *b, T *x) {
     cudaStream_t s = h->stream;
     int n = L.A.n;
     for (int t = 0; t < L.ncolors; t++) {
@@ -983,16 +1124,15 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
         if (from_zero && t == 0 && first_done) {
             // the producer of b already did this color's from-zero work
         } else if (from_zero && t == 0) {
-            launch_b(h, k_smooth_first<T>, blocks_for(n), kBlock, s, n, c0, c1, Vals<T>::b(L), Vals<T>::dinv(L),
-                     Vals<T>::x(L), Vals<T>::s(L, k), done);
+            launch_b(h, k_smooth_first<T>, blocks_for(n), kBlock, s, n, c0, c1, b, Vals<T>::dinv(L), x,
+                     Vals<T>::s(L, k), done);
         } else {
             long thr = std::max<long>((long)(c1 - c0) * L.gA, pd.p1 - pd.p0);
             bool fine = &L == &h->lev[0];
             if (fine) prof_begin(h, CPR_PROF_SMOOTH0);
             CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_smooth_color<T, G>, blocks_for(thr), kBlock, s, c0, c1, pd.p0,
-                                               pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::b(L),
-                                               Vals<T>::dinv(L), Vals<T>::x(L), Vals<T>::s(L, pd.k),
-                                               Vals<T>::s(L, k), done)));
+                                               pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), b,
+                                               Vals<T>::dinv(L), x, Vals<T>::s(L, pd.k), Vals<T>::s(L, k), done)));
             if (fine) prof_end(h);
         }
         pd = Pending{c0, c1, k};
@@ -1098,7 +1238,8 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
         k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, Vals<T>::x(L), done);
         CK_LAUNCH();
     }
-    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0);
+    for (int k = 0; k < h->opt.pre; k++)
+        mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0, Vals<T>::b(L), Vals<T>::x(L));
     long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
     CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
                                        L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), Vals<T>::b(L),
@@ -1122,7 +1263,7 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
     CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
                                        L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
                                        Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
-    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done);
+    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done, false, Vals<T>::b(L), Vals<T>::x(L));
     out = pd;
 }
 
@@ -1136,6 +1277,100 @@ void vcycle_top(cpr_handle *h, T *ep, const int *done, bool first_done = false) 
     int n = L0.A.n;
     launch_b(h, k_commit_natural<T>, blocks_for(n), kBlock, h->stream, n, h->ep_map.p, Vals<T>::x(L0),
              Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
+}
+
+// ------------------------------------------------ the AMLI-cycle (amg = 1)
+
+template <class T>
+void amli_coarse(cpr_handle *h, int k, const int *done);
+
+// The nonlinear AMLI-cycle for A_l x = b from x = 0 (Sec. 6's first stage):
+// the V-cycle's smoothing and transfers, with the coarse problem solved
+// exactly on the coarsest level and by amli_coarse elsewhere.  b and x are
+// any vectors of level l (internal numbering); on return x's range `out` is
+// still staged.  first_done as for vcycle (level 0 only).
+template <class T>
+void kcycle(cpr_handle *h, int l, const T *b, T *x, Pending &out, const int *done, bool first_done = false) {
+    cudaStream_t s = h->stream;
+    Level &L = h->lev[l];
+    int n = L.A.n;
+    int last = (int)h->lev.size() - 1;
+    if (l == last) {
+        launch_b(h, k_coarse_solve<T>, blocks_for((long)n * 32), kBlock, s, n, h->cinv.p, b, x, done);
+        out = Pending{};
+        return;
+    }
+    Pending pd;
+    if (h->opt.pre == 0) {
+        k_zero<T><<<grid_for(n, kBlock, 148 * 8), kBlock, 0, s>>>(n, x, done);
+        CK_LAUNCH();
+    }
+    for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0, b, x);
+    long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
+    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+                                       L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), b, x,
+                                       Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
+    pd = Pending{};
+    Level &C = h->lev[l + 1];
+    CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s, L.Rp.n,
+                                       L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L), 0, 0,
+                                       Vals<T>::b(C), false, done)));
+    if (l + 1 == last)
+        launch_b(h, k_coarse_solve<T>, blocks_for((long)C.A.n * 32), kBlock, s, C.A.n, h->cinv.p, Vals<T>::b(C),
+                 Vals<T>::x(C), done);
+    else
+        amli_coarse<T>(h, l + 1, done);   // e = x(C), fully written
+    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+                                       L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C), Vals<T>::s(C, 0), 0,
+                                       0, x, true, done)));
+    for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done, false, b, x);
+    out = pd;
+}
+
+// The coarse correction on level k (1 <= k < L-1): GCR on A_k e = r with r in
+// b(k) (used in place as the residual) and e in x(k); see k_amli_mv.
+template <class T>
+void amli_coarse(cpr_handle *h, int k, const int *done) {
+    cudaStream_t s = h->stream;
+    Level &L = h->lev[k];
+    int n = L.A.n, m = std::max(1, h->opt.amli_iters);
+    T *res = Vals<T>::b(L), *e = Vals<T>::x(L);
+    unsigned eb = (unsigned)grid_for(n, kBlock, 148 * 4);
+    for (int t = 0; t < m; t++) {
+        T *v = Vals<T>::gv(L) + (size_t)t * n, *w = Vals<T>::gw(L) + (size_t)t * n;
+        Pending pv;
+        kcycle<T>(h, k, res, v, pv, done);
+        long thr = std::max<long>((long)n * L.gA, pv.p1 - pv.p0);
+        const T *y = t == 0 ? res : Vals<T>::gw(L);
+        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_amli_mv<T, G>, blocks_for(thr), kBlock, s, n, pv.p0, pv.p1,
+                                           L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), v,
+                                           Vals<T>::s(L, pv.k), w, y, t, L.gscal.p, m, L.gpart.p, L.gcnt.p, done)));
+        for (int u = 0; u < t; u++) {
+            const T *yu = u + 1 == t ? res : Vals<T>::gw(L) + (size_t)(u + 1) * n;
+            launch_b(h, k_amli_orth<T>, eb, kBlock, s, n, w, v, Vals<T>::gw(L) + (size_t)u * n,
+                     Vals<T>::gv(L) + (size_t)u * n, yu, u, t, L.gscal.p, m, L.gpart.p, L.gcnt.p + 1, done);
+        }
+        launch_b(h, k_amli_update<T>, eb, kBlock, s, n, e, res, (const T *)v, (const T *)w, t,
+                 (const double *)L.gscal.p, m, done);
+    }
+}
+
+// e_P = B_P r_P with the AMLI-cycle (the counterpart of vcycle_top).
+template <class T>
+void kcycle_top(cpr_handle *h, T *ep, const int *done, bool first_done = false) {
+    Level &L0 = h->lev[0];
+    Pending pd;
+    kcycle<T>(h, 0, Vals<T>::b(L0), Vals<T>::x(L0), pd, done, first_done);
+    int n = L0.A.n;
+    launch_b(h, k_commit_natural<T>, blocks_for(n), kBlock, h->stream, n, h->ep_map.p, Vals<T>::x(L0),
+             Vals<T>::s(L0, pd.k), pd.p0, pd.p1, ep, done);
+}
+
+// B_P: the V-cycle, or the AMLI-cycle when amg = 1.
+template <class T>
+void pressure_top(cpr_handle *h, T *ep, const int *done, bool first_done = false) {
+    if (h->opt.amg == 1) kcycle_top<T>(h, ep, done, first_done);
+    else vcycle_top<T>(h, ep, done, first_done);
 }
 
 // BILU(0) solve in place on y (forward by ascending colors, backward by
@@ -1190,8 +1425,8 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     // e_P = B_P r_P (BILU positions)
     prof_begin(h, CPR_PROF_VCYCLE);
     {
-        Nvtx r("V-cycle");
-        vcycle_top<T>(h, Vals<T>::ep(h), done, fuse);
+        Nvtx r("pressure cycle");
+        pressure_top<T>(h, Vals<T>::ep(h), done, fuse);
     }
     prof_end(h);
     // r = v - A Pi_P e_P
@@ -1320,13 +1555,13 @@ void vcycle_apply(cpr_handle *h, const double *b, double *x) {
     if (h->opt.precond_fp32) {
         k_gather_cast<float><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b32.p);
         CK_LAUNCH();
-        vcycle_top<float>(h, h->ep32.p, nullptr);
+        pressure_top<float>(h, h->ep32.p, nullptr);
         k_gather_widen<float><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->bilu.iperm.p, h->ep32.p, x);
         CK_LAUNCH();
     } else {
         k_gather_cast<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, order0, b, L0.b.p);
         CK_LAUNCH();
-        vcycle_top<double>(h, h->ep64.p, nullptr);
+        pressure_top<double>(h, h->ep64.p, nullptr);
         k_gather_widen<double><<<grid_for(n, kBlock), kBlock, 0, s>>>(n, h->bilu.iperm.p, h->ep64.p, x);
         CK_LAUNCH();
     }
@@ -1391,7 +1626,7 @@ void level_part(cpr_handle *h, int l, int part) {
     int n = L.A.n;
     Pending pd;
     if (part == 0) {
-        mcgs_sweep<T>(h, L, false, true, pd, nullptr);
+        mcgs_sweep<T>(h, L, false, true, pd, nullptr, false, Vals<T>::b(L), Vals<T>::x(L));
     } else if (part == 1) {
         pd = Pending{L.color_off[L.ncolors - 1], L.color_off[L.ncolors], 0};
         long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
@@ -1410,7 +1645,7 @@ void level_part(cpr_handle *h, int l, int part) {
                                            L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
                                            Vals<T>::s(C, 0), 0, 0, Vals<T>::x(L), true, (const int *)nullptr)));
     } else {
-        mcgs_sweep<T>(h, L, true, false, pd, nullptr);
+        mcgs_sweep<T>(h, L, true, false, pd, nullptr, false, Vals<T>::b(L), Vals<T>::x(L));
     }
 }
 
@@ -1421,7 +1656,7 @@ int profile_levels_t(cpr_handle *h, int reps, double *us, int n_us) {
     if (n_us < need) fail(CPR_ERR_INVALID, "output array shorter than 3 + 5 * (levels - 1)");
     DVec<double> out;
     out.alloc(3 * (size_t)h->nb, h->stream);
-    us[0] = graph_us(h, reps, [&] { vcycle_top<T>(h, Vals<T>::ep(h), nullptr); });
+    us[0] = graph_us(h, reps, [&] { pressure_top<T>(h, Vals<T>::ep(h), nullptr); });
     us[1] = graph_us(h, reps, [&] { bilu_solve<T>(h, Vals<T>::tmp(h), nullptr, out.p, 0, nullptr, nullptr); });
     Level &C = h->lev.back();
     us[2] = graph_us(h, reps, [&] {
@@ -1443,7 +1678,7 @@ void choose_tail(cpr_handle *h) {
     h->tail_top = -1;
     const cpr_opts &o = h->opt;
     int L = (int)h->lev.size();
-    if (!o.tail || o.pre != 1 || o.post != 1 || L < 3) return;
+    if (!o.tail || o.pre != 1 || o.post != 1 || L < 3 || o.amg == 1) return;
     int nc = h->lev[L - 1].A.n;
     if (nc > kTailMaxCoarse) return;
     size_t elt = o.precond_fp32 ? sizeof(float) : sizeof(double);

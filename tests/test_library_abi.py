@@ -37,7 +37,8 @@ def test_binding_loads_and_defaults():
     # the fields after the stream pointer: a layout mismatch with cpr_opts would misread them
     assert (o.max_restarts, o.decouple, o.pre, o.post, o.max_levels, o.seed) == (100, 1, 1, 1, 20, 0)
     assert (o.pdl, o.tail, o.bilu_order, o.reuse_refresh, o.resetup) == (0, 0, 0, 0, 0)
-    assert ctypes.sizeof(cpr.Opts) == 96   # sizeof(cpr_opts), asserted at compile time in api.cu
+    assert (o.amg, o.amli_iters, o.coloring, o.coloring_rows) == (0, 2, 0, 4096)
+    assert ctypes.sizeof(cpr.Opts) == 112   # sizeof(cpr_opts), asserted at compile time in api.cu
     assert cpr.lib().cpr_strerror(cpr.CPR_ERR_SINGULAR).startswith(b"singular")
 
 
