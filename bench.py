@@ -724,6 +724,8 @@ def main():
                     help="only time setups of the workload, the last one bracketed for ncu and phase-marked")
     ap.add_argument("--no-resetup-numeric", action="store_true",
                     help="skip the numeric-only resetup line")
+    ap.add_argument("--no-ua-amg", action="store_true",
+                    help="skip the UA-AMG (amg = 1) line")
     ap.add_argument("--serve-scaled", action="store_true",
                     help="serving ensemble over the scaled 32x32x8..64x64x16 range instead of the full "
                          "32x32x8..128x128x32 one")
@@ -806,6 +808,10 @@ def main():
     natural = None if args.no_bilu_natural else option_arm(
         cpr, torch, seq_dev, rhs_dev, max(3, K // 3), W, stream,
         "bilu_order = 1: the paper's level-scheduled second stage, one launch per level set", bilu_order=1)
+    ua = None if args.no_ua_amg else option_arm(
+        cpr, torch, seq_dev, rhs_dev, K, W, stream,
+        "amg = 1: the paper's UA-AMG first stage (double pairwise aggregation, handshake rounds with "
+        "attachment, unit P) with the nonlinear AMLI-cycle (2 GCR steps per coarse correction)", amg=1)
     numeric = None if args.no_resetup_numeric else option_arm(
         cpr, torch, seq_dev, rhs_dev, K, W, stream,
         "resetup = 1: each rebuild keeps the first setup's levels, strength sets, C/F splits and colorings "
@@ -940,6 +946,8 @@ def main():
         line["bilu_natural"] = natural
     if numeric is not None:
         line["resetup_numeric"] = numeric
+    if ua is not None:
+        line["ua_amg"] = ua
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:

@@ -52,7 +52,7 @@ class Opts(C.Structure):
                 ("coarse_max", C.c_int), ("max_levels", C.c_int), ("seed", C.c_uint64),
                 ("bilu_order", C.c_int), ("reuse_refresh", C.c_int), ("resetup", C.c_int),
                 ("amg", C.c_int), ("amli_iters", C.c_int), ("coloring", C.c_int),
-                ("agg_match", C.c_int)]
+                ("agg_match", C.c_int), ("coloring_rows", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -1463,6 +1463,7 @@ void o_default_opts(o_opts *o) {
     o->amli_iters = 2;
     o->coloring = 0;
     o->agg_match = 0;
+    o->coloring_rows = 4096;
 }
 
 static void free_setup(o_handle *h) {
@@ -1609,7 +1610,7 @@ static int build_preconditioner(o_handle *h, int numeric) {
             /* the smoother's coloring (Eq. 5.1): JP standing in for Alg. 4-5, or Alg. 4-5 */
             o_csr Sc = strength_color(&L->A, o->theta_color);
             L->color = xcalloc((size_t)n, sizeof(int));
-            if (o->coloring == 1) {
+            if (o->coloring == 1 && (o->coloring_rows <= 0 || n <= o->coloring_rows)) {
                 L->ncolors = vertices_grouping(&Sc, L->color);
             } else {
                 o_csr G = sym_union(&Sc);

@@ -48,6 +48,8 @@ typedef struct {
     int agg_match;        /* amg = 1 matching: 0 greedy by (m_i, i); 1 handshake rounds, the
                              parallel form; 2 handshake rounds, then every node left alone that
                              has a candidate joins its best candidate's pair (0) */
+    int coloring_rows;    /* coloring = 1 applies to levels of at most this many rows; larger
+                             levels take JP (4096; 0 = every level) */
 } o_opts;
 
 typedef struct {

@@ -22,6 +22,7 @@
 #include <functional>
 #include <mutex>
 #include <thread>
+#include <atomic>
 #include <type_traits>
 
 #include "cpr_internal.cuh"
@@ -600,6 +601,214 @@ __global__ void k_level_round(int n, const int *list_in, int *list_out, int *cnt
         }
     }
     if (lmax >= 0) atomicMax(maxlevel, lmax);
+}
+
+// ---------------------------- Alg. 4-5: VerticesSplitting / VerticesGrouping
+//
+// The paper's own coloring of the strong-connection matrix S (Eq. 5.1, rows
+// as computed, not symmetrised), with the readings of its loosely defined
+// parts: "any take" picks, among the candidates of largest |S_i|, the lowest
+// index; the candidates are the second-circle set W^ (restricted to V) when
+// it is not empty, else all of V; S^_i = (union of S_k, k in S_i) minus
+// (S_i and i); W-bar takes only the members of S_i still in V.  The greedy
+// takes one vertex at a time, so it runs on one warp: vertices are ranked once
+// by (|S_i| descending, index), and a pick is the first vertex in rank order
+// that is a candidate, found by ballots over a rank-indexed bitmap of W^ or
+// by a pointer into the ranks that only moves forward within a call (a
+// vertex that leaves the candidates never returns in that call).
+
+constexpr int kGroupSortThreads = 1024;
+constexpr unsigned kGroupIndexBits = 14;   // kMaxGroupingRows = 2^14
+
+// order[r] = the vertex of rank r, rank[i] = the rank of vertex i: a bitonic
+// sort of packed keys ((2^14 - 1 - |S_i|) << 14 | i) in shared memory.
+__global__ void __launch_bounds__(kGroupSortThreads) k_group_order(int n, const int *sr, int *order, int *rank) {
+    extern __shared__ unsigned keys[];
+    int m = 1;
+    while (m < n) m <<= 1;
+    const unsigned top = (1u << kGroupIndexBits) - 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        unsigned key = ~0u;
+        if (i < n) {
+            unsigned d = (unsigned)min(sr[i + 1] - sr[i], (int)top);
+            key = ((top - d) << kGroupIndexBits) | (unsigned)i;
+        }
+        keys[i] = key;
+    }
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned a = keys[i], b = keys[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        keys[i] = b;
+                        keys[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        int v = (int)(keys[r] & top);
+        order[r] = v;
+        rank[v] = r;
+    }
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Alg. 5: calls of Alg. 4 with colors 0, 1, ... until every vertex has one;
+// one warp.  Shared memory: inV, inBar, inW per vertex, then the bitmaps hat
+// (W^, by rank) and si (S_i of the current pick, by vertex).
+__global__ void __launch_bounds__(32) k_vertices_grouping(int n, const int *sr, const int *sc, const int *order,
+                                                          const int *rank, int *color, int *ncolors, int *err) {
+    extern __shared__ unsigned char gsm[];
+    const unsigned full = 0xffffffffu;
+    int lane = threadIdx.x;
+    int nw = (n + 31) >> 5;
+    unsigned char *inV = gsm, *inBar = gsm + n, *inW = gsm + 2 * n;
+    unsigned *hat = reinterpret_cast<unsigned *>(gsm + ((3 * n + 15) & ~15));
+    unsigned *si = hat + nw;
+    for (int i = lane; i < n; i += 32) {
+        inV[i] = 1;
+        color[i] = -1;
+    }
+    __syncwarp();
+    int total = n, c = 0;
+    long steps = 0, cap = (long)n * n + 64;
+    while (total > 0) {
+        // one call of Alg. 4 (VerticesSplitting) on V, giving color c to W
+        int left = 0;
+        for (int i = lane; i < n; i += 32) {
+            inW[i] = 0;
+            inBar[i] = 0;
+            left += inV[i];
+        }
+        for (int w = lane; w < nw; w += 32) {
+            hat[w] = 0u;
+            si[w] = 0u;
+        }
+        left = warp_sum_i(left);
+        __syncwarp();
+        int nhat = 0, hmin = 0, pa = 0, nW = 0;
+        while (left > 0) {
+            if (++steps > cap) {
+                if (lane == 0) set_err(err, CPR_ERR_CUDA);
+                return;
+            }
+            // the pick: the first candidate in rank order
+            int i = -1;
+            if (nhat > 0) {
+                for (int w0 = hmin; w0 < nw && i < 0; w0 += 32) {
+                    int w = w0 + lane;
+                    unsigned bits = w < nw ? hat[w] : 0u;
+                    unsigned ball = __ballot_sync(full, bits != 0u);
+                    if (ball) {
+                        int f = __ffs(ball) - 1;
+                        unsigned wb = __shfl_sync(full, bits, f);
+                        int r = (w0 + f) * 32 + __ffs(wb) - 1;
+                        i = order[r];
+                        hmin = w0 + f;
+                    }
+                }
+            } else {
+                while (pa < n) {
+                    int r = pa + lane;
+                    int v = r < n ? order[r] : -1;
+                    bool av = v >= 0 && inV[v] && !inBar[v] && !inW[v];
+                    unsigned ball = __ballot_sync(full, av);
+                    if (ball) {
+                        int f = __ffs(ball) - 1;
+                        i = __shfl_sync(full, v, f);
+                        pa += f;
+                        break;
+                    }
+                    pa += 32;
+                }
+            }
+            if (i < 0) {   // left > 0 guarantees a candidate; never taken
+                if (lane == 0) set_err(err, CPR_ERR_CUDA);
+                return;
+            }
+            int e0 = sr[i], e1 = sr[i + 1];
+            bool any_w = false;
+            for (int p = e0 + lane; p < e1; p += 32) any_w |= inW[sc[p]] != 0;
+            any_w = __any_sync(full, any_w);
+            int ri = rank[i];
+            unsigned bi = 1u << (ri & 31);
+            bool in_hat = (hat[ri >> 5] & bi) != 0u;
+            __syncwarp();
+            if (in_hat) {
+                if (lane == 0) hat[ri >> 5] &= ~bi;
+                nhat--;
+            }
+            left--;
+            __syncwarp();
+            if (any_w) {   // a strong neighbour is in W already: i waits for a later call
+                if (lane == 0) inBar[i] = 1;
+                __syncwarp();
+                continue;
+            }
+            if (lane == 0) {
+                inW[i] = 1;
+                color[i] = c;
+            }
+            nW++;
+            // S_i: marked in si; its members still in V leave for W-bar
+            int nbar = 0, nout = 0;
+            for (int p = e0 + lane; p < e1; p += 32) {
+                int j = sc[p];
+                atomicOr(&si[j >> 5], 1u << (j & 31));
+                if (inV[j] && !inBar[j] && !inW[j]) {
+                    inBar[j] = 1;
+                    nbar++;
+                    int rj = rank[j];
+                    unsigned bj = 1u << (rj & 31);
+                    if (atomicAnd(&hat[rj >> 5], ~bj) & bj) nout++;
+                }
+            }
+            left -= warp_sum_i(nbar);
+            nhat -= warp_sum_i(nout);
+            __syncwarp();
+            // the second circle of i joins W^
+            for (int q = e0; q < e1; q++) {
+                int k = sc[q];
+                int f0 = sr[k], f1 = sr[k + 1];
+                int nin = 0, wmin = nw;
+                for (int p = f0 + lane; p < f1; p += 32) {
+                    int j = sc[p];
+                    if (j == i || !inV[j] || inBar[j] || inW[j]) continue;
+                    if (si[j >> 5] & (1u << (j & 31))) continue;
+                    int rj = rank[j];
+                    unsigned bj = 1u << (rj & 31);
+                    if (!(atomicOr(&hat[rj >> 5], bj) & bj)) {
+                        nin++;
+                        wmin = min(wmin, rj >> 5);
+                    }
+                }
+                nhat += warp_sum_i(nin);
+                wmin = __reduce_min_sync(full, (unsigned)wmin);
+                hmin = min(hmin, wmin);
+                __syncwarp();
+            }
+            for (int p = e0 + lane; p < e1; p += 32) {
+                int j = sc[p];
+                atomicAnd(&si[j >> 5], ~(1u << (j & 31)));
+            }
+            __syncwarp();
+        }
+        // the next call's V is this call's W-bar
+        for (int i = lane; i < n; i += 32) inV[i] = inBar[i];
+        __syncwarp();
+        total -= nW;
+        c++;
+    }
+    if (lane == 0) *ncolors = c;
 }
 
 // ---------------------------------------------------------------------- PMIS
@@ -2033,6 +2242,44 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
     return read_int(counters.p + 3, s) + 1;
 }
 
+// Alg. 4-5 on S (the raw Eq. 5.1 strength pattern, n <= kMaxGroupingRows);
+// returns the number of groups (colors).
+int vertices_grouping(cpr_handle *h, const Graph &S, DVec<int> &color, cudaStream_t s) {
+    int n = S.n;
+    int m = 1;
+    while (m < n) m <<= 1;
+    size_t sort_smem = sizeof(unsigned) * (size_t)m;
+    int nw = (n + 31) / 32;
+    size_t group_smem = (size_t)((3 * n + 15) & ~15) + 2 * sizeof(unsigned) * (size_t)nw;
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set.load() & bit)) {
+        CK(cudaFuncSetAttribute(k_group_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(unsigned) * kMaxGroupingRows)));
+        CK(cudaFuncSetAttribute(k_vertices_grouping, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                3 * kMaxGroupingRows + 16 + 2 * (kMaxGroupingRows / 32) * (int)sizeof(unsigned)));
+        attr_set.fetch_or(bit);
+    }
+    DVec<int> order, rank, out;   // out: [0] number of groups, [1] error flag
+    order.alloc(std::max(n, 1), s);
+    rank.alloc(std::max(n, 1), s);
+    out.alloc(2, s);
+    out.zero();
+    color.alloc(std::max(n, 1), s);
+    k_group_order<<<1, kGroupSortThreads, sort_smem, s>>>(n, S.rowptr.p, order.p, rank.p);
+    CK_LAUNCH();
+    k_vertices_grouping<<<1, 32, group_smem, s>>>(n, S.rowptr.p, S.col.p, order.p, rank.p, color.p, out.p,
+                                                  out.p + 1);
+    CK_LAUNCH();
+    int res[2] = {0, 0};
+    CK(cudaMemcpyAsync(res, out.p, sizeof(res), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (res[1]) fail(CPR_ERR_CUDA, "Alg. 4-5 grouping did not complete");
+    return res[0];
+}
+
 // Level sets of natural-order block ILU(0) over G (k_level_round), with
 // batches of rounds between host checks; returns the number of levels.
 int level_sets(const SymGraph &G, DVec<int> &level, cudaStream_t s) {
@@ -2889,7 +3136,9 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
                                        }),
                                        ub, s);
                 side.mark("c_graph");
-                L.ncolors = jp_color(h, G, 0, l, L.color, s);
+                // the paper's Alg. 4-5 on small levels (coloring = 1), else JP
+                if (h->opt.coloring == 1 && n <= h->opt.coloring_rows) L.ncolors = vertices_grouping(h, G.S, L.color, s);
+                else L.ncolors = jp_color(h, G, 0, l, L.color, s);
                 side.mark("c_jp");
                 rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
                 CK(cudaEventRecord(h->ev_color[l], s));
