@@ -220,10 +220,12 @@ def host_sequence(seed_offset=0):
 # --------------------------------------------------------------- our arm
 
 def theta_sweep(cpr, torch, J, stream, thetas=(0.0, 0.05, 0.1, 0.2, 0.3, 0.5)):
-    """The Eq. 5.1 threshold of the smoother's coloring (FP32 mode): per theta,
-    the colors of every smoothed level, the in-graph V-cycle and per-level
-    pre+post smoothing times, and one solve's iterations and time.  theta
-    changes only the coloring; the AMG hierarchy is the same."""
+    """The Eq. 5.1 threshold of the smoother's coloring (FP32 mode): per theta
+    and per coloring (JP, and the paper's Alg. 4-5 on every level of at most
+    16384 rows), the colors of every smoothed level, the in-graph V-cycle and
+    per-level pre+post smoothing times, one solve's iterations and time, and
+    the setup time.  theta and the coloring change only the smoother; the AMG
+    hierarchy is the same."""
     class DJ:
         nb = J.nb
         rowptr = torch.from_numpy(J.rowptr).cuda()
@@ -233,16 +235,26 @@ def theta_sweep(cpr, torch, J, stream, thetas=(0.0, 0.05, 0.1, 0.2, 0.3, 0.5)):
     b = torch.from_numpy(J.b).cuda()
     out = []
     for th in thetas:
-        g = cpr.Solver(DJ, precond_fp32=1, theta_color=th, stream=stream.cuda_stream)
-        _, st = g.solve(b, rtol=RTOL)          # first solve: captures the step graphs
-        x = torch.zeros_like(b)
-        _, st = g.solve(b, x, rtol=RTOL)
-        parts = g.profile_vcycle_levels(20)
-        out.append({"theta": th, "colors": [g.level(l)["ncolors"] for l in range(g.nlev - 1)],
-                    "vcycle_us": parts["vcycle_us"],
-                    "smooth_us": [p["pre"] + p["post"] for p in parts["levels"]],
-                    "iters": st["iters"], "solve_ms": st["solve_ms"], "converged": st["converged"]})
-        g.close()
+        for coloring in (0, 1):
+            g = cpr.Solver(DJ, precond_fp32=1, theta_color=th, coloring=coloring, coloring_rows=16384,
+                           stream=stream.cuda_stream)
+            _, st = g.solve(b, rtol=RTOL)          # first solve: captures the step graphs
+            x = torch.zeros_like(b)
+            _, st = g.solve(b, x, rtol=RTOL)
+            parts = g.profile_vcycle_levels(20)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.update(DJ)                           # same pattern, It > mu: a full setup
+            torch.cuda.synchronize()
+            setup_ms = 1000 * (time.perf_counter() - t0)
+            out.append({"theta": th, "coloring": "alg45" if coloring else "jp",
+                        "colors": [g.level(l)["ncolors"] for l in range(g.nlev - 1)],
+                        "rows": [g.level(l)["n"] for l in range(g.nlev - 1)],
+                        "vcycle_us": parts["vcycle_us"],
+                        "smooth_us": [p["pre"] + p["post"] for p in parts["levels"]],
+                        "iters": st["iters"], "solve_ms": st["solve_ms"], "setup_ms": setup_ms,
+                        "converged": st["converged"]})
+            g.close()
     return {"workload": f"{WORKLOAD}, FP32 preconditioner, rtol {RTOL}", "rows": out}
 
 
@@ -428,7 +440,9 @@ def e2e_arm(cpr, torch, seq_host, K, W, stream):
 
 def batched_arm(cpr, torch, K, stream, nsys=64):
     """64 independent systems (16^3 .. 64x64x16): one batched FP32-preconditioner
-    solve vs the same systems solved one after another with plain FP64 CPR."""
+    solve, timed with the fixed lanes-per-row rule and again after the
+    schedule autotuner (cpr_autotune) ran on the batch's hierarchy, vs the same
+    systems solved one after another with plain FP64 CPR."""
     specs = bs.batch_specs(nsys)
     Js = [bs.jacobian(g) for g in specs]
 
@@ -446,15 +460,26 @@ def batched_arm(cpr, torch, K, stream, nsys=64):
     for _ in range(2):
         bt.solve(bvec, xs, rtol=RTOL)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(K):
-        for x in xs:
-            x.zero_()
-        _, sts = bt.solve(bvec, xs, rtol=RTOL)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / K
+
+    def timed():
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(K):
+            for x in xs:
+                x.zero_()
+            _, sts_ = bt.solve(bvec, xs, rtol=RTOL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / K, sts_
+
+    ms_rule, _ = timed()          # the fixed lanes-per-row rule
+    rule = [bt.schedule(l) for l in range(bt.nlev - 1)]
+    t0 = time.perf_counter()
+    bp_before, bp_after = bt.autotune(reps=10)
+    tune_ms = 1000 * (time.perf_counter() - t0)
+    bt.solve(bvec, xs, rtol=RTOL)  # recaptures the step graphs with the tuned schedule
+    ms, sts = timed()
+    tuned = [bt.schedule(l) for l in range(bt.nlev - 1)]
     ok = all(st["converged"] for st in sts)
     iters = [st["iters"] for st in sts]
     bt.close()
@@ -477,6 +502,10 @@ def batched_arm(cpr, torch, K, stream, nsys=64):
     cells = sum(g.ncells for g in specs)
     return {"workload": f"{nsys} systems, 16^3..64x64x16 cells ({cells} cells), FP32 preconditioner",
             "value": nsys / (ms / 1000.0), "unit": UNIT, "ms_per_batch": ms, "all_converged": ok,
+            "autotune": {"schedule": tuned, "fixed_rule_schedule": rule, "tuning_ms": tune_ms,
+                         "fixed_rule_value": nsys / (ms_rule / 1000.0), "fixed_rule_ms_per_batch": ms_rule,
+                         "gain_over_fixed_rule": ms_rule / ms,
+                         "pressure_cycle_us_before": bp_before, "pressure_cycle_us_after": bp_after},
             "iters_max": max(iters), "iters_mean": statistics.mean(iters),
             "fp64_one_by_one": {"value": nsys / (ms_seq / 1000.0), "unit": UNIT, "ms": ms_seq},
             "speedup_vs_fp64_one_by_one": ms_seq / ms}
@@ -726,6 +755,8 @@ def main():
                     help="skip the numeric-only resetup line")
     ap.add_argument("--no-ua-amg", action="store_true",
                     help="skip the UA-AMG (amg = 1) line")
+    ap.add_argument("--no-alg45", action="store_true",
+                    help="skip the Alg. 4-5 coloring (coloring = 1) line")
     ap.add_argument("--serve-scaled", action="store_true",
                     help="serving ensemble over the scaled 32x32x8..64x64x16 range instead of the full "
                          "32x32x8..128x128x32 one")
@@ -808,6 +839,9 @@ def main():
     natural = None if args.no_bilu_natural else option_arm(
         cpr, torch, seq_dev, rhs_dev, max(3, K // 3), W, stream,
         "bilu_order = 1: the paper's level-scheduled second stage, one launch per level set", bilu_order=1)
+    alg45 = None if args.no_alg45 else option_arm(
+        cpr, torch, seq_dev, rhs_dev, K, W, stream,
+        "coloring = 1: the paper's Alg. 4-5 grouping on the levels of at most 4096 rows, JP above", coloring=1)
     ua = None if args.no_ua_amg else option_arm(
         cpr, torch, seq_dev, rhs_dev, K, W, stream,
         "amg = 1: the paper's UA-AMG first stage (double pairwise aggregation, handshake rounds with "
@@ -948,6 +982,8 @@ def main():
         line["resetup_numeric"] = numeric
     if ua is not None:
         line["ua_amg"] = ua
+    if alg45 is not None:
+        line["alg45_coloring"] = alg45
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:

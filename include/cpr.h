@@ -332,6 +332,39 @@ int cpr_profile_read(const cpr_handle *h, int family, long *count, double *ms);
  */
 int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
 
+/* ------------------------------------------------------------------------
+ * V-cycle schedule and its autotuner (not in the paper: how the kernels of
+ * Alg. 6's sweeps and the transfers map onto the GPU).  The results do not
+ * depend on the schedule beyond rounding order: every schedule gives the same
+ * hierarchy, and B's applications agree with the FP64 definition to rounding.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    int lanes_a;   /* lanes per row of the smoothing and residual kernels (A_l): 1, 2, 4, .., 32 */
+    int lanes_p;   /* lanes per row of the prolongation kernel (P_l) */
+    int lanes_r;   /* lanes per row of the restriction kernel (R_l) */
+    int block;     /* threads per CTA of these kernels: 128, 256 or 512 */
+} cpr_schedule;
+
+/* The schedule of level `level` (0 <= level < levels - 1). */
+int cpr_get_schedule(const cpr_handle *h, int level, cpr_schedule *s);
+
+/* Impose a schedule on one level of the current B (CPR_ERR_INVALID for values
+ * outside the sets above).  Kept until the next setup. */
+int cpr_set_schedule(cpr_handle *h, int level, const cpr_schedule *s);
+
+/* Time, on the device, each candidate schedule of every level of the current
+ * hierarchy -- lanes per row for the smoothing/residual, restriction and
+ * prolongation kernels in turn, then the CTA size -- each part captured `reps`
+ * times into a CUDA graph of its own and run on the handle's stream, and keep
+ * the fastest.  The choices apply at once (the Arnoldi step graphs are
+ * recaptured) and are remembered by each level's (rows, nonzeros), so later
+ * setups that build levels of the same sizes use them too.  before_us and
+ * after_us (may be NULL) receive one whole B_P application's in-graph time
+ * with the schedule before and after.  Call between solves: the timed parts
+ * overwrite the work vectors.  Allocates only what the graph timing needs. */
+int cpr_autotune(cpr_handle *h, int reps, double *before_us, double *after_us);
+
 #ifdef __cplusplus
 }
 #endif

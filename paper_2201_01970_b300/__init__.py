@@ -56,6 +56,10 @@ class LevelInfo(C.Structure):
                 ("nnz_p", C.c_int)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("lanes_a", C.c_int), ("lanes_p", C.c_int), ("lanes_r", C.c_int), ("block", C.c_int)]
+
+
 class CprError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -108,6 +112,9 @@ def lib():
         L.cpr_profile.argtypes = [vp, C.c_int]
         L.cpr_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_long), C.POINTER(C.c_double)]
         L.cpr_profile_vcycle_levels.argtypes = [vp, C.c_int, vp, C.c_int]
+        L.cpr_get_schedule.argtypes = [vp, C.c_int, C.POINTER(Schedule)]
+        L.cpr_set_schedule.argtypes = [vp, C.c_int, C.POINTER(Schedule)]
+        L.cpr_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -262,6 +269,23 @@ class Solver:
         parts = ("pre", "resid", "R", "P", "post")
         return {"vcycle_us": us[0], "bilu_us": us[1], "coarse_us": us[2],
                 "levels": [dict(zip(parts, us[3 + 5 * l: 8 + 5 * l])) for l in range(nl - 1)]}
+
+    def schedule(self, level: int) -> dict:
+        """The V-cycle schedule of one level: lanes per row of the A, P and R
+        kernels and the CTA size."""
+        sc = Schedule()
+        _check(lib().cpr_get_schedule(self._h, level, C.byref(sc)), "cpr_get_schedule")
+        return {k: getattr(sc, k) for k, _ in Schedule._fields_}
+
+    def set_schedule(self, level: int, lanes_a: int, lanes_p: int, lanes_r: int, block: int) -> None:
+        sc = Schedule(lanes_a, lanes_p, lanes_r, block)
+        _check(lib().cpr_set_schedule(self._h, level, C.byref(sc)), "cpr_set_schedule")
+
+    def autotune(self, reps: int = 10):
+        """Run the schedule autotuner; returns (B_P microseconds before, after)."""
+        b, a = C.c_double(), C.c_double()
+        _check(lib().cpr_autotune(self._h, reps, C.byref(b), C.byref(a)), "cpr_autotune")
+        return b.value, a.value
 
     def profile_read(self, family: int):
         n, ms = C.c_long(), C.c_double()

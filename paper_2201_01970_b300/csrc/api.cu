@@ -442,6 +442,34 @@ int cpr_profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
     return rc == CPR_OK ? written : rc;
 }
 
+int cpr_get_schedule(const cpr_handle *h, int level, cpr_schedule *s) {
+    if (!h || !s || level < 0 || level >= (int)h->lev.size() - 1) return CPR_ERR_INVALID;
+    const Level &L = h->lev[level];
+    *s = cpr_schedule{L.gA, L.gP, L.gR, L.bs};
+    return CPR_OK;
+}
+
+int cpr_set_schedule(cpr_handle *h, int level, const cpr_schedule *s) {
+    if (!h || !s || level < 0 || level >= (int)h->lev.size() - 1 || !schedule_ok(*s)) return CPR_ERR_INVALID;
+    Level &L = h->lev[level];
+    L.gA = s->lanes_a;
+    L.gP = s->lanes_p;
+    L.gR = s->lanes_r;
+    L.bs = s->block;
+    h->epoch++;   // the step graphs are recaptured
+    return CPR_OK;
+}
+
+int cpr_autotune(cpr_handle *h, int reps, double *before_us, double *after_us) {
+    if (!h || reps < 1 || h->lev.size() < 2) return CPR_ERR_INVALID;
+    return guarded([&] {
+        DeviceGuard dg(h->device);
+        Nvtx nv("cpr_autotune");
+        autotune(h, reps, before_us, after_us);
+        return CPR_OK;
+    });
+}
+
 int cpr_bilu_apply(cpr_handle *h, const double *r, double *z) {
     if (!h || !r || !z) return CPR_ERR_INVALID;
     return guarded([&] {

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <utility>
@@ -169,6 +170,7 @@ struct Level {
     DVec<double> diag, dinv;      // internal numbering
     DVec<float> Aoval32, Ppval32, Rpval32, diag32, dinv32;
     int gA = 8, gP = 4, gR = 8;   // lanes per row of the solve kernels
+    int bs = 256;                 // threads per CTA of the level's V-cycle kernels
     // work vectors (internal numbering); s0, s1: staging of the color being relaxed
     DVec<double> x, b, r, s0, s1;
     DVec<float> x32, b32, r32, s0_32, s1_32;
@@ -292,6 +294,9 @@ struct cpr_handle {
     cpr::BatchInfo *batch = nullptr;
     cudaEvent_t step_done[2] = {nullptr, nullptr};
     int tail_top = -1;               // first level run by the cluster tail kernel, -1 = none
+    // V-cycle schedules chosen by cpr_autotune, keyed by a level's (rows, nonzeros);
+    // a setup that builds a level of a known signature takes its schedule
+    std::map<std::pair<int, long>, cpr_schedule> sched;
 };
 
 namespace cpr {
@@ -346,6 +351,8 @@ void bilu_apply(cpr_handle *h, const double *r, double *z);
 void refresh_outer(cpr_handle *h, bool pattern_changed);
 void choose_tail(cpr_handle *h);   // decide which levels the cluster tail kernel runs
 int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
+void autotune(cpr_handle *h, int reps, double *before_us, double *after_us);
+bool schedule_ok(const cpr_schedule &s);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
 void batch_prepare(cpr_handle *h);
 int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st);

@@ -3285,6 +3285,15 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         Lv.gA = lanes_for((double)Lv.Ao.nnz / n, n / std::max(1, Lv.ncolors), 1L << 16);
         Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
         Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
+        Lv.bs = 256;
+        // a schedule the autotuner chose for a level of these sizes takes precedence
+        auto it = h->sched.find({Lv.A.n, (long)Lv.A.nnz});
+        if (it != h->sched.end()) {
+            Lv.gA = it->second.lanes_a;
+            Lv.gP = it->second.lanes_p;
+            Lv.gR = it->second.lanes_r;
+            Lv.bs = it->second.block;
+        }
     };
     for (int l = 0; l < L - 1; l++) {
         side.wait(l, s);
@@ -3339,8 +3348,9 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             }
             Lv.gscal.alloc(2 * m + 2, s);
             Lv.gscal.zero();
-            // partials of the widest launch: the level's matrix-vector kernel, up to 32 lanes a row
-            Lv.gpart.alloc(2 * ((32 * (size_t)n + 255) / 256 + 1184), s);
+            // partials of the widest launch: the level's matrix-vector kernel, up to 32 lanes a
+            // row in CTAs of at least 128 threads
+            Lv.gpart.alloc(2 * ((32 * (size_t)n + 127) / 128 + 1184), s);
             Lv.gcnt.alloc(2, s);
             Lv.gcnt.zero();
         }

@@ -1084,7 +1084,9 @@ void with_lanes(int g, F f);
     default: { constexpr int G = 32; CALL; break; } \
     }
 
-inline unsigned blocks_for(long threads) { return (unsigned)std::max<long>(1, (threads + kBlock - 1) / kBlock); }
+inline unsigned blocks_for(long threads, int block = kBlock) {
+    return (unsigned)std::max<long>(1, (threads + block - 1) / block);
+}
 
 // Launch one kernel of the B-application chain: with programmatic dependent
 // launch when the handle asks for it (the kernel's prologue may then overlap
@@ -1124,13 +1126,13 @@ void mcgs_sweep(cpr_handle *h, Level &L, bool descending, bool from_zero, Pendin
         if (from_zero && t == 0 && first_done) {
             // the producer of b already did this color's from-zero work
         } else if (from_zero && t == 0) {
-            launch_b(h, k_smooth_first<T>, blocks_for(n), kBlock, s, n, c0, c1, b, Vals<T>::dinv(L), x,
+            launch_b(h, k_smooth_first<T>, blocks_for(n, L.bs), L.bs, s, n, c0, c1, b, Vals<T>::dinv(L), x,
                      Vals<T>::s(L, k), done);
         } else {
             long thr = std::max<long>((long)(c1 - c0) * L.gA, pd.p1 - pd.p0);
             bool fine = &L == &h->lev[0];
             if (fine) prof_begin(h, CPR_PROF_SMOOTH0);
-            CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_smooth_color<T, G>, blocks_for(thr), kBlock, s, c0, c1, pd.p0,
+            CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_smooth_color<T, G>, blocks_for(thr, L.bs), L.bs, s, c0, c1, pd.p0,
                                                pd.p1, L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), b,
                                                Vals<T>::dinv(L), x, Vals<T>::s(L, pd.k), Vals<T>::s(L, k), done)));
             if (fine) prof_end(h);
@@ -1241,7 +1243,7 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
     for (int k = 0; k < h->opt.pre; k++)
         mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0, Vals<T>::b(L), Vals<T>::x(L));
     long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
-    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr, L.bs), L.bs, s, n, pd.p0, pd.p1,
                                        L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), Vals<T>::b(L),
                                        Vals<T>::x(L), Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     pd = Pending{};
@@ -1249,18 +1251,18 @@ void vcycle(cpr_handle *h, int l, Pending &out, const int *done, bool first_done
     // C is smoothed from zero by the next kernel unless the cluster tail takes it
     bool fuse = l + 1 < (int)h->lev.size() - 1 && h->opt.pre > 0 && l + 1 != h->tail_top;
     if (fuse) {
-        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer_first<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer_first<T, G>, blocks_for((long)L.Rp.n * L.gR, L.bs), L.bs, s,
                                            L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
                                            Vals<T>::b(C), Vals<T>::dinv(C), Vals<T>::x(C), Vals<T>::s(C, 1),
                                            C.color_off[0], C.color_off[1], done)));
     } else {
-        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR, L.bs), L.bs, s,
                                            L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
                                            Vals<T>::r(L), 0, 0, Vals<T>::b(C), false, done)));
     }
     Pending cp;
     vcycle<T>(h, l + 1, cp, done, fuse);
-    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP, L.bs), L.bs, s, n,
                                        L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
                                        Vals<T>::s(C, cp.k), cp.p0, cp.p1, Vals<T>::x(L), true, done)));
     for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done, false, Vals<T>::b(L), Vals<T>::x(L));
@@ -1307,12 +1309,12 @@ void kcycle(cpr_handle *h, int l, const T *b, T *x, Pending &out, const int *don
     }
     for (int k = 0; k < h->opt.pre; k++) mcgs_sweep<T>(h, L, false, k == 0, pd, done, first_done && k == 0, b, x);
     long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
-    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+    CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr, L.bs), L.bs, s, n, pd.p0, pd.p1,
                                        L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), b, x,
                                        Vals<T>::s(L, pd.k), Vals<T>::r(L), done)));
     pd = Pending{};
     Level &C = h->lev[l + 1];
-    CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s, L.Rp.n,
+    CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR, L.bs), L.bs, s, L.Rp.n,
                                        L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L), Vals<T>::r(L), 0, 0,
                                        Vals<T>::b(C), false, done)));
     if (l + 1 == last)
@@ -1320,7 +1322,7 @@ void kcycle(cpr_handle *h, int l, const T *b, T *x, Pending &out, const int *don
                  Vals<T>::x(C), done);
     else
         amli_coarse<T>(h, l + 1, done);   // e = x(C), fully written
-    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+    CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP, L.bs), L.bs, s, n,
                                        L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C), Vals<T>::s(C, 0), 0,
                                        0, x, true, done)));
     for (int k = 0; k < h->opt.post; k++) mcgs_sweep<T>(h, L, true, false, pd, done, false, b, x);
@@ -1342,7 +1344,7 @@ void amli_coarse(cpr_handle *h, int k, const int *done) {
         kcycle<T>(h, k, res, v, pv, done);
         long thr = std::max<long>((long)n * L.gA, pv.p1 - pv.p0);
         const T *y = t == 0 ? res : Vals<T>::gw(L);
-        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_amli_mv<T, G>, blocks_for(thr), kBlock, s, n, pv.p0, pv.p1,
+        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_amli_mv<T, G>, blocks_for(thr, L.bs), L.bs, s, n, pv.p0, pv.p1,
                                            L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L), v,
                                            Vals<T>::s(L, pv.k), w, y, t, L.gscal.p, m, L.gpart.p, L.gcnt.p, done)));
         for (int u = 0; u < t; u++) {
@@ -1630,18 +1632,18 @@ void level_part(cpr_handle *h, int l, int part) {
     } else if (part == 1) {
         pd = Pending{L.color_off[L.ncolors - 1], L.color_off[L.ncolors], 0};
         long thr = std::max<long>((long)n * L.gA, pd.p1 - pd.p0);
-        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr), kBlock, s, n, pd.p0, pd.p1,
+        CPR_LANES_DISPATCH(L.gA, (launch_b(h, k_resid_commit<T, G>, blocks_for(thr, L.bs), L.bs, s, n, pd.p0, pd.p1,
                                            L.Ao.rowptr.p, L.Ao.col.p, Vals<T>::Ao(L), Vals<T>::diag(L),
                                            Vals<T>::b(L), Vals<T>::x(L), Vals<T>::s(L, 0), Vals<T>::r(L),
                                            (const int *)nullptr)));
     } else if (part == 2) {
         Level &C = h->lev[l + 1];
-        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR), kBlock, s,
+        CPR_LANES_DISPATCH(L.gR, (launch_b(h, k_transfer<T, G>, blocks_for((long)L.Rp.n * L.gR, L.bs), L.bs, s,
                                            L.Rp.n, L.Rp.rowptr.p, L.Rp.col.p, Vals<T>::R(L), Vals<T>::r(L),
                                            Vals<T>::r(L), 0, 0, Vals<T>::b(C), false, (const int *)nullptr)));
     } else if (part == 3) {
         Level &C = h->lev[l + 1];
-        CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP), kBlock, s, n,
+        CPR_LANES_DISPATCH(L.gP, (launch_b(h, k_transfer<T, G>, blocks_for((long)n * L.gP, L.bs), L.bs, s, n,
                                            L.Pp.rowptr.p, L.Pp.col.p, Vals<T>::P(L), Vals<T>::x(C),
                                            Vals<T>::s(C, 0), 0, 0, Vals<T>::x(L), true, (const int *)nullptr)));
     } else {
@@ -1713,6 +1715,77 @@ void choose_tail(cpr_handle *h) {
         return;
     }
     h->tail_top = top;
+}
+
+bool schedule_ok(const cpr_schedule &s) {
+    auto lanes = [](int g) { return g >= 1 && g <= 32 && (g & (g - 1)) == 0; };
+    return lanes(s.lanes_a) && lanes(s.lanes_p) && lanes(s.lanes_r) &&
+           (s.block == 128 || s.block == 256 || s.block == 512);
+}
+
+namespace {
+
+// The tuner of cpr_autotune, per level: the lanes of each kernel family (the
+// smoothing sweeps with the residual, the restriction, the prolongation)
+// timed over the candidates with the others fixed, then the CTA size over
+// all five parts.  A candidate replaces the current choice only when it is at
+// least 2 % faster, so timing noise does not flip a choice back and forth.
+template <class T>
+void autotune_t(cpr_handle *h, int reps, double *before_us, double *after_us) {
+    static const int lanes[] = {1, 2, 4, 8, 16, 32};
+    static const int blocks[] = {128, 256, 512};
+    auto vc = [&] { return graph_us(h, reps, [&] { pressure_top<T>(h, Vals<T>::ep(h), nullptr); }); };
+    double before = vc();
+    int L = (int)h->lev.size();
+    for (int l = 0; l < L - 1; l++) {
+        Level &Lv = h->lev[l];
+        auto parts = [&](std::initializer_list<int> ps) {
+            double t = 0.0;
+            for (int part : ps) t += graph_us(h, reps, [&] { level_part<T>(h, l, part); });
+            return t;
+        };
+        auto pick = [&](int *field, std::initializer_list<int> ps, const int *cand, int ncand) {
+            double best = parts(ps);
+            int choice = *field;
+            for (int k = 0; k < ncand; k++) {
+                if (cand[k] == choice) continue;
+                int keep = *field;
+                *field = cand[k];
+                double t = parts(ps);
+                if (t < 0.98 * best) {
+                    best = t;
+                    choice = cand[k];
+                } else {
+                    *field = keep;
+                }
+                *field = choice;
+            }
+        };
+        pick(&Lv.gA, {0, 1, 4}, lanes, 6);
+        pick(&Lv.gR, {2}, lanes, 6);
+        pick(&Lv.gP, {3}, lanes, 6);
+        pick(&Lv.bs, {0, 1, 2, 3, 4}, blocks, 3);
+        h->sched[{Lv.A.n, (long)Lv.A.nnz}] = cpr_schedule{Lv.gA, Lv.gP, Lv.gR, Lv.bs};
+    }
+    h->epoch++;   // the step graphs are recaptured with the new schedule
+    double after = vc();
+    if (before_us) *before_us = before;
+    if (after_us) *after_us = after;
+}
+
+}  // namespace
+
+void autotune(cpr_handle *h, int reps, double *before_us, double *after_us) {
+    bool prof = h->prof;
+    h->prof = false;   // no event nodes inside the timed graphs
+    try {
+        if (h->opt.precond_fp32) autotune_t<float>(h, reps, before_us, after_us);
+        else autotune_t<double>(h, reps, before_us, after_us);
+    } catch (...) {
+        h->prof = prof;
+        throw;
+    }
+    h->prof = prof;
 }
 
 int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us) {
