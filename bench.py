@@ -520,14 +520,17 @@ def serve_arm(full: bool):
     from paper_2201_01970_b300 import serve
     members = bs.ensemble_specs(32, full=full)
     reqs = serve.poisson_requests(members, steps=5, rate=200.0, seed=0)
-    # 16 concurrent solves: most members' systems are small (8k-524k cells),
-    # so one solve leaves most of the GPU idle; a slot sweep (4/8/12/16) on the
-    # scaled ensemble measured 81/120/137/152 solves/s
-    srv = serve.Server(slots=16, precond_fp32=1, mu=MU)
+    for r in reqs:          # the payloads arrive in page-locked receive buffers
+        serve.pin_request(r)
+    # 16 concurrent solves driven by one polling thread, first setups on 4
+    # helper threads: the best of a sweep over 16/24/32 slots and 4/8/16
+    # helpers on this ensemble (throughput ~169/s in every case that kept up;
+    # p99 lowest with 16 and 4)
+    srv = serve.Server(slots=16, setup_workers=4, precond_fp32=1, mu=MU)
     m = srv.run(reqs, realtime=True)
     srv.close()
     ok = all(r.stats.get("converged") for r in reqs)
-    base = [serve.Request(r.member, r.step, r.A, r.b, r.arrival) for r in reqs]
+    base = [serve.Request(r.member, r.step, r.A, r.b, r.arrival, same_pattern=r.same_pattern) for r in reqs]
     srv = serve.Server(slots=1, precond_fp32=0, mu=0)
     mb = srv.run(base, realtime=False)
     srv.close()
@@ -762,6 +765,8 @@ def main():
                          "32x32x8..128x128x32 one")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
                     help="precision arms to time (the JSON line needs both)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="only run the serving arm and print its object")
     ap.add_argument("--adaptive-sweep", action="store_true",
                     help="only run Alg. 3's mu sweep on the 60x220x85 sequence and print it")
     ap.add_argument("--profile-region", action="store_true",
@@ -791,6 +796,11 @@ def main():
         res = theta_sweep(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
         if rank == 0:
             print(json.dumps({"theta_sweep": res}), flush=True)
+        return
+    if args.serve_only:
+        res = serve_arm(not args.serve_scaled)
+        if rank == 0:
+            print(json.dumps({"serving": res}), flush=True)
         return
     if args.setup_profile:
         res = setup_profile(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)

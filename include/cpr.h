@@ -47,6 +47,7 @@ extern "C" {
 
 #define CPR_OK 0
 #define CPR_NOT_CONVERGED 1
+#define CPR_RUNNING 2          /* cpr_solve_poll: the solve is still in progress */
 #define CPR_ERR_INVALID (-1)   /* malformed matrix, sizes or options */
 #define CPR_ERR_CUDA (-2)      /* a CUDA call failed */
 #define CPR_ERR_OOM (-3)       /* device memory exhausted */
@@ -159,6 +160,15 @@ int cpr_setup(cpr_handle **h, const cpr_bsr3 *A, const cpr_opts *opts);
 int cpr_update(cpr_handle *h, const cpr_bsr3 *A);
 
 /*
+ * cpr_update for a Jacobian with exactly the current A's block pattern:
+ * only its 9*nnzb values are passed (host or device pointer).  The pattern is
+ * neither uploaded, validated nor compared, so the call makes no host round
+ * trip before Alg. 3's decision; the caller guarantees the pattern (a Newton
+ * sequence of one simulation keeps it).  Not for batch handles.
+ */
+int cpr_update_values(cpr_handle *h, const double *val);
+
+/*
  * Solve A^(k) x = b by FGMRES(m) right-preconditioned with B (Alg. 2): x is
  * the initial guess on entry and the solution on return.  Stops when the true
  * residual satisfies ||b - A x|| < rtol ||b - A x_0|| or after max_restarts
@@ -166,6 +176,20 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A);
  * NULL.
  */
 int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
+
+/*
+ * cpr_solve in two halves, for a host thread that drives many handles (a
+ * serving loop): cpr_solve_start issues the solve's first work and returns
+ * without waiting; each cpr_solve_poll issues what the finished device work
+ * allows (the next Arnoldi steps, the next restart cycle) and returns
+ * CPR_RUNNING, or, once the solve has finished, its cpr_solve return code with
+ * x (host x copied back) and st filled.  The same kernels run in the same
+ * order as in cpr_solve, so results are bit-identical.  While a solve is in
+ * progress the handle accepts only cpr_solve_poll and cpr_destroy (other
+ * calls return CPR_ERR_INVALID).  b and x must stay valid until it finishes.
+ */
+int cpr_solve_start(cpr_handle *h, const double *b, double *x, double rtol);
+int cpr_solve_poll(cpr_handle *h, cpr_stats *st);
 
 /* Release every resource of the handle (NULL is accepted). */
 void cpr_destroy(cpr_handle *h);

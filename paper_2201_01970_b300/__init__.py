@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libcpr_b300.so")
 
 CPR_OK = 0
 CPR_NOT_CONVERGED = 1
+CPR_RUNNING = 2
 CPR_ERR_INVALID = -1
 CPR_ERR_CUDA = -2
 CPR_ERR_OOM = -3
@@ -87,7 +88,10 @@ def lib():
         L.cpr_default_opts.argtypes = [C.POINTER(Opts)]
         L.cpr_setup.argtypes = [C.POINTER(vp), C.POINTER(Bsr3), C.POINTER(Opts)]
         L.cpr_update.argtypes = [vp, C.POINTER(Bsr3)]
+        L.cpr_update_values.argtypes = [vp, vp]
         L.cpr_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Stats)]
+        L.cpr_solve_start.argtypes = [vp, vp, vp, C.c_double]
+        L.cpr_solve_poll.argtypes = [vp, C.POINTER(Stats)]
         L.cpr_destroy.argtypes = [vp]
         L.cpr_strerror.argtypes = [C.c_int]
         L.cpr_strerror.restype = C.c_char_p
@@ -189,6 +193,12 @@ class Solver:
         _check(lib().cpr_update(self._h, C.byref(d)), "cpr_update")
         self.nb, self.nnzb = d.nb, d.nnzb
 
+    def update_values(self, val) -> None:
+        """cpr_update_values: a new Jacobian with the current pattern (its 9 nnzb values only)."""
+        if isinstance(val, np.ndarray):
+            val = np.ascontiguousarray(val, dtype=np.float64)
+        _check(lib().cpr_update_values(self._h, _ptr(val)), "cpr_update_values")
+
     def solve(self, b, x=None, rtol: float = 1e-6):
         """Solve A x = b; returns (x, stats).  x (initial guess) is overwritten in place."""
         if x is None:
@@ -200,6 +210,24 @@ class Solver:
         st = Stats()
         rc = lib().cpr_solve(self._h, _ptr(b), _ptr(x), float(rtol), C.byref(st))
         _check(rc, "cpr_solve", allow_not_converged=True)
+        return x, st.as_dict()
+
+    def solve_start(self, b, x, rtol: float = 1e-6) -> None:
+        """Start a solve without waiting (cpr_solve_start); b and x must stay
+        alive until poll() reports the end."""
+        self._pending = (b, x)
+        _check(lib().cpr_solve_start(self._h, _ptr(b), _ptr(x), float(rtol)), "cpr_solve_start")
+
+    def poll(self):
+        """Advance a started solve (cpr_solve_poll): None while it runs, else
+        (x, stats) once it has finished."""
+        st = Stats()
+        rc = lib().cpr_solve_poll(self._h, C.byref(st))
+        if rc == CPR_RUNNING:
+            return None
+        x = self._pending[1]
+        self._pending = None
+        _check(rc, "cpr_solve_poll", allow_not_converged=True)
         return x, st.as_dict()
 
     # component applications (device tensors)

@@ -62,11 +62,6 @@ __global__ void k_compare(long n, const int *a, const int *b, int *diff) {
         if (a[i] != b[i]) atomicExch(diff, 1);
 }
 
-__global__ void k_has_nonfinite(long n, const double *a, int *flag) {
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        if (!isfinite(a[i])) atomicExch(flag, 1);
-}
-
 void build_timed(cpr_handle *h, bool numeric = false) {
     double t0 = now_ms();
     build_preconditioner(h, numeric);
@@ -285,7 +280,7 @@ int cpr_setup(cpr_handle **out, const cpr_bsr3 *A, const cpr_opts *opts) {
 }
 
 int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
-    if (!h) return CPR_ERR_INVALID;
+    if (!h || h->fs.phase != FgmresState::IDLE) return CPR_ERR_INVALID;
     return guarded([&] {
         DeviceGuard dg(h->device);
         Nvtx nv("cpr_update");
@@ -326,47 +321,112 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
     });
 }
 
+int cpr_update_values(cpr_handle *h, const double *val) {
+    if (!h || !val || h->batch || h->fs.phase != FgmresState::IDLE) return CPR_ERR_INVALID;
+    return guarded([&] {
+        DeviceGuard dg(h->device);
+        Nvtx nv("cpr_update_values");
+        copy_in(h->val.p, val, sizeof(double) * 9 * (size_t)h->nnzb, h->stream);
+        refresh_outer(h, false);
+        h->updates++;
+        // Alg. 3 with an unchanged pattern (Remark 4.2 holds by the caller's guarantee)
+        bool reuse = h->have_B && h->last_iters >= 0 && h->last_iters <= h->opt.mu;
+        if (reuse) {
+            if (h->opt.reuse_refresh) refresh_second_residual(h);
+            h->setup_called = 0;
+            h->setup_ms = 0.0;
+            return CPR_OK;
+        }
+        build_timed(h, h->opt.resetup && h->have_B);
+        return CPR_OK;
+    });
+}
+
+namespace {
+
+// b and x of a solve on the device: host buffers are copied into the
+// handle's vectors (x is copied back by finish_solve).
+void solve_prelude(cpr_handle *h, const double *b, double *x, double rtol) {
+    double t0 = now_ms();
+    cudaStream_t s = h->stream;
+    size_t bytes = sizeof(double) * 3 * (size_t)h->nb;
+    const double *db = b;
+    double *dx = x;
+    if (!is_device_ptr(b)) {
+        CK(cudaMemcpyAsync(h->dev_b.p, b, bytes, cudaMemcpyHostToDevice, s));
+        db = h->dev_b.p;
+    }
+    bool xdev = is_device_ptr(x);
+    if (!xdev) {
+        CK(cudaMemcpyAsync(h->dev_x.p, x, bytes, cudaMemcpyHostToDevice, s));
+        dx = h->dev_x.p;
+    }
+    fgmres_begin(h, db, dx, rtol);
+    h->fs.x_out = xdev ? nullptr : x;
+    h->fs.t0 = t0;
+}
+
+int finish_solve(cpr_handle *h, int rc, cpr_stats *st) {
+    cudaStream_t s = h->stream;
+    prof_flush(h);
+    if (h->fs.x_out)
+        CK(cudaMemcpyAsync(h->fs.x_out, h->fs.x, sizeof(double) * 3 * (size_t)h->nb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    cpr_stats local{};
+    fgmres_stats(h, &local);
+    local.setup_called = h->setup_called;
+    local.setup_count = h->setup_count;
+    local.levels = (int)h->lev.size();
+    local.tail_levels = h->tail_top >= 0 ? (int)h->lev.size() - 1 - h->tail_top : 0;
+    local.setup_ms = h->setup_called ? h->setup_ms : 0.0;
+    local.solve_ms = now_ms() - h->fs.t0;
+    h->fs.phase = FgmresState::IDLE;
+    if (st) *st = local;
+    return rc;
+}
+
+bool solving(const cpr_handle *h) { return h->fs.phase != FgmresState::IDLE; }
+
+}  // namespace
+
 int cpr_solve(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
-    if (!h || !b || !x || !(rtol > 0.0) || h->batch) return CPR_ERR_INVALID;
+    if (!h || !b || !x || !(rtol > 0.0) || h->batch || solving(h)) return CPR_ERR_INVALID;
     return guarded([&] {
         DeviceGuard dg(h->device);
         Nvtx nv("cpr_solve");
-        double t0 = now_ms();
-        cudaStream_t s = h->stream;
-        size_t bytes = sizeof(double) * 3 * (size_t)h->nb;
-        bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
-        const double *db = b;
-        double *dx = x;
-        if (!bdev) {
-            CK(cudaMemcpyAsync(h->dev_b.p, b, bytes, cudaMemcpyHostToDevice, s));
-            db = h->dev_b.p;
+        solve_prelude(h, b, x, rtol);
+        int rc;
+        while ((rc = fgmres_advance(h, true)) == 1) {
         }
-        if (!xdev) {
-            CK(cudaMemcpyAsync(h->dev_x.p, x, bytes, cudaMemcpyHostToDevice, s));
-            dx = h->dev_x.p;
-        }
-        {
-            DVec<int> flag;
-            flag.alloc(1, s);
-            flag.zero();
-            k_has_nonfinite<<<grid_for(3L * h->nb, 256, 1184), 256, 0, s>>>(3L * h->nb, db, flag.p);
-            CK_LAUNCH();
-            if (read_int(flag.p, s)) fail(CPR_ERR_BREAKDOWN, "non-finite right-hand side");
-        }
-        cpr_stats local{};
-        int rc = fgmres(h, db, dx, rtol, &local);
-        prof_flush(h);
-        if (!xdev) CK(cudaMemcpyAsync(x, dx, bytes, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        local.setup_called = h->setup_called;
-        local.setup_count = h->setup_count;
-        local.levels = (int)h->lev.size();
-        local.tail_levels = h->tail_top >= 0 ? (int)h->lev.size() - 1 - h->tail_top : 0;
-        local.setup_ms = h->setup_called ? h->setup_ms : 0.0;
-        local.solve_ms = now_ms() - t0;
-        if (st) *st = local;
-        return rc;
+        return finish_solve(h, rc, st);
     });
+}
+
+int cpr_solve_start(cpr_handle *h, const double *b, double *x, double rtol) {
+    if (!h || !b || !x || !(rtol > 0.0) || h->batch || solving(h)) return CPR_ERR_INVALID;
+    return guarded([&] {
+        DeviceGuard dg(h->device);
+        Nvtx nv("cpr_solve_start");
+        solve_prelude(h, b, x, rtol);
+        int rc = fgmres_advance(h, false);
+        if (rc != 1) {   // finished at once (zero right-hand side, a non-finite b seen immediately)
+            h->fs.phase = FgmresState::DONE;
+            h->fs.rc = rc;
+        }
+        return CPR_OK;
+    });
+}
+
+int cpr_solve_poll(cpr_handle *h, cpr_stats *st) {
+    if (!h || !solving(h)) return CPR_ERR_INVALID;
+    int rc = guarded([&] {
+        DeviceGuard dg(h->device);
+        int r = fgmres_advance(h, false);
+        if (r == 1) return CPR_RUNNING;
+        return finish_solve(h, r, st);
+    });
+    if (rc < 0 && rc != CPR_RUNNING) h->fs.phase = FgmresState::IDLE;
+    return rc;
 }
 
 void cpr_destroy(cpr_handle *h) {

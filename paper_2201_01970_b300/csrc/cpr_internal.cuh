@@ -215,6 +215,22 @@ struct BatchInfo {
 
 }  // namespace cpr
 
+namespace cpr {
+// A solve in progress: FGMRES (Alg. 2) as a state machine that the blocking
+// cpr_solve drives to the end and cpr_solve_poll advances without waiting.
+struct FgmresState {
+    enum { IDLE = 0, START = 1, WAIT_START = 2, STEPS = 3, WAIT_FINAL = 4, DONE = 5 };
+    int phase = IDLE;
+    const double *b = nullptr;   // device right-hand side
+    double *x = nullptr;         // device iterate
+    double *x_out = nullptr;     // the caller's host x, written at the end (null: x is the caller's)
+    double rtol = 0.0, norm0 = 0.0, rnorm = 0.0, t0 = 0.0;
+    int cycle = 0, cycles = 0, iters = 0, rc = 0;
+    int launched = 0, checked = 0, steps = 0;
+    bool stop = false;
+};
+}  // namespace cpr
+
 // The opaque handle of the C ABI.
 struct cpr_handle {
     cpr_opts opt{};
@@ -293,6 +309,9 @@ struct cpr_handle {
     int sgb_epoch = -1;
     cpr::BatchInfo *batch = nullptr;
     cudaEvent_t step_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_norm = nullptr;   // a cycle's start (residual norm, flags) is on the host
+    cpr::FgmresState fs;
+    cpr::DVec<int> bflag;            // b holds a NaN or Inf (checked with the first norm)
     int tail_top = -1;               // first level run by the cluster tail kernel, -1 = none
     // V-cycle schedules chosen by cpr_autotune, keyed by a level's (rows, nonzeros);
     // a setup that builds a level of a known signature takes its schedule
@@ -354,6 +373,9 @@ int profile_vcycle_levels(cpr_handle *h, int reps, double *us, int n_us);
 void autotune(cpr_handle *h, int reps, double *before_us, double *after_us);
 bool schedule_ok(const cpr_schedule &s);
 int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st);
+void fgmres_begin(cpr_handle *h, const double *b, double *x, double rtol);
+int fgmres_advance(cpr_handle *h, bool block);   // 1 while running, else the solve's return code
+void fgmres_stats(const cpr_handle *h, cpr_stats *st);
 void batch_prepare(cpr_handle *h);
 int fgmres_batch(cpr_handle *h, double rtol, cpr_stats *st);
 void bsr3_spmv(int nb, const int *rowptr, const int *col, const double *val, const double *x,

@@ -565,6 +565,11 @@ __global__ void k_zero(long n, T *a, const int *done) {
         a[i] = 0;
 }
 
+__global__ void k_has_nonfinite_b(long n, const double *a, int *flag) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicExch(flag, 1);
+}
+
 // ------------------------------------------------------------ Krylov kernels
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1880,110 +1885,204 @@ void ensure_step_graphs(cpr_handle *h) {
 // Flexible GMRES(m), right-preconditioned with B (Alg. 2): CGS Arnoldi, Givens
 // rotations on the device, stop on |g_{j+1}| < rtol ||r_0|| or h_{j+1,j} = 0,
 // true residual after every cycle.  The host reads one flag per step and one
-// norm per cycle.
-int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
+// norm per cycle.  It runs as a state machine (FgmresState): each call of
+// fgmres_advance issues what can be issued and, unless `block`, returns
+// instead of waiting on the device, so one host thread can drive many solves.
+// Blocking or not, the same work is launched in the same order.
+//
+// Steps: step j's graph is launched before the host reads step j-1's flags
+// (at most two steps in flight); a step launched after convergence finds
+// `done` set and does nothing.
+
+namespace {
+
+bool event_ready(cudaEvent_t e, bool block) {
+    if (block) {
+        CK(cudaEventSynchronize(e));
+        return true;
+    }
+    cudaError_t q = cudaEventQuery(e);
+    if (q == cudaErrorNotReady) {
+        cudaGetLastError();
+        return false;
+    }
+    CK(q);
+    return true;
+}
+
+// r = b - A x, beta = ||r|| and its host copy; first: the cycle-0 scalars.
+void issue_cycle_start(cpr_handle *h, bool first) {
+    FgmresState &F = h->fs;
     cudaStream_t s = h->stream;
     int m = h->opt.restart;
     long N = 3L * h->nb;
     ScalLayout SL{m};
+    spmv_h(h, F.x, 0, nullptr, F.b, h->r.p, s, nullptr);
+    norm_partials(h, h->r.p, N);
+    k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, h->dscal.p, m, h->dint.p, first, F.rtol);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(h->pinned, h->dscal.p + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (first)
+        CK(cudaMemcpyAsync(reinterpret_cast<int *>(h->pinned + 16), h->bflag.p, sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h->ev_norm, s));
+}
+
+}  // namespace
+
+void fgmres_begin(cpr_handle *h, const double *b, double *x, double rtol) {
+    FgmresState &F = h->fs;
+    F = FgmresState{};
+    F.b = b;
+    F.x = x;
+    F.rtol = rtol;
+    F.rc = CPR_NOT_CONVERGED;
+    F.phase = FgmresState::START;
+    cudaStream_t s = h->stream;
+    if (!h->ev_norm) CK(cudaEventCreateWithFlags(&h->ev_norm, cudaEventDisableTiming));
+    if (!h->bflag.p) h->bflag.alloc(1, s);
+    CK(cudaMemsetAsync(h->bflag.p, 0, sizeof(int), s));
+    k_has_nonfinite_b<<<grid_for(3L * h->nb, 256, 1184), 256, 0, s>>>(3L * h->nb, b, h->bflag.p);
+    CK_LAUNCH();
+}
+
+int fgmres_advance(cpr_handle *h, bool block) {
+    FgmresState &F = h->fs;
+    cudaStream_t s = h->stream;
+    int m = h->opt.restart;
+    long N = 3L * h->nb;
     int *di = h->dint.p;
     double *sc = h->dscal.p;
-    const int *done = di + I_DONE;
-    int iters = 0, cycles = 0, rc = CPR_NOT_CONVERGED;
-    double norm0 = 0.0, rnorm = 0.0;
-    int ldp = kMaxRestart + 2;
-    for (int cycle = 0; cycle < h->opt.max_restarts; cycle++) {
-        Nvtx nv("FGMRES cycle");
-        // r = b - A x, beta = ||r||, V_0 = r / beta
-        spmv_h(h, x, 0, nullptr, b, h->r.p, s, nullptr);
-        norm_partials(h, h->r.p, N);
-        k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, cycle == 0, rtol);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rnorm = h->pinned[0];
-        if (cycle == 0) norm0 = rnorm;
-        if (!std::isfinite(rnorm)) {
-            rc = CPR_ERR_BREAKDOWN;
-            break;
+    int *pin = reinterpret_cast<int *>(h->pinned + 8);   // two slots of 4 ints
+    auto check = [&](int step) {
+        const int *f = pin + 4 * (step & 1);
+        if (f[I_K] == step + 1) {
+            F.steps = step + 1;
+            if (h->prof) prof_collect_graph(h, step & 1);
         }
-        if (cycle == 0 && norm0 == 0.0) {
-            rc = CPR_OK;
-            break;
+        if (f[I_BREAK]) {
+            F.rc = CPR_ERR_BREAKDOWN;
+            F.stop = true;
+        } else if (f[I_DONE]) {
+            F.stop = true;
         }
-        if (cycle > 0 && rnorm / norm0 < rtol) {
-            rc = CPR_OK;
-            break;
-        }
-        k_scale_into<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->r.p, h->V.p, sc, m);
-        CK_LAUNCH();
-        cycles++;
-        ensure_step_graphs(h);
-        int *pin = reinterpret_cast<int *>(h->pinned + 8);   // two slots of 4 ints
-        int launched = 0, steps = 0;
-        bool stop = false;
-        // Step j's graph is launched before the host reads step j-1's flags;
-        // a step launched after convergence finds `done` set and does nothing.
-        auto check = [&](int step) {
-            const int *f = pin + 4 * (step & 1);
-            bool real = f[I_K] == step + 1;
-            if (real) {
-                steps = step + 1;
-                if (h->prof) prof_collect_graph(h, step & 1);
+    };
+    for (;;) {
+        switch (F.phase) {
+        case FgmresState::START:
+            if (F.cycle >= h->opt.max_restarts) {
+                if (F.rc == CPR_NOT_CONVERGED && F.cycles == h->opt.max_restarts) {
+                    issue_cycle_start(h, false);   // the true residual after the last cycle
+                    F.phase = FgmresState::WAIT_FINAL;
+                } else {
+                    F.phase = FgmresState::DONE;
+                }
+                continue;
             }
-            if (f[I_BREAK]) {
-                rc = CPR_ERR_BREAKDOWN;
-                stop = true;
-            } else if (f[I_DONE]) {
-                stop = true;
+            issue_cycle_start(h, F.cycle == 0);
+            F.phase = FgmresState::WAIT_START;
+            continue;
+        case FgmresState::WAIT_START: {
+            if (!event_ready(h->ev_norm, block)) return 1;
+            if (F.cycle == 0 && reinterpret_cast<int *>(h->pinned + 16)[0]) {
+                set_last_error("non-finite right-hand side");
+                F.rc = CPR_ERR_BREAKDOWN;
+                F.phase = FgmresState::DONE;
+                continue;
             }
-        };
-        for (int j = 0; j < m && !stop; j++) {
-            CK(cudaGraphLaunch(h->sg[j & 1].exec, s));
-            count_launches(h->sg[j & 1].kernels);
-            CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-            CK(cudaEventRecord(h->step_done[j & 1], s));
-            launched = j + 1;
-            if (j >= 1) {
-                CK(cudaEventSynchronize(h->step_done[(j - 1) & 1]));
-                check(j - 1);
+            F.rnorm = h->pinned[0];
+            if (F.cycle == 0) F.norm0 = F.rnorm;
+            bool fin = true;
+            if (!std::isfinite(F.rnorm)) F.rc = CPR_ERR_BREAKDOWN;
+            else if (F.cycle == 0 && F.norm0 == 0.0) F.rc = CPR_OK;
+            else if (F.cycle > 0 && F.rnorm / F.norm0 < F.rtol) F.rc = CPR_OK;
+            else fin = false;
+            if (fin) {
+                F.phase = FgmresState::DONE;
+                continue;
             }
+            k_scale_into<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->r.p, h->V.p, sc, m);
+            CK_LAUNCH();
+            F.cycles++;
+            ensure_step_graphs(h);
+            F.launched = F.checked = F.steps = 0;
+            F.stop = false;
+            F.phase = FgmresState::STEPS;
+            continue;
         }
-        CK(cudaStreamSynchronize(s));
-        if (!stop) check(launched - 1);
-        else if (launched - 1 >= steps && rc != CPR_ERR_BREAKDOWN) {
-            const int *f = pin + 4 * ((launched - 1) & 1);
-            if (f[I_K] == launched) {
-                steps = launched;
-                if (h->prof) prof_collect_graph(h, (launched - 1) & 1);
+        case FgmresState::STEPS: {
+            // launch step j once steps 0 .. j-2 are checked
+            if (!F.stop && F.launched < m && F.checked >= F.launched - 1) {
+                int j = F.launched;
+                CK(cudaGraphLaunch(h->sg[j & 1].exec, s));
+                count_launches(h->sg[j & 1].kernels);
+                CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+                CK(cudaEventRecord(h->step_done[j & 1], s));
+                F.launched = j + 1;
+                continue;
             }
+            // check step j-1 once step j is launched
+            if (!F.stop && F.checked < F.launched - 1) {
+                if (!event_ready(h->step_done[F.checked & 1], block)) return 1;
+                check(F.checked);
+                F.checked++;
+                continue;
+            }
+            // the cycle's last step (everything launched has completed)
+            if (!event_ready(h->step_done[(F.launched - 1) & 1], block)) return 1;
+            if (!F.stop) {
+                check(F.launched - 1);
+            } else if (F.launched - 1 >= F.steps && F.rc != CPR_ERR_BREAKDOWN) {
+                const int *f = pin + 4 * ((F.launched - 1) & 1);
+                if (f[I_K] == F.launched) {
+                    F.steps = F.launched;
+                    if (h->prof) prof_collect_graph(h, (F.launched - 1) & 1);
+                }
+            }
+            F.iters += F.steps;
+            if (F.rc == CPR_ERR_BREAKDOWN) {
+                F.phase = FgmresState::DONE;
+                continue;
+            }
+            // y = H^-1 g, x += Z y
+            k_solve_y<<<1, 1, 0, s>>>(sc, m, di);
+            CK_LAUNCH();
+            k_update_x<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->Z.p, F.x, sc, m, di);
+            CK_LAUNCH();
+            F.cycle++;
+            F.phase = FgmresState::START;
+            continue;
         }
-        iters += steps;
-        if (rc == CPR_ERR_BREAKDOWN) break;
-        // y = H^-1 g, x += Z y
-        k_solve_y<<<1, 1, 0, s>>>(sc, m, di);
-        CK_LAUNCH();
-        k_update_x<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->Z.p, x, sc, m, di);
-        CK_LAUNCH();
+        case FgmresState::WAIT_FINAL:
+            if (!event_ready(h->ev_norm, block)) return 1;
+            F.rnorm = h->pinned[0];
+            if (F.rnorm / F.norm0 < F.rtol) F.rc = CPR_OK;
+            F.phase = FgmresState::DONE;
+            continue;
+        case FgmresState::DONE:
+            h->last_iters = F.iters;
+            return F.rc;
+        default:
+            fail(CPR_ERR_INVALID, "no solve in progress");
+        }
     }
-    if (rc == CPR_NOT_CONVERGED && cycles == h->opt.max_restarts) {
-        // true residual after the last cycle
-        spmv_h(h, x, 0, nullptr, b, h->r.p, s, nullptr);
-        norm_partials(h, h->r.p, N);
-        k_cycle_start_scal<<<1, 32, 0, s>>>(h->red.p, kRedBlocks, sc, m, di, 0, rtol);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(h->pinned, sc + SL.rnorm(), sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        rnorm = h->pinned[0];
-        if (rnorm / norm0 < rtol) rc = CPR_OK;
+}
+
+void fgmres_stats(const cpr_handle *h, cpr_stats *st) {
+    const FgmresState &F = h->fs;
+    st->iters = F.iters;
+    st->restarts = F.cycles;
+    st->converged = F.rc == CPR_OK;
+    st->rel_res = F.norm0 > 0.0 ? F.rnorm / F.norm0 : 0.0;
+}
+
+int fgmres(cpr_handle *h, const double *b, double *x, double rtol, cpr_stats *st) {
+    fgmres_begin(h, b, x, rtol);
+    int rc;
+    while ((rc = fgmres_advance(h, true)) == 1) {
     }
-    if (st) {
-        st->iters = iters;
-        st->restarts = cycles;
-        st->converged = rc == CPR_OK;
-        st->rel_res = norm0 > 0.0 ? rnorm / norm0 : 0.0;
-    }
-    h->last_iters = iters;
+    if (st) fgmres_stats(h, st);
+    h->fs.phase = FgmresState::IDLE;
     return rc;
 }
 

@@ -457,3 +457,65 @@ def test_vcycle_part_timing_hook(torch, cpr):
     x1, _ = s.solve(b, rtol=1e-8)
     assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
     s.close()
+
+
+@pytest.mark.parametrize("mu", [0, 30])
+def test_update_values_equals_update(torch, cpr, mu):
+    """cpr_update_values (values only, pattern guaranteed unchanged) makes the
+    same Alg. 3 decisions and gives bit-identical solves to cpr_update over a
+    drifting sequence, from host and from device values."""
+    seq = list(bs.jacobian_sequence(bs.GridSpec(12, 10, 4, 0.0, 1.0, 1.0, None, "corners", seed=4), 4))
+    a = cpr.Solver(DevJ(torch, seq[0]), mu=mu)
+    b = cpr.Solver(DevJ(torch, seq[0]), mu=mu)
+    for k, J in enumerate(seq):
+        if k:
+            a.update(DevJ(torch, J))
+            b.update_values(dev(torch, J.val) if k % 2 else J.val)
+        xa, sa = a.solve(dev(torch, J.b), rtol=1e-8)
+        xb, sb = b.solve(dev(torch, J.b), rtol=1e-8)
+        assert sa["setup_called"] == sb["setup_called"] and sa["iters"] == sb["iters"]
+        assert torch.equal(xa, xb)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_polled_solve_equals_blocking_solve(torch, cpr, fp32):
+    """cpr_solve_start / cpr_solve_poll run the same launches as cpr_solve:
+    bit-identical x and the same statistics, from device and host buffers;
+    while a solve runs the handle refuses updates and other solves; a zero
+    right-hand side finishes at once and a NaN in b is a breakdown."""
+    J = ragged()
+    g = cpr.Solver(DevJ(torch, J), precond_fp32=fp32)
+    b = dev(torch, J.b)
+    xa, sa = g.solve(b, rtol=1e-8)
+    for host in (False, True):
+        x = np.zeros(J.n) if host else torch.zeros_like(b)
+        g.solve_start(J.b if host else b, x, rtol=1e-8)
+        with pytest.raises(cpr.CprError) as e:
+            g.update(DevJ(torch, J))
+        assert e.value.code == cpr.CPR_ERR_INVALID
+        polls, out = 0, None
+        while out is None:
+            out = g.poll()
+            polls += 1
+        xb, sb = out
+        xb = xb if host else xb.cpu().numpy()
+        assert polls > 1 and sb["iters"] == sa["iters"] and sb["converged"]
+        np.testing.assert_array_equal(xb, xa.cpu().numpy())
+    x = torch.zeros_like(b)
+    g.solve_start(torch.zeros_like(b), x)
+    out = None
+    while out is None:
+        out = g.poll()
+    assert out[1]["iters"] == 0 and out[1]["converged"]
+    bad = J.b.copy()
+    bad[3] = np.nan
+    g.solve_start(bad, np.zeros(J.n))
+    with pytest.raises(cpr.CprError) as e:
+        while g.poll() is None:
+            pass
+    assert e.value.code == cpr.CPR_ERR_BREAKDOWN
+    xc, sc = g.solve(b, rtol=1e-8)       # the handle is usable afterwards
+    np.testing.assert_array_equal(xc.cpu().numpy(), xa.cpu().numpy())
+    g.close()

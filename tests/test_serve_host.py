@@ -1,6 +1,7 @@
-"""CPU checks of the serving loop's host logic with a stand-in solver: slots,
-a member's Newton steps in order and never concurrent, admission under the
-HBM budget with least-recently-used eviction of idle members, and errors
+"""CPU checks of the serving loop's host logic with a stand-in solver (whose
+polled solves take 10 ms): slots, a member's Newton steps in order and never
+concurrent, admission under the HBM budget with least-recently-used eviction
+of idle members, values-only updates for an unchanged pattern, and errors
 raised to the caller.  The CUDA path of the same loop is tested on the GPU
 (tests/test_gpu_serve.py)."""
 import threading
@@ -28,18 +29,23 @@ class FakeSolver:
     def update(self, A):
         self.updates += 1
 
-    def solve(self, b, x, rtol):
+    def update_values(self, val):
+        self.updates += 1
+
+    def solve_start(self, b, x, rtol):
         with FakeSolver.lock:
             FakeSolver.active += 1
             FakeSolver.peak = max(FakeSolver.peak, FakeSolver.active)
-        try:
-            if self.fail_at is not None and self.updates == self.fail_at:
-                raise RuntimeError("solve failed")
-            time.sleep(0.01)
-            return x, {"iters": 3, "setup_called": int(self.updates == 0)}
-        finally:
-            with FakeSolver.lock:
-                FakeSolver.active -= 1
+        self.x, self.t_end = x, time.perf_counter() + 0.01   # the "device" takes 10 ms
+
+    def poll(self):
+        if time.perf_counter() < self.t_end:
+            return None
+        with FakeSolver.lock:
+            FakeSolver.active -= 1
+        if self.fail_at is not None and self.updates == self.fail_at:
+            raise RuntimeError("solve failed")
+        return self.x, {"iters": 3, "setup_called": int(self.updates == 0)}
 
     def close(self):
         FakeSolver.log.append(("close", self.member))
@@ -58,7 +64,7 @@ def requests(members, steps, nb=100, nnzb=500, gap=0.0):
     out, t = [], 0.0
     for k in range(steps):
         for m in range(members):
-            A = SimpleNamespace(nb=nb, col=np.zeros(nnzb, np.int32), member=m)
+            A = SimpleNamespace(nb=nb, col=np.zeros(nnzb, np.int32), val=np.zeros(9 * nnzb), member=m)
             out.append(serve.Request(m, k, A, np.zeros(3 * nb), t))
             t += gap
     return out
@@ -122,4 +128,32 @@ def test_a_request_larger_than_the_budget_is_rejected():
     assert big.error and "exceeds the HBM budget" in big.error and big.x is None
     assert all(r.error is None and r.stats for r in small)
     assert ("open", 9) not in FakeSolver.log
+    srv.close()
+
+
+def test_same_pattern_requests_update_values_only():
+    """A member's later Newton steps that keep the block pattern go through the
+    values-only update; the others (and the first, a setup) do not."""
+    reqs = requests(members=2, steps=3)
+    for r in reqs:
+        r.same_pattern = r.step > 0
+    calls = []
+
+    class Recording(FakeSolver):
+        def update(self, A):
+            calls.append(("update", self.member))
+            super().update(A)
+
+        def update_values(self, val):
+            calls.append(("values", self.member))
+            super().update_values(val)
+
+    class Srv(FakeServer):
+        def _open(self, A):
+            return Recording(A, A.member)
+
+    srv = Srv(slots=2, hbm_budget=1 << 40)
+    res = srv.run(reqs, realtime=False)
+    assert res["requests"] == 6
+    assert sorted(calls) == [("values", 0), ("values", 0), ("values", 1), ("values", 1)]
     srv.close()
