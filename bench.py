@@ -152,6 +152,22 @@ def smooth0_bytes(level, sv, pre=1, post=1):
     return float(np.mean(launches))
 
 
+def smooth_color_bytes(levels, sv, pre=1, post=1):
+    """Algorithmic bytes and launch count of the k_smooth_color launches of one
+    V(pre,post) cycle, all smoothed levels: smooth0_bytes' model per launch
+    (row pointer, b, 1/a_ii and staged result per row; column, value and
+    gathered x per off-diagonal entry; the previous color's commit)."""
+    tot, n = 0.0, 0
+    for lv in levels[:-1]:
+        if lv.get("color") is None:
+            continue
+        per = smooth0_bytes(lv, sv, pre, post)
+        nlaunch = pre * lv["ncolors"] - 1 + post * lv["ncolors"]   # the very first color is fused elsewhere
+        tot += per * nlaunch
+        n += nlaunch
+    return tot, n
+
+
 def spmv_bytes(nb, nnzb):
     """FP64 BSR: 72 B of values + 4 B of column per block; x, y and rowptr per block row."""
     return 76 * nnzb + 52 * nb
@@ -289,6 +305,46 @@ def setup_profile(cpr, torch, J, stream, warm=4):
     solver.close()
     return {"workload": f"{WORKLOAD} FP32-mode setup", "warm_wall_ms": walls, "profiled_wall_ms": wall,
             "launches": launches}
+
+
+def vcycle_profile(cpr, torch, workload, stream):
+    """One FP32 hierarchy of `workload`: the in-graph time of every V-cycle
+    part (20 repetitions per graph) and the level-0 smoothing colors' rows,
+    entries and algorithmic bytes; then one eager V-cycle (cpr_vcycle)
+    bracketed by cudaProfilerStart/Stop for a one-kernel ncu capture."""
+    J = bs.jacobian(bs.CONFIGS[workload])
+
+    class DJ:
+        nb = J.nb
+        rowptr = torch.from_numpy(J.rowptr).cuda()
+        col = torch.from_numpy(J.col).cuda()
+        val = torch.from_numpy(J.val).cuda()
+
+    b = torch.from_numpy(J.b).cuda()
+    g = cpr.Solver(DJ, precond_fp32=1, stream=stream.cuda_stream)
+    _, st = g.solve(b, rtol=RTOL)
+    parts = g.profile_vcycle_levels(20)
+    lv0 = g.level(0)
+    color, rp = lv0["color"], lv0["rowptr"]
+    off = np.diff(rp) - 1
+    nc = int(color.max()) + 1
+    rows = np.bincount(color, minlength=nc)
+    ents = np.bincount(color, weights=off, minlength=nc)
+    per_color = [{"rows": int(rows[c]), "offdiag": int(ents[c]),
+                  "bytes": int(rows[c] * (4 + 3 * 4) + ents[c] * (4 + 2 * 4))} for c in range(nc)]
+    bp = torch.from_numpy(np.random.default_rng(1).standard_normal(J.nb)).cuda()
+    xp = torch.zeros_like(bp)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    g.vcycle(bp, xp)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    levels = [{k: g.level(l)[k] for k in ("n", "nnz", "ncolors")} for l in range(g.nlev)]
+    g.close()
+    return {"workload": f"{workload}, FP32 preconditioner", "iters": st["iters"], "levels": levels,
+            "vcycle_parts_us": parts, "level0_colors": per_color,
+            "note": "bytes: per row its row pointer, b, 1/a_ii and the staged result; per off-diagonal "
+                    "entry its column, value and the gathered x (FP32)"}
 
 
 def run_arm(cpr, torch, seq_dev, rhs_dev, fp32, K, W, world, stream, profile_region=False):
@@ -765,6 +821,9 @@ def main():
                          "32x32x8..128x128x32 one")
     ap.add_argument("--arm", default="both", choices=["both", "fp32", "fp64"],
                     help="precision arms to time (the JSON line needs both)")
+    ap.add_argument("--vcycle-profile", default=None, metavar="WORKLOAD",
+                    help="only time the V-cycle parts of WORKLOAD's FP32 hierarchy and bracket one eager "
+                         "V-cycle for ncu")
     ap.add_argument("--serve-only", action="store_true",
                     help="only run the serving arm and print its object")
     ap.add_argument("--adaptive-sweep", action="store_true",
@@ -796,6 +855,11 @@ def main():
         res = theta_sweep(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
         if rank == 0:
             print(json.dumps({"theta_sweep": res}), flush=True)
+        return
+    if args.vcycle_profile:
+        res = vcycle_profile(cpr, torch, args.vcycle_profile, stream)
+        if rank == 0:
+            print(json.dumps({"vcycle_profile": res}), flush=True)
         return
     if args.serve_only:
         res = serve_arm(not args.serve_scaled)
@@ -940,6 +1004,24 @@ def main():
                "frac": (sm0.get("gbs") / hbm) if sm0.get("gbs") else None,
                "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
                "bytes_per_launch": sm0.get("bytes_per_launch")}
+    # The dominant kernel by launch-list share is the multi-color GS sweep
+    # k_smooth_color (its instances over all levels: ~26 % of a step's kernel
+    # time).  Its rate: the algorithmic bytes of every color launch of one
+    # V(1,1) cycle (smooth_color_bytes) over the live in-graph time of all
+    # pre- and post-smoothing sweeps (vcycle_parts_us), against HBM.
+    parts32 = r32["parts"]["levels"]
+    sweep_us = sum(d["pre"] + d["post"] for d in parts32)
+    sweep_bytes, sweep_launches = smooth_color_bytes(r32["levels"], 4)
+    tr_sm = NCU_TRAFFIC.get(("k_smooth_color", WORKLOAD))
+    roof_family = {"kernel": "k_smooth_color, all levels (multi-color GS color sweeps, FP32; the largest kernel "
+                             "family of the step by launch-list share)",
+                   "bound": "hbm", "achieved": sweep_bytes / (sweep_us * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": sweep_bytes / (sweep_us * 1e-6) / 1e9 / hbm,
+                   "peak_kind": f"{peak_kind} hbm_gbs (of {peak_kind})",
+                   "bytes_per_launch": sweep_bytes / sweep_launches, "launches_per_vcycle": sweep_launches,
+                   "avg_us": sweep_us / sweep_launches,
+                   "traffic": tr_sm["bytes"] if tr_sm else None,
+                   "traffic_source": tr_sm["source"] if tr_sm else None}
 
     def pct(a, q):
         return float(np.percentile(np.array(a), q))
@@ -974,7 +1056,8 @@ def main():
                              f"{r32['profiled_steps']} steps per arm (bracketed step: "
                              f"{r32['profiled_ms_per_step']:.2f} ms fp32, {r64['profiled_ms_per_step']:.2f} ms fp64); "
                              "the level-0 sweeps (smooth0), nested in the V-cycle, in a further pass of their own"},
-        "roofline": roof,
+        "roofline": roof_family,
+        "roofline_spmv": roof,
         "roofline_smoother_level0": roof_sm,
         "vcycle_hbm_frac_fp32": (f32.get("vcycle", {}).get("gbs") or 0) / hbm,
         "gpu_launches": int(r32["launches"]),
