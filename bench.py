@@ -40,6 +40,10 @@ MU = 30
 # kernel the line rates, from one ncu capture of the build named, at the
 # workload named; a kernel changed since then has no entry (traffic null).
 NCU_TRAFFIC = {
+    ("k_smooth_color", "128x128x32"): {"bytes": 2.524e6,
+                                       "source": "mean DRAM bytes of the 56 color launches of one eager V-cycle, "
+                                                 "ncu capture of the commit ea0b151 build, cold caches "
+                                                 "(profiles/smooth_color_128x128x32.md)"},
     ("k_sell_spmv", "128x128x32"): {"bytes": 302.63e6 + 9.98e6,
                                     "source": "ncu capture of one k_sell_spmv launch of the commit cdabb71 "
                                               "build (profiles/spmv_sell_128x128x32.md)"},
