@@ -542,6 +542,9 @@ def batched_arm(cpr, torch, K, stream, nsys=64):
     tuned = [bt.schedule(l) for l in range(bt.nlev - 1)]
     ok = all(st["converged"] for st in sts)
     iters = [st["iters"] for st in sts]
+    # Alg. 3 on a batch compares the largest step count with mu: the system
+    # that took it decides whether the next batch update rebuilds B
+    forcing = int(np.argmax(iters))
     bt.close()
     # the same systems, one handle each, FP64 preconditioner, solved in turn
     singles = [cpr.Solver(d, precond_fp32=0, mu=MU, stream=stream.cuda_stream) for d in dj]
@@ -567,6 +570,8 @@ def batched_arm(cpr, torch, K, stream, nsys=64):
                          "gain_over_fixed_rule": ms_rule / ms,
                          "pressure_cycle_us_before": bp_before, "pressure_cycle_us_after": bp_after},
             "iters_max": max(iters), "iters_mean": statistics.mean(iters),
+            "alg3": {"deciding_system": forcing, "deciding_iters": iters[forcing], "mu": MU,
+                     "next_update_rebuilds": iters[forcing] > MU},
             "fp64_one_by_one": {"value": nsys / (ms_seq / 1000.0), "unit": UNIT, "ms": ms_seq},
             "speedup_vs_fp64_one_by_one": ms_seq / ms}
 

@@ -218,7 +218,8 @@ const char *cpr_last_error_detail(void);
 int cpr_batch_setup(cpr_handle **h, int nsys, const cpr_bsr3 *A, const cpr_opts *opts);
 
 /* New matrices with unchanged sizes (Alg. 3 decides reuse, with It^(k-1) the
- * largest step count of the previous batch solve). */
+ * largest step count of the previous batch solve: the system with the largest
+ * stats[].iters decides for the whole batch). */
 int cpr_batch_update(cpr_handle *h, const cpr_bsr3 *A);
 
 /* Solve every system: b[k], x[k] (host or device; x[k] is the initial guess and
