@@ -42,11 +42,9 @@ MU = 30
 NCU_TRAFFIC = {
     ("k_smooth_color", "128x128x32"): {"bytes": 2.524e6,
                                        "source": "mean DRAM bytes of the 56 color launches of one eager V-cycle, "
-                                                 "ncu capture of the commit ea0b151 build, cold caches "
-                                                 "(profiles/smooth_color_128x128x32.md)"},
+                                                 "ncu capture of the commit ea0b151 build, cold caches"},
     ("k_sell_spmv", "128x128x32"): {"bytes": 302.63e6 + 9.98e6,
-                                    "source": "ncu capture of one k_sell_spmv launch of the commit cdabb71 "
-                                              "build (profiles/spmv_sell_128x128x32.md)"},
+                                    "source": "ncu capture of one k_sell_spmv launch of the commit cdabb71 build"},
 }
 
 

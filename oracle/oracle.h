@@ -103,7 +103,7 @@ int    o_fgmres_identity(int nb, const int *rowptr, const int *col, const double
                          const double *b, double *x, double rtol, int m, int max_restarts,
                          o_stats *st, double *hist);
 
-/* Threads of this build's parallel loops (1 unless built with OpenMP). */
+/* Threads the library's parallel loops run on (1 unless compiled with OpenMP). */
 int  o_threads(void);
 
 /* ---- the solver (Alg. 2 with Alg. 3 deciding setup) ---- */
