@@ -64,7 +64,8 @@ __global__ void k_compare(long n, const int *a, const int *b, int *diff) {
 
 void build_timed(cpr_handle *h, bool numeric = false) {
     double t0 = now_ms();
-    build_preconditioner(h, numeric);
+    if (numeric && h->nr_ready) numeric_refresh(h);
+    else build_preconditioner(h, numeric);
     h->setup_ms = now_ms() - t0;
     h->setup_count++;
     h->setup_called = 1;
@@ -451,6 +452,8 @@ void cpr_destroy(cpr_handle *h) {
     for (auto e : h->step_done)
         if (e) cudaEventDestroy(e);
     for (auto e : h->ev_coarse)
+        if (e) cudaEventDestroy(e);
+    for (auto e : h->ev_nr)
         if (e) cudaEventDestroy(e);
     for (auto e : h->ev_color) cudaEventDestroy(e);
     if (h->pinned) cudaFreeHost(h->pinned);

@@ -174,6 +174,10 @@ struct Level {
     // work vectors (internal numbering); s0, s1: staging of the color being relaxed
     DVec<double> x, b, r, s0, s1;
     DVec<float> x32, b32, r32, s0_32, s1_32;
+    // resetup = 1: what the in-place numeric refresh needs besides the above
+    DVec<int> dpos;               // position of each row's diagonal in A
+    DVec<int> cidx;               // coarse index of each C point (classical AMG)
+    DCsr AP;                      // the Galerkin product's left factor A P
     // amg = 1, levels 1 .. L-2: the GCR vectors of this level's coarse
     // correction (amli_iters x n each), its scalars and reduction partials
     DVec<double> gv, gw, gscal, gpart;
@@ -279,6 +283,15 @@ struct cpr_handle {
     cpr::DVec<double> dev_b, dev_x; // device copies of host b / x
     double *pinned = nullptr;       // pinned host scalars
     cpr::DVec<int> err;             // device error flag
+    // resetup = 1: the in-place numeric refresh of B (numeric_refresh) and its graph
+    bool nr_ready = false;          // the last full setup kept what the refresh needs
+    cpr::DVec<int> bdiag;           // each block row's diagonal position
+    cpr::DVec<double> c_a, c_lu;    // coarse factorisation scratch
+    cpr::DVec<int> c_piv;
+    cudaGraph_t nr_graph = nullptr;
+    cudaGraphExec_t nr_exec = nullptr;
+    unsigned long long nr_kernels = 0;
+    cudaEvent_t ev_nr[4] = {nullptr, nullptr, nullptr, nullptr};   // fork/join of its side branches
     // --- adaptive state (Alg. 3) ---
     long last_iters = -1;
     int setup_count = 0, setup_called = 0, updates = 0;
@@ -354,6 +367,10 @@ void destroy_step_graphs(cpr_handle *h);
 // C/F splits, colorings, BILU(0) ordering) and recompute every value from A.
 void build_preconditioner(cpr_handle *h, bool numeric = false);
 void free_preconditioner(cpr_handle *h);
+// resetup = 1 with an unchanged pattern: every value of B recomputed from the
+// current A in place (the structure of the last full setup kept), replayed as
+// one CUDA graph; the step graphs stay valid
+void numeric_refresh(cpr_handle *h);
 void refresh_second_residual(cpr_handle *h);   // reuse_refresh: the kept B's copy of A := the current A
 
 // noalloc.cu: resolve (and so load) the allocation-free entry's scratch array

@@ -1605,8 +1605,43 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
     }
 }
 
+// The values of C = A B on C's pattern from an earlier product of the same
+// patterns (rows of B and C sorted).  G lanes per row of C zero the row, then
+// add a_ik b_kJ for the row's A entries k in ascending order, the lanes over
+// B_k's columns; a B row holds each column once, so the lanes of one step
+// never meet, and every C entry is summed in Gustavson's order, as in the
+// tiered product above.  G divides 32 and the block, so a group's lanes share
+// a warp and leave together.
+template <int G>
+__global__ void k_spgemm_numeric(int n, const int *ar, const int *ac, const double *av, const int *br,
+                                 const int *bc, const double *bv, const int *cr, const int *cc, double *cv,
+                                 int *err) {
+    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long i = tid / G;
+    int lane = (int)(tid % G);
+    if (i >= n) return;
+    int wl = threadIdx.x & 31;
+    unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
+    int c0 = cr[i], c1 = cr[i + 1];
+    for (int q = c0 + lane; q < c1; q += G) cv[q] = 0.0;
+    __syncwarp(gmask);
+    for (int p = ar[i]; p < ar[i + 1]; p++) {
+        int k = ac[p];
+        double a = av[p];
+        for (int q = br[k] + lane; q < br[k + 1]; q += G) {
+            int J = bc[q];
+            int pos = find_col(cc, c0, c1, J);
+            if (pos < c1 && cc[pos] == J) cv[pos] = __dadd_rn(cv[pos], __dmul_rn(a, bv[q]));
+            else set_err(err, CPR_ERR_INVALID);   // not the pattern this C was built for
+        }
+        __syncwarp(gmask);
+    }
+}
+
 // -------------------------------------------------------- level helpers
 
+// A zero or non-finite diagonal records CPR_ERR_SINGULAR; dinv (when set)
+// receives 1/a_ii, with 1 standing in for a bad pivot.
 __global__ void k_check_diag(int n, const int *diag, const double *val, double *dinv, int *err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -1616,7 +1651,22 @@ __global__ void k_check_diag(int n, const int *diag, const double *val, double *
         set_err(err, CPR_ERR_SINGULAR);
         d = 1.0;
     }
-    dinv[i] = 1.0 / d;
+    if (dinv) dinv[i] = 1.0 / d;
+}
+
+// The values of R = P^T from P's (R's pattern kept: rows sorted by column,
+// so P entry (i, j) sits at i's place in row j).
+__global__ void k_transpose_values(int n, const int *pr, const int *pc, const double *pv, const int *rr,
+                                   const int *rc, double *rv, int *err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int p = pr[i]; p < pr[i + 1]; p++) {
+        int j = pc[p];
+        int e = rr[j + 1];
+        int q = find_col(rc, rr[j], e, i);
+        if (q < e && rc[q] == i) rv[q] = pv[p];
+        else set_err(err, CPR_ERR_INVALID);
+    }
 }
 
 // Per-color row counts: a block-local histogram in shared memory (colors
@@ -2543,9 +2593,31 @@ void to_f32(const DVec<double> &a, DVec<float> &b, cudaStream_t s) {
     }
 }
 
-// dst = src with rows taken in `order` and columns mapped through icol.
 int lanes_for(double avg, long rows, long target);
 
+// The entries of dst (its row pointers already in place) from src's: the
+// fill pass of perm_csr, also run alone to refresh dst's values.
+void perm_fill(const DCsr &src, const int *order, const int *icol, bool skip_diag, DCsr &dst, cudaStream_t s,
+               float *val32) {
+    int n = src.n;
+    if (!n) return;
+    // lanes per row: a few entries per lane, at least 2^17 threads
+    int g = std::min(8, lanes_for((double)src.nnz / std::max(n, 1), n, 1L << 17));
+    auto fill = [&](auto kern, int G) {
+        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p,
+                                                             skip_diag, icol, dst.rowptr.p, dst.col.p, dst.val.p,
+                                                             val32);
+    };
+    switch (g) {
+    case 1: fill(k_perm_fill<1>, 1); break;
+    case 2: fill(k_perm_fill<2>, 2); break;
+    case 4: fill(k_perm_fill<4>, 4); break;
+    default: fill(k_perm_fill<8>, 8); break;
+    }
+    CK_LAUNCH();
+}
+
+// dst = src with rows taken in `order` and columns mapped through icol.
 void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool skip_diag, DCsr &dst,
               cudaStream_t s, DVec<float> *val32 = nullptr) {
     int n = src.n;
@@ -2564,20 +2636,7 @@ void perm_csr(const DCsr &src, const int *order, const int *icol, int ncol, bool
     dst.col.alloc(std::max(src.nnz, 1), s);
     dst.val.alloc(std::max(src.nnz, 1), s);
     if (val32) val32->alloc(std::max(src.nnz, 1), s);   // the FP32 shadow, filled alongside
-    // lanes per row: a few entries per lane, at least 2^17 threads
-    int g = std::min(8, lanes_for((double)src.nnz / std::max(n, 1), n, 1L << 17));
-    auto fill = [&](auto kern, int G) {
-        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, order, src.rowptr.p, src.col.p, src.val.p,
-                                                             skip_diag, icol, dst.rowptr.p, dst.col.p, dst.val.p,
-                                                             val32 ? val32->p : nullptr);
-    };
-    switch (g) {
-    case 1: fill(k_perm_fill<1>, 1); break;
-    case 2: fill(k_perm_fill<2>, 2); break;
-    case 4: fill(k_perm_fill<4>, 4); break;
-    default: fill(k_perm_fill<8>, 8); break;
-    }
-    CK_LAUNCH();
+    perm_fill(src, order, icol, skip_diag, dst, s, val32 ? val32->p : nullptr);
 }
 
 // Lanes per row for a mean row length: about four entries per lane (1..32
@@ -2602,6 +2661,116 @@ void copy_ints(DVec<int> &dst, const int *src, size_t n, cudaStream_t s) {
     if (n) CK(cudaMemcpyAsync(dst.p, src, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
 }
 
+// ---------------------------------------------- value passes of the setup
+//
+// Each fills buffers that are already in place from the current values, so
+// the full setup and the numeric refresh (resetup = 1) run the same kernels.
+
+// C's values from A's and B's on C's pattern (an earlier spgemm of the same
+// patterns): lanes per row from B's mean row length.
+void spgemm_values(const DCsr &A, const DCsr &B, DCsr &C, int *err, cudaStream_t s) {
+    int n = A.n;
+    if (!n) return;
+    int g = lanes_for((double)B.nnz / std::max(B.n, 1), n, 1L << 17);
+    auto run = [&](auto kern, int G) {
+        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p,
+                                                             B.val.p, C.rowptr.p, C.col.p, C.val.p, err);
+    };
+    switch (g) {
+    case 1: run(k_spgemm_numeric<1>, 1); break;
+    case 2: run(k_spgemm_numeric<2>, 2); break;
+    case 4: run(k_spgemm_numeric<4>, 4); break;
+    case 8: run(k_spgemm_numeric<8>, 8); break;
+    case 16: run(k_spgemm_numeric<16>, 16); break;
+    default: run(k_spgemm_numeric<32>, 32); break;
+    }
+    CK_LAUNCH();
+}
+
+// The BILU(0) factors of the current A on the kept ordering and L/U patterns:
+// A's blocks copied (FP64) or rounded (FP32 mode) into the factor array,
+// factored color by color, then split into L, U and the inverted diagonal
+// blocks in position order.
+void bilu_values(cpr_handle *h, const int *bdiag, cudaStream_t s) {
+    Bilu &B = h->bilu;
+    int nb = h->nb, nnzb = h->nnzb;
+    auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
+        using T = std::remove_pointer_t<decltype(lu)>;
+        for (int c = 0; c < B.ncolors; c++) {
+            int cnt = B.color_off[c + 1] - B.color_off[c];
+            if (!cnt) continue;
+            k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
+                                                                     h->rowptr.p, h->col.p, B.color.p, bdiag, lu,
+                                                                     h->err.p, h->opt.bilu_order);
+            CK_LAUNCH();
+        }
+        // a singular pivot block is reported by the caller's error check
+        k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
+            nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
+            B.Ucol.p, Uv, Dv);
+        CK_LAUNCH();
+    };
+    if (h->opt.precond_fp32) {
+        k_d2f<<<grid_for(9L * nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(9L * nnzb, h->val.p, B.lu32.p);
+        CK_LAUNCH();
+        factor_and_split(B.lu32.p, B.Lval32.p, B.Uval32.p, B.Dinv32.p);
+    } else {
+        CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
+        factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
+    }
+}
+
+// Column 0 of A's blocks in positions (the copy B keeps for the second
+// residual of Alg. 1), and its FP32 shadow when that exists.
+void col0_values(cpr_handle *h, cudaStream_t s) {
+    const Bilu &B = h->bilu;
+    int nb = h->nb;
+    k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
+                                                       h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
+    CK_LAUNCH();
+    size_t n = std::min(h->pcol0.n, h->pcol0_32.n);
+    if (h->pcol0_32.p && n) {
+        k_d2f<<<grid_for((long)n, kBlock, 148 * 16), kBlock, 0, s>>>((long)n, h->pcol0.p, h->pcol0_32.p);
+        CK_LAUNCH();
+    }
+}
+
+// The dense LU factorisation of the coarsest matrix: larger than this it is
+// factored in global memory.
+constexpr int kLuSmemMax = 200 * 1024;
+
+bool lu_in_smem(int n) { return (size_t)n * n * sizeof(double) <= kLuSmemMax; }
+
+// The shared-memory ceiling of k_dense_lu, set before its first launch (and
+// outside any capture): always the same value, so handles set up on other
+// host threads never see a smaller limit than the one they launch with.
+void lu_smem_attr() {
+    CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuSmemMax));
+}
+
+// h->cinv = the inverse of the coarsest matrix by dense LU with partial
+// pivoting, on stream q; a, lu (n*n) and piv (n) are scratch.
+void coarse_values(cpr_handle *h, double *a, double *lu, int *piv, cudaStream_t q) {
+    const Level &C = h->lev.back();
+    int n = C.A.n;
+    size_t bytes = sizeof(double) * (size_t)n * n;
+    CK(cudaMemsetAsync(a, 0, bytes, q));
+    k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, q>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a);
+    CK_LAUNCH();
+    int use_smem = lu_in_smem(n) ? 1 : 0;
+    // global path: factor a copy in storage order, then gather rows into position order
+    if (!use_smem) CK(cudaMemcpyAsync(lu, a, bytes, cudaMemcpyDeviceToDevice, q));
+    k_dense_lu<<<1, kLuThreads, use_smem ? bytes : 0, q>>>(n, a, lu, piv, use_smem, h->err.p);
+    CK_LAUNCH();   // a zero pivot is reported by the caller's error check
+    if (!use_smem) {
+        k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, q>>>(n, lu, piv, a);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(lu, a, bytes, cudaMemcpyDeviceToDevice, q));
+    }
+    k_dense_inv_cols<<<n, 256, sizeof(double) * n, q>>>(n, lu, piv, h->cinv.p);
+    CK_LAUNCH();
+}
+
 }  // namespace
 
 // ================================================================== public
@@ -2612,6 +2781,16 @@ void validate_bsr(const int *rowptr, const int *col, int nb, int nnzb, int *derr
 }
 
 void free_preconditioner(cpr_handle *h) {
+    if (h->nr_exec) cudaGraphExecDestroy(h->nr_exec);
+    if (h->nr_graph) cudaGraphDestroy(h->nr_graph);
+    h->nr_exec = nullptr;
+    h->nr_graph = nullptr;
+    h->nr_kernels = 0;
+    h->nr_ready = false;
+    h->bdiag.release();
+    h->c_a.release();
+    h->c_lu.release();
+    h->c_piv.release();
     h->tail_top = -1;
     h->lev.clear();
     h->pcol0.release();
@@ -2631,19 +2810,7 @@ void free_preconditioner(cpr_handle *h) {
 // column-0 copy, and its FP32 shadow, are refilled in place.  Pattern and
 // positions are A's and B's, both unchanged, so the step graphs captured for
 // B stay valid.
-void refresh_second_residual(cpr_handle *h) {
-    cudaStream_t s = h->stream;
-    const Bilu &B = h->bilu;
-    int nb = h->nb;
-    k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                       h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
-    CK_LAUNCH();
-    size_t n = std::min(h->pcol0.n, h->pcol0_32.n);
-    if (h->pcol0_32.p && n) {
-        k_d2f<<<grid_for((long)n, kBlock, 148 * 16), kBlock, 0, s>>>((long)n, h->pcol0.p, h->pcol0_32.p);
-        CK_LAUNCH();
-    }
-}
+void refresh_second_residual(cpr_handle *h) { col0_values(h, h->stream); }
 
 // Phase marks of a setup, printed to stderr when CPR_SETUP_TIMING is set
 // (diagnostics only).  A mark records a timing event on its clock's stream
@@ -2882,7 +3049,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     }
 
     // ---- decoupling and the pressure matrix A_P (level 0) ----
-    DVec<int> bdiag;
+    DVec<int> &bdiag = h->bdiag;   // kept: the numeric refresh reads it
     bdiag.alloc(nb, s);
     k_diagpos<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->col.p, bdiag.p);
     CK_LAUNCH();
@@ -2954,39 +3121,18 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             B.Ucol.alloc(std::max(nu, 1), s);
             side.mark("bilu_order");
         }
-        auto factor_and_split = [&](auto *lu, auto *Lv, auto *Uv, auto *Dv) {
-            using T = std::remove_pointer_t<decltype(lu)>;
-            for (int c = 0; c < B.ncolors; c++) {
-                int cnt = B.color_off[c + 1] - B.color_off[c];
-                if (!cnt) continue;
-                k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                                         h->rowptr.p, h->col.p, B.color.p,
-                                                                         bdiag.p, lu, h->err.p,
-                                                                         h->opt.bilu_order);
-                CK_LAUNCH();
-            }
-            // a singular pivot block is reported by the check at the end of the setup
-            k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
-                nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
-                B.Ucol.p, Uv, Dv);
-            CK_LAUNCH();
-        };
         if (f32) {
             B.lu32.alloc(9 * (size_t)nnzb, s);
-            k_d2f<<<grid_for(9L * nnzb, kBlock, 148 * 16), kBlock, 0, s>>>(9L * nnzb, h->val.p, B.lu32.p);
-            CK_LAUNCH();
             B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
             B.Uval32.alloc(9 * (size_t)std::max(nu, 1), s);
             B.Dinv32.alloc(9 * (size_t)nb, s);
-            factor_and_split(B.lu32.p, B.Lval32.p, B.Uval32.p, B.Dinv32.p);
         } else {
             B.lu.alloc(9 * (size_t)nnzb, s);
-            CK(cudaMemcpyAsync(B.lu.p, h->val.p, sizeof(double) * 9 * (size_t)nnzb, cudaMemcpyDeviceToDevice, s));
             B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
             B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
             B.Dinv.alloc(9 * (size_t)nb, s);
-            factor_and_split(B.lu.p, B.Lval.p, B.Uval.p, B.Dinv.p);
         }
+        bilu_values(h, bdiag.p, s);
         side.mark("bilu_factor");
         // the frozen column-0 copy of A in positions
         DVec<int> ccnt;
@@ -2998,9 +3144,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
         h->c0col.alloc(nnzb, s);
         h->pcol0.alloc(3 * (size_t)nnzb, s);
-        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                           h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
-        CK_LAUNCH();
+        col0_values(h, s);   // its FP32 shadow is made after the side work has joined
         side.mark("col0");
     });
     // ---- the AMG hierarchy ----
@@ -3009,13 +3153,10 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         Nvtx r("AMG level");
         {
             Level &L = h->lev[l];
-            DVec<int> diag;
-            diag.alloc(n, s);
-            k_diagpos<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, diag.p);
+            L.dpos.alloc(n, s);
+            k_diagpos<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.dpos.p);
             CK_LAUNCH();
-            DVec<double> dtmp;
-            dtmp.alloc(n, s);
-            k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, diag.p, L.A.val.p, dtmp.p, h->err.p);
+            k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.dpos.p, L.A.val.p, nullptr, h->err.p);
             CK_LAUNCH();   // a zero diagonal is reported by the check at the end of the setup
         }
         if (numeric ? l + 1 >= (int)kept.size() : (n <= o.coarse_max || l + 1 >= o.max_levels)) break;
@@ -3173,17 +3314,19 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             L.R.nnz = L.P.nnz;
             transpose(n, nc, L.P.nnz, L.P.rowptr.p, L.P.col.p, L.P.val.p, L.R.rowptr, L.R.col, &L.R.val, s);
         }
-        // the strength set stays with the level for a numeric-only resetup
+        // the strength set and coarse indices stay with the level for a numeric-only resetup
         L.Srow = std::move(S.rowptr);
         L.Scol = std::move(S.col);
         L.Snnz = S.nnz;
+        L.cidx = std::move(cidx);
         clk.mark("interp");
-        // Galerkin coarse matrix A_{l+1} = R (A P)
+        // Galerkin coarse matrix A_{l+1} = R (A P); the numeric refresh keeps A P
         DCsr AP, Ac;
         spgemm(L.A, L.P, AP, s);
         clk.mark("ap");
         spgemm(L.R, AP, Ac, s);
-        AP = DCsr{};
+        if (o.resetup) L.AP = std::move(AP);
+        else AP = DCsr{};
         clk.mark("rap");
         h->lev.emplace_back();
         h->lev[l + 1].A = std::move(Ac);
@@ -3217,40 +3360,17 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         h->cn = n;
         h->cinv.alloc((size_t)n * n, s);    // a handle buffer: allocated and released on the main stream
         cudaStream_t q = h->lu_stream;
+        // scratch of the handle (the numeric refresh reuses it), allocated on the main stream
+        h->c_a.alloc((size_t)n * n, s);
+        h->c_lu.alloc((size_t)n * n, s);
+        h->c_piv.alloc(std::max(n, 1), s);
+        if (lu_in_smem(n)) lu_smem_attr();
         CK(cudaEventRecord(h->ev_coarse[0], s));
         CK(cudaStreamWaitEvent(q, h->ev_coarse[0], 0));
         coarse_join.s = s;
         coarse_join.e = h->ev_coarse[1];
         coarse_join.q = q;
-        // temporaries live and die on that stream
-        DVec<double> a;
-        DVec<int> piv;
-        a.alloc((size_t)n * n, q);
-        a.zero();
-        piv.alloc(n, q);
-        k_csr_to_dense<<<grid_for(n, kBlock), kBlock, 0, q>>>(n, C.A.rowptr.p, C.A.col.p, C.A.val.p, a.p);
-        CK_LAUNCH();
-        constexpr int kLuSmemMax = 200 * 1024;
-        int use_smem = (size_t)n * n * sizeof(double) <= kLuSmemMax ? 1 : 0;
-        size_t smem = use_smem ? (size_t)n * n * sizeof(double) : 0;
-        // always the same ceiling: handles set up concurrently on other host
-        // threads must never see a smaller limit than the one they launch with
-        if (use_smem) CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuSmemMax));
-        DVec<double> lu;
-        lu.alloc((size_t)n * n, q);
-        if (!use_smem) {
-            // global path: factor a copy in storage order, then gather rows into position order
-            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, q));
-        }
-        k_dense_lu<<<1, kLuThreads, smem, q>>>(n, a.p, lu.p, piv.p, use_smem, h->err.p);
-        CK_LAUNCH();   // a zero pivot is reported by the check at the end of the setup
-        if (!use_smem) {
-            k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, q>>>(n, lu.p, piv.p, a.p);
-            CK_LAUNCH();
-            CK(cudaMemcpyAsync(lu.p, a.p, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, q));
-        }
-        k_dense_inv_cols<<<n, 256, sizeof(double) * n, q>>>(n, lu.p, piv.p, h->cinv.p);
-        CK_LAUNCH();
+        coarse_values(h, h->c_a.p, h->c_lu.p, h->c_piv.p, q);
     }
     clk.mark("coarse");
 
@@ -3356,6 +3476,11 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         }
     }
     coarse_join.finish();
+    if (!o.resetup) {   // the coarse scratch serves only the numeric refresh from here on
+        h->c_a.release();
+        h->c_lu.release();
+        h->c_piv.release();
+    }
     choose_tail(h);
     // Kernels that meet a zero or non-finite pivot (an AMG level's diagonal,
     // the coarsest matrix, a BILU(0) block) record CPR_ERR_SINGULAR and go on
@@ -3364,7 +3489,125 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     check_err(h, "zero or non-finite pivot: an AMG level's diagonal, the coarsest matrix or a BILU(0) block");
     clk.mark("layout");
     h->have_B = true;
+    h->nr_ready = o.resetup != 0;
     h->epoch++;
+}
+
+namespace {
+
+// The launches of the numeric refresh on h->stream, with two branches that
+// join back before the end: the second stage (BILU(0) and the column-0 copy,
+// which need only A) on h->side, the coarse inverse on h->lu_stream.  Every
+// launch is a value pass of the full setup on the kept structure, so B comes
+// out bit for bit as a full setup on the same pattern builds it.
+void record_refresh(cpr_handle *h) {
+    cudaStream_t s = h->stream, side = h->side, q = h->lu_stream;
+    const cpr_opts &o = h->opt;
+    int nb = h->nb, L = (int)h->lev.size();
+    bool f32 = o.precond_fp32 != 0;
+    int *err = h->err.p;
+    CK(cudaEventRecord(h->ev_nr[0], s));
+    CK(cudaStreamWaitEvent(side, h->ev_nr[0], 0));
+    bilu_values(h, h->bdiag.p, side);
+    col0_values(h, side);
+    CK(cudaEventRecord(h->ev_nr[1], side));
+    // decoupling and A_P, then each level's P, R and Galerkin product
+    k_decouple<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->bdiag.p, h->val.p, o.decouple, h->w.p, err);
+    CK_LAUNCH();
+    if (f32) {
+        k_d2f<<<grid_for(3L * nb, kBlock, 148 * 16), kBlock, 0, s>>>(3L * nb, h->w.p, h->w32.p);
+        CK_LAUNCH();
+    }
+    k_pressure_matrix<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p, h->val.p, h->w.p, h->lev[0].A.val.p);
+    CK_LAUNCH();
+    for (int l = 0; l < L; l++) {
+        Level &Lv = h->lev[l];
+        int n = Lv.A.n;
+        k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.dpos.p, Lv.A.val.p, nullptr, err);
+        CK_LAUNCH();
+        if (l == L - 1) break;
+        if (o.amg == 0) {   // direct interpolation on the kept strength set and split; R = P^T
+            k_interp_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.A.rowptr.p, Lv.A.col.p, Lv.A.val.p,
+                                                                Lv.Srow.p, Lv.Scol.p, Lv.cf.p, Lv.cidx.p,
+                                                                Lv.P.rowptr.p, Lv.P.col.p, Lv.P.val.p);
+            CK_LAUNCH();
+            k_transpose_values<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.P.rowptr.p, Lv.P.col.p, Lv.P.val.p,
+                                                                     Lv.R.rowptr.p, Lv.R.col.p, Lv.R.val.p, err);
+            CK_LAUNCH();
+        }   // unsmoothed aggregation: P and R are unit, unchanged
+        spgemm_values(Lv.A, Lv.P, Lv.AP, err, s);
+        spgemm_values(Lv.R, Lv.AP, h->lev[l + 1].A, err, s);
+    }
+    CK(cudaEventRecord(h->ev_nr[2], s));
+    CK(cudaStreamWaitEvent(q, h->ev_nr[2], 0));
+    coarse_values(h, h->c_a.p, h->c_lu.p, h->c_piv.p, q);
+    CK(cudaEventRecord(h->ev_nr[3], q));
+    // the solve's copies in color order and their FP32 shadows
+    for (int l = 0; l + 1 < L; l++) {
+        Level &Lv = h->lev[l];
+        Level &Nx = h->lev[l + 1];
+        int n = Lv.A.n;
+        perm_fill(Lv.A, Lv.rows_by_color.p, Lv.iperm.p, true, Lv.Ao, s, f32 ? Lv.Aoval32.p : nullptr);
+        if (o.amg == 0) {
+            bool last = l + 1 == L - 1;   // the coarsest level keeps its natural order
+            perm_fill(Lv.P, Lv.rows_by_color.p, last ? nullptr : Nx.iperm.p, false, Lv.Pp, s,
+                      f32 ? Lv.Ppval32.p : nullptr);
+            perm_fill(Lv.R, last ? nullptr : Nx.rows_by_color.p, Lv.iperm.p, false, Lv.Rp, s,
+                      f32 ? Lv.Rpval32.p : nullptr);
+        }
+        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
+                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p,
+                                                          f32 ? Lv.diag32.p : nullptr, f32 ? Lv.dinv32.p : nullptr);
+        CK_LAUNCH();
+    }
+    CK(cudaStreamWaitEvent(s, h->ev_nr[1], 0));
+    CK(cudaStreamWaitEvent(s, h->ev_nr[3], 0));
+}
+
+}  // namespace
+
+// Alg. 3's rebuild of B with resetup = 1 and an unchanged pattern: every
+// value of B recomputed from the current A into the buffers of the last full
+// setup, whose discrete structure (levels, strength sets, C/F splits or
+// aggregates, colorings, BILU(0) ordering, every pattern) is kept.  The
+// launches are captured once into a CUDA graph and replayed on every later
+// refresh; no buffer moves, so the Arnoldi step graphs stay valid.
+void numeric_refresh(cpr_handle *h) {
+    Nvtx nv("numeric refresh");
+    cudaStream_t s = h->stream;
+    if (!h->nr_ready || !h->side || !h->lu_stream) fail(CPR_ERR_INVALID, "numeric refresh without a kept setup");
+    if (!h->nr_exec) {
+        for (auto &e : h->ev_nr)
+            if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        if (lu_in_smem(h->cn)) lu_smem_attr();
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        set_capturing(true);
+        try {
+            record_refresh(h);
+        } catch (...) {
+            set_capturing(false);
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        set_capturing(false);
+        CK(cudaStreamEndCapture(s, &g));
+        h->nr_graph = g;
+        h->nr_kernels = graph_kernel_nodes(g);
+        CK(cudaGraphInstantiate(&h->nr_exec, g, 0));
+    }
+    CK(cudaGraphLaunch(h->nr_exec, s));
+    count_launches(h->nr_kernels);
+    int e = read_int(h->err.p, s);
+    if (e != 0) {
+        CK(cudaMemsetAsync(h->err.p, 0, sizeof(int), s));
+        free_preconditioner(h);   // B matches no A now: the next update sets up afresh
+        fail(e, e == CPR_ERR_SINGULAR
+                    ? "zero or non-finite pivot in the numeric resetup: a decoupling block, an AMG level's "
+                      "diagonal, the coarsest matrix or a BILU(0) block"
+                    : "numeric resetup: A's pattern is not the one B was set up for");
+    }
 }
 
 }  // namespace cpr

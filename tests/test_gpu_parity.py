@@ -378,12 +378,18 @@ def test_numeric_resetup_matches_oracle(torch, cpr, spec):
     g = cpr.Solver(DevJ(torch, seq[0]), **kw)
     g32 = cpr.Solver(DevJ(torch, seq[0]), precond_fp32=1, **kw)
     first = [g.level(l)["n"] for l in range(g.nlev)]
+    rng = np.random.default_rng(11)
     for J in seq[1:]:
         o.update(J)
         g.update(DevJ(torch, J))
         g32.update(DevJ(torch, J))
         compare_hierarchy(o, g)
         assert [g.level(l)["n"] for l in range(g.nlev)] == first
+        # the solve's own copies (color order, coarse inverse, BILU(0) split) moved too
+        v = rng.standard_normal(J.n)
+        z = torch.zeros(J.n, dtype=torch.float64, device="cuda")
+        g.apply(dev(torch, v), z)
+        assert_apply_close(z.cpu().numpy(), o.cpr_apply(v), what="B v after a numeric resetup")
         xo, so = o.solve(J.b, rtol=1e-6)
         xg, sg = g.solve(dev(torch, J.b), rtol=1e-6)
         assert sg["setup_called"] == 1 and sg["converged"]
@@ -394,6 +400,38 @@ def test_numeric_resetup_matches_oracle(torch, cpr, spec):
         assert s32["setup_called"] == 1 and s32["converged"]
     g.close()
     g32.close()
+
+
+@pytest.mark.parametrize("amg", [0, 1])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_numeric_refresh_is_a_function_of_the_values(torch, cpr, fp32, amg):
+    """With resetup = 1 every rebuild after the first setup replays one
+    captured graph of value passes on the kept structure, so B depends on
+    A's values alone: going A0 -> A1 -> A0 -> A1 gives back, bit for bit,
+    the first setup's B and then the first refresh's (B v equal), in both
+    precisions and with both AMGs; solves after a replay converge."""
+    g0 = bs.GridSpec(37, 23, 9, 0.0, 1.5, 0.3, None, "five_spot", seed=5)
+    J0, J1 = list(bs.jacobian_sequence(g0, 2, drift=0.05))
+    g = cpr.Solver(DevJ(torch, J0), mu=0, resetup=1, precond_fp32=fp32, amg=amg, coarse_max=256)
+    v = dev(torch, np.random.default_rng(12).standard_normal(J0.n))
+
+    def bv():
+        z = torch.zeros(J0.n, dtype=torch.float64, device="cuda")
+        g.apply(v, z)
+        return z
+
+    z0 = bv()
+    seen = []
+    for J in (J1, J0, J1):
+        g.update(DevJ(torch, J))
+        seen.append(bv())
+        x, st = g.solve(dev(torch, J.b), rtol=1e-6)
+        assert st["setup_called"] == 1 and st["converged"], st
+        assert np.linalg.norm(J.b - oracle.bsr3_spmv(J, x.cpu().numpy())) < 1e-6 * np.linalg.norm(J.b)
+    assert not torch.equal(seen[0], z0)
+    assert torch.equal(seen[1], z0)
+    assert torch.equal(seen[2], seen[0])
+    g.close()
 
 
 @pytest.mark.parametrize("fp32", [0, 1])
