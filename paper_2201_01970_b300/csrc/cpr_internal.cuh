@@ -152,6 +152,13 @@ struct DCsr {
     DVec<double> val;
 };
 
+// The product lists of a sparse product C = A B on C's pattern: entry c of C
+// is the sum, in list order (ascending k), of av[pa[t]] * bv[pb[t]] for t in
+// [ptr[c], ptr[c+1]).
+struct ProdPlan {
+    DVec<int> ptr, pa, pb;
+};
+
 // One AMG level.  A, P, R hold the setup result in natural numbering
 // (bit-identical to the plain definition's; used for inspection).  The solve
 // uses copies renumbered into color order, so each color is a contiguous row
@@ -178,6 +185,7 @@ struct Level {
     DVec<int> dpos;               // position of each row's diagonal in A
     DVec<int> cidx;               // coarse index of each C point (classical AMG)
     DCsr AP;                      // the Galerkin product's left factor A P
+    ProdPlan pap, prap;           // the product lists of A P and R (A P)
     // amg = 1, levels 1 .. L-2: the GCR vectors of this level's coarse
     // correction (amli_iters x n each), its scalars and reduction partials
     DVec<double> gv, gw, gscal, gpart;

@@ -1127,8 +1127,56 @@ __global__ void k_interp_count(int n, const int *sr, const int *sc, const int *c
     cnt[i] = c;
 }
 
-// Stueben's direct interpolation with separate negative/positive scaling and
-// lumping of the positive part into the diagonal when C_i has no positive entry.
+// Row i of Stueben's direct interpolation with separate negative/positive
+// scaling and lumping of the positive part into the diagonal when C_i has no
+// positive entry, for an F point.  col/val: row i of A (len entries, sorted);
+// sc: row i of the strength set (slen entries, sorted), of which the entries
+// with cf == 1 are C_i (cf == nullptr: sc holds C_i alone); pc/pv: row i of
+// P.  Every sum runs in row order.
+__device__ void interp_row(int i, const int *col, const double *val, int len, const int *sc, int slen,
+                           const int *cf, const int *cidx, int *pc, double *pv) {
+    double aii = 0.0;
+    for (int p = 0; p < len; p++)
+        if (col[p] == i) aii = val[p];
+    double s = aii < 0.0 ? -1.0 : 1.0;
+    double sum_n_neg = 0.0, sum_n_pos = 0.0;
+    for (int p = 0; p < len; p++) {
+        if (col[p] == i) continue;
+        double v = __dmul_rn(s, val[p]);
+        if (v < 0.0) sum_n_neg = __dadd_rn(sum_n_neg, v);
+        else sum_n_pos = __dadd_rn(sum_n_pos, v);
+    }
+    double sum_c_neg = 0.0, sum_c_pos = 0.0;
+    int pa = 0;
+    for (int t = 0; t < slen; t++) {
+        int j = sc[t];
+        if (cf && cf[j] != 1) continue;
+        while (col[pa] != j) pa++;
+        double v = __dmul_rn(s, val[pa]);
+        if (v < 0.0) sum_c_neg = __dadd_rn(sum_c_neg, v);
+        else sum_c_pos = __dadd_rn(sum_c_pos, v);
+    }
+    double d = __dmul_rn(s, aii);
+    double alpha = 0.0, beta = 0.0;
+    if (sum_c_neg != 0.0) alpha = __ddiv_rn(sum_n_neg, sum_c_neg);
+    if (sum_c_pos != 0.0) beta = __ddiv_rn(sum_n_pos, sum_c_pos);
+    else d = __dadd_rn(d, sum_n_pos);
+    pa = 0;
+    int q = 0;
+    for (int t = 0; t < slen; t++) {
+        int j = sc[t];
+        if (cf && cf[j] != 1) continue;
+        while (col[pa] != j) pa++;
+        double v = __dmul_rn(s, val[pa]);
+        double f = v < 0.0 ? -alpha : -beta;
+        pc[q] = cidx[j];
+        pv[q] = __ddiv_rn(__dmul_rn(f, v), d);
+        q++;
+    }
+}
+
+// Direct interpolation, one thread per row: a C point's row is the unit row
+// of its coarse index.
 __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double *av,
                               const int *sr, const int *sc, const int *cf, const int *cidx,
                               const int *pr, int *pc, double *pv) {
@@ -1140,46 +1188,130 @@ __global__ void k_interp_fill(int n, const int *ar, const int *ac, const double 
         pv[q] = 1.0;
         return;
     }
-    int a = ar[i], b = ar[i + 1];
-    double aii = 0.0;
-    for (int p = a; p < b; p++)
-        if (ac[p] == i) aii = av[p];
-    double s = aii < 0.0 ? -1.0 : 1.0;
-    double sum_n_neg = 0.0, sum_n_pos = 0.0;
-    for (int p = a; p < b; p++) {
-        if (ac[p] == i) continue;
-        double v = __dmul_rn(s, av[p]);
-        if (v < 0.0) sum_n_neg = __dadd_rn(sum_n_neg, v);
-        else sum_n_pos = __dadd_rn(sum_n_pos, v);
-    }
-    double sum_c_neg = 0.0, sum_c_pos = 0.0;
-    int pa = a;
-    for (int p = sr[i]; p < sr[i + 1]; p++) {
-        int j = sc[p];
-        if (cf[j] != 1) continue;
-        while (ac[pa] != j) pa++;
-        double v = __dmul_rn(s, av[pa]);
-        if (v < 0.0) sum_c_neg = __dadd_rn(sum_c_neg, v);
-        else sum_c_pos = __dadd_rn(sum_c_pos, v);
-    }
-    double d = __dmul_rn(s, aii);
-    double alpha = 0.0, beta = 0.0;
-    if (sum_c_neg != 0.0) alpha = __ddiv_rn(sum_n_neg, sum_c_neg);
-    if (sum_c_pos != 0.0) beta = __ddiv_rn(sum_n_pos, sum_c_pos);
-    else d = __dadd_rn(d, sum_n_pos);
-    pa = a;
-    for (int p = sr[i]; p < sr[i + 1]; p++) {
-        int j = sc[p];
-        if (cf[j] != 1) continue;
-        while (ac[pa] != j) pa++;
-        double v = __dmul_rn(s, av[pa]);
-        double f = v < 0.0 ? -alpha : -beta;
-        pc[q] = cidx[j];
-        pv[q] = __ddiv_rn(__dmul_rn(f, v), d);
-        q++;
+    int a = ar[i];
+    interp_row(i, ac + a, av + a, ar[i + 1] - a, sc + sr[i], sr[i + 1] - sr[i], cf, cidx, pc + q, pv + q);
+}
+
+// Direct interpolation for long rows on small levels, one warp per row (there
+// a thread per row leaves most of the GPU idle and walks its row alone).
+// The warp stages row i of A with coalesced loads, finds a_ii, scales the row
+// by its sign s and looks up C_i's entries, all across the lanes; one lane
+// folds the four sums in row order; then each lane writes its share of P's
+// row, one quotient per entry.  The arithmetic, and the order of every sum,
+// is interp_row's.  A row larger than the staging area (row of A, or its
+// strength row) runs interp_row on global memory.
+constexpr int kInterpWarps = 4;
+constexpr int kInterpCapA = 512;
+constexpr int kInterpCapS = 256;
+constexpr int kInterpWarpRows = 16384;   // levels up to this size take the warp kernel
+__global__ void __launch_bounds__(kInterpWarps * 32) k_interp_fill_warp(int n, const int *ar, const int *ac,
+                                                                        const double *av, const int *sr,
+                                                                        const int *sc, const int *cf,
+                                                                        const int *cidx, const int *pr, int *pc,
+                                                                        double *pv) {
+    __shared__ int scol[kInterpWarps][kInterpCapA];
+    __shared__ double sval[kInterpWarps][kInterpCapA];   // a_ij, then s a_ij
+    __shared__ int sC[kInterpWarps][kInterpCapS];        // C_i in strength-row order
+    __shared__ double sv[kInterpWarps][kInterpCapS];     // s a_ij for j in C_i
+    __shared__ double scal[kInterpWarps][3];             // d, alpha, beta
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    unsigned lt = (1u << lane) - 1u;
+    int *col = scol[wl], *C = sC[wl];
+    double *val = sval[wl], *cv = sv[wl];
+    for (int i = blockIdx.x * kInterpWarps + wl; i < n; i += gridDim.x * kInterpWarps) {
+        int q = pr[i];
+        if (cf[i] == 1) {
+            if (lane == 0) {
+                pc[q] = cidx[i];
+                pv[q] = 1.0;
+            }
+            continue;
+        }
+        int a = ar[i], len = ar[i + 1] - a, s0 = sr[i], slen = sr[i + 1] - s0;
+        if (len > kInterpCapA || slen > kInterpCapS) {
+            if (lane == 0) interp_row(i, ac + a, av + a, len, sc + s0, slen, cf, cidx, pc + q, pv + q);
+            __syncwarp();
+            continue;
+        }
+        double aii = 0.0;
+        bool diag = false;
+        for (int t = lane; t < len; t += 32) {
+            int c = ac[a + t];
+            double v = av[a + t];
+            col[t] = c;
+            val[t] = v;
+            if (c == i) {
+                aii = v;
+                diag = true;
+            }
+        }
+        unsigned has = __ballot_sync(0xffffffffu, diag);   // a row holds its diagonal once
+        aii = has ? __shfl_sync(0xffffffffu, aii, 31 - __clz(has)) : 0.0;
+        double s = aii < 0.0 ? -1.0 : 1.0;
+        for (int t = lane; t < len; t += 32) val[t] = __dmul_rn(s, val[t]);
+        int m = 0;
+        for (int t0 = 0; t0 < slen; t0 += 32) {
+            int t = t0 + lane;
+            int j = t < slen ? sc[s0 + t] : 0;
+            bool c = t < slen && cf[j] == 1;
+            unsigned bal = __ballot_sync(0xffffffffu, c);
+            if (c) C[m + __popc(bal & lt)] = j;
+            m += __popc(bal);
+        }
+        __syncwarp();
+        for (int t = lane; t < m; t += 32) {   // C_i lies in row i's pattern
+            int pos = min(find_col(col, 0, len, C[t]), len - 1);
+            cv[t] = val[pos];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            double sum_n_neg = 0.0, sum_n_pos = 0.0, sum_c_neg = 0.0, sum_c_pos = 0.0;
+            for (int p = 0; p < len; p++) {
+                if (col[p] == i) continue;
+                double v = val[p];
+                if (v < 0.0) sum_n_neg = __dadd_rn(sum_n_neg, v);
+                else sum_n_pos = __dadd_rn(sum_n_pos, v);
+            }
+            for (int t = 0; t < m; t++) {
+                double v = cv[t];
+                if (v < 0.0) sum_c_neg = __dadd_rn(sum_c_neg, v);
+                else sum_c_pos = __dadd_rn(sum_c_pos, v);
+            }
+            double d = __dmul_rn(s, aii);
+            double alpha = 0.0, beta = 0.0;
+            if (sum_c_neg != 0.0) alpha = __ddiv_rn(sum_n_neg, sum_c_neg);
+            if (sum_c_pos != 0.0) beta = __ddiv_rn(sum_n_pos, sum_c_pos);
+            else d = __dadd_rn(d, sum_n_pos);
+            scal[wl][0] = d;
+            scal[wl][1] = alpha;
+            scal[wl][2] = beta;
+        }
+        __syncwarp();
+        double d = scal[wl][0], alpha = scal[wl][1], beta = scal[wl][2];
+        for (int t = lane; t < m; t += 32) {
+            double v = cv[t];
+            double f = v < 0.0 ? -alpha : -beta;
+            pc[q + t] = cidx[C[t]];
+            pv[q + t] = __ddiv_rn(__dmul_rn(f, v), d);
+        }
+        __syncwarp();
     }
 }
 
+// Direct interpolation into P's pattern: warp per row on small levels whose
+// rows average more than 16 entries, else thread per row.
+void interp_fill(const DCsr &A, const int *sr, const int *sc, const int *cf, const int *cidx, DCsr &P,
+                 cudaStream_t s) {
+    int n = A.n;
+    if (!n) return;
+    if (n <= kInterpWarpRows && A.nnz > 16L * n)
+        k_interp_fill_warp<<<grid_for(n, kInterpWarps), kInterpWarps * 32, 0, s>>>(
+            n, A.rowptr.p, A.col.p, A.val.p, sr, sc, cf, cidx, P.rowptr.p, P.col.p, P.val.p);
+    else
+        k_interp_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, sr, sc, cf, cidx,
+                                                            P.rowptr.p, P.col.p, P.val.p);
+    CK_LAUNCH();
+}
 
 // ------------------------------------------------- SpGEMM with per-warp hashing
 //
@@ -1605,17 +1737,17 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
     }
 }
 
-// The values of C = A B on C's pattern from an earlier product of the same
-// patterns (rows of B and C sorted).  G lanes per row of C zero the row, then
-// add a_ik b_kJ for the row's A entries k in ascending order, the lanes over
-// B_k's columns; a B row holds each column once, so the lanes of one step
-// never meet, and every C entry is summed in Gustavson's order, as in the
-// tiered product above.  G divides 32 and the block, so a group's lanes share
-// a warp and leave together.
-template <int G>
-__global__ void k_spgemm_numeric(int n, const int *ar, const int *ac, const double *av, const int *br,
-                                 const int *bc, const double *bv, const int *cr, const int *cc, double *cv,
-                                 int *err) {
+// The product lists of C = A B on C's pattern (an earlier product of the
+// same patterns; rows of B and C sorted).  G lanes per row of C walk the
+// row's A entries k in ascending order, the lanes over B_k's columns; a B
+// row holds each column once, so the lanes of one step never meet, and
+// every entry's list comes out in ascending k, the order in which the tiered
+// product above sums it.  Count pass (cur: zeroed, receives the list
+// lengths) or fill pass (cur: each list's next free slot).  G divides 32 and
+// the block, so a group's lanes share a warp and leave together.
+template <int G, bool FILL>
+__global__ void k_plan_pairs(int n, const int *ar, const int *ac, const int *br, const int *bc, const int *cr,
+                             const int *cc, int *cur, int *pa, int *pb, int *err) {
     long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
     long i = tid / G;
     int lane = (int)(tid % G);
@@ -1623,18 +1755,33 @@ __global__ void k_spgemm_numeric(int n, const int *ar, const int *ac, const doub
     int wl = threadIdx.x & 31;
     unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
     int c0 = cr[i], c1 = cr[i + 1];
-    for (int q = c0 + lane; q < c1; q += G) cv[q] = 0.0;
-    __syncwarp(gmask);
     for (int p = ar[i]; p < ar[i + 1]; p++) {
         int k = ac[p];
-        double a = av[p];
         for (int q = br[k] + lane; q < br[k + 1]; q += G) {
             int J = bc[q];
             int pos = find_col(cc, c0, c1, J);
-            if (pos < c1 && cc[pos] == J) cv[pos] = __dadd_rn(cv[pos], __dmul_rn(a, bv[q]));
-            else set_err(err, CPR_ERR_INVALID);   // not the pattern this C was built for
+            if (pos < c1 && cc[pos] == J) {
+                int t = cur[pos]++;
+                if (FILL) {
+                    pa[t] = p;
+                    pb[t] = q;
+                }
+            } else {
+                set_err(err, CPR_ERR_INVALID);   // not the pattern this C was built for
+            }
         }
         __syncwarp(gmask);
+    }
+}
+
+// C's values from its product lists: each entry's products rounded and
+// summed from zero in list order, exactly as the tiered product sums them.
+__global__ void k_plan_values(int nnz, const int *ptr, const int *pa, const int *pb, const double *av,
+                              const double *bv, double *cv) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nnz; c += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = ptr[c]; t < ptr[c + 1]; t++) s = __dadd_rn(s, __dmul_rn(av[pa[t]], bv[pb[t]]));
+        cv[c] = s;
     }
 }
 
@@ -1851,73 +1998,90 @@ __global__ void k_csr_to_dense(int n, const int *rowptr, const int *col, const d
     for (int p = rowptr[i]; p < rowptr[i + 1]; p++) a[(size_t)i * n + col[p]] = val[p];
 }
 
+// |x| as an integer key that orders as the magnitudes do (IEEE doubles of one
+// sign order as their bit patterns), so the pivot search needs no FP64
+// instruction; a NaN is the smallest key, so it never wins, as it never
+// compares larger.
+__device__ __forceinline__ long long abs_key(double x) {
+    long long k = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+    return k > 0x7ff0000000000000LL ? -1 : k;
+}
+
+// The larger of two (key, position) candidates, the lower position on ties.
+__device__ __forceinline__ void pivot_max(long long &best, int &bi, long long ov, int oi) {
+    if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+    }
+}
+
 // Dense LU with partial pivoting of the coarsest matrix (largest |a|, lowest
-// position on ties), one CTA.  Rows are never moved: perm[k] is the storage row
-// at position k.  The factors leave in position order in `lu` (row-major, row k
-// = position k).  The matrix is staged in shared memory when it fits.
-constexpr int kLuThreads = 256;
-__global__ void __launch_bounds__(kLuThreads) k_dense_lu(int n, const double *a_g, double *lu, int *perm,
+// position on ties), one CTA of 32 warps.  Rows are never moved: perm[k] is
+// the storage row at position k, kept in shared memory.  Step k finds the
+// pivot (integer keys: the warps holding candidates, then warp 0), scales
+// column k below it into the multipliers, then updates the trailing rows, a
+// warp per row and the lanes over its columns.  The factors leave in
+// position order in `lu` (row-major, row k = position k) when the matrix is
+// staged in shared memory; otherwise `lu` holds the copy factored in storage
+// order.  Dynamic shared memory: n*n doubles when use_smem, then n ints.
+constexpr int kLuThreads = 1024;
+__global__ void __launch_bounds__(kLuThreads) k_dense_lu(int n, const double *a_g, double *lu, int *perm_g,
                                                          int use_smem, int *err) {
     extern __shared__ double sm[];
-    __shared__ double wv[kLuThreads / 32];
+    __shared__ long long wv[kLuThreads / 32];
     __shared__ int wi[kLuThreads / 32];
     __shared__ int prow;
     __shared__ double pinv;
     double *a = use_smem ? sm : lu;
-    int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    for (long e = tid; e < (long)n * n; e += nt) a[e] = a_g[e];
+    int *perm = reinterpret_cast<int *>(sm + (use_smem ? (size_t)n * n : 0));
+    int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    if (use_smem)
+        for (long e = tid; e < (long)n * n; e += nt) a[e] = a_g[e];
     for (int i = tid; i < n; i += nt) perm[i] = i;
     __syncthreads();
     for (int k = 0; k < n; k++) {
-        double best = -1.0;
-        int bi = INT_MAX;
-        for (int i = k + tid; i < n; i += nt) {
-            double v = fabs(a[(size_t)perm[i] * n + k]);
-            if (v > best) {
-                best = v;
-                bi = i;
+        int cw = min(nw, (n - k + 31) / 32);   // warps holding candidates
+        if (wid < cw) {
+            long long best = -1;
+            int bi = INT_MAX;
+            for (int i = k + tid; i < n; i += nt) pivot_max(best, bi, abs_key(a[(size_t)perm[i] * n + k]), i);
+            for (int sh = 16; sh > 0; sh >>= 1)
+                pivot_max(best, bi, __shfl_xor_sync(0xffffffffu, best, sh), __shfl_xor_sync(0xffffffffu, bi, sh));
+            if (lane == 0) {
+                wv[wid] = best;
+                wi[wid] = bi;
             }
-        }
-        for (int sh = 16; sh > 0; sh >>= 1) {
-            double ov = __shfl_xor_sync(0xffffffffu, best, sh);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, sh);
-            if (ov > best || (ov == best && oi < bi)) {
-                best = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            wv[wid] = best;
-            wi[wid] = bi;
         }
         __syncthreads();
-        if (tid == 0) {
-            double bv = wv[0];
-            int b = wi[0];
-            for (int w = 1; w < nt / 32; w++)
-                if (wv[w] > bv || (wv[w] == bv && wi[w] < b)) {
-                    bv = wv[w];
-                    b = wi[w];
+        if (wid == 0) {
+            long long best = lane < cw ? wv[lane] : -1;
+            int bi = lane < cw ? wi[lane] : INT_MAX;
+            for (int sh = 16; sh > 0; sh >>= 1)
+                pivot_max(best, bi, __shfl_xor_sync(0xffffffffu, best, sh), __shfl_xor_sync(0xffffffffu, bi, sh));
+            if (lane == 0) {
+                if (best <= 0) {   // zero or NaN column
+                    set_err(err, CPR_ERR_SINGULAR);
+                    bi = k;
                 }
-            if (!(bv > 0.0)) {
-                set_err(err, CPR_ERR_SINGULAR);
-                b = k;
+                int t = perm[k];
+                perm[k] = perm[bi];
+                perm[bi] = t;
+                prow = perm[k];
+                double pv = a[(size_t)prow * n + k];
+                pinv = pv == 0.0 ? 1.0 : 1.0 / pv;
             }
-            int t = perm[k];
-            perm[k] = perm[b];
-            perm[b] = t;
-            prow = perm[k];
-            double pv = a[(size_t)prow * n + k];
-            pinv = pv == 0.0 ? 1.0 : 1.0 / pv;
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < n; i += nt) {
+            double *ri = a + (size_t)perm[i] * n;
+            ri[k] = ri[k] * pinv;
         }
         __syncthreads();
         const double *pr = a + (size_t)prow * n;
-        for (int i = k + 1 + wid; i < n; i += nt / 32) {
+        for (int i = k + 1 + wid; i < n; i += nw) {
             double *ri = a + (size_t)perm[i] * n;
-            double l = ri[k] * pinv;
+            double l = ri[k];
             for (int j = k + 1 + lane; j < n; j += 32) ri[j] -= l * pr[j];
-            __syncwarp();
-            if (lane == 0) ri[k] = l;
         }
         __syncthreads();
     }
@@ -1928,6 +2092,7 @@ __global__ void __launch_bounds__(kLuThreads) k_dense_lu(int n, const double *a_
             lu[e] = a[(size_t)perm[k] * n + q];
         }
     }
+    for (int i = tid; i < n; i += nt) perm_g[i] = perm[i];
 }
 
 // out[k*n + q] = in[perm[k]*n + q] (rows gathered into position order).
@@ -1938,27 +2103,45 @@ __global__ void k_gather_rows(int n, const double *in, const int *perm, double *
     out[e] = in[(size_t)perm[k] * n + q];
 }
 
-// Column j of A^-1 from the LU factors (one CTA per column): x = P e_j
-// (x_k = 1 where perm[k] = j), then column-oriented forward (unit L) and
-// backward (U) substitution in shared memory; written row-major (inv[i*n + j]).
-__global__ void k_dense_inv_cols(int n, const double *lu, const int *perm, double *inv) {
-    extern __shared__ double x[];
-    int j = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid; i < n; i += nt) x[i] = perm[i] == j ? 1.0 : 0.0;
+// Column j of A^-1 from the LU factors, one CTA per column: the factors are
+// staged in shared memory when `staged` (n*n doubles), then one warp runs the
+// substitutions column by column -- y = L^-1 P e_j (unit L; y_k = 1 where
+// perm[k] = j), x = U^-1 y -- each step taking the finished entry and
+// updating the ones after (before) it across the lanes.  The reciprocals of
+// U's diagonal are formed first, off that chain.  Written row-major
+// (inv[i*n + j]).  Dynamic shared memory: 2n doubles, then the factors.
+constexpr int kInvThreads = 128;
+__global__ void __launch_bounds__(kInvThreads) k_dense_inv_cols(int n, const double *lu, const int *perm,
+                                                                double *inv, int staged) {
+    extern __shared__ double sm[];
+    double *x = sm, *rd = sm + n;
+    const double *f = lu;
+    int tid = threadIdx.x, nt = blockDim.x, j = blockIdx.x;
+    if (staged) {
+        double *fs = sm + 2 * (size_t)n;
+        for (long e = tid; e < (long)n * n; e += nt) fs[e] = lu[e];
+        f = fs;
+    }
+    for (int i = tid; i < n; i += nt) {
+        x[i] = perm[i] == j ? 1.0 : 0.0;
+        rd[i] = 1.0 / lu[(size_t)i * n + i];
+    }
     __syncthreads();
+    if (tid >= 32) return;
+    int lane = tid;
     for (int k = 0; k < n; k++) {
         double xk = x[k];
-        for (int i = k + 1 + tid; i < n; i += nt) x[i] -= lu[(size_t)i * n + k] * xk;
-        __syncthreads();
+        for (int i = k + 1 + lane; i < n; i += 32) x[i] -= f[(size_t)i * n + k] * xk;
+        __syncwarp();
     }
     for (int k = n - 1; k >= 0; k--) {
-        if (tid == 0) x[k] /= lu[(size_t)k * n + k];
-        __syncthreads();
-        double xk = x[k];
-        for (int i = tid; i < k; i += nt) x[i] -= lu[(size_t)i * n + k] * xk;
-        __syncthreads();
+        double xk = x[k] * rd[k];
+        for (int i = lane; i < k; i += 32) x[i] -= f[(size_t)i * n + k] * xk;
+        __syncwarp();
+        if (lane == 0) x[k] = xk;
+        __syncwarp();
     }
-    for (int i = tid; i < n; i += nt) inv[(size_t)i * n + j] = x[i];
+    for (int i = lane; i < n; i += 32) inv[(size_t)i * n + j] = x[i];
 }
 
 // ------------------------------------------------------------------ BILU(0)
@@ -2666,24 +2849,48 @@ void copy_ints(DVec<int> &dst, const int *src, size_t n, cudaStream_t s) {
 // Each fills buffers that are already in place from the current values, so
 // the full setup and the numeric refresh (resetup = 1) run the same kernels.
 
-// C's values from A's and B's on C's pattern (an earlier spgemm of the same
-// patterns): lanes per row from B's mean row length.
-void spgemm_values(const DCsr &A, const DCsr &B, DCsr &C, int *err, cudaStream_t s) {
-    int n = A.n;
-    if (!n) return;
+// The product lists of C = A B (C from an earlier spgemm of A and B's
+// patterns): count pass, scan, fill pass; lanes per row from B's mean row
+// length.
+void plan_product(const DCsr &A, const DCsr &B, const DCsr &C, ProdPlan &pl, int *err, cudaStream_t s) {
+    int n = A.n, nnz = C.nnz;
+    DVec<int> cur;
+    cur.alloc(std::max(nnz, 1), s);
+    cur.zero();
     int g = lanes_for((double)B.nnz / std::max(B.n, 1), n, 1L << 17);
     auto run = [&](auto kern, int G) {
-        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p,
-                                                             B.val.p, C.rowptr.p, C.col.p, C.val.p, err);
+        kern<<<grid_for((long)n * G, kBlock), kBlock, 0, s>>>(n, A.rowptr.p, A.col.p, B.rowptr.p, B.col.p,
+                                                             C.rowptr.p, C.col.p, cur.p, pl.pa.p, pl.pb.p, err);
+        CK_LAUNCH();
     };
-    switch (g) {
-    case 1: run(k_spgemm_numeric<1>, 1); break;
-    case 2: run(k_spgemm_numeric<2>, 2); break;
-    case 4: run(k_spgemm_numeric<4>, 4); break;
-    case 8: run(k_spgemm_numeric<8>, 8); break;
-    case 16: run(k_spgemm_numeric<16>, 16); break;
-    default: run(k_spgemm_numeric<32>, 32); break;
-    }
+    auto pass = [&](auto fill) {
+        constexpr bool F = decltype(fill)::value;
+        if (!n) return;
+        switch (g) {
+        case 1: run(k_plan_pairs<1, F>, 1); break;
+        case 2: run(k_plan_pairs<2, F>, 2); break;
+        case 4: run(k_plan_pairs<4, F>, 4); break;
+        case 8: run(k_plan_pairs<8, F>, 8); break;
+        case 16: run(k_plan_pairs<16, F>, 16); break;
+        default: run(k_plan_pairs<32, F>, 32); break;
+        }
+    };
+    pass(std::false_type{});
+    pl.ptr.alloc((size_t)nnz + 1, s);
+    exclusive_scan(cur.p, pl.ptr.p, nnz, s);
+    int np = read_int(pl.ptr.p + nnz, s);
+    if (np < 0) fail(CPR_ERR_OOM, "product lists of a Galerkin product too large");
+    pl.pa.alloc(std::max(np, 1), s);
+    pl.pb.alloc(std::max(np, 1), s);
+    if (nnz) CK(cudaMemcpyAsync(cur.p, pl.ptr.p, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
+    pass(std::true_type{});
+}
+
+// C's values from its product lists.
+void plan_values(const ProdPlan &pl, const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
+    if (!C.nnz) return;
+    k_plan_values<<<grid_for(C.nnz, kBlock), kBlock, 0, s>>>(C.nnz, pl.ptr.p, pl.pa.p, pl.pb.p, A.val.p, B.val.p,
+                                                             C.val.p);
     CK_LAUNCH();
 }
 
@@ -2741,11 +2948,16 @@ constexpr int kLuSmemMax = 200 * 1024;
 
 bool lu_in_smem(int n) { return (size_t)n * n * sizeof(double) <= kLuSmemMax; }
 
-// The shared-memory ceiling of k_dense_lu, set before its first launch (and
-// outside any capture): always the same value, so handles set up on other
-// host threads never see a smaller limit than the one they launch with.
+// The shared-memory ceiling of k_dense_lu (the staged matrix and the row
+// order), set before its first launch and outside any capture: always the
+// same value, so handles set up on other host threads never see a smaller
+// limit than the one they launch with.
 void lu_smem_attr() {
-    CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, kLuSmemMax));
+    CK(cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            kLuSmemMax + (int)sizeof(int) * kMaxCoarse));
+    // staged factors (n*n*8 <= kLuSmemMax, so n <= 160) and 2n doubles; unstaged, 2n doubles
+    CK(cudaFuncSetAttribute(k_dense_inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            std::max(kLuSmemMax + 16 * 160, 16 * kMaxCoarse)));
 }
 
 // h->cinv = the inverse of the coarsest matrix by dense LU with partial
@@ -2760,14 +2972,15 @@ void coarse_values(cpr_handle *h, double *a, double *lu, int *piv, cudaStream_t 
     int use_smem = lu_in_smem(n) ? 1 : 0;
     // global path: factor a copy in storage order, then gather rows into position order
     if (!use_smem) CK(cudaMemcpyAsync(lu, a, bytes, cudaMemcpyDeviceToDevice, q));
-    k_dense_lu<<<1, kLuThreads, use_smem ? bytes : 0, q>>>(n, a, lu, piv, use_smem, h->err.p);
+    k_dense_lu<<<1, kLuThreads, (use_smem ? bytes : 0) + sizeof(int) * n, q>>>(n, a, lu, piv, use_smem, h->err.p);
     CK_LAUNCH();   // a zero pivot is reported by the caller's error check
     if (!use_smem) {
         k_gather_rows<<<grid_for((long)n * n, kBlock), kBlock, 0, q>>>(n, lu, piv, a);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(lu, a, bytes, cudaMemcpyDeviceToDevice, q));
     }
-    k_dense_inv_cols<<<n, 256, sizeof(double) * n, q>>>(n, lu, piv, h->cinv.p);
+    size_t inv_smem = sizeof(double) * (2 * (size_t)n + (use_smem ? (size_t)n * n : 0));
+    k_dense_inv_cols<<<n, kInvThreads, inv_smem, q>>>(n, lu, piv, h->cinv.p, use_smem);
     CK_LAUNCH();
 }
 
@@ -3305,10 +3518,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             L.P.nnz = read_int(L.P.rowptr.p + n, s);
             L.P.col.alloc(std::max(L.P.nnz, 1), s);
             L.P.val.alloc(std::max(L.P.nnz, 1), s);
-            k_interp_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
-                                                                S.rowptr.p, S.col.p, L.cf.p, cidx.p,
-                                                                L.P.rowptr.p, L.P.col.p, L.P.val.p);
-            CK_LAUNCH();
+            interp_fill(L.A, S.rowptr.p, S.col.p, L.cf.p, cidx.p, L.P, s);
             L.R.n = nc;
             L.R.ncol = n;
             L.R.nnz = L.P.nnz;
@@ -3364,7 +3574,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         h->c_a.alloc((size_t)n * n, s);
         h->c_lu.alloc((size_t)n * n, s);
         h->c_piv.alloc(std::max(n, 1), s);
-        if (lu_in_smem(n)) lu_smem_attr();
+        lu_smem_attr();
         CK(cudaEventRecord(h->ev_coarse[0], s));
         CK(cudaStreamWaitEvent(q, h->ev_coarse[0], 0));
         coarse_join.s = s;
@@ -3527,16 +3737,13 @@ void record_refresh(cpr_handle *h) {
         CK_LAUNCH();
         if (l == L - 1) break;
         if (o.amg == 0) {   // direct interpolation on the kept strength set and split; R = P^T
-            k_interp_fill<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.A.rowptr.p, Lv.A.col.p, Lv.A.val.p,
-                                                                Lv.Srow.p, Lv.Scol.p, Lv.cf.p, Lv.cidx.p,
-                                                                Lv.P.rowptr.p, Lv.P.col.p, Lv.P.val.p);
-            CK_LAUNCH();
+            interp_fill(Lv.A, Lv.Srow.p, Lv.Scol.p, Lv.cf.p, Lv.cidx.p, Lv.P, s);
             k_transpose_values<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.P.rowptr.p, Lv.P.col.p, Lv.P.val.p,
                                                                      Lv.R.rowptr.p, Lv.R.col.p, Lv.R.val.p, err);
             CK_LAUNCH();
         }   // unsmoothed aggregation: P and R are unit, unchanged
-        spgemm_values(Lv.A, Lv.P, Lv.AP, err, s);
-        spgemm_values(Lv.R, Lv.AP, h->lev[l + 1].A, err, s);
+        plan_values(Lv.pap, Lv.A, Lv.P, Lv.AP, s);
+        plan_values(Lv.prap, Lv.R, Lv.AP, h->lev[l + 1].A, s);
     }
     CK(cudaEventRecord(h->ev_nr[2], s));
     CK(cudaStreamWaitEvent(q, h->ev_nr[2], 0));
@@ -3577,9 +3784,16 @@ void numeric_refresh(cpr_handle *h) {
     cudaStream_t s = h->stream;
     if (!h->nr_ready || !h->side || !h->lu_stream) fail(CPR_ERR_INVALID, "numeric refresh without a kept setup");
     if (!h->nr_exec) {
+        // the Galerkin products' lists, once per kept structure
+        for (int l = 0; l + 1 < (int)h->lev.size(); l++) {
+            Level &Lv = h->lev[l];
+            plan_product(Lv.A, Lv.P, Lv.AP, Lv.pap, h->err.p, s);
+            plan_product(Lv.R, Lv.AP, h->lev[l + 1].A, Lv.prap, h->err.p, s);
+        }
+        check_err(h, "numeric resetup: the kept Galerkin patterns do not fit");
         for (auto &e : h->ev_nr)
             if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        if (lu_in_smem(h->cn)) lu_smem_attr();
+        lu_smem_attr();
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         set_capturing(true);
