@@ -152,51 +152,72 @@ __global__ void k_compose(int n, const int *first, const int *second, int *out) 
 
 // -------------------------------------------------------- strength (Eq. 5.1)
 
-// j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik| (sum over the whole row).
-// srowptr == nullptr: count pass (out = counts); otherwise fill pass (out = columns).
+// The strength tests compare FP64 values on the integer pipe (B300's FP64
+// pipe is 1/64 of its FP32 rate): ord_key maps a double's bits to a signed
+// integer with key(x) < key(y) iff x < y and equal keys for equal values
+// (-0 taken as +0).  A NaN has no place in that order; the callers skip it,
+// so a NaN entry is never strong and never the row's maximum.
+constexpr long long kSignBit = (long long)0x8000000000000000ULL;
+constexpr long long kMagBits = 0x7fffffffffffffffLL;
+__device__ __forceinline__ long long ord_key(long long u) {
+    if (u == kSignBit) u = 0;
+    return u >= 0 ? u : u ^ kMagBits;
+}
+__device__ __forceinline__ bool nan_bits(long long u) { return (u & kMagBits) > 0x7ff0000000000000LL; }
+
+// Eq. 5.1: j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik| (the sum in
+// row order over the whole row).  srowptr == nullptr: count pass (out =
+// counts); otherwise fill pass (out = columns).
 __global__ void k_strength51(int n, const int *rowptr, const int *col, const double *val,
                              double theta, const int *srowptr, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
+    const long long *vb = reinterpret_cast<const long long *>(val);
     double rowsum = 0.0;
-    for (int p = a; p < b; p++) rowsum = __dadd_rn(rowsum, fabs(val[p]));
-    double t = __dmul_rn(theta, rowsum);
+    for (int p = a; p < b; p++) rowsum = __dadd_rn(rowsum, __longlong_as_double(vb[p] & kMagBits));
+    long long tb = __double_as_longlong(__dmul_rn(theta, rowsum));
     int q = srowptr ? srowptr[i] : 0, c = 0;
-    for (int p = a; p < b; p++) {
-        int j = col[p];
-        if (j != i && fabs(val[p]) > t) {
-            if (srowptr) out[q + c] = j;
-            c++;
+    if (!nan_bits(tb)) {
+        long long tk = ord_key(tb);
+        for (int p = a; p < b; p++) {
+            int j = col[p];
+            long long u = vb[p] & kMagBits;   // |a_ij|: its bits are its key
+            if (j != i && !nan_bits(u) && u > tk) {
+                if (srowptr) out[q + c] = j;
+                c++;
+            }
         }
     }
     if (!srowptr) out[i] = c;
 }
 
-// Classical strength: with s = sign(a_ii), j in S_i iff -s a_ij >= theta max_{k!=i}(-s a_ik) > 0.
+// Classical strength: with s = sign(a_ii), j in S_i iff
+// -s a_ij >= theta max_{k!=i}(-s a_ik) > 0.  -s a_ij is a_ij with its sign
+// bit flipped when a_ii >= 0, so the maximum and the tests are integer work;
+// the threshold is the one FP64 product of the row.
 __global__ void k_strength_rs(int n, const int *rowptr, const int *col, const double *val,
                               double theta, const int *srowptr, int *out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
+    const long long *vb = reinterpret_cast<const long long *>(val);
     double aii = 0.0;
     for (int p = a; p < b; p++)
         if (col[p] == i) aii = val[p];
-    double s = aii < 0.0 ? -1.0 : 1.0;
-    double m = 0.0;
-    bool have = false;
+    long long flip = aii < 0.0 ? 0 : kSignBit;
+    long long mk = LLONG_MIN;
     for (int p = a; p < b; p++) {
-        if (col[p] == i) continue;
-        double v = -s * val[p];
-        if (!have || v > m) m = v;
-        have = true;
+        long long u = vb[p] ^ flip;
+        if (col[p] != i && !nan_bits(u)) mk = max(mk, ord_key(u));
     }
     int q = srowptr ? srowptr[i] : 0, c = 0;
-    if (have && m > 0.0) {
-        double t = __dmul_rn(theta, m);
+    if (mk > 0) {   // the largest -s a_ik is positive: its key is its bits
+        long long tk = ord_key(__double_as_longlong(__dmul_rn(theta, __longlong_as_double(mk))));
         for (int p = a; p < b; p++) {
             int j = col[p];
-            if (j != i && -s * val[p] >= t) {
+            long long u = vb[p] ^ flip;
+            if (j != i && !nan_bits(u) && ord_key(u) >= tk) {
                 if (srowptr) out[q + c] = j;
                 c++;
             }
@@ -208,14 +229,15 @@ __global__ void k_strength_rs(int n, const int *rowptr, const int *col, const do
 // Warp-per-row form of the classical strength kernel for levels with long
 // rows (coarse levels average 16-40 entries per row): a row's entries are
 // loaded by all lanes at once instead of one after another by one thread.
-// Same arithmetic (a maximum and comparisons, all exact) and the same output
-// order (ballot compaction in entry order).
+// Same tests on the same keys (the maximum an integer warp reduction) and
+// the same output order (ballot compaction in entry order).
 __global__ void k_strength_rs_warp(int n, const int *rowptr, const int *col, const double *val,
                                    double theta, const int *srowptr, int *out) {
     int lane = threadIdx.x & 31;
     int i = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
+    const long long *vb = reinterpret_cast<const long long *>(val);
     unsigned lt = (1u << lane) - 1u;
     double aii = 0.0;
     bool found = false;
@@ -226,25 +248,23 @@ __global__ void k_strength_rs_warp(int n, const int *rowptr, const int *col, con
         }
     unsigned fm = __ballot_sync(0xffffffffu, found);
     aii = fm ? __shfl_sync(0xffffffffu, aii, __ffs(fm) - 1) : 0.0;
-    double s = aii < 0.0 ? -1.0 : 1.0;
-    double m = -INFINITY;
-    bool have = false;
-    for (int p = a + lane; p < b; p += 32)
-        if (col[p] != i) {
-            m = fmax(m, -s * val[p]);
-            have = true;
-        }
-    for (int sh = 16; sh > 0; sh >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, sh));
-    have = __any_sync(0xffffffffu, have);
+    long long flip = aii < 0.0 ? 0 : kSignBit;
+    long long mk = LLONG_MIN;
+    for (int p = a + lane; p < b; p += 32) {
+        long long u = vb[p] ^ flip;
+        if (col[p] != i && !nan_bits(u)) mk = max(mk, ord_key(u));
+    }
+    for (int sh = 16; sh > 0; sh >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, sh));
     int q = srowptr ? srowptr[i] : 0, c = 0;
-    if (have && m > 0.0) {
-        double t = __dmul_rn(theta, m);
+    if (mk > 0) {
+        long long tk = ord_key(__double_as_longlong(__dmul_rn(theta, __longlong_as_double(mk))));
         for (int p0 = a; p0 < b; p0 += 32) {
             int p = p0 + lane, j = 0;
             bool keep = false;
             if (p < b) {
                 j = col[p];
-                keep = j != i && -s * val[p] >= t;
+                long long u = vb[p] ^ flip;
+                keep = j != i && !nan_bits(u) && ord_key(u) >= tk;
             }
             unsigned bm = __ballot_sync(0xffffffffu, keep);
             if (keep && srowptr) out[q + c + __popc(bm & lt)] = j;
@@ -2213,18 +2233,28 @@ __device__ __forceinline__ bool mat3_inv_t(const float *a, float *inv) {
 // before i are taken in index order alone: the operations, and their order,
 // of sequential block ILU(0) in index order.  FP64: every operation rounded as the plain definition orders it; FP32 (the
 // FP32-preconditioner mode, whose B only ever uses FP32 factors): FMA allowed.
-template <class T>
+//
+// G lanes per row: the lanes search the row for the next k together (a
+// group minimum), one lane forms L_ik, and the lanes share the updates of
+// row k's entries, each of which lands on its own block of row i.  Every
+// block operation is the one-thread form's, in the same order.  G divides
+// 32 and the block, so a group's lanes share a warp and leave together.
+template <class T, int G>
 __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr, const int *col,
                                     const int *color, const int *diag, T *lu, int *err, int natural) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
     if (t >= cnt) return;
+    int wl = threadIdx.x & 31;
+    unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
     int i = rows[t];
     int a = rowptr[i], b = rowptr[i + 1];
     int ci = color[i];
     int last_c = -1, last_k = -1;
     for (;;) {
         int best = -1, bc = INT_MAX, bk = INT_MAX;
-        for (int p = a; p < b; p++) {
+        for (int p = a + lane; p < b; p += G) {
             int k = col[p];
             int ck = color[k];
             if (ck >= ci) continue;
@@ -2237,23 +2267,41 @@ __global__ void k_bilu_factor_color(const int *rows, int cnt, const int *rowptr,
                 bk = k;
             }
         }
+        for (int o = G / 2; o > 0; o >>= 1) {
+            int obest = __shfl_xor_sync(gmask, best, o), obc = __shfl_xor_sync(gmask, bc, o),
+                obk = __shfl_xor_sync(gmask, bk, o);
+            if (obc < bc || (obc == bc && obk < bk)) {
+                best = obest;
+                bc = obc;
+                bk = obk;
+            }
+        }
         if (best < 0) break;
         int k = bk;
+        T *Lb = lu + 9 * (size_t)best;
+        if (lane == 0) {
+            T L[9];
+            mat3_mul_t<T>(Lb, lu + 9 * (size_t)diag[k], L);
+            for (int e = 0; e < 9; e++) Lb[e] = L[e];
+        }
+        __syncwarp(gmask);
         T L[9];
-        mat3_mul_t<T>(lu + 9 * (size_t)best, lu + 9 * (size_t)diag[k], L);
-        for (int e = 0; e < 9; e++) lu[9 * (size_t)best + e] = L[e];
-        for (int q = rowptr[k]; q < rowptr[k + 1]; q++) {
+        for (int e = 0; e < 9; e++) L[e] = Lb[e];
+        int ck = color[k];
+        for (int q = rowptr[k] + lane; q < rowptr[k + 1]; q += G) {
             int j = col[q];
-            if (j == k || color[j] <= color[k]) continue;
+            if (j == k || color[j] <= ck) continue;
             int r = find_col(col, a, b, j);
             if (r >= b || col[r] != j) continue;
             T P[9];
             mat3_mul_t<T>(L, lu + 9 * (size_t)q, P);
             for (int e = 0; e < 9; e++) lu[9 * (size_t)r + e] = sub_t(lu[9 * (size_t)r + e], P[e]);
         }
+        __syncwarp(gmask);
         last_c = bc;
         last_k = bk;
     }
+    if (lane != 0) return;
     T inv[9];
     T *D = lu + 9 * (size_t)diag[i];
     if (!mat3_inv_t(D, inv)) {
@@ -2894,6 +2942,12 @@ void plan_values(const ProdPlan &pl, const DCsr &A, const DCsr &B, DCsr &C, cuda
     CK_LAUNCH();
 }
 
+// Lanes per block row in k_bilu_factor_color: FP32 rows take a group of
+// lanes; FP64 rows one thread each (B300's FP64 pipe pays for every issued
+// instruction whatever its active lanes, so idle lanes of a group cost FP64
+// throughput).
+constexpr int kBiluFactorLanesF32 = 8;
+
 // The BILU(0) factors of the current A on the kept ordering and L/U patterns:
 // A's blocks copied (FP64) or rounded (FP32 mode) into the factor array,
 // factored color by color, then split into L, U and the inverted diagonal
@@ -2906,9 +2960,10 @@ void bilu_values(cpr_handle *h, const int *bdiag, cudaStream_t s) {
         for (int c = 0; c < B.ncolors; c++) {
             int cnt = B.color_off[c + 1] - B.color_off[c];
             if (!cnt) continue;
-            k_bilu_factor_color<T><<<grid_for(cnt, 128), 128, 0, s>>>(B.rows_by_color.p + B.color_off[c], cnt,
-                                                                     h->rowptr.p, h->col.p, B.color.p, bdiag, lu,
-                                                                     h->err.p, h->opt.bilu_order);
+            constexpr int G = sizeof(T) == 4 ? kBiluFactorLanesF32 : 1;
+            k_bilu_factor_color<T, G><<<grid_for((long)cnt * G, 128), 128, 0, s>>>(
+                B.rows_by_color.p + B.color_off[c], cnt, h->rowptr.p, h->col.p, B.color.p, bdiag, lu, h->err.p,
+                h->opt.bilu_order);
             CK_LAUNCH();
         }
         // a singular pivot block is reported by the caller's error check
