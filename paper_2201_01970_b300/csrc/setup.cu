@@ -145,6 +145,27 @@ __global__ void k_col0_perm(int nb, const int *order, const int *iperm, const in
     }
 }
 
+// The fill pass of k_col0_perm with G lanes per row (a lane per block, so a
+// warp reads whole rows of blocks instead of one block from each of 32 rows).
+template <int G>
+__global__ void k_col0_fill(int nb, const int *order, const int *iperm, const int *rowptr, const int *col,
+                            const double *val, const int *crow, int *ccol, double *cval) {
+    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    if (t >= nb) return;
+    int i = order[t];
+    int a = rowptr[i], q0 = crow[t] - a;
+    for (int p = a + lane; p < rowptr[i + 1]; p += G) {
+        const double *b = val + 9 * (size_t)p;
+        size_t q = (size_t)(q0 + p);
+        ccol[q] = iperm[col[p]];
+        cval[3 * q] = b[0];
+        cval[3 * q + 1] = b[3];
+        cval[3 * q + 2] = b[6];
+    }
+}
+
 __global__ void k_compose(int n, const int *first, const int *second, int *out) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) out[t] = second[first ? first[t] : t];
@@ -1994,14 +2015,14 @@ __global__ void k_perm_fill(int n, const int *order, const int *rowptr, const in
     }
 }
 
-__global__ void k_perm_diag(int n, const int *order, const int *rowptr, const int *col,
-                            const double *val, double *diag, double *dinv, float *diag32, float *dinv32) {
+// The diagonal and its reciprocal in color order (dpos: each natural row's
+// diagonal position, -1 for none, which reads as 0).
+__global__ void k_perm_diag(int n, const int *order, const int *dpos, const double *val, double *diag,
+                            double *dinv, float *diag32, float *dinv32) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    int i = order[t];
-    double d = 0.0;
-    for (int p = rowptr[i]; p < rowptr[i + 1]; p++)
-        if (col[p] == i) d = val[p];
+    int p = dpos[order[t]];
+    double d = p >= 0 ? val[p] : 0.0;
     double r = 1.0 / d;
     diag[t] = d;
     dinv[t] = r;
@@ -2328,42 +2349,50 @@ __global__ void k_bilu_split_count(int nb, const int *order, const int *rowptr, 
     ucnt[t] = u;
 }
 
-// One thread per block entry p of the natural factor array (its row found by
-// binary search in rowptr): copy its 9 values to L, U or D^-1 at the row's
-// position, with the column renumbered to its position.
-template <class T>
-__global__ void k_bilu_split_fill(long nnzb, int nb, const int *rowptr, const int *col,
-                                  const int *color, const int *iperm, const T *lu, const int *lr, int *lc,
-                                  T *lv, const int *ur, int *uc, T *uv, T *dinv) {
-    long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (p >= nnzb) return;
-    int lo = 0, hi = nb;   // row i: rowptr[i] <= p < rowptr[i+1]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (rowptr[mid] <= p) lo = mid;
-        else hi = mid;
-    }
-    int i = lo, j = col[p], ci = color[i], t = iperm[i];
-    T *dst;
-    if (j == i) {
-        dst = dinv + 9 * (size_t)t;
-    } else {
-        bool lower = color[j] < ci;
-        int k = 0;
-        for (int q = rowptr[i]; q < p; q++) {
-            int jq = col[q];
-            if (jq != i && (color[jq] < ci) == lower) k++;
+// G lanes per natural block row i: each entry of the factor array goes to L
+// (lower color), U (higher color) or D^-1 (the diagonal) at the row's
+// position, its index within L or U counted by group ballots, its column
+// renumbered to its position.  G divides 32 and the block.
+template <class T, int G>
+__global__ void k_bilu_split_fill(int nb, const int *rowptr, const int *col, const int *color, const int *iperm,
+                                  const T *lu, const int *lr, int *lc, T *lv, const int *ur, int *uc, T *uv,
+                                  T *dinv) {
+    long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    long i = tid / G;
+    int lane = (int)(tid % G);
+    if (i >= nb) return;
+    int wl = threadIdx.x & 31;
+    unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (wl & ~(G - 1));
+    unsigned below = gmask & ((1u << wl) - 1u);
+    int ci = color[i], t = iperm[(int)i];
+    int nl = lr[t], nu = ur[t];   // next free slots of the row's L and U parts
+    for (int p0 = rowptr[i]; p0 < rowptr[i + 1]; p0 += G) {
+        int p = p0 + lane;
+        bool in = p < rowptr[i + 1];
+        int j = in ? col[p] : 0;
+        bool d = in && j == i;
+        bool lower = in && !d && color[j] < ci;
+        bool upper = in && !d && !lower;
+        unsigned ml = __ballot_sync(gmask, lower), mu = __ballot_sync(gmask, upper);
+        T *dst = nullptr;
+        if (d) {
+            dst = dinv + 9 * (size_t)t;
+        } else if (lower) {
+            int k = nl + __popc(ml & below);
+            lc[k] = iperm[j];
+            dst = lv + 9 * (size_t)k;
+        } else if (upper) {
+            int k = nu + __popc(mu & below);
+            uc[k] = iperm[j];
+            dst = uv + 9 * (size_t)k;
         }
-        if (lower) {
-            lc[lr[t] + k] = iperm[j];
-            dst = lv + 9 * (size_t)(lr[t] + k);
-        } else {
-            uc[ur[t] + k] = iperm[j];
-            dst = uv + 9 * (size_t)(ur[t] + k);
+        if (dst) {
+            const T *src = lu + 9 * (size_t)p;
+            for (int e = 0; e < 9; e++) dst[e] = src[e];
         }
+        nl += __popc(ml);
+        nu += __popc(mu);
     }
-    const T *src = lu + 9 * (size_t)p;
-    for (int e = 0; e < 9; e++) dst[e] = src[e];
 }
 
 __global__ void k_d2f(long n, const double *a, float *b) {
@@ -2967,9 +2996,9 @@ void bilu_values(cpr_handle *h, const int *bdiag, cudaStream_t s) {
             CK_LAUNCH();
         }
         // a singular pivot block is reported by the caller's error check
-        k_bilu_split_fill<T><<<grid_for(nnzb, kBlock), kBlock, 0, s>>>(
-            nnzb, nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p,
-            B.Ucol.p, Uv, Dv);
+        k_bilu_split_fill<T, 8><<<grid_for(8L * nb, kBlock), kBlock, 0, s>>>(
+            nb, h->rowptr.p, h->col.p, B.color.p, B.iperm.p, lu, B.Lrowptr.p, B.Lcol.p, Lv, B.Urowptr.p, B.Ucol.p,
+            Uv, Dv);
         CK_LAUNCH();
     };
     if (h->opt.precond_fp32) {
@@ -2987,8 +3016,9 @@ void bilu_values(cpr_handle *h, const int *bdiag, cudaStream_t s) {
 void col0_values(cpr_handle *h, cudaStream_t s) {
     const Bilu &B = h->bilu;
     int nb = h->nb;
-    k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                       h->val.p, h->c0rowptr.p, h->c0col.p, h->pcol0.p, nullptr);
+    k_col0_fill<8><<<grid_for(8L * nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p,
+                                                               h->col.p, h->val.p, h->c0rowptr.p, h->c0col.p,
+                                                               h->pcol0.p);
     CK_LAUNCH();
     size_t n = std::min(h->pcol0.n, h->pcol0_32.n);
     if (h->pcol0_32.p && n) {
@@ -3661,8 +3691,8 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             Lv.diag32.alloc(n, s);
             Lv.dinv32.alloc(n, s);
         }
-        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
-                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p,
+        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.dpos.p, Lv.A.val.p,
+                                                          Lv.diag.p, Lv.dinv.p,
                                                           f32 ? Lv.diag32.p : nullptr, f32 ? Lv.dinv32.p : nullptr);
         CK_LAUNCH();
         // smoothing launches cover one color (n / ncolors rows on average);
@@ -3817,8 +3847,8 @@ void record_refresh(cpr_handle *h) {
             perm_fill(Lv.R, last ? nullptr : Nx.rows_by_color.p, Lv.iperm.p, false, Lv.Rp, s,
                       f32 ? Lv.Rpval32.p : nullptr);
         }
-        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.A.rowptr.p, Lv.A.col.p,
-                                                          Lv.A.val.p, Lv.diag.p, Lv.dinv.p,
+        k_perm_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, Lv.rows_by_color.p, Lv.dpos.p, Lv.A.val.p,
+                                                          Lv.diag.p, Lv.dinv.p,
                                                           f32 ? Lv.diag32.p : nullptr, f32 ? Lv.dinv32.p : nullptr);
         CK_LAUNCH();
     }
