@@ -309,6 +309,31 @@ def setup_profile(cpr, torch, J, stream, warm=4):
             "launches": launches}
 
 
+def resetup_profile(cpr, torch, seq, stream, updates=4):
+    """The numeric-only resetup (resetup = 1, FP32 mode) alone: a setup on the
+    sequence's first Jacobian, then `updates` rebuilds on the next ones (the
+    first captures the refresh graph, the rest replay it), each inside the
+    library's NVTX range "numeric refresh" (ncu --nvtx-include)."""
+    class DJ:
+        def __init__(self, J):
+            self.nb = J.nb
+            self.rowptr = torch.from_numpy(J.rowptr).cuda()
+            self.col = torch.from_numpy(J.col).cuda()
+            self.val = torch.from_numpy(J.val).cuda()
+
+    dev = [DJ(J) for J in seq]
+    solver = cpr.Solver(dev[0], precond_fp32=1, mu=0, resetup=1, stream=stream.cuda_stream)
+    walls = []
+    for k in range(1, updates + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        solver.update(dev[k % len(dev)])
+        torch.cuda.synchronize()
+        walls.append((time.perf_counter() - t) * 1e3)
+    solver.close()
+    return {"workload": f"{WORKLOAD} FP32-mode numeric resetup", "update_wall_ms": walls}
+
+
 def vcycle_profile(cpr, torch, workload, stream):
     """One FP32 hierarchy of `workload`: the in-graph time of every V-cycle
     part (20 repetitions per graph) and the level-0 smoothing colors' rows,
@@ -817,6 +842,8 @@ def main():
                     help="only sweep the smoother coloring's Eq. 5.1 threshold: colors, V-cycle time, iterations")
     ap.add_argument("--setup-profile", action="store_true",
                     help="only time setups of the workload, the last one bracketed for ncu and phase-marked")
+    ap.add_argument("--resetup-profile", action="store_true",
+                    help="only run numeric-only resetups of the workload (NVTX range 'numeric refresh')")
     ap.add_argument("--no-resetup-numeric", action="store_true",
                     help="skip the numeric-only resetup line")
     ap.add_argument("--no-ua-amg", action="store_true",
@@ -872,6 +899,11 @@ def main():
         res = serve_arm(not args.serve_scaled)
         if rank == 0:
             print(json.dumps({"serving": res}), flush=True)
+        return
+    if args.resetup_profile:
+        res = resetup_profile(cpr, torch, host_sequence(), stream)
+        if rank == 0:
+            print(json.dumps({"resetup_profile": res}), flush=True)
         return
     if args.setup_profile:
         res = setup_profile(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)

@@ -231,25 +231,11 @@ void exclusive_scan(const int *in, int *out, int n, cudaStream_t s) {
     CK_LAUNCH();
 }
 
-// The setup reads counts back from several host threads at once (the main
-// chain and its side worker).  A copy into pageable memory goes through the
-// driver's staging buffer, so each thread reads into a pinned int of its own,
-// allocated on its first read-back and freed when the thread ends.
-namespace {
-struct PinnedSlot {
-    int *p = nullptr;
-    ~PinnedSlot() {
-        if (p) cudaFreeHost(p);   // at process exit the runtime may already be gone: no check
-    }
-};
-}  // namespace
-
 int read_int(const int *dptr, cudaStream_t s) {
-    thread_local PinnedSlot slot;
-    if (!slot.p) CK(cudaMallocHost(&slot.p, sizeof(int)));
-    CK(cudaMemcpyAsync(slot.p, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return *slot.p;
+    return v;
 }
 
 // Hash weight of vertex i is fmix32(i ^ base), base = fmix32(seed32 + 1000003*salt + level);
