@@ -62,10 +62,13 @@ __global__ void k_compare(long n, const int *a, const int *b, int *diff) {
         if (a[i] != b[i]) atomicExch(diff, 1);
 }
 
+// The rebuild of B that Alg. 3 asks for: the numeric refresh when `numeric`
+// (resetup = 1, same pattern, a B set up with resetup = 1 in place), else
+// the full setup.
 void build_timed(cpr_handle *h, bool numeric = false) {
     double t0 = now_ms();
     if (numeric && h->nr_ready) numeric_refresh(h);
-    else build_preconditioner(h, numeric);
+    else build_preconditioner(h);
     h->setup_ms = now_ms() - t0;
     h->setup_count++;
     h->setup_called = 1;

@@ -371,9 +371,9 @@ void prof_collect_graph(cpr_handle *h, int which);
 void destroy_step_graphs(cpr_handle *h);
 
 // setup.cu
-// numeric: keep the last setup's discrete structure (levels, strength sets,
-// C/F splits, colorings, BILU(0) ordering) and recompute every value from A.
-void build_preconditioner(cpr_handle *h, bool numeric = false);
+// The full setup of B from the handle's current A; with resetup = 1 it also
+// keeps what numeric_refresh needs.
+void build_preconditioner(cpr_handle *h);
 void free_preconditioner(cpr_handle *h);
 // resetup = 1 with an unchanged pattern: every value of B recomputed from the
 // current A in place (the structure of the last full setup kept), replayed as

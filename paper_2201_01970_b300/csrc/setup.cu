@@ -3293,43 +3293,9 @@ class SideWorker {
 
 
 // Build B from the handle's current A (Sec. 3.1; the setup steps of Alg. 6 per level).
-void build_preconditioner(cpr_handle *h, bool numeric) {
-    // resetup = 1: the discrete structure of the last setup, set aside before
-    // everything else of it is released
-    struct KeptLevel {
-        DVec<int> Srow, Scol, cf, color, rows_by_color;
-        int Snnz = 0, nc = 0, ncolors = 0;
-        std::vector<int> color_off;
-    };
-    std::vector<KeptLevel> kept;
-    Bilu kept_b;
-    if (numeric) {
-        for (Level &L : h->lev) {
-            KeptLevel K;
-            K.Srow = std::move(L.Srow);
-            K.Scol = std::move(L.Scol);
-            K.Snnz = L.Snnz;
-            K.cf = std::move(L.cf);
-            K.nc = L.nc;
-            K.color = std::move(L.color);
-            K.rows_by_color = std::move(L.rows_by_color);
-            K.ncolors = L.ncolors;
-            K.color_off = std::move(L.color_off);
-            kept.push_back(std::move(K));
-        }
-        Bilu &B = h->bilu;
-        kept_b.color = std::move(B.color);
-        kept_b.ncolors = B.ncolors;
-        kept_b.color_off = std::move(B.color_off);
-        kept_b.rows_by_color = std::move(B.rows_by_color);
-        kept_b.iperm = std::move(B.iperm);
-        kept_b.Lrowptr = std::move(B.Lrowptr);
-        kept_b.Lcol = std::move(B.Lcol);
-        kept_b.Urowptr = std::move(B.Urowptr);
-        kept_b.Ucol = std::move(B.Ucol);
-    }
+void build_preconditioner(cpr_handle *h) {
     free_preconditioner(h);
-    Nvtx nv(numeric ? "numeric resetup" : "setup");
+    Nvtx nv("setup");
     cudaStream_t s = h->stream;
     PhaseClock clk;
     clk.start(s);
@@ -3371,54 +3337,40 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
     clk.mark("decouple");
     // ---- second stage: multicolor BILU(0), on the side worker ----
     SideWorker side(h, &clk);
-    side.post([h, nb, nnzb, f32, &bdiag, &side, numeric, &kept_b](cudaStream_t s) {
+    side.post([h, nb, nnzb, f32, &bdiag, &side](cudaStream_t s) {
         Nvtx r("BILU(0) setup");
         Bilu &B = h->bilu;
         int nl = 0, nu = 0;
-        if (numeric) {   // the kept ordering and L/U patterns
-            B.color = std::move(kept_b.color);
-            B.ncolors = kept_b.ncolors;
-            B.color_off = std::move(kept_b.color_off);
-            B.rows_by_color = std::move(kept_b.rows_by_color);
-            B.iperm = std::move(kept_b.iperm);
-            B.Lrowptr = std::move(kept_b.Lrowptr);
-            B.Lcol = std::move(kept_b.Lcol);
-            B.Urowptr = std::move(kept_b.Urowptr);
-            B.Ucol = std::move(kept_b.Ucol);
-            nl = (int)B.Lcol.n;
-            nu = (int)B.Ucol.n;
-        } else {
-            // every row holds exactly one diagonal block: nnzb - nb entries
-            SymGraph G = sym_graph(build_pattern_ub(nb, (long)nnzb - nb, s, [&](const int *srow, int *out) {
-                                       k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p,
-                                                                                                h->col.p, srow, out);
-                                       CK_LAUNCH();
-                                   }),
-                                   (long)nnzb - nb, s);
-            side.mark("bilu_graph");
-            // multicolor (JP at theta = 0), or the natural order's level sets
-            B.ncolors = h->opt.bilu_order ? level_sets(G, B.color, s) : jp_color(h, G, 2, 0, B.color, s);
-            side.mark("bilu_jp");
-            rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
-            B.iperm.alloc(nb, s);
-            k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
-            CK_LAUNCH();
-            DVec<int> lcnt, ucnt;
-            lcnt.alloc(nb, s);
-            ucnt.alloc(nb, s);
-            k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
-                                                                      B.color.p, lcnt.p, ucnt.p);
-            CK_LAUNCH();
-            B.Lrowptr.alloc(nb + 1, s);
-            B.Urowptr.alloc(nb + 1, s);
-            exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
-            exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
-            nl = read_int(B.Lrowptr.p + nb, s);
-            nu = read_int(B.Urowptr.p + nb, s);
-            B.Lcol.alloc(std::max(nl, 1), s);
-            B.Ucol.alloc(std::max(nu, 1), s);
-            side.mark("bilu_order");
-        }
+        // every row holds exactly one diagonal block: nnzb - nb entries
+        SymGraph G = sym_graph(build_pattern_ub(nb, (long)nnzb - nb, s, [&](const int *srow, int *out) {
+                                   k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p,
+                                                                                            h->col.p, srow, out);
+                                   CK_LAUNCH();
+                               }),
+                               (long)nnzb - nb, s);
+        side.mark("bilu_graph");
+        // multicolor (JP at theta = 0), or the natural order's level sets
+        B.ncolors = h->opt.bilu_order ? level_sets(G, B.color, s) : jp_color(h, G, 2, 0, B.color, s);
+        side.mark("bilu_jp");
+        rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
+        B.iperm.alloc(nb, s);
+        k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
+        CK_LAUNCH();
+        DVec<int> lcnt, ucnt;
+        lcnt.alloc(nb, s);
+        ucnt.alloc(nb, s);
+        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
+                                                                  B.color.p, lcnt.p, ucnt.p);
+        CK_LAUNCH();
+        B.Lrowptr.alloc(nb + 1, s);
+        B.Urowptr.alloc(nb + 1, s);
+        exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
+        exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
+        nl = read_int(B.Lrowptr.p + nb, s);
+        nu = read_int(B.Urowptr.p + nb, s);
+        B.Lcol.alloc(std::max(nl, 1), s);
+        B.Ucol.alloc(std::max(nu, 1), s);
+        side.mark("bilu_order");
         if (f32) {
             B.lu32.alloc(9 * (size_t)nnzb, s);
             B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
@@ -3457,7 +3409,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             k_check_diag<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.dpos.p, L.A.val.p, nullptr, h->err.p);
             CK_LAUNCH();   // a zero diagonal is reported by the check at the end of the setup
         }
-        if (numeric ? l + 1 >= (int)kept.size() : (n <= o.coarse_max || l + 1 >= o.max_levels)) break;
+        if (n <= o.coarse_max || l + 1 >= o.max_levels) break;
         Level &L = h->lev[l];
         clk.mark("diag");
         Graph S;
@@ -3465,35 +3417,12 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         int nc = 0;
         bool ua = o.amg == 1;
         if (ua) {   // UA-AMG (Sec. 6): cf holds every node's aggregate
-            if (numeric) {
-                KeptLevel &K = kept[l];
-                if (K.cf.n != (size_t)n || K.rows_by_color.n != (size_t)n)
-                    fail(CPR_ERR_INVALID, "numeric resetup: the kept hierarchy does not fit A");
-                L.cf = std::move(K.cf);
-                nc = K.nc;
-            } else {
-                nc = aggregate_double(L.A, o.theta_amg, hash_base(o.seed, 3, l), L.cf, s);
-                clk.mark("aggregate");
-                if (nc == 0 || (double)nc > 0.95 * (double)n) {
-                    L.cf.release();
-                    break;
-                }
+            nc = aggregate_double(L.A, o.theta_amg, hash_base(o.seed, 3, l), L.cf, s);
+            clk.mark("aggregate");
+            if (nc == 0 || (double)nc > 0.95 * (double)n) {
+                L.cf.release();
+                break;
             }
-        } else if (numeric) {   // the kept strength set and C/F split; coarse indices from it
-            KeptLevel &K = kept[l];
-            if (K.cf.n != (size_t)n || K.rows_by_color.n != (size_t)n)
-                fail(CPR_ERR_INVALID, "numeric resetup: the kept hierarchy does not fit A");
-            S.n = n;
-            S.nnz = K.Snnz;
-            S.rowptr = std::move(K.Srow);
-            S.col = std::move(K.Scol);
-            L.cf = std::move(K.cf);
-            nc = K.nc;
-            flag.alloc(n, s);
-            cidx.alloc(n + 1, s);
-            k_is_c<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.cf.p, flag.p);
-            CK_LAUNCH();
-            exclusive_scan(flag.p, cidx.p, n, s);
         } else {
             // classical strength and PMIS
             bool long_rows = L.A.nnz > 16L * n;   // warp per row pays once rows average over 16 entries
@@ -3553,38 +3482,28 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
         // the smoother's coloring of this level (Eq. 5.1 strength, symmetrised,
         // JP), on the side worker: it needs only A_l, and
         // level l is smoothed now that it is not the coarsest
-        if (numeric) {   // the kept coloring
-            KeptLevel &K = kept[l];
-            L.color = std::move(K.color);
-            L.rows_by_color = std::move(K.rows_by_color);
-            L.ncolors = K.ncolors;
-            L.color_off = std::move(K.color_off);
+        side.post([h, l, n, &side](cudaStream_t s) {
+            Nvtx r("level coloring");
+            side.mark("idle");
+            Level &L = h->lev[l];
+            // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
+            long ub = L.A.nnz;
+            SymGraph G = sym_graph(build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
+                                       k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(
+                                           n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out);
+                                       CK_LAUNCH();
+                                   }),
+                                   ub, s);
+            side.mark("c_graph");
+            // the paper's Alg. 4-5 on small levels (coloring = 1), else JP
+            if (h->opt.coloring == 1 && n <= h->opt.coloring_rows) L.ncolors = vertices_grouping(h, G.S, L.color, s);
+            else L.ncolors = jp_color(h, G, 0, l, L.color, s);
+            side.mark("c_jp");
+            rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
             CK(cudaEventRecord(h->ev_color[l], s));
+            side.mark("c_order");
             side.finished(l);
-        } else {
-            side.post([h, l, n, &side](cudaStream_t s) {
-                Nvtx r("level coloring");
-                side.mark("idle");
-                Level &L = h->lev[l];
-                // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
-                long ub = L.A.nnz;
-                SymGraph G = sym_graph(build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
-                                           k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(
-                                               n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out);
-                                           CK_LAUNCH();
-                                       }),
-                                       ub, s);
-                side.mark("c_graph");
-                // the paper's Alg. 4-5 on small levels (coloring = 1), else JP
-                if (h->opt.coloring == 1 && n <= h->opt.coloring_rows) L.ncolors = vertices_grouping(h, G.S, L.color, s);
-                else L.ncolors = jp_color(h, G, 0, l, L.color, s);
-                side.mark("c_jp");
-                rows_by_color(n, L.color.p, L.ncolors, L.color_off, L.rows_by_color, s);
-                CK(cudaEventRecord(h->ev_color[l], s));
-                side.mark("c_order");
-                side.finished(l);
-            });
-        }
+        });
         if (ua) {   // unsmoothed aggregation: unit rows, R = P^T
             unit_p(n, nc, L.cf.p, L.P, s);
             L.R.n = nc;
@@ -3609,7 +3528,7 @@ void build_preconditioner(cpr_handle *h, bool numeric) {
             L.R.nnz = L.P.nnz;
             transpose(n, nc, L.P.nnz, L.P.rowptr.p, L.P.col.p, L.P.val.p, L.R.rowptr, L.R.col, &L.R.val, s);
         }
-        // the strength set and coarse indices stay with the level for a numeric-only resetup
+        // the strength set and coarse indices stay with the level (the numeric refresh reads them)
         L.Srow = std::move(S.rowptr);
         L.Scol = std::move(S.col);
         L.Snnz = S.nnz;
