@@ -105,7 +105,11 @@ typedef struct {
                            number of levels, classical strength sets, C/F splits, smoother
                            colorings and BILU(0) ordering are kept, and every value (weights,
                            A_P, interpolation, Galerkin products, coarse LU, BILU(0) factors)
-                           is recomputed from A^(k).  Not in the paper. */
+                           is recomputed from A^(k).  The recomputation writes into the
+                           buffers of the last full setup and is replayed as one CUDA graph
+                           (captured on the first such rebuild, which also builds the
+                           Galerkin products' lists); the handle then holds each level's
+                           A P and those lists besides B.  Not in the paper. */
     int amg;            /* first stage's AMG.  0 (default): classical -- strength, PMIS C/F split,
                            direct interpolation, R A P -- with a V(pre,post) cycle.  1: the paper's
                            own first stage (Sec. 6): unsmoothed aggregation by double pairwise
