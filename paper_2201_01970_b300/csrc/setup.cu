@@ -458,12 +458,14 @@ struct JpGraph {
 // (degree, hash, index) beats every neighbour uncolored at the start of the
 // round takes the smallest color not held by a neighbour colored in an
 // earlier round.  state packs (round << 32 | color) into one 64-bit word,
-// written in one store.  Returns the color taken, or -1.
+// written in one store.  Returns the color taken, or -1.  A state written in
+// this round reads as uncolored whether or not the store is seen yet, so
+// the loads need no volatile and may hit L1.
 __device__ int jp_vertex(int i, const JpGraph &g, uint32_t hbase, unsigned long long *state, unsigned r) {
     if (state[i] != kUncolored) return -1;
     int di = g.deg[i];
     uint32_t hi = fmix32((uint32_t)i ^ hbase);
-    volatile unsigned long long *vs = state;
+    const unsigned long long *vs = state;
     for (int pass = 0; pass < 2; pass++) {
         const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
         for (int p = R[i]; p < R[i + 1]; p++) {
@@ -883,17 +885,17 @@ __device__ int pmis_select(int i, const int *sr, const int *sc, const int *tr, c
 }
 
 // Selected points become C; undecided points with a C point in S_i become F.
-// Returns 1 if point i was decided in this call.
+// Returns 1 if point i was decided in this call.  A point made C in this
+// pass is also selected, so cf needs no volatile read.
 __device__ int pmis_commit(int i, const int *sr, const int *sc, int *cf, const int *sel) {
     if (sel[i]) {
         cf[i] = 1;
         return 1;
     }
     if (cf[i] != -1) return 0;
-    volatile int *vcf = cf;
     for (int p = sr[i]; p < sr[i + 1]; p++) {
         int j = sc[p];
-        if (sel[j] || vcf[j] == 1) {
+        if (sel[j] || cf[j] == 1) {
             cf[i] = 0;
             return 1;
         }
@@ -1774,6 +1776,92 @@ __global__ void __launch_bounds__(WARPS * 32) k_spgemm_rowfill(int n, const int 
     for (int w = blockIdx.x * WARPS + wl; w < nn; w += gridDim.x * WARPS) {
         spgemm_fill_row<CAP, HMAX, SKIP>(rows ? rows[w] : w, ar, ac, av, br, bc, bv, cr, cc, cv, tab[wl], keys[wl],
                                          acc[wl], &cnt[wl], pcs[wl], lane);
+        __syncwarp();
+    }
+}
+
+// C = A B for products with few columns (B.ncol <= kDenseCols): one warp per
+// row of C with a dense accumulator of B.ncol values and a bitmap of the
+// columns present, both in shared memory.  The row's products are taken in
+// (A entry, B entry) order, one per lane, and the lanes add them in
+// ascending A entry (ascending k) order, as the table tiers do, so every C
+// entry is summed in Gustavson's order; the columns leave in ascending order
+// from the bitmap.  Count pass (FILL false: ucnt = distinct columns) or fill
+// pass.  The accumulator is zero between rows: a row's extraction clears
+// what it used.  Dynamic shared memory: kDenseWarps * (ncol doubles when
+// FILL, then ceil(ncol / 32) words).
+constexpr int kDenseCols = 4096;
+constexpr int kDenseWarps = 4;
+template <bool FILL>
+__global__ void __launch_bounds__(kDenseWarps * 32) k_spgemm_dense(int n, int ncol, const int *ar, const int *ac,
+                                                                   const double *av, const int *br, const int *bc,
+                                                                   const double *bv, const int *cr, int *cc,
+                                                                   double *cv, int *ucnt) {
+    extern __shared__ double dsm[];
+    __shared__ ProdChunk pcs[kDenseWarps];
+    int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    int nw = (ncol + 31) / 32;
+    size_t per_warp = (FILL ? (size_t)ncol * sizeof(double) : 0) + (size_t)nw * sizeof(unsigned);
+    per_warp = (per_warp + 15) & ~(size_t)15;
+    char *base = reinterpret_cast<char *>(dsm) + wl * per_warp;
+    double *acc = reinterpret_cast<double *>(base);
+    unsigned *bits = reinterpret_cast<unsigned *>(base + (FILL ? (size_t)ncol * sizeof(double) : 0));
+    if (FILL)
+        for (int t = lane; t < ncol; t += 32) acc[t] = 0.0;
+    for (int t = lane; t < nw; t += 32) bits[t] = 0u;
+    __syncwarp();
+    ProdChunk &pc = pcs[wl];
+    for (int i = blockIdx.x * kDenseWarps + wl; i < n; i += gridDim.x * kDenseWarps) {
+        int a = ar[i], b = ar[i + 1];
+        for (int a0 = a; a0 < b; a0 += 32) {
+            int tot = load_chunk(a0, b, ac, FILL ? av : nullptr, br, pc, lane);
+            for (int t0 = 0; t0 < tot; t0 += 32) {
+                int t = t0 + lane;
+                int e = 32, J = 0;
+                double prod = 0.0;
+                if (t < tot) {
+                    e = chunk_owner(pc, t);
+                    int q = pc.st[e] + t - pc.off[e];
+                    J = bc[q];
+                    atomicOr(&bits[J >> 5], 1u << (J & 31));
+                    if (FILL) prod = __dmul_rn(pc.av[e], bv[q]);
+                }
+                if (FILL) {
+                    int e_first = __shfl_sync(0xffffffffu, e, 0);
+                    int e_last = __shfl_sync(0xffffffffu, e, min(31, tot - 1 - t0));
+                    for (int ee = e_first; ee <= e_last; ee++) {   // a B row holds each column once
+                        if (e == ee) acc[J] = __dadd_rn(acc[J], prod);
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // the row's columns in ascending order: words across the lanes, a warp scan of their counts
+        int o = FILL ? cr[i] : 0, total = 0;
+        for (int w0 = 0; w0 < nw; w0 += 32) {
+            int w = w0 + lane;
+            unsigned word = w < nw ? bits[w] : 0u;
+            int c = __popc(word), inc = c;
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, inc, sh);
+                if (lane >= sh) inc += y;
+            }
+            if (FILL) {
+                int q = o + total + inc - c;
+                while (word) {
+                    int J = (w << 5) + __ffs(word) - 1;
+                    word &= word - 1;
+                    cc[q] = J;
+                    cv[q] = acc[J];
+                    acc[J] = 0.0;
+                    q++;
+                }
+            }
+            if (w < nw) bits[w] = 0u;
+            total += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (!FILL && lane == 0) ucnt[i] = total;
         __syncwarp();
     }
 }
@@ -2673,9 +2761,46 @@ void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, 
 // B sorted).  Each row belongs to exactly one tier (spgemm_tier) and is
 // written by exactly one launch: the three per-thread tiers over all rows,
 // the table tiers over their lists.
+size_t dense_smem(int ncol, bool fill) {
+    size_t per_warp = (fill ? (size_t)ncol * sizeof(double) : 0) + (size_t)((ncol + 31) / 32) * sizeof(unsigned);
+    return kDenseWarps * ((per_warp + 15) & ~(size_t)15);
+}
+
+// C = A B with the dense-accumulator kernel (B.ncol <= kDenseCols): a count
+// pass, a scan, one read-back of the size, a fill pass.
+void spgemm_dense(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
+    int n = A.n, ncol = B.ncol;
+    static std::once_flag attr;   // the same ceiling for every handle and thread
+    std::call_once(attr, [] {
+        CK(cudaFuncSetAttribute(k_spgemm_dense<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dense_smem(kDenseCols, true)));
+    });
+    DVec<int> ucnt;
+    ucnt.alloc(std::max(n, 1), s);
+    unsigned blocks = (unsigned)grid_for(std::max(n, 1), kDenseWarps, 148 * 8);
+    k_spgemm_dense<false><<<blocks, kDenseWarps * 32, dense_smem(ncol, false), s>>>(
+        n, ncol, A.rowptr.p, A.col.p, nullptr, B.rowptr.p, B.col.p, nullptr, nullptr, nullptr, nullptr, ucnt.p);
+    CK_LAUNCH();
+    C.n = n;
+    C.ncol = ncol;
+    C.rowptr.alloc(n + 1, s);
+    exclusive_scan(ucnt.p, C.rowptr.p, n, s);
+    C.nnz = read_int(C.rowptr.p + n, s);
+    if (C.nnz < 0) fail(CPR_ERR_OOM, "Galerkin product too large");
+    C.col.alloc(std::max(C.nnz, 1), s);
+    C.val.alloc(std::max(C.nnz, 1), s);
+    k_spgemm_dense<true><<<blocks, kDenseWarps * 32, dense_smem(ncol, true), s>>>(
+        n, ncol, A.rowptr.p, A.col.p, A.val.p, B.rowptr.p, B.col.p, B.val.p, C.rowptr.p, C.col.p, C.val.p, nullptr);
+    CK_LAUNCH();
+}
+
 void spgemm(const DCsr &A, const DCsr &B, DCsr &C, cudaStream_t s) {
     constexpr int kSW = 16, kMW = 8, kBW = 4;   // warps per block: small, medium and large tables
     int n = A.n;
+    if (B.ncol <= kDenseCols) {   // few columns: a dense accumulator per row
+        spgemm_dense(A, B, C, s);
+        return;
+    }
     DVec<int> ucnt, small, mid, big, cnts;
     ucnt.alloc(std::max(n, 1), s);
     small.alloc(std::max(n, 1), s);
