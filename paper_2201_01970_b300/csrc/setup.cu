@@ -2536,9 +2536,10 @@ Graph build_pattern_ub(int n, long ub, cudaStream_t s, CountFill cf) {
     return g;
 }
 
-// Transpose (pattern, or with values when val != nullptr); rows of the result sorted.
+// Transpose (pattern, or with values when val != nullptr); rows of the
+// result sorted, or (sorted false) in the order the scatter left them.
 void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, const double *val,
-               DVec<int> &trow, DVec<int> &tcol, DVec<double> *tval, cudaStream_t s) {
+               DVec<int> &trow, DVec<int> &tcol, DVec<double> *tval, cudaStream_t s, bool sorted = true) {
     DVec<int> cnt, cursor;
     cnt.alloc(std::max(ncol, 1), s);
     cnt.zero();
@@ -2555,7 +2556,7 @@ void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, cons
     k_scatter_t<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, rowptr, col, val, cursor.p, tcol.p,
                                                       tval ? tval->p : nullptr);
     CK_LAUNCH();
-    if (ncol) {
+    if (ncol && sorted) {
         DVec<int> longrows, nlong;
         longrows.alloc(ncol, s);
         nlong.alloc(1, s);
@@ -3562,7 +3563,8 @@ void build_preconditioner(cpr_handle *h) {
             });
             clk.mark("strength");
             DVec<int> trow, tcol;
-            transpose(n, n, S.nnz, S.rowptr.p, S.col.p, nullptr, trow, tcol, nullptr, s);
+            // PMIS reads S^T's rows as sets (|S^T_i| and all-neighbour tests): left unsorted
+            transpose(n, n, S.nnz, S.rowptr.p, S.col.p, nullptr, trow, tcol, nullptr, s, false);
             clk.mark("st");
             L.cf.alloc(n, s);
             DVec<int> sel, und;
