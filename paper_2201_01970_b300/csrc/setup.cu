@@ -188,16 +188,24 @@ __device__ __forceinline__ bool nan_bits(long long u) { return (u & kMagBits) > 
 
 // Eq. 5.1: j in S_i iff j != i and |a_ij| > theta * sum_k |a_ik| (the sum in
 // row order over the whole row).  srowptr == nullptr: count pass (out =
-// counts); otherwise fill pass (out = columns).
+// counts), which also leaves each row's threshold in thr; otherwise fill
+// pass (out = columns), which reads it back instead of summing again.
 __global__ void k_strength51(int n, const int *rowptr, const int *col, const double *val,
-                             double theta, const int *srowptr, int *out) {
+                             double theta, const int *srowptr, int *out, double *thr) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int a = rowptr[i], b = rowptr[i + 1];
     const long long *vb = reinterpret_cast<const long long *>(val);
-    double rowsum = 0.0;
-    for (int p = a; p < b; p++) rowsum = __dadd_rn(rowsum, __longlong_as_double(vb[p] & kMagBits));
-    long long tb = __double_as_longlong(__dmul_rn(theta, rowsum));
+    long long tb;
+    if (srowptr) {
+        tb = __double_as_longlong(thr[i]);
+    } else {
+        double rowsum = 0.0;
+        for (int p = a; p < b; p++) rowsum = __dadd_rn(rowsum, __longlong_as_double(vb[p] & kMagBits));
+        double t = __dmul_rn(theta, rowsum);
+        thr[i] = t;
+        tb = __double_as_longlong(t);
+    }
     int q = srowptr ? srowptr[i] : 0, c = 0;
     if (!nan_bits(tb)) {
         long long tk = ord_key(tb);
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kSortWarps * 32) k_sort_long_rows(const int *l
 
 constexpr unsigned long long kUncolored = ~0ull;
 constexpr int kSmallLevel = 4096;    // levels up to this size run their rounds in one CTA
-constexpr int kJpBatch = 8;          // JP rounds launched per host check of the remaining count
+constexpr int kJpBatch = 16;         // JP rounds launched per host check of the remaining count
 constexpr int kPmisBatch = 6;        // PMIS rounds launched per host check of the undecided count
 
 // The symmetric graph G = S u S^T that JP colors, held as two disjoint
@@ -3615,9 +3623,12 @@ void build_preconditioner(cpr_handle *h) {
             Level &L = h->lev[l];
             // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
             long ub = L.A.nnz;
+            DVec<double> thr;   // each row's threshold, from the count pass to the fill pass
+            thr.alloc(std::max(n, 1), s);
             SymGraph G = sym_graph(build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
                                        k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(
-                                           n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out);
+                                           n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out,
+                                           thr.p);
                                        CK_LAUNCH();
                                    }),
                                    ub, s);
