@@ -466,27 +466,50 @@ struct JpGraph {
 // (degree, hash, index) beats every neighbour uncolored at the start of the
 // round takes the smallest color not held by a neighbour colored in an
 // earlier round.  state packs (round << 32 | color) into one 64-bit word,
-// written in one store.  Returns the color taken, or -1.  A state written in
-// this round reads as uncolored whether or not the store is seen yet, so
-// the loads need no volatile and may hit L1.
-__device__ int jp_vertex(int i, const JpGraph &g, uint32_t hbase, unsigned long long *state, unsigned r) {
-    if (state[i] != kUncolored) return -1;
-    int di = g.deg[i];
-    uint32_t hi = fmix32((uint32_t)i ^ hbase);
-    const unsigned long long *vs = state;
-    for (int pass = 0; pass < 2; pass++) {
-        const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
-        for (int p = R[i]; p < R[i + 1]; p++) {
-            int j = C[p];
-            if (j == i) continue;
-            unsigned long long sj = vs[j];
-            bool unc = sj == kUncolored || (unsigned)(sj >> 32) == r;
-            if (!unc) continue;
-            if (!key_greater(di, hi, i, g.deg[j], fmix32((uint32_t)j ^ hbase), j)) return -1;
-        }
+// written in one store.  A state written in this round reads as uncolored
+// whether or not the store is seen yet, so the loads need no volatile and
+// may hit L1.
+//
+// G lanes share the vertex: lane l takes entries l, l + G, ... of the
+// concatenation of S_i and T_i, P at a time, loading all their columns,
+// then all their states and degrees, before comparing.  A vertex thus waits
+// on about deg / (G P) dependent load pairs instead of one pair per
+// neighbour.  The lanes' verdicts are AND-ed and their masks of the colors
+// below 64 held by earlier-colored neighbours OR-ed; a vertex whose
+// neighbours hold all of them searches on from 64 on lane 0.  The outcome
+// is the one of a neighbour-by-neighbour walk.  Every lane of the warp calls
+// this (act false for an empty slot); the result is valid on the group's
+// lane 0, which also writes the state.
+constexpr int kJpPre = 4;      // entries per lane and batch in the multi-CTA rounds
+constexpr int kJpPreSmall = 8; // in the one-CTA kernels, whose few lanes each walk many entries
+
+template <int G>
+__device__ __forceinline__ bool group_all(bool v) {
+    unsigned x = v ? 1u : 0u;
+    for (int o = G >> 1; o > 0; o >>= 1) x &= __shfl_xor_sync(0xffffffffu, x, o, G);
+    return x != 0;
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool v) {
+    unsigned x = v ? 1u : 0u;
+    for (int o = G >> 1; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o, G);
+    return x != 0;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned long long group_or64(unsigned long long v) {
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, o, G);
+        unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), o, G);
+        v |= ((unsigned long long)hi << 32) | lo;
     }
-    int c = 0;
-    for (int base = 0;; base += 64) {
+    return v;
+}
+
+// The smallest color >= 64 not held by a neighbour of i colored before round r.
+__device__ int jp_color_from64(int i, const JpGraph &g, const unsigned long long *vs, unsigned r) {
+    for (int base = 64;; base += 64) {
         unsigned long long mask = 0;
         for (int pass = 0; pass < 2; pass++) {
             const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
@@ -497,12 +520,61 @@ __device__ int jp_vertex(int i, const JpGraph &g, uint32_t hbase, unsigned long 
                 if (cj >= base && cj < base + 64) mask |= 1ull << (cj - base);
             }
         }
-        if (mask != ~0ull) {
-            c = base + __ffsll((long long)~mask) - 1;
-            break;
+        if (mask != ~0ull) return base + __ffsll((long long)~mask) - 1;
+    }
+}
+
+template <int G, int P>
+__device__ int jp_vertex(int i, bool act, int lane, const JpGraph &g, uint32_t hbase, unsigned long long *state,
+                         unsigned r) {
+    const unsigned long long *vs = state;
+    bool cand = act && vs[i] == kUncolored;   // the same on every lane of the group
+    int di = 0, a0 = 0, na = 0, b0 = 0, nt = 0;
+    uint32_t hi = 0;
+    if (cand) {
+        di = g.deg[i];
+        hi = fmix32((uint32_t)i ^ hbase);
+        a0 = g.sr[i];
+        na = g.sr[i + 1] - a0;
+        b0 = g.tr[i];
+        nt = na + (g.tr[i + 1] - b0);
+    }
+    bool win = cand;
+    unsigned long long used = 0;   // colors below 64 of neighbours colored in earlier rounds
+    for (int q0 = 0; q0 < nt; q0 += G * P) {
+        int jj[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            int q = q0 + lane + u * G;
+            jj[u] = q < nt ? (q < na ? g.sc[a0 + q] : g.tc[b0 + q - na]) : -1;
+        }
+        unsigned long long sj[P];
+        int dj[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            sj[u] = jj[u] >= 0 ? vs[jj[u]] : 0ull;
+            dj[u] = jj[u] >= 0 ? g.deg[jj[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            int j = jj[u];
+            if (j < 0 || j == i) continue;
+            bool unc = sj[u] == kUncolored || (unsigned)(sj[u] >> 32) == r;
+            if (unc) {
+                if (!key_greater(di, hi, i, dj[u], fmix32((uint32_t)j ^ hbase), j)) win = false;
+            } else {
+                int cj = (int)(unsigned)sj[u];
+                if (cj < 64) used |= 1ull << cj;
+            }
         }
     }
-    state[i] = ((unsigned long long)r << 32) | (unsigned)c;
+    win = group_all<G>(win);
+    used = group_or64<G>(used);
+    int c = -1;
+    if (win && lane == 0) {
+        c = used != ~0ull ? __ffsll((long long)~used) - 1 : jp_color_from64(i, g, vs, r);
+        state[i] = ((unsigned long long)r << 32) | (unsigned)c;
+    }
     return c;
 }
 
@@ -538,36 +610,38 @@ __global__ void k_sym_degree(int n, const int *sr, const int *tr, int *deg) {
 }
 
 // One JP round over a worklist: the vertices still uncolored when the round
-// starts (round 0: all n, list_in == nullptr).  A vertex's decision depends
-// only on the states left by earlier rounds, so the order of the list does not
-// matter; the losers are appended to list_out (warp-aggregated).  Counts cycle
-// through three slots: this round reads cnt[r % 3], appends to cnt[(r+1) % 3]
-// (zeroed by the previous round) and zeroes cnt[(r+2) % 3] for the next one.
-// Rounds are launched in batches between host checks; once the list is empty
-// the rest of the batch returns at once.
+// starts (round 0: all n, list_in == nullptr), G lanes per vertex.  A
+// vertex's decision depends only on the states left by earlier rounds, so the
+// order of the list does not matter; the losers are appended to list_out
+// (warp-aggregated).  Counts cycle through three slots: this round reads
+// cnt[r % 3], appends to cnt[(r+1) % 3] (zeroed by the previous round) and
+// zeroes cnt[(r+2) % 3] for the next one.  Rounds are launched in batches
+// between host checks; once the list is empty the rest of the batch returns
+// at once.
+template <int G>
 __global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, JpGraph g, uint32_t hbase,
                            unsigned long long *state, unsigned r, int *maxcolor) {
     int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
     int *out_cnt = &cnt[(r + 1) % 3];
-    int lane = threadIdx.x & 31;
+    int lane32 = threadIdx.x & 31, lane = threadIdx.x % G;
+    int per = blockDim.x / G;
     int cmax = -1;
-    // t0 is uniform over the block, so whole warps run each pass together
-    for (int t0 = blockIdx.x * blockDim.x; t0 < m; t0 += gridDim.x * blockDim.x) {
-        int t = t0 + threadIdx.x, i = 0;
-        bool lost = false;
-        if (t < m) {
-            i = list_in ? list_in[t] : t;
-            int c = jp_vertex(i, g, hbase, state, r);
-            if (c >= 0) cmax = max(cmax, c);
-            else lost = true;
-        }
+    // v0 is uniform over the block, so whole warps run each pass together
+    for (long v0 = (long)blockIdx.x * per; v0 < m; v0 += (long)gridDim.x * per) {
+        long t = v0 + threadIdx.x / G;
+        bool act = t < m;
+        int i = act ? (list_in ? list_in[t] : (int)t) : 0;
+        int c = jp_vertex<G, kJpPre>(i, act, lane, g, hbase, state, r);
+        bool lead = act && lane == 0;
+        if (lead && c >= 0) cmax = max(cmax, c);
+        bool lost = lead && c < 0;
         unsigned b = __ballot_sync(0xffffffffu, lost);
         if (b) {
             int leader = __ffs(b) - 1, base = 0;
-            if (lane == leader) base = atomicAdd(out_cnt, __popc(b));
+            if (lane32 == leader) base = atomicAdd(out_cnt, __popc(b));
             base = __shfl_sync(0xffffffffu, base, leader);
-            if (lost) list_out[base + __popc(b & ((1u << lane) - 1u))] = i;
+            if (lost) list_out[base + __popc(b & ((1u << lane32) - 1u))] = i;
         }
     }
     if (cmax >= 0) atomicMax(maxcolor, cmax);
@@ -575,6 +649,7 @@ __global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, J
 
 // All JP rounds of a small graph in one CTA, rounds separated by barriers
 // (the same rounds as k_jp_round, without host round trips).
+template <int G>
 __global__ void __launch_bounds__(1024) k_jp_small(int n, JpGraph g, uint32_t hbase, unsigned long long *state,
                                                    int *maxcolor) {
     __shared__ int rem;
@@ -584,13 +659,15 @@ __global__ void __launch_bounds__(1024) k_jp_small(int n, JpGraph g, uint32_t hb
         mx = 0;
     }
     __syncthreads();
+    int lane = threadIdx.x % G, per = blockDim.x / G;
     for (unsigned r = 0; r < (unsigned)n + 8; r++) {
         int left = rem;
         __syncthreads();
         if (left == 0) break;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            int c = jp_vertex(i, g, hbase, state, r);
-            if (c >= 0) {
+        for (int v0 = 0; v0 < n; v0 += per) {   // uniform over the block
+            int i = v0 + (int)threadIdx.x / G;
+            int c = jp_vertex<G, kJpPreSmall>(i, i < n, lane, g, hbase, state, r);
+            if (i < n && lane == 0 && c >= 0) {
                 atomicSub(&rem, 1);
                 atomicMax(&mx, c);
             }
@@ -874,76 +951,154 @@ __global__ void k_pmis_init(int n, const int *sr, const int *tr, int *cf, int *u
 
 // An undecided point whose key (lambda = |S^T_i|, hash, index) beats every
 // undecided point of S_i u S^T_i is selected (cf is not written in this pass).
-__device__ int pmis_select(int i, const int *sr, const int *sc, const int *tr, const int *tc,
-                           uint32_t hbase, const int *cf) {
-    if (cf[i] != -1) return 0;
-    int li = tr[i + 1] - tr[i];
-    uint32_t hi = fmix32((uint32_t)i ^ hbase);
-    for (int pass = 0; pass < 2; pass++) {
-        const int *R = pass ? tr : sr;
-        const int *Cc = pass ? tc : sc;
-        for (int p = R[i]; p < R[i + 1]; p++) {
-            int j = Cc[p];
-            if (cf[j] != -1) continue;
-            int lj = tr[j + 1] - tr[j];
-            if (!key_greater(li, hi, i, lj, fmix32((uint32_t)j ^ hbase), j)) return 0;
+// G lanes share the point and load its entries P at a time, as in
+// jp_vertex; every lane of the warp calls this, and the verdict is the
+// group's.
+template <int G, int P>
+__device__ bool pmis_select(int i, bool act, int lane, const int *sr, const int *sc, const int *tr, const int *tc,
+                            uint32_t hbase, const int *cf) {
+    bool cand = act && cf[i] == -1;
+    int li = 0, a0 = 0, na = 0, b0 = 0, nt = 0;
+    uint32_t hi = 0;
+    if (cand) {
+        a0 = sr[i];
+        na = sr[i + 1] - a0;
+        b0 = tr[i];
+        li = tr[i + 1] - b0;
+        nt = na + li;
+        hi = fmix32((uint32_t)i ^ hbase);
+    }
+    bool win = cand;
+    for (int q0 = 0; q0 < nt; q0 += G * P) {
+        int jj[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            int q = q0 + lane + u * G;
+            jj[u] = q < nt ? (q < na ? sc[a0 + q] : tc[b0 + q - na]) : -1;
+        }
+        int cj[P], t0[P], t1[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            bool in = jj[u] >= 0;
+            cj[u] = in ? cf[jj[u]] : 0;
+            t0[u] = in ? tr[jj[u]] : 0;
+            t1[u] = in ? tr[jj[u] + 1] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            int j = jj[u];
+            if (j < 0 || cj[u] != -1) continue;
+            if (!key_greater(li, hi, i, t1[u] - t0[u], fmix32((uint32_t)j ^ hbase), j)) win = false;
         }
     }
-    return 1;
+    return group_all<G>(win);
 }
 
 // Selected points become C; undecided points with a C point in S_i become F.
-// Returns 1 if point i was decided in this call.  A point made C in this
-// pass is also selected, so cf needs no volatile read.
-__device__ int pmis_commit(int i, const int *sr, const int *sc, int *cf, const int *sel) {
-    if (sel[i]) {
-        cf[i] = 1;
-        return 1;
+// Returns, on the group's lane 0, whether point i was decided in this call.
+// A point made C in this pass is also selected, so cf needs no volatile
+// read.  Every lane of the warp calls this.
+template <int G, int P>
+__device__ bool pmis_commit(int i, bool act, int lane, const int *sr, const int *sc, int *cf, const int *sel) {
+    bool si = act && sel[i] != 0;
+    bool und = act && !si && cf[i] == -1;
+    int a0 = 0, na = 0;
+    if (und) {
+        a0 = sr[i];
+        na = sr[i + 1] - a0;
     }
-    if (cf[i] != -1) return 0;
-    for (int p = sr[i]; p < sr[i + 1]; p++) {
-        int j = sc[p];
-        if (sel[j] || cf[j] == 1) {
-            cf[i] = 0;
-            return 1;
+    bool found = false;
+    for (int q0 = 0; q0 < na; q0 += G * P) {
+        int jj[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            int q = q0 + lane + u * G;
+            jj[u] = q < na ? sc[a0 + q] : -1;
         }
+        int sj[P], cj[P];
+#pragma unroll
+        for (int u = 0; u < P; u++) {
+            bool in = jj[u] >= 0;
+            sj[u] = in ? sel[jj[u]] : 0;
+            cj[u] = in ? cf[jj[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < P; u++)
+            if (jj[u] >= 0 && (sj[u] || cj[u] == 1)) found = true;
     }
-    return 0;
+    found = group_any<G>(found);
+    if (lane != 0) return false;
+    if (si) {
+        cf[i] = 1;
+        return true;
+    }
+    if (und && found) {
+        cf[i] = 0;
+        return true;
+    }
+    return false;
+}
+
+// The undecided count as lane 0 of the warp reads it, given to every lane, so
+// that a warp returns early as a whole.
+__device__ __forceinline__ int warp_read(const int *p) {
+    int v = (threadIdx.x & 31) == 0 ? *(volatile const int *)p : 0;
+    return __shfl_sync(0xffffffffu, v, 0);
 }
 
 // Rounds are launched in batches between host checks.  Once every point is
 // decided the count is 0 and both kernels return at once.  The count reaches 0
 // only with the last decision, and a point with a decision pending still
-// counts itself, so no commit that is due is skipped.
+// counts itself, so no commit that is due is skipped.  G lanes per point.
+template <int G>
 __global__ void k_pmis_select(int n, const int *sr, const int *sc, const int *tr, const int *tc,
                               uint32_t hbase, const int *cf, int *sel, const int *undecided) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || *(volatile const int *)undecided == 0) return;
-    sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
+    if (warp_read(undecided) == 0) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    bool act = t < n;
+    int i = act ? (int)t : 0;
+    bool w = pmis_select<G, kJpPre>(i, act, lane, sr, sc, tr, tc, hbase, cf);
+    if (act && lane == 0) sel[i] = w ? 1 : 0;
 }
 
-__global__ void k_pmis_commit(int n, const int *sr, const int *sc, int *cf, const int *sel,
-                              int *undecided) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || *(volatile int *)undecided == 0) return;
-    if (pmis_commit(i, sr, sc, cf, sel)) atomicSub(undecided, 1);
+template <int G>
+__global__ void k_pmis_commit(int n, const int *sr, const int *sc, int *cf, const int *sel, int *undecided) {
+    if (warp_read(undecided) == 0) return;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    bool act = t < n;
+    int i = act ? (int)t : 0;
+    bool d = pmis_commit<G, kJpPre>(i, act, lane, sr, sc, cf, sel);
+    unsigned b = __ballot_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0 && b) atomicSub(undecided, __popc(b));
 }
 
 // All PMIS rounds of a small level in one CTA (the same rounds as above).
+template <int G>
 __global__ void __launch_bounds__(1024) k_pmis_small(int n, const int *sr, const int *sc, const int *tr,
                                                      const int *tc, uint32_t hbase, int *cf, int *sel,
                                                      const int *undecided0) {
     __shared__ int und;
     if (threadIdx.x == 0) und = *undecided0;
     __syncthreads();
+    int lane = threadIdx.x % G, per = blockDim.x / G;
     for (int round = 0; round < n + 8; round++) {
         int left = und;
         __syncthreads();
         if (left == 0) break;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sel[i] = pmis_select(i, sr, sc, tr, tc, hbase, cf);
+        for (int v0 = 0; v0 < n; v0 += per) {   // uniform over the block
+            int i = v0 + (int)threadIdx.x / G;
+            bool w = pmis_select<G, kJpPreSmall>(i, i < n, lane, sr, sc, tr, tc, hbase, cf);
+            if (i < n && lane == 0) sel[i] = w ? 1 : 0;
+        }
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x)
-            if (pmis_commit(i, sr, sc, cf, sel)) atomicSub(&und, 1);
+        for (int v0 = 0; v0 < n; v0 += per) {
+            int i = v0 + (int)threadIdx.x / G;
+            if (pmis_commit<G, kJpPreSmall>(i, i < n, lane, sr, sc, cf, sel)) atomicSub(&und, 1);
+        }
         __syncthreads();
     }
 }
@@ -2583,6 +2738,7 @@ void transpose(int n, int ncol, int nnz, const int *rowptr, const int *col, cons
 // nothing here reads the count back.
 struct SymGraph {
     int n = 0;
+    long ub = 0;   // bound of S's entry count (an average degree estimate for the lanes per vertex)
     Graph S;
     DVec<int> trow, tcol, deg;
     JpGraph dev() const { return JpGraph{S.rowptr.p, S.col.p, trow.p, tcol.p, deg.p}; }
@@ -2591,6 +2747,7 @@ struct SymGraph {
 SymGraph sym_graph(Graph &&S, long ub, cudaStream_t s) {
     SymGraph g;
     int n = g.n = S.n;
+    g.ub = ub;
     g.S = std::move(S);
     DVec<int> cnt, cursor;
     cnt.alloc(std::max(n, 1), s);
@@ -2620,9 +2777,24 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
     counters.alloc(4, s);
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
     uint32_t hb = hash_base(h->opt.seed, salt, level);
+    // lanes per vertex: about kJpPre of a typical row's entries per lane
+    int lanes = 1;
+    while (lanes < 16 && (long)lanes * kJpPre * n < G.ub) lanes <<= 1;
     if (n <= kSmallLevel) {
-        k_jp_small<<<1, 1024, 0, s>>>(n, G.dev(), hb, state.p, counters.p + 3);
-        CK_LAUNCH();
+        // one CTA: lanes only while every vertex still fits one pass of its 1024 threads
+        lanes = 1;
+        while (lanes < 8 && (long)2 * lanes * n <= 1024) lanes <<= 1;
+        auto small = [&](auto kern) {
+            kern<<<1, 1024, 0, s>>>(n, G.dev(), hb, state.p, counters.p + 3);
+            CK_LAUNCH();
+        };
+        switch (lanes) {
+        case 1: small(k_jp_small<1>); break;
+        case 2: small(k_jp_small<2>); break;
+        case 4: small(k_jp_small<4>); break;
+        case 8: small(k_jp_small<8>); break;
+        default: small(k_jp_small<16>); break;
+        }
         color.alloc(n, s);
         k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
         CK_LAUNCH();
@@ -2630,14 +2802,23 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
     }
     DVec<int> lists;   // two worklists, used alternately
     lists.alloc(2 * (size_t)n, s);
-    int grid = grid_for(n, kBlock, 148 * 8);
+    int grid = grid_for((long)n * lanes, kBlock, 148 * 8);
     unsigned r = 0;
+    auto round = [&](auto kern, const int *in, int *out) {
+        kern<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.dev(), hb, state.p, r, counters.p + 3);
+        CK_LAUNCH();
+    };
     for (;;) {
         for (int k = 0; k < kJpBatch; k++, r++) {
             const int *in = r == 0 ? nullptr : lists.p + (size_t)(r % 2) * n;
             int *out = lists.p + (size_t)((r + 1) % 2) * n;
-            k_jp_round<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.dev(), hb, state.p, r, counters.p + 3);
-            CK_LAUNCH();
+            switch (lanes) {
+            case 1: round(k_jp_round<1>, in, out); break;
+            case 2: round(k_jp_round<2>, in, out); break;
+            case 4: round(k_jp_round<4>, in, out); break;
+            case 8: round(k_jp_round<8>, in, out); break;
+            default: round(k_jp_round<16>, in, out); break;
+            }
         }
         if (read_int(counters.p + r % 3, s) == 0) break;
         if (r > (unsigned)n + 8) fail(CPR_ERR_CUDA, "coloring did not terminate");
@@ -3583,19 +3764,42 @@ void build_preconditioner(cpr_handle *h) {
             CK_LAUNCH();
             uint32_t hb = hash_base(o.seed, 1, l);
             int rounds = 0;
+            // lanes per point: about kJpPre of a typical |S_i| + |S^T_i| entries per lane
+            int lanes = 1;
+            while (lanes < 16 && (long)lanes * kJpPre * n < 2L * S.nnz) lanes <<= 1;
             if (n <= kSmallLevel) {
-                k_pmis_small<<<1, 1024, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, hb, L.cf.p, sel.p, und.p);
-                CK_LAUNCH();
+                // one CTA: lanes only while every point still fits one pass of its 1024 threads
+                lanes = 1;
+                while (lanes < 8 && (long)2 * lanes * n <= 1024) lanes <<= 1;
+                auto small = [&](auto kern) {
+                    kern<<<1, 1024, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, hb, L.cf.p, sel.p, und.p);
+                    CK_LAUNCH();
+                };
+                switch (lanes) {
+                case 1: small(k_pmis_small<1>); break;
+                case 2: small(k_pmis_small<2>); break;
+                case 4: small(k_pmis_small<4>); break;
+                case 8: small(k_pmis_small<8>); break;
+                default: small(k_pmis_small<16>); break;
+                }
             }
             if (n > kSmallLevel) {
+                unsigned grid = grid_for((long)n * lanes, kBlock);
+                auto round = [&](auto ksel, auto kcom) {
+                    ksel<<<grid, kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p, tcol.p, hb, L.cf.p, sel.p, und.p);
+                    CK_LAUNCH();
+                    kcom<<<grid, kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, L.cf.p, sel.p, und.p);
+                    CK_LAUNCH();
+                };
                 do {
                     for (int k = 0; k < kPmisBatch; k++, rounds++) {
-                        k_pmis_select<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, trow.p,
-                                                                            tcol.p, hb, L.cf.p, sel.p, und.p);
-                        CK_LAUNCH();
-                        k_pmis_commit<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, S.rowptr.p, S.col.p, L.cf.p,
-                                                                            sel.p, und.p);
-                        CK_LAUNCH();
+                        switch (lanes) {
+                        case 1: round(k_pmis_select<1>, k_pmis_commit<1>); break;
+                        case 2: round(k_pmis_select<2>, k_pmis_commit<2>); break;
+                        case 4: round(k_pmis_select<4>, k_pmis_commit<4>); break;
+                        case 8: round(k_pmis_select<8>, k_pmis_commit<8>); break;
+                        default: round(k_pmis_select<16>, k_pmis_commit<16>); break;
+                        }
                     }
                     if (rounds > n + 8) fail(CPR_ERR_CUDA, "C/F splitting did not terminate");
                 } while (read_int(und.p, s) > 0);
@@ -3608,6 +3812,7 @@ void build_preconditioner(cpr_handle *h) {
             CK_LAUNCH();
             exclusive_scan(flag.p, cidx.p, n, s);
             nc = read_int(cidx.p + n, s);
+            clk.mark("nc");
             if (nc == 0 || (double)nc > 0.95 * (double)n) {
                 L.cf.release();
                 break;
@@ -3625,13 +3830,13 @@ void build_preconditioner(cpr_handle *h) {
             long ub = L.A.nnz;
             DVec<double> thr;   // each row's threshold, from the count pass to the fill pass
             thr.alloc(std::max(n, 1), s);
-            SymGraph G = sym_graph(build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
-                                       k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(
-                                           n, L.A.rowptr.p, L.A.col.p, L.A.val.p, h->opt.theta_color, srow, out,
-                                           thr.p);
-                                       CK_LAUNCH();
-                                   }),
-                                   ub, s);
+            Graph S51 = build_pattern_ub(n, ub, s, [&](const int *srow, int *out) {
+                k_strength51<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, L.A.rowptr.p, L.A.col.p, L.A.val.p,
+                                                                   h->opt.theta_color, srow, out, thr.p);
+                CK_LAUNCH();
+            });
+            side.mark("c_str");
+            SymGraph G = sym_graph(std::move(S51), ub, s);
             side.mark("c_graph");
             // the paper's Alg. 4-5 on small levels (coloring = 1), else JP
             if (h->opt.coloring == 1 && n <= h->opt.coloring_rows) L.ncolors = vertices_grouping(h, G.S, L.color, s);
@@ -3658,9 +3863,11 @@ void build_preconditioner(cpr_handle *h) {
             L.P.rowptr.alloc(n + 1, s);
             exclusive_scan(cnt.p, L.P.rowptr.p, n, s);
             L.P.nnz = read_int(L.P.rowptr.p + n, s);
+            clk.mark("p_nnz");
             L.P.col.alloc(std::max(L.P.nnz, 1), s);
             L.P.val.alloc(std::max(L.P.nnz, 1), s);
             interp_fill(L.A, S.rowptr.p, S.col.p, L.cf.p, cidx.p, L.P, s);
+            clk.mark("p_fill");
             L.R.n = nc;
             L.R.ncol = n;
             L.R.nnz = L.P.nnz;
