@@ -481,6 +481,7 @@ struct JpGraph {
 // this (act false for an empty slot); the result is valid on the group's
 // lane 0, which also writes the state.
 constexpr int kJpPre = 4;      // entries per lane and batch in the multi-CTA rounds
+constexpr long kResidentThreads = 148L * 2048;   // threads resident at once on B300
 constexpr int kJpPreSmall = 8; // in the one-CTA kernels, whose few lanes each walk many entries
 
 template <int G>
@@ -2777,9 +2778,10 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
     counters.alloc(4, s);
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
     uint32_t hb = hash_base(h->opt.seed, salt, level);
-    // lanes per vertex: about kJpPre of a typical row's entries per lane
+    // lanes per vertex: about kJpPre of a typical row's entries per lane, as
+    // long as every vertex of the round still has its lanes resident at once
     int lanes = 1;
-    while (lanes < 16 && (long)lanes * kJpPre * n < G.ub) lanes <<= 1;
+    while (lanes < 16 && (long)lanes * kJpPre * n < G.ub && 2L * lanes * n <= kResidentThreads) lanes <<= 1;
     if (n <= kSmallLevel) {
         // one CTA: lanes only while every vertex still fits one pass of its 1024 threads
         lanes = 1;
@@ -3764,9 +3766,11 @@ void build_preconditioner(cpr_handle *h) {
             CK_LAUNCH();
             uint32_t hb = hash_base(o.seed, 1, l);
             int rounds = 0;
-            // lanes per point: about kJpPre of a typical |S_i| + |S^T_i| entries per lane
+            // lanes per point: about kJpPre of a typical |S_i| + |S^T_i| entries per
+            // lane, as long as every point still has its lanes resident at once
             int lanes = 1;
-            while (lanes < 16 && (long)lanes * kJpPre * n < 2L * S.nnz) lanes <<= 1;
+            while (lanes < 16 && (long)lanes * kJpPre * n < 2L * S.nnz && 2L * lanes * n <= kResidentThreads)
+                lanes <<= 1;
             if (n <= kSmallLevel) {
                 // one CTA: lanes only while every point still fits one pass of its 1024 threads
                 lanes = 1;
