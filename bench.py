@@ -276,21 +276,29 @@ def theta_sweep(cpr, torch, J, stream, thetas=(0.0, 0.05, 0.1, 0.2, 0.3, 0.5)):
     return {"workload": f"{WORKLOAD}, FP32 preconditioner, rtol {RTOL}", "rows": out}
 
 
-def setup_profile(cpr, torch, J, stream, warm=4):
-    """Setup alone (FP32 mode): `warm` setups, then one more bracketed by
-    cudaProfilerStart/Stop (ncu --profile-from-start off) and recorded by the
-    setup's phase clock (CPR_SETUP_TIMING: per mark, host and device ms)."""
+def setup_profile(cpr, torch, seq, stream, warm=8):
+    """Setup alone (FP32 mode) as the timed step runs it: one handle with
+    mu = 0, so that every cpr_update of the drifting sequence is a full setup;
+    `warm` updates timed on the host (synchronised), then one more bracketed
+    by cudaProfilerStart/Stop (ncu --profile-from-start off) and recorded by
+    the setup's phase clock (CPR_SETUP_TIMING: per mark, host and device ms;
+    the marks add their own event records, so that setup runs longer)."""
     class DJ:
-        nb = J.nb
-        rowptr = torch.from_numpy(J.rowptr).cuda()
-        col = torch.from_numpy(J.col).cuda()
-        val = torch.from_numpy(J.val).cuda()
+        def __init__(self, J):
+            self.nb = J.nb
+            self.rowptr = torch.from_numpy(J.rowptr).cuda()
+            self.col = torch.from_numpy(J.col).cuda()
+            self.val = torch.from_numpy(J.val).cuda()
 
+    dev = [DJ(J) for J in seq]
+    solver = cpr.Solver(dev[0], precond_fp32=1, mu=0, stream=stream.cuda_stream)
     walls = []
-    for _ in range(warm):
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    for k in range(warm):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        cpr.Solver(DJ, precond_fp32=1, stream=stream.cuda_stream).close()
+        solver.update(dev[(k + 1) % len(dev)])
         torch.cuda.synchronize()
         walls.append((time.perf_counter() - t) * 1e3)
     os.environ["CPR_SETUP_TIMING"] = "1"
@@ -298,15 +306,18 @@ def setup_profile(cpr, torch, J, stream, warm=4):
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     t = time.perf_counter()
-    solver = cpr.Solver(DJ, precond_fp32=1, stream=stream.cuda_stream)
+    solver.update(dev[(warm + 1) % len(dev)])
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t) * 1e3
     torch.cuda.profiler.stop()
     del os.environ["CPR_SETUP_TIMING"]
     launches = cpr.launch_count() - launches0
+    clocks = clk.stop()
     solver.close()
-    return {"workload": f"{WORKLOAD} FP32-mode setup", "warm_wall_ms": walls, "profiled_wall_ms": wall,
-            "launches": launches}
+    return {"workload": f"{WORKLOAD} FP32-mode setup through cpr_update (mu = 0)", "clocks": clocks,
+            "warm_wall_ms": walls,
+            "warm_wall_ms_median": statistics.median(walls[len(walls) // 2:]),
+            "profiled_wall_ms": wall, "launches": launches}
 
 
 def resetup_profile(cpr, torch, seq, stream, updates=4):
@@ -906,7 +917,7 @@ def main():
             print(json.dumps({"resetup_profile": res}), flush=True)
         return
     if args.setup_profile:
-        res = setup_profile(cpr, torch, bs.jacobian(bs.CONFIGS[WORKLOAD]), stream)
+        res = setup_profile(cpr, torch, host_sequence(), stream)
         if rank == 0:
             print(json.dumps({"setup_profile": res}), flush=True)
         return
