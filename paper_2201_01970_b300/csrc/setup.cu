@@ -610,169 +610,46 @@ __global__ void k_sym_degree(int n, const int *sr, const int *tr, int *deg) {
     if (i < n) deg[i] = (sr[i + 1] - sr[i]) + (tr[i + 1] - tr[i]);
 }
 
-// The smallest color >= 64 not held by a neighbour of larger key (all of
-// them colored), for the counted coloring.
-__device__ int jp_count_color_from64(int i, const JpGraph &g, uint32_t hbase, const int *color) {
-    int di = g.deg[i];
-    uint32_t hi = fmix32((uint32_t)i ^ hbase);
-    for (int base = 64;; base += 64) {
-        unsigned long long mask = 0;
-        for (int pass = 0; pass < 2; pass++) {
-            const int *R = pass ? g.tr : g.sr, *C = pass ? g.tc : g.sc;
-            for (int p = R[i]; p < R[i + 1]; p++) {
-                int j = C[p];
-                if (j == i || !key_greater(g.deg[j], fmix32((uint32_t)j ^ hbase), j, di, hi, i)) continue;
-                int cj = color[j];
-                if (cj >= base && cj < base + 64) mask |= 1ull << (cj - base);
-            }
-        }
-        if (mask != ~0ull) return base + __ffsll((long long)~mask) - 1;
-    }
-}
-
-// Graphs of more than kSmallLevel vertices take the rounds in counted form:
-// a vertex is ready once every neighbour of larger key is colored, and then
-// takes the smallest color those neighbours left free.  That is the round in which JP selects it (all larger
-// neighbours colored before the round starts) and the color JP gives it (a
-// smaller neighbour cannot be colored before it), so the colors are JP's;
-// but a vertex is visited once when it is colored instead of once per round
-// while it waits (as jp_vertex's rounds do), so the rounds cost O(edges) in
-// all instead of O(edges) each.
-// k_jp_count: cnt[i] = the number of neighbours of larger key; vertices with
-// none form round 0's list (slot 0 of the counts).  G lanes per vertex, the
-// neighbour loop made warp-uniform so that appends aggregate by ballot.
+// One JP round over a worklist: the vertices still uncolored when the round
+// starts (round 0: all n, list_in == nullptr), G lanes per vertex.  A
+// vertex's decision depends only on the states left by earlier rounds, so the
+// order of the list does not matter; the losers are appended to list_out
+// (warp-aggregated).  Counts cycle through three slots: this round reads
+// cnt[r % 3], appends to cnt[(r+1) % 3] (zeroed by the previous round) and
+// zeroes cnt[(r+2) % 3] for the next one.  Rounds are launched in batches
+// between host checks; once the list is empty the rest of the batch returns
+// at once.
 template <int G>
-__global__ void k_jp_count(int n, JpGraph g, uint32_t hbase, int *cnt, int *list_out, int *counts) {
-    int lane32 = threadIdx.x & 31, lane = threadIdx.x % G;
-    int per = blockDim.x / G;
-    for (long v0 = (long)blockIdx.x * per; v0 < n; v0 += (long)gridDim.x * per) {   // uniform over the block
-        long t = v0 + threadIdx.x / G;
-        bool act = t < n;
-        int i = act ? (int)t : 0;
-        int di = 0, a0 = 0, na = 0, b0 = 0, nt = 0;
-        uint32_t hi = 0;
-        if (act) {
-            di = g.deg[i];
-            hi = fmix32((uint32_t)i ^ hbase);
-            a0 = g.sr[i];
-            na = g.sr[i + 1] - a0;
-            b0 = g.tr[i];
-            nt = na + (g.tr[i + 1] - b0);
-        }
-        int c = 0;
-        for (int q0 = 0; q0 < nt; q0 += G * kJpPre) {
-            int jj[kJpPre], dj[kJpPre];
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) {
-                int q = q0 + lane + u * G;
-                jj[u] = q < nt ? (q < na ? g.sc[a0 + q] : g.tc[b0 + q - na]) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) dj[u] = jj[u] >= 0 ? g.deg[jj[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) {
-                int j = jj[u];
-                if (j >= 0 && j != i && key_greater(dj[u], fmix32((uint32_t)j ^ hbase), j, di, hi, i)) c++;
-            }
-        }
-        for (int o = G >> 1; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o, G);
-        bool lead = act && lane == 0;
-        if (lead) cnt[i] = c;
-        bool ready = lead && c == 0;
-        unsigned b = __ballot_sync(0xffffffffu, ready);
-        if (b) {
-            int leader = __ffs(b) - 1, base = 0;
-            if (lane32 == leader) base = atomicAdd(&counts[0], __popc(b));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (ready) list_out[base + __popc(b & ((1u << lane32) - 1u))] = i;
-        }
-    }
-}
-
-// One round r of the counted coloring over the ready list.  Counts cycle
-// through three slots: this round reads counts[r % 3], appends to
-// counts[(r+1) % 3] (zeroed by the previous round) and zeroes
-// counts[(r+2) % 3] for the next one; once a list is empty the rest of the
-// batch of rounds returns at once.  Each ready vertex takes the smallest
-// color its larger neighbours (all colored in earlier rounds) left free,
-// then counts itself off every smaller neighbour; a neighbour whose count
-// reaches zero is ready for the next round.  G lanes per vertex; every loop
-// is warp-uniform (its trip count is the warp's largest), so that the
-// appends aggregate by ballot.
-template <int G>
-__global__ void k_jp_push(const int *list_in, int *list_out, int *counts, JpGraph g, uint32_t hbase, int *cnt,
-                          int *color, unsigned r, int *maxcolor) {
-    int m = *(volatile const int *)&counts[r % 3];
-    if (blockIdx.x == 0 && threadIdx.x == 0) counts[(r + 2) % 3] = 0;
-    int *out_cnt = &counts[(r + 1) % 3];
+__global__ void k_jp_round(int n, const int *list_in, int *list_out, int *cnt, JpGraph g, uint32_t hbase,
+                           unsigned long long *state, unsigned r, int *maxcolor) {
+    int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[(r + 2) % 3] = 0;
+    int *out_cnt = &cnt[(r + 1) % 3];
     int lane32 = threadIdx.x & 31, lane = threadIdx.x % G;
     int per = blockDim.x / G;
     int cmax = -1;
-    for (long v0 = (long)blockIdx.x * per; v0 < m; v0 += (long)gridDim.x * per) {   // uniform over the block
+    // v0 is uniform over the block, so whole warps run each pass together
+    for (long v0 = (long)blockIdx.x * per; v0 < m; v0 += (long)gridDim.x * per) {
         long t = v0 + threadIdx.x / G;
         bool act = t < m;
-        int i = act ? list_in[t] : 0;
-        int di = 0, a0 = 0, na = 0, b0 = 0, nt = 0;
-        uint32_t hi = 0;
-        if (act) {
-            di = g.deg[i];
-            hi = fmix32((uint32_t)i ^ hbase);
-            a0 = g.sr[i];
-            na = g.sr[i + 1] - a0;
-            b0 = g.tr[i];
-            nt = na + (g.tr[i + 1] - b0);
-        }
-        int ntw = nt;   // the warp's longest list
-        for (int o = 16; o > 0; o >>= 1) ntw = max(ntw, __shfl_xor_sync(0xffffffffu, ntw, o));
-        unsigned long long used = 0;   // colors below 64 of the larger neighbours
-        int jl[kJpPre], nl = 0;          // this batch's smaller neighbours
-        for (int q0 = 0; q0 < ntw; q0 += G * kJpPre) {
-            int jj[kJpPre], dj[kJpPre];
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) {
-                int q = q0 + lane + u * G;
-                jj[u] = q < nt ? (q < na ? g.sc[a0 + q] : g.tc[b0 + q - na]) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) dj[u] = jj[u] >= 0 ? g.deg[jj[u]] : 0;
-            nl = 0;
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) {
-                int j = jj[u];
-                jl[u] = -1;
-                if (j < 0 || j == i) continue;
-                if (key_greater(dj[u], fmix32((uint32_t)j ^ hbase), j, di, hi, i)) {
-                    int cj = color[j];
-                    if (cj < 64) used |= 1ull << cj;
-                } else {
-                    jl[u] = j;
-                    nl++;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kJpPre; u++) {
-                bool ready = jl[u] >= 0 && atomicSub(&cnt[jl[u]], 1) == 1;
-                unsigned b = __ballot_sync(0xffffffffu, ready);
-                if (b) {
-                    int leader = __ffs(b) - 1, base = 0;
-                    if (lane32 == leader) base = atomicAdd(out_cnt, __popc(b));
-                    base = __shfl_sync(0xffffffffu, base, leader);
-                    if (ready) list_out[base + __popc(b & ((1u << lane32) - 1u))] = jl[u];
-                }
-            }
-        }
-        used = group_or64<G>(used);
-        if (act && lane == 0) {
-            int c = used != ~0ull ? __ffsll((long long)~used) - 1 : jp_count_color_from64(i, g, hbase, color);
-            color[i] = c;
-            cmax = max(cmax, c);
+        int i = act ? (list_in ? list_in[t] : (int)t) : 0;
+        int c = jp_vertex<G, kJpPre>(i, act, lane, g, hbase, state, r);
+        bool lead = act && lane == 0;
+        if (lead && c >= 0) cmax = max(cmax, c);
+        bool lost = lead && c < 0;
+        unsigned b = __ballot_sync(0xffffffffu, lost);
+        if (b) {
+            int leader = __ffs(b) - 1, base = 0;
+            if (lane32 == leader) base = atomicAdd(out_cnt, __popc(b));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (lost) list_out[base + __popc(b & ((1u << lane32) - 1u))] = i;
         }
     }
     if (cmax >= 0) atomicMax(maxcolor, cmax);
 }
 
 // All JP rounds of a small graph in one CTA, rounds separated by barriers
-// (jp_vertex's rounds, without host round trips).
+// (the same rounds as k_jp_round, without host round trips).
 template <int G>
 __global__ void __launch_bounds__(1024) k_jp_small(int n, JpGraph g, uint32_t hbase, unsigned long long *state,
                                                    int *maxcolor) {
@@ -812,7 +689,7 @@ __global__ void k_state_to_color(int n, const unsigned long long *state, int *co
 // largest of them, or 0 with none; the others are appended to list_out.  A
 // level, once written, is final, so a row may read one written earlier in
 // this same round: rounds decide only when a row is reached, never its value.
-// Count slots cycle as in k_jp_push.
+// Count slots cycle as in k_jp_round.
 __global__ void k_level_round(int n, const int *list_in, int *list_out, int *cnt, JpGraph g, int *level,
                               unsigned r, int *maxlevel) {
     int m = list_in ? *(volatile const int *)&cnt[r % 3] : n;
@@ -2894,6 +2771,9 @@ SymGraph sym_graph(Graph &&S, long ub, cudaStream_t s) {
 // Jones-Plassmann coloring of graph G; returns the number of colors.
 int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &color, cudaStream_t s) {
     int n = G.n;
+    DVec<unsigned long long> state;
+    state.alloc(n, s);
+    CK(cudaMemsetAsync(state.p, 0xff, sizeof(unsigned long long) * n, s));
     DVec<int> counters;  // list counts (three slots), max color
     counters.alloc(4, s);
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int), s));
@@ -2906,9 +2786,6 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
         // one CTA: lanes only while every vertex still fits one pass of its 1024 threads
         lanes = 1;
         while (lanes < 8 && (long)2 * lanes * n <= 1024) lanes <<= 1;
-        DVec<unsigned long long> state;
-        state.alloc(n, s);
-        CK(cudaMemsetAsync(state.p, 0xff, sizeof(unsigned long long) * n, s));
         auto small = [&](auto kern) {
             kern<<<1, 1024, 0, s>>>(n, G.dev(), hb, state.p, counters.p + 3);
             CK_LAUNCH();
@@ -2925,44 +2802,33 @@ int jp_color(cpr_handle *h, const SymGraph &G, int salt, int level, DVec<int> &c
         CK_LAUNCH();
         return read_int(counters.p + 3, s) + 1;
     }
-    // larger graphs: the counted form of the rounds (k_jp_count, k_jp_push)
-    DVec<int> lists, cnt;   // two ready lists, used alternately; larger-neighbour counts
+    DVec<int> lists;   // two worklists, used alternately
     lists.alloc(2 * (size_t)n, s);
-    cnt.alloc(n, s);
-    color.alloc(n, s);
     int grid = grid_for((long)n * lanes, kBlock, 148 * 8);
-    auto count = [&](auto kern) {
-        kern<<<grid, kBlock, 0, s>>>(n, G.dev(), hb, cnt.p, lists.p, counters.p);
-        CK_LAUNCH();
-    };
-    switch (lanes) {
-    case 1: count(k_jp_count<1>); break;
-    case 2: count(k_jp_count<2>); break;
-    case 4: count(k_jp_count<4>); break;
-    case 8: count(k_jp_count<8>); break;
-    default: count(k_jp_count<16>); break;
-    }
     unsigned r = 0;
     auto round = [&](auto kern, const int *in, int *out) {
-        kern<<<grid, kBlock, 0, s>>>(in, out, counters.p, G.dev(), hb, cnt.p, color.p, r, counters.p + 3);
+        kern<<<grid, kBlock, 0, s>>>(n, in, out, counters.p, G.dev(), hb, state.p, r, counters.p + 3);
         CK_LAUNCH();
     };
     for (;;) {
         for (int k = 0; k < kJpBatch; k++, r++) {
-            const int *in = lists.p + (size_t)(r % 2) * n;
+            const int *in = r == 0 ? nullptr : lists.p + (size_t)(r % 2) * n;
             int *out = lists.p + (size_t)((r + 1) % 2) * n;
             switch (lanes) {
-            case 1: round(k_jp_push<1>, in, out); break;
-            case 2: round(k_jp_push<2>, in, out); break;
-            case 4: round(k_jp_push<4>, in, out); break;
-            case 8: round(k_jp_push<8>, in, out); break;
-            default: round(k_jp_push<16>, in, out); break;
+            case 1: round(k_jp_round<1>, in, out); break;
+            case 2: round(k_jp_round<2>, in, out); break;
+            case 4: round(k_jp_round<4>, in, out); break;
+            case 8: round(k_jp_round<8>, in, out); break;
+            default: round(k_jp_round<16>, in, out); break;
             }
         }
         if (read_int(counters.p + r % 3, s) == 0) break;
         if (r > (unsigned)n + 8) fail(CPR_ERR_CUDA, "coloring did not terminate");
     }
     if (getenv("CPR_SETUP_TIMING")) fprintf(stderr, "[cpr setup] jp n=%d rounds<=%u\n", n, r);
+    color.alloc(n, s);
+    k_state_to_color<<<grid_for(n, kBlock), kBlock, 0, s>>>(n, state.p, color.p);
+    CK_LAUNCH();
     return read_int(counters.p + 3, s) + 1;
 }
 
