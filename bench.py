@@ -859,6 +859,8 @@ def main():
                     help="skip the numeric-only resetup line")
     ap.add_argument("--no-ua-amg", action="store_true",
                     help="skip the UA-AMG (amg = 1) line")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip Alg. 3 on the 60x220x85 drifting sequence (mu = 0, 30, 60) in the line")
     ap.add_argument("--no-alg45", action="store_true",
                     help="skip the Alg. 4-5 coloring (coloring = 1) line")
     ap.add_argument("--serve-scaled", action="store_true",
@@ -970,6 +972,9 @@ def main():
         cpr, torch, seq_dev, rhs_dev, K, W, stream,
         "amg = 1: the paper's UA-AMG first stage (double pairwise aggregation, handshake rounds with "
         "attachment, unit P) with the nonlinear AMLI-cycle (2 GCR steps per coarse correction)", amg=1)
+    # Alg. 3 on the 60x220x85 sequence: mu = 0 and 30 rebuild B every step at
+    # this size (every solve takes over 40 inner steps), mu = 60 keeps B^(1)
+    adaptive = None if args.no_adaptive else adaptive_sweep(cpr, torch, stream, mus=(0, 30, 60))
     numeric = None if args.no_resetup_numeric else option_arm(
         cpr, torch, seq_dev, rhs_dev, K, W, stream,
         "resetup = 1: each rebuild keeps the first setup's levels, strength sets, C/F splits and colorings "
@@ -1127,6 +1132,8 @@ def main():
         line["ua_amg"] = ua
     if alg45 is not None:
         line["alg45_coloring"] = alg45
+    if adaptive is not None:
+        line["adaptive_60x220x85"] = adaptive
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if err is not None:
