@@ -147,6 +147,7 @@ void prof_collect_graph(cpr_handle *h, int which) {
 }
 
 void destroy_step_graphs(cpr_handle *h) {
+    if (h->sg[1].exec == h->sg[0].exec) h->sg[1].exec = nullptr;   // one graph served both slots
     for (auto &g : h->sg) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
         if (g.graph) cudaGraphDestroy(g.graph);

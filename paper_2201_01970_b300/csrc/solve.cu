@@ -1851,13 +1851,18 @@ void record_step(cpr_handle *h) {
     CK_LAUNCH();
 }
 
-// (Re)capture the two step graphs when B, the workspace or profiling changed.
+// (Re)capture the step graphs when B, the workspace or profiling changed.
+// With profiling on, the two graphs differ in their event nodes and steps
+// alternate between them; without it one graph serves both slots (launches of
+// one executable graph run in stream order).  An executable graph kept from an
+// earlier capture without profiling is updated in place when the new graph has
+// its topology -- a new setup of the same level and color counts -- which
+// costs less than instantiating it afresh.
 void ensure_step_graphs(cpr_handle *h) {
     unsigned pm = h->prof ? h->prof_mask : 0u;
     if (h->sg_epoch == h->epoch && h->sg_prof == pm && h->sg[0].exec && h->sg[1].exec) return;
-    destroy_step_graphs(h);
     Nvtx nv("capture Arnoldi step graphs");
-    for (int k = 0; k < 2; k++) {
+    auto capture = [&](int k) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         h->capturing = k;
@@ -1874,9 +1879,40 @@ void ensure_step_graphs(cpr_handle *h) {
         h->capturing = -1;
         set_capturing(false);
         CK(cudaStreamEndCapture(h->stream, &g));
-        h->sg[k].graph = g;
-        h->sg[k].kernels = graph_kernel_nodes(g);
-        CK(cudaGraphInstantiate(&h->sg[k].exec, g, 0));
+        return g;
+    };
+    if (pm == 0) {
+        bool reuse = h->sg_prof == 0 && h->sg[0].exec && h->sg[1].exec == h->sg[0].exec;
+        cudaGraph_t g = capture(0);
+        if (reuse) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(h->sg[0].exec, g, &info) != cudaSuccess) {
+                cudaGetLastError();
+                reuse = false;
+            }
+        }
+        if (!reuse) {
+            destroy_step_graphs(h);
+            cudaGraphExec_t e = nullptr;
+            cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+            if (err != cudaSuccess) {
+                cudaGraphDestroy(g);
+                CK(err);
+            }
+            h->sg[0].exec = h->sg[1].exec = e;
+        } else if (h->sg[0].graph) {
+            cudaGraphDestroy(h->sg[0].graph);
+        }
+        h->sg[0].graph = g;
+        h->sg[0].kernels = h->sg[1].kernels = graph_kernel_nodes(g);
+    } else {
+        destroy_step_graphs(h);
+        for (int k = 0; k < 2; k++) {
+            cudaGraph_t g = capture(k);
+            h->sg[k].graph = g;
+            h->sg[k].kernels = graph_kernel_nodes(g);
+            CK(cudaGraphInstantiate(&h->sg[k].exec, g, 0));
+        }
     }
     h->sg_epoch = h->epoch;
     h->sg_prof = pm;
@@ -1980,6 +2016,8 @@ int fgmres_advance(cpr_handle *h, bool block) {
                 continue;
             }
             issue_cycle_start(h, F.cycle == 0);
+            // capture (after a new setup) while the device computes the residual
+            ensure_step_graphs(h);
             F.phase = FgmresState::WAIT_START;
             continue;
         case FgmresState::WAIT_START: {
