@@ -225,6 +225,15 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
     pdl_wait();
     pdl_trigger();
     if (done && *done) return;
+    // v's three entries of this row are loaded with the gathers, not after them
+    bool lead = active && lane == 0;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (lead) {
+        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)brow;
+        v0 = v[0];
+        v1 = v[1];
+        v2 = v[2];
+    }
     T a0 = 0, a1 = 0, a2 = 0;
     if (active) {
 #pragma unroll
@@ -249,11 +258,10 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
         a1 += __shfl_xor_sync(0xffffffffu, a1, o, G);
         a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
     }
-    if (active && lane == 0) {
-        const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)brow;
-        r[3 * (size_t)row] = (T)v[0] - a0;
-        r[3 * (size_t)row + 1] = (T)v[1] - a1;
-        r[3 * (size_t)row + 2] = (T)v[2] - a2;
+    if (lead) {
+        r[3 * (size_t)row] = (T)v0 - a0;
+        r[3 * (size_t)row + 1] = (T)v1 - a1;
+        r[3 * (size_t)row + 2] = (T)v2 - a2;
     }
 }
 
@@ -387,11 +395,19 @@ __global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__rest
     pdl_wait();
     pdl_trigger();
     if (done && *done) return;
-    for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
+    // every read of the pending range goes to sp, so its commit into x can
+    // wait until the row's gathers are issued: a commit store ahead of them
+    // would hold them back by a round trip (the compiler cannot reorder loads
+    // of x past a store to x)
+    long np = p1 - p0;
+    T cv = tid < np ? sp[p0 + tid] : (T)0;
+    T bi = active && lane == 0 ? b[i] : (T)0;
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
-    if (active && lane == 0) sc[i] = (b[i] - s) * di;
+    if (active && lane == 0) sc[i] = (bi - s) * di;
+    if (tid < np) x[p0 + tid] = cv;
+    for (long t = tid + nthr; t < np; t += nthr) x[p0 + t] = sp[p0 + t];
 }
 
 // r = b - A x with x's pending range read from sp (and committed into x).
@@ -412,10 +428,14 @@ __global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ ro
     pdl_wait();
     pdl_trigger();
     if (done && *done) return;
+    // the row's own b_i and x_i are loaded with its gathers, not after them
+    bool lead = active && lane == 0;
+    T bi = lead ? b[i] : (T)0;
+    T xi = lead ? xval(x, sp, p0, p1, i) : (T)0;
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
-    if (active && lane == 0) r[i] = b[i] - s - dg * xval(x, sp, p0, p1, i);
+    if (lead) r[i] = bi - s - dg * xi;
     // commit after every read of this kernel's own rows is done is not
     // guaranteed across CTAs, so readers above take the pending range from sp
     for (long t = tid; t < p1 - p0; t += nthr) x[p0 + t] = sp[p0 + t];
@@ -437,10 +457,12 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
     pdl_wait();
     pdl_trigger();
     if (done && *done) return;
+    bool lead = active && lane == 0;
+    T yi = lead && add ? y[i] : (T)0;   // loaded with the gathers
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
-    if (active && lane == 0) y[i] = add ? y[i] + s : s;
+    if (lead) y[i] = add ? yi + s : s;
 }
 
 // Restriction fused with the first pre-smoothing color of the coarser level

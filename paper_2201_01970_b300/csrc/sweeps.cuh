@@ -95,7 +95,11 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
         y[3 * (size_t)i + 1] = s1;
         y[3 * (size_t)i + 2] = s2;
     } else {
-        // G lanes share the row: lane sums of L_ij y_j, then one group sum
+        // G lanes share the row: lane sums of L_ij y_j, then one group sum;
+        // the row's own y_i is loaded with the gathers, not after them
+        bool lead = active && lane == 0;
+        T yi0 = lead ? y[3 * (size_t)i] : (T)0, yi1 = lead ? y[3 * (size_t)i + 1] : (T)0,
+          yi2 = lead ? y[3 * (size_t)i + 2] : (T)0;
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
         for (int u = 0; u < kPreB; u++)
@@ -118,10 +122,10 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
         a0 = group_sum(a0, G);
         a1 = group_sum(a1, G);
         a2 = group_sum(a2, G);
-        if (active && lane == 0) {
-            y[3 * (size_t)i] -= a0;
-            y[3 * (size_t)i + 1] -= a1;
-            y[3 * (size_t)i + 2] -= a2;
+        if (lead) {
+            y[3 * (size_t)i] = yi0 - a0;
+            y[3 * (size_t)i + 1] = yi1 - a1;
+            y[3 * (size_t)i + 2] = yi2 - a2;
         }
     }
 }
@@ -163,6 +167,10 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
     pdl_wait();
     pdl_trigger();
     if (done && *done) return;
+    // where the result goes, and the V-cycle's part of it, are loaded before
+    // the gathers: the stores at the end then wait on nothing
+    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
+    double e0v = lead && ep ? (double)ep[i] : 0.0;
     T s0, s1, s2;
     if constexpr (G == 1) {
         if (!active) return;
@@ -187,6 +195,9 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
             s2 -= U[6] * z0 + U[7] * z1 + U[8] * z2;
         }
     } else {
+        // the row's own y_i is loaded with the gathers, not after them
+        T yi0 = lead ? y[3 * (size_t)i] : (T)0, yi1 = lead ? y[3 * (size_t)i + 1] : (T)0,
+          yi2 = lead ? y[3 * (size_t)i + 2] : (T)0;
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
         for (int u = 0; u < kPreB; u++)
@@ -210,9 +221,9 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
         a1 = group_sum(a1, G);
         a2 = group_sum(a2, G);
         if (!lead) return;
-        s0 = y[3 * (size_t)i] - a0;
-        s1 = y[3 * (size_t)i + 1] - a1;
-        s2 = y[3 * (size_t)i + 2] - a2;
+        s0 = yi0 - a0;
+        s1 = yi1 - a1;
+        s2 = yi2 - a2;
     }
     T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
     T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
@@ -220,8 +231,7 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
     y[3 * (size_t)i] = z0;
     y[3 * (size_t)i + 1] = z1;
     y[3 * (size_t)i + 2] = z2;
-    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
-    out[0] = (double)z0 + (ep ? (double)ep[i] : 0.0);
+    out[0] = (double)z0 + e0v;
     out[1] = (double)z1;
     out[2] = (double)z2;
 }
