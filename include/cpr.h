@@ -79,10 +79,10 @@ typedef struct {
     int max_levels;     /* default 20 */
     uint64_t seed;      /* hash seed of coloring and C/F splitting; default 0 */
     void *stream;       /* cudaStream_t; NULL = the handle creates its own */
-    int pdl;            /* 1: the kernels of a B application use programmatic dependent launch,
-                           each loading its setup-time operands while its predecessor runs;
-                           0 (default, measured as fast on B300): plain stream order.  Results
-                           are identical either way. */
+    int pdl;            /* 1 (default): the kernels of a B application use programmatic
+                           dependent launch, each loading its setup-time operands while its
+                           predecessor runs (FP64 BILU(0) sweeps excepted: slower so on
+                           B300); 0: plain stream order.  Results are identical either way. */
     int tail;           /* 1: the last one or two smoothed AMG levels (never level 0) and the
                            coarse solve run as one kernel on one thread-block cluster when
                            they are small enough (at most 4096 rows per level, 16 colors, a

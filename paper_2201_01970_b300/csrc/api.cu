@@ -214,7 +214,7 @@ void cpr_default_opts(cpr_opts *o) {
     o->max_levels = 20;
     o->seed = 0;
     o->stream = nullptr;
-    o->pdl = 0;
+    o->pdl = 1;
     o->tail = 0;
     o->bilu_order = 0;
     o->reuse_refresh = 0;

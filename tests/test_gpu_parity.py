@@ -460,16 +460,18 @@ def test_cluster_tail_changes_no_result(torch, cpr, fp32):
         assert out[0][2]["iters"] == out[1][2]["iters"]
 
 
+@pytest.mark.parametrize("amg", [0, 1])
 @pytest.mark.parametrize("fp32", [0, 1])
-def test_dependent_launch_changes_no_result(torch, cpr, fp32):
+def test_dependent_launch_changes_no_result(torch, cpr, fp32, amg):
     """Programmatic dependent launch only moves the loads of setup-time
     operands ahead of the wait on the previous kernel: solves with it on and
-    off must agree bit for bit (same iterations, same x)."""
+    off must agree bit for bit (same iterations, same x), for the V-cycle
+    (amg = 0) and for the AMLI-cycle with its device-side GCR scalars (amg = 1)."""
     J = ragged()
     b = dev(torch, J.b)
     xs, its = [], []
     for pdl in (1, 0):
-        s = cpr.Solver(DevJ(torch, J), precond_fp32=fp32, pdl=pdl)
+        s = cpr.Solver(DevJ(torch, J), precond_fp32=fp32, pdl=pdl, amg=amg)
         x, st = s.solve(b, rtol=1e-8)
         xs.append(x.cpu().numpy())
         its.append(st["iters"])

@@ -36,7 +36,7 @@ def test_binding_loads_and_defaults():
     assert (o.theta_color, o.theta_amg, o.mu, o.restart, o.coarse_max) == (0.05, 0.25, 30, 30, 256)
     # the fields after the stream pointer: a layout mismatch with cpr_opts would misread them
     assert (o.max_restarts, o.decouple, o.pre, o.post, o.max_levels, o.seed) == (100, 1, 1, 1, 20, 0)
-    assert (o.pdl, o.tail, o.bilu_order, o.reuse_refresh, o.resetup) == (0, 0, 0, 0, 0)
+    assert (o.pdl, o.tail, o.bilu_order, o.reuse_refresh, o.resetup) == (1, 0, 0, 0, 0)
     assert (o.amg, o.amli_iters, o.coloring, o.coloring_rows) == (0, 2, 0, 4096)
     assert ctypes.sizeof(cpr.Opts) == 112   # sizeof(cpr_opts), asserted at compile time in api.cu
     assert cpr.lib().cpr_strerror(cpr.CPR_ERR_SINGULAR).startswith(b"singular")
