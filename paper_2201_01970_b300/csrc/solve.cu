@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int nslices, int nb, const in
                                                    const double *__restrict__ x_base, long xld, const int *jptr,
                                                    const double *__restrict__ b, double *__restrict__ y,
                                                    const int *done) {
+    pdl_wait();
     if (done && *done) return;
     int slice = (int)(((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     int lane = threadIdx.x & 31;
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(256) k_sell_spmv(int nslices, int nb, const in
         a2 = fma(v[224], x1, a2);
         a2 = fma(v[256], x2, a2);
     }
+    pdl_trigger();
     if (row < nb) {
         size_t q = 3 * (size_t)row;
         if (b) {
@@ -843,6 +845,7 @@ __global__ void __launch_bounds__(kBlock) k_cgs_dots(long N, const double *__res
                                                      const double *__restrict__ w, const int *jptr,
                                                      double *part, int ldp, double *hcol, int *counter,
                                                      const int *done) {
+    pdl_wait();
     if (*done) return;
     __shared__ double red[kBlock / 32][kCgsGroup];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -863,6 +866,7 @@ __global__ void __launch_bounds__(kBlock) k_cgs_dots(long N, const double *__res
         }
         __syncthreads();
     }
+    pdl_trigger();
     if (!arrive_last(counter)) return;
     for (int i = wid; i < nvec; i += kBlock / 32) {
         double t = 0.0;
@@ -915,6 +919,7 @@ __device__ __forceinline__ double cgs_update_loop(long N, const double *__restri
 __global__ void __launch_bounds__(kBlock) k_cgs_update_givens(long N, const double *__restrict__ V,
                                                               double *__restrict__ w, double *part,
                                                               int *counter, double *sc, int m, int *di) {
+    pdl_wait();
     if (di[I_DONE]) return;
     ScalLayout SL{m};
     __shared__ double sh[kMaxRestart + 2], rc[kMaxRestart], rs[kMaxRestart];
@@ -937,6 +942,7 @@ __global__ void __launch_bounds__(kBlock) k_cgs_update_givens(long N, const doub
     }
     s = block_sum(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+    pdl_trigger();
     if (!arrive_last(counter)) return;
     if (threadIdx.x >= 32) return;
     int lane = threadIdx.x;
@@ -985,6 +991,7 @@ __global__ void __launch_bounds__(kBlock) k_cgs_update_givens(long N, const doub
 // V_{j+1} = w / h_{j+1,j} (after k_givens advanced the step index to j+1).
 __global__ void k_next_basis(long N, const double *w, double *V, const double *sc, int m,
                              const int *di) {
+    pdl_wait();
     if (di[I_DONE]) return;
     ScalLayout L{m};
     double s = sc[L.inv_hn()];
@@ -1508,9 +1515,8 @@ void spmv_h(cpr_handle *h, const double *x, long xld, const int *jptr, const dou
         return;
     }
     unsigned blocks = (unsigned)((h->sell_slices + 7) / 8);
-    k_sell_spmv<<<blocks, 256, 0, s>>>(h->sell_slices, h->nb, h->sell_off.p, h->sell_col.p, h->sell_val.p, x, xld,
-                                       jptr, b, y, done);
-    CK_LAUNCH();
+    launch_pdl(h->opt.pdl != 0, k_sell_spmv, blocks, 256, s, h->sell_slices, h->nb, h->sell_off.p, h->sell_col.p,
+               h->sell_val.p, x, xld, jptr, b, y, done);
 }
 
 // ||a||^2 partials into h->red, then a one-thread kernel consumes them.
@@ -1878,15 +1884,14 @@ void record_step(cpr_handle *h) {
     prof_end(h);
     // CGS: h_ij = (w, v_i), w -= sum h_ij v_i, h_{j+1,j} = ||w||, Givens
     prof_begin(h, CPR_PROF_CGS);
-    k_cgs_dots<<<kCgsDotBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, di + I_J, h->red.p, ldp, sc + SL.hcol(),
-                                             di + I_CNT_DOT, done);
-    CK_LAUNCH();
-    k_cgs_update_givens<<<kCgsBlocks, kBlock, 0, s>>>(N, h->V.p, h->wv.p, h->red.p + (size_t)kCgsDotBlocks * ldp,
-                                                      di + I_CNT_UPD, sc, m, di);
-    CK_LAUNCH();
+    bool pdl = h->opt.pdl != 0;
+    launch_pdl(pdl, k_cgs_dots, kCgsDotBlocks, kBlock, s, N, (const double *)h->V.p, (const double *)h->wv.p,
+               (const int *)(di + I_J), h->red.p, ldp, sc + SL.hcol(), di + I_CNT_DOT, done);
+    launch_pdl(pdl, k_cgs_update_givens, kCgsBlocks, kBlock, s, N, (const double *)h->V.p, h->wv.p,
+               h->red.p + (size_t)kCgsDotBlocks * ldp, di + I_CNT_UPD, sc, m, di);
     prof_end(h);
-    k_next_basis<<<grid_for(N, kBlock, 148 * 8), kBlock, 0, s>>>(N, h->wv.p, h->V.p, sc, m, di);
-    CK_LAUNCH();
+    launch_pdl(pdl, k_next_basis, grid_for(N, kBlock, 148 * 8), kBlock, s, N, (const double *)h->wv.p, h->V.p,
+               (const double *)sc, m, (const int *)di);
 }
 
 // (Re)capture the step graphs when B, the workspace or profiling changed.
