@@ -303,6 +303,7 @@ int cpr_update(cpr_handle *h, const cpr_bsr3 *A) {
             same = read_int(diff.p, s) == 0;
         }
         if (!same) {
+            h->pattern_id++;   // structure kept from the old pattern is stale
             h->rowptr = std::move(rp);
             h->col = std::move(cl);
             h->nb = A->nb;

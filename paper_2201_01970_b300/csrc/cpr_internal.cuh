@@ -199,6 +199,7 @@ struct Level {
 // each color a contiguous range [color_off[c], color_off[c+1])): L (lower
 // colors), U (higher colors) and D^-1 with rows and columns in positions.
 struct Bilu {
+    int pattern = -1;              // the handle's pattern_id the structure below was built for
     DVec<int> color;
     int ncolors = 0;
     std::vector<int> color_off;
@@ -207,6 +208,7 @@ struct Bilu {
     DVec<double> lu;
     DVec<float> lu32;
     DVec<int> Lrowptr, Lcol, Urowptr, Ucol;
+    int nl = 0, nu = 0;            // entries of L and U
     DVec<double> Lval, Uval, Dinv;
     DVec<float> Lval32, Uval32, Dinv32;
 };
@@ -264,6 +266,8 @@ struct cpr_handle {
     int nb = 0, nnzb = 0;
     cpr::DVec<int> rowptr, col;     // outer operator A^(k) (copy)
     cpr::DVec<double> val;
+    // bumped whenever A's block pattern changes (cpr_setup, cpr_update with a new pattern)
+    int pattern_id = 0;
     // --- the preconditioner B (frozen between setups) ---
     bool have_B = false;
     // column 0 of every block of the A that B was built from (Alg. 1, second residual),

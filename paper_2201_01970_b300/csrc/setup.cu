@@ -3611,7 +3611,25 @@ class SideWorker {
 
 // Build B from the handle's current A (Sec. 3.1; the setup steps of Alg. 6 per level).
 void build_preconditioner(cpr_handle *h) {
+    // BILU(0)'s coloring (JP at theta = 0 on the off-diagonal block pattern,
+    // hashed by the seed), its order and its L/U pattern, and the column-0
+    // copy's pattern are functions of A's block pattern alone: while that is
+    // unchanged they are kept from the last setup, bit for bit what a rebuild
+    // would give, and only their values are recomputed.
+    bool keep = h->bilu.pattern == h->pattern_id && h->bilu.ncolors > 0 && h->c0rowptr.p && h->c0col.p;
+    Bilu kept_bilu;
+    DVec<int> kept_c0rowptr, kept_c0col;
+    if (keep) {
+        kept_bilu = std::move(h->bilu);
+        kept_c0rowptr = std::move(h->c0rowptr);
+        kept_c0col = std::move(h->c0col);
+    }
     free_preconditioner(h);
+    if (keep) {
+        h->bilu = std::move(kept_bilu);
+        h->c0rowptr = std::move(kept_c0rowptr);
+        h->c0col = std::move(kept_c0col);
+    }
     Nvtx nv("setup");
     cudaStream_t s = h->stream;
     PhaseClock clk;
@@ -3654,62 +3672,76 @@ void build_preconditioner(cpr_handle *h) {
     clk.mark("decouple");
     // ---- second stage: multicolor BILU(0), on the side worker ----
     SideWorker side(h, &clk);
-    side.post([h, nb, nnzb, f32, &bdiag, &side](cudaStream_t s) {
+    side.post([h, nb, nnzb, f32, keep, &bdiag, &side](cudaStream_t s) {
         Nvtx r("BILU(0) setup");
         Bilu &B = h->bilu;
         int nl = 0, nu = 0;
-        // every row holds exactly one diagonal block: nnzb - nb entries
-        SymGraph G = sym_graph(build_pattern_ub(nb, (long)nnzb - nb, s, [&](const int *srow, int *out) {
-                                   k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p,
-                                                                                            h->col.p, srow, out);
-                                   CK_LAUNCH();
-                               }),
-                               (long)nnzb - nb, s);
-        side.mark("bilu_graph");
-        // multicolor (JP at theta = 0), or the natural order's level sets
-        B.ncolors = h->opt.bilu_order ? level_sets(G, B.color, s) : jp_color(h, G, 2, 0, B.color, s);
-        side.mark("bilu_jp");
-        rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
-        B.iperm.alloc(nb, s);
-        k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
-        CK_LAUNCH();
-        DVec<int> lcnt, ucnt;
-        lcnt.alloc(nb, s);
-        ucnt.alloc(nb, s);
-        k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
-                                                                  B.color.p, lcnt.p, ucnt.p);
-        CK_LAUNCH();
-        B.Lrowptr.alloc(nb + 1, s);
-        B.Urowptr.alloc(nb + 1, s);
-        exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
-        exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
-        nl = read_int(B.Lrowptr.p + nb, s);
-        nu = read_int(B.Urowptr.p + nb, s);
-        B.Lcol.alloc(std::max(nl, 1), s);
-        B.Ucol.alloc(std::max(nu, 1), s);
-        side.mark("bilu_order");
-        if (f32) {
-            B.lu32.alloc(9 * (size_t)nnzb, s);
-            B.Lval32.alloc(9 * (size_t)std::max(nl, 1), s);
-            B.Uval32.alloc(9 * (size_t)std::max(nu, 1), s);
-            B.Dinv32.alloc(9 * (size_t)nb, s);
+        if (keep) {   // the kept structure
+            nl = B.nl;
+            nu = B.nu;
+            side.mark("bilu_kept");
         } else {
-            B.lu.alloc(9 * (size_t)nnzb, s);
-            B.Lval.alloc(9 * (size_t)std::max(nl, 1), s);
-            B.Uval.alloc(9 * (size_t)std::max(nu, 1), s);
-            B.Dinv.alloc(9 * (size_t)nb, s);
+            // every row holds exactly one diagonal block: nnzb - nb entries
+            SymGraph G = sym_graph(build_pattern_ub(nb, (long)nnzb - nb, s, [&](const int *srow, int *out) {
+                                       k_offdiag_pattern<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, h->rowptr.p,
+                                                                                                h->col.p, srow, out);
+                                       CK_LAUNCH();
+                                   }),
+                                   (long)nnzb - nb, s);
+            side.mark("bilu_graph");
+            // multicolor (JP at theta = 0), or the natural order's level sets
+            B.ncolors = h->opt.bilu_order ? level_sets(G, B.color, s) : jp_color(h, G, 2, 0, B.color, s);
+            side.mark("bilu_jp");
+            rows_by_color(nb, B.color.p, B.ncolors, B.color_off, B.rows_by_color, s);
+            B.iperm.alloc(nb, s);
+            k_iperm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p);
+            CK_LAUNCH();
+            DVec<int> lcnt, ucnt;
+            lcnt.alloc(nb, s);
+            ucnt.alloc(nb, s);
+            k_bilu_split_count<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, h->rowptr.p, h->col.p,
+                                                                      B.color.p, lcnt.p, ucnt.p);
+            CK_LAUNCH();
+            B.Lrowptr.alloc(nb + 1, s);
+            B.Urowptr.alloc(nb + 1, s);
+            exclusive_scan(lcnt.p, B.Lrowptr.p, nb, s);
+            exclusive_scan(ucnt.p, B.Urowptr.p, nb, s);
+            nl = read_int(B.Lrowptr.p + nb, s);
+            nu = read_int(B.Urowptr.p + nb, s);
+            B.nl = nl;
+            B.nu = nu;
+            B.Lcol.alloc(std::max(nl, 1), s);
+            B.Ucol.alloc(std::max(nu, 1), s);
+            side.mark("bilu_order");
+        }
+        // value buffers: a kept structure keeps them too (every entry is rewritten)
+        auto sized = [s](auto &v, size_t count) {
+            if (v.n != count || !v.p) v.alloc(count, s);
+        };
+        if (f32) {
+            sized(B.lu32, 9 * (size_t)nnzb);
+            sized(B.Lval32, 9 * (size_t)std::max(nl, 1));
+            sized(B.Uval32, 9 * (size_t)std::max(nu, 1));
+            sized(B.Dinv32, 9 * (size_t)nb);
+        } else {
+            sized(B.lu, 9 * (size_t)nnzb);
+            sized(B.Lval, 9 * (size_t)std::max(nl, 1));
+            sized(B.Uval, 9 * (size_t)std::max(nu, 1));
+            sized(B.Dinv, 9 * (size_t)nb);
         }
         bilu_values(h, bdiag.p, s);
         side.mark("bilu_factor");
         // the frozen column-0 copy of A in positions
-        DVec<int> ccnt;
-        ccnt.alloc(nb, s);
-        k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p, h->col.p,
-                                                           h->val.p, nullptr, nullptr, nullptr, ccnt.p);
-        CK_LAUNCH();
-        h->c0rowptr.alloc(nb + 1, s);
-        exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
-        h->c0col.alloc(nnzb, s);
+        if (!keep) {
+            DVec<int> ccnt;
+            ccnt.alloc(nb, s);
+            k_col0_perm<<<grid_for(nb, kBlock), kBlock, 0, s>>>(nb, B.rows_by_color.p, B.iperm.p, h->rowptr.p,
+                                                               h->col.p, h->val.p, nullptr, nullptr, nullptr, ccnt.p);
+            CK_LAUNCH();
+            h->c0rowptr.alloc(nb + 1, s);
+            exclusive_scan(ccnt.p, h->c0rowptr.p, nb, s);
+            h->c0col.alloc(nnzb, s);
+        }
         h->pcol0.alloc(3 * (size_t)nnzb, s);
         col0_values(h, s);   // its FP32 shadow is made after the side work has joined
         side.mark("col0");
@@ -4052,6 +4084,7 @@ void build_preconditioner(cpr_handle *h) {
     check_err(h, "zero or non-finite pivot: an AMG level's diagonal, the coarsest matrix or a BILU(0) block");
     clk.mark("layout");
     h->have_B = true;
+    h->bilu.pattern = h->pattern_id;
     h->nr_ready = o.resetup != 0;
     h->epoch++;
 }

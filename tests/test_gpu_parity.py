@@ -499,6 +499,47 @@ def test_vcycle_part_timing_hook(torch, cpr):
     s.close()
 
 
+@pytest.mark.parametrize("bilu_order", [0, 1])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_full_setup_on_a_kept_pattern_equals_a_fresh_setup(torch, cpr, fp32, bilu_order):
+    """With mu = 0 Alg. 3 rebuilds B at every update.  On an unchanged block
+    pattern the rebuild keeps BILU(0)'s coloring, order and L/U pattern (they
+    depend on the pattern alone) and recomputes everything else, so after each
+    update the handle's B equals, bit for bit, that of a fresh handle set up on
+    the same Jacobian (BILU colors and factors, B v, a whole solve), and in
+    FP64 with the multicolor order its hierarchy and BILU(0) equal the
+    oracle's.  An update to another grid in between rebuilds the structure
+    for the new pattern."""
+    g0 = bs.GridSpec(37, 23, 9, 0.0, 1.5, 0.3, None, "five_spot", seed=5)
+    seq = list(bs.jacobian_sequence(g0, 3, drift=0.05))
+    other = bs.jacobian(bs.GridSpec(20, 17, 6, 0.0, 1.0, 1.0, None, "corners", seed=2))
+    kw = dict(mu=0, bilu_order=bilu_order)
+    g = cpr.Solver(DevJ(torch, seq[0]), precond_fp32=fp32, **kw)
+    rng = np.random.default_rng(21)
+    for J in (seq[1], other, seq[2], seq[1]):
+        g.update(DevJ(torch, J))
+        f = cpr.Solver(DevJ(torch, J), precond_fp32=fp32, **kw)
+        gbc, gnc, glu = g.bilu()
+        fbc, fnc, flu = f.bilu()
+        assert gnc == fnc
+        np.testing.assert_array_equal(gbc, fbc)
+        np.testing.assert_array_equal(glu, flu)
+        v = dev(torch, rng.standard_normal(J.n))
+        zg, zf = torch.zeros_like(v), torch.zeros_like(v)
+        g.apply(v, zg)
+        f.apply(v, zf)
+        assert torch.equal(zg, zf)
+        xg, sg = g.solve(dev(torch, J.b), rtol=1e-8)
+        xf, sf = f.solve(dev(torch, J.b), rtol=1e-8)
+        assert sg["setup_called"] == 1 and sg["iters"] == sf["iters"] and torch.equal(xg, xf)
+        if not fp32 and not bilu_order:   # the oracle's level-set BILU has its own checks
+            o = oracle.Solver(J, **kw)
+            compare_hierarchy(o, g)
+            o.close()
+        f.close()
+    g.close()
+
+
 @pytest.mark.parametrize("mu", [0, 30])
 def test_update_values_equals_update(torch, cpr, mu):
     """cpr_update_values (values only, pattern guaranteed unchanged) makes the
