@@ -40,11 +40,9 @@ MU = 30
 # kernel the line rates, from one ncu capture of the build named, at the
 # workload named; a kernel changed since then has no entry (traffic null).
 NCU_TRAFFIC = {
-    ("k_smooth_color", "128x128x32"): {"bytes": 2.524e6,
+    ("k_smooth_color", "128x128x32"): {"bytes": 2.525e6,
                                        "source": "mean DRAM bytes of the 56 color launches of one eager V-cycle, "
-                                                 "ncu capture of the commit ea0b151 build, cold caches"},
-    ("k_sell_spmv", "128x128x32"): {"bytes": 302.63e6 + 9.98e6,
-                                    "source": "ncu capture of one k_sell_spmv launch of the commit cdabb71 build"},
+                                                 "ncu capture of the commit eb27359 build, cold caches"},
 }
 
 
@@ -1060,7 +1058,7 @@ def main():
                "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
                "bytes_per_launch": sm0.get("bytes_per_launch")}
     # The dominant kernel by launch-list share is the multi-color GS sweep
-    # k_smooth_color (its instances over all levels: ~26 % of a step's kernel
+    # k_smooth_color (its instances over all levels: ~29 % of a step's kernel
     # time).  Its rate: the algorithmic bytes of every color launch of one
     # V(1,1) cycle (smooth_color_bytes) over the live in-graph time of all
     # pre- and post-smoothing sweeps (vcycle_parts_us), against HBM.
