@@ -190,10 +190,12 @@ __device__ __forceinline__ bool nan_bits(long long u) { return (u & kMagBits) > 
 // row order over the whole row).  srowptr == nullptr: count pass (out =
 // counts), which also leaves each row's threshold in thr; otherwise fill
 // pass (out = columns), which reads it back instead of summing again.
-__global__ void k_strength51(int n, const int *rowptr, const int *col, const double *val,
-                             double theta, const int *srowptr, int *out, double *thr) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// Row i of Eq. 5.1's strength set.  Without srowptr: the row's threshold
+// theta * sum_k |a_ik| (summed in entry order) goes to thr[i] and the count
+// of its strong entries is returned; with srowptr: the threshold is read from
+// thr[i] and the strong columns are written from out[srowptr[i]] on.
+__device__ __forceinline__ int strength51_row(int i, const int *rowptr, const int *col, const double *val,
+                                              double theta, const int *srowptr, int *out, double *thr) {
     int a = rowptr[i], b = rowptr[i + 1];
     const long long *vb = reinterpret_cast<const long long *>(val);
     long long tb;
@@ -218,6 +220,14 @@ __global__ void k_strength51(int n, const int *rowptr, const int *col, const dou
             }
         }
     }
+    return c;
+}
+
+__global__ void k_strength51(int n, const int *rowptr, const int *col, const double *val,
+                             double theta, const int *srowptr, int *out, double *thr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = strength51_row(i, rowptr, col, val, theta, srowptr, out, thr);
     if (!srowptr) out[i] = c;
 }
 
@@ -681,6 +691,135 @@ __global__ void __launch_bounds__(1024) k_jp_small(int n, JpGraph g, uint32_t hb
 __global__ void k_state_to_color(int n, const unsigned long long *state, int *color) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) color[i] = (int)(unsigned)state[i];
+}
+
+// Exclusive scan of a[0 .. n) in place, a[n] = the total, by one CTA of
+// kSmallLevel / 4 threads, each taking four consecutive entries (n <= kSmallLevel).
+__device__ void cta_scan_small(int *a, int n) {
+    __shared__ int wsum[32];
+    int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    int base = 4 * t, v[4], sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        v[k] = base + k < n ? a[base + k] : 0;
+        sum += v[k];
+    }
+    int x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    int e = x - sum + (wid > 0 ? wsum[wid - 1] : 0);
+    int total = wsum[(blockDim.x >> 5) - 1];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        if (base + k < n) a[base + k] = e;
+        e += v[k];
+    }
+    if (t == 0) a[n] = total;
+    __syncthreads();
+}
+
+// The smoother's coloring of a level of n <= kSmallLevel rows in one CTA and
+// one launch: Eq. 5.1's strength set S (k_strength51's row logic: counts, a
+// scan, the columns), T, the entries of S^T that S lacks (counts, a scan,
+// a scatter), the degrees |S_i| + |T_i|, the JP rounds of k_jp_small, and the
+// rows grouped by color, index-ascending within a color.  The same S, keys
+// and rounds as the multi-launch path, so the same colors and order.  info[0]
+// receives the color count, info[1 .. ncolors + 1] the color offsets.
+template <int G>
+__global__ void __launch_bounds__(kSmallLevel / 4) k_color_small(int n, const int *rowptr, const int *col,
+                                                                const double *val, double theta, uint32_t hbase,
+                                                                double *thr, int *srow, int *scol, int *trow,
+                                                                int *tcol, int *deg, unsigned long long *state,
+                                                                int *color, int *rows, int *info) {
+    __shared__ int rem, mx, run;
+    __shared__ int cnt[kSmallLevel / 4 + 1];
+    int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < n; i += nt) srow[i] = strength51_row(i, rowptr, col, val, theta, nullptr, nullptr, thr);
+    __syncthreads();
+    cta_scan_small(srow, n);
+    for (int i = t; i < n; i += nt) strength51_row(i, rowptr, col, val, theta, srow, scol, thr);
+    for (int i = t; i < n; i += nt) trow[i] = 0;
+    __syncthreads();
+    for (int i = t; i < n; i += nt)
+        for (int p = srow[i]; p < srow[i + 1]; p++) {
+            int j = scol[p];
+            if (!row_has(srow, scol, j, i)) atomicAdd(&trow[j], 1);
+        }
+    __syncthreads();
+    cta_scan_small(trow, n);
+    for (int i = t; i < n; i += nt) deg[i] = trow[i];   // scatter cursors
+    __syncthreads();
+    for (int i = t; i < n; i += nt)
+        for (int p = srow[i]; p < srow[i + 1]; p++) {
+            int j = scol[p];
+            if (!row_has(srow, scol, j, i)) tcol[atomicAdd(&deg[j], 1)] = i;
+        }
+    __syncthreads();
+    for (int i = t; i < n; i += nt) {
+        deg[i] = (srow[i + 1] - srow[i]) + (trow[i + 1] - trow[i]);
+        state[i] = kUncolored;
+    }
+    if (t == 0) {
+        rem = n;
+        mx = 0;
+    }
+    __syncthreads();
+    JpGraph g{srow, scol, trow, tcol, deg};
+    int lane = t % G, per = nt / G;
+    for (unsigned r = 0; r < (unsigned)n + 8; r++) {
+        int left = rem;
+        __syncthreads();
+        if (left == 0) break;
+        for (int v0 = 0; v0 < n; v0 += per) {   // uniform over the block
+            int i = v0 + t / G;
+            int c = jp_vertex<G, kJpPreSmall>(i, i < n, lane, g, hbase, state, r);
+            if (i < n && lane == 0 && c >= 0) {
+                atomicSub(&rem, 1);
+                atomicMax(&mx, c);
+            }
+        }
+        __syncthreads();
+    }
+    int nc = n ? mx + 1 : 0;
+    for (int i = t; i < n; i += nt) color[i] = (int)(unsigned)state[i];
+    if (t == 0) run = 0;
+    __syncthreads();
+    // color c's rows in index order: each thread's four consecutive rows, a
+    // scan of the per-thread counts, then the scatter after the running offset
+    for (int c = 0; c < nc; c++) {
+        int base = 4 * t, f = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (base + k < n && color[base + k] == c) f |= 1 << k;
+        cnt[t] = __popc(f);
+        __syncthreads();
+        cta_scan_small(cnt, nt);
+        int off = run + cnt[t];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (f & (1 << k)) rows[off++] = base + k;
+        if (t == 0) info[1 + c] = run;
+        __syncthreads();
+        if (t == 0) run += cnt[nt];
+        __syncthreads();
+    }
+    if (t == 0) {
+        info[0] = nc;
+        info[1 + nc] = run;
+    }
 }
 
 // One round of the level sets of natural-order block ILU(0) over a worklist
@@ -2898,6 +3037,57 @@ int level_sets(const SymGraph &G, DVec<int> &level, cudaStream_t s) {
     return read_int(counters.p + 3, s) + 1;
 }
 
+// The smoother's coloring of a level of at most kSmallLevel rows in one
+// launch (k_color_small) and one read-back: the colors, the color offsets and
+// the rows grouped by color, as the strength / graph / JP / ordering launches
+// of the larger levels give them.
+int color_small(cpr_handle *h, const DCsr &A, int level, DVec<int> &color, std::vector<int> &off, DVec<int> &rows,
+                cudaStream_t s) {
+    int n = A.n;
+    size_t ub = std::max<size_t>((size_t)A.nnz, 1);   // S holds at most A's entries
+    DVec<double> thr;
+    DVec<int> srow, scol, trow, tcol, deg, info;
+    DVec<unsigned long long> state;
+    thr.alloc(n, s);
+    srow.alloc(n + 1, s);
+    scol.alloc(ub, s);
+    trow.alloc(n + 1, s);
+    tcol.alloc(ub, s);
+    deg.alloc(n, s);
+    state.alloc(n, s);
+    info.alloc(n + 2, s);
+    color.alloc(n, s);
+    rows.alloc(n, s);
+    uint32_t hb = hash_base(h->opt.seed, 0, level);
+    // lanes per vertex as in the one-CTA JP rounds
+    int lanes = 1;
+    while (lanes < 8 && 2L * lanes * n <= kSmallLevel / 4) lanes <<= 1;
+    auto go = [&](auto kern) {
+        kern<<<1, kSmallLevel / 4, 0, s>>>(n, A.rowptr.p, A.col.p, A.val.p, h->opt.theta_color, hb, thr.p, srow.p,
+                                           scol.p, trow.p, tcol.p, deg.p, state.p, color.p, rows.p, info.p);
+        CK_LAUNCH();
+    };
+    switch (lanes) {
+    case 1: go(k_color_small<1>); break;
+    case 2: go(k_color_small<2>); break;
+    case 4: go(k_color_small<4>); break;
+    default: go(k_color_small<8>); break;
+    }
+    int head[64];
+    int m = std::min(n + 2, 64);
+    CK(cudaMemcpyAsync(head, info.p, sizeof(int) * m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int nc = head[0];
+    off.assign(nc + 1, 0);
+    if (nc + 2 <= m) {
+        for (int c = 0; c <= nc; c++) off[c] = head[1 + c];
+    } else {   // more colors than the first read-back held
+        CK(cudaMemcpyAsync(off.data(), info.p + 1, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return nc;
+}
+
 // Rows grouped by color, index-ascending within a color.
 void rows_by_color(int n, const int *color, int ncolors, std::vector<int> &off, DVec<int> &rows,
                    cudaStream_t s) {
@@ -3862,6 +4052,14 @@ void build_preconditioner(cpr_handle *h) {
             Nvtx r("level coloring");
             side.mark("idle");
             Level &L = h->lev[l];
+            if (n <= kSmallLevel && !(h->opt.coloring == 1 && n <= h->opt.coloring_rows)) {
+                // a small level (JP): the whole coloring in one launch
+                L.ncolors = color_small(h, L.A, l, L.color, L.color_off, L.rows_by_color, s);
+                CK(cudaEventRecord(h->ev_color[l], s));
+                side.mark("c_small");
+                side.finished(l);
+                return;
+            }
             // the strength pattern is a subset of A_l's: at most nnz(A_l) entries
             long ub = L.A.nnz;
             DVec<double> thr;   // each row's threshold, from the count pass to the fill pass
