@@ -185,9 +185,11 @@ __global__ void k_restrict_first(int nb, const int *order, const double *v_base,
     }
     pdl_wait();
     pdl_trigger();
-    if (!active || (done && *done)) return;
+    int dn = stop_flag(done);
+    if (!active) return;
     const double *v = v_base + (size_t)step_of(jptr) * ld + 3 * (size_t)i;
     T r = (w0 * (T)v[0] + w1 * (T)v[1]) + w2 * (T)v[2];
+    if (dn) return;
     rp[t] = r;
     if (mine) sc[t] = r * di;
     else x[t] = (T)0;
@@ -224,7 +226,7 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
     }
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     // v's three entries of this row are loaded with the gathers, not after them
     bool lead = active && lane == 0;
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
@@ -258,6 +260,7 @@ __global__ void k_prolong_resid(int nb, const int *__restrict__ rowptr, const in
         a1 += __shfl_xor_sync(0xffffffffu, a1, o, G);
         a2 += __shfl_xor_sync(0xffffffffu, a2, o, G);
     }
+    if (dn) return;
     if (lead) {
         r[3 * (size_t)row] = (T)v0 - a0;
         r[3 * (size_t)row + 1] = (T)v1 - a1;
@@ -374,8 +377,10 @@ __global__ void k_smooth_first(int n, int c0, int c1, const T *b, const T *dinv,
     T di = mine ? dinv[t] : (T)0;
     pdl_wait();
     pdl_trigger();
-    if (t >= n || (done && *done)) return;
-    if (mine) sc[t] = b[t] * di;
+    int dn = stop_flag(done);
+    T bt = mine && t < n ? b[t] : (T)0;
+    if (t >= n || dn) return;
+    if (mine) sc[t] = bt * di;
     else x[t] = (T)0;
 }
 
@@ -396,7 +401,7 @@ __global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__rest
     T di = active ? dinv[i] : (T)0;
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     // every read of the pending range goes to sp, so its commit into x can
     // wait until the row's gathers are issued: a commit store ahead of them
     // would hold them back by a round trip (the compiler cannot reorder loads
@@ -407,6 +412,7 @@ __global__ void k_smooth_color(int c0, int c1, int p0, int p1, const int *__rest
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
+    if (dn) return;
     if (active && lane == 0) sc[i] = (bi - s) * di;
     if (tid < np) x[p0 + tid] = cv;
     for (long t = tid + nthr; t < np; t += nthr) x[p0 + t] = sp[p0 + t];
@@ -429,7 +435,7 @@ __global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ ro
     T dg = active ? diag[i] : (T)0;
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     // the row's own b_i and x_i are loaded with its gathers, not after them
     bool lead = active && lane == 0;
     T bi = lead ? b[i] : (T)0;
@@ -437,6 +443,7 @@ __global__ void k_resid_commit(int n, int p0, int p1, const int *__restrict__ ro
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
+    if (dn) return;
     if (lead) r[i] = bi - s - dg * xi;
     // commit after every read of this kernel's own rows is done is not
     // guaranteed across CTAs, so readers above take the pending range from sp
@@ -458,12 +465,13 @@ __global__ void k_transfer(int n, const int *__restrict__ rowptr, const int *__r
     rp.load(rowptr, col, val, i, lane, active);
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     bool lead = active && lane == 0;
     T yi = lead && add ? y[i] : (T)0;   // loaded with the gathers
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return xval(x, sp, p0, p1, j); });
     s = group_sum(s, G);
+    if (dn) return;
     if (lead) y[i] = add ? yi + s : s;
 }
 
@@ -486,10 +494,11 @@ __global__ void k_transfer_first(int n, const int *__restrict__ rowptr, const in
     T di = mine ? dinv[i] : (T)0;
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     T s = 0;
     if (active) s = rp.dot(col, val, lane, [&](int j) { return x[j]; });
     s = group_sum(s, G);
+    if (dn) return;
     if (active && lane == 0) {
         y[i] = s;
         if (mine) sc[i] = s * di;
@@ -505,8 +514,10 @@ __global__ void k_commit_natural(int n, const int *order, const T *x, const T *s
     int o = t < n ? order[t] : 0;
     pdl_wait();
     pdl_trigger();
-    if (t >= n || (done && *done)) return;
-    out[o] = xval(x, sp, p0, p1, t);
+    int dn = stop_flag(done);
+    T v = t < n ? xval(x, sp, p0, p1, t) : (T)0;
+    if (t >= n || dn) return;
+    out[o] = v;
 }
 
 // Coarsest level: x = A_L^-1 b, one warp per row of the row-major inverse.
@@ -524,7 +535,7 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b
     }
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);
     double s = 0.0;
     if (i < n) {
 #pragma unroll
@@ -533,6 +544,7 @@ __global__ void k_coarse_solve(int n, const double *__restrict__ inv, const T *b
         for (int j = lane + 32 * kPreC; j < n; j += 32) s += inv[(size_t)i * n + j] * (double)b[j];
     }
     s = group_sum(s, 32);
+    if (dn) return;
     if (i < n && lane == 0) x[i] = (T)s;
 }
 

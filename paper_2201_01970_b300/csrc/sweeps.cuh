@@ -36,6 +36,13 @@ __device__ __forceinline__ T group_sum(T v, int G) {
 // before the current kernel has completed when a prologue runs.  Without the
 // launch attribute both instructions are no-ops.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// The step's stop flag, read after the wait together with a kernel's
+// gathers and tested only before its first store: a test right after the wait
+// would hold every gather back by the flag's round trip.  (A stopped step's
+// kernels then load what they would have used, all in bounds, and store
+// nothing.)
+__device__ __forceinline__ int stop_flag(const int *done) { return done ? *done : 0; }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Forward substitution for the color of positions [c0, c0 + cnt), in place:
@@ -68,7 +75,7 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
     }
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);   // tested before the first store, not ahead of the gathers
     if constexpr (G == 1) {
         if (!active) return;
         T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
@@ -91,6 +98,7 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
             s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
             s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
         }
+        if (dn) return;
         y[3 * (size_t)i] = s0;
         y[3 * (size_t)i + 1] = s1;
         y[3 * (size_t)i + 2] = s2;
@@ -122,6 +130,7 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
         a0 = group_sum(a0, G);
         a1 = group_sum(a1, G);
         a2 = group_sum(a2, G);
+        if (dn) return;
         if (lead) {
             y[3 * (size_t)i] = yi0 - a0;
             y[3 * (size_t)i + 1] = yi1 - a1;
@@ -166,7 +175,7 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
     }
     pdl_wait();
     pdl_trigger();
-    if (done && *done) return;
+    int dn = stop_flag(done);   // tested before the first store, not ahead of the gathers
     // where the result goes, and the V-cycle's part of it, are loaded before
     // the gathers: the stores at the end then wait on nothing
     double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
@@ -228,6 +237,7 @@ __global__ void k_bilu_bwd(int c0, int cnt, const int *__restrict__ ur,
     T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
     T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
     T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
+    if (dn) return;
     y[3 * (size_t)i] = z0;
     y[3 * (size_t)i + 1] = z1;
     y[3 * (size_t)i + 2] = z2;
