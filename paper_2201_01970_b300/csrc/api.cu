@@ -467,6 +467,7 @@ void cpr_destroy(cpr_handle *h) {
         if (h->ev_b[k]) cudaEventDestroy(h->ev_b[k]);
     }
     h->pinned = nullptr;
+    h->pinned_dev_flags = nullptr;
     cudaStream_t side = h->side, lu = h->lu_stream;
     delete h;  // DVec destructors free on the stream each buffer was allocated on
     if (s) cudaStreamSynchronize(s);

@@ -294,6 +294,7 @@ struct cpr_handle {
     cpr::DVec<float> ep32;
     cpr::DVec<double> dev_b, dev_x; // device copies of host b / x
     double *pinned = nullptr;       // pinned host scalars
+    int *pinned_dev_flags = nullptr; // device address of the two step-flag slots in pinned (at pinned + 8)
     cpr::DVec<int> err;             // device error flag
     // resetup = 1: the in-place numeric refresh of B (numeric_refresh) and its graph
     bool nr_ready = false;          // the last full setup kept what the refresh needs

@@ -45,7 +45,7 @@ struct ScalLayout {
     __host__ __device__ int size() const { return norm0() + 5; }
 };
 // Device ints: [0] step j, [1] done, [2] steps in this cycle, [3] breakdown.
-enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_CNT_DOT = 5, I_CNT_UPD = 6, I_COUNT = 8 };
+enum { I_J = 0, I_DONE = 1, I_K = 2, I_BREAK = 3, I_ZERO = 4, I_CNT_DOT = 5, I_CNT_UPD = 6, I_SEQ = 7, I_COUNT = 8 };
 
 
 constexpr int kPre = 4;   // row entries per lane loaded before the dependency wait
@@ -1001,9 +1001,20 @@ __global__ void __launch_bounds__(kBlock) k_cgs_update_givens(long N, const doub
 }
 
 // V_{j+1} = w / h_{j+1,j} (after k_givens advanced the step index to j+1).
+// The step's flags (di[0 .. 3]: step index, stop, steps done, breakdown) also
+// go to the host: into slot (seq & 1) of two page-locked slots, seq counting
+// the steps launched in this cycle, stopped ones included.  Written here, at
+// the end of every step graph, they spare a copy between the step graphs.
 __global__ void k_next_basis(long N, const double *w, double *V, const double *sc, int m,
-                             const int *di) {
+                             int *di, int *flags_host) {
     pdl_wait();
+    if (flags_host && blockIdx.x == 0 && threadIdx.x == 0) {
+        int q = di[I_SEQ];
+        int *f = flags_host + 4 * (q & 1);
+        for (int k = 0; k < 4; k++) f[k] = di[k];
+        __threadfence_system();
+        di[I_SEQ] = q + 1;
+    }
     if (di[I_DONE]) return;
     ScalLayout L{m};
     double s = sc[L.inv_hn()];
@@ -1035,6 +1046,7 @@ __global__ void k_cycle_start_scal(const double *part, int nblk, double *sc, int
     di[I_BREAK] = isfinite(beta) ? 0 : 1;
     di[I_DONE] = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
     di[I_ZERO] = 0;
+    di[I_SEQ] = 0;
 }
 
 __global__ void k_scale_into(long N, const double *r, double *v, const double *sc, int m) {
@@ -1599,7 +1611,13 @@ void ensure_workspace(cpr_handle *h) {
     if (h->opt.precond_fp32 && h->t32a.n != (size_t)N) h->t32a.alloc(N, s);
     if (h->opt.precond_fp32 && h->ep32.n != (size_t)h->nb) h->ep32.alloc(h->nb, s);
     if (!h->opt.precond_fp32 && h->ep64.n != (size_t)h->nb) h->ep64.alloc(h->nb, s);
-    if (!h->pinned) CK(cudaMallocHost((void **)&h->pinned, 64 * sizeof(double)));
+    if (!h->pinned) {
+        CK(cudaMallocHost((void **)&h->pinned, 64 * sizeof(double)));
+        // the step kernels write their flags into these page-locked slots directly
+        void *d = nullptr;
+        CK(cudaHostGetDevicePointer(&d, h->pinned, 0));
+        h->pinned_dev_flags = reinterpret_cast<int *>(reinterpret_cast<double *>(d) + 8);
+    }
     for (auto &e : h->step_done)
         if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
@@ -1903,7 +1921,7 @@ void record_step(cpr_handle *h) {
                h->red.p + (size_t)kCgsDotBlocks * ldp, di + I_CNT_UPD, sc, m, di);
     prof_end(h);
     launch_pdl(pdl, k_next_basis, grid_for(N, kBlock, 148 * 8), kBlock, s, N, (const double *)h->wv.p, h->V.p,
-               (const double *)sc, m, (const int *)di);
+               (const double *)sc, m, di, h->pinned_dev_flags);
 }
 
 // (Re)capture the step graphs when B, the workspace or profiling changed.
@@ -2109,7 +2127,7 @@ int fgmres_advance(cpr_handle *h, bool block) {
                 int j = F.launched;
                 CK(cudaGraphLaunch(h->sg[j & 1].exec, s));
                 count_launches(h->sg[j & 1].kernels);
-                CK(cudaMemcpyAsync(pin + 4 * (j & 1), di, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+                // the graph's last kernel has written step j's flags into pin slot j & 1
                 CK(cudaEventRecord(h->step_done[j & 1], s));
                 F.launched = j + 1;
                 continue;
