@@ -1459,18 +1459,30 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
     // with dependent launch on B300 (241 -> 268 us per application at
     // 128x128x32), FP32 sweeps faster (90.6 -> 86.1 us)
     bool pdl = h->opt.pdl && sizeof(T) == 4;
-    for (int c = 1; c < B.ncolors; c++) {
+    // the highest non-empty color has no upper neighbours (L and U split by
+    // color, and same-colored rows are never adjacent), so its forward and
+    // backward steps run as one launch
+    int last = B.ncolors - 1;
+    while (last > 0 && B.color_off[last + 1] == B.color_off[last]) last--;
+    for (int c = 1; c < last; c++) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
         launch_pdl(pdl, k_bilu_fwd<T, G>, grid_for((long)cnt * G, kBlock), kBlock, s, B.color_off[c], cnt,
-                 B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), y, done);
+                   B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), y, done);
     }
-    for (int c = B.ncolors - 1; c >= 0; c--) {
+    if (last >= 0) {
+        int cnt = B.color_off[last + 1] - B.color_off[last];
+        if (cnt)
+            launch_pdl(pdl, k_bilu_last<T, G>, grid_for((long)cnt * G, kBlock), kBlock, s, B.color_off[last], cnt,
+                       B.Lrowptr.p, B.Lcol.p, Vals<T>::Lv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base,
+                       ld, jptr, done);
+    }
+    for (int c = last - 1; c >= 0; c--) {
         int cnt = B.color_off[c + 1] - B.color_off[c];
         if (!cnt) continue;
         launch_pdl(pdl, k_bilu_bwd<T, G>, grid_for((long)cnt * G, kBlock), kBlock, s, B.color_off[c], cnt,
-                 B.Urowptr.p, B.Ucol.p, Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base, ld,
-                 jptr, done);
+                   B.Urowptr.p, B.Ucol.p, Vals<T>::Uv(h), Vals<T>::Dv(h), y, ep, B.rows_by_color.p, out_base, ld,
+                   jptr, done);
     }
 }
 

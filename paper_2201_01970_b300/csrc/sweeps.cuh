@@ -45,40 +45,17 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ int stop_flag(const int *done) { return done ? *done : 0; }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Forward substitution for the color of positions [c0, c0 + cnt), in place:
-// y_i = r_i - sum_{lower} L_ij y_j (everything in BILU positions).  G lanes
-// share a block row (G = 1: one thread, blocks in order).
-template <class T, int G>
-__global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
-                           const int *__restrict__ lc, const T *__restrict__ lv, T *y,
-                           const int *done) {
-    constexpr int kPreB = G == 1 ? 2 : 1;   // blocks per lane loaded before the wait
-    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long t = tid / G;
-    int lane = (int)(tid % G);
-    bool active = t < cnt;
-    int i = c0 + (int)t;
-    int e0 = 0, e1 = 0;
-    if (active) {
-        e0 = lr[i];
-        e1 = lr[i + 1];
-    }
-    int cj[kPreB];
-    T Lp[kPreB][9];
-#pragma unroll
-    for (int u = 0; u < kPreB; u++) {
-        int p = e0 + lane + u * G;
-        bool in = p < e1;
-        cj[u] = in ? lc[p] : 0;
-#pragma unroll
-        for (int k = 0; k < 9; k++) Lp[u][k] = in ? lv[9 * (size_t)p + k] : (T)0;
-    }
-    pdl_wait();
-    pdl_trigger();
-    int dn = stop_flag(done);   // tested before the first store, not ahead of the gathers
+// Forward substitution of row i: y_i - sum_{lower} L_ij y_j, left in
+// (s0, s1, s2) on the row's lead lane (G == 1: its thread).  The first kPreB
+// blocks of each lane (columns cj, values Lp) were loaded before the wait.
+template <class T, int G, int kPreB>
+__device__ __forceinline__ void bilu_fwd_row(bool active, int lane, int i, int e0, int e1,
+                                             const int (&cj)[kPreB], const T (&Lp)[kPreB][9],
+                                             const int *__restrict__ lc, const T *__restrict__ lv, const T *y,
+                                             T &s0, T &s1, T &s2) {
     if constexpr (G == 1) {
         if (!active) return;
-        T s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
+        s0 = y[3 * (size_t)i], s1 = y[3 * (size_t)i + 1], s2 = y[3 * (size_t)i + 2];
 #pragma unroll
         for (int u = 0; u < kPreB; u++)
             if (e0 + u < e1) {
@@ -98,10 +75,6 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
             s1 -= L[3] * y0 + L[4] * y1 + L[5] * y2;
             s2 -= L[6] * y0 + L[7] * y1 + L[8] * y2;
         }
-        if (dn) return;
-        y[3 * (size_t)i] = s0;
-        y[3 * (size_t)i + 1] = s1;
-        y[3 * (size_t)i + 2] = s2;
     } else {
         // G lanes share the row: lane sums of L_ij y_j, then one group sum;
         // the row's own y_i is loaded with the gathers, not after them
@@ -130,13 +103,103 @@ __global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
         a0 = group_sum(a0, G);
         a1 = group_sum(a1, G);
         a2 = group_sum(a2, G);
-        if (dn) return;
-        if (lead) {
-            y[3 * (size_t)i] = yi0 - a0;
-            y[3 * (size_t)i + 1] = yi1 - a1;
-            y[3 * (size_t)i + 2] = yi2 - a2;
-        }
+        s0 = yi0 - a0;
+        s1 = yi1 - a1;
+        s2 = yi2 - a2;
     }
+}
+
+// The first blocks of each lane's share of row i of L (or U), loaded before the wait.
+template <class T, int G, int kPreB>
+__device__ __forceinline__ void bilu_pre(int e0, int e1, int lane, const int *__restrict__ c,
+                                         const T *__restrict__ v, int (&cj)[kPreB], T (&Vp)[kPreB][9]) {
+#pragma unroll
+    for (int u = 0; u < kPreB; u++) {
+        int p = e0 + lane + u * G;
+        bool in = p < e1;
+        cj[u] = in ? c[p] : 0;
+#pragma unroll
+        for (int k = 0; k < 9; k++) Vp[u][k] = in ? v[9 * (size_t)p + k] : (T)0;
+    }
+}
+
+// Forward substitution for the color of positions [c0, c0 + cnt), in place:
+// y_i = r_i - sum_{lower} L_ij y_j (everything in BILU positions).  G lanes
+// share a block row (G = 1: one thread, blocks in order).
+template <class T, int G>
+__global__ void k_bilu_fwd(int c0, int cnt, const int *__restrict__ lr,
+                           const int *__restrict__ lc, const T *__restrict__ lv, T *y,
+                           const int *done) {
+    constexpr int kPreB = G == 1 ? 2 : 1;   // blocks per lane loaded before the wait
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    bool active = t < cnt;
+    int i = c0 + (int)t;
+    int e0 = 0, e1 = 0;
+    if (active) {
+        e0 = lr[i];
+        e1 = lr[i + 1];
+    }
+    int cj[kPreB];
+    T Lp[kPreB][9];
+    bilu_pre<T, G, kPreB>(e0, e1, lane, lc, lv, cj, Lp);
+    pdl_wait();
+    pdl_trigger();
+    int dn = stop_flag(done);   // tested before the first store, not ahead of the gathers
+    T s0 = 0, s1 = 0, s2 = 0;
+    bilu_fwd_row<T, G, kPreB>(active, lane, i, e0, e1, cj, Lp, lc, lv, y, s0, s1, s2);
+    if (dn || !active || lane != 0) return;
+    y[3 * (size_t)i] = s0;
+    y[3 * (size_t)i + 1] = s1;
+    y[3 * (size_t)i + 2] = s2;
+}
+
+// The highest color in one launch: its rows have no higher-color (upper)
+// neighbours, so the backward step is z_i = U_ii^-1 y_i right after the
+// forward one, with the same operations as the two kernels apart.  Writes z
+// into y and, plus Pi_P e_P when ep != nullptr, into out (as k_bilu_bwd).
+template <class T, int G>
+__global__ void k_bilu_last(int c0, int cnt, const int *__restrict__ lr, const int *__restrict__ lc,
+                            const T *__restrict__ lv, const T *__restrict__ dinv, T *y, const T *ep,
+                            const int *__restrict__ border, double *out_base, long ld, const int *jptr,
+                            const int *done) {
+    constexpr int kPreB = G == 1 ? 2 : 1;
+    long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long t = tid / G;
+    int lane = (int)(tid % G);
+    bool active = t < cnt;
+    bool lead = active && lane == 0;
+    int i = c0 + (int)t;
+    int e0 = 0, e1 = 0, bi = 0;
+    if (active) {
+        e0 = lr[i];
+        e1 = lr[i + 1];
+    }
+    if (lead) bi = border[i];
+    T D[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) D[k] = lead ? dinv[9 * (size_t)i + k] : (T)0;
+    int cj[kPreB];
+    T Lp[kPreB][9];
+    bilu_pre<T, G, kPreB>(e0, e1, lane, lc, lv, cj, Lp);
+    pdl_wait();
+    pdl_trigger();
+    int dn = stop_flag(done);
+    double *out = out_base + (size_t)step_of(jptr) * ld + 3 * (size_t)bi;
+    double e0v = lead && ep ? (double)ep[i] : 0.0;
+    T s0 = 0, s1 = 0, s2 = 0;
+    bilu_fwd_row<T, G, kPreB>(active, lane, i, e0, e1, cj, Lp, lc, lv, y, s0, s1, s2);
+    if (dn || !lead) return;
+    T z0 = D[0] * s0 + D[1] * s1 + D[2] * s2;
+    T z1 = D[3] * s0 + D[4] * s1 + D[5] * s2;
+    T z2 = D[6] * s0 + D[7] * s1 + D[8] * s2;
+    y[3 * (size_t)i] = z0;
+    y[3 * (size_t)i + 1] = z1;
+    y[3 * (size_t)i + 2] = z2;
+    out[0] = (double)z0 + e0v;
+    out[1] = (double)z1;
+    out[2] = (double)z2;
 }
 
 // Backward substitution for the color of positions [c0, c0 + cnt), in place:
