@@ -4199,6 +4199,10 @@ void build_preconditioner(cpr_handle *h) {
         Lv.gP = lanes_for((double)Lv.Pp.nnz / n, n, 1L << 16);
         Lv.gR = lanes_for((double)Lv.Rp.nnz / std::max(1, Lv.Rp.n), Lv.Rp.n, 1L << 18);
         Lv.bs = 256;
+        if (!f32) {   // FP64: an FP64 instruction costs its issue slot whatever its active lanes
+            if (n >= 4096 && Lv.gA >= 8) Lv.gA /= 2;
+            Lv.gP = std::min(Lv.gP, 4);
+        }
         // a schedule the autotuner chose for a level of these sizes takes precedence
         auto it = h->sched.find({Lv.A.n, (long)Lv.A.nnz});
         if (it != h->sched.end()) {
