@@ -40,9 +40,9 @@ MU = 30
 # kernel the line rates, from one ncu capture of the build named, at the
 # workload named; a kernel changed since then has no entry (traffic null).
 NCU_TRAFFIC = {
-    ("k_smooth_color", "128x128x32"): {"bytes": 2.525e6,
+    ("k_smooth_color", "128x128x32"): {"bytes": 2.5246e6,
                                        "source": "mean DRAM bytes of the 56 color launches of one eager V-cycle, "
-                                                 "ncu capture of the commit eb27359 build, cold caches"},
+                                                 "ncu capture of the commit 1246587 build, cold caches"},
     ("k_sell_spmv", "128x128x32"): {"bytes": 302.96e6 + 10.15e6,
                                     "source": "ncu capture of one k_sell_spmv launch of the commit 1298109 build"},
 }
