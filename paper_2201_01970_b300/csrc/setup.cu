@@ -3678,9 +3678,13 @@ class SideWorker {
         int dev = 0;
         CK(cudaGetDevice(&dev));
         if (!h->side) {
+            // the side chain (BILU(0) values, the level colorings) has slack
+            // behind the main AMG chain, so it takes no priority over it: at
+            // the highest priority 20 warm setups of 128x128x32 took 7.84 and
+            // 8.39 ms (median; up to 13.6), at this one 7.72 and 7.70 (up to 8.4)
             int lo = 0, hi = 0;
             CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
-            CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi));
+            CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo));
         }
         clk_.s = h->side;
         clk_.tag = " side:";
