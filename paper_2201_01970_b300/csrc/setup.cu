@@ -693,6 +693,18 @@ __global__ void k_state_to_color(int n, const unsigned long long *state, int *co
     if (i < n) color[i] = (int)(unsigned)state[i];
 }
 
+// Whether row j of S holds column i, for the one-CTA coloring: a row of up
+// to 64 entries is scanned with independent loads (one round trip to L2)
+// instead of a binary search's chain of dependent ones; longer rows search.
+__device__ __forceinline__ bool row_has_short(const int *sr, const int *sc, int j, int i) {
+    int lo = sr[j], hi = sr[j + 1];
+    if (hi - lo > 64) return row_has(sr, sc, j, i);
+    bool f = false;
+#pragma unroll 8
+    for (int p = lo; p < hi; p++) f |= sc[p] == i;
+    return f;
+}
+
 // Exclusive scan of a[0 .. n) in place, a[n] = the total, by one CTA of
 // kSmallLevel / 4 threads, each taking four consecutive entries (n <= kSmallLevel).
 __device__ void cta_scan_small(int *a, int n) {
@@ -756,7 +768,7 @@ __global__ void __launch_bounds__(kSmallLevel / 4) k_color_small(int n, const in
     for (int i = t; i < n; i += nt)
         for (int p = srow[i]; p < srow[i + 1]; p++) {
             int j = scol[p];
-            if (!row_has(srow, scol, j, i)) atomicAdd(&trow[j], 1);
+            if (!row_has_short(srow, scol, j, i)) atomicAdd(&trow[j], 1);
         }
     __syncthreads();
     cta_scan_small(trow, n);
@@ -765,7 +777,7 @@ __global__ void __launch_bounds__(kSmallLevel / 4) k_color_small(int n, const in
     for (int i = t; i < n; i += nt)
         for (int p = srow[i]; p < srow[i + 1]; p++) {
             int j = scol[p];
-            if (!row_has(srow, scol, j, i)) tcol[atomicAdd(&deg[j], 1)] = i;
+            if (!row_has_short(srow, scol, j, i)) tcol[atomicAdd(&deg[j], 1)] = i;
         }
     __syncthreads();
     for (int i = t; i < n; i += nt) {
