@@ -2005,8 +2005,8 @@ void ensure_step_graphs(cpr_handle *h) {
 
 // Flexible GMRES(m), right-preconditioned with B (Alg. 2): CGS Arnoldi, Givens
 // rotations on the device, stop on |g_{j+1}| < rtol ||r_0|| or h_{j+1,j} = 0,
-// true residual after every cycle.  The host reads one flag per step and one
-// norm per cycle.  It runs as a state machine (FgmresState): each call of
+// true residual after every cycle.  The host reads each step's flags from the
+// page-locked slot its last kernel wrote, and one norm per cycle.  It runs as a state machine (FgmresState): each call of
 // fgmres_advance issues what can be issued and, unless `block`, returns
 // instead of waiting on the device, so one host thread can drive many solves.
 // Blocking or not, the same work is launched in the same order.
