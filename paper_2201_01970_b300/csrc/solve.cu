@@ -1490,7 +1490,11 @@ void bilu_solve(cpr_handle *h, T *y, const T *ep, double *out_base, long ld, con
 #define CPR_SPMV_LANES 1
 #endif
 constexpr int kSpmvLanes = CPR_SPMV_LANES;  // outer BSR SpMV (lanes per block row)
-constexpr int kResidLanes = 2;     // second residual
+// second residual: lanes per block row (FP32 2, FP64 1: one FP64 instruction
+// costs its issue slot whatever its active lanes; FP64 solve at 128x128x32
+// 32.54 -> 32.23 ms with 1 lane, FP32 22.31 -> 22.39 ms)
+template <class T>
+constexpr int kResidLanes = sizeof(T) == 4 ? 2 : 1;
 
 template <class T>
 void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, double *z_base,
@@ -1518,9 +1522,9 @@ void apply_B_t(cpr_handle *h, const double *v_base, long v_ld, const int *jptr, 
     }
     prof_end(h);
     // r = v - A Pi_P e_P
-    long threads = (long)nb * kResidLanes;
+    long threads = (long)nb * kResidLanes<T>;
     prof_begin(h, CPR_PROF_RESID2);
-    launch_b(h, k_prolong_resid<T, kResidLanes>, (unsigned)((threads + kBlock - 1) / kBlock), kBlock, s, nb,
+    launch_b(h, k_prolong_resid<T, kResidLanes<T>>, (unsigned)((threads + kBlock - 1) / kBlock), kBlock, s, nb,
              h->c0rowptr.p, h->c0col.p, Vals<T>::c0(h), Vals<T>::ep(h), h->bilu.rows_by_color.p, v_base, v_ld,
              jptr, Vals<T>::tmp(h), done);
     prof_end(h);
